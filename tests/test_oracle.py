@@ -1,0 +1,324 @@
+"""Pins for the FP64 oracle against what the paper and the mathematics fix.
+
+Every test here runs on the CPU only.  None of them compares the oracle with
+itself: they use independent quadrature, analytic limits, lattice constants,
+the paper's printed results, brute-force finite differences and invariances.
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+from scipy.integrate import quad
+
+import oracle as o
+from workloads import configs as C
+from workloads import geometry as G
+
+GOLDEN = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "paper_values.json")))
+
+
+def _phi_by_quadrature(r, a, xi):
+    """Inverse 3-D Fourier transform of j0^2(ka)(1 - e^{-k^2/4xi^2})/k^2 (the real-space
+    share of Eq. splitting), computed by numerical quadrature."""
+    def f(k):
+        return (math.sin(k * a) / (k * a)) ** 2 * (1 - math.exp(-k * k / (4 * xi * xi))) / k
+
+    K0 = 60.0
+    i1, _ = quad(lambda k: f(k) * math.sin(k * r), 1e-12, K0, limit=4000, epsabs=1e-14, epsrel=1e-12)
+    i2, _ = quad(f, K0, np.inf, weight="sin", wvar=r, limlst=400)
+    return (i1 + i2) / (2 * math.pi ** 2 * r)
+
+
+@pytest.mark.parametrize("a,xi,r", [(0.5, 0.8, 0.3), (0.5, 0.8, 0.7), (0.5, 0.8, 1.5), (0.5, 0.8, 2.5),
+                                    (0.05, 1.79, 0.04), (0.05, 1.79, 0.3), (0.1, 1.153, 0.15)])
+def test_real_kernel_matches_inverse_transform(a, xi, r):
+    """Eq. psi_Re_1 (with the Heaviside sign read as -1/(4 pi r) + (4a-r)/(16 pi a^2))
+    equals the inverse transform of its Fourier-space definition."""
+    ref = _phi_by_quadrature(r, a, xi)
+    assert abs(o.phi_real(r, a, xi) - ref) <= 1e-8 * max(abs(ref), 1e-3)
+
+
+def test_printed_heaviside_sign_is_wrong():
+    """The sign as printed, -(1/(4 pi r) + (4a-r)/(16 pi a^2)), misses the transform by
+    2(4a-r)/(16 pi a^2): this is the reading recorded for Eq. psi_Re_1."""
+    a, xi, r = 0.5, 0.8, 0.3
+    printed = o.phi_real(r, a, xi) - 2 * (4 * a - r) / (16 * math.pi * a * a)
+    assert abs(printed - _phi_by_quadrature(r, a, xi)) > 0.1
+
+
+@pytest.mark.parametrize("a,xi", [(0.5, 0.8), (0.05, 1.79), (0.1, 7.0)])
+def test_real_kernel_derivative(a, xi):
+    for r in [0.3 * a, 1.3 * a, 2.5 * a, 5 * a, 1.0 / xi]:
+        h = 1e-6 * max(r, 1e-3)
+        fd = (o.phi_real(r + h, a, xi) - o.phi_real(r - h, a, xi)) / (2 * h)
+        assert abs(o.dphi_real(r, a, xi) - fd) <= 1e-6 * max(abs(fd), 1e-2)
+
+
+def test_real_kernel_limits():
+    a = 0.4
+    # xi -> 0: real-space kernel -> M(r) (Sec. II), error O(xi)
+    for r in [0.2, 0.79, 0.81, 1.7, 3.0]:
+        e1 = abs(o.phi_real(r, a, 1e-3) - o.M_free(r, a))
+        e2 = abs(o.phi_real(r, a, 1e-4) - o.M_free(r, a))
+        assert e2 < 0.2 * e1 + 1e-12 and e2 < 1e-4
+    # a -> 0: point-charge Ewald erfc(xi r)/(4 pi r) (Eq. psi_Re_point)
+    for r in [0.3, 1.0, 2.0]:
+        pc = math.erfc(0.9 * r) / (4 * math.pi * r)
+        assert abs(o.phi_real(r, 1e-4, 0.9) - pc) < 1e-8
+    # r -> 0: self term (equation after psi_Re_1).  The wave share is smooth and
+    # even in r, so the slope at 0 is that of M(r) = (4a - r)/(16 pi a^2): -1/(16 pi a^2)
+    for xi in [0.5, 1.5]:
+        for r in [1e-3, 1e-4]:
+            slope = (o.phi_real(r, a, xi) - o.phi_self(a, xi)) / r
+            assert abs(slope + 1 / (16 * math.pi * a * a)) < 50 * r
+    # continuity at r = 2a
+    assert abs(o.phi_real(2 * a * (1 + 1e-9), a, 1.0) - o.phi_real(2 * a * (1 - 1e-9), a, 1.0)) < 1e-8
+    # M(r) continuous at 2a and 1/(4 pi a) at r = 0
+    assert abs(o.M_free(0.0, a) - 1 / (4 * math.pi * a)) < 1e-15
+    assert abs(o.M_free(2 * a - 1e-12, a) - o.M_free(2 * a, a)) < 1e-10
+
+
+def test_madelung_rocksalt():
+    """Rock salt with d > 2a: every pair interacts by plain Coulomb, so
+    psi_alpha = q_alpha/(4 pi eps a) - M_NaCl q_alpha/(4 pi eps d)."""
+    mad = GOLDEN["nacl_madelung_constant"]["value"]
+    for m, xi in [(1, None), (2, 1.3), (2, 2.7)]:
+        s = C.rocksalt(m=m, d=1.0, a=0.3)
+        psi = o.potential(s.x, s.Q, s.box, s.a, s.eps, xi=xi)
+        got = 1.0 / s.a - 4 * math.pi * psi / s.Q
+        assert np.max(np.abs(got - mad)) < 1e-9
+
+
+def _random_neutral(n=40, L=5.0, a=0.3, seed=3):
+    rng = np.random.default_rng(seed)
+    x = rng.uniform(0, L, size=(n, 3))
+    x[1] = x[0] + np.array([0.2, 0.1, 0.0])      # an overlapping pair (r < 2a)
+    q = rng.normal(size=n)
+    q -= q.mean()
+    return x, q, np.array([L, L * 1.1, L * 0.9]), a
+
+
+def test_xi_independence():
+    x, q, box, a = _random_neutral()
+    p1, E1 = o.potential(x, q, box, a, 1.0, xi=0.9, field=True)
+    p2, E2 = o.potential(x, q, box, a, 1.0, xi=2.2, field=True)
+    assert np.max(np.abs(p1 - p2)) < 1e-11 * np.max(np.abs(p1))
+    assert np.max(np.abs(E1 - E2)) < 1e-10 * np.max(np.abs(E1))
+
+
+def test_translation_invariance():
+    x, q, box, a = _random_neutral()
+    p1 = o.potential(x, q, box, a, 1.0)
+    p2 = o.potential(x + np.array([1.234, -7.1, 0.33]), q, box, a, 1.0)
+    assert np.max(np.abs(p1 - p2)) < 1e-12 * np.max(np.abs(p1)) * 10
+
+
+def test_dense_matrix_matches_sums_and_is_spd():
+    x, q, box, a = _random_neutral(n=30)
+    M = o.M_dense(x, box, a, 0.7)
+    assert np.max(np.abs(M - M.T)) < 1e-13 * np.max(np.abs(M))
+    assert np.linalg.eigvalsh(M).min() > 0
+    p = o.potential(x, q, box, a, 0.7)
+    assert np.max(np.abs(M @ q - p)) < 1e-11 * np.max(np.abs(p))
+
+
+def test_large_box_pair_tends_to_free_space():
+    """A neutral pair in a growing box: the periodic M_12 tends to M(r) (Sec. II)
+    up to the O(1/L) image/background correction."""
+    a, r = 0.3, 0.45
+    errs = []
+    for L in [10.0, 20.0, 40.0]:
+        x = np.array([[L / 2, L / 2, L / 2], [L / 2 + r, L / 2, L / 2]])
+        M = o.M_dense(x, [L] * 3, a, 1.0)
+        errs.append(abs((M[0, 0] - M[0, 1]) - (o.M_free(0, a) - o.M_free(r, a))))
+    assert errs[2] < errs[1] < errs[0] and errs[2] < 1e-3
+
+
+def test_saddle_constraint_linearity_and_gmres():
+    s = C.small_system(seed=11, n_bodies=2, level=1, n_ions=5, nrhs=3)
+    M = o.M_dense(s.x, s.box, s.a, s.eps)
+    q, psi = o.solve_dense(s.x, s.body_offsets, s.X, s.Q, s.E0, s.box, s.a, s.eps, M=M)
+    off = s.body_offsets
+    for r in range(3):
+        sums = np.add.reduceat(q[r], off[:-1])
+        assert np.max(np.abs(sums - s.Q)) < 1e-12 * max(1.0, np.abs(s.Q).max())
+        # the solution satisfies Eq. saddle: bead potentials = body potential + r.E0
+        rel = o.relative_positions(s.x, s.X, off, s.box)
+        bid = o.body_index(off)
+        assert np.max(np.abs(M @ q[r] - (psi[r][bid] + rel @ s.E0[r]))) < 1e-10
+    # linearity in E0 (the Q part is common to all three right-hand sides)
+    q0, _ = o.solve_dense(s.x, off, s.X, s.Q, np.zeros(3), s.box, s.a, s.eps, M=M)
+    qz, _ = o.solve_dense(s.x, off, s.X, np.zeros_like(s.Q), s.E0, s.box, s.a, s.eps, M=M)
+    comb = 2.0 * s.E0[0] - 0.5 * s.E0[1]
+    qc, _ = o.solve_dense(s.x, off, s.X, s.Q, comb, s.box, s.a, s.eps, M=M)
+    assert np.max(np.abs(qc - (q0 + 2.0 * qz[0] - 0.5 * qz[1]))) < 1e-10 * np.max(np.abs(qc))
+    # restarted GMRES on the matrix-free operator converges to the dense solution
+    qg, psig, it, res = o.solve_gmres(s.x, off, s.X, s.Q, s.E0[0], s.box, s.a, s.eps, rtol=1e-11, restart=20)
+    assert res <= 1e-11
+    assert np.max(np.abs(qg - q[0])) < 1e-8 * np.max(np.abs(q[0]))
+
+
+def test_body_permutation_symmetry():
+    s = C.small_system(seed=5, n_bodies=2, level=1, n_ions=0)
+    q, psi = o.solve_dense(s.x, s.body_offsets, s.X, s.Q, s.E0[0], s.box, s.a, s.eps)
+    n0 = s.body_offsets[1]
+    xs = np.concatenate([s.x[n0:], s.x[:n0]])
+    offs = np.array([0, s.n - n0, s.n], dtype=np.int32)
+    q2, psi2 = o.solve_dense(xs, offs, s.X[::-1], s.Q[::-1], s.E0[0], s.box, s.a, s.eps)
+    assert np.max(np.abs(np.concatenate([q2[s.n - n0:], q2[:s.n - n0]]) - q)) < 1e-10 * np.abs(q).max()
+    assert np.max(np.abs(psi2[::-1] - psi)) < 1e-10 * np.abs(psi).max()
+
+
+def test_single_sphere_dipole_against_paper():
+    """Sec. IV.A: S -> 4 pi a^3 eps E0 from above (a_eff > a_b), error ~ N^-1/2,
+    about 5% near N = 1000; the dipole is exactly along E0."""
+    coef = GOLDEN["single_sphere_dipole_coefficient"]["value"]
+    errs, ns = [], []
+    for lev in [1, 2, 3]:
+        a = G.min_spacing(G.icosphere(lev)) / 2.0    # beads as large as possible without overlap
+        s = C.config1(level=lev, a=a)
+        q, _ = o.solve_dense(s.x, s.body_offsets, s.X, s.Q, s.E0[0], s.box, s.a, s.eps)
+        S = o.dipoles(s.x, s.X, s.body_offsets, q, s.box)[0]
+        assert abs(S[0]) < 1e-10 * S[2] and abs(S[1]) < 1e-10 * S[2]
+        errs.append(S[2] / coef - 1.0)
+        ns.append(s.n)
+    assert all(e > 0 for e in errs)                       # a_eff > a_b
+    assert errs[0] > errs[1] > errs[2]
+    slope = np.polyfit(np.log(ns), np.log(errs), 1)[0]
+    assert -0.75 < slope < -0.4                           # ~ N^-1/2
+    err_1000 = math.exp(np.polyval(np.polyfit(np.log(ns), np.log(errs), 1), math.log(1000.0)))
+    assert 0.03 < err_1000 < 0.08                         # "about 5% at N ~ 1000"
+    # config-1 sphere (162 beads of radius 0.1) as in the workload
+    s = C.config1()
+    q, _ = o.solve_dense(s.x, s.body_offsets, s.X, s.Q, s.E0[0], s.box, s.a, s.eps)
+    S = o.dipoles(s.x, s.X, s.body_offsets, q, s.box)[0]
+    assert 0.0 < S[2] / coef - 1.0 < 0.3
+
+
+def _energy_of(x, s, M_fn):
+    M = M_fn(x)
+    q, psi = o.solve_dense(x, s.body_offsets, s.X, s.Q, s.E0[0], s.box, s.a, s.eps, M=M)
+    S = o.dipoles(x, s.X, s.body_offsets, q, s.box)
+    return o.energy(s.X, s.Q, psi, S, s.E0[0]), q
+
+
+def test_forces_are_energy_gradient():
+    """Eq. beadforce against central differences of U (Eq. pot_syst) for bead-wise moves
+    with the body reference points held fixed (Appendix derivation)."""
+    s = C.small_system(seed=21, n_bodies=2, level=0, n_ions=3, L=6.0, a=0.2)
+
+    def Mf(x):
+        return o.M_dense(x, s.box, s.a, s.eps, xi=1.4)
+
+    U0, q = _energy_of(s.x, s, Mf)
+    f = o.bead_forces(s.x, q, s.E0[0], s.box, s.a, s.eps, xi=1.4)
+    rng = np.random.default_rng(0)
+    for al in rng.choice(s.n, size=5, replace=False):
+        for d in range(3):
+            h = 1e-5
+            xp = s.x.copy(); xp[al, d] += h
+            xm = s.x.copy(); xm[al, d] -= h
+            fd = -(_energy_of(xp, s, Mf)[0] - _energy_of(xm, s, Mf)[0]) / (2 * h)
+            assert abs(fd - f[al, d]) < 2e-6 * max(1.0, np.abs(f).max())
+
+
+def test_newton_third_law_and_torque_identity():
+    s = C.small_system(seed=9, n_bodies=2, level=1, n_ions=4)
+    q, psi = o.solve_dense(s.x, s.body_offsets, s.X, s.Q, s.E0[0], s.box, s.a, s.eps)
+    f = o.bead_forces(s.x, q, s.E0[0], s.box, s.a, s.eps)
+    assert np.max(np.abs(f.sum(axis=0) - q.sum() * s.E0[0])) < 1e-9 * np.abs(f).max()
+    # isolated neutral body in a big box: torque = S x E0 up to image terms
+    s1 = C.config1(level=1, a=0.25)
+    s1.E0 = np.array([[0.3, 0.0, 1.0]])
+    q, psi = o.solve_dense(s1.x, s1.body_offsets, s1.X, s1.Q, s1.E0[0], s1.box, s1.a, s1.eps)
+    f = o.bead_forces(s1.x, q, s1.E0[0], s1.box, s1.a, s1.eps)
+    F, L = o.body_force_torque(s1.x, s1.X, s1.body_offsets, f, s1.box)
+    S = o.dipoles(s1.x, s1.X, s1.body_offsets, q, s1.box)
+    assert np.linalg.norm(L[0] - np.cross(S[0], s1.E0[0])) < 1e-2 * np.linalg.norm(S[0]) + 1e-9
+
+
+def test_auto_params_balance_the_paper_error_bounds():
+    """Sec. III.D.2: eta = h^2 xi^2 P / pi equalises the truncation bound
+    e^{-h^2 P^2 xi^2/2 eta} and the quadrature bound e^{-pi^2 eta/2 xi^2 h^2}, both
+    then e^{-pi P/2}; the wave-space bound e^{-k_c^2/4xi^2} and the real-space bound
+    meet the tolerance; N_g = 1 + L k_c / pi."""
+    for L, mesh, tol, a in [(20.0, 64, 1e-8, 0.1), (30.0, 128, 1e-6, 0.05), (13.89, 256, 1e-6, 0.05)]:
+        p = o.auto_params([L] * 3, [mesh] * 3, tol, a)
+        h, xi, P, eta = p["h"], p["xi"], p["P"], p["eta"]
+        trunc = math.exp(-h * h * P * P * xi * xi / (2 * eta))
+        quadr = math.exp(-math.pi ** 2 * eta / (2 * xi * xi * h * h))
+        assert abs(trunc - quadr) <= 1e-12 * trunc
+        assert abs(trunc - math.exp(-math.pi * P / 2)) <= 1e-12 * trunc
+        assert math.exp(-math.pi * P / 2) <= tol < math.exp(-math.pi * (P - 1) / 2)
+        assert math.exp(-p["k_c"] ** 2 / (4 * xi * xi)) <= tol * (1 + 1e-9)
+        assert math.exp(-((p["r_cut"] - 2 * a) * xi) ** 2) <= tol * (1 + 1e-9)
+        assert abs(1 + L * p["k_c"] / math.pi - mesh) < 1e-9
+
+
+def test_philox_counter_based_generator():
+    a = o.philox4x32_10((0, 0, 0, 0), (0, 0))
+    b = o.philox4x32_10((1, 0, 0, 0), (0, 0))
+    c = o.philox4x32_10((0, 0, 0, 0), (1, 0))
+    assert a != b and a != c and all(0 <= v < 2 ** 32 for v in a + b + c)
+    assert a == o.philox4x32_10((0, 0, 0, 0), (0, 0))
+    z = np.array([o.normals(i, 3, 12345, 6) for i in range(20000)]).ravel()
+    assert abs(z.mean()) < 5 / math.sqrt(z.size)
+    assert abs(z.var() - 1) < 5 * math.sqrt(2 / z.size)
+    # uniformity of the raw words (chi-square over 16 bins)
+    w = np.array([o.philox4x32_10((i, 7, 0, 0), (99, 1))[2] for i in range(16000)]) >> 28
+    cnt = np.bincount(w, minlength=16)
+    chi2 = ((cnt - 1000) ** 2 / 1000).sum()
+    assert chi2 < 45  # 15 dof, p ~ 1e-4
+
+
+def test_hard_sphere_force_is_minus_gradient():
+    box = np.array([5.0, 5.0, 5.0])
+    x = np.array([[1.0, 1.0, 1.0], [1.07, 1.02, 0.99], [3.0, 3.0, 3.0]])
+    off = np.array([0, 1, 2, 3])
+    a, gamma, dt = 0.05, 1.0, 1e-3
+    f = o.hard_sphere_forces(x, off, box, a, gamma, dt)
+
+    def U(xx):
+        d = np.linalg.norm(o.min_image(xx[0] - xx[1], box))
+        return gamma / (4 * dt) * (d - 2 * a) ** 2 if d < 2 * a else 0.0
+
+    for d in range(3):
+        h = 1e-7
+        xp = x.copy(); xp[0, d] += h
+        xm = x.copy(); xm[0, d] -= h
+        assert abs(-(U(xp) - U(xm)) / (2 * h) - f[0, d]) < 1e-4 * np.abs(f).max()
+    assert np.allclose(f[0], -f[1]) and np.allclose(f[2], 0)
+
+
+def test_bd_step_deterministic_limits():
+    """kT = 0: ions move by F dt / gamma exactly (Eq. forward with M^H = I/gamma);
+    a rigid body under a uniform force translates without rotating."""
+    s = C.small_system(seed=4, n_bodies=1, level=1, n_ions=3)
+    f = np.zeros((s.n, 3))
+    f[:, 0] = 2.0
+    xn, Xn = o.bd_step(s.x, s.X, s.body_offsets, f, s.box, s.a, dt=1e-3, kT=0.0)
+    assert np.allclose(xn - s.x, np.array([2e-3, 0, 0]), atol=1e-15)
+    # torque about the reference point rotates the body by Omega dt, rigidly
+    f2 = np.zeros((s.n, 3))
+    r = o.relative_positions(s.x, s.X, s.body_offsets, s.box)
+    nb0 = s.body_offsets[1]
+    f2[:nb0] = np.cross(np.array([0, 0, 1.0]), r[:nb0])
+    xn, Xn = o.bd_step(s.x, s.X, s.body_offsets, f2, s.box, s.a, dt=1e-2, kT=0.0)
+    d0 = np.linalg.norm(r[:nb0], axis=1)
+    d1 = np.linalg.norm(xn[:nb0] - Xn[0], axis=1)
+    assert np.allclose(d0, d1, atol=1e-12)
+
+
+def test_bd_noise_variance():
+    """Ion displacement variance 2 kT dt / gamma per axis (fluctuation-dissipation, Sec. V.A)."""
+    n = 4000
+    x = np.random.default_rng(1).uniform(0, 10, size=(n, 3))
+    off = np.arange(n + 1, dtype=np.int32)
+    xn, _ = o.bd_step(x, x.copy(), off, np.zeros((n, 3)), np.array([10.0] * 3), 0.05, dt=1e-3,
+                      gamma=2.0, kT=1.5, seed=77, step=5)
+    d = (xn - x).ravel()
+    var = 2 * 1.5 * 1e-3 / 2.0
+    assert abs(d.mean()) < 5 * math.sqrt(var / d.size)
+    assert abs(d.var() / var - 1) < 5 * math.sqrt(2 / d.size)
