@@ -117,11 +117,11 @@ double ibo_dphi_real(double r, double a, double xi)
     return d;
 }
 
-/* Number of periodic images needed along one axis so that every image within
- * the cutoff is visited. */
+/* Number of periodic images needed along one axis so that every image of a
+ * displacement already reduced to [-L/2, L/2] within the cutoff is visited. */
 static int image_range(double rc, double L)
 {
-    return (int)ceil(rc / L) + 1;
+    return (int)ceil((rc + 0.5 * L) / L);
 }
 
 /*

@@ -122,6 +122,17 @@ def ewald_split(box, a: float, n_src: int, tol: float = 1e-13, xi: float | None 
     return float(xi), float(rc), float(kc)
 
 
+def k0_term(box, xi, eps):
+    """k = 0 Fourier weight carried by the real-space image sum.
+
+    By Poisson summation, sum_n phi_r(|r + n L|) = (1/V) sum_k phihat_r(k) e^{i k.r}
+    over ALL k, and phihat_r(k) = j0^2(ka)(1 - e^{-k^2/4xi^2})/k^2 -> 1/(4 xi^2) at
+    k = 0.  M of Eq. M00_Fourier has no k = 0 term (Sec. II: electroneutrality), so
+    1/(4 xi^2 V eps) is subtracted from every element; for neutral charges it cancels."""
+    V = float(np.prod(np.asarray(box, dtype=np.float64)))
+    return 1.0 / (4.0 * xi * xi * V * eps)
+
+
 def potential(x, q, box, a, eps, targets=None, field=False, xi=None, tol=1e-13):
     """psi_alpha - psi_0 (and E_alpha) at the targets, Eq. splitting + self term.
 
@@ -143,9 +154,11 @@ def potential(x, q, box, a, eps, targets=None, field=False, xi=None, tol=1e-13):
     Ek = np.zeros((nt, 3)) if field else None
     L.ibo_real_sum(n, _ptr(x), _ptr(q), _ptr(box), a, xi, rc, eps, nt, _ptr(targets), _ptr(pr), _ptr(Er))
     L.ibo_wave_sum(n, _ptr(x), _ptr(q), _ptr(box), a, xi, kc, eps, nt, _ptr(targets), _ptr(pk), _ptr(Ek))
+    # k = 0 is excluded from M (Sec. II); the real-space image sum carries it (see k0_term)
+    pb = -k0_term(box, xi, eps) * float(np.sum(q))
     if field:
-        return pr + pk, Er + Ek
-    return pr + pk
+        return pr + pk + pb, Er + Ek
+    return pr + pk + pb
 
 
 def wave_vectors(box, a, xi, kc):
@@ -179,7 +192,35 @@ def M_dense(x, box, a, eps, xi=None, tol=1e-13, k_chunk=4096):
         S = np.sin(ph)
         g = G[s:s + k_chunk]
         Mw += (C * g) @ C.T + (S * g) @ S.T
-    return (Mr + Mw / V) / eps
+    return (Mr + Mw / V) / eps - k0_term(box, xi, eps)
+
+
+def spread_grid(x, q, box, mesh, xi, eta, P):
+    """The spread grid of Eq. H_hat, written out:
+    H(x_g) = (2 xi^2/(pi eta))^{3/2} sum_beta q_beta exp(-2 xi^2 |x_g - x_beta|^2 / eta)
+    on the nodes x_g = (i h_x, j h_y, k h_z), h_d = L_d / N_d, each bead restricted
+    to the P closest nodes per axis (Sec. III.D.2), i.e. the nodes
+    floor(x/h - P/2) + 1 ... floor(x/h - P/2) + P, taken periodically.
+    Returns [N_z, N_y, N_x] (x fastest)."""
+    x = _c(x).reshape(-1, 3)
+    box = _c(box).reshape(3)
+    N = [int(m) for m in mesh]
+    h = box / np.array(N, dtype=np.float64)
+    c = (2.0 * xi * xi / (math.pi * eta)) ** 1.5
+    H = np.zeros((N[2], N[1], N[0]))
+    for b in range(x.shape[0]):
+        idx, w = [], []
+        for d in range(3):
+            xd = x[b, d] - box[d] * math.floor(x[b, d] / box[d])
+            u = xd / h[d]
+            s = math.floor(u - 0.5 * P) + 1
+            nodes = s + np.arange(P)
+            dist = nodes * h[d] - xd
+            w.append(np.exp(-2.0 * xi * xi * dist * dist / eta))
+            idx.append(np.mod(nodes, N[d]))
+        blk = c * q[b] * w[2][:, None, None] * w[1][None, :, None] * w[0][None, None, :]
+        np.add.at(H, np.ix_(idx[2], idx[1], idx[0]), blk)
+    return H
 
 
 # ---------------------------------------------------------------------------
@@ -546,8 +587,8 @@ def reference_solution(x, body_offsets, X, Q, E0, box, a, eps, dense=None, xi=No
 
 
 __all__ = [
-    "lib", "num_threads", "M_free", "phi_real", "dphi_real", "phi_self", "ewald_split",
-    "potential", "wave_vectors", "M_dense", "min_image", "body_index", "sigma_matrix",
+    "lib", "num_threads", "k0_term", "M_free", "phi_real", "dphi_real", "phi_self", "ewald_split",
+    "potential", "wave_vectors", "M_dense", "spread_grid", "min_image", "body_index", "sigma_matrix",
     "relative_positions", "saddle_rhs", "saddle_matrix", "solve_dense", "gmres",
     "saddle_operator", "solve_gmres", "dipoles", "energy", "bead_forces",
     "body_force_torque", "auto_params", "philox4x32_10", "normals",

@@ -108,6 +108,42 @@ def test_xi_independence():
     assert np.max(np.abs(E1 - E2)) < 1e-10 * np.max(np.abs(E1))
 
 
+def test_xi_independence_non_neutral():
+    """With k = 0 excluded (Sec. II) the sums stay independent of xi for a net charge."""
+    x, q, box, a = _random_neutral()
+    q = q + 0.37
+    p1 = o.potential(x, q, box, a, 1.0, xi=0.9)
+    p2 = o.potential(x, q, box, a, 1.0, xi=2.2)
+    assert np.max(np.abs(p1 - p2)) < 1e-11 * np.max(np.abs(p1))
+    M1 = o.M_dense(x[:12], box, a, 1.0, xi=0.9)
+    M2 = o.M_dense(x[:12], box, a, 1.0, xi=2.2)
+    assert np.max(np.abs(M1 - M2)) < 1e-11 * np.max(np.abs(M1))
+
+
+def test_single_charge_is_the_k_sum_of_its_images():
+    """One unit charge: psi = (1/(eps V)) sum_{k != 0} j0^2(ka)/k^2 (Eq. M00_Fourier at r = 0),
+    summed directly over a cube of wave vectors; the truncation error falls like 1/K,
+    so two cubes are Richardson-extrapolated.  Without the k = 0 correction the
+    oracle would be off by 1/(4 xi^2 V eps), about 10% here."""
+    box = np.array([4.0, 4.0, 4.0])
+    a = 0.3
+    psi = o.potential(np.array([[1.0, 2.0, 3.0]]), [1.0], box, a, 1.0)[0]
+
+    def cube_sum(M):
+        m = np.arange(-M, M + 1)
+        kx, ky, kz = np.meshgrid(*(2 * np.pi * m / 4.0,) * 3, indexing="ij")
+        k2 = kx ** 2 + ky ** 2 + kz ** 2
+        k2[M, M, M] = 1.0
+        kk = np.sqrt(k2)
+        t = (np.sin(kk * a) / (kk * a)) ** 2 / k2
+        t[M, M, M] = 0.0
+        return t.sum() / 64.0
+
+    extrapolated = 2 * cube_sum(80) - cube_sum(40)
+    assert abs(psi - extrapolated) < 2e-4 * abs(psi)
+    assert abs(o.k0_term(box, 0.44, 1.0)) > 0.05 * abs(psi)
+
+
 def test_translation_invariance():
     x, q, box, a = _random_neutral()
     p1 = o.potential(x, q, box, a, 1.0)
