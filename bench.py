@@ -1,0 +1,503 @@
+"""Benchmark: induced-charge solves/s on the charged-sphere workload.
+
+One step = one induced-charge solve (mixed precision: FP32 mesh, FP64 Krylov,
+FP64-operator residual <= 1e-6), the force/torque pass and one Brownian
+dynamics step of a 642-bead colloid (Q = -50) with 2,050 ions in L = 30 on a
+128^3 mesh; positions advance from step to step.  Inputs are resident in HBM
+when the timed region starts; the L2 is flushed (a 256 MB write) before every
+timed step, outside the step's CUDA-event pair.
+
+Also reported on the same JSON line: PME evaluations/s of the same system,
+the dominant kernel against the HBM roofline, the plain FP64 GPU path, the
+end-to-end rate through the C ABI with host buffers, the oracle timed on the
+host cores, SM clocks sampled during the timed region and the number of the
+library's kernel launches.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+For N > 1 launch with torchrun; every rank runs its own replica (weak scaling).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "induced-charge solves/s and PME evals/s (HBM roofline %) vs plain FP64 GPU"
+WORKLOAD = ("charged sphere: 642-bead icosphere (Q=-50) + 2,050 monovalent ions, L=30, l_B=0.7, bead radius 0.05, "
+            "mesh 128^3, tol 1e-6 (xi=1.79, P=9); step = mixed-precision induced-charge solve to FP64 residual "
+            "1e-6 from the uniform guess + forces/torques/energy + one BD step (dt=1e-3)")
+HBM_FALLBACK_GBS = 6800.0
+DT = 1e-3
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return HBM_FALLBACK_GBS, "fallback"
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+# ---------------------------------------------------------------------------
+# clocks
+# ---------------------------------------------------------------------------
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.dev), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+            time.sleep(0.3)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if self.path is None or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        rows = []
+        for line in open(self.path):
+            p = [v.strip() for v in line.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                rows.append((float(p[1]), float(p[2]), p[5], p[6], p[7], p[8]))
+            except ValueError:
+                continue
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = np.array([r[0] for r in rows])
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[2 + i].lower() == "active"})
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(r[1] for r in rows)),
+                "samples": len(rows), "reasons": reasons}
+
+
+# ---------------------------------------------------------------------------
+# the workload
+# ---------------------------------------------------------------------------
+
+def make_system(rank: int):
+    from workloads import configs as C
+    return C.config2(seed=1001 + 7919 * rank)
+
+
+class Step:
+    """Device-resident state of one replica and the three calls of one step."""
+
+    def __init__(self, ib, torch, s, precision):
+        self.ib, self.torch, self.s = ib, torch, s
+        dev = "cuda"
+        f64 = torch.float64
+        self.n, self.nb = s.n, s.n_bodies
+        self.stream = torch.cuda.current_stream()
+        self.ctx = ib.pme_setup(ib.make_params(box=s.box, mesh=s.mesh, tol=s.tol, bead_radius=s.a, eps_f=s.eps,
+                                               precision=ib.IBPME_MIXED, max_rhs=1), self.stream)
+        self.precision = precision
+        t = lambda a, dt=f64: torch.as_tensor(np.ascontiguousarray(a)).to(dt).to(dev)
+        self.x = t(s.x)
+        self.x_next = torch.empty_like(self.x)
+        self.X = t(s.X)
+        self.X_next = torch.empty_like(self.X)
+        self.off = t(s.body_offsets, torch.int32)
+        self.Q = t(s.Q)
+        self.E0 = t(s.E0[:1])
+        self.q0 = t(s.q_guess.reshape(1, -1))
+        self.q = torch.empty_like(self.q0)
+        self.psi = torch.zeros((1, self.nb), dtype=f64, device=dev)
+        self.S = torch.zeros((1, self.nb, 3), dtype=f64, device=dev)
+        self.f = torch.zeros((self.n, 3), dtype=f64, device=dev)
+        self.F = torch.zeros((self.nb, 3), dtype=f64, device=dev)
+        self.L = torch.zeros((self.nb, 3), dtype=f64, device=dev)
+        self.U = torch.zeros(1, dtype=f64, device=dev)
+        self.opts = ib.make_opts(rtol=1e-6, guess=ib.IBPME_GUESS_USER, precision=precision)
+        self.step_no = 0
+        self.last_stats = None
+
+    def run(self):
+        ib = self.ib
+        bodies = ib.Bodies(self.off, self.X, self.Q)
+        self.q.copy_(self.q0)
+        status, st = ib.induced_charge_solve(self.ctx, self.n, self.x, bodies, self.E0, 1, self.opts, self.q,
+                                             self.psi, self.S)
+        if status != ib.IBPME_OK:
+            raise RuntimeError(f"solve did not converge: residual {st.rel_residual:.3e}")
+        ib.body_force_torque(self.ctx, self.n, self.x, self.q[0], bodies, self.E0[0], self.f, self.F, self.L,
+                             self.U)
+        ib.ibpme_bd_step(self.ctx, self.n, self.x, bodies, self.f, DT, 1.0, 1.0, 1234, self.step_no,
+                         self.x_next, self.X_next)
+        self.x, self.x_next = self.x_next, self.x
+        self.X, self.X_next = self.X_next, self.X
+        self.step_no += 1
+        self.last_stats = st
+        return st
+
+    def close(self):
+        self.ib.pme_destroy(self.ctx)
+
+
+class HostStep:
+    """The same step through the C ABI with host (numpy) buffers: the library
+    stages every input to the device and every output back."""
+
+    def __init__(self, ib, s, ctx):
+        self.ib, self.s, self.ctx = ib, s, ctx
+        self.x = np.ascontiguousarray(s.x)
+        self.X = np.ascontiguousarray(s.X)
+        self.off = np.ascontiguousarray(s.body_offsets, dtype=np.int32)
+        self.Q = np.ascontiguousarray(s.Q)
+        self.E0 = np.ascontiguousarray(s.E0[:1])
+        self.q0 = np.ascontiguousarray(s.q_guess.reshape(1, -1))
+        n, nb = s.n, s.n_bodies
+        self.q = np.zeros((1, n))
+        self.psi = np.zeros((1, nb))
+        self.S = np.zeros((1, nb, 3))
+        self.f = np.zeros((n, 3))
+        self.F = np.zeros((nb, 3))
+        self.L = np.zeros((nb, 3))
+        self.U = np.zeros(1)
+        self.x_next = np.zeros_like(self.x)
+        self.X_next = np.zeros_like(self.X)
+        self.opts = ib.make_opts(rtol=1e-6, guess=ib.IBPME_GUESS_USER, precision=ib.IBPME_MIXED)
+        self.step_no = 0
+        body = self.off.nbytes + self.X.nbytes + self.Q.nbytes
+        # bytes copied per step, counted from the arrays each call stages
+        self.h2d = (self.x.nbytes + body + self.E0.nbytes + self.q.nbytes           # solve (q_out read as guess)
+                    + self.x.nbytes + self.q.nbytes + body + 24                     # forces
+                    + self.x.nbytes + body + self.f.nbytes)                         # BD step
+        self.d2h = (self.q.nbytes + self.psi.nbytes + self.S.nbytes
+                    + self.f.nbytes + self.F.nbytes + self.L.nbytes + self.U.nbytes
+                    + self.x_next.nbytes + self.X_next.nbytes)
+
+    def run(self):
+        ib = self.ib
+        bodies = ib.Bodies(self.off, self.X, self.Q)
+        self.q[:] = self.q0
+        status, st = ib.induced_charge_solve(self.ctx, self.s.n, self.x, bodies, self.E0, 1, self.opts, self.q,
+                                             self.psi, self.S)
+        if status != ib.IBPME_OK:
+            raise RuntimeError("host-buffer solve did not converge")
+        q0 = np.ascontiguousarray(self.q[0])
+        ib.body_force_torque(self.ctx, self.s.n, self.x, q0, bodies, np.ascontiguousarray(self.E0[0]), self.f,
+                             self.F, self.L, self.U)
+        ib.ibpme_bd_step(self.ctx, self.s.n, self.x, bodies, self.f, DT, 1.0, 1.0, 1234, self.step_no,
+                         self.x_next, self.X_next)
+        self.x, self.x_next = self.x_next, self.x
+        self.X, self.X_next = self.X_next, self.X
+        self.step_no += 1
+
+
+# algorithmic bytes per launch of each timed stage (mesh w = 4 or 8 bytes, R = 1)
+def stage_bytes(stage, s, npairs):
+    G = int(np.prod(s.mesh))
+    Gc = s.mesh[2] * s.mesh[1] * (s.mesh[0] // 2 + 1)
+    n = s.n
+    w = 8 if stage.endswith("64") else 4
+    base = stage[:-2] if stage.endswith("64") else stage
+    if base == "spread":
+        return G * w + n * (24 + 8)           # grid written once; positions and charges read
+    if base == "gather":
+        return G * w + n * (24 + 8)           # grid read once; positions read, potentials written
+    if base == "scale":
+        return Gc * (2 * 2 * w + w)           # half spectrum read and written, Green's table read
+    if base in ("fft_forward", "fft_inverse"):
+        return 2 * G * w
+    if base == "near_apply":
+        return npairs * (4 + 8) + n * (8 + 8 + 8 + 8)   # col + value per pair; q, psi, row offsets
+    return None
+
+
+def bench_ours(args, ib, torch, rank, world, local):
+    dev_index = local
+    torch.cuda.set_device(dev_index)
+    s = make_system(rank)
+    st = Step(ib, torch, s, ib.IBPME_MIXED)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")   # 256 MB > L2
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    # warm-up, with every stage timed once to find the dominant kernel
+    ib.ibpme_profile((1 << len(ib.STAGES)) - 1)
+    for _ in range(args.warmup):
+        st.run()
+    prof = ib.ibpme_profile_read()
+    # candidates: the library's own memory-bound kernels (cuFFT is a library; the pair-table
+    # build, the Krylov group and the body reductions are reported in warmup_stage_ms)
+    own = {k: v for k, v in prof.items() if stage_bytes(k, s, 1) is not None and not k.startswith("fft")
+           and v[1] > 0}
+    dominant = max(own, key=lambda k: own[k][0]) if own else "spread"
+    dom_idx = ib.STAGES.index(dominant)
+    warm_profile = {k: {"ms": round(v[0], 4), "launches": v[1]} for k, v in prof.items() if v[1]}
+
+    # timed region: only the dominant stage carries events
+    ib.ibpme_profile(1 << dom_idx)
+    launches0 = ib.ibpme_kernel_launches()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    iters = []
+    with ClockSampler(dev_index) as clk:
+        barrier()
+        t0 = time.perf_counter()
+        for i in range(args.steps):
+            flush.zero_()
+            ev[i][0].record(st.stream)
+            stats = st.run()
+            ev[i][1].record(st.stream)
+            iters.append((stats.iters, stats.outer, stats.matvecs_fp64, stats.rel_residual))
+        barrier()
+        wall = time.perf_counter() - t0
+    launches = ib.ibpme_kernel_launches() - launches0
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    total_ms = float(np.sum(step_ms))
+    dom = ib.ibpme_profile_read()[dominant]
+    ib.ibpme_profile(0)
+    if world > 1:
+        t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t.item())
+    value = world * args.steps / (total_ms / 1e3)
+
+    # PME evaluations alone on the same system (potential of the current charges)
+    npairs = pair_count(ib, st)
+    pme = pme_rate(ib, torch, st, flush, max(10, args.steps))
+
+    # plain FP64 GPU path: the same step with every mesh step in FP64
+    fp64 = None
+    if not args.skip_fp64:
+        st64 = Step(ib, torch, s, ib.IBPME_FP64)
+        st64.run()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        k64 = max(2, args.steps // 5)
+        tot = 0.0
+        for _ in range(k64):
+            flush.zero_()
+            e0.record(st64.stream)
+            st64.run()
+            e1.record(st64.stream)
+            torch.cuda.synchronize()
+            tot += e0.elapsed_time(e1)
+        s64 = st64.last_stats
+        fp64 = {"solves_per_s": k64 / (tot / 1e3), "ms_per_step": tot / k64, "steps": k64, "iters": s64.iters,
+                "rel_residual": s64.rel_residual}
+        st64.close()
+
+    # end to end through the C ABI with host buffers
+    hs = HostStep(ib, s, st.ctx)
+    hs.run()
+    torch.cuda.synchronize()
+    k_e2e = max(3, args.steps // 2)
+    t0 = time.perf_counter()
+    for _ in range(k_e2e):
+        hs.run()
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+
+    peak, peak_kind = peaks()
+    launches_dom = dom[1]
+    avg_ms = dom[0] / launches_dom if launches_dom else float("nan")
+    alg = stage_bytes(dominant, s, npairs)
+    achieved = alg / (avg_ms / 1e3) / 1e9 if alg and launches_dom else None
+    out = {
+        "metric": METRIC,
+        "value": value,
+        "unit": "solves/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": total_ms / args.steps,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32 mesh / f64 near-field+krylov",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n_beads": s.n, "n_bodies": s.n_bodies, "mesh": list(s.mesh),
+                   "l2": "L2 flushed (256 MB write) before every timed step, outside its events",
+                   "parallelism": f"replicas x{world} (independent systems, no collective)"},
+        "roofline": {"kernel": dominant, "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": (achieved / peak) if achieved else None, "peak_source": peak_kind,
+                     "alg_bytes_per_launch": alg, "avg_launch_ms": avg_ms, "launches": launches_dom,
+                     "traffic": None},
+        "pme_evals_per_s": pme["evals_per_s"],
+        "pme_roofline": pme["roofline"],
+        "fp64_gpu": fp64,
+        "speedup_vs_fp64": (value / world / fp64["solves_per_s"]) if fp64 else None,
+        "solve": {"iters_mean": float(np.mean([i[0] for i in iters])), "outer_mean": float(np.mean([i[1] for i in iters])),
+                  "fp64_matvecs_mean": float(np.mean([i[2] for i in iters])),
+                  "rel_residual_max": float(np.max([i[3] for i in iters]))},
+        "e2e": {"value": world * k_e2e / e2e_s if world == 1 else k_e2e / e2e_s, "unit": "solves/s",
+                "h2d_bytes_per_step": hs.h2d, "d2h_bytes_per_step": hs.d2h},
+        "gpu_launches": int(launches),
+        "wall_s": wall,
+        "warmup_stage_ms": warm_profile,
+        "clocks": clk.summary(),
+    }
+    st.close()
+    return out, s
+
+
+def pair_count(ib, st):
+    """Real-space pairs within r_cut of the current configuration (a property of
+    the workload, counted on the host; it sizes the SpMV's algorithmic bytes)."""
+    p = ib.ibpme_get_params(st.ctx)
+    x = st.x.cpu().numpy()
+    box = np.asarray(st.s.box)
+    rc = p.r_cut
+    cnt = 0
+    for i in range(0, x.shape[0], 512):
+        d = x[i:i + 512, None, :] - x[None, :, :]
+        d -= box * np.floor(d / box + 0.5)
+        r2 = (d * d).sum(axis=2)
+        cnt += int((r2 < rc * rc).sum()) - min(512, x.shape[0] - i)
+    return cnt
+
+
+def pme_rate(ib, torch, st, flush, k):
+    s = st.s
+    psi = torch.zeros((1, s.n), dtype=torch.float64, device="cuda")
+    ib.pme_field(st.ctx, s.n, st.x, st.q, 1, psi, None)
+    torch.cuda.synchronize()
+    tot = 0.0
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for _ in range(k):
+        flush.zero_()
+        e0.record(st.stream)
+        ib.pme_field(st.ctx, s.n, st.x, st.q, 1, psi, None)
+        e1.record(st.stream)
+        torch.cuda.synchronize()
+        tot += e0.elapsed_time(e1)
+    t = tot / k / 1e3
+    G = int(np.prod(s.mesh))
+    alg = 6 * G * 4 + s.n * (32 + 8)   # 6 G w R + N (32 + 8R), FP32 mesh, R = 1
+    peak, kind = peaks()
+    return {"evals_per_s": 1.0 / t, "roofline": {"bound": "hbm", "achieved": alg / t / 1e9, "peak": peak,
+                                                  "unit": "GB/s", "frac": alg / t / 1e9 / peak,
+                                                  "alg_bytes_per_eval": alg, "ms_per_eval": t * 1e3,
+                                                  "peak_source": kind}}
+
+
+# ---------------------------------------------------------------------------
+# the oracle on the host cores
+# ---------------------------------------------------------------------------
+
+def oracle_step(o, s, x, X):
+    """One step of the workload with the FP64 oracle: dense saddle solve, Ewald
+    forces and torques, energy, hard-sphere forces and the BD step."""
+    q, psi = o.solve_dense(x, s.body_offsets, X, s.Q, s.E0[0], s.box, s.a, s.eps)
+    S = o.dipoles(x, X, s.body_offsets, q, s.box)
+    o.energy(X, s.Q, psi, S, s.E0[0])
+    f = o.bead_forces(x, q, s.E0[0], s.box, s.a, s.eps)
+    o.body_force_torque(x, X, s.body_offsets, f, s.box)
+    f = f + o.hard_sphere_forces(x, s.body_offsets, s.box, s.a, 1.0, DT)
+    return o.bd_step(x, X, s.body_offsets, f, s.box, s.a, DT, seed=1234, step=0)
+
+
+def cpu_baseline(min_seconds=10.0, max_steps=4):
+    import oracle as o
+    s = make_system(0)
+    x, X = s.x, s.X
+    t0 = time.perf_counter()
+    k = 0
+    while k < max_steps and (k == 0 or time.perf_counter() - t0 < min_seconds):
+        x, X = oracle_step(o, s, x, X)
+        k += 1
+    dt = time.perf_counter() - t0
+    return {"value": k / dt, "unit": "solves/s", "cores": o.num_threads(), "kind": "oracle",
+            "sample": f"{k} full step(s) of the same workload (dense LU saddle solve, explicit-k Ewald forces, "
+                      f"hard spheres, BD step) in {dt:.1f} s"}
+
+
+def bench_reference(args):
+    import oracle as o
+    s = make_system(0)
+    x, X = s.x, s.X
+    for _ in range(args.warmup):
+        x, X = oracle_step(o, s, x, X)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        x, X = oracle_step(o, s, x, X)
+    dt = time.perf_counter() - t0
+    v = args.steps / dt
+    return {"impl": "reference", "metric": METRIC, "value": v, "unit": "solves/s", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD},
+            "cpu_baseline": {"value": v, "unit": "solves/s", "cores": o.num_threads(), "kind": "oracle",
+                             "sample": f"{args.steps} timed full steps after {args.warmup} warm-up steps"},
+            "e2e": {"value": v, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--skip-fp64", action="store_true", help="do not time the plain FP64 path")
+    ap.add_argument("--skip-cpu", action="store_true", help="do not time the oracle on the host")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    rank, world, local = dist_env()
+    if args.impl == "reference":
+        if rank == 0:
+            print(json.dumps(bench_reference(args)), flush=True)
+        return
+    import torch
+
+    import paper_2401_04865_gb300 as ib
+    ib.load()
+    if world > 1:
+        torch.cuda.set_device(local)
+        torch.distributed.init_process_group("nccl", device_id=torch.device("cuda", local))
+    out, s = bench_ours(args, ib, torch, rank, world, local)
+    if rank == 0:
+        out["cpu_baseline"] = None if args.skip_cpu else cpu_baseline()
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,230 @@
+/*
+ * ibpme.h -- C ABI of the GB300 immersed-boundary PME library.
+ *
+ * The library evaluates the regularized, spectrally accurate particle-mesh
+ * Ewald sums of Krucker-Velasquez, Swan & Sherman, "Immersed boundary method
+ * for dynamic simulation of polarizable colloids of arbitrary shape in
+ * explicit ion electrolytes" (arXiv:2401.04865), Sec. III.D, and uses them
+ * as the matrix-vector product of the induced-charge saddle system of
+ * Sec. III.B (Eq. saddle), the bead forces of Sec. III.C (Eq. beadforce)
+ * and the Brownian-dynamics step of Sec. V.A.
+ *
+ * Conventions shared by every entry point:
+ *   - Arrays are plain pointers to IEEE double (or int32 where stated),
+ *     row-major.  A pointer may address device memory or host memory: the
+ *     library asks the CUDA driver which it is and stages host arrays through
+ *     its own device buffers (the copies run on the context stream).
+ *   - Positions x are [n][3]; they may lie anywhere (they are wrapped into the
+ *     periodic box internally).  Charges q are [nrhs][n].
+ *   - Potentials are psi_alpha - psi_0(x_alpha) (Eq. pot_charge), fields are
+ *     E = -grad psi, in units where the fluid permittivity is eps_f.
+ *   - Bodies are contiguous ranges of beads given by CSR offsets (Appendix,
+ *     summation tensor Sigma); an ion is a body of one bead (Sec. III.B).
+ *   - Ownership: the caller owns every array; the library never keeps a
+ *     pointer after a call returns.  The context owns its device scratch.
+ *   - Streams: all work is enqueued on the context stream.  Entry points that
+ *     return results in host memory, and induced_charge_solve (which needs its
+ *     convergence flag), synchronize that stream before they return.
+ *   - Errors: every entry point returns an ibpme_status and never throws;
+ *     ibpme_last_error() gives a message for the calling thread.  After an
+ *     error the outputs are unspecified.
+ *   - All beads share one radius a (Sec. III.A).
+ */
+#ifndef IBPME_H
+#define IBPME_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct ibpme_ctx ibpme_ctx;
+
+typedef enum {
+    IBPME_OK = 0,
+    IBPME_ERR_ARG = 1,            /* invalid argument (sizes, box, mesh < P, r_cut >= L/2, ...) */
+    IBPME_ERR_CUDA = 2,           /* a CUDA runtime call failed */
+    IBPME_ERR_CUFFT = 3,          /* a cuFFT call failed */
+    IBPME_ERR_OOM = 4,            /* device allocation failed */
+    IBPME_ERR_NOT_CONVERGED = 5,  /* the Krylov solve hit max_iter; outputs hold the last iterate */
+    IBPME_ERR_UNEQUAL_RADII = 6,  /* reserved: one bead radius per system (Sec. III.A) */
+    IBPME_ERR_TIMEOUT = 7,        /* a bounded device wait ran out */
+    IBPME_ERR_NONFINITE = 8       /* NaN/Inf in an input or in the iteration */
+} ibpme_status;
+
+enum { IBPME_FP64 = 0,            /* every step in FP64 */
+       IBPME_MIXED = 1 };         /* FP32 mesh (spread, FFT, scale, gather), FP64 near field,
+                                     FP64 Krylov; solves refine against the FP64 operator */
+
+/* Parameters of the spectral Ewald split (Sec. III.D).  A zero in a field
+ * marked "auto" asks pme_setup to derive it with the rules of Sec. III.D.2:
+ *   k_c = pi (N_g - 1) / L          (from N_g = 1 + L k_c / pi, smallest axis)
+ *   xi  = k_c / (2 sqrt(ln(1/tol))) (wave-space bound e^{-k_c^2/4xi^2} = tol)
+ *   r_cut = sqrt(ln(1/tol)) / xi + 2a (real-space bound, Eq. realspaceerror)
+ *   P   = ceil(2 ln(1/tol) / pi)    (contraction bound e^{-pi P/2} <= tol, Eq. contractionerror)
+ *   eta = h^2 xi^2 P / pi           (h = largest L_d / N_d)
+ * If mesh is {0,0,0}, xi must be given and N_g = 1 + L k_c/pi with
+ * k_c = 2 xi sqrt(ln(1/tol)), rounded up to a size with prime factors 2, 3, 5, 7. */
+typedef struct {
+    double box[3];        /* periodic box side lengths L_x, L_y, L_z (> 0) */
+    int mesh[3];          /* grid points per axis N_x, N_y, N_z (>= P), or 0 = auto */
+    double xi;            /* Ewald splitting parameter, 0 = auto */
+    double eta;           /* spectral-Ewald Gaussian split, 0 = auto */
+    double r_cut;         /* real-space cutoff, 0 = auto; must be < L/2 */
+    int P;                /* stencil points per axis (<= 32), 0 = auto */
+    double tol;           /* accuracy target of the automatic rules (e.g. 1e-6); 0 -> 1e-6 */
+    double bead_radius;   /* a, shared by all beads (> 0) */
+    double eps_f;         /* fluid permittivity (> 0); eps_f = 1/(4 pi l_B) with kT = 1 */
+    int precision;        /* IBPME_FP64 or IBPME_MIXED */
+    int max_rhs;          /* largest nrhs a call will pass (1..8); 0 -> 3 */
+} ibpme_params;
+
+/* Create a context: resolves the automatic parameters, allocates the meshes
+ * (FP64, plus FP32 in mixed precision), builds cuFFT plans and the k-space
+ * Green's-function table of Sec. III.D.2 (Eq. after H_hat).  cuda_stream is a
+ * cudaStream_t (NULL = legacy default stream).  On error *ctx is NULL. */
+ibpme_status pme_setup(ibpme_ctx** ctx, const ibpme_params* params, void* cuda_stream);
+
+/* Free the context and all its device memory.  NULL is accepted. */
+ibpme_status pme_destroy(ibpme_ctx* ctx);
+
+/* Change the stream on which later calls enqueue their work. */
+ibpme_status ibpme_set_stream(ibpme_ctx* ctx, void* cuda_stream);
+
+/* Copy the resolved parameters (all "auto" fields filled in) to *out. */
+ibpme_status ibpme_get_params(const ibpme_ctx* ctx, ibpme_params* out);
+
+/* Message of the last error raised on the calling thread ("" if none). */
+const char* ibpme_last_error(void);
+
+/* Spreading, Sec. III.D.2 Eq. H_hat and step 2 of Sec. III.D.3:
+ *   H(x_g) = (2 xi^2/(pi eta))^{3/2} sum_beta q_beta exp(-2 xi^2 |x_g - x_beta|^2 / eta)
+ * on the grid nodes x_g = (i h_x, j h_y, k h_z), each bead restricted to the
+ * P closest nodes per axis (first node floor(x/h - P/2) + 1, periodic).
+ *   n      number of beads (>= 0)
+ *   x      [n][3] positions; q [nrhs][n] charges; 1 <= nrhs <= max_rhs
+ *   grid_out  NULL, or [nrhs][N_z][N_y][N_x] of the context precision's
+ *          real type (double for IBPME_FP64, float for IBPME_MIXED), x fastest.
+ * The grid stays in the context for inspection; it is overwritten by the next call. */
+ibpme_status pme_spread(ibpme_ctx* ctx, int n, const double* x, const double* q, int nrhs, void* grid_out);
+
+/* One PME evaluation, Sec. III.D.3 steps 1-6: psi = M q for every bead
+ * (real-space sum with the cell list + self term + spread, FFT, Green's-function
+ * scaling, inverse FFT, trapezoid-rule gather), optionally the field.
+ *   psi  [nrhs][n] (required), E [nrhs][n][3] or NULL.
+ * The near field is computed in FP64; the mesh in the context precision. */
+ibpme_status pme_field(ibpme_ctx* ctx, int n, const double* x, const double* q, int nrhs,
+                       double* psi, double* E);
+
+/* Bodies for the saddle system (Sec. III.B, Appendix). */
+typedef struct {
+    int n_bodies;              /* N_b >= 1 */
+    const int* body_offsets;   /* [N_b + 1] int32 CSR offsets into the beads, offsets[0] = 0,
+                                  offsets[N_b] = n, every body non-empty */
+    const double* X;           /* [N_b][3] body reference points (centre of mass, Sec. III.B) */
+    const double* Q;           /* [N_b] net body charges (Eq. Q_tot) */
+} ibpme_bodies;
+
+enum { IBPME_GUESS_ZERO = 0, IBPME_GUESS_USER = 1, IBPME_GUESS_LEARNED = 2 };
+
+typedef struct {
+    double rtol;        /* target relative residual of Eq. saddle, ||b - A u|| / ||b||; 0 -> 1e-6 */
+    int restart;        /* GMRES restart length m (1..128); 0 -> 50 */
+    int max_iter;       /* cap on Krylov iterations (all restarts, all refinement steps); 0 -> 3000 */
+    int guess;          /* IBPME_GUESS_*; USER reads q_out as the initial charges.  The initial
+                           body potentials are always the least-squares fit to the initial
+                           charges (mean over each body of (M q)_j - r_j.E0) */
+    const void* mlp;    /* trained warm-start model (IBPME_GUESS_LEARNED), else NULL */
+    int precision;      /* -1 = context precision, else IBPME_FP64 / IBPME_MIXED (mixed needs a
+                           mixed context) */
+} ibpme_solve_opts;
+
+typedef struct {
+    int iters;              /* Krylov iterations (operator applications inside GMRES) */
+    int outer;              /* refinement steps (mixed precision), 1 for FP64 */
+    int matvecs_fp64;       /* FP64 operator applications (true residuals, RHS) */
+    double rel_residual;    /* final ||b - A u||_2 / ||b||_2 with the FP64 operator, worst RHS */
+    double time_ms;         /* wall time of the call */
+    int fell_back;          /* 1 if the learned guess was rejected for the zero guess */
+} ibpme_solve_stats;
+
+/* Induced-charge solve, Sec. III.B Eq. saddle:
+ *   [-M  Sigma^T] [q          ]   [-r . E0]
+ *   [Sigma    0 ] [Psi - Psi_0] = [   Q   ],   r_ij = x_ij - X_i (minimum image)
+ * by restarted GMRES with every vector and scalar on the device.  Single-bead
+ * bodies (ions) have q = Q fixed; they are eliminated exactly and their
+ * Psi - Psi_0 is recovered with one FP64 evaluation.  Convergence is judged
+ * on the full system with the FP64 operator.
+ *   E0       [nrhs][3] external field per right-hand side
+ *   q_out    [nrhs][n] bead charges (initial guess on input when guess = USER)
+ *   psi_out  [nrhs][N_b] Psi - Psi_0 per body, or NULL
+ *   S_out    [nrhs][N_b][3] body dipoles S_i = sum_j r_ij q_ij (Eq. rigid_dipole), or NULL
+ *   stats    or NULL
+ * Returns IBPME_ERR_NOT_CONVERGED (with the last iterate written) if max_iter is hit. */
+ibpme_status induced_charge_solve(ibpme_ctx* ctx, int n, const double* x, const ibpme_bodies* bodies,
+                                  const double* E0, int nrhs, const ibpme_solve_opts* opts,
+                                  double* q_out, double* psi_out, double* S_out,
+                                  ibpme_solve_stats* stats);
+
+/* Forces and torques, Sec. III.C:
+ *   f_alpha = q_alpha E0 - 1/2 (grad_alpha M) : q q = q_alpha (E0 + E_alpha)   (Eq. beadforce)
+ *   F_i = sum_j f_ij,  L_i = sum_j r_ij x f_ij
+ *   U = 1/2 sum_i (Q_i Psi_i - S_i . E0), Psi_i = (Psi - Psi_0)_i - X_i . E0   (Eq. pot_syst)
+ * where E_alpha is the PME field of all charges at bead alpha (one spread, one
+ * FFT pair, a gradient gather and the real-space gradient), q a converged
+ * solution and E0 one field [3].  Q is taken from bodies->Q.
+ *   f_bead [n][3] or NULL; F, L [N_b][3] required; U [1] or NULL. */
+ibpme_status body_force_torque(ibpme_ctx* ctx, int n, const double* x, const double* q,
+                               const ibpme_bodies* bodies, const double* E0,
+                               double* f_bead, double* F, double* L, double* U);
+
+/* Brownian dynamics, Sec. V.A. */
+typedef struct {
+    double dt;                    /* time step (> 0) */
+    double gamma;                 /* drag coefficient of one bead (> 0) */
+    double kT;                    /* thermal energy (>= 0; 0 = deterministic) */
+    unsigned long long seed;      /* Philox4x32-10 key */
+    long long step;               /* step counter (part of the Philox counter) */
+} ibpme_bd_params;
+
+/* One Euler-Maruyama step (Eq. forward) with free-draining mobility M^H = I/gamma.
+ * The bead forces f_bead [n][3] are augmented by the Heyes-Melrose hard-sphere
+ * pair forces of Eq. hardsphereFD (beads of different bodies closer than 2a).
+ * Ions: dx = F dt/gamma + sqrt(2 kT dt/gamma) n.  Rigid bodies: U = F_i/(N_i gamma),
+ * Omega = (gamma J_i)^{-1} L_i, J_i = sum_j (|r_ij|^2 I - r_ij r_ij^T), Brownian
+ * displacements with covariance 2 kT dt times the same mobilities; beads move
+ * rigidly with the body.  Normals: Philox4x32-10 on counter
+ * (body, step, t, 0x1B5EED), key (seed lo, seed hi), Box-Muller on the first two words.
+ *   x_out [n][3] new positions, X_out [N_b][3] new reference points (may alias x / bodies->X
+ *   only if they are device pointers). */
+ibpme_status ibpme_bd_step(ibpme_ctx* ctx, int n, const double* x, const ibpme_bodies* bodies,
+                           const double* f_bead, const ibpme_bd_params* bd,
+                           double* x_out, double* X_out);
+
+/* ---- Instrumentation (no counterpart in the paper) ---- */
+
+/* Number of kernel launches the library has issued in this process (its own
+ * kernels only; cuFFT's launches are not counted). */
+long long ibpme_kernel_launches(void);
+
+/* Stages that can be timed: 0 near_build (cell list + pair table), 1 near_apply
+ * (real-space SpMV/field), 2 spread, 3 fft_forward, 4 scale, 5 fft_inverse,
+ * 6 gather (2-6: FP32 mesh), 7 krylov (Arnoldi/Givens kernels of one iteration),
+ * 8 bodies, 9-13 the FP64 mesh (spread64, fft_forward64, scale64, fft_inverse64,
+ * gather64).
+ * ibpme_profile(mask) enables CUDA-event timing of the stages in the bit mask
+ * (0 disables) and resets the totals; each enabled stage then records an event
+ * pair on the stream it runs on. */
+ibpme_status ibpme_profile(unsigned stage_mask);
+
+/* Synchronizes the device, then writes the accumulated milliseconds and the
+ * number of timed launches of the first max_stages stages (either array may be NULL). */
+ibpme_status ibpme_profile_read(int max_stages, double* total_ms, long long* launches);
+
+/* Name of a stage ("" if out of range). */
+const char* ibpme_stage_name(int stage);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* IBPME_H */

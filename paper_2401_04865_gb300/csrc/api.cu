@@ -1,0 +1,549 @@
+// api.cu -- the C ABI: context set-up (automatic parameters of Sec. III.D.2),
+// staging of host arrays, and the entry points declared in include/ibpme.h.
+#include "common.cuh"
+
+#include <chrono>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+namespace ibp {
+
+namespace {
+thread_local char g_err[1024] = "";
+constexpr double kPi = 3.14159265358979323846264338327950288;
+}  // namespace
+
+void set_error(const char* fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+}
+
+void fail(ibpme_status s, const char* fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+    throw Error(s);
+}
+
+namespace {
+
+template <typename F>
+ibpme_status guard(F&& f) {
+    try {
+        g_err[0] = '\0';
+        return f();
+    } catch (const Error& e) {
+        return e.status;
+    } catch (const std::bad_alloc&) {
+        set_error("host allocation failed");
+        return IBPME_ERR_OOM;
+    } catch (...) {
+        set_error("unexpected internal exception");
+        return IBPME_ERR_CUDA;
+    }
+}
+
+// Keeps the context's device current for the duration of a call.
+struct DeviceScope {
+    int prev = -1;
+    explicit DeviceScope(int dev) {
+        IBP_CUDA(cudaGetDevice(&prev));
+        if (prev != dev) IBP_CUDA(cudaSetDevice(dev));
+    }
+    ~DeviceScope() {
+        int cur = -1;
+        if (cudaGetDevice(&cur) == cudaSuccess && prev >= 0 && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+bool is_device_ptr(const void* p) {
+    if (!p) return false;
+    cudaPointerAttributes at{};
+    cudaError_t e = cudaPointerGetAttributes(&at, p);
+    if (e != cudaSuccess) {
+        cudaGetLastError();   // clear the sticky-free error of an unknown pointer
+        return false;
+    }
+    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+// Input array: device pointers pass through, host arrays are copied into the stage.
+const void* stage_in(ibpme_ctx* c, const void* p, size_t bytes, DevBuf& st) {
+    if (!p || bytes == 0 || is_device_ptr(p)) return p;
+    void* d = st.ensure(bytes);
+    IBP_CUDA(cudaMemcpyAsync(d, p, bytes, cudaMemcpyHostToDevice, c->stream));
+    return d;
+}
+
+// Output array: returns a device pointer to write to; host arrays get a stage
+// that finish_out() copies back.
+struct OutArg {
+    void* user = nullptr;
+    void* dev = nullptr;
+    size_t bytes = 0;
+    bool host = false;
+};
+
+OutArg stage_out(ibpme_ctx* c, void* p, size_t bytes, DevBuf& st, bool read_first = false) {
+    OutArg o;
+    o.user = p;
+    o.bytes = bytes;
+    if (!p || bytes == 0) return o;
+    if (is_device_ptr(p)) {
+        o.dev = p;
+        return o;
+    }
+    o.host = true;
+    o.dev = st.ensure(bytes);
+    if (read_first) IBP_CUDA(cudaMemcpyAsync(o.dev, p, bytes, cudaMemcpyHostToDevice, c->stream));
+    return o;
+}
+
+void finish_out(ibpme_ctx* c, const OutArg& o) {
+    if (o.host && o.bytes) IBP_CUDA(cudaMemcpyAsync(o.user, o.dev, o.bytes, cudaMemcpyDeviceToHost, c->stream));
+}
+
+__global__ void wrap_kernel(int n, const double* __restrict__ x, double L0, double L1, double L2,
+                            double* __restrict__ xw) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= 3 * n) return;
+    const int d = i % 3;
+    const double L = d == 0 ? L0 : (d == 1 ? L1 : L2);
+    xw[i] = wrap_coord(x[i], L);
+}
+
+__global__ void add_kernel(long long m, const double* __restrict__ a, const double* __restrict__ b,
+                           double* __restrict__ out) {
+    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i < m) out[i] = a[i] + b[i];
+}
+
+// qsum[r] += sum of the charges of right-hand side r
+__global__ void qsum_kernel(int n, const double* __restrict__ q, double* __restrict__ qsum) {
+    const int r = blockIdx.y;
+    double acc = 0.0;
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x)
+        acc += q[(size_t)r * n + t];
+    acc = warp_sum(acc);
+    if ((threadIdx.x & 31) == 0) atomicAdd(qsum + r, acc);
+}
+
+// psi = psi_real + psi_wave - k0 * sum(q): the real-space image sum carries the
+// k = 0 Fourier mode 1/(4 xi^2 V eps) that M (Sec. II) excludes.
+__global__ void combine_kernel(long long m, int n, const double* __restrict__ a, const double* __restrict__ b,
+                               const double* __restrict__ qsum, double k0, double* __restrict__ out) {
+    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i < m) out[i] = a[i] + b[i] - k0 * qsum[i / n];
+}
+
+bool good_fft_size(int n) {
+    for (int p : {2, 3, 5, 7})
+        while (n % p == 0) n /= p;
+    return n == 1;
+}
+
+void resolve_params(const ibpme_params* in, ibpme_params* p) {
+    *p = *in;
+    for (int d = 0; d < 3; ++d)
+        if (!(p->box[d] > 0.0) || !std::isfinite(p->box[d])) fail(IBPME_ERR_ARG, "box[%d] must be > 0", d);
+    if (!(p->bead_radius > 0.0)) fail(IBPME_ERR_ARG, "bead_radius must be > 0");
+    if (!(p->eps_f > 0.0)) fail(IBPME_ERR_ARG, "eps_f must be > 0");
+    if (p->precision != IBPME_FP64 && p->precision != IBPME_MIXED) fail(IBPME_ERR_ARG, "unknown precision");
+    if (p->max_rhs == 0) p->max_rhs = 3;
+    if (p->max_rhs < 1 || p->max_rhs > kMaxRhs) fail(IBPME_ERR_ARG, "max_rhs must be in 1..%d", kMaxRhs);
+    if (p->tol == 0.0) p->tol = 1e-6;
+    if (!(p->tol > 0.0 && p->tol < 1.0)) fail(IBPME_ERR_ARG, "tol must be in (0, 1)");
+    const double lnt = std::log(1.0 / p->tol);
+    const bool mesh_auto = p->mesh[0] == 0 && p->mesh[1] == 0 && p->mesh[2] == 0;
+    if (mesh_auto) {
+        if (!(p->xi > 0.0)) fail(IBPME_ERR_ARG, "mesh = 0 needs xi > 0");
+        const double kc = 2.0 * p->xi * std::sqrt(lnt);
+        for (int d = 0; d < 3; ++d) {
+            int m = (int)std::ceil(1.0 + p->box[d] * kc / kPi);
+            if (m < 8) m = 8;
+            while (!good_fft_size(m)) ++m;
+            p->mesh[d] = m;
+        }
+    }
+    for (int d = 0; d < 3; ++d)
+        if (p->mesh[d] < 2 || p->mesh[d] > 2048) fail(IBPME_ERR_ARG, "mesh[%d] = %d outside 2..2048", d, p->mesh[d]);
+    double kc = 1e300, h = 0.0, lmin = 1e300;
+    for (int d = 0; d < 3; ++d) {
+        kc = std::fmin(kc, kPi * (p->mesh[d] - 1) / p->box[d]);
+        h = std::fmax(h, p->box[d] / p->mesh[d]);
+        lmin = std::fmin(lmin, p->box[d]);
+    }
+    if (p->xi == 0.0) p->xi = kc / (2.0 * std::sqrt(lnt));
+    if (!(p->xi > 0.0)) fail(IBPME_ERR_ARG, "xi must be > 0");
+    if (p->P == 0) p->P = (int)std::ceil(2.0 * lnt / kPi);
+    if (p->P < 1 || p->P > kMaxP) fail(IBPME_ERR_ARG, "P = %d outside 1..%d", p->P, kMaxP);
+    for (int d = 0; d < 3; ++d)
+        if (p->mesh[d] < p->P) fail(IBPME_ERR_ARG, "mesh[%d] = %d smaller than P = %d", d, p->mesh[d], p->P);
+    if (p->eta == 0.0) p->eta = h * h * p->xi * p->xi * p->P / kPi;
+    if (!(p->eta > 0.0)) fail(IBPME_ERR_ARG, "eta must be > 0");
+    if (p->r_cut == 0.0) p->r_cut = std::sqrt(lnt) / p->xi + 2.0 * p->bead_radius;
+    if (!(p->r_cut > 0.0) || p->r_cut >= 0.5 * lmin)
+        fail(IBPME_ERR_ARG, "r_cut = %g must be in (0, L/2 = %g); use a finer mesh or a larger xi", p->r_cut,
+             0.5 * lmin);
+}
+
+MeshGeom make_geom(const ibpme_params& p) {
+    MeshGeom g{};
+    const double xi = p.xi, eta = p.eta;
+    double vh = 1.0;
+    for (int d = 0; d < 3; ++d) {
+        g.L[d] = p.box[d];
+        g.N[d] = p.mesh[d];
+        g.h[d] = p.box[d] / p.mesh[d];
+        g.inv_h[d] = p.mesh[d] / p.box[d];
+        g.kappa[d] = 2.0 * xi * xi * g.h[d] * g.h[d] / eta;
+        vh *= g.h[d];
+    }
+    g.P = p.P;
+    g.c = std::pow(2.0 * xi * xi / (kPi * eta), 1.5);
+    g.gather = g.c * vh / p.eps_f;
+    g.grad = g.gather * 4.0 * xi * xi / eta;
+    g.G = (long long)p.mesh[0] * p.mesh[1] * p.mesh[2];
+    g.Gc = (long long)(p.mesh[0] / 2 + 1) * p.mesh[1] * p.mesh[2];
+    return g;
+}
+
+void check_n(int n) {
+    if (n < 0) fail(IBPME_ERR_ARG, "n must be >= 0");
+}
+
+}  // namespace
+
+void* pinned_host(ibpme_ctx* c, size_t bytes) {
+    if (bytes > c->pinned_bytes) {
+        if (c->pinned) cudaFreeHost(c->pinned);
+        c->pinned = nullptr;
+        c->pinned_bytes = 0;
+        size_t want = bytes < 4096 ? 4096 : bytes;
+        IBP_CUDA(cudaMallocHost(&c->pinned, want));
+        c->pinned_bytes = want;
+    }
+    return c->pinned;
+}
+
+void wrap_positions(ibpme_ctx* c, int n, const double* x, double* xw) {
+    if (n == 0) return;
+    wrap_kernel<<<div_up(3LL * n, 256), 256, 0, c->stream>>>(n, x, c->p.box[0], c->p.box[1], c->p.box[2], xw);
+    IBP_CHECK_LAUNCH();
+}
+
+void pme_apply(ibpme_ctx* c, int n, const double* xw, const double* q, int nrhs, int prec, double* psi,
+               double* E, bool near_ready) {
+    if (!near_ready) near_build(c, n, xw, E != nullptr);
+    const size_t m = (size_t)nrhs * n;
+    double* pr = static_cast<double*>(c->psi_r.ensure(sizeof(double) * (m ? m : 1)));
+    double* pk = static_cast<double*>(c->psi_k.ensure(sizeof(double) * (m ? m : 1)));
+    double* er = nullptr;
+    double* ek = nullptr;
+    if (E) {
+        er = static_cast<double*>(c->E_r.ensure(sizeof(double) * 3 * (m ? m : 1)));
+        ek = static_cast<double*>(c->E_k.ensure(sizeof(double) * 3 * (m ? m : 1)));
+    }
+    near_apply(c, n, q, nrhs, pr);
+    if (E) near_field(c, n, xw, q, nrhs, er);
+    if (prec == IBPME_MIXED) {
+        if (!c->have32) fail(IBPME_ERR_ARG, "mixed precision needs a context created with IBPME_MIXED");
+        c->mesh32.spread(n, xw, q, nrhs, c->stream);
+        c->mesh32.transform(nrhs, c->stream);
+        c->mesh32.gather(n, xw, nrhs, pk, ek, c->stream);
+    } else {
+        c->mesh64.spread(n, xw, q, nrhs, c->stream);
+        c->mesh64.transform(nrhs, c->stream);
+        c->mesh64.gather(n, xw, nrhs, pk, ek, c->stream);
+    }
+    if (m) {
+        double* qsum = static_cast<double*>(c->scalars.ensure(sizeof(double) * kMaxRhs));
+        IBP_CUDA(cudaMemsetAsync(qsum, 0, sizeof(double) * nrhs, c->stream));
+        qsum_kernel<<<dim3(div_up(n, 256) < 64 ? div_up(n, 256) : 64, nrhs), 256, 0, c->stream>>>(n, q, qsum);
+        IBP_CHECK_LAUNCH();
+        const double V = c->p.box[0] * c->p.box[1] * c->p.box[2];
+        const double k0 = 1.0 / (4.0 * c->xi * c->xi * V * c->eps);
+        combine_kernel<<<div_up((long long)m, 256), 256, 0, c->stream>>>((long long)m, n, pr, pk, qsum, k0, psi);
+        IBP_CHECK_LAUNCH();
+        if (E) {
+            add_kernel<<<div_up(3LL * m, 256), 256, 0, c->stream>>>(3LL * (long long)m, er, ek, E);
+            IBP_CHECK_LAUNCH();
+        }
+    }
+}
+
+}  // namespace ibp
+
+using namespace ibp;
+
+IBP_API const char* ibpme_last_error(void) { return g_err; }
+
+IBP_API ibpme_status pme_setup(ibpme_ctx** ctx, const ibpme_params* params, void* cuda_stream) {
+    if (!ctx) {
+        set_error("ctx is NULL");
+        return IBPME_ERR_ARG;
+    }
+    *ctx = nullptr;
+    return guard([&]() -> ibpme_status {
+        if (!params) fail(IBPME_ERR_ARG, "params is NULL");
+        ibpme_ctx* c = new ibpme_ctx();
+        try {
+            resolve_params(params, &c->p);
+            IBP_CUDA(cudaGetDevice(&c->device));
+            c->stream = static_cast<cudaStream_t>(cuda_stream);
+            c->xi = c->p.xi;
+            c->eta = c->p.eta;
+            c->rc = c->p.r_cut;
+            c->a = c->p.bead_radius;
+            c->eps = c->p.eps_f;
+            c->P = c->p.P;
+            c->geom = make_geom(c->p);
+            c->mesh64.init(c->geom, c->p.max_rhs, c->xi, c->eta, c->a, c->stream);
+            c->mesh64.plans(1, c->stream);
+            if (c->p.precision == IBPME_MIXED) {
+                c->mesh32.init(c->geom, c->p.max_rhs, c->xi, c->eta, c->a, c->stream);
+                c->mesh32.plans(1, c->stream);
+                c->have32 = true;
+            }
+            near_setup(c);
+            pinned_host(c, 4096);
+            IBP_CUDA(cudaStreamSynchronize(c->stream));
+        } catch (...) {
+            pme_destroy(c);
+            throw;
+        }
+        *ctx = c;
+        return IBPME_OK;
+    });
+}
+
+IBP_API ibpme_status pme_destroy(ibpme_ctx* c) {
+    if (!c) return IBPME_OK;
+    if (c->stream || true) cudaStreamSynchronize(c->stream);
+    krylov_destroy(c);
+    c->mesh64.destroy();
+    c->mesh32.destroy();
+    if (c->pinned) cudaFreeHost(c->pinned);
+    c->pinned = nullptr;
+    delete c;
+    return IBPME_OK;
+}
+
+IBP_API ibpme_status ibpme_set_stream(ibpme_ctx* c, void* cuda_stream) {
+    if (!c) {
+        set_error("ctx is NULL");
+        return IBPME_ERR_ARG;
+    }
+    c->stream = static_cast<cudaStream_t>(cuda_stream);
+    return IBPME_OK;
+}
+
+IBP_API ibpme_status ibpme_get_params(const ibpme_ctx* c, ibpme_params* out) {
+    if (!c || !out) {
+        set_error("NULL argument");
+        return IBPME_ERR_ARG;
+    }
+    *out = c->p;
+    return IBPME_OK;
+}
+
+IBP_API ibpme_status pme_spread(ibpme_ctx* c, int n, const double* x, const double* q, int nrhs, void* grid_out) {
+    return guard([&]() -> ibpme_status {
+        if (!c) fail(IBPME_ERR_ARG, "ctx is NULL");
+        DeviceScope ds(c->device);
+        check_n(n);
+        if (nrhs < 1 || nrhs > c->p.max_rhs) fail(IBPME_ERR_ARG, "nrhs %d outside 1..%d", nrhs, c->p.max_rhs);
+        if (n > 0 && (!x || !q)) fail(IBPME_ERR_ARG, "x and q are required");
+        const double* dx = static_cast<const double*>(stage_in(c, x, sizeof(double) * 3 * n, c->st_x));
+        const double* dq = static_cast<const double*>(stage_in(c, q, sizeof(double) * (size_t)nrhs * n, c->st_q));
+        double* xw = static_cast<double*>(c->xw.ensure(sizeof(double) * 3 * (n ? n : 1)));
+        wrap_positions(c, n, dx, xw);
+        const bool mixed = c->p.precision == IBPME_MIXED;
+        const size_t gb = (mixed ? sizeof(float) : sizeof(double)) * (size_t)c->geom.G * nrhs;
+        if (mixed)
+            c->mesh32.spread(n, xw, dq, nrhs, c->stream);
+        else
+            c->mesh64.spread(n, xw, dq, nrhs, c->stream);
+        if (grid_out) {
+            const void* src = mixed ? c->mesh32.grid.p : c->mesh64.grid.p;
+            const cudaMemcpyKind kind = is_device_ptr(grid_out) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+            IBP_CUDA(cudaMemcpyAsync(grid_out, src, gb, kind, c->stream));
+            if (kind == cudaMemcpyDeviceToHost) IBP_CUDA(cudaStreamSynchronize(c->stream));
+        }
+        return IBPME_OK;
+    });
+}
+
+IBP_API ibpme_status pme_field(ibpme_ctx* c, int n, const double* x, const double* q, int nrhs, double* psi,
+                               double* E) {
+    return guard([&]() -> ibpme_status {
+        if (!c) fail(IBPME_ERR_ARG, "ctx is NULL");
+        DeviceScope ds(c->device);
+        check_n(n);
+        if (nrhs < 1 || nrhs > c->p.max_rhs) fail(IBPME_ERR_ARG, "nrhs %d outside 1..%d", nrhs, c->p.max_rhs);
+        if (n > 0 && (!x || !q || !psi)) fail(IBPME_ERR_ARG, "x, q and psi are required");
+        const double* dx = static_cast<const double*>(stage_in(c, x, sizeof(double) * 3 * n, c->st_x));
+        const double* dq = static_cast<const double*>(stage_in(c, q, sizeof(double) * (size_t)nrhs * n, c->st_q));
+        OutArg op = stage_out(c, psi, sizeof(double) * (size_t)nrhs * n, c->st_out1);
+        OutArg oe = stage_out(c, E, sizeof(double) * 3 * (size_t)nrhs * n, c->st_out2);
+        if (n == 0) return IBPME_OK;
+        double* xw = static_cast<double*>(c->xw.ensure(sizeof(double) * 3 * n));
+        wrap_positions(c, n, dx, xw);
+        pme_apply(c, n, xw, dq, nrhs, c->p.precision, static_cast<double*>(op.dev), static_cast<double*>(oe.dev),
+                  false);
+        finish_out(c, op);
+        finish_out(c, oe);
+        if (op.host || oe.host) IBP_CUDA(cudaStreamSynchronize(c->stream));
+        return IBPME_OK;
+    });
+}
+
+namespace {
+
+struct BodiesDev {
+    ibpme_bodies b{};
+};
+
+// Stages the body arrays and uploads the bookkeeping; returns the device-side view.
+void prepare_bodies(ibpme_ctx* c, int n, const ibpme_bodies* bodies, const double* xw) {
+    if (!bodies) fail(IBPME_ERR_ARG, "bodies is NULL");
+    const int nb = bodies->n_bodies;
+    if (nb < 1) fail(IBPME_ERR_ARG, "n_bodies must be >= 1");
+    if (!bodies->body_offsets || !bodies->X || !bodies->Q) fail(IBPME_ERR_ARG, "body arrays are required");
+    ibpme_bodies d{};
+    d.n_bodies = nb;
+    d.body_offsets = static_cast<const int*>(stage_in(c, bodies->body_offsets, sizeof(int) * (nb + 1), c->st_off));
+    d.X = static_cast<const double*>(stage_in(c, bodies->X, sizeof(double) * 3 * nb, c->st_X));
+    d.Q = static_cast<const double*>(stage_in(c, bodies->Q, sizeof(double) * nb, c->st_Q));
+    bodies_upload(c, n, &d, xw);
+}
+
+}  // namespace
+
+IBP_API ibpme_status induced_charge_solve(ibpme_ctx* c, int n, const double* x, const ibpme_bodies* bodies,
+                                          const double* E0, int nrhs, const ibpme_solve_opts* opts,
+                                          double* q_out, double* psi_out, double* S_out,
+                                          ibpme_solve_stats* stats) {
+    return guard([&]() -> ibpme_status {
+        if (!c) fail(IBPME_ERR_ARG, "ctx is NULL");
+        DeviceScope ds(c->device);
+        const auto t0 = std::chrono::steady_clock::now();
+        check_n(n);
+        if (n == 0) fail(IBPME_ERR_ARG, "a solve needs at least one bead");
+        if (nrhs < 1 || nrhs > c->p.max_rhs) fail(IBPME_ERR_ARG, "nrhs %d outside 1..%d", nrhs, c->p.max_rhs);
+        if (!x || !E0 || !q_out) fail(IBPME_ERR_ARG, "x, E0 and q_out are required");
+        ibpme_solve_opts o{};
+        o.precision = -1;
+        if (opts) o = *opts;
+        SolveArgs a{};
+        a.n = n;
+        a.nrhs = nrhs;
+        a.prec = o.precision < 0 ? c->p.precision : o.precision;
+        if (a.prec != IBPME_FP64 && a.prec != IBPME_MIXED) fail(IBPME_ERR_ARG, "unknown solve precision");
+        if (a.prec == IBPME_MIXED && !c->have32) fail(IBPME_ERR_ARG, "mixed solve needs a mixed context");
+        a.rtol = o.rtol > 0 ? o.rtol : 1e-6;
+        a.restart = o.restart > 0 ? o.restart : 50;
+        if (a.restart > 128) fail(IBPME_ERR_ARG, "restart must be <= 128");
+        a.max_iter = o.max_iter > 0 ? o.max_iter : 3000;
+        if (o.guess == IBPME_GUESS_LEARNED) fail(IBPME_ERR_ARG, "learned warm start is not available in this build");
+        if (o.guess != IBPME_GUESS_ZERO && o.guess != IBPME_GUESS_USER) fail(IBPME_ERR_ARG, "unknown guess mode");
+        a.user_guess = o.guess == IBPME_GUESS_USER;
+        const double* dx = static_cast<const double*>(stage_in(c, x, sizeof(double) * 3 * n, c->st_x));
+        a.E0 = static_cast<const double*>(stage_in(c, E0, sizeof(double) * 3 * nrhs, c->st_E0));
+        double* xw = static_cast<double*>(c->xw.ensure(sizeof(double) * 3 * n));
+        wrap_positions(c, n, dx, xw);
+        a.xw = xw;
+        prepare_bodies(c, n, bodies, xw);
+        const int nb = bodies->n_bodies;
+        OutArg oq = stage_out(c, q_out, sizeof(double) * (size_t)nrhs * n, c->st_out1, a.user_guess);
+        OutArg op = stage_out(c, psi_out, sizeof(double) * (size_t)nrhs * nb, c->st_out2);
+        OutArg os = stage_out(c, S_out, sizeof(double) * 3 * (size_t)nrhs * nb, c->st_out3);
+        a.q = static_cast<double*>(oq.dev);
+        a.psi = static_cast<double*>(op.dev);
+        ibpme_solve_stats st{};
+        solve(c, a, &st);
+        if (S_out) body_dipoles(c, n, a.q, nrhs, static_cast<double*>(os.dev));
+        finish_out(c, oq);
+        finish_out(c, op);
+        finish_out(c, os);
+        IBP_CUDA(cudaStreamSynchronize(c->stream));
+        st.time_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+        if (stats) *stats = st;
+        if (!(st.rel_residual <= a.rtol)) {
+            if (!std::isfinite(st.rel_residual)) fail(IBPME_ERR_NONFINITE, "non-finite residual in the solve");
+            set_error("not converged: relative residual %.3e after %d iterations", st.rel_residual, st.iters);
+            return IBPME_ERR_NOT_CONVERGED;
+        }
+        return IBPME_OK;
+    });
+}
+
+IBP_API ibpme_status body_force_torque(ibpme_ctx* c, int n, const double* x, const double* q,
+                                       const ibpme_bodies* bodies, const double* E0, double* f_bead, double* F,
+                                       double* L, double* U) {
+    return guard([&]() -> ibpme_status {
+        if (!c) fail(IBPME_ERR_ARG, "ctx is NULL");
+        DeviceScope ds(c->device);
+        check_n(n);
+        if (n == 0) fail(IBPME_ERR_ARG, "n must be >= 1");
+        if (!x || !q || !E0 || !F || !L) fail(IBPME_ERR_ARG, "x, q, E0, F and L are required");
+        const int nb = bodies ? bodies->n_bodies : 0;
+        const double* dx = static_cast<const double*>(stage_in(c, x, sizeof(double) * 3 * n, c->st_x));
+        const double* dq = static_cast<const double*>(stage_in(c, q, sizeof(double) * n, c->st_q));
+        const double* dE0 = static_cast<const double*>(stage_in(c, E0, sizeof(double) * 3, c->st_E0));
+        double* xw = static_cast<double*>(c->xw.ensure(sizeof(double) * 3 * n));
+        wrap_positions(c, n, dx, xw);
+        prepare_bodies(c, n, bodies, xw);
+        OutArg of = stage_out(c, f_bead, sizeof(double) * 3 * n, c->st_out1);
+        OutArg oF = stage_out(c, F, sizeof(double) * 3 * nb, c->st_out2);
+        OutArg oL = stage_out(c, L, sizeof(double) * 3 * nb, c->st_out3);
+        OutArg oU = stage_out(c, U, sizeof(double), c->st_out4);
+        double* psi = static_cast<double*>(c->qfull.ensure(sizeof(double) * 4 * n));   // psi [n] then E [n][3]
+        double* E = psi + n;
+        pme_apply(c, n, xw, dq, 1, c->p.precision, psi, E, false);
+        double* f = of.dev ? static_cast<double*>(of.dev) : static_cast<double*>(c->st_f.ensure(sizeof(double) * 3 * n));
+        bead_forces(c, n, dq, dE0, E, f);
+        body_reduce_force_torque(c, n, f, static_cast<double*>(oF.dev), static_cast<double*>(oL.dev));
+        if (U) body_energy(c, n, dq, psi, dE0, static_cast<double*>(oU.dev));
+        finish_out(c, of);
+        finish_out(c, oF);
+        finish_out(c, oL);
+        finish_out(c, oU);
+        if (of.host || oF.host || oL.host || oU.host) IBP_CUDA(cudaStreamSynchronize(c->stream));
+        return IBPME_OK;
+    });
+}
+
+IBP_API ibpme_status ibpme_bd_step(ibpme_ctx* c, int n, const double* x, const ibpme_bodies* bodies,
+                                   const double* f_bead, const ibpme_bd_params* bd, double* x_out,
+                                   double* X_out) {
+    return guard([&]() -> ibpme_status {
+        if (!c) fail(IBPME_ERR_ARG, "ctx is NULL");
+        DeviceScope ds(c->device);
+        check_n(n);
+        if (n == 0) fail(IBPME_ERR_ARG, "n must be >= 1");
+        if (!x || !f_bead || !bd || !x_out || !X_out) fail(IBPME_ERR_ARG, "missing argument");
+        if (!(bd->dt > 0) || !(bd->gamma > 0) || !(bd->kT >= 0)) fail(IBPME_ERR_ARG, "need dt > 0, gamma > 0, kT >= 0");
+        const int nb = bodies ? bodies->n_bodies : 0;
+        const double* dx = static_cast<const double*>(stage_in(c, x, sizeof(double) * 3 * n, c->st_x));
+        const double* df = static_cast<const double*>(stage_in(c, f_bead, sizeof(double) * 3 * n, c->st_q));
+        double* xw = static_cast<double*>(c->xw.ensure(sizeof(double) * 3 * n));
+        wrap_positions(c, n, dx, xw);
+        prepare_bodies(c, n, bodies, xw);
+        near_build(c, n, xw, false);
+        OutArg ox = stage_out(c, x_out, sizeof(double) * 3 * n, c->st_out1);
+        OutArg oX = stage_out(c, X_out, sizeof(double) * 3 * nb, c->st_out2);
+        bd_step(c, n, xw, df, bd, static_cast<double*>(ox.dev), static_cast<double*>(oX.dev));
+        finish_out(c, ox);
+        finish_out(c, oX);
+        if (ox.host || oX.host) IBP_CUDA(cudaStreamSynchronize(c->stream));
+        return IBPME_OK;
+    });
+}

@@ -1,0 +1,399 @@
+// bodies.cu -- bead <-> body bookkeeping and segmented reductions over the
+// contiguous bead ranges of the summation tensor Sigma (Appendix): dipoles
+// (Eq. rigid_dipole), bead forces (Eq. beadforce), body forces and torques
+// (Sec. III.C), the energy (Eq. pot_syst) and the Brownian-dynamics step of
+// Sec. V.A (Eq. forward, Eq. hardsphereFD).  One warp per body.
+#include "common.cuh"
+
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+namespace ibp {
+
+namespace {
+
+__global__ void bead_body_kernel(int nb, const int* __restrict__ off, int* __restrict__ bead_body) {
+    const int b = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (b >= nb) return;
+    for (int j = off[b] + lane; j < off[b + 1]; j += 32) bead_body[j] = b;
+}
+
+__global__ void rel_kernel(int n, const double* __restrict__ xw, const int* __restrict__ bead_body,
+                           const double* __restrict__ X, double L0, double L1, double L2, double* __restrict__ rel) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int b = bead_body[i];
+    rel[3 * i + 0] = min_image(xw[3 * i + 0] - X[3 * b + 0], L0);
+    rel[3 * i + 1] = min_image(xw[3 * i + 1] - X[3 * b + 1], L1);
+    rel[3 * i + 2] = min_image(xw[3 * i + 2] - X[3 * b + 2], L2);
+}
+
+__global__ void dipole_kernel(int nb, int n, int nrhs, const int* __restrict__ off, const double* __restrict__ rel,
+                              const double* __restrict__ q, double* __restrict__ S) {
+    const int b = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (b >= nb) return;
+    for (int r = 0; r < nrhs; ++r) {
+        double sx = 0, sy = 0, sz = 0;
+        for (int j = off[b] + lane; j < off[b + 1]; j += 32) {
+            const double qq = q[(size_t)r * n + j];
+            sx += rel[3 * j + 0] * qq;
+            sy += rel[3 * j + 1] * qq;
+            sz += rel[3 * j + 2] * qq;
+        }
+        sx = warp_sum(sx);
+        sy = warp_sum(sy);
+        sz = warp_sum(sz);
+        if (lane == 0) {
+            double* o = S + ((size_t)r * nb + b) * 3;
+            o[0] = sx;
+            o[1] = sy;
+            o[2] = sz;
+        }
+    }
+}
+
+__global__ void force_kernel(int n, const double* __restrict__ q, const double* __restrict__ E0,
+                             const double* __restrict__ E, double* __restrict__ f) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= 3 * n) return;
+    f[i] = q[i / 3] * (E0[i % 3] + E[i]);
+}
+
+__global__ void force_torque_kernel(int nb, const int* __restrict__ off, const double* __restrict__ rel,
+                                    const double* __restrict__ f, double* __restrict__ F, double* __restrict__ L) {
+    const int b = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (b >= nb) return;
+    double fx = 0, fy = 0, fz = 0, lx = 0, ly = 0, lz = 0;
+    for (int j = off[b] + lane; j < off[b + 1]; j += 32) {
+        const double ax = f[3 * j], ay = f[3 * j + 1], az = f[3 * j + 2];
+        const double rx = rel[3 * j], ry = rel[3 * j + 1], rz = rel[3 * j + 2];
+        fx += ax; fy += ay; fz += az;
+        lx += ry * az - rz * ay;
+        ly += rz * ax - rx * az;
+        lz += rx * ay - ry * ax;
+    }
+    fx = warp_sum(fx); fy = warp_sum(fy); fz = warp_sum(fz);
+    lx = warp_sum(lx); ly = warp_sum(ly); lz = warp_sum(lz);
+    if (lane == 0) {
+        F[3 * b] = fx; F[3 * b + 1] = fy; F[3 * b + 2] = fz;
+        L[3 * b] = lx; L[3 * b + 1] = ly; L[3 * b + 2] = lz;
+    }
+}
+
+// Per-body energy contribution Q_i Psi_i - S_i . E0 with
+// Psi_i - Psi_0,i = mean_j (psi_ij - r_ij . E0) (Eq. beadpot1) and Psi_0,i = -X_i . E0.
+__global__ void energy_body_kernel(int nb, const int* __restrict__ off, const double* __restrict__ rel,
+                                   const double* __restrict__ q, const double* __restrict__ psi,
+                                   const double* __restrict__ E0, const double* __restrict__ X,
+                                   const double* __restrict__ Q, double* __restrict__ contrib) {
+    const int b = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (b >= nb) return;
+    const double e0 = E0[0], e1 = E0[1], e2 = E0[2];
+    double pr = 0, sE = 0;
+    for (int j = off[b] + lane; j < off[b + 1]; j += 32) {
+        const double rE = rel[3 * j] * e0 + rel[3 * j + 1] * e1 + rel[3 * j + 2] * e2;
+        pr += psi[j] - rE;
+        sE += q[j] * rE;
+    }
+    pr = warp_sum(pr);
+    sE = warp_sum(sE);
+    if (lane == 0) {
+        const double cnt = (double)(off[b + 1] - off[b]);
+        const double Psi = pr / cnt - (X[3 * b] * e0 + X[3 * b + 1] * e1 + X[3 * b + 2] * e2);
+        contrib[b] = Q[b] * Psi - sE;
+    }
+}
+
+__global__ void half_sum_kernel(int m, const double* __restrict__ v, double* __restrict__ out) {
+    __shared__ double s[32];
+    double acc = 0;
+    for (int i = threadIdx.x; i < m; i += blockDim.x) acc += v[i];
+    acc = warp_sum(acc);
+    if ((threadIdx.x & 31) == 0) s[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        double t = threadIdx.x < (blockDim.x >> 5) ? s[threadIdx.x] : 0.0;
+        t = warp_sum(t);
+        if (threadIdx.x == 0) *out = 0.5 * t;
+    }
+}
+
+// ---- Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11) and Box-Muller ----
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k) {
+    const unsigned M0 = 0xD2511F53u, M1 = 0xCD9E8D57u, W0 = 0x9E3779B9u, W1 = 0xBB67AE85u;
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const unsigned lo0 = M0 * c.x, hi0 = __umulhi(M0, c.x);
+        const unsigned lo1 = M1 * c.z, hi1 = __umulhi(M1, c.z);
+        c = make_uint4(hi1 ^ c.y ^ k.x, lo1, hi0 ^ c.w ^ k.y, lo0);
+        if (r < 9) {
+            k.x += W0;
+            k.y += W1;
+        }
+    }
+    return c;
+}
+
+__device__ void normals6(unsigned entity, unsigned step, unsigned long long seed, double* z) {
+    const uint2 key = make_uint2((unsigned)(seed & 0xffffffffull), (unsigned)(seed >> 32));
+    const double two_pi = 6.283185307179586476925286766559;
+    for (unsigned t = 0; t < 3; ++t) {
+        const uint4 w = philox4x32_10(make_uint4(entity, step, t, 0x1B5EEDu), key);
+        const double u1 = ((double)w.x + 0.5) * 2.3283064365386963e-10;
+        const double u2 = ((double)w.y + 0.5) * 2.3283064365386963e-10;
+        const double rad = sqrt(-2.0 * log(u1));
+        z[2 * t] = rad * cos(two_pi * u2);
+        z[2 * t + 1] = rad * sin(two_pi * u2);
+    }
+}
+
+// f_tot = f_bead + Heyes-Melrose forces gamma/(2 dt) (2a - r) (x_a - x_b)/r for
+// r < 2a between beads of different bodies (Eq. hardsphereFD).
+__global__ void hard_sphere_kernel(int n, const double* __restrict__ xw, double L0, double L1, double L2,
+                                   const long long* __restrict__ rowptr, const int* __restrict__ col,
+                                   const int* __restrict__ bead_body, double a, double coef,
+                                   const double* __restrict__ f_in, double* __restrict__ f_out) {
+    const int al = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (al >= n) return;
+    const int ba = bead_body[al];
+    const double x0 = xw[3 * al], y0 = xw[3 * al + 1], z0 = xw[3 * al + 2];
+    double fx = 0, fy = 0, fz = 0;
+    for (long long p = rowptr[al] + lane; p < rowptr[al + 1]; p += 32) {
+        const int be = col[p];
+        if (bead_body[be] == ba) continue;
+        const double dx = min_image(x0 - xw[3 * be], L0);
+        const double dy = min_image(y0 - xw[3 * be + 1], L1);
+        const double dz = min_image(z0 - xw[3 * be + 2], L2);
+        const double r = sqrt(dx * dx + dy * dy + dz * dz);
+        if (r < 2.0 * a && r > 0.0) {
+            const double m = coef * (2.0 * a - r) / r;
+            fx += m * dx;
+            fy += m * dy;
+            fz += m * dz;
+        }
+    }
+    fx = warp_sum(fx);
+    fy = warp_sum(fy);
+    fz = warp_sum(fz);
+    if (lane == 0) {
+        f_out[3 * al] = f_in[3 * al] + fx;
+        f_out[3 * al + 1] = f_in[3 * al + 1] + fy;
+        f_out[3 * al + 2] = f_in[3 * al + 2] + fz;
+    }
+}
+
+struct BdConst {
+    double dt, gamma, kT;
+    unsigned long long seed;
+    unsigned step;
+};
+
+__device__ void rotation_matrix(const double* th, double* R) {
+    const double ang = sqrt(th[0] * th[0] + th[1] * th[1] + th[2] * th[2]);
+    if (ang == 0.0) {
+        for (int i = 0; i < 9; ++i) R[i] = (i % 4 == 0) ? 1.0 : 0.0;
+        return;
+    }
+    const double kx = th[0] / ang, ky = th[1] / ang, kz = th[2] / ang;
+    const double K[9] = {0, -kz, ky, kz, 0, -kx, -ky, kx, 0};
+    const double s = sin(ang), c1 = 1.0 - cos(ang);
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) {
+            double k2 = 0;
+            for (int m = 0; m < 3; ++m) k2 += K[3 * i + m] * K[3 * m + j];
+            R[3 * i + j] = (i == j ? 1.0 : 0.0) + s * K[3 * i + j] + c1 * k2;
+        }
+}
+
+// One warp per body: F, L, J; lane 0 draws the noise and forms U, Omega, R.
+__global__ void bd_body_kernel(int nb, const int* __restrict__ off, const double* __restrict__ rel,
+                               const double* __restrict__ f, const double* __restrict__ X, BdConst bc,
+                               double* __restrict__ X_out, double* __restrict__ Rm) {
+    const int b = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (b >= nb) return;
+    double F[3] = {0, 0, 0}, L[3] = {0, 0, 0}, J[6] = {0, 0, 0, 0, 0, 0};
+    for (int j = off[b] + lane; j < off[b + 1]; j += 32) {
+        const double rx = rel[3 * j], ry = rel[3 * j + 1], rz = rel[3 * j + 2];
+        const double ax = f[3 * j], ay = f[3 * j + 1], az = f[3 * j + 2];
+        F[0] += ax; F[1] += ay; F[2] += az;
+        L[0] += ry * az - rz * ay;
+        L[1] += rz * ax - rx * az;
+        L[2] += rx * ay - ry * ax;
+        const double rr = rx * rx + ry * ry + rz * rz;
+        J[0] += rr - rx * rx; J[1] += -rx * ry; J[2] += -rx * rz;
+        J[3] += rr - ry * ry; J[4] += -ry * rz; J[5] += rr - rz * rz;
+    }
+    for (int i = 0; i < 3; ++i) { F[i] = warp_sum(F[i]); L[i] = warp_sum(L[i]); }
+    for (int i = 0; i < 6; ++i) J[i] = warp_sum(J[i]);
+    if (lane != 0) return;
+    const int Ni = off[b + 1] - off[b];
+    double z[6];
+    normals6((unsigned)b, bc.step, bc.seed, z);
+    const double mt = 1.0 / (Ni * bc.gamma);
+    const double st = sqrt(2.0 * bc.kT * bc.dt * mt);
+    for (int i = 0; i < 3; ++i) X_out[3 * b + i] = X[3 * b + i] + F[i] * mt * bc.dt + st * z[i];
+    double R[9] = {1, 0, 0, 0, 1, 0, 0, 0, 1};
+    if (Ni > 1) {
+        // symmetric 3x3 gamma J and its inverse (adjugate / determinant)
+        const double a00 = bc.gamma * J[0], a01 = bc.gamma * J[1], a02 = bc.gamma * J[2];
+        const double a11 = bc.gamma * J[3], a12 = bc.gamma * J[4], a22 = bc.gamma * J[5];
+        const double c00 = a11 * a22 - a12 * a12, c01 = a02 * a12 - a01 * a22, c02 = a01 * a12 - a02 * a11;
+        const double det = a00 * c00 + a01 * c01 + a02 * c02;
+        const double tr = a00 + a11 + a22;
+        if (det > 1e-14 * tr * tr * tr) {
+            const double id = 1.0 / det;
+            const double m00 = c00 * id, m01 = c01 * id, m02 = c02 * id;
+            const double m11 = (a00 * a22 - a02 * a02) * id, m12 = (a01 * a02 - a00 * a12) * id;
+            const double m22 = (a00 * a11 - a01 * a01) * id;
+            const double Om[3] = {m00 * L[0] + m01 * L[1] + m02 * L[2], m01 * L[0] + m11 * L[1] + m12 * L[2],
+                                  m02 * L[0] + m12 * L[1] + m22 * L[2]};
+            // Cholesky factor of the rotational mobility
+            const double l00 = sqrt(m00);
+            const double l10 = m01 / l00, l20 = m02 / l00;
+            const double l11 = sqrt(m11 - l10 * l10);
+            const double l21 = (m12 - l20 * l10) / l11;
+            const double l22 = sqrt(m22 - l20 * l20 - l21 * l21);
+            const double sr = sqrt(2.0 * bc.kT * bc.dt);
+            const double th[3] = {Om[0] * bc.dt + sr * (l00 * z[3]),
+                                  Om[1] * bc.dt + sr * (l10 * z[3] + l11 * z[4]),
+                                  Om[2] * bc.dt + sr * (l20 * z[3] + l21 * z[4] + l22 * z[5])};
+            rotation_matrix(th, R);
+        }
+    }
+    for (int i = 0; i < 9; ++i) Rm[9 * b + i] = R[i];
+}
+
+__global__ void bd_bead_kernel(int n, const int* __restrict__ bead_body, const double* __restrict__ rel,
+                               const double* __restrict__ X_out, const double* __restrict__ Rm,
+                               double* __restrict__ x_out) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int b = bead_body[i];
+    const double* R = Rm + 9 * b;
+    const double rx = rel[3 * i], ry = rel[3 * i + 1], rz = rel[3 * i + 2];
+    x_out[3 * i + 0] = X_out[3 * b + 0] + R[0] * rx + R[1] * ry + R[2] * rz;
+    x_out[3 * i + 1] = X_out[3 * b + 1] + R[3] * rx + R[4] * ry + R[5] * rz;
+    x_out[3 * i + 2] = X_out[3 * b + 2] + R[6] * rx + R[7] * ry + R[8] * rz;
+}
+
+}  // namespace
+
+void bodies_upload(ibpme_ctx* c, int n, const ibpme_bodies* b, const double* xw) {
+    BodyData& bd = c->bodies;
+    cudaStream_t s = c->stream;
+    const int nb = b->n_bodies;
+    std::vector<int> off(nb + 1);
+    IBP_CUDA(cudaMemcpyAsync(off.data(), b->body_offsets, sizeof(int) * (nb + 1), cudaMemcpyDeviceToHost, s));
+    IBP_CUDA(cudaStreamSynchronize(s));
+    if (off[0] != 0 || off[nb] != n) fail(IBPME_ERR_ARG, "body_offsets must start at 0 and end at n = %d", n);
+    for (int i = 0; i < nb; ++i)
+        if (off[i + 1] <= off[i]) fail(IBPME_ERR_ARG, "body %d is empty or offsets decrease", i);
+    // unchanged body structure (e.g. along a trajectory): keep the unknown lists
+    const bool same = bd.host_n == n && bd.host_off.size() == off.size() && bd.nb == nb &&
+                      std::memcmp(bd.host_off.data(), off.data(), sizeof(int) * off.size()) == 0;
+    if (!same) {
+        std::vector<int> free_idx, free_off{0}, mb_body, mb_of_free, free_pos(n, -1);
+        for (int i = 0; i < nb; ++i) {
+            if (off[i + 1] - off[i] < 2) continue;
+            for (int j = off[i]; j < off[i + 1]; ++j) {
+                free_pos[j] = (int)free_idx.size();
+                free_idx.push_back(j);
+                mb_of_free.push_back((int)mb_body.size());
+            }
+            mb_body.push_back(i);
+            free_off.push_back((int)free_idx.size());
+        }
+        bd.nb = nb;
+        bd.nmb = (int)mb_body.size();
+        bd.nfree = (int)free_idx.size();
+        auto up = [&](DevBuf& dst, const std::vector<int>& v) {
+            dst.ensure(sizeof(int) * (v.size() + 1));
+            if (!v.empty())
+                IBP_CUDA(cudaMemcpyAsync(dst.p, v.data(), sizeof(int) * v.size(), cudaMemcpyHostToDevice, s));
+        };
+        up(bd.free_idx, free_idx);
+        up(bd.free_off, free_off);
+        up(bd.mb_body, mb_body);
+        up(bd.mb_of_free, mb_of_free);
+        up(bd.free_pos, free_pos);
+        up(bd.off, off);
+        bd.bead_body.ensure(sizeof(int) * (n + 1));
+        bead_body_kernel<<<div_up((long long)nb * 32, 128), 128, 0, s>>>(nb, bd.off.as<int>(), bd.bead_body.as<int>());
+        IBP_CHECK_LAUNCH();
+        IBP_CUDA(cudaStreamSynchronize(s));   // host vectors go out of scope
+        bd.host_off = off;
+        bd.host_n = n;
+    }
+    bd.X.ensure(sizeof(double) * 3 * nb);
+    bd.Q.ensure(sizeof(double) * nb);
+    IBP_CUDA(cudaMemcpyAsync(bd.X.p, b->X, sizeof(double) * 3 * nb, cudaMemcpyDeviceToDevice, s));
+    IBP_CUDA(cudaMemcpyAsync(bd.Q.p, b->Q, sizeof(double) * nb, cudaMemcpyDeviceToDevice, s));
+    bd.rel.ensure(sizeof(double) * 3 * n);
+    rel_kernel<<<div_up(n, 256), 256, 0, s>>>(n, xw, bd.bead_body.as<int>(), bd.X.as<double>(), c->p.box[0],
+                                              c->p.box[1], c->p.box[2], bd.rel.as<double>());
+    IBP_CHECK_LAUNCH();
+}
+
+void body_dipoles(ibpme_ctx* c, int n, const double* q, int nrhs, double* S) {
+    ProfScope ps(ST_BODIES, c->stream);
+    BodyData& bd = c->bodies;
+    dipole_kernel<<<div_up((long long)bd.nb * 32, 128), 128, 0, c->stream>>>(bd.nb, n, nrhs, bd.off.as<int>(),
+                                                                              bd.rel.as<double>(), q, S);
+    IBP_CHECK_LAUNCH();
+}
+
+void bead_forces(ibpme_ctx* c, int n, const double* q, const double* E0, const double* E, double* f) {
+    ProfScope ps(ST_BODIES, c->stream);
+    force_kernel<<<div_up(3LL * n, 256), 256, 0, c->stream>>>(n, q, E0, E, f);
+    IBP_CHECK_LAUNCH();
+}
+
+void body_reduce_force_torque(ibpme_ctx* c, int n, const double* f, double* F, double* L) {
+    ProfScope ps(ST_BODIES, c->stream);
+    (void)n;
+    BodyData& bd = c->bodies;
+    force_torque_kernel<<<div_up((long long)bd.nb * 32, 128), 128, 0, c->stream>>>(bd.nb, bd.off.as<int>(),
+                                                                                    bd.rel.as<double>(), f, F, L);
+    IBP_CHECK_LAUNCH();
+}
+
+void body_energy(ibpme_ctx* c, int n, const double* q, const double* psi, const double* E0, double* U) {
+    ProfScope ps(ST_BODIES, c->stream);
+    (void)n;
+    BodyData& bd = c->bodies;
+    double* contrib = static_cast<double*>(bd.scratch.ensure(sizeof(double) * (bd.nb + 1)));
+    energy_body_kernel<<<div_up((long long)bd.nb * 32, 128), 128, 0, c->stream>>>(
+        bd.nb, bd.off.as<int>(), bd.rel.as<double>(), q, psi, E0, bd.X.as<double>(), bd.Q.as<double>(), contrib);
+    IBP_CHECK_LAUNCH();
+    half_sum_kernel<<<1, 1024, 0, c->stream>>>(bd.nb, contrib, U);
+    IBP_CHECK_LAUNCH();
+}
+
+void bd_step(ibpme_ctx* c, int n, const double* xw, const double* f, const ibpme_bd_params* p, double* x_out,
+             double* X_out) {
+    BodyData& bd = c->bodies;
+    NearList& nl = c->near;
+    cudaStream_t s = c->stream;
+    ProfScope ps(ST_BODIES, s);
+    double* ftot = static_cast<double*>(bd.scratch.ensure(sizeof(double) * (3 * (size_t)n + 9 * (size_t)bd.nb)));
+    double* Rm = ftot + 3 * (size_t)n;
+    hard_sphere_kernel<<<div_up((long long)n * 32, 128), 128, 0, s>>>(
+        n, xw, c->p.box[0], c->p.box[1], c->p.box[2], nl.rowptr.as<long long>(), nl.col.as<int>(),
+        bd.bead_body.as<int>(), c->a, p->gamma / (2.0 * p->dt), f, ftot);
+    IBP_CHECK_LAUNCH();
+    BdConst bc{p->dt, p->gamma, p->kT, p->seed, (unsigned)(p->step & 0xffffffffLL)};
+    bd_body_kernel<<<div_up((long long)bd.nb * 32, 128), 128, 0, s>>>(bd.nb, bd.off.as<int>(), bd.rel.as<double>(),
+                                                                       ftot, bd.X.as<double>(), bc, X_out, Rm);
+    IBP_CHECK_LAUNCH();
+    bd_bead_kernel<<<div_up(n, 256), 256, 0, s>>>(n, bd.bead_body.as<int>(), bd.rel.as<double>(), X_out, Rm, x_out);
+    IBP_CHECK_LAUNCH();
+}
+
+}  // namespace ibp

@@ -1,0 +1,281 @@
+// common.cuh -- internal declarations shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cufft.h>
+
+#include <cstddef>
+#include <cstdint>
+#include <exception>
+#include <string>
+#include <vector>
+
+#include "../../include/ibpme.h"
+
+#define IBP_API extern "C" __attribute__((visibility("default")))
+
+namespace ibp {
+
+// ---------------------------------------------------------------------------
+// Errors: internal code throws ibp::Error; the C ABI converts it to a status.
+// ---------------------------------------------------------------------------
+struct Error : std::exception {
+    ibpme_status status;
+    explicit Error(ibpme_status s) : status(s) {}
+};
+
+void set_error(const char* fmt, ...);
+[[noreturn]] void fail(ibpme_status s, const char* fmt, ...);
+
+#define IBP_CUDA(call)                                                                      \
+    do {                                                                                    \
+        cudaError_t e_ = (call);                                                            \
+        if (e_ != cudaSuccess)                                                              \
+            ::ibp::fail(e_ == cudaErrorMemoryAllocation ? IBPME_ERR_OOM : IBPME_ERR_CUDA,  \
+                        "%s:%d %s: %s", __FILE__, __LINE__, #call, cudaGetErrorString(e_)); \
+    } while (0)
+
+#define IBP_CUFFT(call)                                                                           \
+    do {                                                                                          \
+        cufftResult r_ = (call);                                                                  \
+        if (r_ != CUFFT_SUCCESS)                                                                  \
+            ::ibp::fail(IBPME_ERR_CUFFT, "%s:%d %s: cufft error %d", __FILE__, __LINE__, #call, \
+                        (int)r_);                                                                 \
+    } while (0)
+
+// Every kernel launch of the library is followed by IBP_CHECK_LAUNCH(), which
+// also counts it (cuFFT's own launches are not counted).
+void count_launch();
+#define IBP_CHECK_LAUNCH()                 \
+    do {                                   \
+        ::ibp::count_launch();             \
+        IBP_CUDA(cudaGetLastError());      \
+    } while (0)
+
+// ---------------------------------------------------------------------------
+// Device buffer that only grows.
+// ---------------------------------------------------------------------------
+struct DevBuf {
+    void* p = nullptr;
+    size_t bytes = 0;
+    DevBuf() = default;
+    DevBuf(const DevBuf&) = delete;
+    DevBuf& operator=(const DevBuf&) = delete;
+    ~DevBuf() { release(); }
+    void release() {
+        if (p) cudaFree(p);
+        p = nullptr;
+        bytes = 0;
+    }
+    void* ensure(size_t b) {
+        if (b > bytes) {
+            release();
+            size_t want = b < 256 ? 256 : b;
+            IBP_CUDA(cudaMalloc(&p, want));
+            bytes = want;
+        }
+        return p;
+    }
+    template <typename T>
+    T* as() const { return static_cast<T*>(p); }
+};
+
+// ---------------------------------------------------------------------------
+// Geometry of the spectral-Ewald mesh (Sec. III.D.2), passed to kernels by value.
+// ---------------------------------------------------------------------------
+struct MeshGeom {
+    double L[3];       // box
+    double h[3];       // L_d / N_d
+    double inv_h[3];
+    double kappa[3];   // 2 xi^2 h_d^2 / eta: Gaussian exponent in grid units
+    double c;          // (2 xi^2 / (pi eta))^{3/2}: spreading normalisation
+    double gather;     // c * h_x h_y h_z / eps_f: trapezoid weight of the gather
+    double grad;       // gather * 4 xi^2 / eta: prefactor of the gradient gather
+    int N[3];
+    int P;
+    long long G;       // N_x N_y N_z real grid points
+    long long Gc;      // N_z N_y (N_x/2+1) complex points of the half spectrum
+};
+
+template <typename T> struct Cplx;
+template <> struct Cplx<float> { using type = cufftComplex; };
+template <> struct Cplx<double> { using type = cufftDoubleComplex; };
+
+constexpr int kMaxRhs = 8;
+constexpr int kMaxP = 32;
+
+// Spectral-Ewald mesh engine in one precision: grids, spectrum, Green's table, plans.
+template <typename T>
+struct Mesh {
+    MeshGeom g{};
+    int rcap = 0;
+    DevBuf grid;    // [rcap][G] real
+    DevBuf spec;    // [rcap][Gc] complex
+    DevBuf green;   // [Gc] real: G(k) / (N_x N_y N_z), 0 at k = 0
+    DevBuf work;    // cuFFT work area shared by the plans
+    cufftHandle r2c[kMaxRhs + 1] = {};
+    cufftHandle c2r[kMaxRhs + 1] = {};
+    bool have[kMaxRhs + 1] = {};
+    void init(const MeshGeom& geom, int max_rhs, double xi, double eta, double a, cudaStream_t s);
+    void destroy();
+    void plans(int nrhs, cudaStream_t s);
+    // psi_k[r][alpha] (= overwrite) and optionally E_k[r][alpha][3] for the given charges
+    void spread(int n, const double* xw, const double* q, int nrhs, cudaStream_t s);
+    void transform(int nrhs, cudaStream_t s);   // R2C, scale, C2R
+    void gather(int n, const double* xw, int nrhs, double* psi, double* E, cudaStream_t s);
+};
+
+// Cell list and real-space pair table (Sec. III.D.1, Sec. III.D.3 step 1).
+struct NearList {
+    int n = 0;
+    long long npairs = 0;
+    int nc[3] = {1, 1, 1};
+    double L[3] = {0, 0, 0};
+    double rc = 0;
+    bool have_grad = false;
+    DevBuf cell_of, cell_count, cell_start64, cell_start, cell_beads, cursor;
+    DevBuf row_count, rowptr;
+    DevBuf col, val, gfac;
+    DevBuf scan_tmp, flag;
+    DevBuf table;                  // tabulated pair kernel (phi, phi', phi'') on [2a, r_c]
+    DevBuf fp_dev;                 // fingerprint of the positions + non-finite flag
+    unsigned long long fp = 0;     // fingerprint of the positions the table was built for
+    bool fp_valid = false;
+};
+
+// Body bookkeeping on the device for solves, forces and BD steps.
+struct BodyData {
+    int nb = 0;         // bodies
+    int nmb = 0;        // multi-bead bodies
+    int nfree = 0;      // beads of multi-bead bodies (the unknown charges)
+    DevBuf off;         // [nb+1] int offsets
+    DevBuf bead_body;   // [n] int body id
+    DevBuf X, Q;        // [nb][3], [nb]
+    DevBuf free_idx;    // [nfree] bead index of each unknown charge
+    DevBuf free_off;    // [nmb+1] offsets of the multi-bead bodies in the unknown list
+    DevBuf mb_body;     // [nmb] body id of each multi-bead body
+    DevBuf mb_of_free;  // [nfree] multi-bead body index of each unknown charge
+    DevBuf free_pos;    // [n] position of each bead in the unknown list, -1 for ions
+    DevBuf rel;         // [n][3] r_ij = minimum image of x_ij - X_i
+    DevBuf scratch;     // reductions and BD temporaries
+    std::vector<int> host_off;   // offsets of the last upload (to skip rebuilding the lists)
+    int host_n = -1;
+};
+
+struct Krylov;   // krylov.cu
+
+// Optional per-stage timing with CUDA events on the launching stream.
+enum Stage {
+    ST_NEAR_BUILD = 0,   // cell list + pair table
+    ST_NEAR_APPLY,       // real-space SpMV / field
+    ST_SPREAD,           // FP32 mesh: spread (grid clear + atomics)
+    ST_FFT_FWD,          //            cuFFT R2C
+    ST_SCALE,            //            Green's-function scaling
+    ST_FFT_INV,          //            cuFFT C2R
+    ST_GATHER,           //            gather
+    ST_KRYLOV,           // Arnoldi / Givens / update kernels of one iteration
+    ST_BODIES,           // body reductions and the BD step
+    ST_SPREAD64,         // FP64 mesh: the same five stages
+    ST_FFT_FWD64,
+    ST_SCALE64,
+    ST_FFT_INV64,
+    ST_GATHER64,
+    ST_COUNT
+};
+// stage of a mesh step for the mesh precision T
+template <typename T>
+constexpr int mesh_stage(int st32) { return sizeof(T) == 8 ? st32 - ST_SPREAD + ST_SPREAD64 : st32; }
+struct ProfScope {
+    int stage;
+    cudaStream_t s;
+    bool on;
+    ProfScope(int stage, cudaStream_t s);
+    ~ProfScope();
+};
+
+}  // namespace ibp
+
+// The context (opaque in the C ABI).
+struct ibpme_ctx {
+    ibpme_params p{};              // resolved parameters
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    double xi = 0, eta = 0, rc = 0, a = 0, eps = 1;
+    int P = 0;
+    ibp::MeshGeom geom{};
+    ibp::Mesh<double> mesh64;
+    ibp::Mesh<float> mesh32;
+    bool have32 = false;
+    ibp::NearList near;
+    ibp::BodyData bodies;
+    ibp::Krylov* kry = nullptr;
+    // working vectors
+    ibp::DevBuf xw;          // [n][3] wrapped positions
+    ibp::DevBuf psi_r, psi_k, E_r, E_k;   // [R][n], [R][n][3]
+    ibp::DevBuf qfull;       // [R][n]
+    // staging of host arrays
+    ibp::DevBuf st_x, st_q, st_out1, st_out2, st_out3, st_out4, st_E0, st_off, st_X, st_Q, st_f;
+    ibp::DevBuf scalars;     // small device scratch
+    void* pinned = nullptr;  // small pinned host scratch
+    size_t pinned_bytes = 0;
+};
+
+namespace ibp {
+
+// ---- near.cu ----
+void near_setup(ibpme_ctx* c);   // tabulates the pair kernel (once per context)
+void near_build(ibpme_ctx* c, int n, const double* xw, bool need_grad);
+void near_apply(ibpme_ctx* c, int n, const double* q, int nrhs, double* psi_r);    // overwrite
+void near_field(ibpme_ctx* c, int n, const double* xw, const double* q, int nrhs, double* E_r);  // overwrite
+double self_term(const ibpme_ctx* c);   // phi_self (without 1/eps)
+
+// ---- api.cu helpers ----
+void wrap_positions(ibpme_ctx* c, int n, const double* x, double* xw);
+// psi = M q (real + self + wave) in the given precision; E optional
+void pme_apply(ibpme_ctx* c, int n, const double* xw, const double* q, int nrhs, int prec,
+               double* psi, double* E, bool near_ready);
+void* pinned_host(ibpme_ctx* c, size_t bytes);
+
+// ---- bodies.cu ----
+void bodies_upload(ibpme_ctx* c, int n, const ibpme_bodies* b, const double* xw);
+void body_dipoles(ibpme_ctx* c, int n, const double* q, int nrhs, double* S);
+void bead_forces(ibpme_ctx* c, int n, const double* q, const double* E0, const double* E, double* f);
+void body_reduce_force_torque(ibpme_ctx* c, int n, const double* f, double* F, double* L);
+void body_energy(ibpme_ctx* c, int n, const double* q, const double* psi, const double* E0, double* U);
+void bd_step(ibpme_ctx* c, int n, const double* x, const double* f, const ibpme_bd_params* bd,
+             double* x_out, double* X_out);
+
+// ---- krylov.cu ----
+struct SolveArgs {
+    int n, nrhs, prec;
+    const double* xw;
+    const double* E0;   // device [nrhs][3]
+    double* q;          // device [nrhs][n] (guess in, solution out)
+    double* psi;        // device [nrhs][nb] or nullptr
+    bool user_guess;
+    double rtol;
+    int restart, max_iter;
+};
+void solve(ibpme_ctx* c, const SolveArgs& a, ibpme_solve_stats* st);
+void krylov_destroy(ibpme_ctx* c);
+
+// small device helpers
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+__host__ __device__ __forceinline__ double wrap_coord(double x, double L) {
+    double w = x - L * floor(x / L);
+    return (w >= L) ? w - L : w;   // guard x/L rounding to exactly 1
+}
+
+__host__ __device__ __forceinline__ double min_image(double d, double L) {
+    return d - L * floor(d / L + 0.5);
+}
+
+inline int div_up(long long a, long long b) { return (int)((a + b - 1) / b); }
+
+}  // namespace ibp

@@ -1,0 +1,295 @@
+// mesh.cu -- wave-space half of the spectral Ewald sum (Sec. III.D.2 and
+// steps 2-6 of Sec. III.D.3): Gaussian spreading onto the grid, forward FFT,
+// Green's-function scaling, inverse FFT and trapezoid-rule gather (with the
+// gradient for the field).
+//
+// Spreading and gathering use one warp per bead.  The Gaussian window is
+// separable, exp(-2 xi^2 |x_g - x|^2 / eta) = w_x(i) w_y(j) w_z(k), so a warp
+// evaluates 3P exponentials and then streams the P^3 products; lane
+// (i, row) owns one x offset i of the stencil and walks the (j, k) rows, so
+// the addresses of neighbouring lanes are contiguous along x.
+#include "common.cuh"
+
+#include <cmath>
+
+namespace ibp {
+
+namespace {
+
+constexpr int kWarpsPerBlock = 4;
+
+template <typename T> __device__ __forceinline__ T dexp(T v);
+template <> __device__ __forceinline__ float dexp<float>(float v) { return expf(v); }
+template <> __device__ __forceinline__ double dexp<double>(double v) { return exp(v); }
+
+// Per-warp stencil set-up: for axis d, node indices (periodic) and window
+// weights of the P closest nodes, first node floor(u - P/2) + 1, u = x / h.
+template <typename T, bool DIST>
+__device__ __forceinline__ void stencil_setup(const MeshGeom& g, const double* __restrict__ xw, int bead, int lane,
+                                              T (*sw)[kMaxP], int (*sidx)[kMaxP], T (*sdist)[kMaxP]) {
+    const int P = g.P;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        const double u = xw[3 * bead + d] * g.inv_h[d];
+        const double sf = floor(u - 0.5 * P) + 1.0;
+        if (lane < P) {
+            const T f = (T)(sf - u) + (T)lane;          // (node - x) / h, exact to rounding of T
+            sw[d][lane] = dexp<T>(-(T)g.kappa[d] * f * f);
+            if (DIST) sdist[d][lane] = f * (T)g.h[d];
+            int idx = ((int)sf + lane) % g.N[d];
+            if (idx < 0) idx += g.N[d];
+            sidx[d][lane] = idx;
+        }
+    }
+    __syncwarp();
+}
+
+template <typename T>
+__global__ void __launch_bounds__(32 * kWarpsPerBlock)
+spread_kernel(int n, const double* __restrict__ xw, const double* __restrict__ q, int nrhs, MeshGeom g,
+              T* __restrict__ grid) {
+    __shared__ T s_w[kWarpsPerBlock][3][kMaxP];
+    __shared__ int s_idx[kWarpsPerBlock][3][kMaxP];
+    const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int bead = blockIdx.x * kWarpsPerBlock + wib;
+    if (bead >= n) return;
+    stencil_setup<T, false>(g, xw, bead, lane, s_w[wib], s_idx[wib], nullptr);
+    const int P = g.P;
+    const int rows_per = 32 / P;
+    const int i = lane % P, rsub = lane / P;
+    if (rsub >= rows_per) return;
+    const T wx = s_w[wib][0][i];
+    const int ix = s_idx[wib][0][i];
+    T qc[kMaxRhs];
+#pragma unroll
+    for (int r = 0; r < kMaxRhs; ++r)
+        qc[r] = (r < nrhs) ? (T)(g.c * q[(size_t)r * n + bead]) * wx : (T)0;
+    const int P2 = P * P;
+    for (int row = rsub; row < P2; row += rows_per) {
+        const int k = row / P, j = row - k * P;
+        const T wyz = s_w[wib][1][j] * s_w[wib][2][k];
+        const long long off = ((long long)s_idx[wib][2][k] * g.N[1] + s_idx[wib][1][j]) * g.N[0] + ix;
+#pragma unroll
+        for (int r = 0; r < kMaxRhs; ++r)
+            if (r < nrhs) atomicAdd(grid + (size_t)r * g.G + off, qc[r] * wyz);
+    }
+}
+
+template <typename T, bool GRAD>
+__global__ void __launch_bounds__(32 * kWarpsPerBlock)
+gather_kernel(int n, const double* __restrict__ xw, int nrhs, MeshGeom g, const T* __restrict__ grid,
+              double* __restrict__ psi, double* __restrict__ E) {
+    __shared__ T s_w[kWarpsPerBlock][3][kMaxP];
+    __shared__ T s_d[kWarpsPerBlock][3][kMaxP];
+    __shared__ int s_idx[kWarpsPerBlock][3][kMaxP];
+    const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int bead = blockIdx.x * kWarpsPerBlock + wib;
+    if (bead >= n) return;
+    stencil_setup<T, GRAD>(g, xw, bead, lane, s_w[wib], s_idx[wib], s_d[wib]);
+    const int P = g.P;
+    const int rows_per = 32 / P;
+    const int i = lane % P, rsub = lane / P;
+    const bool active = rsub < rows_per;
+    T acc[kMaxRhs], accy[kMaxRhs], accz[kMaxRhs];
+#pragma unroll
+    for (int r = 0; r < kMaxRhs; ++r) acc[r] = accy[r] = accz[r] = (T)0;
+    T wx = 0, dx = 0;
+    if (active) {
+        wx = s_w[wib][0][i];
+        if (GRAD) dx = s_d[wib][0][i];
+        const int ix = s_idx[wib][0][i];
+        const int P2 = P * P;
+        for (int row = rsub; row < P2; row += rows_per) {
+            const int k = row / P, j = row - k * P;
+            const T wyz = s_w[wib][1][j] * s_w[wib][2][k];
+            const long long off = ((long long)s_idx[wib][2][k] * g.N[1] + s_idx[wib][1][j]) * g.N[0] + ix;
+#pragma unroll
+            for (int r = 0; r < kMaxRhs; ++r) {
+                if (r < nrhs) {
+                    const T v = __ldg(grid + (size_t)r * g.G + off) * wyz;
+                    acc[r] += v;
+                    if (GRAD) {
+                        accy[r] += v * s_d[wib][1][j];
+                        accz[r] += v * s_d[wib][2][k];
+                    }
+                }
+            }
+        }
+    }
+#pragma unroll
+    for (int r = 0; r < kMaxRhs; ++r) {
+        if (r >= nrhs) break;
+        const double p = warp_sum((double)(wx * acc[r]));
+        if (lane == 0) psi[(size_t)r * n + bead] = g.gather * p;
+        if (GRAD) {
+            const double ex = warp_sum((double)(wx * dx * acc[r]));
+            const double ey = warp_sum((double)(wx * accy[r]));
+            const double ez = warp_sum((double)(wx * accz[r]));
+            if (lane == 0) {
+                double* e = E + ((size_t)r * n + bead) * 3;
+                // E = -grad psi; d/dx_alpha of the window gives (4 xi^2/eta)(x_g - x_alpha)
+                e[0] = -g.grad * ex;
+                e[1] = -g.grad * ey;
+                e[2] = -g.grad * ez;
+            }
+        }
+    }
+}
+
+// G(k)/(N_x N_y N_z) on the half spectrum, Eq. after H_hat:
+// j0^2(k a) e^{-(1 - eta) k^2 / (4 xi^2)} / k^2, zero at k = 0 (Sec. II, k = 0 removed).
+template <typename T>
+__global__ void green_kernel(MeshGeom g, double xi, double eta, double a, T* __restrict__ green) {
+    const int nxh = g.N[0] / 2 + 1;
+    const double two_pi = 6.283185307179586476925286766559;
+    const double norm = 1.0 / ((double)g.N[0] * g.N[1] * g.N[2]);
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < g.Gc;
+         t += (long long)gridDim.x * blockDim.x) {
+        const int kx_i = (int)(t % nxh);
+        const long long rest = t / nxh;
+        const int ky_i = (int)(rest % g.N[1]);
+        const int kz_i = (int)(rest / g.N[1]);
+        const int my = ky_i <= g.N[1] / 2 ? ky_i : ky_i - g.N[1];
+        const int mz = kz_i <= g.N[2] / 2 ? kz_i : kz_i - g.N[2];
+        const double kx = two_pi * kx_i / g.L[0], ky = two_pi * my / g.L[1], kz = two_pi * mz / g.L[2];
+        const double k2 = kx * kx + ky * ky + kz * kz;
+        double v = 0.0;
+        if (k2 > 0.0) {
+            const double k = sqrt(k2);
+            const double j0 = sin(k * a) / (k * a);
+            v = j0 * j0 * exp(-(1.0 - eta) * k2 / (4.0 * xi * xi)) / k2 * norm;
+        }
+        green[t] = (T)v;
+    }
+}
+
+template <typename T>
+__global__ void scale_kernel(long long Gc, int nrhs, const T* __restrict__ green,
+                             typename Cplx<T>::type* __restrict__ spec) {
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < Gc * nrhs;
+         t += (long long)gridDim.x * blockDim.x) {
+        const T gk = green[t % Gc];
+        typename Cplx<T>::type v = spec[t];
+        v.x *= gk;
+        v.y *= gk;
+        spec[t] = v;
+    }
+}
+
+int grid_blocks(long long work, int threads) {
+    long long b = (work + threads - 1) / threads;
+    const long long cap = 152LL * 16;
+    return (int)(b < 1 ? 1 : (b > cap ? cap : b));
+}
+
+}  // namespace
+
+template <typename T>
+void Mesh<T>::init(const MeshGeom& geom, int max_rhs, double xi, double eta, double a, cudaStream_t s) {
+    g = geom;
+    rcap = max_rhs;
+    grid.ensure(sizeof(T) * (size_t)g.G * rcap);
+    spec.ensure(sizeof(typename Cplx<T>::type) * (size_t)g.Gc * rcap);
+    green.ensure(sizeof(T) * (size_t)g.Gc);
+    green_kernel<T><<<grid_blocks(g.Gc, 256), 256, 0, s>>>(g, xi, eta, a, green.as<T>());
+    IBP_CHECK_LAUNCH();
+}
+
+template <typename T>
+void Mesh<T>::plans(int nrhs, cudaStream_t s) {
+    if (nrhs < 1 || nrhs > rcap) fail(IBPME_ERR_ARG, "nrhs %d outside 1..%d", nrhs, rcap);
+    if (!have[nrhs]) {
+        int dims[3] = {g.N[2], g.N[1], g.N[0]};   // slowest to fastest: z, y, x
+        const cufftType tf = sizeof(T) == 8 ? CUFFT_D2Z : CUFFT_R2C;
+        const cufftType tb = sizeof(T) == 8 ? CUFFT_Z2D : CUFFT_C2R;
+        size_t ws1 = 0, ws2 = 0;
+        IBP_CUFFT(cufftCreate(&r2c[nrhs]));
+        IBP_CUFFT(cufftCreate(&c2r[nrhs]));
+        IBP_CUFFT(cufftSetAutoAllocation(r2c[nrhs], 0));
+        IBP_CUFFT(cufftSetAutoAllocation(c2r[nrhs], 0));
+        IBP_CUFFT(cufftMakePlanMany(r2c[nrhs], 3, dims, nullptr, 1, (int)g.G, nullptr, 1, (int)g.Gc, tf,
+                                    nrhs, &ws1));
+        IBP_CUFFT(cufftMakePlanMany(c2r[nrhs], 3, dims, nullptr, 1, (int)g.Gc, nullptr, 1, (int)g.G, tb,
+                                    nrhs, &ws2));
+        have[nrhs] = true;
+        const size_t need = ws1 > ws2 ? ws1 : ws2;
+        if (need > work.bytes) {
+            work.ensure(need);
+            for (int r = 1; r <= kMaxRhs; ++r)
+                if (have[r]) {
+                    IBP_CUFFT(cufftSetWorkArea(r2c[r], work.p));
+                    IBP_CUFFT(cufftSetWorkArea(c2r[r], work.p));
+                }
+        } else {
+            IBP_CUFFT(cufftSetWorkArea(r2c[nrhs], work.p));
+            IBP_CUFFT(cufftSetWorkArea(c2r[nrhs], work.p));
+        }
+    }
+    IBP_CUFFT(cufftSetStream(r2c[nrhs], s));
+    IBP_CUFFT(cufftSetStream(c2r[nrhs], s));
+}
+
+template <typename T>
+void Mesh<T>::destroy() {
+    for (int r = 0; r <= kMaxRhs; ++r)
+        if (have[r]) {
+            cufftDestroy(r2c[r]);
+            cufftDestroy(c2r[r]);
+            have[r] = false;
+        }
+    grid.release();
+    spec.release();
+    green.release();
+    work.release();
+}
+
+template <typename T>
+void Mesh<T>::spread(int n, const double* xw, const double* q, int nrhs, cudaStream_t s) {
+    ProfScope ps(mesh_stage<T>(ST_SPREAD), s);
+    IBP_CUDA(cudaMemsetAsync(grid.p, 0, sizeof(T) * (size_t)g.G * nrhs, s));
+    if (n == 0) return;
+    spread_kernel<T><<<div_up(n, kWarpsPerBlock), 32 * kWarpsPerBlock, 0, s>>>(n, xw, q, nrhs, g, grid.as<T>());
+    IBP_CHECK_LAUNCH();
+}
+
+template <typename T>
+void Mesh<T>::transform(int nrhs, cudaStream_t s) {
+    plans(nrhs, s);
+    using C = typename Cplx<T>::type;
+    {
+        ProfScope ps(mesh_stage<T>(ST_FFT_FWD), s);
+        if constexpr (sizeof(T) == 8) {
+            IBP_CUFFT(cufftExecD2Z(r2c[nrhs], grid.as<double>(), spec.as<C>()));
+        } else {
+            IBP_CUFFT(cufftExecR2C(r2c[nrhs], grid.as<float>(), spec.as<C>()));
+        }
+    }
+    {
+        ProfScope ps(mesh_stage<T>(ST_SCALE), s);
+        scale_kernel<T><<<grid_blocks(g.Gc * nrhs, 256), 256, 0, s>>>(g.Gc, nrhs, green.as<T>(), spec.as<C>());
+        IBP_CHECK_LAUNCH();
+    }
+    ProfScope ps(mesh_stage<T>(ST_FFT_INV), s);
+    if constexpr (sizeof(T) == 8) {
+        IBP_CUFFT(cufftExecZ2D(c2r[nrhs], spec.as<C>(), grid.as<double>()));
+    } else {
+        IBP_CUFFT(cufftExecC2R(c2r[nrhs], spec.as<C>(), grid.as<float>()));
+    }
+}
+
+template <typename T>
+void Mesh<T>::gather(int n, const double* xw, int nrhs, double* psi, double* E, cudaStream_t s) {
+    if (n == 0) return;
+    ProfScope ps(mesh_stage<T>(ST_GATHER), s);
+    const int blocks = div_up(n, kWarpsPerBlock);
+    if (E)
+        gather_kernel<T, true><<<blocks, 32 * kWarpsPerBlock, 0, s>>>(n, xw, nrhs, g, grid.as<T>(), psi, E);
+    else
+        gather_kernel<T, false><<<blocks, 32 * kWarpsPerBlock, 0, s>>>(n, xw, nrhs, g, grid.as<T>(), psi, nullptr);
+    IBP_CHECK_LAUNCH();
+}
+
+template struct Mesh<float>;
+template struct Mesh<double>;
+
+}  // namespace ibp

@@ -1,0 +1,279 @@
+"""GPU parity: the CUDA library through its C ABI against the FP64 oracle.
+
+Bars: 1e-5 (FP64 path) and 1e-3 (mixed precision) relative to each result's
+largest magnitude, element by element (helpers.rel_err).  Sizes span several
+tiles with ragged tails; the full-size cases compare sampled outputs.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as o
+from workloads import configs as C
+
+from helpers import FP64_RTOL, MIXED_RTOL, context, cuda, random_neutral_charges, rel_err
+
+pytestmark = pytest.mark.gpu
+
+
+def _field(ib, ctx, x, q, nrhs=1, with_E=True):
+    import torch
+    n = x.shape[0]
+    xd = cuda(x)
+    qd = cuda(np.asarray(q).reshape(nrhs, n))
+    psi = torch.zeros((nrhs, n), dtype=torch.float64, device="cuda")
+    E = torch.zeros((nrhs, n, 3), dtype=torch.float64, device="cuda") if with_E else None
+    ib.pme_field(ctx, n, xd, qd, nrhs, psi, E)
+    torch.cuda.synchronize()
+    return psi.cpu().numpy(), (E.cpu().numpy() if with_E else None)
+
+
+def test_setup_applies_the_paper_parameter_rules(cuda_lib):
+    ib = cuda_lib
+    for L, mesh, tol, a in [(20.0, 64, 1e-8, 0.1), (30.0, 128, 1e-6, 0.05), (13.89, 256, 1e-6, 0.05)]:
+        ctx = ib.pme_setup(ib.make_params(box=[L] * 3, mesh=[mesh] * 3, tol=tol, bead_radius=a))
+        p = ib.ibpme_get_params(ctx)
+        ref = o.auto_params([L] * 3, [mesh] * 3, tol, a)
+        assert p.P == ref["P"]
+        for k in ("xi", "eta", "r_cut"):
+            assert abs(getattr(p, k) - ref[k]) <= 1e-12 * ref[k]
+        ib.pme_destroy(ctx)
+    # invalid arguments are rejected with IBPME_ERR_ARG, not a fault
+    bad = [dict(box=[10.0] * 3, mesh=[8] * 3, tol=1e-8),                 # mesh < P
+           dict(box=[3.0] * 3, mesh=[16] * 3, tol=1e-10, bead_radius=0.4),  # r_cut >= L/2
+           dict(box=[10.0] * 3, mesh=[32] * 3, bead_radius=0.0)]
+    for kw in bad:
+        kw.setdefault("bead_radius", 0.1)
+        with pytest.raises(ib.IbpmeError) as e:
+            ib.pme_setup(ib.make_params(**kw))
+        assert e.value.status == ib.IBPME_ERR_ARG
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_spread_matches_its_definition(cuda_lib, prec):
+    import torch
+    ib = cuda_lib
+    rng = np.random.default_rng(3)
+    n, nrhs = 37, 2
+    box = np.array([5.0, 6.0, 5.5])
+    mesh = (40, 48, 45)
+    x = rng.uniform(-3, 9, size=(n, 3))          # outside the box too: wrapped internally
+    q = rng.normal(size=(nrhs, n))
+    ctx = ib.pme_setup(ib.make_params(box=box, mesh=mesh, tol=1e-6, bead_radius=0.1,
+                                      precision=ib.IBPME_FP64 if prec == "fp64" else ib.IBPME_MIXED))
+    p = ib.ibpme_get_params(ctx)
+    dt = torch.float64 if prec == "fp64" else torch.float32
+    grid = torch.zeros((nrhs, mesh[2], mesh[1], mesh[0]), dtype=dt, device="cuda")
+    ib.pme_spread(ctx, n, cuda(x), cuda(q), nrhs, grid)
+    got = grid.cpu().double().numpy()
+    for r in range(nrhs):
+        ref = o.spread_grid(x, q[r], box, mesh, p.xi, p.eta, p.P)
+        assert rel_err(got[r], ref) < (1e-12 if prec == "fp64" else 2e-6)
+    ib.pme_destroy(ctx)
+
+
+def _field_case(name):
+    if name == "sphere162":
+        s = C.config1()
+        q = random_neutral_charges(s.n, 1)
+        return s.x, q, s.box, s.a, s.eps, s.mesh, s.tol
+    if name == "overlapping_rect":
+        rng = np.random.default_rng(5)
+        box = np.array([6.0, 7.0, 6.5])
+        x = rng.uniform(0, 1, size=(301, 3)) * box
+        x[1] = x[0] + [0.05, 0.02, 0.0]           # overlapping beads (r < 2a)
+        x[2] = x[0]                               # coincident beads
+        q = random_neutral_charges(301, 2)
+        return x, q, box, 0.2, 0.7, (40, 48, 45), 1e-8
+    raise KeyError(name)
+
+
+@pytest.mark.parametrize("case", ["sphere162", "overlapping_rect"])
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_pme_field_matches_oracle(cuda_lib, case, prec):
+    ib = cuda_lib
+    x, q, box, a, eps, mesh, tol = _field_case(case)
+    ref_psi, ref_E = o.potential(x, q, box, a, eps, field=True)
+    ctx = ib.pme_setup(ib.make_params(box=box, mesh=mesh, tol=tol, bead_radius=a, eps_f=eps,
+                                      precision=ib.IBPME_FP64 if prec == "fp64" else ib.IBPME_MIXED))
+    psi, E = _field(ib, ctx, x, q)
+    bar = FP64_RTOL if prec == "fp64" else MIXED_RTOL
+    assert rel_err(psi[0], ref_psi) < bar
+    assert rel_err(E[0], ref_E) < bar
+    ib.pme_destroy(ctx)
+
+
+def test_pme_field_multi_rhs_host_pointers_and_edge_cases(cuda_lib):
+    ib = cuda_lib
+    x, q0, box, a, eps, mesh, tol = _field_case("sphere162")
+    n = x.shape[0]
+    qs = np.stack([q0, random_neutral_charges(n, 7), random_neutral_charges(n, 8)])
+    ctx = ib.pme_setup(ib.make_params(box=box, mesh=mesh, tol=tol, bead_radius=a, eps_f=eps))
+    psi3, E3 = _field(ib, ctx, x, qs, nrhs=3)
+    for r in range(3):
+        psi1, E1 = _field(ib, ctx, x, qs[r])
+        assert rel_err(psi3[r], psi1[0]) < 1e-12 and rel_err(E3[r], E1[0]) < 1e-12
+    # host (numpy) arrays go through the library's staging
+    psi_h = np.zeros((3, n))
+    E_h = np.zeros((3, n, 3))
+    ib.pme_field(ctx, n, np.ascontiguousarray(x), np.ascontiguousarray(qs), 3, psi_h, E_h)
+    assert rel_err(psi_h, psi3) < 1e-12 and rel_err(E_h, E3) < 1e-12
+    # empty input is a no-op
+    ib.pme_field(ctx, 0, None, None, 1, None, None)
+    # a single bead: only itself and its images
+    one = np.array([[3.0, 4.0, 5.0]])
+    psi1, _ = _field(ib, ctx, one, np.array([1.5]))
+    assert rel_err(psi1[0], o.potential(one, [1.5], box, a, eps)) < FP64_RTOL
+    # non-finite positions are reported, not propagated
+    bad = x.copy()
+    bad[5, 1] = np.nan
+    with pytest.raises(ib.IbpmeError) as e:
+        _field(ib, ctx, bad, q0)
+    assert e.value.status == ib.IBPME_ERR_NONFINITE
+    # nrhs beyond the context capacity
+    with pytest.raises(ib.IbpmeError):
+        _field(ib, ctx, x, np.zeros((4, n)), nrhs=4)
+    ib.pme_destroy(ctx)
+
+
+def _solve(ib, ctx, s, prec=-1, rtol=1e-6, guess=None, restart=50):
+    import torch
+    n, nb, R = s.n, s.n_bodies, s.nrhs
+    bodies = ib.Bodies(cuda(s.body_offsets.astype(np.int32)), cuda(s.X), cuda(s.Q))
+    q = torch.zeros((R, n), dtype=torch.float64, device="cuda")
+    mode = ib.IBPME_GUESS_ZERO
+    if guess is not None:
+        q.copy_(torch.as_tensor(np.array(np.broadcast_to(guess, (R, n)))))
+        mode = ib.IBPME_GUESS_USER
+    psi = torch.zeros((R, nb), dtype=torch.float64, device="cuda")
+    S = torch.zeros((R, nb, 3), dtype=torch.float64, device="cuda")
+    status, st = ib.induced_charge_solve(ctx, n, cuda(s.x), bodies, cuda(s.E0), R,
+                                         ib.make_opts(rtol=rtol, guess=mode, precision=prec, restart=restart),
+                                         q, psi, S)
+    torch.cuda.synchronize()
+    return status, st, q.cpu().numpy(), psi.cpu().numpy(), S.cpu().numpy()
+
+
+def _check_solution(s, q, psi, S, bar, M=None):
+    qr, psr = o.solve_dense(s.x, s.body_offsets, s.X, s.Q, s.E0, s.box, s.a, s.eps, M=M)
+    Sr = np.stack([o.dipoles(s.x, s.X, s.body_offsets, qr[r], s.box) for r in range(s.nrhs)])
+    rel = o.relative_positions(s.x, s.X, s.body_offsets, s.box)
+    for r in range(s.nrhs):
+        assert rel_err(q[r], qr[r]) < bar, ("q", r, rel_err(q[r], qr[r]))
+        # Psi - Psi_0 can vanish by symmetry (a neutral sphere): measure it on the scale of
+        # the bead potentials it is balanced against, max(|Psi - Psi_0|, |r.E0|)
+        pscale = max(np.abs(psr[r]).max(), np.abs(rel @ s.E0[r]).max())
+        assert np.abs(psi[r] - psr[r]).max() < bar * pscale, ("psi", r, np.abs(psi[r] - psr[r]).max() / pscale)
+        assert rel_err(S[r], Sr[r]) < bar, ("S", r, rel_err(S[r], Sr[r]))
+    return qr, psr, Sr
+
+
+def test_solve_single_sphere_fp64(cuda_lib):
+    ib = cuda_lib
+    s = C.config1()
+    ctx = context(ib, s)
+    status, st, q, psi, S = _solve(ib, ctx, s)
+    assert status == ib.IBPME_OK and st.rel_residual <= 1e-6
+    _check_solution(s, q, psi, S, FP64_RTOL)
+    # Sec. IV.A: dipole along E0, a little above 4 pi a^3 eps E0
+    assert abs(S[0, 0, 0]) < 1e-8 * S[0, 0, 2] and abs(S[0, 0, 1]) < 1e-8 * S[0, 0, 2]
+    assert 0.0 < S[0, 0, 2] / (4 * math.pi) - 1.0 < 0.3
+    ib.pme_destroy(ctx)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_solve_bodies_ions_three_fields(cuda_lib, prec):
+    ib = cuda_lib
+    s = C.small_system(seed=11, n_bodies=3, level=2, n_ions=25, L=9.0, a=0.12, mesh=(48, 48, 48), tol=1e-7,
+                       nrhs=3)
+    ctx = context(ib, s, precision=prec)
+    status, st, q, psi, S = _solve(ib, ctx, s)
+    assert status == ib.IBPME_OK and st.rel_residual <= 1e-6
+    _check_solution(s, q, psi, S, FP64_RTOL if prec == "fp64" else MIXED_RTOL)
+    # the constraint Sigma q = Q holds for every body to the solve's residual
+    rel = o.relative_positions(s.x, s.X, s.body_offsets, s.box)
+    for r in range(3):
+        bnorm = np.sqrt(np.sum((rel @ s.E0[r]) ** 2) + np.sum(s.Q ** 2))
+        assert np.max(np.abs(np.add.reduceat(q[r], s.body_offsets[:-1]) - s.Q)) <= 1e-6 * bnorm
+    ib.pme_destroy(ctx)
+
+
+def test_solve_charged_sphere_with_ions_full_size_mixed(cuda_lib):
+    """The 642-bead sphere with 2,050 ions in L = 30 on 128^3 (mixed precision), solved
+    from the uniform initial charge, against the dense FP64 oracle solve."""
+    ib = cuda_lib
+    s = C.config2()
+    ctx = context(ib, s)
+    status, st, q, psi, S = _solve(ib, ctx, s, guess=s.q_guess)
+    assert status == ib.IBPME_OK and st.rel_residual <= 1e-6
+    _check_solution(s, q, psi, S, MIXED_RTOL)
+    ib.pme_destroy(ctx)
+
+
+def test_forces_torques_energy_fp64(cuda_lib):
+    import torch
+    ib = cuda_lib
+    s = C.small_system(seed=21, n_bodies=2, level=2, n_ions=12, L=8.0, a=0.14, mesh=(48, 48, 48), tol=1e-8)
+    M = o.M_dense(s.x, s.box, s.a, s.eps)
+    qr, psr = o.solve_dense(s.x, s.body_offsets, s.X, s.Q, s.E0[0], s.box, s.a, s.eps, M=M)
+    f_ref = o.bead_forces(s.x, qr, s.E0[0], s.box, s.a, s.eps)
+    F_ref, L_ref = o.body_force_torque(s.x, s.X, s.body_offsets, f_ref, s.box)
+    U_ref = o.energy(s.X, s.Q, psr, o.dipoles(s.x, s.X, s.body_offsets, qr, s.box), s.E0[0])
+    ctx = context(ib, s)
+    n, nb = s.n, s.n_bodies
+    bodies = ib.Bodies(cuda(s.body_offsets.astype(np.int32)), cuda(s.X), cuda(s.Q))
+    f = torch.zeros((n, 3), dtype=torch.float64, device="cuda")
+    F = torch.zeros((nb, 3), dtype=torch.float64, device="cuda")
+    L = torch.zeros((nb, 3), dtype=torch.float64, device="cuda")
+    U = torch.zeros(1, dtype=torch.float64, device="cuda")
+    ib.body_force_torque(ctx, n, cuda(s.x), cuda(qr), bodies, cuda(s.E0[0]), f, F, L, U)
+    torch.cuda.synchronize()
+    assert rel_err(f.cpu().numpy(), f_ref) < FP64_RTOL
+    assert rel_err(F.cpu().numpy(), F_ref) < FP64_RTOL
+    # a torque is a sum of cancelling moments: measure it on the scale sum_j |r_ij| |f_ij|
+    r = o.relative_positions(s.x, s.X, s.body_offsets, s.box)
+    moment = np.add.reduceat(np.linalg.norm(r, axis=1) * np.linalg.norm(f_ref, axis=1), s.body_offsets[:-1])
+    assert np.max(np.abs(L.cpu().numpy() - L_ref)) < FP64_RTOL * moment.max()
+    assert abs(U.item() - U_ref) < FP64_RTOL * abs(U_ref)
+    ib.pme_destroy(ctx)
+
+
+def test_bd_step_matches_oracle(cuda_lib):
+    import torch
+    ib = cuda_lib
+    s = C.small_system(seed=4, n_bodies=2, level=1, n_ions=40, L=8.0, a=0.15, mesh=(32, 32, 32), tol=1e-6)
+    x = s.x.copy()
+    x[-1] = x[-2] + [0.1, 0.05, 0.0]     # two overlapping ions: hard-sphere push
+    X = s.X.copy()
+    X[-1] = x[-1]
+    rng = np.random.default_rng(9)
+    f = rng.normal(size=(s.n, 3))
+    dt, gamma, kT, seed, step = 1e-3, 1.3, 0.9, 12345, 17
+    f_tot = f + o.hard_sphere_forces(x, s.body_offsets, s.box, s.a, gamma, dt)
+    xr, Xr = o.bd_step(x, X, s.body_offsets, f_tot, s.box, s.a, dt, gamma=gamma, kT=kT, seed=seed, step=step)
+    ctx = context(ib, s)
+    bodies = ib.Bodies(cuda(s.body_offsets.astype(np.int32)), cuda(X), cuda(s.Q))
+    xo = torch.zeros((s.n, 3), dtype=torch.float64, device="cuda")
+    Xo = torch.zeros((s.n_bodies, 3), dtype=torch.float64, device="cuda")
+    ib.ibpme_bd_step(ctx, s.n, cuda(x), bodies, cuda(f), dt, gamma, kT, seed, step, xo, Xo)
+    torch.cuda.synchronize()
+    # positions are compared modulo the box (the library works with wrapped positions)
+    dx = o.min_image(xo.cpu().numpy() - xr, s.box)
+    dX = o.min_image(Xo.cpu().numpy() - Xr, s.box)
+    assert np.max(np.abs(dx)) < 1e-12 and np.max(np.abs(dX)) < 1e-12
+    ib.pme_destroy(ctx)
+
+
+def test_full_size_lattice_field_sampled(cuda_lib):
+    """64 spheres + 100,000 ions on 256^3 in mixed precision: the potential at a
+    seeded sample of beads against the oracle's exact Ewald sum at those beads."""
+    ib = cuda_lib
+    s = C.config3()
+    q = random_neutral_charges(s.n, 3)
+    ctx = context(ib, s)
+    psi, _ = _field(ib, ctx, s.x, q, with_E=False)
+    t = np.random.default_rng(0).choice(s.n, size=64, replace=False).astype(np.int32)
+    ref = o.potential(s.x, q, s.box, s.a, s.eps, targets=t, xi=0.5)   # small xi: few k-vectors
+    assert rel_err(psi[0][t], ref) < MIXED_RTOL
+    ib.pme_destroy(ctx)
