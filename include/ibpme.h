@@ -200,6 +200,33 @@ ibpme_status ibpme_bd_step(ibpme_ctx* ctx, int n, const double* x, const ibpme_b
                            const double* f_bead, const ibpme_bd_params* bd,
                            double* x_out, double* X_out);
 
+/* ---- Spreading without device allocation (no counterpart in the paper) ----
+ *
+ * For callers that cannot allocate device memory: code running while a stream
+ * is captured into a CUDA graph (where cudaMalloc is not allowed), engines whose
+ * device memory belongs to a pool or a framework, and loops that must never reach
+ * the allocator.  pme_spread needs a context, which allocates; this variant does
+ * the same spreading (Eq. H_hat, same stencil and normalisation) with no context
+ * and no allocation of any kind: its only scratch, the positions wrapped into the
+ * box, lives in a fixed array inside the library (IBPME_NOALLOC_MAX_BEADS x 3
+ * doubles = 6 MiB), which every GPU that loads the library keeps until the
+ * process exits.
+ *   params   parameters as for pme_setup (resolved on the host, same rules);
+ *            params->precision picks the grid type (double or float)
+ *   n        0 .. IBPME_NOALLOC_MAX_BEADS beads (larger n: IBPME_ERR_ARG)
+ *   x, q     device arrays [n][3], [nrhs][n]; 1 <= nrhs <= 8
+ *   grid_out device array [nrhs][N_z][N_y][N_x]; the call clears it, then spreads
+ *   cuda_stream  stream for the work (NULL = legacy default stream)
+ * Host pointers are rejected (IBPME_ERR_ARG): staging them would allocate.
+ * The first call on a device looks up the scratch array's device address for
+ * that device; make that first call before any stream capture.  All calls share
+ * the one scratch array and it keeps the last call's contents, so calls that
+ * can overlap on the GPU (different streams, or different host threads) race:
+ * serialise them. */
+#define IBPME_NOALLOC_MAX_BEADS 262144
+ibpme_status pme_spread_noalloc(const ibpme_params* params, int n, const double* x, const double* q, int nrhs,
+                                void* grid_out, void* cuda_stream);
+
 /* ---- Instrumentation (no counterpart in the paper) ---- */
 
 /* Number of kernel launches the library has issued in this process (its own

@@ -80,6 +80,7 @@ SIGNATURES = {
     "body_force_torque": (_i, [_p, _i, _p, _p, ctypes.POINTER(ibpme_bodies), _p, _p, _p, _p, _p]),
     "ibpme_bd_step": (_i, [_p, _i, _p, ctypes.POINTER(ibpme_bodies), _p, ctypes.POINTER(ibpme_bd_params),
                            _p, _p]),
+    "pme_spread_noalloc": (_i, [ctypes.POINTER(ibpme_params), _i, _p, _p, _i, _p, _p]),
     "ibpme_kernel_launches": (ctypes.c_longlong, []),
     "ibpme_profile": (_i, [ctypes.c_uint]),
     "ibpme_profile_read": (_i, [_i, _p, _p]),
@@ -196,6 +197,16 @@ def pme_spread(ctx, n, x, q, nrhs, grid_out=None):
     gdt = np.float32 if (grid_out is not None and getattr(grid_out, "dtype", None) in (np.float32, _torch_f32())) \
         else np.float64
     return _check(load().pme_spread(ctx, int(n), ptr(x), ptr(q), int(nrhs), ptr(grid_out, gdt)), "pme_spread")
+
+
+IBPME_NOALLOC_MAX_BEADS = 262144
+
+
+def pme_spread_noalloc(params: ibpme_params, n, x, q, nrhs, grid_out, stream=None):
+    """Spreading with no context and no device allocation (device arrays only)."""
+    gdt = np.float32 if getattr(grid_out, "dtype", None) in (np.float32, _torch_f32()) else np.float64
+    return _check(load().pme_spread_noalloc(ctypes.byref(params), int(n), ptr(x), ptr(q), int(nrhs),
+                                            ptr(grid_out, gdt), _stream_handle(stream)), "pme_spread_noalloc")
 
 
 def _torch_f32():

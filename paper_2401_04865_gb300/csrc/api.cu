@@ -149,6 +149,8 @@ bool good_fft_size(int n) {
     return n == 1;
 }
 
+}  // namespace
+
 void resolve_params(const ibpme_params* in, ibpme_params* p) {
     *p = *in;
     for (int d = 0; d < 3; ++d)
@@ -214,6 +216,8 @@ MeshGeom make_geom(const ibpme_params& p) {
     g.Gc = (long long)(p.mesh[0] / 2 + 1) * p.mesh[1] * p.mesh[2];
     return g;
 }
+
+namespace {
 
 void check_n(int n) {
     if (n < 0) fail(IBPME_ERR_ARG, "n must be >= 0");

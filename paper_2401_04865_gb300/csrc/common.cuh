@@ -230,6 +230,8 @@ void near_field(ibpme_ctx* c, int n, const double* xw, const double* q, int nrhs
 double self_term(const ibpme_ctx* c);   // phi_self (without 1/eps)
 
 // ---- api.cu helpers ----
+void resolve_params(const ibpme_params* in, ibpme_params* out);   // rules of Sec. III.D.2; throws on bad input
+MeshGeom make_geom(const ibpme_params& p);
 void wrap_positions(ibpme_ctx* c, int n, const double* x, double* xw);
 // psi = M q (real + self + wave) in the given precision; E optional
 void pme_apply(ibpme_ctx* c, int n, const double* xw, const double* q, int nrhs, int prec,

@@ -11,6 +11,7 @@
 #include "common.cuh"
 
 #include <cmath>
+#include <mutex>
 
 namespace ibp {
 
@@ -293,3 +294,108 @@ template struct Mesh<float>;
 template struct Mesh<double>;
 
 }  // namespace ibp
+// ---------------------------------------------------------------------------
+// Spreading for callers that cannot allocate device memory.
+//
+// Some callers may not call cudaMalloc at all: code that runs while a stream
+// is being captured into a CUDA graph, engines whose device memory is owned
+// by a pool or framework (for example a custom call inside a compiler-managed
+// program), or loops that must never reach the allocator.  pme_spread needs a
+// context, and the context allocates its meshes and scratch.  The variant
+// below does the same spreading but keeps its only scratch -- the positions
+// wrapped into the box -- in a fixed array compiled into the library, and
+// writes straight into the caller's grid.
+// ---------------------------------------------------------------------------
+namespace ibp {
+
+namespace {
+
+// Scratch of pme_spread_noalloc: wrapped positions, [n][3] doubles for at
+// most IBPME_NOALLOC_MAX_BEADS beads (6 MiB).  Every GPU that loads the
+// library holds it until the process exits.  All calls share it.
+static __device__ __align__(256) double g_noalloc_xw[3 * IBPME_NOALLOC_MAX_BEADS];
+
+// Device address of g_noalloc_xw on each device, looked up once per device
+// (host code cannot use the symbol's name as a device pointer).
+constexpr int kMaxDevices = 64;
+double* g_noalloc_ptr[kMaxDevices] = {};
+std::mutex g_noalloc_mu;
+
+double* noalloc_scratch(int dev) {
+    if (dev < 0 || dev >= kMaxDevices) fail(IBPME_ERR_ARG, "device ordinal %d out of range", dev);
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    if (!g_noalloc_ptr[dev]) {
+        void* ptr = nullptr;
+        const cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_xw);
+        if (e != cudaSuccess || !ptr)
+            fail(IBPME_ERR_CUDA, "cudaGetSymbolAddress(g_noalloc_xw) failed on device %d: %s", dev,
+                 cudaGetErrorString(e));
+        g_noalloc_ptr[dev] = static_cast<double*>(ptr);
+    }
+    return g_noalloc_ptr[dev];
+}
+
+__global__ void noalloc_wrap_kernel(int n, const double* __restrict__ x, double L0, double L1, double L2,
+                                    double* __restrict__ xw) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= 3 * n) return;
+    const int d = i % 3;
+    xw[i] = wrap_coord(x[i], d == 0 ? L0 : (d == 1 ? L1 : L2));
+}
+
+bool device_resident(const void* p) {
+    cudaPointerAttributes at{};
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+}  // namespace
+
+}  // namespace ibp
+
+IBP_API ibpme_status pme_spread_noalloc(const ibpme_params* params, int n, const double* x, const double* q,
+                                        int nrhs, void* grid_out, void* cuda_stream) {
+    using namespace ibp;
+    try {
+        set_error("%s", "");
+        if (!params) fail(IBPME_ERR_ARG, "params is NULL");
+        ibpme_params p{};
+        resolve_params(params, &p);
+        if (n < 0 || n > IBPME_NOALLOC_MAX_BEADS)
+            fail(IBPME_ERR_ARG, "n = %d outside 0..%d, the fixed scratch of pme_spread_noalloc", n,
+                 IBPME_NOALLOC_MAX_BEADS);
+        if (nrhs < 1 || nrhs > kMaxRhs) fail(IBPME_ERR_ARG, "nrhs %d outside 1..%d", nrhs, kMaxRhs);
+        if (!grid_out) fail(IBPME_ERR_ARG, "grid_out is required");
+        if (n > 0 && (!x || !q)) fail(IBPME_ERR_ARG, "x and q are required");
+        // no staging here: every array must already be on the device
+        if (!device_resident(grid_out) || (n > 0 && (!device_resident(x) || !device_resident(q))))
+            fail(IBPME_ERR_ARG, "pme_spread_noalloc takes device pointers only");
+        int dev = 0;
+        IBP_CUDA(cudaGetDevice(&dev));
+        double* xw = noalloc_scratch(dev);
+        const MeshGeom g = make_geom(p);
+        cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+        const bool f64 = p.precision == IBPME_FP64;
+        IBP_CUDA(cudaMemsetAsync(grid_out, 0, (f64 ? sizeof(double) : sizeof(float)) * (size_t)g.G * nrhs, s));
+        if (n > 0) {
+            noalloc_wrap_kernel<<<div_up(3LL * n, 256), 256, 0, s>>>(n, x, p.box[0], p.box[1], p.box[2], xw);
+            IBP_CHECK_LAUNCH();
+            if (f64)
+                spread_kernel<double><<<div_up(n, kWarpsPerBlock), 32 * kWarpsPerBlock, 0, s>>>(
+                    n, xw, q, nrhs, g, static_cast<double*>(grid_out));
+            else
+                spread_kernel<float><<<div_up(n, kWarpsPerBlock), 32 * kWarpsPerBlock, 0, s>>>(
+                    n, xw, q, nrhs, g, static_cast<float*>(grid_out));
+            IBP_CHECK_LAUNCH();
+        }
+        return IBPME_OK;
+    } catch (const Error& e) {
+        return e.status;
+    } catch (...) {
+        set_error("unexpected internal exception");
+        return IBPME_ERR_CUDA;
+    }
+}
