@@ -133,7 +133,7 @@ typedef struct {
     int guess;          /* IBPME_GUESS_*; USER reads q_out as the initial charges.  The initial
                            body potentials are always the least-squares fit to the initial
                            charges (mean over each body of (M q)_j - r_j.E0) */
-    const void* mlp;    /* trained warm-start model (IBPME_GUESS_LEARNED), else NULL */
+    const void* mlp;    /* trained ibpme_mlp (IBPME_GUESS_LEARNED), else NULL */
     int precision;      /* -1 = context precision, else IBPME_FP64 / IBPME_MIXED (mixed needs a
                            mixed context) */
 } ibpme_solve_opts;
@@ -200,6 +200,51 @@ ibpme_status ibpme_bd_step(ibpme_ctx* ctx, int n, const double* x, const ibpme_b
                            const double* f_bead, const ibpme_bd_params* bd,
                            double* x_out, double* X_out);
 
+/* ---- Learned warm start (not in the paper) ----
+ *
+ * A small network (IBPME_MLP_IN features -> 64 -> 64 -> 1, tanh, FP32) maps
+ * per-bead features to a first guess of the induced charge of beads on
+ * multi-bead bodies.  Features, for field E0 and the "fixed" charges (ions and
+ * each body's net charge spread evenly over its beads) with potential psi_fix and
+ * field E_fix from one PME evaluation; u = eps A (E0 + E_fix), A = 4 pi R^2 / N the
+ * area per bead of a body of N beads and mean bead distance R from its reference
+ * point, S the rms of |u| over the body, n = r/|r| the outward radial direction:
+ *   f0 = u.n / S, f1 = |u - (u.n) n| / S, f2 = (psi_fix - <psi_fix>_body) 4 pi eps a / S,
+ *   f3 = (Q/N) / S (clipped to +-10), f4 = |r|/R - 1, f5 = ln(N)/8, f6 = 10 a / R,
+ *   f7 = eps A |E_fix| / S.
+ * The guess is q = Q/N + S y, then shifted body by body so that sum q = Q exactly.
+ * The network is trained on converged solves (ibpme_mlp_train); the solve uses it
+ * with IBPME_GUESS_LEARNED and falls back to the zero guess (stats.fell_back = 1)
+ * if its residual is not smaller than |b|.
+ * Parameter layout (floats): W1[64][IN], b1[64], W2[64][64], b2[64], W3[64], b3. */
+#define IBPME_MLP_IN 8
+#define IBPME_MLP_HIDDEN 64
+#define IBPME_MLP_NPARAM (IBPME_MLP_HIDDEN * IBPME_MLP_IN + IBPME_MLP_HIDDEN + IBPME_MLP_HIDDEN * IBPME_MLP_HIDDEN + \
+                          IBPME_MLP_HIDDEN + IBPME_MLP_HIDDEN + 1)
+typedef struct ibpme_mlp ibpme_mlp;
+
+/* New network on the current device, weights N(0, 1/fan_in) from seed, biases 0. */
+ibpme_status ibpme_mlp_create(ibpme_mlp** mlp, unsigned long long seed);
+ibpme_status ibpme_mlp_destroy(ibpme_mlp* mlp);
+/* Copy the IBPME_MLP_NPARAM parameters out / in (host or device pointer); set resets Adam. */
+ibpme_status ibpme_mlp_get(const ibpme_mlp* mlp, float* params);
+ibpme_status ibpme_mlp_set(ibpme_mlp* mlp, const float* params);
+/* y[i] = net(feat[i]) for n samples; feat [n][IBPME_MLP_IN], y [n], device pointers. */
+ibpme_status ibpme_mlp_forward(ibpme_mlp* mlp, int n, const float* feat, float* y, void* cuda_stream);
+/* Gradient of the mean squared error L = (1/n) sum (net(feat_i) - target_i)^2 with
+ * respect to the parameters (grad [IBPME_MLP_NPARAM], host or device) and L. */
+ibpme_status ibpme_mlp_gradient(ibpme_mlp* mlp, int n, const float* feat, const float* target, float* grad,
+                                float* loss, void* cuda_stream);
+/* Adam (lr, beta1 0.9, beta2 0.999) on the mean squared error over shuffled
+ * mini-batches of `batch` samples for `epochs` passes; loss_out gets the last
+ * epoch's mean batch loss.  feat, target: device arrays. */
+ibpme_status ibpme_mlp_train(ibpme_mlp* mlp, int n, const float* feat, const float* target, int batch, int epochs,
+                             float lr, unsigned long long seed, float* loss_out, void* cuda_stream);
+/* The features above for every bead and field: feat [nrhs][n][IBPME_MLP_IN]
+ * (zeros for single-bead bodies); device pointers only. */
+ibpme_status ibpme_features(ibpme_ctx* ctx, int n, const double* x, const ibpme_bodies* bodies, const double* E0,
+                            int nrhs, float* feat);
+
 /* ---- Spreading without device allocation (no counterpart in the paper) ----
  *
  * For callers that cannot allocate device memory: code running while a stream
@@ -230,7 +275,8 @@ ibpme_status pme_spread_noalloc(const ibpme_params* params, int n, const double*
 /* ---- Instrumentation (no counterpart in the paper) ---- */
 
 /* Number of kernel launches the library has issued in this process (its own
- * kernels only; cuFFT's launches are not counted). */
+ * kernels, including those replayed from its captured CUDA graphs; cuFFT's
+ * launches are not counted). */
 long long ibpme_kernel_launches(void);
 
 /* Stages that can be timed: 0 near_build (cell list + pair table), 1 near_apply

@@ -316,6 +316,9 @@ IBP_API ibpme_status pme_setup(ibpme_ctx** ctx, const ibpme_params* params, void
                 c->mesh32.plans(1, c->stream);
                 c->have32 = true;
             }
+            IBP_CUDA(cudaStreamCreateWithFlags(&c->work, cudaStreamNonBlocking));
+            IBP_CUDA(cudaEventCreateWithFlags(&c->ev_in, cudaEventDisableTiming));
+            IBP_CUDA(cudaEventCreateWithFlags(&c->ev_out, cudaEventDisableTiming));
             near_setup(c);
             pinned_host(c, 4096);
             IBP_CUDA(cudaStreamSynchronize(c->stream));
@@ -330,8 +333,14 @@ IBP_API ibpme_status pme_setup(ibpme_ctx** ctx, const ibpme_params* params, void
 
 IBP_API ibpme_status pme_destroy(ibpme_ctx* c) {
     if (!c) return IBPME_OK;
-    if (c->stream || true) cudaStreamSynchronize(c->stream);
+    cudaStreamSynchronize(c->stream);
     krylov_destroy(c);
+    if (c->work) {
+        cudaStreamSynchronize(c->work);
+        cudaStreamDestroy(c->work);
+    }
+    if (c->ev_in) cudaEventDestroy(c->ev_in);
+    if (c->ev_out) cudaEventDestroy(c->ev_out);
     c->mesh64.destroy();
     c->mesh32.destroy();
     if (c->pinned) cudaFreeHost(c->pinned);
@@ -456,9 +465,11 @@ IBP_API ibpme_status induced_charge_solve(ibpme_ctx* c, int n, const double* x, 
         a.restart = o.restart > 0 ? o.restart : 50;
         if (a.restart > 128) fail(IBPME_ERR_ARG, "restart must be <= 128");
         a.max_iter = o.max_iter > 0 ? o.max_iter : 3000;
-        if (o.guess == IBPME_GUESS_LEARNED) fail(IBPME_ERR_ARG, "learned warm start is not available in this build");
-        if (o.guess != IBPME_GUESS_ZERO && o.guess != IBPME_GUESS_USER) fail(IBPME_ERR_ARG, "unknown guess mode");
-        a.user_guess = o.guess == IBPME_GUESS_USER;
+        if (o.guess == IBPME_GUESS_LEARNED && !o.mlp) fail(IBPME_ERR_ARG, "IBPME_GUESS_LEARNED needs opts->mlp");
+        if (o.guess != IBPME_GUESS_ZERO && o.guess != IBPME_GUESS_USER && o.guess != IBPME_GUESS_LEARNED)
+            fail(IBPME_ERR_ARG, "unknown guess mode");
+        a.user_guess = o.guess == IBPME_GUESS_USER || o.guess == IBPME_GUESS_LEARNED;
+        a.learned = o.guess == IBPME_GUESS_LEARNED;
         const double* dx = static_cast<const double*>(stage_in(c, x, sizeof(double) * 3 * n, c->st_x));
         a.E0 = static_cast<const double*>(stage_in(c, E0, sizeof(double) * 3 * nrhs, c->st_E0));
         double* xw = static_cast<double*>(c->xw.ensure(sizeof(double) * 3 * n));
@@ -471,6 +482,7 @@ IBP_API ibpme_status induced_charge_solve(ibpme_ctx* c, int n, const double* x, 
         OutArg os = stage_out(c, S_out, sizeof(double) * 3 * (size_t)nrhs * nb, c->st_out3);
         a.q = static_cast<double*>(oq.dev);
         a.psi = static_cast<double*>(op.dev);
+        if (a.learned) learned_guess(c, static_cast<const ibpme_mlp*>(o.mlp), n, xw, a.E0, nrhs, a.q);
         ibpme_solve_stats st{};
         solve(c, a, &st);
         if (S_out) body_dipoles(c, n, a.q, nrhs, static_cast<double*>(os.dev));

@@ -45,7 +45,8 @@ void set_error(const char* fmt, ...);
 
 // Every kernel launch of the library is followed by IBP_CHECK_LAUNCH(), which
 // also counts it (cuFFT's own launches are not counted).
-void count_launch();
+void count_launch(long long k = 1);
+long long launch_count();
 #define IBP_CHECK_LAUNCH()                 \
     do {                                   \
         ::ibp::count_launch();             \
@@ -192,6 +193,13 @@ struct ProfScope {
     ProfScope(int stage, cudaStream_t s);
     ~ProfScope();
 };
+unsigned prof_mask();
+// Scopes opened between begin and end are being captured into CUDA graph `gid`:
+// their events become graph nodes, re-recorded by every replay, and
+// prof_graph_collect(gid) adds the last replay's times (call it after a sync).
+void prof_capture_begin(int gid);
+void prof_capture_end();
+void prof_graph_collect(int gid);
 
 }  // namespace ibp
 
@@ -218,6 +226,9 @@ struct ibpme_ctx {
     ibp::DevBuf scalars;     // small device scratch
     void* pinned = nullptr;  // small pinned host scratch
     size_t pinned_bytes = 0;
+    cudaStream_t work = nullptr;              // the context's own stream (solves, graph capture)
+    ibp::DevBuf ml_feat, ml_scratch, ml_scales, ml_y;   // learned warm start
+    cudaEvent_t ev_in = nullptr, ev_out = nullptr;
 };
 
 namespace ibp {
@@ -247,6 +258,12 @@ void body_energy(ibpme_ctx* c, int n, const double* q, const double* psi, const 
 void bd_step(ibpme_ctx* c, int n, const double* x, const double* f, const ibpme_bd_params* bd,
              double* x_out, double* X_out);
 
+// ---- mlp.cu ----
+void compute_features(ibpme_ctx* c, int n, const double* xw, const double* E0, int nrhs, float* feat,
+                      DevBuf& scratch, DevBuf& scales);
+void learned_guess(ibpme_ctx* c, const ibpme_mlp* mlp, int n, const double* xw, const double* E0, int nrhs,
+                   double* q);
+
 // ---- krylov.cu ----
 struct SolveArgs {
     int n, nrhs, prec;
@@ -255,6 +272,7 @@ struct SolveArgs {
     double* q;          // device [nrhs][n] (guess in, solution out)
     double* psi;        // device [nrhs][nb] or nullptr
     bool user_guess;
+    bool learned;       // the guess came from the learned model: fall back to zero if it is worse
     double rtol;
     int restart, max_iter;
 };

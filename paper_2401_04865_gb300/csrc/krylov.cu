@@ -27,7 +27,15 @@ namespace ibp {
 
 struct Krylov {
     int nk = 0, R = 0, m = 0, nblk = 0;
-    DevBuf V, H, cs, sn, g, y, w, x, d, r, rc, part, scal, active, qop, psi, psi_tot, qtot, Ax, norms;
+    DevBuf V, H, cs, sn, g, y, w, x, d, r, rc, part, scal, active, qop, psi, psi_tot, qtot, Ax, norms, jdev;
+    // one captured Arnoldi iteration per mesh precision, replayed for every j
+    cudaGraphExec_t exec[2] = {nullptr, nullptr};
+    std::vector<long long> sig[2];
+    long long nodes[2] = {0, 0};   // library kernels captured in each graph (counted per replay)
+    ~Krylov() {
+        for (auto& e : exec)
+            if (e) cudaGraphExecDestroy(e);
+    }
 };
 
 namespace {
@@ -53,9 +61,10 @@ __device__ __forceinline__ double block_sum(double v, double* sh) {
 }
 
 // part[r][blk][i] = sum over this block's chunk of V_i . w, i = 0..j
-__global__ void __launch_bounds__(kThreads) dots_kernel(int nk, int m, int j, const double* __restrict__ V,
-                                                         const double* __restrict__ w, const int* __restrict__ active,
-                                                         double* __restrict__ part) {
+__global__ void __launch_bounds__(kThreads) dots_kernel(int nk, int m, const int* __restrict__ jdev,
+                                                         const double* __restrict__ V, const double* __restrict__ w,
+                                                         const int* __restrict__ active, double* __restrict__ part) {
+    const int j = *jdev;
     const int r = blockIdx.y;
     if (!active[r]) return;
     const int nblk = gridDim.x;
@@ -74,9 +83,11 @@ __global__ void __launch_bounds__(kThreads) dots_kernel(int nk, int m, int j, co
 
 // w -= sum_i h_i V_i with h_i = sum over blocks of part; H[:, j] (+)= h.
 // In the second pass also the partial sums of |w|^2 go to part[.., m+1].
-__global__ void __launch_bounds__(kThreads) update_kernel(int nk, int m, int j, int pass, const double* __restrict__ V,
-                                                           double* __restrict__ w, double* __restrict__ H,
-                                                           const int* __restrict__ active, double* __restrict__ part) {
+__global__ void __launch_bounds__(kThreads) update_kernel(int nk, int m, const int* __restrict__ jdev, int pass,
+                                                           const double* __restrict__ V, double* __restrict__ w,
+                                                           double* __restrict__ H, const int* __restrict__ active,
+                                                           double* __restrict__ part) {
+    const int j = *jdev;
     const int r = blockIdx.y;
     if (!active[r]) return;
     const int nblk = gridDim.x;
@@ -111,17 +122,10 @@ __global__ void __launch_bounds__(kThreads) update_kernel(int nk, int m, int j, 
 }
 
 // h_{j+1,j} = |w|; Givens rotations on column j; g update; residual estimate |g_{j+1}|.
-__global__ void finish_kernel(int m, int j, int nblk, const double* __restrict__ part, double* __restrict__ H,
-                              double* __restrict__ cs, double* __restrict__ sn, double* __restrict__ g,
-                              double* __restrict__ scal, const int* __restrict__ active) {
-    const int r = blockIdx.x;
-    const int lane = threadIdx.x;
-    if (!active[r]) return;
-    double s = 0.0;
-    for (int bb = lane; bb < nblk; bb += 32) s += part[((size_t)r * nblk + bb) * (m + 2) + m + 1];
-    s = warp_sum(s);
-    if (lane != 0) return;
-    const double h = sqrt(s);
+// Givens rotations of column j of H and the residual estimate; shared by the
+// multi-block and the single-block Arnoldi paths.
+__device__ void givens_column(int m, int j, int r, double h, double* __restrict__ H, double* __restrict__ cs,
+                              double* __restrict__ sn, double* __restrict__ g, double* __restrict__ scal) {
     double* Hc = H + ((size_t)r * m + j) * (m + 1);
     double* c = cs + (size_t)r * m;
     double* sg = sn + (size_t)r * m;
@@ -150,15 +154,101 @@ __global__ void finish_kernel(int m, int j, int nblk, const double* __restrict__
     sc[S_INVH] = (h > 1e-300 && h > 1e-14 * den) ? 1.0 / h : 0.0;
 }
 
-__global__ void normalize_kernel(int nk, int m, int j, int R, const double* __restrict__ w,
+__global__ void finish_kernel(int m, const int* __restrict__ jdev, int nblk, const double* __restrict__ part,
+                              double* __restrict__ H, double* __restrict__ cs, double* __restrict__ sn,
+                              double* __restrict__ g, double* __restrict__ scal, const int* __restrict__ active) {
+    const int j = *jdev;
+    const int r = blockIdx.x;
+    const int lane = threadIdx.x;
+    if (!active[r]) return;
+    double s = 0.0;
+    for (int bb = lane; bb < nblk; bb += 32) s += part[((size_t)r * nblk + bb) * (m + 2) + m + 1];
+    s = warp_sum(s);
+    if (lane != 0) return;
+    givens_column(m, j, r, sqrt(s), H, cs, sn, g, scal);
+}
+
+__global__ void normalize_kernel(int nk, int m, const int* __restrict__ jdev, int R, const double* __restrict__ w,
                                  const double* __restrict__ scal, const int* __restrict__ active,
                                  double* __restrict__ V) {
+    const int j = *jdev;
     const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (t >= (long long)nk * R) return;
     const int r = (int)(t / nk);
     const long long e = t - (long long)r * nk;
     if (!active[r]) return;
     V[((size_t)r * (m + 1) + j + 1) * nk + e] = w[t] * scal[(size_t)r * S_COUNT + S_INVH];
+}
+
+__global__ void advance_kernel(int* __restrict__ jdev) { *jdev += 1; }
+
+// One Arnoldi step (CGS2 + Givens + normalisation) by a single block per
+// right-hand side, for Krylov vectors short enough that one block streams them
+// faster than a chain of six grid-wide launches.  Ends by advancing j.
+constexpr int kSmallThreads = 1024;
+constexpr int kSmallMaxNk = 32 * kSmallThreads;
+
+__global__ void __launch_bounds__(kSmallThreads)
+arnoldi_small_kernel(int nk, int m, int* __restrict__ jdev, const double* __restrict__ V, double* __restrict__ w,
+                     double* __restrict__ H, double* __restrict__ cs, double* __restrict__ sn, double* __restrict__ g,
+                     double* __restrict__ scal, const int* __restrict__ active, double* __restrict__ Vout) {
+    __shared__ double hc[130];
+    __shared__ double sh[32];
+    __shared__ double inv_h;
+    const int j = *jdev;
+    const int r = blockIdx.x;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarp = blockDim.x >> 5;
+    const bool act = active[r] != 0;
+    double* wr = w + (size_t)r * nk;
+    const double* Vr = V + (size_t)r * (m + 1) * nk;
+    double* Hc = H + ((size_t)r * m + j) * (m + 1);
+    if (act) {
+        for (int pass = 0; pass < 2; ++pass) {
+            for (int i = warp; i <= j; i += nwarp) {
+                const double* vi = Vr + (size_t)i * nk;
+                double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;   // independent chains for ILP
+                int t = lane;
+                for (; t + 96 < nk; t += 128) {
+                    a0 += vi[t] * wr[t];
+                    a1 += vi[t + 32] * wr[t + 32];
+                    a2 += vi[t + 64] * wr[t + 64];
+                    a3 += vi[t + 96] * wr[t + 96];
+                }
+                for (; t < nk; t += 32) a0 += vi[t] * wr[t];
+                const double acc = warp_sum((a0 + a1) + (a2 + a3));
+                if (lane == 0) hc[i] = acc;
+            }
+            __syncthreads();
+            for (int t = threadIdx.x; t < nk; t += blockDim.x) {
+                double v0 = wr[t], v1 = 0.0, v2 = 0.0, v3 = 0.0;
+                int i = 0;
+                for (; i + 3 <= j; i += 4) {
+                    v0 -= hc[i] * Vr[(size_t)i * nk + t];
+                    v1 -= hc[i + 1] * Vr[(size_t)(i + 1) * nk + t];
+                    v2 -= hc[i + 2] * Vr[(size_t)(i + 2) * nk + t];
+                    v3 -= hc[i + 3] * Vr[(size_t)(i + 3) * nk + t];
+                }
+                for (; i <= j; ++i) v0 -= hc[i] * Vr[(size_t)i * nk + t];
+                wr[t] = (v0 + v1) + (v2 + v3);
+            }
+            if (threadIdx.x <= j) Hc[threadIdx.x] = (pass == 0 ? 0.0 : Hc[threadIdx.x]) + hc[threadIdx.x];
+            __syncthreads();
+        }
+        double acc = 0.0;
+        for (int t = threadIdx.x; t < nk; t += blockDim.x) acc += wr[t] * wr[t];
+        const double nrm2 = block_sum(acc, sh);
+        if (threadIdx.x == 0) {
+            givens_column(m, j, r, sqrt(nrm2), H, cs, sn, g, scal);
+            inv_h = scal[(size_t)r * S_COUNT + S_INVH];
+        }
+        __syncthreads();
+        double* vn = Vout + ((size_t)r * (m + 1) + j + 1) * nk;
+        for (int t = threadIdx.x; t < nk; t += blockDim.x) vn[t] = wr[t] * inv_h;
+    }
+    // with one block, every thread has read j by now: advance it here (with several
+    // right-hand sides a separate launch advances it, after all blocks are done)
+    __syncthreads();
+    if (gridDim.x == 1 && threadIdx.x == 0) *jdev = j + 1;
 }
 
 // Back substitution H(0:k,0:k) y = g(0:k) per right-hand side.
@@ -227,10 +317,13 @@ __global__ void start_kernel(int nk, int m, int R, const double* __restrict__ rr
 }
 
 // ---- the reduced saddle operator ----
+// u of right-hand side r starts at u + r * ustride (+ j * nk when jdev is given: V_j)
 __global__ void scatter_kernel(int nfree, long long ustride, int n, int R, const int* __restrict__ free_idx,
-                               const double* __restrict__ u, double* __restrict__ qop) {
+                               const double* __restrict__ u, const int* __restrict__ jdev, int nk,
+                               double* __restrict__ qop) {
     const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (t >= (long long)nfree * R) return;
+    if (jdev) u += (size_t)(*jdev) * nk;
     const int r = (int)(t / nfree), i = (int)(t % nfree);
     qop[(size_t)r * n + free_idx[i]] = u[(size_t)r * ustride + i];
 }
@@ -239,7 +332,8 @@ __global__ void scatter_kernel(int nfree, long long ustride, int n, int R, const
 __global__ void assemble_kernel(int nfree, int nmb, int nk, long long ustride, int n, int R,
                                 const int* __restrict__ free_idx, const int* __restrict__ mb_of_free,
                                 const int* __restrict__ free_off, const double* __restrict__ psi,
-                                const double* __restrict__ u, double* __restrict__ y) {
+                                const double* __restrict__ u, const int* __restrict__ jdev, double* __restrict__ y) {
+    if (jdev) u += (size_t)(*jdev) * nk;
     const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     const long long top = (long long)nfree * R;
     if (t < top) {
@@ -425,24 +519,115 @@ struct Solver {
         k->scal.ensure(sizeof(double) * (size_t)R * S_COUNT);
         k->active.ensure(sizeof(int) * R);
         k->norms.ensure(sizeof(double) * R);
+        k->jdev.ensure(sizeof(int));
         const size_t full = (size_t)R * n;
         for (DevBuf* b : {&k->qop, &k->psi, &k->psi_tot, &k->qtot}) b->ensure(sizeof(double) * full);
     }
 
     // y = A(prec) u for the reduced saddle operator; u[r] starts at u + r * ustride
-    void apply(int prec, const double* u, double* y, long long ustride = -1) {
+    // (+ j * nk with j read on the device when jdev is given)
+    void apply(int prec, const double* u, double* y, long long ustride = -1, const int* jdev = nullptr) {
         const BodyData& bd = c->bodies;
         if (ustride < 0) ustride = nk;
         scatter_kernel<<<blocks_for((long long)nfree * R), 256, 0, s()>>>(nfree, ustride, n, R,
-                                                                          bd.free_idx.as<int>(), u, D(k->qop));
+                                                                          bd.free_idx.as<int>(), u, jdev, nk,
+                                                                          D(k->qop));
         IBP_CHECK_LAUNCH();
         pme_apply(c, n, a.xw, D(k->qop), R, prec, D(k->psi), nullptr, true);
         const long long work = ((long long)nfree * R + 31) / 32 * 32 + 32LL * nmb * R;
         assemble_kernel<<<blocks_for(work), 256, 0, s()>>>(nfree, nmb, nk, ustride, n, R, bd.free_idx.as<int>(),
                                                            bd.mb_of_free.as<int>(), bd.free_off.as<int>(), D(k->psi),
-                                                           u, y);
+                                                           u, jdev, y);
         IBP_CHECK_LAUNCH();
-        if (prec == IBPME_FP64) ++matvec64;
+    }
+
+    // One Arnoldi iteration entirely on the device: w = A V_j, CGS2 against
+    // V_0..V_j, Givens on column j, V_{j+1} = w / h_{j+1,j}, j += 1.
+    void iterate(int prec) {
+        int* jd = k->jdev.as<int>();
+        apply(prec, D(k->V), D(k->w), (long long)(m + 1) * nk, jd);
+        ProfScope ps(ST_KRYLOV, s());
+        if (nk <= kSmallMaxNk) {
+            arnoldi_small_kernel<<<R, kSmallThreads, 0, s()>>>(nk, m, jd, D(k->V), D(k->w), D(k->H), D(k->cs),
+                                                               D(k->sn), D(k->g), D(k->scal), k->active.as<int>(),
+                                                               D(k->V));
+            IBP_CHECK_LAUNCH();
+            if (R > 1) {
+                advance_kernel<<<1, 1, 0, s()>>>(jd);
+                IBP_CHECK_LAUNCH();
+            }
+            return;
+        }
+        dim3 ag(k->nblk, R);
+        for (int pass = 0; pass < 2; ++pass) {   // CGS2
+            dots_kernel<<<ag, kThreads, 0, s()>>>(nk, m, jd, D(k->V), D(k->w), k->active.as<int>(), D(k->part));
+            IBP_CHECK_LAUNCH();
+            update_kernel<<<ag, kThreads, 0, s()>>>(nk, m, jd, pass, D(k->V), D(k->w), D(k->H),
+                                                    k->active.as<int>(), D(k->part));
+            IBP_CHECK_LAUNCH();
+        }
+        finish_kernel<<<R, 32, 0, s()>>>(m, jd, k->nblk, D(k->part), D(k->H), D(k->cs), D(k->sn), D(k->g),
+                                         D(k->scal), k->active.as<int>());
+        IBP_CHECK_LAUNCH();
+        normalize_kernel<<<blocks_for((long long)nk * R), 256, 0, s()>>>(nk, m, jd, R, D(k->w), D(k->scal),
+                                                                        k->active.as<int>(), D(k->V));
+        IBP_CHECK_LAUNCH();
+        advance_kernel<<<1, 1, 0, s()>>>(jd);
+        IBP_CHECK_LAUNCH();
+    }
+
+    // The captured iteration for this precision, re-captured when any size,
+    // buffer or the profiling mask differs from the last capture.
+    cudaGraphExec_t iteration_graph(int prec) {
+        const Mesh<float>& m32 = c->mesh32;
+        const Mesh<double>& m64 = c->mesh64;
+        std::vector<long long> sig = {prec, R, nk, n, m, nfree, nmb, (long long)prof_mask(),
+                                      (long long)(size_t)k->V.p, (long long)(size_t)k->w.p, (long long)(size_t)k->qop.p,
+                                      (long long)(size_t)k->psi.p, (long long)(size_t)k->H.p,
+                                      (long long)(size_t)c->psi_r.p, (long long)(size_t)c->psi_k.p,
+                                      (long long)(size_t)c->scalars.p, (long long)(size_t)c->near.col.p,
+                                      (long long)(size_t)c->near.val.p, (long long)(size_t)c->near.rowptr.p,
+                                      (long long)(size_t)a.xw, (long long)(size_t)c->bodies.free_idx.p,
+                                      (long long)(size_t)c->bodies.mb_of_free.p,
+                                      (long long)(size_t)c->bodies.free_off.p,
+                                      (long long)(size_t)(prec == IBPME_MIXED ? m32.grid.p : m64.grid.p),
+                                      (long long)(size_t)(prec == IBPME_MIXED ? m32.work.p : m64.work.p)};
+        const int gi = prec == IBPME_MIXED ? 1 : 0;
+        if (k->exec[gi] && k->sig[gi] == sig) return k->exec[gi];
+        if (k->exec[gi]) {
+            IBP_CUDA(cudaGraphExecDestroy(k->exec[gi]));
+            k->exec[gi] = nullptr;
+        }
+        // make every lazily created resource exist before capture
+        if (prec == IBPME_MIXED) c->mesh32.plans(R, s()); else c->mesh64.plans(R, s());
+        prof_capture_begin(gi);
+        const long long launches0 = launch_count();
+        cudaGraph_t graph = nullptr;
+        IBP_CUDA(cudaStreamBeginCapture(s(), cudaStreamCaptureModeThreadLocal));
+        try {
+            iterate(prec);
+        } catch (...) {
+            cudaStreamEndCapture(s(), &graph);
+            if (graph) cudaGraphDestroy(graph);
+            prof_capture_end();
+            throw;
+        }
+        IBP_CUDA(cudaStreamEndCapture(s(), &graph));
+        prof_capture_end();
+        k->nodes[gi] = launch_count() - launches0;
+        count_launch(-k->nodes[gi]);   // capturing is not launching
+        cudaGraphExec_t exec = nullptr;
+        const cudaError_t e = cudaGraphInstantiate(&exec, graph, 0);
+        cudaGraphDestroy(graph);
+        IBP_CUDA(e);
+        k->exec[gi] = exec;
+        k->sig[gi] = sig;
+        return exec;
+    }
+
+    static bool use_graphs() {
+        static const bool off = std::getenv("IBPME_NO_GRAPHS") != nullptr;
+        return !off;
     }
 
     // host copy of R doubles
@@ -508,7 +693,6 @@ struct Solver {
         IBP_CUDA(cudaMemsetAsync(dd, 0, sizeof(double) * len, s()));
         const double* res_vec = rhs;   // residual the next cycle starts from
         std::vector<double> rn = norms(rhs);
-        dim3 ag(k->nblk, R);
         for (;;) {
             std::vector<int> act(R);
             bool any = false;
@@ -525,26 +709,22 @@ struct Solver {
             IBP_CHECK_LAUNCH();
             int kk = 0;
             bool cycle_converged = false;
+            IBP_CUDA(cudaMemsetAsync(k->jdev.p, 0, sizeof(int), s()));
+            const bool graphs = use_graphs();
+            const int gi = prec == IBPME_MIXED ? 1 : 0;
+            cudaGraphExec_t exec = graphs ? iteration_graph(prec) : nullptr;
             for (int j = 0; j < m; ++j) {
-                apply(prec, D(k->V) + (size_t)j * nk, D(k->w), (long long)(m + 1) * nk);
-                ProfScope ps(ST_KRYLOV, s());
-                for (int pass = 0; pass < 2; ++pass) {   // CGS2
-                    dots_kernel<<<ag, kThreads, 0, s()>>>(nk, m, j, D(k->V), D(k->w), k->active.as<int>(),
-                                                          D(k->part));
-                    IBP_CHECK_LAUNCH();
-                    update_kernel<<<ag, kThreads, 0, s()>>>(nk, m, j, pass, D(k->V), D(k->w), D(k->H),
-                                                            k->active.as<int>(), D(k->part));
-                    IBP_CHECK_LAUNCH();
+                if (graphs) {
+                    IBP_CUDA(cudaGraphLaunch(exec, s()));
+                    count_launch(k->nodes[gi]);
+                } else {
+                    iterate(prec);
                 }
-                finish_kernel<<<R, 32, 0, s()>>>(m, j, k->nblk, D(k->part), D(k->H), D(k->cs), D(k->sn), D(k->g),
-                                                 D(k->scal), k->active.as<int>());
-                IBP_CHECK_LAUNCH();
-                normalize_kernel<<<blocks_for(len), 256, 0, s()>>>(nk, m, j, R, D(k->w), D(k->scal),
-                                                                    k->active.as<int>(), D(k->V));
-                IBP_CHECK_LAUNCH();
+                if (prec == IBPME_FP64) ++matvec64;
                 ++iters;
                 kk = j + 1;
-                std::vector<double> est = fetch(D(k->scal) + S_RES, R, S_COUNT);
+                std::vector<double> est = fetch(D(k->scal) + S_RES, R, S_COUNT);   // synchronises
+                if (graphs) prof_graph_collect(gi);
                 bool done = true;
                 for (int r = 0; r < R; ++r) {
                     if (!act[r]) continue;
@@ -562,6 +742,7 @@ struct Solver {
             if (cycle_converged || iters >= a.max_iter) return;
             // restart: residual of this operator for the next cycle
             apply(prec, dd, D(k->Ax));
+            if (prec == IBPME_FP64) ++matvec64;
             axpby_kernel<<<blocks_for(len), 256, 0, s()>>>(len, 1.0, rhs, -1.0, D(k->Ax), D(k->rc));
             IBP_CHECK_LAUNCH();
             res_vec = D(k->rc);
@@ -591,17 +772,30 @@ struct Solver {
         } else if (nk > 0) {
             IBP_CUDA(cudaMemsetAsync(k->x.p, 0, sizeof(double) * len, s()));
         }
-        // Iterative refinement on the full system.  The first residual may use the
-        // inner operator (it only seeds the first correction); every later one,
-        // and the final one, uses the FP64 operator.
+        // Iterative refinement on the full system.  Every residual uses the FP64
+        // operator; in mixed precision the corrections come from the FP32-mesh
+        // operator, whose rounding then scales with the residual, not with the
+        // (possibly much larger) potentials of the guess itself.
         const bool mixed = a.prec == IBPME_MIXED;
-        std::vector<double> res = residual(nk > 0 && mixed ? IBPME_MIXED : IBPME_FP64, true);
+        std::vector<double> res = residual(IBPME_FP64, true);
+        int fell_back = 0;
+        if (a.learned && nk > 0) {
+            // the learned guess must beat the zero guess, whose residual is |b| up to the ions' share
+            bool worse = false;
+            for (int r = 0; r < R; ++r)
+                if (!(res[r] < bnorm[r])) worse = true;
+            if (worse) {
+                IBP_CUDA(cudaMemsetAsync(k->x.p, 0, sizeof(double) * len, s()));
+                res = residual(IBPME_FP64, true);
+                fell_back = 1;
+            }
+        }
         const bool verbose = std::getenv("IBPME_VERBOSE") != nullptr;
         if (verbose)
             for (int r = 0; r < R; ++r)
                 std::fprintf(stderr, "[ibpme] start rhs %d: nk %d |b| = %.6e |r0|/|b| = %.3e\n", r, nk, bnorm[r],
                              res[r] / bnorm[r]);
-        bool res_is_fp64 = !(nk > 0 && mixed);
+        bool res_is_fp64 = true;
         int outer = 0;
         auto converged = [&]() {
             if (!res_is_fp64) return false;
@@ -645,7 +839,7 @@ struct Solver {
         st->outer = outer;
         st->matvecs_fp64 = matvec64;
         st->rel_residual = worst;
-        st->fell_back = 0;
+        st->fell_back = fell_back;
     }
 };
 
@@ -653,9 +847,25 @@ struct Solver {
 
 void solve(ibpme_ctx* c, const SolveArgs& a, ibpme_solve_stats* st) {
     if (!c->kry) c->kry = new Krylov();
-    near_build(c, a.n, a.xw, false);
-    Solver sv(c, a);
-    sv.run(st);
+    // The solve runs on the context's own non-blocking stream (graph capture is not
+    // possible on the legacy default stream), ordered after and before the caller's.
+    cudaStream_t user = c->stream;
+    IBP_CUDA(cudaEventRecord(c->ev_in, user));
+    IBP_CUDA(cudaStreamWaitEvent(c->work, c->ev_in, 0));
+    c->stream = c->work;
+    try {
+        near_build(c, a.n, a.xw, false);
+        Solver sv(c, a);
+        sv.run(st);
+    } catch (...) {
+        c->stream = user;
+        cudaEventRecord(c->ev_out, c->work);
+        cudaStreamWaitEvent(user, c->ev_out, 0);
+        throw;
+    }
+    c->stream = user;
+    IBP_CUDA(cudaEventRecord(c->ev_out, c->work));
+    IBP_CUDA(cudaStreamWaitEvent(user, c->ev_out, 0));
 }
 
 void krylov_destroy(ibpme_ctx* c) {

@@ -45,14 +45,18 @@ __device__ __forceinline__ void stencil_setup(const MeshGeom& g, const double* _
     __syncwarp();
 }
 
-template <typename T>
+// Spreading, one bead per WPB warps.  Lane (i, rsub) of warp w of the bead
+// owns stencil column i and walks the rows rsub + rows_per (w + WPB t) of the
+// P^2 (j, k) rows; NR right-hand sides share the window weights.
+template <typename T, int NR, int WPB>
 __global__ void __launch_bounds__(32 * kWarpsPerBlock)
-spread_kernel(int n, const double* __restrict__ xw, const double* __restrict__ q, int nrhs, MeshGeom g,
+spread_kernel(int n, const double* __restrict__ xw, const double* __restrict__ q, MeshGeom g,
               T* __restrict__ grid) {
     __shared__ T s_w[kWarpsPerBlock][3][kMaxP];
     __shared__ int s_idx[kWarpsPerBlock][3][kMaxP];
     const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int bead = blockIdx.x * kWarpsPerBlock + wib;
+    const int bead = (blockIdx.x * kWarpsPerBlock + wib) / WPB;
+    const int part = wib % WPB;
     if (bead >= n) return;
     stencil_setup<T, false>(g, xw, bead, lane, s_w[wib], s_idx[wib], nullptr);
     const int P = g.P;
@@ -61,79 +65,194 @@ spread_kernel(int n, const double* __restrict__ xw, const double* __restrict__ q
     if (rsub >= rows_per) return;
     const T wx = s_w[wib][0][i];
     const int ix = s_idx[wib][0][i];
-    T qc[kMaxRhs];
+    T qc[NR];
 #pragma unroll
-    for (int r = 0; r < kMaxRhs; ++r)
-        qc[r] = (r < nrhs) ? (T)(g.c * q[(size_t)r * n + bead]) * wx : (T)0;
+    for (int r = 0; r < NR; ++r) qc[r] = (T)(g.c * q[(size_t)r * n + bead]) * wx;
     const int P2 = P * P;
-    for (int row = rsub; row < P2; row += rows_per) {
-        const int k = row / P, j = row - k * P;
+    const int step = rows_per * WPB;
+    int row = rsub + rows_per * part;
+    int k = row / P, j = row - k * P;
+    const int nxy = g.N[0] * g.N[1];
+    for (; row < P2; row += step) {
         const T wyz = s_w[wib][1][j] * s_w[wib][2][k];
-        const long long off = ((long long)s_idx[wib][2][k] * g.N[1] + s_idx[wib][1][j]) * g.N[0] + ix;
+        const int off = s_idx[wib][2][k] * nxy + s_idx[wib][1][j] * g.N[0] + ix;
 #pragma unroll
-        for (int r = 0; r < kMaxRhs; ++r)
-            if (r < nrhs) atomicAdd(grid + (size_t)r * g.G + off, qc[r] * wyz);
+        for (int r = 0; r < NR; ++r) atomicAdd(grid + (size_t)r * g.G + off, qc[r] * wyz);
+        j += step;
+        while (j >= P) {
+            j -= P;
+            ++k;
+        }
     }
 }
 
-template <typename T, bool GRAD>
+// Gather (trapezoid rule, Eq. psi_wave) and, with GRAD, the gradient of the
+// window for the field; WPB warps per bead combine their partial sums in
+// shared memory.
+template <typename T, int NR, int WPB, bool GRAD>
 __global__ void __launch_bounds__(32 * kWarpsPerBlock)
-gather_kernel(int n, const double* __restrict__ xw, int nrhs, MeshGeom g, const T* __restrict__ grid,
+gather_kernel(int n, const double* __restrict__ xw, MeshGeom g, const T* __restrict__ grid,
               double* __restrict__ psi, double* __restrict__ E) {
     __shared__ T s_w[kWarpsPerBlock][3][kMaxP];
     __shared__ T s_d[kWarpsPerBlock][3][kMaxP];
     __shared__ int s_idx[kWarpsPerBlock][3][kMaxP];
+    __shared__ double s_part[kWarpsPerBlock][GRAD ? 4 * NR : NR];
     const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int bead = blockIdx.x * kWarpsPerBlock + wib;
-    if (bead >= n) return;
-    stencil_setup<T, GRAD>(g, xw, bead, lane, s_w[wib], s_idx[wib], s_d[wib]);
+    const int bead = (blockIdx.x * kWarpsPerBlock + wib) / WPB;
+    const int part = wib % WPB;
+    const bool valid = bead < n;   // no early exit: every warp must reach the block barrier below
+    if (valid) stencil_setup<T, GRAD>(g, xw, bead, lane, s_w[wib], s_idx[wib], s_d[wib]);
     const int P = g.P;
     const int rows_per = 32 / P;
     const int i = lane % P, rsub = lane / P;
-    const bool active = rsub < rows_per;
-    T acc[kMaxRhs], accy[kMaxRhs], accz[kMaxRhs];
+    const bool active = valid && rsub < rows_per;
+    T acc[NR], accy[NR], accz[NR];
 #pragma unroll
-    for (int r = 0; r < kMaxRhs; ++r) acc[r] = accy[r] = accz[r] = (T)0;
+    for (int r = 0; r < NR; ++r) acc[r] = accy[r] = accz[r] = (T)0;
     T wx = 0, dx = 0;
     if (active) {
         wx = s_w[wib][0][i];
         if (GRAD) dx = s_d[wib][0][i];
         const int ix = s_idx[wib][0][i];
         const int P2 = P * P;
-        for (int row = rsub; row < P2; row += rows_per) {
-            const int k = row / P, j = row - k * P;
+        const int step = rows_per * WPB;
+        int row = rsub + rows_per * part;
+        int k = row / P, j = row - k * P;
+        const int nxy = g.N[0] * g.N[1];
+#pragma unroll 4
+        for (; row < P2; row += step) {
             const T wyz = s_w[wib][1][j] * s_w[wib][2][k];
-            const long long off = ((long long)s_idx[wib][2][k] * g.N[1] + s_idx[wib][1][j]) * g.N[0] + ix;
+            const int off = s_idx[wib][2][k] * nxy + s_idx[wib][1][j] * g.N[0] + ix;
 #pragma unroll
-            for (int r = 0; r < kMaxRhs; ++r) {
-                if (r < nrhs) {
-                    const T v = __ldg(grid + (size_t)r * g.G + off) * wyz;
-                    acc[r] += v;
-                    if (GRAD) {
-                        accy[r] += v * s_d[wib][1][j];
-                        accz[r] += v * s_d[wib][2][k];
-                    }
+            for (int r = 0; r < NR; ++r) {
+                const T v = __ldg(grid + (size_t)r * g.G + off) * wyz;
+                acc[r] += v;
+                if (GRAD) {
+                    accy[r] += v * s_d[wib][1][j];
+                    accz[r] += v * s_d[wib][2][k];
                 }
+            }
+            j += step;
+            while (j >= P) {
+                j -= P;
+                ++k;
             }
         }
     }
 #pragma unroll
-    for (int r = 0; r < kMaxRhs; ++r) {
-        if (r >= nrhs) break;
+    for (int r = 0; r < NR; ++r) {
         const double p = warp_sum((double)(wx * acc[r]));
-        if (lane == 0) psi[(size_t)r * n + bead] = g.gather * p;
+        double ex = 0, ey = 0, ez = 0;
         if (GRAD) {
-            const double ex = warp_sum((double)(wx * dx * acc[r]));
-            const double ey = warp_sum((double)(wx * accy[r]));
-            const double ez = warp_sum((double)(wx * accz[r]));
-            if (lane == 0) {
-                double* e = E + ((size_t)r * n + bead) * 3;
-                // E = -grad psi; d/dx_alpha of the window gives (4 xi^2/eta)(x_g - x_alpha)
-                e[0] = -g.grad * ex;
-                e[1] = -g.grad * ey;
-                e[2] = -g.grad * ez;
+            ex = warp_sum((double)(wx * dx * acc[r]));
+            ey = warp_sum((double)(wx * accy[r]));
+            ez = warp_sum((double)(wx * accz[r]));
+        }
+        if (lane == 0) {
+            if (GRAD) {
+                s_part[wib][4 * r] = p;
+                s_part[wib][4 * r + 1] = ex;
+                s_part[wib][4 * r + 2] = ey;
+                s_part[wib][4 * r + 3] = ez;
+            } else {
+                s_part[wib][r] = p;
             }
         }
+    }
+    if (WPB > 1) __syncthreads();
+    if (!valid || part != 0 || lane != 0) return;
+#pragma unroll
+    for (int r = 0; r < NR; ++r) {
+        double p = 0, ex = 0, ey = 0, ez = 0;
+#pragma unroll
+        for (int w = 0; w < WPB; ++w) {
+            if (GRAD) {
+                p += s_part[wib + w][4 * r];
+                ex += s_part[wib + w][4 * r + 1];
+                ey += s_part[wib + w][4 * r + 2];
+                ez += s_part[wib + w][4 * r + 3];
+            } else {
+                p += s_part[wib + w][r];
+            }
+        }
+        psi[(size_t)r * n + bead] = g.gather * p;
+        if (GRAD) {
+            double* e = E + ((size_t)r * n + bead) * 3;
+            // E = -grad psi; d/dx_alpha of the window gives (4 xi^2/eta)(x_g - x_alpha)
+            e[0] = -g.grad * ex;
+            e[1] = -g.grad * ey;
+            e[2] = -g.grad * ez;
+        }
+    }
+}
+
+// warps per bead: enough warps to fill the GPU at small bead counts
+int warps_per_bead(int n) {
+    const long long want = 152LL * 48;   // about 48 resident warps per SM
+    if ((long long)n * 2 > want) return 1;
+    if ((long long)n * 4 > want) return 2;
+    return 4;
+}
+
+template <typename T, int NR, int WPB>
+void launch_spread(int n, const double* xw, const double* q, const MeshGeom& g, T* grid, cudaStream_t s) {
+    const int blocks = div_up((long long)n * WPB, kWarpsPerBlock);
+    spread_kernel<T, NR, WPB><<<blocks, 32 * kWarpsPerBlock, 0, s>>>(n, xw, q, g, grid);
+}
+
+template <typename T, int NR>
+void launch_spread_w(int n, const double* xw, const double* q, const MeshGeom& g, T* grid, cudaStream_t s) {
+    switch (warps_per_bead(n)) {
+        case 1: launch_spread<T, NR, 1>(n, xw, q, g, grid, s); break;
+        case 2: launch_spread<T, NR, 2>(n, xw, q, g, grid, s); break;
+        default: launch_spread<T, NR, 4>(n, xw, q, g, grid, s); break;
+    }
+}
+
+template <typename T>
+void spread_dispatch(int n, const double* xw, const double* q, int nrhs, const MeshGeom& g, T* grid,
+                     cudaStream_t s) {
+    switch (nrhs) {
+        case 1: launch_spread_w<T, 1>(n, xw, q, g, grid, s); break;
+        case 2: launch_spread_w<T, 2>(n, xw, q, g, grid, s); break;
+        case 3: launch_spread_w<T, 3>(n, xw, q, g, grid, s); break;
+        case 4: launch_spread_w<T, 4>(n, xw, q, g, grid, s); break;
+        case 5: launch_spread_w<T, 5>(n, xw, q, g, grid, s); break;
+        case 6: launch_spread_w<T, 6>(n, xw, q, g, grid, s); break;
+        case 7: launch_spread_w<T, 7>(n, xw, q, g, grid, s); break;
+        default: launch_spread_w<T, 8>(n, xw, q, g, grid, s); break;
+    }
+}
+
+template <typename T, int NR, int WPB, bool GRAD>
+void launch_gather(int n, const double* xw, const MeshGeom& g, const T* grid, double* psi, double* E,
+                   cudaStream_t s) {
+    const int blocks = div_up((long long)n * WPB, kWarpsPerBlock);
+    gather_kernel<T, NR, WPB, GRAD><<<blocks, 32 * kWarpsPerBlock, 0, s>>>(n, xw, g, grid, psi, E);
+}
+
+template <typename T, int NR, bool GRAD>
+void launch_gather_w(int n, const double* xw, const MeshGeom& g, const T* grid, double* psi, double* E,
+                     cudaStream_t s) {
+    switch (warps_per_bead(n)) {
+        case 1: launch_gather<T, NR, 1, GRAD>(n, xw, g, grid, psi, E, s); break;
+        case 2: launch_gather<T, NR, 2, GRAD>(n, xw, g, grid, psi, E, s); break;
+        default: launch_gather<T, NR, 4, GRAD>(n, xw, g, grid, psi, E, s); break;
+    }
+}
+
+template <typename T, bool GRAD>
+void gather_dispatch(int n, const double* xw, int nrhs, const MeshGeom& g, const T* grid, double* psi, double* E,
+                     cudaStream_t s) {
+    switch (nrhs) {
+        case 1: launch_gather_w<T, 1, GRAD>(n, xw, g, grid, psi, E, s); break;
+        case 2: launch_gather_w<T, 2, GRAD>(n, xw, g, grid, psi, E, s); break;
+        case 3: launch_gather_w<T, 3, GRAD>(n, xw, g, grid, psi, E, s); break;
+        case 4: launch_gather_w<T, 4, GRAD>(n, xw, g, grid, psi, E, s); break;
+        case 5: launch_gather_w<T, 5, GRAD>(n, xw, g, grid, psi, E, s); break;
+        case 6: launch_gather_w<T, 6, GRAD>(n, xw, g, grid, psi, E, s); break;
+        case 7: launch_gather_w<T, 7, GRAD>(n, xw, g, grid, psi, E, s); break;
+        default: launch_gather_w<T, 8, GRAD>(n, xw, g, grid, psi, E, s); break;
     }
 }
 
@@ -164,16 +283,17 @@ __global__ void green_kernel(MeshGeom g, double xi, double eta, double a, T* __r
     }
 }
 
+// Scaling of the half spectrum by the Green's table; blockIdx.y is the
+// right-hand side, so the table index needs no division.
 template <typename T>
-__global__ void scale_kernel(long long Gc, int nrhs, const T* __restrict__ green,
-                             typename Cplx<T>::type* __restrict__ spec) {
-    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < Gc * nrhs;
-         t += (long long)gridDim.x * blockDim.x) {
-        const T gk = green[t % Gc];
-        typename Cplx<T>::type v = spec[t];
+__global__ void scale_kernel(long long Gc, const T* __restrict__ green, typename Cplx<T>::type* __restrict__ spec) {
+    typename Cplx<T>::type* sp = spec + (size_t)blockIdx.y * Gc;
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < Gc; t += (long long)gridDim.x * blockDim.x) {
+        const T gk = green[t];
+        typename Cplx<T>::type v = sp[t];
         v.x *= gk;
         v.y *= gk;
-        spec[t] = v;
+        sp[t] = v;
     }
 }
 
@@ -249,7 +369,7 @@ void Mesh<T>::spread(int n, const double* xw, const double* q, int nrhs, cudaStr
     ProfScope ps(mesh_stage<T>(ST_SPREAD), s);
     IBP_CUDA(cudaMemsetAsync(grid.p, 0, sizeof(T) * (size_t)g.G * nrhs, s));
     if (n == 0) return;
-    spread_kernel<T><<<div_up(n, kWarpsPerBlock), 32 * kWarpsPerBlock, 0, s>>>(n, xw, q, nrhs, g, grid.as<T>());
+    spread_dispatch<T>(n, xw, q, nrhs, g, grid.as<T>(), s);
     IBP_CHECK_LAUNCH();
 }
 
@@ -267,7 +387,7 @@ void Mesh<T>::transform(int nrhs, cudaStream_t s) {
     }
     {
         ProfScope ps(mesh_stage<T>(ST_SCALE), s);
-        scale_kernel<T><<<grid_blocks(g.Gc * nrhs, 256), 256, 0, s>>>(g.Gc, nrhs, green.as<T>(), spec.as<C>());
+        scale_kernel<T><<<dim3(grid_blocks(g.Gc, 256), nrhs), 256, 0, s>>>(g.Gc, green.as<T>(), spec.as<C>());
         IBP_CHECK_LAUNCH();
     }
     ProfScope ps(mesh_stage<T>(ST_FFT_INV), s);
@@ -282,11 +402,10 @@ template <typename T>
 void Mesh<T>::gather(int n, const double* xw, int nrhs, double* psi, double* E, cudaStream_t s) {
     if (n == 0) return;
     ProfScope ps(mesh_stage<T>(ST_GATHER), s);
-    const int blocks = div_up(n, kWarpsPerBlock);
     if (E)
-        gather_kernel<T, true><<<blocks, 32 * kWarpsPerBlock, 0, s>>>(n, xw, nrhs, g, grid.as<T>(), psi, E);
+        gather_dispatch<T, true>(n, xw, nrhs, g, grid.as<T>(), psi, E, s);
     else
-        gather_kernel<T, false><<<blocks, 32 * kWarpsPerBlock, 0, s>>>(n, xw, nrhs, g, grid.as<T>(), psi, nullptr);
+        gather_dispatch<T, false>(n, xw, nrhs, g, grid.as<T>(), psi, nullptr, s);
     IBP_CHECK_LAUNCH();
 }
 
@@ -294,6 +413,7 @@ template struct Mesh<float>;
 template struct Mesh<double>;
 
 }  // namespace ibp
+
 // ---------------------------------------------------------------------------
 // Spreading for callers that cannot allocate device memory.
 //
@@ -384,11 +504,9 @@ IBP_API ibpme_status pme_spread_noalloc(const ibpme_params* params, int n, const
             noalloc_wrap_kernel<<<div_up(3LL * n, 256), 256, 0, s>>>(n, x, p.box[0], p.box[1], p.box[2], xw);
             IBP_CHECK_LAUNCH();
             if (f64)
-                spread_kernel<double><<<div_up(n, kWarpsPerBlock), 32 * kWarpsPerBlock, 0, s>>>(
-                    n, xw, q, nrhs, g, static_cast<double*>(grid_out));
+                spread_dispatch<double>(n, xw, q, nrhs, g, static_cast<double*>(grid_out), s);
             else
-                spread_kernel<float><<<div_up(n, kWarpsPerBlock), 32 * kWarpsPerBlock, 0, s>>>(
-                    n, xw, q, nrhs, g, static_cast<float*>(grid_out));
+                spread_dispatch<float>(n, xw, q, nrhs, g, static_cast<float*>(grid_out), s);
             IBP_CHECK_LAUNCH();
         }
         return IBPME_OK;

@@ -1,0 +1,534 @@
+// mlp.cu -- learned warm start for the induced-charge solve (not in the paper).
+//
+// A small fully connected network maps per-bead features (the local field
+// driving the induced charge, the bead's place on its body, the body's net
+// charge and size) to a first guess of the induced bead charge.  Everything
+// runs in this file's kernels: feature extraction, inference, and training
+// (forward, backward and Adam).  Architecture (fixed): IN -> 64 -> 64 -> 1 with
+// tanh hidden units; FP32 weights and arithmetic.
+//
+// Layout of the flat parameter vector: W1[H][IN], b1[H], W2[H][H], b2[H],
+// W3[H], b3 (row-major, out x in).
+#include "common.cuh"
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <random>
+#include <vector>
+
+struct ibpme_mlp {
+    int device = 0;
+    ibp::DevBuf params, grad, m1, m2, perm, loss;
+    long long step = 0;
+};
+
+namespace ibp {
+
+namespace {
+
+constexpr int IN = IBPME_MLP_IN;
+constexpr int H = IBPME_MLP_HIDDEN;
+constexpr int NP = IBPME_MLP_NPARAM;
+constexpr int OFF_W1 = 0, OFF_B1 = OFF_W1 + H * IN, OFF_W2 = OFF_B1 + H, OFF_B2 = OFF_W2 + H * H,
+              OFF_W3 = OFF_B2 + H, OFF_B3 = OFF_W3 + H;
+static_assert(OFF_B3 + 1 == NP, "parameter layout");
+constexpr int TILE = 128;   // samples per block in the training kernel
+constexpr int HS = H + 1;   // padded row stride of the hidden activations (no bank conflicts)
+
+// ---- inference: one thread per sample, weights broadcast from shared memory ----
+__global__ void __launch_bounds__(128) mlp_forward_kernel(int n, const float* __restrict__ P,
+                                                          const float* __restrict__ X, float* __restrict__ Y) {
+    __shared__ float w[NP];
+    for (int i = threadIdx.x; i < NP; i += blockDim.x) w[i] = P[i];
+    __syncthreads();
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= n) return;
+    float x[IN];
+#pragma unroll
+    for (int f = 0; f < IN; ++f) x[f] = X[(size_t)s * IN + f];
+    float h1[H];
+#pragma unroll
+    for (int o = 0; o < H; ++o) {
+        float a = w[OFF_B1 + o];
+#pragma unroll
+        for (int f = 0; f < IN; ++f) a += w[OFF_W1 + o * IN + f] * x[f];
+        h1[o] = tanhf(a);
+    }
+    float y = w[OFF_B3];
+    for (int o = 0; o < H; ++o) {
+        float a = w[OFF_B2 + o];
+#pragma unroll
+        for (int i = 0; i < H; ++i) a += w[OFF_W2 + o * H + i] * h1[i];
+        y += w[OFF_W3 + o] * tanhf(a);
+    }
+    Y[s] = y;
+}
+
+// ---- gradient of the mean squared error over a batch ----
+// Block of TILE threads owns TILE samples (rows idx[base .. base + TILE) of X
+// through the permutation, or rows base.. when idx is NULL).  Forward pass
+// kept in shared memory, then the backward pass as small products over the
+// tile's samples; the block's gradient is added to G.
+__global__ void __launch_bounds__(TILE) mlp_grad_kernel(int n, int base, int count, const int* __restrict__ idx,
+                                                         const float* __restrict__ P, const float* __restrict__ X,
+                                                         const float* __restrict__ T, float inv_batch,
+                                                         float* __restrict__ G, float* __restrict__ loss) {
+    extern __shared__ float sm[];
+    float* w = sm;                       // NP
+    float* xs = w + NP;                  // TILE x IN
+    float* h1 = xs + TILE * IN;          // TILE x HS (later dH1)
+    float* h2 = h1 + TILE * HS;          // TILE x HS (later dH2)
+    float* dy = h2 + TILE * HS;          // TILE
+    const int tid = threadIdx.x;
+    for (int i = tid; i < NP; i += blockDim.x) w[i] = P[i];
+    const int first = base + blockIdx.x * TILE;
+    const int s = first + tid;
+    const bool valid = tid < count - blockIdx.x * TILE && s < n;
+    const int row = valid ? (idx ? idx[s] : s) : 0;
+    for (int f = 0; f < IN; ++f) xs[tid * IN + f] = valid ? X[(size_t)row * IN + f] : 0.f;
+    __syncthreads();
+    // forward
+    for (int o = 0; o < H; ++o) {
+        float a = w[OFF_B1 + o];
+        for (int f = 0; f < IN; ++f) a += w[OFF_W1 + o * IN + f] * xs[tid * IN + f];
+        h1[tid * HS + o] = tanhf(a);
+    }
+    float y = w[OFF_B3];
+    for (int o = 0; o < H; ++o) {
+        float a = w[OFF_B2 + o];
+        for (int i = 0; i < H; ++i) a += w[OFF_W2 + o * H + i] * h1[tid * HS + i];
+        const float t = tanhf(a);
+        h2[tid * HS + o] = t;
+        y += w[OFF_W3 + o] * t;
+    }
+    const float err = valid ? y - T[row] : 0.f;
+    dy[tid] = 2.f * err * inv_batch;
+    float l = err * err * inv_batch;
+    for (int o = 16; o > 0; o >>= 1) l += __shfl_xor_sync(0xffffffffu, l, o);
+    if ((tid & 31) == 0) atomicAdd(loss, l);
+    __syncthreads();
+    // output layer: dW3[o] = sum_s dy h2[s][o], db3 = sum_s dy
+    if (tid < H) {
+        float a = 0.f;
+        for (int q = 0; q < TILE; ++q) a += dy[q] * h2[q * HS + tid];
+        atomicAdd(G + OFF_W3 + tid, a);
+    }
+    if (tid == H) {
+        float a = 0.f;
+        for (int q = 0; q < TILE; ++q) a += dy[q];
+        atomicAdd(G + OFF_B3, a);
+    }
+    __syncthreads();
+    // dH2 = dy W3 (1 - h2^2), in place
+    for (int o = 0; o < H; ++o) {
+        const float t = h2[tid * HS + o];
+        h2[tid * HS + o] = dy[tid] * w[OFF_W3 + o] * (1.f - t * t);
+    }
+    __syncthreads();
+    // dW2[o][i] = sum_s dH2[s][o] h1[s][i]; db2[o] = sum_s dH2[s][o]
+    for (int e = tid; e < H * H; e += blockDim.x) {
+        const int o = e / H, i = e % H;
+        float a = 0.f;
+        for (int q = 0; q < TILE; ++q) a += h2[q * HS + o] * h1[q * HS + i];
+        atomicAdd(G + OFF_W2 + e, a);
+    }
+    if (tid < H) {
+        float a = 0.f;
+        for (int q = 0; q < TILE; ++q) a += h2[q * HS + tid];
+        atomicAdd(G + OFF_B2 + tid, a);
+    }
+    // dH1[s][i] = (sum_o W2[o][i] dH2[s][o]) (1 - h1^2): each thread its own sample
+    float d1[H];
+    for (int i = 0; i < H; ++i) {
+        float a = 0.f;
+        for (int o = 0; o < H; ++o) a += w[OFF_W2 + o * H + i] * h2[tid * HS + o];
+        const float t = h1[tid * HS + i];
+        d1[i] = a * (1.f - t * t);
+    }
+    __syncthreads();   // every dW2 sum has read h1 before it is overwritten
+    for (int i = 0; i < H; ++i) h1[tid * HS + i] = d1[i];
+    __syncthreads();
+    // dW1[o][f] = sum_s dH1[s][o] x[s][f]; db1[o] = sum_s dH1[s][o]
+    for (int e = tid; e < H * IN; e += blockDim.x) {
+        const int o = e / IN, f = e % IN;
+        float a = 0.f;
+        for (int q = 0; q < TILE; ++q) a += h1[q * HS + o] * xs[q * IN + f];
+        atomicAdd(G + OFF_W1 + e, a);
+    }
+    if (tid < H) {
+        float a = 0.f;
+        for (int q = 0; q < TILE; ++q) a += h1[q * HS + tid];
+        atomicAdd(G + OFF_B1 + tid, a);
+    }
+}
+
+constexpr size_t kGradSmem = sizeof(float) * (NP + TILE * IN + 2 * TILE * HS + TILE);
+
+// Adam (Kingma & Ba 2015) with bias correction; clears the gradient.
+__global__ void adam_kernel(float* __restrict__ P, float* __restrict__ G, float* __restrict__ m1,
+                            float* __restrict__ m2, float lr, float b1, float b2, float c1, float c2, float eps) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= NP) return;
+    const float g = G[i];
+    const float a = b1 * m1[i] + (1.f - b1) * g;
+    const float v = b2 * m2[i] + (1.f - b2) * g * g;
+    m1[i] = a;
+    m2[i] = v;
+    P[i] -= lr * (a / c1) / (sqrtf(v / c2) + eps);
+    G[i] = 0.f;
+}
+
+void grad_launch(ibpme_mlp* m, int n, int base, int count, const int* idx, const float* X, const float* T,
+                 float inv_batch, cudaStream_t s) {
+    const int blocks = div_up(count, TILE);
+    mlp_grad_kernel<<<blocks, TILE, kGradSmem, s>>>(n, base, count, idx, m->params.as<float>(), X, T, inv_batch,
+                                                     m->grad.as<float>(), m->loss.as<float>());
+    IBP_CHECK_LAUNCH();
+}
+
+void init_params(std::vector<float>& p, unsigned long long seed) {
+    std::mt19937_64 rng(seed);
+    std::normal_distribution<double> nd(0.0, 1.0);
+    p.assign(NP, 0.f);
+    for (int i = 0; i < H * IN; ++i) p[OFF_W1 + i] = (float)(nd(rng) / std::sqrt((double)IN));
+    for (int i = 0; i < H * H; ++i) p[OFF_W2 + i] = (float)(nd(rng) / std::sqrt((double)H));
+    for (int i = 0; i < H; ++i) p[OFF_W3 + i] = (float)(nd(rng) / std::sqrt((double)H));
+}
+
+// ---- features -----------------------------------------------------------------
+// Per multi-bead body (one warp): R = mean |r_ij|, the per-bead area
+// A = 4 pi R^2 / N, and, per right-hand side, S = rms over the body of
+// |u_ij|, u = eps A E_ext with E_ext = E0 + E_fix, and the mean of psi_fix.
+__global__ void body_scale_kernel(int nb, int n, int R, const int* __restrict__ off, const double* __restrict__ rel,
+                                  const double* __restrict__ E0, const double* __restrict__ Efix,
+                                  const double* __restrict__ psifix, double eps, double* __restrict__ bs) {
+    const int b = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (b >= nb) return;
+    const int s = off[b], e = off[b + 1], N = e - s;
+    double rs = 0.0;
+    for (int j = s + lane; j < e; j += 32)
+        rs += sqrt(rel[3 * j] * rel[3 * j] + rel[3 * j + 1] * rel[3 * j + 1] + rel[3 * j + 2] * rel[3 * j + 2]);
+    rs = warp_sum(rs);
+    const double Rb = rs / N;
+    const double A = 4.0 * 3.14159265358979323846 * Rb * Rb / N;
+    for (int r = 0; r < R; ++r) {
+        double u2 = 0.0, pm = 0.0;
+        for (int j = s + lane; j < e; j += 32) {
+            const double* ef = Efix + ((size_t)r * n + j) * 3;
+            const double ux = E0[3 * r] + ef[0], uy = E0[3 * r + 1] + ef[1], uz = E0[3 * r + 2] + ef[2];
+            u2 += (ux * ux + uy * uy + uz * uz);
+            pm += psifix[(size_t)r * n + j];
+        }
+        u2 = warp_sum(u2);
+        pm = warp_sum(pm);
+        if (lane == 0) {
+            double* o = bs + ((size_t)r * nb + b) * 4;
+            o[0] = Rb;
+            o[1] = A;
+            o[2] = eps * A * sqrt(u2 / N);   // S
+            o[3] = pm / N;
+        }
+    }
+}
+
+__global__ void feature_kernel(int n, int nb, int R, const int* __restrict__ bead_body, const int* __restrict__ off,
+                               const double* __restrict__ rel, const double* __restrict__ E0,
+                               const double* __restrict__ Efix, const double* __restrict__ psifix,
+                               const double* __restrict__ Q, const double* __restrict__ bs, double eps, double a,
+                               float* __restrict__ feat) {
+    const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (t >= (long long)n * R) return;
+    const int r = (int)(t / n), j = (int)(t % n);
+    const int b = bead_body[j];
+    const int N = off[b + 1] - off[b];
+    float* f = feat + (size_t)t * IN;
+    const double* o = bs + ((size_t)r * nb + b) * 4;
+    const double Rb = o[0], A = o[1], S = o[2], pm = o[3];
+    if (N < 2 || !(S > 0.0)) {
+        for (int k = 0; k < IN; ++k) f[k] = 0.f;
+        return;
+    }
+    const double rx = rel[3 * j], ry = rel[3 * j + 1], rz = rel[3 * j + 2];
+    const double rr = sqrt(rx * rx + ry * ry + rz * rz);
+    const double nx = rr > 0 ? rx / rr : 0.0, ny = rr > 0 ? ry / rr : 0.0, nz = rr > 0 ? rz / rr : 0.0;
+    const double* ef = Efix + ((size_t)r * n + j) * 3;
+    const double ux = eps * A * (E0[3 * r] + ef[0]), uy = eps * A * (E0[3 * r + 1] + ef[1]),
+                 uz = eps * A * (E0[3 * r + 2] + ef[2]);
+    const double un = ux * nx + uy * ny + uz * nz;
+    const double tx = ux - un * nx, ty = uy - un * ny, tz = uz - un * nz;
+    const double fix = eps * A * sqrt(ef[0] * ef[0] + ef[1] * ef[1] + ef[2] * ef[2]);
+    const double qb = Q[b] / N / S;
+    f[0] = (float)(un / S);
+    f[1] = (float)(sqrt(tx * tx + ty * ty + tz * tz) / S);
+    f[2] = (float)((psifix[(size_t)r * n + j] - pm) * 4.0 * 3.14159265358979323846 * eps * a / S);
+    f[3] = (float)(qb > 10.0 ? 10.0 : (qb < -10.0 ? -10.0 : qb));
+    f[4] = (float)(Rb > 0 ? rr / Rb - 1.0 : 0.0);
+    f[5] = (float)(log((double)N) / 8.0);
+    f[6] = (float)(Rb > 0 ? 10.0 * a / Rb : 0.0);
+    f[7] = (float)(fix / S);
+}
+
+// charge q = Q/N + S y on the beads of multi-bead bodies
+__global__ void guess_from_net_kernel(int n, int nb, int R, const int* __restrict__ bead_body,
+                                      const int* __restrict__ off, const double* __restrict__ Q,
+                                      const double* __restrict__ bs, const float* __restrict__ y,
+                                      double* __restrict__ q) {
+    const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (t >= (long long)n * R) return;
+    const int r = (int)(t / n), j = (int)(t % n);
+    const int b = bead_body[j];
+    const int N = off[b + 1] - off[b];
+    const double S = bs[((size_t)r * nb + b) * 4 + 2];
+    double v = Q[b] / N;
+    if (N > 1 && S > 0.0) v += S * (double)y[t];
+    q[t] = v;
+}
+
+// restore the constraint sum_j q_ij = Q_i of every body (uniform shift)
+__global__ void project_kernel(int nb, int n, int R, const int* __restrict__ off, const double* __restrict__ Q,
+                               double* __restrict__ q) {
+    const long long wid = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (wid >= (long long)nb * R) return;
+    const int r = (int)(wid / nb), b = (int)(wid % nb);
+    const int s = off[b], e = off[b + 1];
+    double sm = 0.0;
+    for (int j = s + lane; j < e; j += 32) sm += q[(size_t)r * n + j];
+    sm = warp_sum(sm);
+    const double shift = (Q[b] - sm) / (e - s);
+    for (int j = s + lane; j < e; j += 32) q[(size_t)r * n + j] += shift;
+}
+
+__global__ void fixed_charge_kernel(int n, const int* __restrict__ bead_body, const int* __restrict__ off,
+                                    const double* __restrict__ Q, double* __restrict__ q) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n) return;
+    const int b = bead_body[j];
+    q[j] = Q[b] / (off[b + 1] - off[b]);
+}
+
+}  // namespace
+
+// Features of every bead for nrhs fields E0 [nrhs][3] (bodies already uploaded,
+// positions wrapped, context stream current).  The fixed charges -- ions and the
+// bodies' net charges spread evenly -- give psi_fix and E_fix by one PME
+// evaluation.  Also leaves the per-body scales in `scales` [nrhs][nb][4].
+void compute_features(ibpme_ctx* c, int n, const double* xw, const double* E0, int nrhs, float* feat,
+                      DevBuf& scratch, DevBuf& scales) {
+    BodyData& bd = c->bodies;
+    cudaStream_t s = c->stream;
+    double* qf = static_cast<double*>(scratch.ensure(sizeof(double) * (size_t)n * 5));
+    double* psif = qf + n;
+    double* Ef = psif + n;
+    fixed_charge_kernel<<<div_up(n, 256), 256, 0, s>>>(n, bd.bead_body.as<int>(), bd.off.as<int>(),
+                                                       bd.Q.as<double>(), qf);
+    IBP_CHECK_LAUNCH();
+    pme_apply(c, n, xw, qf, 1, c->have32 ? IBPME_MIXED : IBPME_FP64, psif, Ef, false);
+    // the fixed field does not depend on E0: broadcast it to every right-hand side
+    double* Efr = static_cast<double*>(c->E_r.ensure(sizeof(double) * 3 * (size_t)n * nrhs));
+    double* psir = static_cast<double*>(c->psi_r.ensure(sizeof(double) * (size_t)n * nrhs));
+    for (int r = 0; r < nrhs; ++r) {
+        IBP_CUDA(cudaMemcpyAsync(Efr + (size_t)r * 3 * n, Ef, sizeof(double) * 3 * n, cudaMemcpyDeviceToDevice, s));
+        IBP_CUDA(cudaMemcpyAsync(psir + (size_t)r * n, psif, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+    }
+    double* bs = static_cast<double*>(scales.ensure(sizeof(double) * 4 * (size_t)bd.nb * nrhs));
+    body_scale_kernel<<<div_up((long long)bd.nb * 32, 128), 128, 0, s>>>(bd.nb, n, nrhs, bd.off.as<int>(),
+                                                                         bd.rel.as<double>(), E0, Efr, psir, c->eps,
+                                                                         bs);
+    IBP_CHECK_LAUNCH();
+    feature_kernel<<<div_up((long long)n * nrhs, 256), 256, 0, s>>>(n, bd.nb, nrhs, bd.bead_body.as<int>(),
+                                                                    bd.off.as<int>(), bd.rel.as<double>(), E0, Efr,
+                                                                    psir, bd.Q.as<double>(), bs, c->eps, c->a, feat);
+    IBP_CHECK_LAUNCH();
+}
+
+// Learned initial charges q [nrhs][n] (constraint restored body by body).
+void learned_guess(ibpme_ctx* c, const ibpme_mlp* mlp, int n, const double* xw, const double* E0, int nrhs,
+                   double* q) {
+    DevBuf& feat = c->ml_feat;
+    DevBuf& scratch = c->ml_scratch;
+    DevBuf& scales = c->ml_scales;
+    DevBuf& y = c->ml_y;
+    BodyData& bd = c->bodies;
+    cudaStream_t s = c->stream;
+    float* f = static_cast<float*>(feat.ensure(sizeof(float) * IN * (size_t)n * nrhs));
+    compute_features(c, n, xw, E0, nrhs, f, scratch, scales);
+    float* yy = static_cast<float*>(y.ensure(sizeof(float) * (size_t)n * nrhs));
+    mlp_forward_kernel<<<div_up((long long)n * nrhs, 128), 128, 0, s>>>(n * nrhs, mlp->params.as<float>(), f, yy);
+    IBP_CHECK_LAUNCH();
+    guess_from_net_kernel<<<div_up((long long)n * nrhs, 256), 256, 0, s>>>(n, bd.nb, nrhs, bd.bead_body.as<int>(),
+                                                                           bd.off.as<int>(), bd.Q.as<double>(),
+                                                                           scales.as<double>(), yy, q);
+    IBP_CHECK_LAUNCH();
+    project_kernel<<<div_up((long long)bd.nb * nrhs * 32, 128), 128, 0, s>>>(bd.nb, n, nrhs, bd.off.as<int>(),
+                                                                             bd.Q.as<double>(), q);
+    IBP_CHECK_LAUNCH();
+}
+
+}  // namespace ibp
+
+using namespace ibp;
+
+namespace {
+
+template <typename F>
+ibpme_status mlp_guard(F&& f) {
+    try {
+        set_error("%s", "");
+        return f();
+    } catch (const Error& e) {
+        return e.status;
+    } catch (...) {
+        set_error("unexpected internal exception");
+        return IBPME_ERR_CUDA;
+    }
+}
+
+}  // namespace
+
+IBP_API ibpme_status ibpme_mlp_create(ibpme_mlp** out, unsigned long long seed) {
+    if (!out) {
+        set_error("out is NULL");
+        return IBPME_ERR_ARG;
+    }
+    *out = nullptr;
+    return mlp_guard([&]() -> ibpme_status {
+        ibpme_mlp* m = new ibpme_mlp();
+        try {
+            IBP_CUDA(cudaGetDevice(&m->device));
+            std::vector<float> p;
+            init_params(p, seed);
+            m->params.ensure(sizeof(float) * NP);
+            m->grad.ensure(sizeof(float) * NP);
+            m->m1.ensure(sizeof(float) * NP);
+            m->m2.ensure(sizeof(float) * NP);
+            m->loss.ensure(sizeof(float));
+            IBP_CUDA(cudaMemcpy(m->params.p, p.data(), sizeof(float) * NP, cudaMemcpyHostToDevice));
+            IBP_CUDA(cudaMemset(m->grad.p, 0, sizeof(float) * NP));
+            IBP_CUDA(cudaMemset(m->m1.p, 0, sizeof(float) * NP));
+            IBP_CUDA(cudaMemset(m->m2.p, 0, sizeof(float) * NP));
+            IBP_CUDA(cudaFuncSetAttribute(mlp_grad_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)kGradSmem));
+        } catch (...) {
+            delete m;
+            throw;
+        }
+        *out = m;
+        return IBPME_OK;
+    });
+}
+
+IBP_API ibpme_status ibpme_mlp_destroy(ibpme_mlp* m) {
+    delete m;
+    return IBPME_OK;
+}
+
+IBP_API ibpme_status ibpme_mlp_get(const ibpme_mlp* m, float* params) {
+    return mlp_guard([&]() -> ibpme_status {
+        if (!m || !params) fail(IBPME_ERR_ARG, "NULL argument");
+        IBP_CUDA(cudaMemcpy(params, m->params.p, sizeof(float) * NP, cudaMemcpyDefault));
+        return IBPME_OK;
+    });
+}
+
+IBP_API ibpme_status ibpme_mlp_set(ibpme_mlp* m, const float* params) {
+    return mlp_guard([&]() -> ibpme_status {
+        if (!m || !params) fail(IBPME_ERR_ARG, "NULL argument");
+        IBP_CUDA(cudaMemcpy(m->params.p, params, sizeof(float) * NP, cudaMemcpyDefault));
+        IBP_CUDA(cudaMemset(m->m1.p, 0, sizeof(float) * NP));
+        IBP_CUDA(cudaMemset(m->m2.p, 0, sizeof(float) * NP));
+        m->step = 0;
+        return IBPME_OK;
+    });
+}
+
+IBP_API ibpme_status ibpme_mlp_forward(ibpme_mlp* m, int n, const float* feat, float* out, void* cuda_stream) {
+    return mlp_guard([&]() -> ibpme_status {
+        if (!m || n < 0 || (n > 0 && (!feat || !out))) fail(IBPME_ERR_ARG, "bad argument");
+        if (n == 0) return IBPME_OK;
+        cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+        mlp_forward_kernel<<<div_up(n, 128), 128, 0, s>>>(n, m->params.as<float>(), feat, out);
+        IBP_CHECK_LAUNCH();
+        return IBPME_OK;
+    });
+}
+
+IBP_API ibpme_status ibpme_mlp_gradient(ibpme_mlp* m, int n, const float* feat, const float* target, float* grad,
+                                        float* loss, void* cuda_stream) {
+    return mlp_guard([&]() -> ibpme_status {
+        if (!m || n < 1 || !feat || !target || !grad) fail(IBPME_ERR_ARG, "bad argument");
+        cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+        IBP_CUDA(cudaMemsetAsync(m->grad.p, 0, sizeof(float) * NP, s));
+        IBP_CUDA(cudaMemsetAsync(m->loss.p, 0, sizeof(float), s));
+        grad_launch(m, n, 0, n, nullptr, feat, target, 1.0f / n, s);
+        IBP_CUDA(cudaMemcpyAsync(grad, m->grad.p, sizeof(float) * NP, cudaMemcpyDefault, s));
+        if (loss) IBP_CUDA(cudaMemcpyAsync(loss, m->loss.p, sizeof(float), cudaMemcpyDefault, s));
+        IBP_CUDA(cudaMemsetAsync(m->grad.p, 0, sizeof(float) * NP, s));
+        IBP_CUDA(cudaStreamSynchronize(s));
+        return IBPME_OK;
+    });
+}
+
+IBP_API ibpme_status ibpme_mlp_train(ibpme_mlp* m, int n, const float* feat, const float* target, int batch,
+                                     int epochs, float lr, unsigned long long seed, float* loss_out,
+                                     void* cuda_stream) {
+    return mlp_guard([&]() -> ibpme_status {
+        if (!m || n < 1 || !feat || !target || batch < 1 || epochs < 0) fail(IBPME_ERR_ARG, "bad argument");
+        cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+        int* perm = static_cast<int*>(m->perm.ensure(sizeof(int) * n));
+        std::vector<int> hp(n);
+        std::mt19937_64 rng(seed);
+        const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
+        float last = 0.f;
+        for (int ep = 0; ep < epochs; ++ep) {
+            for (int i = 0; i < n; ++i) hp[i] = i;
+            std::shuffle(hp.begin(), hp.end(), rng);
+            IBP_CUDA(cudaMemcpyAsync(perm, hp.data(), sizeof(int) * n, cudaMemcpyHostToDevice, s));
+            IBP_CUDA(cudaMemsetAsync(m->loss.p, 0, sizeof(float), s));
+            int batches = 0;
+            for (int base = 0; base < n; base += batch) {
+                const int cnt = (n - base < batch) ? n - base : batch;
+                grad_launch(m, n, base, cnt, perm, feat, target, 1.0f / cnt, s);
+                ++m->step;
+                const float c1 = 1.f - std::pow(b1, (float)m->step), c2 = 1.f - std::pow(b2, (float)m->step);
+                adam_kernel<<<div_up(NP, 256), 256, 0, s>>>(m->params.as<float>(), m->grad.as<float>(),
+                                                            m->m1.as<float>(), m->m2.as<float>(), lr, b1, b2, c1, c2,
+                                                            eps);
+                IBP_CHECK_LAUNCH();
+                ++batches;
+            }
+            float h = 0.f;
+            IBP_CUDA(cudaMemcpyAsync(&h, m->loss.p, sizeof(float), cudaMemcpyDeviceToHost, s));
+            IBP_CUDA(cudaStreamSynchronize(s));   // also keeps hp alive until the copy is done
+            last = batches ? h / batches : 0.f;
+        }
+        if (loss_out) *loss_out = last;
+        return IBPME_OK;
+    });
+}
+
+IBP_API ibpme_status ibpme_features(ibpme_ctx* c, int n, const double* x, const ibpme_bodies* bodies,
+                                    const double* E0, int nrhs, float* feat) {
+    return mlp_guard([&]() -> ibpme_status {
+        if (!c || n < 1 || !x || !bodies || !E0 || !feat || nrhs < 1 || nrhs > c->p.max_rhs)
+            fail(IBPME_ERR_ARG, "bad argument");
+        bool dev_ok = true;
+        for (const void* p : {(const void*)x, (const void*)E0, (const void*)feat, (const void*)bodies->body_offsets,
+                              (const void*)bodies->X, (const void*)bodies->Q}) {
+            cudaPointerAttributes at{};
+            if (cudaPointerGetAttributes(&at, p) != cudaSuccess ||
+                !(at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged)) {
+                cudaGetLastError();
+                dev_ok = false;
+            }
+        }
+        if (!dev_ok) fail(IBPME_ERR_ARG, "ibpme_features takes device pointers");
+        double* xw = static_cast<double*>(c->xw.ensure(sizeof(double) * 3 * n));
+        wrap_positions(c, n, x, xw);
+        bodies_upload(c, n, bodies, xw);
+        compute_features(c, n, xw, E0, nrhs, feat, c->ml_scratch, c->ml_scales);
+        return IBPME_OK;
+    });
+}

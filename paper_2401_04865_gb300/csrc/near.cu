@@ -233,28 +233,41 @@ __global__ void pair_fill_kernel(int n, const double* __restrict__ xw, PairConst
                    });
 }
 
-// psi_r[r][alpha] = (phi_self q_alpha + sum_pairs phi_r q_beta) / eps
-__global__ void near_apply_kernel(int n, int nrhs, const long long* __restrict__ rowptr, const int* __restrict__ col,
+// psi_r[r][alpha] = (phi_self q_alpha + sum_pairs phi_r q_beta) / eps.
+// One warp per row for NR right-hand sides; four independent accumulation
+// chains per lane keep several gathers of q in flight on long rows.
+template <int NR>
+__global__ void near_apply_kernel(int n, const long long* __restrict__ rowptr, const int* __restrict__ col,
                                   const double* __restrict__ val, double self, double inv_eps,
                                   const double* __restrict__ q, double* __restrict__ psi) {
     const int alpha = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (alpha >= n) return;
     const long long s = rowptr[alpha], e = rowptr[alpha + 1];
-    double acc[kMaxRhs];
+    double acc[4][NR];
 #pragma unroll
-    for (int r = 0; r < kMaxRhs; ++r) acc[r] = 0.0;
-    for (long long p = s + lane; p < e; p += 32) {
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int r = 0; r < NR; ++r) acc[u][r] = 0.0;
+    long long p = s + lane;
+    for (; p + 96 < e; p += 128) {
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int b = col[p + 32 * u];
+            const double v = val[p + 32 * u];
+#pragma unroll
+            for (int r = 0; r < NR; ++r) acc[u][r] += v * q[(size_t)r * n + b];
+        }
+    }
+    for (; p < e; p += 32) {
         const int b = col[p];
         const double v = val[p];
 #pragma unroll
-        for (int r = 0; r < kMaxRhs; ++r)
-            if (r < nrhs) acc[r] += v * q[(size_t)r * n + b];
+        for (int r = 0; r < NR; ++r) acc[0][r] += v * q[(size_t)r * n + b];
     }
 #pragma unroll
-    for (int r = 0; r < kMaxRhs; ++r) {
-        if (r >= nrhs) break;
-        const double t = warp_sum(acc[r]);
+    for (int r = 0; r < NR; ++r) {
+        const double t = warp_sum((acc[0][r] + acc[1][r]) + (acc[2][r] + acc[3][r]));
         if (lane == 0) psi[(size_t)r * n + alpha] = (t + self * q[(size_t)r * n + alpha]) * inv_eps;
     }
 }
@@ -518,8 +531,22 @@ void near_apply(ibpme_ctx* c, int n, const double* q, int nrhs, double* psi_r) {
     ProfScope ps(ST_NEAR_APPLY, c->stream);
     NearList& nl = c->near;
     const PairConst k = make_const(c);
-    near_apply_kernel<<<div_up((long long)n * 32, 128), 128, 0, c->stream>>>(
-        n, nrhs, nl.rowptr.as<long long>(), nl.col.as<int>(), nl.val.as<double>(), k.self, 1.0 / c->eps, q, psi_r);
+    const int blocks = div_up((long long)n * 32, 128);
+    const long long* rp = nl.rowptr.as<long long>();
+    const int* cl = nl.col.as<int>();
+    const double* vl = nl.val.as<double>();
+    const double ie = 1.0 / c->eps;
+    cudaStream_t s = c->stream;
+    switch (nrhs) {
+        case 1: near_apply_kernel<1><<<blocks, 128, 0, s>>>(n, rp, cl, vl, k.self, ie, q, psi_r); break;
+        case 2: near_apply_kernel<2><<<blocks, 128, 0, s>>>(n, rp, cl, vl, k.self, ie, q, psi_r); break;
+        case 3: near_apply_kernel<3><<<blocks, 128, 0, s>>>(n, rp, cl, vl, k.self, ie, q, psi_r); break;
+        case 4: near_apply_kernel<4><<<blocks, 128, 0, s>>>(n, rp, cl, vl, k.self, ie, q, psi_r); break;
+        case 5: near_apply_kernel<5><<<blocks, 128, 0, s>>>(n, rp, cl, vl, k.self, ie, q, psi_r); break;
+        case 6: near_apply_kernel<6><<<blocks, 128, 0, s>>>(n, rp, cl, vl, k.self, ie, q, psi_r); break;
+        case 7: near_apply_kernel<7><<<blocks, 128, 0, s>>>(n, rp, cl, vl, k.self, ie, q, psi_r); break;
+        default: near_apply_kernel<8><<<blocks, 128, 0, s>>>(n, rp, cl, vl, k.self, ie, q, psi_r); break;
+    }
     IBP_CHECK_LAUNCH();
 }
 

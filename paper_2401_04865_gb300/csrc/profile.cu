@@ -7,6 +7,8 @@
 #include "common.cuh"
 
 #include <atomic>
+#include <cstdio>
+#include <cstdlib>
 #include <mutex>
 #include <vector>
 
@@ -19,12 +21,15 @@ std::atomic<long long> g_launches{0};
 struct Rec {
     int stage;
     cudaEvent_t a, b;
+    int gid;   // -1: ordinary launch; >= 0: event nodes of captured graph gid
 };
 
 struct Profiler {
     std::mutex mu;
     unsigned mask = 0;
+    int capturing = -1;            // graph id being captured, -1 if none
     std::vector<Rec> recs;
+    std::vector<Rec> graph_recs;   // event pairs owned by captured graphs
     std::vector<cudaEvent_t> pool;
     double total[ST_COUNT] = {};
     long long count[ST_COUNT] = {};
@@ -64,15 +69,18 @@ const char* kStageNames[ST_COUNT] = {"near_build", "near_apply", "spread", "fft_
 
 }  // namespace
 
-void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+void count_launch(long long k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
+long long launch_count() { return g_launches.load(std::memory_order_relaxed); }
 
 ProfScope::ProfScope(int st, cudaStream_t strm) : stage(st), s(strm), on(false) {
     Profiler& p = prof();
     if (!(p.mask & (1u << st))) return;
     std::lock_guard<std::mutex> lk(p.mu);
-    Rec r{st, p.take(), p.take()};
-    IBP_CUDA(cudaEventRecord(r.a, s));
-    p.recs.push_back(r);
+    Rec r{st, p.take(), p.take(), p.capturing};
+    // inside a stream capture an ordinary record only becomes a graph edge; an
+    // external record becomes an event node that every replay re-records
+    IBP_CUDA(cudaEventRecordWithFlags(r.a, s, r.gid >= 0 ? cudaEventRecordExternal : cudaEventRecordDefault));
+    (r.gid >= 0 ? p.graph_recs : p.recs).push_back(r);
     on = true;
 }
 
@@ -80,11 +88,59 @@ ProfScope::~ProfScope() {
     if (!on) return;
     Profiler& p = prof();
     std::lock_guard<std::mutex> lk(p.mu);
-    for (auto it = p.recs.rbegin(); it != p.recs.rend(); ++it)
+    std::vector<Rec>& v = p.capturing >= 0 ? p.graph_recs : p.recs;
+    for (auto it = v.rbegin(); it != v.rend(); ++it)
         if (it->stage == stage) {
-            cudaEventRecord(it->b, s);
+            cudaEventRecordWithFlags(it->b, s, it->gid >= 0 ? cudaEventRecordExternal : cudaEventRecordDefault);
             break;
         }
+}
+
+unsigned prof_mask() {
+    Profiler& p = prof();
+    std::lock_guard<std::mutex> lk(p.mu);
+    return p.mask;
+}
+
+void prof_capture_begin(int gid) {
+    Profiler& p = prof();
+    std::lock_guard<std::mutex> lk(p.mu);
+    // a re-capture replaces the graph's previous event nodes
+    for (auto it = p.graph_recs.begin(); it != p.graph_recs.end();) {
+        if (it->gid == gid) {
+            p.pool.push_back(it->a);
+            p.pool.push_back(it->b);
+            it = p.graph_recs.erase(it);
+        } else {
+            ++it;
+        }
+    }
+    p.capturing = gid;
+}
+
+void prof_capture_end() {
+    Profiler& p = prof();
+    std::lock_guard<std::mutex> lk(p.mu);
+    p.capturing = -1;
+}
+
+void prof_graph_collect(int gid) {
+    Profiler& p = prof();
+    std::lock_guard<std::mutex> lk(p.mu);
+    for (const Rec& r : p.graph_recs) {
+        if (r.gid != gid || !(p.mask & (1u << r.stage))) continue;
+        float ms = 0.f;
+        const cudaError_t e = cudaEventElapsedTime(&ms, r.a, r.b);
+        if (e == cudaSuccess) {
+            p.total[r.stage] += ms;
+            p.count[r.stage] += 1;
+        } else {
+            cudaGetLastError();   // a failed query must not surface as a later launch error
+            if (std::getenv("IBPME_VERBOSE"))
+                std::fprintf(stderr, "[ibpme] graph event timing failed for stage %d: %s\n", r.stage,
+                             cudaGetErrorString(e));
+        }
+    }
 }
 
 }  // namespace ibp
