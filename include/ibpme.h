@@ -145,6 +145,7 @@ typedef struct {
     double rel_residual;    /* final ||b - A u||_2 / ||b||_2 with the FP64 operator, worst RHS */
     double time_ms;         /* wall time of the call */
     int fell_back;          /* 1 if the learned guess was rejected for the zero guess */
+    double init_rel_residual;   /* ||b - A u0|| / ||b|| of the initial guess actually used (FP64 operator) */
 } ibpme_solve_stats;
 
 /* Induced-charge solve, Sec. III.B Eq. saddle:
@@ -241,9 +242,11 @@ ibpme_status ibpme_mlp_gradient(ibpme_mlp* mlp, int n, const float* feat, const 
 ibpme_status ibpme_mlp_train(ibpme_mlp* mlp, int n, const float* feat, const float* target, int batch, int epochs,
                              float lr, unsigned long long seed, float* loss_out, void* cuda_stream);
 /* The features above for every bead and field: feat [nrhs][n][IBPME_MLP_IN]
- * (zeros for single-bead bodies); device pointers only. */
+ * (zeros for single-bead bodies).  If q [nrhs][n] (converged charges) and target
+ * [nrhs][n] are given, also the training targets y = (q - Q/N) / S (0 on
+ * single-bead bodies).  Device pointers only. */
 ibpme_status ibpme_features(ibpme_ctx* ctx, int n, const double* x, const ibpme_bodies* bodies, const double* E0,
-                            int nrhs, float* feat);
+                            int nrhs, float* feat, const double* q, float* target);
 
 /* ---- Spreading without device allocation (no counterpart in the paper) ----
  *

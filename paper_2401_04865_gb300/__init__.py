@@ -50,7 +50,7 @@ class ibpme_solve_opts(ctypes.Structure):
 
 class ibpme_solve_stats(ctypes.Structure):
     _fields_ = [("iters", _i), ("outer", _i), ("matvecs_fp64", _i), ("rel_residual", _d), ("time_ms", _d),
-                ("fell_back", _i)]
+                ("fell_back", _i), ("init_rel_residual", _d)]
 
 
 class ibpme_bd_params(ctypes.Structure):
@@ -81,6 +81,14 @@ SIGNATURES = {
     "ibpme_bd_step": (_i, [_p, _i, _p, ctypes.POINTER(ibpme_bodies), _p, ctypes.POINTER(ibpme_bd_params),
                            _p, _p]),
     "pme_spread_noalloc": (_i, [ctypes.POINTER(ibpme_params), _i, _p, _p, _i, _p, _p]),
+    "ibpme_mlp_create": (_i, [ctypes.POINTER(_p), ctypes.c_ulonglong]),
+    "ibpme_mlp_destroy": (_i, [_p]),
+    "ibpme_mlp_get": (_i, [_p, _p]),
+    "ibpme_mlp_set": (_i, [_p, _p]),
+    "ibpme_mlp_forward": (_i, [_p, _i, _p, _p, _p]),
+    "ibpme_mlp_gradient": (_i, [_p, _i, _p, _p, _p, _p, _p]),
+    "ibpme_mlp_train": (_i, [_p, _i, _p, _p, _i, _i, ctypes.c_float, ctypes.c_ulonglong, _p, _p]),
+    "ibpme_features": (_i, [_p, _i, _p, ctypes.POINTER(ibpme_bodies), _p, _i, _p, _p, _p]),
     "ibpme_kernel_launches": (ctypes.c_longlong, []),
     "ibpme_profile": (_i, [ctypes.c_uint]),
     "ibpme_profile_read": (_i, [_i, _p, _p]),
@@ -200,6 +208,51 @@ def pme_spread(ctx, n, x, q, nrhs, grid_out=None):
 
 
 IBPME_NOALLOC_MAX_BEADS = 262144
+IBPME_MLP_IN = 8
+IBPME_MLP_HIDDEN = 64
+IBPME_MLP_NPARAM = 64 * 8 + 64 + 64 * 64 + 64 + 64 + 1
+
+
+def ibpme_mlp_create(seed=0):
+    m = _p()
+    _check(load().ibpme_mlp_create(ctypes.byref(m), int(seed)), "ibpme_mlp_create")
+    return m
+
+
+def ibpme_mlp_destroy(m):
+    return _check(load().ibpme_mlp_destroy(m), "ibpme_mlp_destroy")
+
+
+def ibpme_mlp_get(m, params):
+    return _check(load().ibpme_mlp_get(m, ptr(params, np.float32)), "ibpme_mlp_get")
+
+
+def ibpme_mlp_set(m, params):
+    return _check(load().ibpme_mlp_set(m, ptr(params, np.float32)), "ibpme_mlp_set")
+
+
+def ibpme_mlp_forward(m, n, feat, y, stream=None):
+    return _check(load().ibpme_mlp_forward(m, int(n), ptr(feat, np.float32), ptr(y, np.float32),
+                                           _stream_handle(stream)), "ibpme_mlp_forward")
+
+
+def ibpme_mlp_gradient(m, n, feat, target, grad, loss=None, stream=None):
+    return _check(load().ibpme_mlp_gradient(m, int(n), ptr(feat, np.float32), ptr(target, np.float32),
+                                            ptr(grad, np.float32), ptr(loss, np.float32), _stream_handle(stream)),
+                  "ibpme_mlp_gradient")
+
+
+def ibpme_mlp_train(m, n, feat, target, batch=4096, epochs=1, lr=1e-3, seed=0, stream=None):
+    loss = np.zeros(1, dtype=np.float32)
+    _check(load().ibpme_mlp_train(m, int(n), ptr(feat, np.float32), ptr(target, np.float32), int(batch),
+                                  int(epochs), float(lr), int(seed), ptr(loss, np.float32), _stream_handle(stream)),
+           "ibpme_mlp_train")
+    return float(loss[0])
+
+
+def ibpme_features(ctx, n, x, bodies: "Bodies", E0, nrhs, feat, q=None, target=None):
+    return _check(load().ibpme_features(ctx, int(n), ptr(x), ctypes.byref(bodies.c), ptr(E0), int(nrhs),
+                                        ptr(feat, np.float32), ptr(q), ptr(target, np.float32)), "ibpme_features")
 
 
 def pme_spread_noalloc(params: ibpme_params, n, x, q, nrhs, grid_out, stream=None):
@@ -221,8 +274,9 @@ def pme_field(ctx, n, x, q, nrhs, psi, E=None):
     return _check(load().pme_field(ctx, int(n), ptr(x), ptr(q), int(nrhs), ptr(psi), ptr(E)), "pme_field")
 
 
-def make_opts(rtol=1e-6, restart=50, max_iter=3000, guess=IBPME_GUESS_ZERO, precision=-1) -> ibpme_solve_opts:
-    return ibpme_solve_opts(float(rtol), int(restart), int(max_iter), int(guess), None, int(precision))
+def make_opts(rtol=1e-6, restart=50, max_iter=3000, guess=IBPME_GUESS_ZERO, precision=-1, mlp=None) -> ibpme_solve_opts:
+    handle = mlp.value if isinstance(mlp, ctypes.c_void_p) else mlp
+    return ibpme_solve_opts(float(rtol), int(restart), int(max_iter), int(guess), handle, int(precision))
 
 
 def induced_charge_solve(ctx, n, x, bodies: Bodies, E0, nrhs, opts: ibpme_solve_opts | None, q_out, psi_out=None,

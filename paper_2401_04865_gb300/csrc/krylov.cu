@@ -790,6 +790,8 @@ struct Solver {
                 fell_back = 1;
             }
         }
+        double init_worst = 0.0;
+        for (int r = 0; r < R; ++r) init_worst = std::max(init_worst, bnorm[r] > 0 ? res[r] / bnorm[r] : res[r]);
         const bool verbose = std::getenv("IBPME_VERBOSE") != nullptr;
         if (verbose)
             for (int r = 0; r < R; ++r)
@@ -840,6 +842,7 @@ struct Solver {
         st->matvecs_fp64 = matvec64;
         st->rel_residual = worst;
         st->fell_back = fell_back;
+        st->init_rel_residual = init_worst;
     }
 };
 

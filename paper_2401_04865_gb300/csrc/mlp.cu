@@ -270,6 +270,19 @@ __global__ void feature_kernel(int n, int nb, int R, const int* __restrict__ bea
     f[7] = (float)(fix / S);
 }
 
+// training target y = (q - Q/N) / S on beads of multi-bead bodies (0 elsewhere)
+__global__ void target_kernel(int n, int nb, int R, const int* __restrict__ bead_body, const int* __restrict__ off,
+                              const double* __restrict__ Q, const double* __restrict__ bs,
+                              const double* __restrict__ q, float* __restrict__ y) {
+    const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (t >= (long long)n * R) return;
+    const int r = (int)(t / n), j = (int)(t % n);
+    const int b = bead_body[j];
+    const int N = off[b + 1] - off[b];
+    const double S = bs[((size_t)r * nb + b) * 4 + 2];
+    y[t] = (N > 1 && S > 0.0) ? (float)((q[t] - Q[b] / N) / S) : 0.f;
+}
+
 // charge q = Q/N + S y on the beads of multi-bead bodies
 __global__ void guess_from_net_kernel(int n, int nb, int R, const int* __restrict__ bead_body,
                                       const int* __restrict__ off, const double* __restrict__ Q,
@@ -510,13 +523,14 @@ IBP_API ibpme_status ibpme_mlp_train(ibpme_mlp* m, int n, const float* feat, con
 }
 
 IBP_API ibpme_status ibpme_features(ibpme_ctx* c, int n, const double* x, const ibpme_bodies* bodies,
-                                    const double* E0, int nrhs, float* feat) {
+                                    const double* E0, int nrhs, float* feat, const double* q, float* target) {
     return mlp_guard([&]() -> ibpme_status {
         if (!c || n < 1 || !x || !bodies || !E0 || !feat || nrhs < 1 || nrhs > c->p.max_rhs)
             fail(IBPME_ERR_ARG, "bad argument");
         bool dev_ok = true;
         for (const void* p : {(const void*)x, (const void*)E0, (const void*)feat, (const void*)bodies->body_offsets,
-                              (const void*)bodies->X, (const void*)bodies->Q}) {
+                              (const void*)bodies->X, (const void*)bodies->Q, (const void*)q, (const void*)target}) {
+            if (!p) continue;
             cudaPointerAttributes at{};
             if (cudaPointerGetAttributes(&at, p) != cudaSuccess ||
                 !(at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged)) {
@@ -529,6 +543,13 @@ IBP_API ibpme_status ibpme_features(ibpme_ctx* c, int n, const double* x, const 
         wrap_positions(c, n, x, xw);
         bodies_upload(c, n, bodies, xw);
         compute_features(c, n, xw, E0, nrhs, feat, c->ml_scratch, c->ml_scales);
+        if (q && target) {
+            const BodyData& bd = c->bodies;
+            target_kernel<<<div_up((long long)n * nrhs, 256), 256, 0, c->stream>>>(
+                n, bd.nb, nrhs, bd.bead_body.as<int>(), bd.off.as<int>(), bd.Q.as<double>(), c->ml_scales.as<double>(),
+                q, target);
+            IBP_CHECK_LAUNCH();
+        }
         return IBPME_OK;
     });
 }

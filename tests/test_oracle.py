@@ -358,3 +358,20 @@ def test_bd_noise_variance():
     var = 2 * 1.5 * 1e-3 / 2.0
     assert abs(d.mean()) < 5 * math.sqrt(var / d.size)
     assert abs(d.var() / var - 1) < 5 * math.sqrt(2 / d.size)
+
+
+def test_mlp_reference_gradient_by_finite_differences():
+    """The oracle network's back-propagated gradient equals central differences of its loss."""
+    from oracle import mlp_ref as M
+    rng = np.random.default_rng(4)
+    p = rng.normal(size=M.NPARAM) * 0.3
+    X = rng.normal(size=(40, M.IN))
+    T = rng.normal(size=40)
+    L, g = M.loss_and_grad(p, X, T)
+    assert abs(L - np.mean((M.forward(p, X) - T) ** 2)) < 1e-14
+    for i in rng.choice(M.NPARAM, size=60, replace=False).tolist() + [M.NPARAM - 1, 0]:
+        h = 1e-6
+        pp = p.copy(); pp[i] += h
+        pm = p.copy(); pm[i] -= h
+        fd = (M.loss_and_grad(pp, X, T)[0] - M.loss_and_grad(pm, X, T)[0]) / (2 * h)
+        assert abs(fd - g[i]) < 1e-7 * max(1.0, abs(g[i]))
