@@ -166,6 +166,30 @@ ibpme_status induced_charge_solve(ibpme_ctx* ctx, int n, const double* x, const 
                                   double* q_out, double* psi_out, double* S_out,
                                   ibpme_solve_stats* stats);
 
+/* Batched configurations: n_configs independent systems of Eq. saddle solved in
+ * one call (not in the paper, which solves one system at a time; its
+ * polarizability tensors of Sec. IV need three field directions per shape).
+ * Configuration k owns the bodies cfg_bodies[k] .. cfg_bodies[k+1]-1 and hence a
+ * contiguous range of beads; each lives in its own periodic copy of the context's
+ * box with the context's bead radius and permittivity.  Beads of different
+ * configurations never interact: no real-space pairs, separate mesh channels,
+ * separate k = 0 sums.  Every PME evaluation serves all configurations and all
+ * right-hand sides at once (nrhs * n_configs mesh channels, one batched FFT),
+ * and each (configuration, right-hand side) pair is its own GMRES system with
+ * its own Hessenberg matrix and convergence test.
+ *   cfg_bodies  HOST int32 [n_configs + 1], cfg_bodies[0] = 0, cfg_bodies[n_configs]
+ *               = bodies->n_bodies, strictly increasing (no empty configuration)
+ *   E0          [nrhs][3], the same fields for every configuration
+ *   q_out, psi_out, S_out  as for induced_charge_solve over all n beads / N_b bodies
+ *   stats       [n_configs] or NULL: per configuration, the worst right-hand side;
+ *               iteration counts are those of the common loop
+ * guess = IBPME_GUESS_LEARNED is not accepted here (IBPME_ERR_ARG).
+ * Returns IBPME_ERR_NOT_CONVERGED if any configuration misses rtol. */
+ibpme_status induced_charge_solve_batch(ibpme_ctx* ctx, int n, const double* x, const ibpme_bodies* bodies,
+                                        int n_configs, const int* cfg_bodies, const double* E0, int nrhs,
+                                        const ibpme_solve_opts* opts, double* q_out, double* psi_out,
+                                        double* S_out, ibpme_solve_stats* stats);
+
 /* Forces and torques, Sec. III.C:
  *   f_alpha = q_alpha E0 - 1/2 (grad_alpha M) : q q = q_alpha (E0 + E_alpha)   (Eq. beadforce)
  *   F_i = sum_j f_ij,  L_i = sum_j r_ij x f_ij

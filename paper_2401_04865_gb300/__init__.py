@@ -77,6 +77,8 @@ SIGNATURES = {
     "induced_charge_solve": (_i, [_p, _i, _p, ctypes.POINTER(ibpme_bodies), _p, _i,
                                   ctypes.POINTER(ibpme_solve_opts), _p, _p, _p,
                                   ctypes.POINTER(ibpme_solve_stats)]),
+    "induced_charge_solve_batch": (_i, [_p, _i, _p, ctypes.POINTER(ibpme_bodies), _i, _p, _p, _i,
+                                        ctypes.POINTER(ibpme_solve_opts), _p, _p, _p, _p]),
     "body_force_torque": (_i, [_p, _i, _p, _p, ctypes.POINTER(ibpme_bodies), _p, _p, _p, _p, _p]),
     "ibpme_bd_step": (_i, [_p, _i, _p, ctypes.POINTER(ibpme_bodies), _p, ctypes.POINTER(ibpme_bd_params),
                            _p, _p]),
@@ -288,6 +290,20 @@ def induced_charge_solve(ctx, n, x, bodies: Bodies, E0, nrhs, opts: ibpme_solve_
                                          ptr(S_out), ctypes.byref(st))
     _check(status, "induced_charge_solve", ok=(IBPME_OK, IBPME_ERR_NOT_CONVERGED))
     return status, st
+
+
+def induced_charge_solve_batch(ctx, n, x, bodies: Bodies, cfg_bodies, E0, nrhs, opts: ibpme_solve_opts | None,
+                               q_out, psi_out=None, S_out=None):
+    """Independent configurations (bodies cfg_bodies[k]..cfg_bodies[k+1]-1) in one call.
+    Returns (status, [stats per configuration]); raises like induced_charge_solve."""
+    cb = np.ascontiguousarray(np.asarray(cfg_bodies, dtype=np.int32))
+    ncfg = int(cb.size) - 1
+    st = (ibpme_solve_stats * max(ncfg, 1))()
+    status = load().induced_charge_solve_batch(ctx, int(n), ptr(x), ctypes.byref(bodies.c), ncfg, cb.ctypes.data,
+                                               ptr(E0), int(nrhs), ctypes.byref(opts) if opts is not None else None,
+                                               ptr(q_out), ptr(psi_out), ptr(S_out), st)
+    _check(status, "induced_charge_solve_batch", ok=(IBPME_OK, IBPME_ERR_NOT_CONVERGED))
+    return status, list(st)[:ncfg]
 
 
 def body_force_torque(ctx, n, x, q, bodies: Bodies, E0, f_bead, F, L, U=None):

@@ -2,6 +2,7 @@
 // staging of host arrays, and the entry points declared in include/ibpme.h.
 #include "common.cuh"
 
+#include <algorithm>
 #include <chrono>
 #include <cmath>
 #include <cstdarg>
@@ -125,22 +126,48 @@ __global__ void add_kernel(long long m, const double* __restrict__ a, const doub
     if (i < m) out[i] = a[i] + b[i];
 }
 
-// qsum[r] += sum of the charges of right-hand side r
-__global__ void qsum_kernel(int n, const double* __restrict__ q, double* __restrict__ qsum) {
+// qsum[cfg * nrhs + r] += sum of the charges of right-hand side r in configuration cfg
+__global__ void qsum_kernel(int n, int nrhs, const double* __restrict__ q, const int* __restrict__ bcfg,
+                            double* __restrict__ qsum) {
     const int r = blockIdx.y;
-    double acc = 0.0;
-    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x)
-        acc += q[(size_t)r * n + t];
-    acc = warp_sum(acc);
-    if ((threadIdx.x & 31) == 0) atomicAdd(qsum + r, acc);
+    if (!bcfg) {
+        double acc = 0.0;
+        for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n;
+             t += (long long)gridDim.x * blockDim.x)
+            acc += q[(size_t)r * n + t];
+        acc = warp_sum(acc);
+        if ((threadIdx.x & 31) == 0) atomicAdd(qsum + r, acc);
+        return;
+    }
+    // configurations are contiguous bead ranges: a warp whose beads share one
+    // configuration adds once, a warp on a boundary adds per bead
+    const int lane = threadIdx.x & 31;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long w0 = blockIdx.x * (long long)blockDim.x + (threadIdx.x & ~31); w0 < n; w0 += stride) {
+        const long long t = w0 + lane;
+        const bool ok = t < n;
+        const int cf = ok ? bcfg[t] : -1;
+        double v = ok ? q[(size_t)r * n + t] : 0.0;
+        const int c0 = __shfl_sync(0xffffffffu, cf, 0);
+        if (__all_sync(0xffffffffu, !ok || cf == c0)) {
+            v = warp_sum(v);
+            if (lane == 0) atomicAdd(qsum + (size_t)c0 * nrhs + r, v);
+        } else if (ok) {
+            atomicAdd(qsum + (size_t)cf * nrhs + r, v);
+        }
+    }
 }
 
 // psi = psi_real + psi_wave - k0 * sum(q): the real-space image sum carries the
-// k = 0 Fourier mode 1/(4 xi^2 V eps) that M (Sec. II) excludes.
-__global__ void combine_kernel(long long m, int n, const double* __restrict__ a, const double* __restrict__ b,
-                               const double* __restrict__ qsum, double k0, double* __restrict__ out) {
+// k = 0 Fourier mode 1/(4 xi^2 V eps) that M (Sec. II) excludes (per configuration).
+__global__ void combine_kernel(long long m, int n, int nrhs, const double* __restrict__ a,
+                               const double* __restrict__ b, const double* __restrict__ qsum,
+                               const int* __restrict__ bcfg, double k0, double* __restrict__ out) {
     const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (i < m) out[i] = a[i] + b[i] - k0 * qsum[i / n];
+    if (i >= m) return;
+    const int r = (int)(i / n);
+    const int cfg = bcfg ? bcfg[i - (long long)r * n] : 0;
+    out[i] = a[i] + b[i] - k0 * qsum[(size_t)cfg * nrhs + r];
 }
 
 bool good_fft_size(int n) {
@@ -257,24 +284,27 @@ void pme_apply(ibpme_ctx* c, int n, const double* xw, const double* q, int nrhs,
     }
     near_apply(c, n, q, nrhs, pr);
     if (E) near_field(c, n, xw, q, nrhs, er);
+    const int ch = nrhs * c->ncfg;
     if (prec == IBPME_MIXED) {
         if (!c->have32) fail(IBPME_ERR_ARG, "mixed precision needs a context created with IBPME_MIXED");
-        c->mesh32.spread(n, xw, q, nrhs, c->stream);
-        c->mesh32.transform(nrhs, c->stream);
-        c->mesh32.gather(n, xw, nrhs, pk, ek, c->stream);
+        c->mesh32.spread(n, xw, q, nrhs, c->bcfg, c->ncfg, c->stream);
+        c->mesh32.transform(ch, c->stream);
+        c->mesh32.gather(n, xw, nrhs, c->bcfg, pk, ek, c->stream);
     } else {
-        c->mesh64.spread(n, xw, q, nrhs, c->stream);
-        c->mesh64.transform(nrhs, c->stream);
-        c->mesh64.gather(n, xw, nrhs, pk, ek, c->stream);
+        c->mesh64.spread(n, xw, q, nrhs, c->bcfg, c->ncfg, c->stream);
+        c->mesh64.transform(ch, c->stream);
+        c->mesh64.gather(n, xw, nrhs, c->bcfg, pk, ek, c->stream);
     }
     if (m) {
-        double* qsum = static_cast<double*>(c->scalars.ensure(sizeof(double) * kMaxRhs));
-        IBP_CUDA(cudaMemsetAsync(qsum, 0, sizeof(double) * nrhs, c->stream));
-        qsum_kernel<<<dim3(div_up(n, 256) < 64 ? div_up(n, 256) : 64, nrhs), 256, 0, c->stream>>>(n, q, qsum);
+        double* qsum = static_cast<double*>(c->scalars.ensure(sizeof(double) * (size_t)ch));
+        IBP_CUDA(cudaMemsetAsync(qsum, 0, sizeof(double) * ch, c->stream));
+        qsum_kernel<<<dim3(div_up(n, 256) < 64 ? div_up(n, 256) : 64, nrhs), 256, 0, c->stream>>>(n, nrhs, q,
+                                                                                                c->bcfg, qsum);
         IBP_CHECK_LAUNCH();
         const double V = c->p.box[0] * c->p.box[1] * c->p.box[2];
         const double k0 = 1.0 / (4.0 * c->xi * c->xi * V * c->eps);
-        combine_kernel<<<div_up((long long)m, 256), 256, 0, c->stream>>>((long long)m, n, pr, pk, qsum, k0, psi);
+        combine_kernel<<<div_up((long long)m, 256), 256, 0, c->stream>>>((long long)m, n, nrhs, pr, pk, qsum,
+                                                                         c->bcfg, k0, psi);
         IBP_CHECK_LAUNCH();
         if (E) {
             add_kernel<<<div_up(3LL * m, 256), 256, 0, c->stream>>>(3LL * (long long)m, er, ek, E);
@@ -381,9 +411,9 @@ IBP_API ibpme_status pme_spread(ibpme_ctx* c, int n, const double* x, const doub
         const bool mixed = c->p.precision == IBPME_MIXED;
         const size_t gb = (mixed ? sizeof(float) : sizeof(double)) * (size_t)c->geom.G * nrhs;
         if (mixed)
-            c->mesh32.spread(n, xw, dq, nrhs, c->stream);
+            c->mesh32.spread(n, xw, dq, nrhs, nullptr, 1, c->stream);
         else
-            c->mesh64.spread(n, xw, dq, nrhs, c->stream);
+            c->mesh64.spread(n, xw, dq, nrhs, nullptr, 1, c->stream);
         if (grid_out) {
             const void* src = mixed ? c->mesh32.grid.p : c->mesh64.grid.p;
             const cudaMemcpyKind kind = is_device_ptr(grid_out) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
@@ -425,7 +455,8 @@ struct BodiesDev {
 };
 
 // Stages the body arrays and uploads the bookkeeping; returns the device-side view.
-void prepare_bodies(ibpme_ctx* c, int n, const ibpme_bodies* bodies, const double* xw) {
+void prepare_bodies(ibpme_ctx* c, int n, const ibpme_bodies* bodies, const double* xw, int ncfg = 1,
+                    const int* cfg_bodies = nullptr) {
     if (!bodies) fail(IBPME_ERR_ARG, "bodies is NULL");
     const int nb = bodies->n_bodies;
     if (nb < 1) fail(IBPME_ERR_ARG, "n_bodies must be >= 1");
@@ -435,7 +466,93 @@ void prepare_bodies(ibpme_ctx* c, int n, const ibpme_bodies* bodies, const doubl
     d.body_offsets = static_cast<const int*>(stage_in(c, bodies->body_offsets, sizeof(int) * (nb + 1), c->st_off));
     d.X = static_cast<const double*>(stage_in(c, bodies->X, sizeof(double) * 3 * nb, c->st_X));
     d.Q = static_cast<const double*>(stage_in(c, bodies->Q, sizeof(double) * nb, c->st_Q));
-    bodies_upload(c, n, &d, xw);
+    bodies_upload(c, n, &d, xw, ncfg, nullptr, cfg_bodies);
+}
+
+// The configuration split of a batched call, undone when the call ends so that
+// every other entry point sees one configuration.
+struct ConfigScope {
+    ibpme_ctx* c;
+    ConfigScope(ibpme_ctx* c_, int ncfg) : c(c_) {
+        c->ncfg = ncfg;
+        c->bcfg = ncfg > 1 ? c->bodies.bead_cfg.as<int>() : nullptr;
+    }
+    ~ConfigScope() {
+        c->ncfg = 1;
+        c->bcfg = nullptr;
+    }
+};
+
+// Shared by induced_charge_solve (one configuration) and induced_charge_solve_batch.
+ibpme_status solve_entry(ibpme_ctx* c, int n, const double* x, const ibpme_bodies* bodies, int ncfg,
+                         const int* cfg_bodies, const double* E0, int nrhs, const ibpme_solve_opts* opts,
+                         double* q_out, double* psi_out, double* S_out, ibpme_solve_stats* stats) {
+    if (!c) fail(IBPME_ERR_ARG, "ctx is NULL");
+    DeviceScope ds(c->device);
+    const auto t0 = std::chrono::steady_clock::now();
+    check_n(n);
+    if (n == 0) fail(IBPME_ERR_ARG, "a solve needs at least one bead");
+    if (nrhs < 1 || nrhs > c->p.max_rhs) fail(IBPME_ERR_ARG, "nrhs %d outside 1..%d", nrhs, c->p.max_rhs);
+    if (!x || !E0 || !q_out) fail(IBPME_ERR_ARG, "x, E0 and q_out are required");
+    if (ncfg < 1) fail(IBPME_ERR_ARG, "n_configs must be >= 1");
+    if (ncfg > 1 && !cfg_bodies) fail(IBPME_ERR_ARG, "cfg_bodies is required");
+    if (cfg_bodies && is_device_ptr(cfg_bodies)) fail(IBPME_ERR_ARG, "cfg_bodies must be a host array");
+    ibpme_solve_opts o{};
+    o.precision = -1;
+    if (opts) o = *opts;
+    SolveArgs a{};
+    a.n = n;
+    a.nrhs = nrhs;
+    a.prec = o.precision < 0 ? c->p.precision : o.precision;
+    if (a.prec != IBPME_FP64 && a.prec != IBPME_MIXED) fail(IBPME_ERR_ARG, "unknown solve precision");
+    if (a.prec == IBPME_MIXED && !c->have32) fail(IBPME_ERR_ARG, "mixed solve needs a mixed context");
+    a.rtol = o.rtol > 0 ? o.rtol : 1e-6;
+    a.restart = o.restart > 0 ? o.restart : 50;
+    if (a.restart > 128) fail(IBPME_ERR_ARG, "restart must be <= 128");
+    a.max_iter = o.max_iter > 0 ? o.max_iter : 3000;
+    if (o.guess == IBPME_GUESS_LEARNED && !o.mlp) fail(IBPME_ERR_ARG, "IBPME_GUESS_LEARNED needs opts->mlp");
+    if (o.guess != IBPME_GUESS_ZERO && o.guess != IBPME_GUESS_USER && o.guess != IBPME_GUESS_LEARNED)
+        fail(IBPME_ERR_ARG, "unknown guess mode");
+    if (o.guess == IBPME_GUESS_LEARNED && cfg_bodies) fail(IBPME_ERR_ARG, "a batched solve takes no learned guess");
+    a.user_guess = o.guess == IBPME_GUESS_USER || o.guess == IBPME_GUESS_LEARNED;
+    a.learned = o.guess == IBPME_GUESS_LEARNED;
+    const double* dx = static_cast<const double*>(stage_in(c, x, sizeof(double) * 3 * n, c->st_x));
+    a.E0 = static_cast<const double*>(stage_in(c, E0, sizeof(double) * 3 * nrhs, c->st_E0));
+    double* xw = static_cast<double*>(c->xw.ensure(sizeof(double) * 3 * n));
+    wrap_positions(c, n, dx, xw);
+    a.xw = xw;
+    prepare_bodies(c, n, bodies, xw, ncfg, cfg_bodies);
+    ConfigScope scope(c, ncfg);
+    const int nb = bodies->n_bodies;
+    OutArg oq = stage_out(c, q_out, sizeof(double) * (size_t)nrhs * n, c->st_out1, a.user_guess);
+    OutArg op = stage_out(c, psi_out, sizeof(double) * (size_t)nrhs * nb, c->st_out2);
+    OutArg os = stage_out(c, S_out, sizeof(double) * 3 * (size_t)nrhs * nb, c->st_out3);
+    a.q = static_cast<double*>(oq.dev);
+    a.psi = static_cast<double*>(op.dev);
+    if (a.learned) learned_guess(c, static_cast<const ibpme_mlp*>(o.mlp), n, xw, a.E0, nrhs, a.q);
+    std::vector<ibpme_solve_stats> st(ncfg);
+    solve(c, a, st.data());
+    if (S_out) body_dipoles(c, n, a.q, nrhs, static_cast<double*>(os.dev));
+    finish_out(c, oq);
+    finish_out(c, op);
+    finish_out(c, os);
+    IBP_CUDA(cudaStreamSynchronize(c->stream));
+    const double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    double worst = 0.0;
+    bool finite = true;
+    for (auto& e : st) {
+        e.time_ms = ms;
+        finite = finite && std::isfinite(e.rel_residual);
+        worst = std::max(worst, e.rel_residual);
+    }
+    if (stats)
+        for (int k = 0; k < ncfg; ++k) stats[k] = st[k];
+    if (!finite) fail(IBPME_ERR_NONFINITE, "non-finite residual in the solve");
+    if (!(worst <= a.rtol)) {
+        set_error("not converged: relative residual %.3e after %d iterations", worst, st[0].iters);
+        return IBPME_ERR_NOT_CONVERGED;
+    }
+    return IBPME_OK;
 }
 
 }  // namespace
@@ -445,59 +562,16 @@ IBP_API ibpme_status induced_charge_solve(ibpme_ctx* c, int n, const double* x, 
                                           double* q_out, double* psi_out, double* S_out,
                                           ibpme_solve_stats* stats) {
     return guard([&]() -> ibpme_status {
-        if (!c) fail(IBPME_ERR_ARG, "ctx is NULL");
-        DeviceScope ds(c->device);
-        const auto t0 = std::chrono::steady_clock::now();
-        check_n(n);
-        if (n == 0) fail(IBPME_ERR_ARG, "a solve needs at least one bead");
-        if (nrhs < 1 || nrhs > c->p.max_rhs) fail(IBPME_ERR_ARG, "nrhs %d outside 1..%d", nrhs, c->p.max_rhs);
-        if (!x || !E0 || !q_out) fail(IBPME_ERR_ARG, "x, E0 and q_out are required");
-        ibpme_solve_opts o{};
-        o.precision = -1;
-        if (opts) o = *opts;
-        SolveArgs a{};
-        a.n = n;
-        a.nrhs = nrhs;
-        a.prec = o.precision < 0 ? c->p.precision : o.precision;
-        if (a.prec != IBPME_FP64 && a.prec != IBPME_MIXED) fail(IBPME_ERR_ARG, "unknown solve precision");
-        if (a.prec == IBPME_MIXED && !c->have32) fail(IBPME_ERR_ARG, "mixed solve needs a mixed context");
-        a.rtol = o.rtol > 0 ? o.rtol : 1e-6;
-        a.restart = o.restart > 0 ? o.restart : 50;
-        if (a.restart > 128) fail(IBPME_ERR_ARG, "restart must be <= 128");
-        a.max_iter = o.max_iter > 0 ? o.max_iter : 3000;
-        if (o.guess == IBPME_GUESS_LEARNED && !o.mlp) fail(IBPME_ERR_ARG, "IBPME_GUESS_LEARNED needs opts->mlp");
-        if (o.guess != IBPME_GUESS_ZERO && o.guess != IBPME_GUESS_USER && o.guess != IBPME_GUESS_LEARNED)
-            fail(IBPME_ERR_ARG, "unknown guess mode");
-        a.user_guess = o.guess == IBPME_GUESS_USER || o.guess == IBPME_GUESS_LEARNED;
-        a.learned = o.guess == IBPME_GUESS_LEARNED;
-        const double* dx = static_cast<const double*>(stage_in(c, x, sizeof(double) * 3 * n, c->st_x));
-        a.E0 = static_cast<const double*>(stage_in(c, E0, sizeof(double) * 3 * nrhs, c->st_E0));
-        double* xw = static_cast<double*>(c->xw.ensure(sizeof(double) * 3 * n));
-        wrap_positions(c, n, dx, xw);
-        a.xw = xw;
-        prepare_bodies(c, n, bodies, xw);
-        const int nb = bodies->n_bodies;
-        OutArg oq = stage_out(c, q_out, sizeof(double) * (size_t)nrhs * n, c->st_out1, a.user_guess);
-        OutArg op = stage_out(c, psi_out, sizeof(double) * (size_t)nrhs * nb, c->st_out2);
-        OutArg os = stage_out(c, S_out, sizeof(double) * 3 * (size_t)nrhs * nb, c->st_out3);
-        a.q = static_cast<double*>(oq.dev);
-        a.psi = static_cast<double*>(op.dev);
-        if (a.learned) learned_guess(c, static_cast<const ibpme_mlp*>(o.mlp), n, xw, a.E0, nrhs, a.q);
-        ibpme_solve_stats st{};
-        solve(c, a, &st);
-        if (S_out) body_dipoles(c, n, a.q, nrhs, static_cast<double*>(os.dev));
-        finish_out(c, oq);
-        finish_out(c, op);
-        finish_out(c, os);
-        IBP_CUDA(cudaStreamSynchronize(c->stream));
-        st.time_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
-        if (stats) *stats = st;
-        if (!(st.rel_residual <= a.rtol)) {
-            if (!std::isfinite(st.rel_residual)) fail(IBPME_ERR_NONFINITE, "non-finite residual in the solve");
-            set_error("not converged: relative residual %.3e after %d iterations", st.rel_residual, st.iters);
-            return IBPME_ERR_NOT_CONVERGED;
-        }
-        return IBPME_OK;
+        return solve_entry(c, n, x, bodies, 1, nullptr, E0, nrhs, opts, q_out, psi_out, S_out, stats);
+    });
+}
+
+IBP_API ibpme_status induced_charge_solve_batch(ibpme_ctx* c, int n, const double* x, const ibpme_bodies* bodies,
+                                                int n_configs, const int* cfg_bodies, const double* E0, int nrhs,
+                                                const ibpme_solve_opts* opts, double* q_out, double* psi_out,
+                                                double* S_out, ibpme_solve_stats* stats) {
+    return guard([&]() -> ibpme_status {
+        return solve_entry(c, n, x, bodies, n_configs, cfg_bodies, E0, nrhs, opts, q_out, psi_out, S_out, stats);
     });
 }
 

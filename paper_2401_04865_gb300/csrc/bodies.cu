@@ -285,7 +285,8 @@ __global__ void bd_bead_kernel(int n, const int* __restrict__ bead_body, const d
 
 }  // namespace
 
-void bodies_upload(ibpme_ctx* c, int n, const ibpme_bodies* b, const double* xw) {
+void bodies_upload(ibpme_ctx* c, int n, const ibpme_bodies* b, const double* xw, int ncfg, const int* cfg_beads,
+                   const int* cfg_bodies) {
     BodyData& bd = c->bodies;
     cudaStream_t s = c->stream;
     const int nb = b->n_bodies;
@@ -295,40 +296,85 @@ void bodies_upload(ibpme_ctx* c, int n, const ibpme_bodies* b, const double* xw)
     if (off[0] != 0 || off[nb] != n) fail(IBPME_ERR_ARG, "body_offsets must start at 0 and end at n = %d", n);
     for (int i = 0; i < nb; ++i)
         if (off[i + 1] <= off[i]) fail(IBPME_ERR_ARG, "body %d is empty or offsets decrease", i);
-    // unchanged body structure (e.g. along a trajectory): keep the unknown lists
-    const bool same = bd.host_n == n && bd.host_off.size() == off.size() && bd.nb == nb &&
-                      std::memcmp(bd.host_off.data(), off.data(), sizeof(int) * off.size()) == 0;
-    if (!same) {
-        std::vector<int> free_idx, free_off{0}, mb_body, mb_of_free, free_pos(n, -1);
-        for (int i = 0; i < nb; ++i) {
-            if (off[i + 1] - off[i] < 2) continue;
-            for (int j = off[i]; j < off[i + 1]; ++j) {
-                free_pos[j] = (int)free_idx.size();
-                free_idx.push_back(j);
-                mb_of_free.push_back((int)mb_body.size());
-            }
-            mb_body.push_back(i);
-            free_off.push_back((int)free_idx.size());
+    // configurations: contiguous ranges of bodies (and hence of beads)
+    std::vector<int> cb(ncfg + 1), cbe(ncfg + 1);
+    if (ncfg == 1 && !cfg_bodies) {
+        cb = {0, nb};
+        cbe = {0, n};
+    } else {
+        for (int k = 0; k <= ncfg; ++k) cb[k] = cfg_bodies[k];
+        if (cb[0] != 0 || cb[ncfg] != nb) fail(IBPME_ERR_ARG, "configuration body ranges must cover 0..n_bodies");
+        for (int k = 0; k < ncfg; ++k)
+            if (cb[k + 1] <= cb[k]) fail(IBPME_ERR_ARG, "configuration %d has no body", k);
+        for (int k = 0; k <= ncfg; ++k) {
+            cbe[k] = off[cb[k]];
+            if (cfg_beads && cfg_beads[k] != cbe[k])
+                fail(IBPME_ERR_ARG, "configuration %d: bead offset %d does not start body %d", k, cfg_beads[k], cb[k]);
         }
+    }
+    // unchanged structure (e.g. along a trajectory): keep the unknown lists
+    const bool same = bd.host_n == n && bd.host_off == off && bd.host_cfg == cb;
+    if (!same) {
+        // unknowns of configuration k: its free beads (beads of multi-bead bodies), then its multi-bead bodies
+        std::vector<int> free_idx, free_unk, mb_body, mb_unk, mb_first, mb_cnt, bead_unk(n, -1), body_unk(nb, -1),
+            unk_cfg, bead_cfg(n), uo(ncfg + 1, 0);
+        int u = 0;
+        for (int k = 0; k < ncfg; ++k) {
+            uo[k] = u;
+            for (int i = cb[k]; i < cb[k + 1]; ++i) {
+                for (int j = off[i]; j < off[i + 1]; ++j) bead_cfg[j] = k;
+                if (off[i + 1] - off[i] < 2) continue;
+                for (int j = off[i]; j < off[i + 1]; ++j) {
+                    bead_unk[j] = u;
+                    free_idx.push_back(j);
+                    free_unk.push_back(u++);
+                    unk_cfg.push_back(k);
+                }
+            }
+            for (int i = cb[k]; i < cb[k + 1]; ++i) {
+                if (off[i + 1] - off[i] < 2) continue;
+                body_unk[i] = u;
+                mb_body.push_back(i);
+                mb_unk.push_back(u++);
+                mb_first.push_back(bead_unk[off[i]]);
+                mb_cnt.push_back(off[i + 1] - off[i]);
+                unk_cfg.push_back(k);
+            }
+        }
+        uo[ncfg] = u;
         bd.nb = nb;
         bd.nmb = (int)mb_body.size();
         bd.nfree = (int)free_idx.size();
+        bd.nk = u;
+        bd.ncfg = ncfg;
+        bd.uo_h = uo;
+        bd.cfg_beads_h = cbe;
+        bd.cfg_bodies_h = cb;
         auto up = [&](DevBuf& dst, const std::vector<int>& v) {
             dst.ensure(sizeof(int) * (v.size() + 1));
             if (!v.empty())
                 IBP_CUDA(cudaMemcpyAsync(dst.p, v.data(), sizeof(int) * v.size(), cudaMemcpyHostToDevice, s));
         };
         up(bd.free_idx, free_idx);
-        up(bd.free_off, free_off);
+        up(bd.free_unk, free_unk);
         up(bd.mb_body, mb_body);
-        up(bd.mb_of_free, mb_of_free);
-        up(bd.free_pos, free_pos);
+        up(bd.mb_unk, mb_unk);
+        up(bd.mb_first, mb_first);
+        up(bd.mb_cnt, mb_cnt);
+        up(bd.bead_unk, bead_unk);
+        up(bd.body_unk, body_unk);
+        up(bd.unk_cfg, unk_cfg);
+        up(bd.bead_cfg, bead_cfg);
+        up(bd.uo, uo);
+        up(bd.cfg_beads, cbe);
+        up(bd.cfg_bodies, cb);
         up(bd.off, off);
         bd.bead_body.ensure(sizeof(int) * (n + 1));
         bead_body_kernel<<<div_up((long long)nb * 32, 128), 128, 0, s>>>(nb, bd.off.as<int>(), bd.bead_body.as<int>());
         IBP_CHECK_LAUNCH();
         IBP_CUDA(cudaStreamSynchronize(s));   // host vectors go out of scope
         bd.host_off = off;
+        bd.host_cfg = cb;
         bd.host_n = n;
     }
     bd.X.ensure(sizeof(double) * 3 * nb);

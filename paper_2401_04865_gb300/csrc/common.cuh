@@ -8,6 +8,8 @@
 #include <cstdint>
 #include <exception>
 #include <string>
+#include <map>
+#include <utility>
 #include <vector>
 
 #include "../../include/ibpme.h"
@@ -106,24 +108,25 @@ constexpr int kMaxRhs = 8;
 constexpr int kMaxP = 32;
 
 // Spectral-Ewald mesh engine in one precision: grids, spectrum, Green's table, plans.
+// A grid "channel" holds one right-hand side of one configuration: channel
+// cfg * nrhs + r (a single system is configuration 0).
 template <typename T>
 struct Mesh {
     MeshGeom g{};
-    int rcap = 0;
+    int rcap = 0;   // channels the buffers hold
     DevBuf grid;    // [rcap][G] real
     DevBuf spec;    // [rcap][Gc] complex
     DevBuf green;   // [Gc] real: G(k) / (N_x N_y N_z), 0 at k = 0
     DevBuf work;    // cuFFT work area shared by the plans
-    cufftHandle r2c[kMaxRhs + 1] = {};
-    cufftHandle c2r[kMaxRhs + 1] = {};
-    bool have[kMaxRhs + 1] = {};
-    void init(const MeshGeom& geom, int max_rhs, double xi, double eta, double a, cudaStream_t s);
+    std::map<int, std::pair<cufftHandle, cufftHandle>> plan;   // R2C and C2R plans by channel count
+    void init(const MeshGeom& geom, int channels, double xi, double eta, double a, cudaStream_t s);
     void destroy();
-    void plans(int nrhs, cudaStream_t s);
-    // psi_k[r][alpha] (= overwrite) and optionally E_k[r][alpha][3] for the given charges
-    void spread(int n, const double* xw, const double* q, int nrhs, cudaStream_t s);
-    void transform(int nrhs, cudaStream_t s);   // R2C, scale, C2R
-    void gather(int n, const double* xw, int nrhs, double* psi, double* E, cudaStream_t s);
+    void ensure_channels(int ch);
+    void plans(int ch, cudaStream_t s);
+    // bead_cfg (device, or NULL for one configuration) maps each bead to its configuration
+    void spread(int n, const double* xw, const double* q, int nrhs, const int* bead_cfg, int ncfg, cudaStream_t s);
+    void transform(int ch, cudaStream_t s);   // R2C, scale, C2R over ch channels
+    void gather(int n, const double* xw, int nrhs, const int* bead_cfg, double* psi, double* E, cudaStream_t s);
 };
 
 // Cell list and real-space pair table (Sec. III.D.1, Sec. III.D.3 step 1).
@@ -142,24 +145,39 @@ struct NearList {
     DevBuf fp_dev;                 // fingerprint of the positions + non-finite flag
     unsigned long long fp = 0;     // fingerprint of the positions the table was built for
     bool fp_valid = false;
+    int ncfg = 1;
 };
 
 // Body bookkeeping on the device for solves, forces and BD steps.
+// Unknowns of the reduced saddle system (krylov.cu), configuration by
+// configuration: the configuration's free beads (beads of multi-bead bodies,
+// in bead order), then its multi-bead bodies (one body potential each).
 struct BodyData {
     int nb = 0;         // bodies
     int nmb = 0;        // multi-bead bodies
     int nfree = 0;      // beads of multi-bead bodies (the unknown charges)
-    DevBuf off;         // [nb+1] int offsets
-    DevBuf bead_body;   // [n] int body id
+    int nk = 0;         // unknowns (nfree + nmb)
+    int ncfg = 1;       // configurations
+    DevBuf off;         // [nb+1] int body offsets
+    DevBuf bead_body;   // [n] body of each bead
     DevBuf X, Q;        // [nb][3], [nb]
-    DevBuf free_idx;    // [nfree] bead index of each unknown charge
-    DevBuf free_off;    // [nmb+1] offsets of the multi-bead bodies in the unknown list
-    DevBuf mb_body;     // [nmb] body id of each multi-bead body
-    DevBuf mb_of_free;  // [nfree] multi-bead body index of each unknown charge
-    DevBuf free_pos;    // [n] position of each bead in the unknown list, -1 for ions
+    DevBuf free_idx;    // [nfree] bead of each free bead
+    DevBuf free_unk;    // [nfree] unknown index of each free bead
+    DevBuf mb_body;     // [nmb] body of each multi-bead body
+    DevBuf mb_unk;      // [nmb] unknown index of its potential
+    DevBuf mb_first;    // [nmb] unknown index of its first bead (its beads' unknowns are contiguous)
+    DevBuf mb_cnt;      // [nmb] its bead count
+    DevBuf bead_unk;    // [n] unknown index of a bead's charge, -1 for ions
+    DevBuf body_unk;    // [nb] unknown index of a body's potential, -1 for ions
+    DevBuf unk_cfg;     // [nk] configuration of each unknown
+    DevBuf bead_cfg;    // [n] configuration of each bead
+    DevBuf uo;          // [ncfg+1] unknown offsets of the configurations
+    DevBuf cfg_beads;   // [ncfg+1] bead offsets of the configurations
+    DevBuf cfg_bodies;  // [ncfg+1] body offsets of the configurations
     DevBuf rel;         // [n][3] r_ij = minimum image of x_ij - X_i
     DevBuf scratch;     // reductions and BD temporaries
-    std::vector<int> host_off;   // offsets of the last upload (to skip rebuilding the lists)
+    std::vector<int> uo_h, cfg_beads_h, cfg_bodies_h;
+    std::vector<int> host_off, host_cfg;   // structure of the last upload (to skip rebuilding the lists)
     int host_n = -1;
 };
 
@@ -227,6 +245,10 @@ struct ibpme_ctx {
     void* pinned = nullptr;  // small pinned host scratch
     size_t pinned_bytes = 0;
     cudaStream_t work = nullptr;              // the context's own stream (solves, graph capture)
+    // batch of independent configurations (1 and NULL outside a batched call):
+    // bead b belongs to configuration bcfg[b]
+    int ncfg = 1;
+    const int* bcfg = nullptr;
     ibp::DevBuf ml_feat, ml_scratch, ml_scales, ml_y;   // learned warm start
     cudaEvent_t ev_in = nullptr, ev_out = nullptr;
 };
@@ -250,7 +272,9 @@ void pme_apply(ibpme_ctx* c, int n, const double* xw, const double* q, int nrhs,
 void* pinned_host(ibpme_ctx* c, size_t bytes);
 
 // ---- bodies.cu ----
-void bodies_upload(ibpme_ctx* c, int n, const ibpme_bodies* b, const double* xw);
+// cfg_beads / cfg_bodies: host [ncfg+1] offsets of the configurations (NULL for one)
+void bodies_upload(ibpme_ctx* c, int n, const ibpme_bodies* b, const double* xw, int ncfg = 1,
+                   const int* cfg_beads = nullptr, const int* cfg_bodies = nullptr);
 void body_dipoles(ibpme_ctx* c, int n, const double* q, int nrhs, double* S);
 void bead_forces(ibpme_ctx* c, int n, const double* q, const double* E0, const double* E, double* f);
 void body_reduce_force_torque(ibpme_ctx* c, int n, const double* f, double* F, double* L);

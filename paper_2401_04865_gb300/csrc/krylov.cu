@@ -8,13 +8,19 @@
 // The ion rows of the full system then hold exactly, and the ions'
 // Psi - Psi_0 = (M q)_ion - r.E0 follow from the final evaluation.
 //
+// Systems.  A call solves S = (configurations) x (right-hand sides)
+// independent systems in lockstep: system s = cfg * R + r owns the segment
+// [uo[cfg], uo[cfg+1]) of row r of every Krylov vector, its own Hessenberg
+// matrix, Givens rotations and convergence flag; every PME evaluation serves
+// all systems at once (batched mesh channels, batched FFTs).
+//
 // Arnoldi uses classical Gram-Schmidt with one re-orthogonalisation (CGS2),
 // the Hessenberg least-squares problem is kept triangular by Givens rotations
 // (Saad & Schultz), and each restart cycle recomputes the residual.  In mixed
 // precision the cycles run on the FP32-mesh operator inside an iterative
 // refinement whose residual b - A x always uses the FP64 operator; in FP64 the
-// same loop is plain restarted GMRES.  Several right-hand sides (field
-// directions) iterate in lockstep and share every PME evaluation.
+// same loop is plain restarted GMRES.  One Arnoldi iteration (operator and
+// orthogonalisation) is captured once as a CUDA graph and replayed.
 #include "common.cuh"
 
 #include <algorithm>
@@ -26,7 +32,7 @@
 namespace ibp {
 
 struct Krylov {
-    int nk = 0, R = 0, m = 0, nblk = 0;
+    int nk = 0, R = 0, S = 0, m = 0, nblk = 0;
     DevBuf V, H, cs, sn, g, y, w, x, d, r, rc, part, scal, active, qop, psi, psi_tot, qtot, Ax, norms, jdev;
     // one captured Arnoldi iteration per mesh precision, replayed for every j
     cudaGraphExec_t exec[2] = {nullptr, nullptr};
@@ -40,10 +46,10 @@ struct Krylov {
 
 namespace {
 
-constexpr int kChunk = 2048;   // vector elements per block in the Arnoldi kernels
+constexpr int kChunk = 2048;   // vector elements per block in the multi-block Arnoldi kernels
 constexpr int kThreads = 256;
 
-// scal[r][*] slots
+// scal[s][*] slots
 enum { S_BETA = 0, S_RES = 1, S_INVH = 2, S_COUNT = 4 };
 
 __device__ __forceinline__ double block_sum(double v, double* sh) {
@@ -59,6 +65,8 @@ __device__ __forceinline__ double block_sum(double v, double* sh) {
     __syncthreads();
     return t;   // valid in warp 0
 }
+
+// ---- multi-block Arnoldi (one configuration, long vectors) ----
 
 // part[r][blk][i] = sum over this block's chunk of V_i . w, i = 0..j
 __global__ void __launch_bounds__(kThreads) dots_kernel(int nk, int m, const int* __restrict__ jdev,
@@ -114,22 +122,20 @@ __global__ void __launch_bounds__(kThreads) update_kernel(int nk, int m, const i
         wr[t] = v;
         acc += v * v;
     }
-    __syncthreads();   // part[] slots 0..j are read above by every block before any block writes slot m+1
+    __syncthreads();
     if (pass == 1) {
         const double s = block_sum(acc, sh);
         if (threadIdx.x == 0) part[((size_t)r * nblk + blockIdx.x) * (m + 2) + m + 1] = s;
     }
 }
 
-// h_{j+1,j} = |w|; Givens rotations on column j; g update; residual estimate |g_{j+1}|.
-// Givens rotations of column j of H and the residual estimate; shared by the
-// multi-block and the single-block Arnoldi paths.
-__device__ void givens_column(int m, int j, int r, double h, double* __restrict__ H, double* __restrict__ cs,
+// Givens rotations of column j of system s's H and its residual estimate.
+__device__ void givens_column(int m, int j, int s, double h, double* __restrict__ H, double* __restrict__ cs,
                               double* __restrict__ sn, double* __restrict__ g, double* __restrict__ scal) {
-    double* Hc = H + ((size_t)r * m + j) * (m + 1);
-    double* c = cs + (size_t)r * m;
-    double* sg = sn + (size_t)r * m;
-    double* gr = g + (size_t)r * (m + 1);
+    double* Hc = H + ((size_t)s * m + j) * (m + 1);
+    double* c = cs + (size_t)s * m;
+    double* sg = sn + (size_t)s * m;
+    double* gr = g + (size_t)s * (m + 1);
     Hc[j + 1] = h;
     for (int i = 0; i < j; ++i) {
         const double t = c[i] * Hc[i] + sg[i] * Hc[i + 1];
@@ -148,7 +154,7 @@ __device__ void givens_column(int m, int j, int r, double h, double* __restrict_
     Hc[j + 1] = 0.0;
     gr[j + 1] = -sg[j] * gr[j];
     gr[j] = c[j] * gr[j];
-    double* sc = scal + (size_t)r * S_COUNT;
+    double* sc = scal + (size_t)s * S_COUNT;
     sc[S_RES] = fabs(gr[j + 1]);
     // happy breakdown: the Krylov space is invariant, the estimate above is exact (0)
     sc[S_INVH] = (h > 1e-300 && h > 1e-14 * den) ? 1.0 / h : 0.0;
@@ -182,44 +188,45 @@ __global__ void normalize_kernel(int nk, int m, const int* __restrict__ jdev, in
 
 __global__ void advance_kernel(int* __restrict__ jdev) { *jdev += 1; }
 
-// One Arnoldi step (CGS2 + Givens + normalisation) by a single block per
-// right-hand side, for Krylov vectors short enough that one block streams them
-// faster than a chain of six grid-wide launches.  Ends by advancing j.
+// ---- single-block Arnoldi: one block per system, any number of systems ----
 constexpr int kSmallThreads = 1024;
 constexpr int kSmallMaxNk = 32 * kSmallThreads;
 
 __global__ void __launch_bounds__(kSmallThreads)
-arnoldi_small_kernel(int nk, int m, int* __restrict__ jdev, const double* __restrict__ V, double* __restrict__ w,
-                     double* __restrict__ H, double* __restrict__ cs, double* __restrict__ sn, double* __restrict__ g,
+arnoldi_small_kernel(int nk, int m, int R, const int* __restrict__ uo, int* __restrict__ jdev,
+                     const double* __restrict__ V, double* __restrict__ w, double* __restrict__ H,
+                     double* __restrict__ cs, double* __restrict__ sn, double* __restrict__ g,
                      double* __restrict__ scal, const int* __restrict__ active, double* __restrict__ Vout) {
     __shared__ double hc[130];
     __shared__ double sh[32];
     __shared__ double inv_h;
     const int j = *jdev;
-    const int r = blockIdx.x;
+    const int s = blockIdx.x;
+    const int r = s % R, cfg = s / R;
+    const int base = uo[cfg], len = uo[cfg + 1] - base;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarp = blockDim.x >> 5;
-    const bool act = active[r] != 0;
-    double* wr = w + (size_t)r * nk;
-    const double* Vr = V + (size_t)r * (m + 1) * nk;
-    double* Hc = H + ((size_t)r * m + j) * (m + 1);
+    const bool act = active[s] != 0;
+    double* wr = w + (size_t)r * nk + base;
+    const double* Vr = V + (size_t)r * (m + 1) * nk + base;
+    double* Hc = H + ((size_t)s * m + j) * (m + 1);
     if (act) {
         for (int pass = 0; pass < 2; ++pass) {
             for (int i = warp; i <= j; i += nwarp) {
                 const double* vi = Vr + (size_t)i * nk;
                 double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;   // independent chains for ILP
                 int t = lane;
-                for (; t + 96 < nk; t += 128) {
+                for (; t + 96 < len; t += 128) {
                     a0 += vi[t] * wr[t];
                     a1 += vi[t + 32] * wr[t + 32];
                     a2 += vi[t + 64] * wr[t + 64];
                     a3 += vi[t + 96] * wr[t + 96];
                 }
-                for (; t < nk; t += 32) a0 += vi[t] * wr[t];
+                for (; t < len; t += 32) a0 += vi[t] * wr[t];
                 const double acc = warp_sum((a0 + a1) + (a2 + a3));
                 if (lane == 0) hc[i] = acc;
             }
             __syncthreads();
-            for (int t = threadIdx.x; t < nk; t += blockDim.x) {
+            for (int t = threadIdx.x; t < len; t += blockDim.x) {
                 double v0 = wr[t], v1 = 0.0, v2 = 0.0, v3 = 0.0;
                 int i = 0;
                 for (; i + 3 <= j; i += 4) {
@@ -235,49 +242,51 @@ arnoldi_small_kernel(int nk, int m, int* __restrict__ jdev, const double* __rest
             __syncthreads();
         }
         double acc = 0.0;
-        for (int t = threadIdx.x; t < nk; t += blockDim.x) acc += wr[t] * wr[t];
+        for (int t = threadIdx.x; t < len; t += blockDim.x) acc += wr[t] * wr[t];
         const double nrm2 = block_sum(acc, sh);
         if (threadIdx.x == 0) {
-            givens_column(m, j, r, sqrt(nrm2), H, cs, sn, g, scal);
-            inv_h = scal[(size_t)r * S_COUNT + S_INVH];
+            givens_column(m, j, s, sqrt(nrm2), H, cs, sn, g, scal);
+            inv_h = scal[(size_t)s * S_COUNT + S_INVH];
         }
         __syncthreads();
-        double* vn = Vout + ((size_t)r * (m + 1) + j + 1) * nk;
-        for (int t = threadIdx.x; t < nk; t += blockDim.x) vn[t] = wr[t] * inv_h;
+        double* vn = Vout + ((size_t)r * (m + 1) + j + 1) * nk + base;
+        for (int t = threadIdx.x; t < len; t += blockDim.x) vn[t] = wr[t] * inv_h;
     }
     // with one block, every thread has read j by now: advance it here (with several
-    // right-hand sides a separate launch advances it, after all blocks are done)
+    // systems a separate launch advances it, after all blocks are done)
     __syncthreads();
     if (gridDim.x == 1 && threadIdx.x == 0) *jdev = j + 1;
 }
 
-// Back substitution H(0:k,0:k) y = g(0:k) per right-hand side.
+// Back substitution H(0:k,0:k) y = g(0:k) per system.
 __global__ void trisolve_kernel(int m, int k, const double* __restrict__ H, const double* __restrict__ g,
                                 const int* __restrict__ active, double* __restrict__ y) {
-    const int r = blockIdx.x;
+    const int s = blockIdx.x;
     if (threadIdx.x != 0) return;
-    double* yr = y + (size_t)r * m;
-    if (!active[r]) {
-        for (int i = 0; i < k; ++i) yr[i] = 0.0;
+    double* ys = y + (size_t)s * m;
+    if (!active[s]) {
+        for (int i = 0; i < k; ++i) ys[i] = 0.0;
         return;
     }
     for (int i = k - 1; i >= 0; --i) {
-        double s = g[(size_t)r * (m + 1) + i];
-        for (int l = i + 1; l < k; ++l) s -= H[((size_t)r * m + l) * (m + 1) + i] * yr[l];
-        const double hii = H[((size_t)r * m + i) * (m + 1) + i];
-        yr[i] = hii != 0.0 ? s / hii : 0.0;
+        double v = g[(size_t)s * (m + 1) + i];
+        for (int l = i + 1; l < k; ++l) v -= H[((size_t)s * m + l) * (m + 1) + i] * ys[l];
+        const double hii = H[((size_t)s * m + i) * (m + 1) + i];
+        ys[i] = hii != 0.0 ? v / hii : 0.0;
     }
 }
 
-__global__ void xupdate_kernel(int nk, int m, int k, int R, const double* __restrict__ V, const double* __restrict__ y,
-                               double* __restrict__ x) {
+// x[r][t] += sum_i y[s][i] V_i[r][t], s the system of unknown t in row r
+__global__ void xupdate_kernel(int nk, int m, int k, int R, const int* __restrict__ unk_cfg,
+                               const double* __restrict__ V, const double* __restrict__ y, double* __restrict__ x) {
     const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (t >= (long long)nk * R) return;
     const int r = (int)(t / nk);
     const long long e = t - (long long)r * nk;
-    double s = x[t];
-    for (int i = 0; i < k; ++i) s += y[(size_t)r * m + i] * V[((size_t)r * (m + 1) + i) * nk + e];
-    x[t] = s;
+    const int s = unk_cfg[e] * R + r;
+    double v = x[t];
+    for (int i = 0; i < k; ++i) v += y[(size_t)s * m + i] * V[((size_t)r * (m + 1) + i) * nk + e];
+    x[t] = v;
 }
 
 __global__ void axpby_kernel(long long len, double a, const double* __restrict__ u, double b,
@@ -286,59 +295,68 @@ __global__ void axpby_kernel(long long len, double a, const double* __restrict__
     if (t < len) out[t] = a * u[t] + b * v[t];
 }
 
-// norms[r] += sum_t v[r][t]^2
-__global__ void norm2_kernel(int nk, const double* __restrict__ v, double* __restrict__ norms) {
+// norms[s] += sum over system s's segment of v^2  (grid: chunks x S)
+__global__ void norm2_kernel(int nk, int R, const int* __restrict__ uo, const double* __restrict__ v,
+                             double* __restrict__ norms) {
     __shared__ double sh[32];
-    const int r = blockIdx.y;
+    const int s = blockIdx.y;
+    const int r = s % R, cfg = s / R;
+    const int b0 = uo[cfg], b1 = uo[cfg + 1];
     double acc = 0.0;
-    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < nk; t += (long long)gridDim.x * blockDim.x) {
+    for (long long t = b0 + blockIdx.x * (long long)blockDim.x + threadIdx.x; t < b1;
+         t += (long long)gridDim.x * blockDim.x) {
         const double e = v[(size_t)r * nk + t];
         acc += e * e;
     }
-    const double s = block_sum(acc, sh);
-    if (threadIdx.x == 0) atomicAdd(norms + r, s);
+    const double sm = block_sum(acc, sh);
+    if (threadIdx.x == 0 && sm != 0.0) atomicAdd(norms + s, sm);
 }
 
-// Start of a cycle: beta = |r|, V_0 = r / beta, g = beta e_1 (inactive systems: V_0 = 0).
-__global__ void start_kernel(int nk, int m, int R, const double* __restrict__ rr, const double* __restrict__ norms,
+// Start of a cycle: V_0 = res / |res| per system, g = |res| e_1 (inactive systems: V_0 = 0).
+__global__ void start_kernel(int nk, int m, int R, int S, const int* __restrict__ unk_cfg,
+                             const double* __restrict__ rr, const double* __restrict__ norms,
                              const int* __restrict__ active, double* __restrict__ V, double* __restrict__ g,
                              double* __restrict__ scal) {
     const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (t < (long long)R * (m + 1)) {
-        const int r = (int)(t / (m + 1)), i = (int)(t % (m + 1));
-        g[t] = (i == 0 && active[r]) ? sqrt(norms[r]) : 0.0;
-        if (i == 0) scal[(size_t)r * S_COUNT + S_BETA] = sqrt(norms[r]);
+    if (t < (long long)S * (m + 1)) {
+        const int s = (int)(t / (m + 1)), i = (int)(t % (m + 1));
+        g[t] = (i == 0 && active[s]) ? sqrt(norms[s]) : 0.0;
+        if (i == 0) scal[(size_t)s * S_COUNT + S_BETA] = sqrt(norms[s]);
     }
     if (t >= (long long)nk * R) return;
     const int r = (int)(t / nk);
     const long long e = t - (long long)r * nk;
-    const double beta = sqrt(norms[r]);
-    V[(size_t)r * (m + 1) * nk + e] = (active[r] && beta > 0.0) ? rr[t] / beta : 0.0;
+    const int s = unk_cfg[e] * R + r;
+    const double beta = sqrt(norms[s]);
+    V[(size_t)r * (m + 1) * nk + e] = (active[s] && beta > 0.0) ? rr[t] / beta : 0.0;
 }
 
 // ---- the reduced saddle operator ----
-// u of right-hand side r starts at u + r * ustride (+ j * nk when jdev is given: V_j)
+// u of row r starts at u + r * ustride (+ j * nk when jdev is given: V_j)
 __global__ void scatter_kernel(int nfree, long long ustride, int n, int R, const int* __restrict__ free_idx,
-                               const double* __restrict__ u, const int* __restrict__ jdev, int nk,
-                               double* __restrict__ qop) {
+                               const int* __restrict__ free_unk, const double* __restrict__ u,
+                               const int* __restrict__ jdev, int nk, double* __restrict__ qop) {
     const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (t >= (long long)nfree * R) return;
     if (jdev) u += (size_t)(*jdev) * nk;
     const int r = (int)(t / nfree), i = (int)(t % nfree);
-    qop[(size_t)r * n + free_idx[i]] = u[(size_t)r * ustride + i];
+    qop[(size_t)r * n + free_idx[i]] = u[(size_t)r * ustride + free_unk[i]];
 }
 
-// y_F = -psi_F + Psi'(body); y_B = sum of the body's charges
+// y_bead = -psi_bead + Psi'(body); y_body = sum of the body's charges
 __global__ void assemble_kernel(int nfree, int nmb, int nk, long long ustride, int n, int R,
-                                const int* __restrict__ free_idx, const int* __restrict__ mb_of_free,
-                                const int* __restrict__ free_off, const double* __restrict__ psi,
+                                const int* __restrict__ free_idx, const int* __restrict__ free_unk,
+                                const int* __restrict__ bead_body, const int* __restrict__ body_unk,
+                                const int* __restrict__ mb_unk, const int* __restrict__ mb_first,
+                                const int* __restrict__ mb_cnt, const double* __restrict__ psi,
                                 const double* __restrict__ u, const int* __restrict__ jdev, double* __restrict__ y) {
     if (jdev) u += (size_t)(*jdev) * nk;
     const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     const long long top = (long long)nfree * R;
     if (t < top) {
         const int r = (int)(t / nfree), i = (int)(t % nfree);
-        y[(size_t)r * nk + i] = -psi[(size_t)r * n + free_idx[i]] + u[(size_t)r * ustride + nfree + mb_of_free[i]];
+        const int j = free_idx[i];
+        y[(size_t)r * nk + free_unk[i]] = -psi[(size_t)r * n + j] + u[(size_t)r * ustride + body_unk[bead_body[j]]];
         return;
     }
     // one warp per (rhs, body) for the constraint rows; the warp section starts on a
@@ -351,68 +369,48 @@ __global__ void assemble_kernel(int nfree, int nmb, int nk, long long ustride, i
     if (wid >= (long long)nmb * R) return;
     const int r = (int)(wid / nmb), b = (int)(wid % nmb);
     double s = 0.0;
-    for (int i = free_off[b] + lane; i < free_off[b + 1]; i += 32) s += u[(size_t)r * ustride + i];
+    for (int i = lane; i < mb_cnt[b]; i += 32) s += u[(size_t)r * ustride + mb_first[b] + i];
     s = warp_sum(s);
-    if (lane == 0) y[(size_t)r * nk + nfree + b] = s;
-}
-
-// |b_full|^2 = sum_all beads (r.E0)^2 + sum_bodies Q^2 (Eq. saddle right-hand side)
-__global__ void bfull_kernel(int n, int nb, int R, const double* __restrict__ rel, const double* __restrict__ E0,
-                             const double* __restrict__ Q, double* __restrict__ norms) {
-    __shared__ double sh[32];
-    const int r = blockIdx.y;
-    const double* e = E0 + 3 * r;
-    double acc = 0.0;
-    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < (long long)n + nb;
-         t += (long long)gridDim.x * blockDim.x) {
-        if (t < n) {
-            const double v = rel[3 * t] * e[0] + rel[3 * t + 1] * e[1] + rel[3 * t + 2] * e[2];
-            acc += v * v;
-        } else {
-            const double v = Q[t - n];
-            acc += v * v;
-        }
-    }
-    const double s = block_sum(acc, sh);
-    if (threadIdx.x == 0) atomicAdd(norms + r, s);
+    if (lane == 0) y[(size_t)r * nk + mb_unk[b]] = s;
 }
 
 // all bead charges of the current iterate: free beads from x, ions fixed at Q
-__global__ void compose_kernel(int n, int nk, int R, const int* __restrict__ free_pos,
+__global__ void compose_kernel(int n, int nk, int R, const int* __restrict__ bead_unk,
                                const int* __restrict__ bead_body, const double* __restrict__ Q,
                                const double* __restrict__ x, double* __restrict__ qtot) {
     const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (t >= (long long)n * R) return;
     const int r = (int)(t / n), j = (int)(t % n);
-    const int f = free_pos[j];
+    const int f = bead_unk[j];
     qtot[t] = f >= 0 ? x[(size_t)r * nk + f] : Q[bead_body[j]];
 }
 
 // Least-squares body potentials for given charges: Psi'_b = mean over the body's
 // beads of ((M q)_j - r_j.E0), the value that minimises the bead rows' residual.
-__global__ void fit_psi_kernel(int nfree, int nmb, int nk, int n, int R, const int* __restrict__ free_idx,
-                               const int* __restrict__ free_off, const double* __restrict__ rel,
-                               const double* __restrict__ E0, const double* __restrict__ psi,
-                               double* __restrict__ x) {
+__global__ void fit_psi_kernel(int nmb, int nk, int n, int R, const int* __restrict__ mb_body,
+                               const int* __restrict__ mb_unk, const int* __restrict__ off,
+                               const double* __restrict__ rel, const double* __restrict__ E0,
+                               const double* __restrict__ psi, double* __restrict__ x) {
     const long long wid = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (wid >= (long long)nmb * R) return;
     const int r = (int)(wid / nmb), b = (int)(wid % nmb);
+    const int body = mb_body[b];
     const double* e = E0 + 3 * r;
     double sm = 0.0;
-    for (int i = free_off[b] + lane; i < free_off[b + 1]; i += 32) {
-        const int j = free_idx[i];
+    for (int j = off[body] + lane; j < off[body + 1]; j += 32)
         sm += psi[(size_t)r * n + j] - (rel[3 * j] * e[0] + rel[3 * j + 1] * e[1] + rel[3 * j + 2] * e[2]);
-    }
     sm = warp_sum(sm);
-    if (lane == 0) x[(size_t)r * nk + nfree + b] = sm / (double)(free_off[b + 1] - free_off[b]);
+    if (lane == 0) x[(size_t)r * nk + mb_unk[b]] = sm / (double)(off[body + 1] - off[body]);
 }
 
 // residual of the full saddle system on the free rows (the ion rows hold exactly):
-//   r_F = -r.E0 - (-(M q)_F + Psi'_body),   r_B = Q - sum of the body's charges
+//   r_bead = -r.E0 - (-(M q)_bead + Psi'_body),   r_body = Q - sum of the body's charges
 __global__ void residual_kernel(int nfree, int nmb, int nk, int n, int R, const int* __restrict__ free_idx,
-                                const int* __restrict__ mb_of_free, const int* __restrict__ free_off,
-                                const int* __restrict__ mb_body, const double* __restrict__ rel,
+                                const int* __restrict__ free_unk, const int* __restrict__ bead_body,
+                                const int* __restrict__ body_unk, const int* __restrict__ mb_body,
+                                const int* __restrict__ mb_unk, const int* __restrict__ mb_first,
+                                const int* __restrict__ mb_cnt, const double* __restrict__ rel,
                                 const double* __restrict__ E0, const double* __restrict__ Q,
                                 const double* __restrict__ psi, const double* __restrict__ x,
                                 double* __restrict__ res) {
@@ -423,7 +421,7 @@ __global__ void residual_kernel(int nfree, int nmb, int nk, int n, int R, const 
         const int j = free_idx[i];
         const double* e = E0 + 3 * r;
         const double rE = rel[3 * j] * e[0] + rel[3 * j + 1] * e[1] + rel[3 * j + 2] * e[2];
-        res[(size_t)r * nk + i] = -rE + psi[(size_t)r * n + j] - x[(size_t)r * nk + nfree + mb_of_free[i]];
+        res[(size_t)r * nk + free_unk[i]] = -rE + psi[(size_t)r * n + j] - x[(size_t)r * nk + body_unk[bead_body[j]]];
         return;
     }
     const long long top_pad = (top + 31) / 32 * 32;   // warp section aligned to hardware warps
@@ -434,47 +432,70 @@ __global__ void residual_kernel(int nfree, int nmb, int nk, int n, int R, const 
     if (wid >= (long long)nmb * R) return;
     const int r = (int)(wid / nmb), b = (int)(wid % nmb);
     double sm = 0.0;
-    for (int i = free_off[b] + lane; i < free_off[b + 1]; i += 32) sm += x[(size_t)r * nk + i];
+    for (int i = lane; i < mb_cnt[b]; i += 32) sm += x[(size_t)r * nk + mb_first[b] + i];
     sm = warp_sum(sm);
-    if (lane == 0) res[(size_t)r * nk + nfree + b] = Q[mb_body[b]] - sm;
+    if (lane == 0) res[(size_t)r * nk + mb_unk[b]] = Q[mb_body[b]] - sm;
 }
 
-__global__ void guess_kernel(int nfree, int nmb, int nk, int n, int nb, int R, const int* __restrict__ free_idx,
-                             const int* __restrict__ mb_body, const double* __restrict__ q_in,
-                             const double* __restrict__ psi_in, double* __restrict__ x) {
+// |b_s|^2 = sum over the configuration's beads of (r.E0_r)^2 + sum over its bodies of Q^2
+// (Eq. saddle right-hand side), grid: chunks x S
+__global__ void bfull_kernel(int R, const int* __restrict__ cfg_beads, const int* __restrict__ cfg_bodies,
+                             const double* __restrict__ rel, const double* __restrict__ E0,
+                             const double* __restrict__ Q, double* __restrict__ norms) {
+    __shared__ double sh[32];
+    const int s = blockIdx.y;
+    const int r = s % R, cfg = s / R;
+    const double* e = E0 + 3 * r;
+    const long long nb0 = cfg_beads[cfg], nb1 = cfg_beads[cfg + 1];
+    const long long q0 = cfg_bodies[cfg], q1 = cfg_bodies[cfg + 1];
+    const long long len = (nb1 - nb0) + (q1 - q0);
+    double acc = 0.0;
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < len; t += (long long)gridDim.x * blockDim.x) {
+        if (t < nb1 - nb0) {
+            const long long j = nb0 + t;
+            const double v = rel[3 * j] * e[0] + rel[3 * j + 1] * e[1] + rel[3 * j + 2] * e[2];
+            acc += v * v;
+        } else {
+            const double v = Q[q0 + t - (nb1 - nb0)];
+            acc += v * v;
+        }
+    }
+    const double sm = block_sum(acc, sh);
+    if (threadIdx.x == 0 && sm != 0.0) atomicAdd(norms + s, sm);
+}
+
+__global__ void guess_kernel(int nfree, int nk, int n, int R, const int* __restrict__ free_idx,
+                             const int* __restrict__ free_unk, const double* __restrict__ q_in,
+                             double* __restrict__ x) {
     const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (t >= (long long)nk * R) return;
-    const int r = (int)(t / nk), i = (int)(t % nk);
-    if (i < nfree)
-        x[t] = q_in[(size_t)r * n + free_idx[i]];
-    else
-        x[t] = psi_in ? psi_in[(size_t)r * nb + mb_body[i - nfree]] : 0.0;
+    if (t >= (long long)nfree * R) return;
+    const int r = (int)(t / nfree), i = (int)(t % nfree);
+    x[(size_t)r * nk + free_unk[i]] = q_in[(size_t)r * n + free_idx[i]];
 }
 
-// q_out (free beads from x, ions = Q); psi_out (multi-bead bodies from x, ions from M q of the
-// last full-system evaluation: Psi - Psi_0 = (M q)_ion - r.E0)
-__global__ void extract_kernel(int n, int nb, int nfree, int nk, int R, const int* __restrict__ bead_body,
-                               const int* __restrict__ off, const int* __restrict__ free_idx,
-                               const int* __restrict__ mb_body, const double* __restrict__ x,
+// q_out (free beads from x, ions = Q); psi_out per body (multi-bead bodies from x, ions from
+// M q of the last full-system evaluation: Psi - Psi_0 = (M q)_ion - r.E0)
+__global__ void extract_kernel(int n, int nb, int nk, int R, const int* __restrict__ bead_body,
+                               const int* __restrict__ off, const int* __restrict__ bead_unk,
+                               const int* __restrict__ body_unk, const double* __restrict__ x,
                                const double* __restrict__ Q, const double* __restrict__ rel,
                                const double* __restrict__ E0, const double* __restrict__ psi_tot,
                                double* __restrict__ q_out, double* __restrict__ psi_out) {
     const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (t < (long long)nfree * R) {
-        const int r = (int)(t / nfree), i = (int)(t % nfree);
-        q_out[(size_t)r * n + free_idx[i]] = x[(size_t)r * nk + i];
-        if (psi_out && i < nk - nfree) psi_out[(size_t)r * nb + mb_body[i]] = x[(size_t)r * nk + nfree + i];
-    }
     if (t < (long long)n * R) {
         const int r = (int)(t / n), j = (int)(t % n);
-        const int b = bead_body[j];
-        if (off[b + 1] - off[b] == 1) {
-            q_out[t] = Q[b];
-            if (psi_out) {
-                const double* e = E0 + 3 * r;
-                psi_out[(size_t)r * nb + b] =
-                    psi_tot[t] - (rel[3 * j] * e[0] + rel[3 * j + 1] * e[1] + rel[3 * j + 2] * e[2]);
-            }
+        const int u = bead_unk[j];
+        q_out[t] = u >= 0 ? x[(size_t)r * nk + u] : Q[bead_body[j]];
+    }
+    if (psi_out && t < (long long)nb * R) {
+        const int r = (int)(t / nb), b = (int)(t % nb);
+        const int u = body_unk[b];
+        if (u >= 0) {
+            psi_out[t] = x[(size_t)r * nk + u];
+        } else {
+            const int j = off[b];
+            const double* e = E0 + 3 * r;
+            psi_out[t] = psi_tot[(size_t)r * n + j] - (rel[3 * j] * e[0] + rel[3 * j + 1] * e[1] + rel[3 * j + 2] * e[2]);
         }
     }
 }
@@ -485,40 +506,45 @@ struct Solver {
     ibpme_ctx* c;
     Krylov* k;
     const SolveArgs& a;
-    int n, R, nk, nfree, nmb, nb, m;
+    int n, R, S, ncfg, nk, nfree, nmb, nb, m;
     int iters = 0, matvec64 = 0;
-    std::vector<double> bnorm;   // |b_full| per rhs
+    std::vector<double> bnorm;   // |b| per system
 
     Solver(ibpme_ctx* c_, const SolveArgs& a_) : c(c_), k(c_->kry), a(a_) {
         n = a.n;
         R = a.nrhs;
+        ncfg = c->bodies.ncfg;
+        S = ncfg * R;
         nfree = c->bodies.nfree;
         nmb = c->bodies.nmb;
         nb = c->bodies.nb;
-        nk = nfree + nmb;
+        nk = c->bodies.nk;
         m = a.restart;
     }
 
     cudaStream_t s() const { return c->stream; }
     double* D(DevBuf& b) const { return b.as<double>(); }
+    const int* I(const DevBuf& b) const { return b.as<int>(); }
+    bool single_block() const { return ncfg > 1 || nk <= kSmallMaxNk; }
 
     void alloc() {
         k->nk = nk;
         k->R = R;
+        k->S = S;
         k->m = m;
         k->nblk = div_up(nk > 0 ? nk : 1, kChunk);
         const size_t v = (size_t)R * (nk > 0 ? nk : 1);
         k->V.ensure(sizeof(double) * v * (m + 1));
-        k->H.ensure(sizeof(double) * (size_t)R * m * (m + 1));
-        k->cs.ensure(sizeof(double) * (size_t)R * m);
-        k->sn.ensure(sizeof(double) * (size_t)R * m);
-        k->g.ensure(sizeof(double) * (size_t)R * (m + 1));
-        k->y.ensure(sizeof(double) * (size_t)R * m);
+        k->H.ensure(sizeof(double) * (size_t)S * m * (m + 1));
+        k->cs.ensure(sizeof(double) * (size_t)S * m);
+        k->sn.ensure(sizeof(double) * (size_t)S * m);
+        k->g.ensure(sizeof(double) * (size_t)S * (m + 1));
+        k->y.ensure(sizeof(double) * (size_t)S * m);
         for (DevBuf* b : {&k->w, &k->x, &k->d, &k->r, &k->rc, &k->Ax}) b->ensure(sizeof(double) * v);
         k->part.ensure(sizeof(double) * (size_t)R * k->nblk * (m + 2));
-        k->scal.ensure(sizeof(double) * (size_t)R * S_COUNT);
-        k->active.ensure(sizeof(int) * R);
-        k->norms.ensure(sizeof(double) * R);
+        k->scal.ensure(sizeof(double) * (size_t)S * S_COUNT);
+        k->active.ensure(sizeof(int) * S);
+        k->norms.ensure(sizeof(double) * S);
         k->jdev.ensure(sizeof(int));
         const size_t full = (size_t)R * n;
         for (DevBuf* b : {&k->qop, &k->psi, &k->psi_tot, &k->qtot}) b->ensure(sizeof(double) * full);
@@ -529,30 +555,30 @@ struct Solver {
     void apply(int prec, const double* u, double* y, long long ustride = -1, const int* jdev = nullptr) {
         const BodyData& bd = c->bodies;
         if (ustride < 0) ustride = nk;
-        scatter_kernel<<<blocks_for((long long)nfree * R), 256, 0, s()>>>(nfree, ustride, n, R,
-                                                                          bd.free_idx.as<int>(), u, jdev, nk,
-                                                                          D(k->qop));
+        scatter_kernel<<<blocks_for((long long)nfree * R), 256, 0, s()>>>(nfree, ustride, n, R, I(bd.free_idx),
+                                                                          I(bd.free_unk), u, jdev, nk, D(k->qop));
         IBP_CHECK_LAUNCH();
         pme_apply(c, n, a.xw, D(k->qop), R, prec, D(k->psi), nullptr, true);
         const long long work = ((long long)nfree * R + 31) / 32 * 32 + 32LL * nmb * R;
-        assemble_kernel<<<blocks_for(work), 256, 0, s()>>>(nfree, nmb, nk, ustride, n, R, bd.free_idx.as<int>(),
-                                                           bd.mb_of_free.as<int>(), bd.free_off.as<int>(), D(k->psi),
-                                                           u, jdev, y);
+        assemble_kernel<<<blocks_for(work), 256, 0, s()>>>(nfree, nmb, nk, ustride, n, R, I(bd.free_idx),
+                                                           I(bd.free_unk), I(bd.bead_body), I(bd.body_unk),
+                                                           I(bd.mb_unk), I(bd.mb_first), I(bd.mb_cnt), D(k->psi), u,
+                                                           jdev, y);
         IBP_CHECK_LAUNCH();
     }
 
     // One Arnoldi iteration entirely on the device: w = A V_j, CGS2 against
-    // V_0..V_j, Givens on column j, V_{j+1} = w / h_{j+1,j}, j += 1.
+    // V_0..V_j, Givens on column j, V_{j+1} = w / h_{j+1,j}, j += 1 (every system).
     void iterate(int prec) {
         int* jd = k->jdev.as<int>();
         apply(prec, D(k->V), D(k->w), (long long)(m + 1) * nk, jd);
         ProfScope ps(ST_KRYLOV, s());
-        if (nk <= kSmallMaxNk) {
-            arnoldi_small_kernel<<<R, kSmallThreads, 0, s()>>>(nk, m, jd, D(k->V), D(k->w), D(k->H), D(k->cs),
-                                                               D(k->sn), D(k->g), D(k->scal), k->active.as<int>(),
-                                                               D(k->V));
+        if (single_block()) {
+            arnoldi_small_kernel<<<S, kSmallThreads, 0, s()>>>(nk, m, R, I(c->bodies.uo), jd, D(k->V), D(k->w),
+                                                               D(k->H), D(k->cs), D(k->sn), D(k->g), D(k->scal),
+                                                               k->active.as<int>(), D(k->V));
             IBP_CHECK_LAUNCH();
-            if (R > 1) {
+            if (S > 1) {
                 advance_kernel<<<1, 1, 0, s()>>>(jd);
                 IBP_CHECK_LAUNCH();
             }
@@ -576,30 +602,35 @@ struct Solver {
         IBP_CHECK_LAUNCH();
     }
 
+    static bool use_graphs() {
+        static const bool off = std::getenv("IBPME_NO_GRAPHS") != nullptr;
+        return !off;
+    }
+
     // The captured iteration for this precision, re-captured when any size,
     // buffer or the profiling mask differs from the last capture.
     cudaGraphExec_t iteration_graph(int prec) {
+        const BodyData& bd = c->bodies;
         const Mesh<float>& m32 = c->mesh32;
         const Mesh<double>& m64 = c->mesh64;
-        std::vector<long long> sig = {prec, R, nk, n, m, nfree, nmb, (long long)prof_mask(),
-                                      (long long)(size_t)k->V.p, (long long)(size_t)k->w.p, (long long)(size_t)k->qop.p,
-                                      (long long)(size_t)k->psi.p, (long long)(size_t)k->H.p,
-                                      (long long)(size_t)c->psi_r.p, (long long)(size_t)c->psi_k.p,
-                                      (long long)(size_t)c->scalars.p, (long long)(size_t)c->near.col.p,
-                                      (long long)(size_t)c->near.val.p, (long long)(size_t)c->near.rowptr.p,
-                                      (long long)(size_t)a.xw, (long long)(size_t)c->bodies.free_idx.p,
-                                      (long long)(size_t)c->bodies.mb_of_free.p,
-                                      (long long)(size_t)c->bodies.free_off.p,
-                                      (long long)(size_t)(prec == IBPME_MIXED ? m32.grid.p : m64.grid.p),
-                                      (long long)(size_t)(prec == IBPME_MIXED ? m32.work.p : m64.work.p)};
+        // make every lazily created resource exist before capture (this may grow the meshes)
+        if (prec == IBPME_MIXED) c->mesh32.plans(R * ncfg, s()); else c->mesh64.plans(R * ncfg, s());
+        auto P = [](const void* p) { return (long long)(size_t)p; };
+        std::vector<long long> sig = {prec, R, S, ncfg, nk, n, m, nfree, nmb, (long long)prof_mask(),
+                                      P(k->V.p), P(k->w.p), P(k->qop.p), P(k->psi.p), P(k->H.p), P(k->scal.p),
+                                      P(c->psi_r.p), P(c->psi_k.p), P(c->scalars.p), P(c->near.col.p),
+                                      P(c->near.val.p), P(c->near.rowptr.p), P(a.xw), P(bd.free_idx.p),
+                                      P(bd.free_unk.p), P(bd.bead_body.p), P(bd.body_unk.p), P(bd.mb_unk.p),
+                                      P(bd.mb_first.p), P(bd.mb_cnt.p), P(bd.uo.p), P(c->bcfg),
+                                      P(prec == IBPME_MIXED ? m32.grid.p : m64.grid.p),
+                                      P(prec == IBPME_MIXED ? m32.spec.p : m64.spec.p),
+                                      P(prec == IBPME_MIXED ? m32.work.p : m64.work.p)};
         const int gi = prec == IBPME_MIXED ? 1 : 0;
         if (k->exec[gi] && k->sig[gi] == sig) return k->exec[gi];
         if (k->exec[gi]) {
             IBP_CUDA(cudaGraphExecDestroy(k->exec[gi]));
             k->exec[gi] = nullptr;
         }
-        // make every lazily created resource exist before capture
-        if (prec == IBPME_MIXED) c->mesh32.plans(R, s()); else c->mesh64.plans(R, s());
         prof_capture_begin(gi);
         const long long launches0 = launch_count();
         cudaGraph_t graph = nullptr;
@@ -625,12 +656,7 @@ struct Solver {
         return exec;
     }
 
-    static bool use_graphs() {
-        static const bool off = std::getenv("IBPME_NO_GRAPHS") != nullptr;
-        return !off;
-    }
-
-    // host copy of R doubles
+    // host copy of `count` doubles, `stride` apart
     std::vector<double> fetch(const double* dev, int count, size_t stride = 1) {
         const size_t elems = (size_t)(count - 1) * stride + 1;
         double* h = static_cast<double*>(pinned_host(c, sizeof(double) * elems));
@@ -641,71 +667,73 @@ struct Solver {
         return out;
     }
 
+    // |v| per system (k->norms keeps the squares)
     std::vector<double> norms(const double* v) {
-        IBP_CUDA(cudaMemsetAsync(k->norms.p, 0, sizeof(double) * R, s()));
-        dim3 grid(std::min(blocks_for(nk), 152 * 4), R);
-        norm2_kernel<<<grid, 256, 0, s()>>>(nk, v, D(k->norms));
+        IBP_CUDA(cudaMemsetAsync(k->norms.p, 0, sizeof(double) * S, s()));
+        const int per = nk / std::max(1, ncfg) + 1;
+        const int chunks = std::max(1, std::min(blocks_for(per), 608 / S + 1));
+        norm2_kernel<<<dim3(chunks, S), 256, 0, s()>>>(nk, R, I(c->bodies.uo), v, D(k->norms));
         IBP_CHECK_LAUNCH();
-        std::vector<double> h = fetch(D(k->norms), R);
+        std::vector<double> h = fetch(D(k->norms), S);
         for (double& e : h) e = std::sqrt(e);
         return h;
     }
 
     void set_active(const std::vector<int>& act) {
-        int* h = static_cast<int*>(pinned_host(c, sizeof(int) * R));
-        for (int r = 0; r < R; ++r) h[r] = act[r];
-        IBP_CUDA(cudaMemcpyAsync(k->active.p, h, sizeof(int) * R, cudaMemcpyHostToDevice, s()));
+        int* h = static_cast<int*>(pinned_host(c, sizeof(int) * S));
+        for (int i = 0; i < S; ++i) h[i] = act[i];
+        IBP_CUDA(cudaMemcpyAsync(k->active.p, h, sizeof(int) * S, cudaMemcpyHostToDevice, s()));
         IBP_CUDA(cudaStreamSynchronize(s()));   // the pinned scratch is reused right after
     }
 
     // Residual of the full saddle system at the iterate x with the operator of the
     // given precision: one PME evaluation of all charges (free beads and ions).
-    // Leaves r, and psi_tot = M q_total for the ions' potentials.  Returns |r| per rhs.
+    // Leaves r, and psi_tot = M q_total for the ions' potentials.  Returns |r| per system.
     // With fit_psi the body potentials of x are first replaced by their
     // least-squares fit to the charges (initial guess).
     std::vector<double> residual(int prec, bool fit_psi = false) {
         const BodyData& bd = c->bodies;
-        compose_kernel<<<blocks_for((long long)n * R), 256, 0, s()>>>(n, nk, R, bd.free_pos.as<int>(),
-                                                                       bd.bead_body.as<int>(), bd.Q.as<double>(),
-                                                                       D(k->x), D(k->qtot));
+        compose_kernel<<<blocks_for((long long)n * R), 256, 0, s()>>>(n, nk, R, I(bd.bead_unk), I(bd.bead_body),
+                                                                       bd.Q.as<double>(), D(k->x), D(k->qtot));
         IBP_CHECK_LAUNCH();
         pme_apply(c, n, a.xw, D(k->qtot), R, prec, D(k->psi_tot), nullptr, true);
         if (prec == IBPME_FP64) ++matvec64;
         if (fit_psi && nmb > 0) {
-            fit_psi_kernel<<<blocks_for(32LL * nmb * R), 256, 0, s()>>>(nfree, nmb, nk, n, R, bd.free_idx.as<int>(),
-                                                                        bd.free_off.as<int>(), bd.rel.as<double>(),
-                                                                        a.E0, D(k->psi_tot), D(k->x));
+            fit_psi_kernel<<<blocks_for(32LL * nmb * R), 256, 0, s()>>>(nmb, nk, n, R, I(bd.mb_body), I(bd.mb_unk),
+                                                                        I(bd.off), bd.rel.as<double>(), a.E0,
+                                                                        D(k->psi_tot), D(k->x));
             IBP_CHECK_LAUNCH();
         }
         const long long work = ((long long)nfree * R + 31) / 32 * 32 + 32LL * nmb * R;
-        residual_kernel<<<blocks_for(work), 256, 0, s()>>>(nfree, nmb, nk, n, R, bd.free_idx.as<int>(),
-                                                           bd.mb_of_free.as<int>(), bd.free_off.as<int>(),
-                                                           bd.mb_body.as<int>(), bd.rel.as<double>(), a.E0,
-                                                           bd.Q.as<double>(), D(k->psi_tot), D(k->x), D(k->r));
+        residual_kernel<<<blocks_for(work), 256, 0, s()>>>(nfree, nmb, nk, n, R, I(bd.free_idx), I(bd.free_unk),
+                                                           I(bd.bead_body), I(bd.body_unk), I(bd.mb_body),
+                                                           I(bd.mb_unk), I(bd.mb_first), I(bd.mb_cnt),
+                                                           bd.rel.as<double>(), a.E0, bd.Q.as<double>(),
+                                                           D(k->psi_tot), D(k->x), D(k->r));
         IBP_CHECK_LAUNCH();
         return norms(D(k->r));
     }
 
-    // GMRES on A(prec) d = rhs (d = 0 on entry), cycles of at most m iterations,
-    // until |rhs - A d| <= target per rhs or the iteration budget is spent.
+    // GMRES on A(prec) d = rhs (d = 0 on entry) for every system, cycles of at most m
+    // iterations, until |rhs - A d| <= target per system or the iteration budget is spent.
     void gmres(int prec, const double* rhs, double* dd, const std::vector<double>& target) {
         const long long len = (long long)nk * R;
         IBP_CUDA(cudaMemsetAsync(dd, 0, sizeof(double) * len, s()));
         const double* res_vec = rhs;   // residual the next cycle starts from
         std::vector<double> rn = norms(rhs);
         for (;;) {
-            std::vector<int> act(R);
+            std::vector<int> act(S);
             bool any = false;
-            for (int r = 0; r < R; ++r) {
-                act[r] = rn[r] > target[r] ? 1 : 0;
-                any = any || act[r];
+            for (int i = 0; i < S; ++i) {
+                act[i] = rn[i] > target[i] ? 1 : 0;
+                any = any || act[i];
             }
             if (!any || iters >= a.max_iter) return;
             set_active(act);
             // V_0 = res / |res|, g = |res| e_1 (k->norms still holds |res|^2 from norms())
-            const long long work = std::max(len, (long long)R * (m + 1));
-            start_kernel<<<blocks_for(work), 256, 0, s()>>>(nk, m, R, res_vec, D(k->norms), k->active.as<int>(),
-                                                             D(k->V), D(k->g), D(k->scal));
+            const long long work = std::max(len, (long long)S * (m + 1));
+            start_kernel<<<blocks_for(work), 256, 0, s()>>>(nk, m, R, S, I(c->bodies.unk_cfg), res_vec, D(k->norms),
+                                                             k->active.as<int>(), D(k->V), D(k->g), D(k->scal));
             IBP_CHECK_LAUNCH();
             int kk = 0;
             bool cycle_converged = false;
@@ -723,20 +751,21 @@ struct Solver {
                 if (prec == IBPME_FP64) ++matvec64;
                 ++iters;
                 kk = j + 1;
-                std::vector<double> est = fetch(D(k->scal) + S_RES, R, S_COUNT);   // synchronises
+                std::vector<double> est = fetch(D(k->scal) + S_RES, S, S_COUNT);   // synchronises
                 if (graphs) prof_graph_collect(gi);
                 bool done = true;
-                for (int r = 0; r < R; ++r) {
-                    if (!act[r]) continue;
-                    if (!std::isfinite(est[r])) fail(IBPME_ERR_NONFINITE, "non-finite Krylov residual estimate");
-                    if (!(est[r] <= target[r])) done = false;
+                for (int i = 0; i < S; ++i) {
+                    if (!act[i]) continue;
+                    if (!std::isfinite(est[i])) fail(IBPME_ERR_NONFINITE, "non-finite Krylov residual estimate");
+                    if (!(est[i] <= target[i])) done = false;
                 }
                 cycle_converged = done;
                 if (done || iters >= a.max_iter) break;
             }
-            trisolve_kernel<<<R, 32, 0, s()>>>(m, kk, D(k->H), D(k->g), k->active.as<int>(), D(k->y));
+            trisolve_kernel<<<S, 32, 0, s()>>>(m, kk, D(k->H), D(k->g), k->active.as<int>(), D(k->y));
             IBP_CHECK_LAUNCH();
-            xupdate_kernel<<<blocks_for(len), 256, 0, s()>>>(nk, m, kk, R, D(k->V), D(k->y), dd);
+            xupdate_kernel<<<blocks_for(len), 256, 0, s()>>>(nk, m, kk, R, I(c->bodies.unk_cfg), D(k->V), D(k->y),
+                                                             dd);
             IBP_CHECK_LAUNCH();
             // the estimate reached the target: the caller's full-system residual decides
             if (cycle_converged || iters >= a.max_iter) return;
@@ -755,22 +784,22 @@ struct Solver {
         alloc();
         const long long len = (long long)nk * R;
         IBP_CUDA(cudaMemsetAsync(k->qop.p, 0, sizeof(double) * (size_t)R * n, s()));   // ions stay 0
-        // |b| of the full system of Eq. saddle, b = [-r.E0 ; Q]
-        IBP_CUDA(cudaMemsetAsync(k->norms.p, 0, sizeof(double) * R, s()));
-        bfull_kernel<<<dim3(std::min(blocks_for((long long)n + nb), 152 * 4), R), 256, 0, s()>>>(
-            n, nb, R, bd.rel.as<double>(), a.E0, bd.Q.as<double>(), D(k->norms));
+        // |b| of the full system of Eq. saddle, b = [-r.E0 ; Q], per system
+        IBP_CUDA(cudaMemsetAsync(k->norms.p, 0, sizeof(double) * S, s()));
+        const int per = (n + nb) / ncfg + 1;
+        bfull_kernel<<<dim3(std::max(1, std::min(blocks_for(per), 608 / S + 1)), S), 256, 0, s()>>>(
+            R, I(bd.cfg_beads), I(bd.cfg_bodies), bd.rel.as<double>(), a.E0, bd.Q.as<double>(), D(k->norms));
         IBP_CHECK_LAUNCH();
-        bnorm = fetch(D(k->norms), R);
+        bnorm = fetch(D(k->norms), S);
         for (double& e : bnorm) e = std::sqrt(e);
-        std::vector<double> tol_abs(R);
-        for (int r = 0; r < R; ++r) tol_abs[r] = a.rtol * bnorm[r];
+        std::vector<double> tol_abs(S);
+        for (int i = 0; i < S; ++i) tol_abs[i] = a.rtol * bnorm[i];
 
+        if (nk > 0) IBP_CUDA(cudaMemsetAsync(k->x.p, 0, sizeof(double) * len, s()));
         if (nk > 0 && a.user_guess) {
-            guess_kernel<<<blocks_for(len), 256, 0, s()>>>(nfree, nmb, nk, n, nb, R, bd.free_idx.as<int>(),
-                                                           bd.mb_body.as<int>(), a.q, nullptr, D(k->x));
+            guess_kernel<<<blocks_for((long long)nfree * R), 256, 0, s()>>>(nfree, nk, n, R, I(bd.free_idx),
+                                                                            I(bd.free_unk), a.q, D(k->x));
             IBP_CHECK_LAUNCH();
-        } else if (nk > 0) {
-            IBP_CUDA(cudaMemsetAsync(k->x.p, 0, sizeof(double) * len, s()));
         }
         // Iterative refinement on the full system.  Every residual uses the FP64
         // operator; in mixed precision the corrections come from the FP32-mesh
@@ -782,27 +811,26 @@ struct Solver {
         if (a.learned && nk > 0) {
             // the learned guess must beat the zero guess, whose residual is |b| up to the ions' share
             bool worse = false;
-            for (int r = 0; r < R; ++r)
-                if (!(res[r] < bnorm[r])) worse = true;
+            for (int i = 0; i < S; ++i)
+                if (!(res[i] < bnorm[i])) worse = true;
             if (worse) {
                 IBP_CUDA(cudaMemsetAsync(k->x.p, 0, sizeof(double) * len, s()));
                 res = residual(IBPME_FP64, true);
                 fell_back = 1;
             }
         }
-        double init_worst = 0.0;
-        for (int r = 0; r < R; ++r) init_worst = std::max(init_worst, bnorm[r] > 0 ? res[r] / bnorm[r] : res[r]);
+        auto relres = [&](int i) { return bnorm[i] > 0 ? res[i] / bnorm[i] : res[i]; };
+        std::vector<double> init(S);
+        for (int i = 0; i < S; ++i) init[i] = relres(i);
         const bool verbose = std::getenv("IBPME_VERBOSE") != nullptr;
         if (verbose)
-            for (int r = 0; r < R; ++r)
-                std::fprintf(stderr, "[ibpme] start rhs %d: nk %d |b| = %.6e |r0|/|b| = %.3e\n", r, nk, bnorm[r],
-                             res[r] / bnorm[r]);
-        bool res_is_fp64 = true;
+            for (int i = 0; i < S; ++i)
+                std::fprintf(stderr, "[ibpme] start system %d: nk %d |b| = %.6e |r0|/|b| = %.3e\n", i, nk, bnorm[i],
+                             relres(i));
         int outer = 0;
         auto converged = [&]() {
-            if (!res_is_fp64) return false;
-            for (int r = 0; r < R; ++r)
-                if (!(res[r] <= tol_abs[r])) return false;
+            for (int i = 0; i < S; ++i)
+                if (!(res[i] <= tol_abs[i])) return false;
             return true;
         };
         while (nk > 0 && !converged() && iters < a.max_iter && outer < 50) {
@@ -810,39 +838,39 @@ struct Solver {
             // FP64: plain restarted GMRES (one cycle per outer step, the same operator).
             // Mixed: the FP32-mesh solve aims below the target so that a single FP64
             // check usually confirms it.
-            std::vector<double> tgt(R);
-            for (int r = 0; r < R; ++r) tgt[r] = (mixed ? 0.25 : 0.9) * tol_abs[r];
+            std::vector<double> tgt(S);
+            for (int i = 0; i < S; ++i) tgt[i] = (mixed ? 0.25 : 0.9) * tol_abs[i];
             gmres(a.prec, D(k->r), D(k->d), tgt);
             axpby_kernel<<<blocks_for(len), 256, 0, s()>>>(len, 1.0, D(k->x), 1.0, D(k->d), D(k->x));
             IBP_CHECK_LAUNCH();
             res = residual(IBPME_FP64);
-            res_is_fp64 = true;
             if (verbose)
-                for (int r = 0; r < R; ++r)
-                    std::fprintf(stderr, "[ibpme] outer %d rhs %d: iters %d  |r|/|b| = %.3e (fp64 matvecs %d)\n",
-                                 outer, r, iters, res[r] / bnorm[r], matvec64);
+                for (int i = 0; i < S; ++i)
+                    std::fprintf(stderr, "[ibpme] outer %d system %d: iters %d  |r|/|b| = %.3e (fp64 matvecs %d)\n",
+                                 outer, i, iters, relres(i), matvec64);
         }
-        if (!res_is_fp64) res = residual(IBPME_FP64);
         // outputs
-        extract_kernel<<<blocks_for((long long)n * R), 256, 0, s()>>>(
-            n, nb, nfree, nk, R, bd.bead_body.as<int>(), bd.off.as<int>(), bd.free_idx.as<int>(),
-            bd.mb_body.as<int>(), D(k->x), bd.Q.as<double>(), bd.rel.as<double>(), a.E0, D(k->psi_tot), a.q, a.psi);
+        extract_kernel<<<blocks_for((long long)std::max(n, nb) * R), 256, 0, s()>>>(
+            n, nb, nk, R, I(bd.bead_body), I(bd.off), I(bd.bead_unk), I(bd.body_unk), D(k->x), bd.Q.as<double>(),
+            bd.rel.as<double>(), a.E0, D(k->psi_tot), a.q, a.psi);
         IBP_CHECK_LAUNCH();
-        double worst = 0.0;
-        for (int r = 0; r < R; ++r) {
-            const double rel = bnorm[r] > 0 ? res[r] / bnorm[r] : res[r];
-            if (!std::isfinite(rel)) {
-                worst = rel;
-                break;
+        // statistics per configuration (worst of its right-hand sides)
+        for (int cfg = 0; cfg < ncfg; ++cfg) {
+            double worst = 0.0, iw = 0.0;
+            for (int r = 0; r < R; ++r) {
+                const int i = cfg * R + r;
+                const double v = relres(i);
+                worst = std::isfinite(v) && std::isfinite(worst) ? std::max(worst, v) : NAN;
+                iw = std::max(iw, init[i]);
             }
-            worst = std::max(worst, rel);
+            ibpme_solve_stats& o = st[cfg];
+            o.iters = iters;
+            o.outer = outer;
+            o.matvecs_fp64 = matvec64;
+            o.rel_residual = worst;
+            o.fell_back = fell_back;
+            o.init_rel_residual = iw;
         }
-        st->iters = iters;
-        st->outer = outer;
-        st->matvecs_fp64 = matvec64;
-        st->rel_residual = worst;
-        st->fell_back = fell_back;
-        st->init_rel_residual = init_worst;
     }
 };
 

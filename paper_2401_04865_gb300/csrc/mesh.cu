@@ -50,8 +50,8 @@ __device__ __forceinline__ void stencil_setup(const MeshGeom& g, const double* _
 // P^2 (j, k) rows; NR right-hand sides share the window weights.
 template <typename T, int NR, int WPB>
 __global__ void __launch_bounds__(32 * kWarpsPerBlock)
-spread_kernel(int n, const double* __restrict__ xw, const double* __restrict__ q, MeshGeom g,
-              T* __restrict__ grid) {
+spread_kernel(int n, const double* __restrict__ xw, const double* __restrict__ q, const int* __restrict__ bead_cfg,
+              MeshGeom g, T* __restrict__ grid) {
     __shared__ T s_w[kWarpsPerBlock][3][kMaxP];
     __shared__ int s_idx[kWarpsPerBlock][3][kMaxP];
     const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -65,6 +65,7 @@ spread_kernel(int n, const double* __restrict__ xw, const double* __restrict__ q
     if (rsub >= rows_per) return;
     const T wx = s_w[wib][0][i];
     const int ix = s_idx[wib][0][i];
+    if (bead_cfg) grid += (size_t)bead_cfg[bead] * NR * g.G;
     T qc[NR];
 #pragma unroll
     for (int r = 0; r < NR; ++r) qc[r] = (T)(g.c * q[(size_t)r * n + bead]) * wx;
@@ -91,8 +92,8 @@ spread_kernel(int n, const double* __restrict__ xw, const double* __restrict__ q
 // shared memory.
 template <typename T, int NR, int WPB, bool GRAD>
 __global__ void __launch_bounds__(32 * kWarpsPerBlock)
-gather_kernel(int n, const double* __restrict__ xw, MeshGeom g, const T* __restrict__ grid,
-              double* __restrict__ psi, double* __restrict__ E) {
+gather_kernel(int n, const double* __restrict__ xw, const int* __restrict__ bead_cfg, MeshGeom g,
+              const T* __restrict__ grid, double* __restrict__ psi, double* __restrict__ E) {
     __shared__ T s_w[kWarpsPerBlock][3][kMaxP];
     __shared__ T s_d[kWarpsPerBlock][3][kMaxP];
     __shared__ int s_idx[kWarpsPerBlock][3][kMaxP];
@@ -114,6 +115,7 @@ gather_kernel(int n, const double* __restrict__ xw, MeshGeom g, const T* __restr
         wx = s_w[wib][0][i];
         if (GRAD) dx = s_d[wib][0][i];
         const int ix = s_idx[wib][0][i];
+        if (bead_cfg) grid += (size_t)bead_cfg[bead] * NR * g.G;
         const int P2 = P * P;
         const int step = rows_per * WPB;
         int row = rsub + rows_per * part;
@@ -195,64 +197,66 @@ int warps_per_bead(int n) {
 }
 
 template <typename T, int NR, int WPB>
-void launch_spread(int n, const double* xw, const double* q, const MeshGeom& g, T* grid, cudaStream_t s) {
+void launch_spread(int n, const double* xw, const double* q, const int* cfg, const MeshGeom& g, T* grid,
+                   cudaStream_t s) {
     const int blocks = div_up((long long)n * WPB, kWarpsPerBlock);
-    spread_kernel<T, NR, WPB><<<blocks, 32 * kWarpsPerBlock, 0, s>>>(n, xw, q, g, grid);
+    spread_kernel<T, NR, WPB><<<blocks, 32 * kWarpsPerBlock, 0, s>>>(n, xw, q, cfg, g, grid);
 }
 
 template <typename T, int NR>
-void launch_spread_w(int n, const double* xw, const double* q, const MeshGeom& g, T* grid, cudaStream_t s) {
+void launch_spread_w(int n, const double* xw, const double* q, const int* cfg, const MeshGeom& g, T* grid,
+                     cudaStream_t s) {
     switch (warps_per_bead(n)) {
-        case 1: launch_spread<T, NR, 1>(n, xw, q, g, grid, s); break;
-        case 2: launch_spread<T, NR, 2>(n, xw, q, g, grid, s); break;
-        default: launch_spread<T, NR, 4>(n, xw, q, g, grid, s); break;
+        case 1: launch_spread<T, NR, 1>(n, xw, q, cfg, g, grid, s); break;
+        case 2: launch_spread<T, NR, 2>(n, xw, q, cfg, g, grid, s); break;
+        default: launch_spread<T, NR, 4>(n, xw, q, cfg, g, grid, s); break;
     }
 }
 
 template <typename T>
-void spread_dispatch(int n, const double* xw, const double* q, int nrhs, const MeshGeom& g, T* grid,
+void spread_dispatch(int n, const double* xw, const double* q, int nrhs, const int* cfg, const MeshGeom& g, T* grid,
                      cudaStream_t s) {
     switch (nrhs) {
-        case 1: launch_spread_w<T, 1>(n, xw, q, g, grid, s); break;
-        case 2: launch_spread_w<T, 2>(n, xw, q, g, grid, s); break;
-        case 3: launch_spread_w<T, 3>(n, xw, q, g, grid, s); break;
-        case 4: launch_spread_w<T, 4>(n, xw, q, g, grid, s); break;
-        case 5: launch_spread_w<T, 5>(n, xw, q, g, grid, s); break;
-        case 6: launch_spread_w<T, 6>(n, xw, q, g, grid, s); break;
-        case 7: launch_spread_w<T, 7>(n, xw, q, g, grid, s); break;
-        default: launch_spread_w<T, 8>(n, xw, q, g, grid, s); break;
+        case 1: launch_spread_w<T, 1>(n, xw, q, cfg, g, grid, s); break;
+        case 2: launch_spread_w<T, 2>(n, xw, q, cfg, g, grid, s); break;
+        case 3: launch_spread_w<T, 3>(n, xw, q, cfg, g, grid, s); break;
+        case 4: launch_spread_w<T, 4>(n, xw, q, cfg, g, grid, s); break;
+        case 5: launch_spread_w<T, 5>(n, xw, q, cfg, g, grid, s); break;
+        case 6: launch_spread_w<T, 6>(n, xw, q, cfg, g, grid, s); break;
+        case 7: launch_spread_w<T, 7>(n, xw, q, cfg, g, grid, s); break;
+        default: launch_spread_w<T, 8>(n, xw, q, cfg, g, grid, s); break;
     }
 }
 
 template <typename T, int NR, int WPB, bool GRAD>
-void launch_gather(int n, const double* xw, const MeshGeom& g, const T* grid, double* psi, double* E,
+void launch_gather(int n, const double* xw, const int* cfg, const MeshGeom& g, const T* grid, double* psi, double* E,
                    cudaStream_t s) {
     const int blocks = div_up((long long)n * WPB, kWarpsPerBlock);
-    gather_kernel<T, NR, WPB, GRAD><<<blocks, 32 * kWarpsPerBlock, 0, s>>>(n, xw, g, grid, psi, E);
+    gather_kernel<T, NR, WPB, GRAD><<<blocks, 32 * kWarpsPerBlock, 0, s>>>(n, xw, cfg, g, grid, psi, E);
 }
 
 template <typename T, int NR, bool GRAD>
-void launch_gather_w(int n, const double* xw, const MeshGeom& g, const T* grid, double* psi, double* E,
-                     cudaStream_t s) {
+void launch_gather_w(int n, const double* xw, const int* cfg, const MeshGeom& g, const T* grid, double* psi,
+                     double* E, cudaStream_t s) {
     switch (warps_per_bead(n)) {
-        case 1: launch_gather<T, NR, 1, GRAD>(n, xw, g, grid, psi, E, s); break;
-        case 2: launch_gather<T, NR, 2, GRAD>(n, xw, g, grid, psi, E, s); break;
-        default: launch_gather<T, NR, 4, GRAD>(n, xw, g, grid, psi, E, s); break;
+        case 1: launch_gather<T, NR, 1, GRAD>(n, xw, cfg, g, grid, psi, E, s); break;
+        case 2: launch_gather<T, NR, 2, GRAD>(n, xw, cfg, g, grid, psi, E, s); break;
+        default: launch_gather<T, NR, 4, GRAD>(n, xw, cfg, g, grid, psi, E, s); break;
     }
 }
 
 template <typename T, bool GRAD>
-void gather_dispatch(int n, const double* xw, int nrhs, const MeshGeom& g, const T* grid, double* psi, double* E,
-                     cudaStream_t s) {
+void gather_dispatch(int n, const double* xw, int nrhs, const int* cfg, const MeshGeom& g, const T* grid,
+                     double* psi, double* E, cudaStream_t s) {
     switch (nrhs) {
-        case 1: launch_gather_w<T, 1, GRAD>(n, xw, g, grid, psi, E, s); break;
-        case 2: launch_gather_w<T, 2, GRAD>(n, xw, g, grid, psi, E, s); break;
-        case 3: launch_gather_w<T, 3, GRAD>(n, xw, g, grid, psi, E, s); break;
-        case 4: launch_gather_w<T, 4, GRAD>(n, xw, g, grid, psi, E, s); break;
-        case 5: launch_gather_w<T, 5, GRAD>(n, xw, g, grid, psi, E, s); break;
-        case 6: launch_gather_w<T, 6, GRAD>(n, xw, g, grid, psi, E, s); break;
-        case 7: launch_gather_w<T, 7, GRAD>(n, xw, g, grid, psi, E, s); break;
-        default: launch_gather_w<T, 8, GRAD>(n, xw, g, grid, psi, E, s); break;
+        case 1: launch_gather_w<T, 1, GRAD>(n, xw, cfg, g, grid, psi, E, s); break;
+        case 2: launch_gather_w<T, 2, GRAD>(n, xw, cfg, g, grid, psi, E, s); break;
+        case 3: launch_gather_w<T, 3, GRAD>(n, xw, cfg, g, grid, psi, E, s); break;
+        case 4: launch_gather_w<T, 4, GRAD>(n, xw, cfg, g, grid, psi, E, s); break;
+        case 5: launch_gather_w<T, 5, GRAD>(n, xw, cfg, g, grid, psi, E, s); break;
+        case 6: launch_gather_w<T, 6, GRAD>(n, xw, cfg, g, grid, psi, E, s); break;
+        case 7: launch_gather_w<T, 7, GRAD>(n, xw, cfg, g, grid, psi, E, s); break;
+        default: launch_gather_w<T, 8, GRAD>(n, xw, cfg, g, grid, psi, E, s); break;
     }
 }
 
@@ -306,106 +310,117 @@ int grid_blocks(long long work, int threads) {
 }  // namespace
 
 template <typename T>
-void Mesh<T>::init(const MeshGeom& geom, int max_rhs, double xi, double eta, double a, cudaStream_t s) {
+void Mesh<T>::init(const MeshGeom& geom, int channels, double xi, double eta, double a, cudaStream_t s) {
     g = geom;
-    rcap = max_rhs;
-    grid.ensure(sizeof(T) * (size_t)g.G * rcap);
-    spec.ensure(sizeof(typename Cplx<T>::type) * (size_t)g.Gc * rcap);
+    rcap = 0;
+    ensure_channels(channels);
     green.ensure(sizeof(T) * (size_t)g.Gc);
     green_kernel<T><<<grid_blocks(g.Gc, 256), 256, 0, s>>>(g, xi, eta, a, green.as<T>());
     IBP_CHECK_LAUNCH();
 }
 
 template <typename T>
-void Mesh<T>::plans(int nrhs, cudaStream_t s) {
-    if (nrhs < 1 || nrhs > rcap) fail(IBPME_ERR_ARG, "nrhs %d outside 1..%d", nrhs, rcap);
-    if (!have[nrhs]) {
+void Mesh<T>::ensure_channels(int ch) {
+    if (ch <= rcap) return;
+    grid.ensure(sizeof(T) * (size_t)g.G * ch);
+    spec.ensure(sizeof(typename Cplx<T>::type) * (size_t)g.Gc * ch);
+    rcap = ch;
+}
+
+template <typename T>
+void Mesh<T>::plans(int ch, cudaStream_t s) {
+    if (ch < 1) fail(IBPME_ERR_ARG, "channel count %d < 1", ch);
+    ensure_channels(ch);
+    auto it = plan.find(ch);
+    if (it == plan.end()) {
         int dims[3] = {g.N[2], g.N[1], g.N[0]};   // slowest to fastest: z, y, x
         const cufftType tf = sizeof(T) == 8 ? CUFFT_D2Z : CUFFT_R2C;
         const cufftType tb = sizeof(T) == 8 ? CUFFT_Z2D : CUFFT_C2R;
         size_t ws1 = 0, ws2 = 0;
-        IBP_CUFFT(cufftCreate(&r2c[nrhs]));
-        IBP_CUFFT(cufftCreate(&c2r[nrhs]));
-        IBP_CUFFT(cufftSetAutoAllocation(r2c[nrhs], 0));
-        IBP_CUFFT(cufftSetAutoAllocation(c2r[nrhs], 0));
-        IBP_CUFFT(cufftMakePlanMany(r2c[nrhs], 3, dims, nullptr, 1, (int)g.G, nullptr, 1, (int)g.Gc, tf,
-                                    nrhs, &ws1));
-        IBP_CUFFT(cufftMakePlanMany(c2r[nrhs], 3, dims, nullptr, 1, (int)g.Gc, nullptr, 1, (int)g.G, tb,
-                                    nrhs, &ws2));
-        have[nrhs] = true;
+        cufftHandle f = 0, b = 0;
+        IBP_CUFFT(cufftCreate(&f));
+        IBP_CUFFT(cufftCreate(&b));
+        IBP_CUFFT(cufftSetAutoAllocation(f, 0));
+        IBP_CUFFT(cufftSetAutoAllocation(b, 0));
+        IBP_CUFFT(cufftMakePlanMany(f, 3, dims, nullptr, 1, (int)g.G, nullptr, 1, (int)g.Gc, tf, ch, &ws1));
+        IBP_CUFFT(cufftMakePlanMany(b, 3, dims, nullptr, 1, (int)g.Gc, nullptr, 1, (int)g.G, tb, ch, &ws2));
+        it = plan.emplace(ch, std::make_pair(f, b)).first;
         const size_t need = ws1 > ws2 ? ws1 : ws2;
         if (need > work.bytes) {
             work.ensure(need);
-            for (int r = 1; r <= kMaxRhs; ++r)
-                if (have[r]) {
-                    IBP_CUFFT(cufftSetWorkArea(r2c[r], work.p));
-                    IBP_CUFFT(cufftSetWorkArea(c2r[r], work.p));
-                }
+            for (auto& kv : plan) {
+                IBP_CUFFT(cufftSetWorkArea(kv.second.first, work.p));
+                IBP_CUFFT(cufftSetWorkArea(kv.second.second, work.p));
+            }
         } else {
-            IBP_CUFFT(cufftSetWorkArea(r2c[nrhs], work.p));
-            IBP_CUFFT(cufftSetWorkArea(c2r[nrhs], work.p));
+            IBP_CUFFT(cufftSetWorkArea(f, work.p));
+            IBP_CUFFT(cufftSetWorkArea(b, work.p));
         }
     }
-    IBP_CUFFT(cufftSetStream(r2c[nrhs], s));
-    IBP_CUFFT(cufftSetStream(c2r[nrhs], s));
+    IBP_CUFFT(cufftSetStream(it->second.first, s));
+    IBP_CUFFT(cufftSetStream(it->second.second, s));
 }
 
 template <typename T>
 void Mesh<T>::destroy() {
-    for (int r = 0; r <= kMaxRhs; ++r)
-        if (have[r]) {
-            cufftDestroy(r2c[r]);
-            cufftDestroy(c2r[r]);
-            have[r] = false;
-        }
+    for (auto& kv : plan) {
+        cufftDestroy(kv.second.first);
+        cufftDestroy(kv.second.second);
+    }
+    plan.clear();
     grid.release();
     spec.release();
     green.release();
     work.release();
+    rcap = 0;
 }
 
 template <typename T>
-void Mesh<T>::spread(int n, const double* xw, const double* q, int nrhs, cudaStream_t s) {
+void Mesh<T>::spread(int n, const double* xw, const double* q, int nrhs, const int* bead_cfg, int ncfg,
+                     cudaStream_t s) {
     ProfScope ps(mesh_stage<T>(ST_SPREAD), s);
-    IBP_CUDA(cudaMemsetAsync(grid.p, 0, sizeof(T) * (size_t)g.G * nrhs, s));
+    ensure_channels(nrhs * ncfg);
+    IBP_CUDA(cudaMemsetAsync(grid.p, 0, sizeof(T) * (size_t)g.G * nrhs * ncfg, s));
     if (n == 0) return;
-    spread_dispatch<T>(n, xw, q, nrhs, g, grid.as<T>(), s);
+    spread_dispatch<T>(n, xw, q, nrhs, bead_cfg, g, grid.as<T>(), s);
     IBP_CHECK_LAUNCH();
 }
 
 template <typename T>
-void Mesh<T>::transform(int nrhs, cudaStream_t s) {
-    plans(nrhs, s);
+void Mesh<T>::transform(int ch, cudaStream_t s) {
+    plans(ch, s);
+    const auto& pl = plan.at(ch);
     using C = typename Cplx<T>::type;
     {
         ProfScope ps(mesh_stage<T>(ST_FFT_FWD), s);
         if constexpr (sizeof(T) == 8) {
-            IBP_CUFFT(cufftExecD2Z(r2c[nrhs], grid.as<double>(), spec.as<C>()));
+            IBP_CUFFT(cufftExecD2Z(pl.first, grid.as<double>(), spec.as<C>()));
         } else {
-            IBP_CUFFT(cufftExecR2C(r2c[nrhs], grid.as<float>(), spec.as<C>()));
+            IBP_CUFFT(cufftExecR2C(pl.first, grid.as<float>(), spec.as<C>()));
         }
     }
     {
         ProfScope ps(mesh_stage<T>(ST_SCALE), s);
-        scale_kernel<T><<<dim3(grid_blocks(g.Gc, 256), nrhs), 256, 0, s>>>(g.Gc, green.as<T>(), spec.as<C>());
+        scale_kernel<T><<<dim3(grid_blocks(g.Gc, 256), ch), 256, 0, s>>>(g.Gc, green.as<T>(), spec.as<C>());
         IBP_CHECK_LAUNCH();
     }
     ProfScope ps(mesh_stage<T>(ST_FFT_INV), s);
     if constexpr (sizeof(T) == 8) {
-        IBP_CUFFT(cufftExecZ2D(c2r[nrhs], spec.as<C>(), grid.as<double>()));
+        IBP_CUFFT(cufftExecZ2D(pl.second, spec.as<C>(), grid.as<double>()));
     } else {
-        IBP_CUFFT(cufftExecC2R(c2r[nrhs], spec.as<C>(), grid.as<float>()));
+        IBP_CUFFT(cufftExecC2R(pl.second, spec.as<C>(), grid.as<float>()));
     }
 }
 
 template <typename T>
-void Mesh<T>::gather(int n, const double* xw, int nrhs, double* psi, double* E, cudaStream_t s) {
+void Mesh<T>::gather(int n, const double* xw, int nrhs, const int* bead_cfg, double* psi, double* E,
+                     cudaStream_t s) {
     if (n == 0) return;
     ProfScope ps(mesh_stage<T>(ST_GATHER), s);
     if (E)
-        gather_dispatch<T, true>(n, xw, nrhs, g, grid.as<T>(), psi, E, s);
+        gather_dispatch<T, true>(n, xw, nrhs, bead_cfg, g, grid.as<T>(), psi, E, s);
     else
-        gather_dispatch<T, false>(n, xw, nrhs, g, grid.as<T>(), psi, nullptr, s);
+        gather_dispatch<T, false>(n, xw, nrhs, bead_cfg, g, grid.as<T>(), psi, nullptr, s);
     IBP_CHECK_LAUNCH();
 }
 
@@ -504,9 +519,9 @@ IBP_API ibpme_status pme_spread_noalloc(const ibpme_params* params, int n, const
             noalloc_wrap_kernel<<<div_up(3LL * n, 256), 256, 0, s>>>(n, x, p.box[0], p.box[1], p.box[2], xw);
             IBP_CHECK_LAUNCH();
             if (f64)
-                spread_dispatch<double>(n, xw, q, nrhs, g, static_cast<double*>(grid_out), s);
+                spread_dispatch<double>(n, xw, q, nrhs, nullptr, g, static_cast<double*>(grid_out), s);
             else
-                spread_dispatch<float>(n, xw, q, nrhs, g, static_cast<float*>(grid_out), s);
+                spread_dispatch<float>(n, xw, q, nrhs, nullptr, g, static_cast<float*>(grid_out), s);
             IBP_CHECK_LAUNCH();
         }
         return IBPME_OK;

@@ -114,14 +114,15 @@ __device__ __forceinline__ unsigned long long mix64(unsigned long long z) {
     return z ^ (z >> 31);
 }
 
-__global__ void fingerprint_kernel(long long m, const double* __restrict__ xw, unsigned long long* __restrict__ out,
-                                   int* __restrict__ bad) {
+__global__ void fingerprint_kernel(long long m, const double* __restrict__ xw, const int* __restrict__ bcfg,
+                                   unsigned long long* __restrict__ out, int* __restrict__ bad) {
     unsigned long long acc = 0;
     int nonfinite = 0;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < m; i += (long long)gridDim.x * blockDim.x) {
         const double v = xw[i];
         nonfinite |= !isfinite(v);
         acc += mix64((unsigned long long)__double_as_longlong(v) ^ mix64((unsigned long long)i));
+        if (bcfg && i % 3 == 0) acc += mix64(0x5BD1E995ull * (unsigned long long)(bcfg[i / 3] + 1) + (unsigned long long)i);
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
@@ -132,14 +133,15 @@ __global__ void fingerprint_kernel(long long m, const double* __restrict__ xw, u
     }
 }
 
-__global__ void cell_count_kernel(int n, const double* __restrict__ xw, PairConst k, int* __restrict__ cell_of,
-                                  int* __restrict__ cell_count) {
+__global__ void cell_count_kernel(int n, const double* __restrict__ xw, PairConst k, const int* __restrict__ bcfg,
+                                  int* __restrict__ cell_of, int* __restrict__ cell_count) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
+    const int base = bcfg ? bcfg[i] * (k.nc[0] * k.nc[1] * k.nc[2]) : 0;   // cells of the bead's configuration
     const int cx = cell_coord(xw[3 * i + 0], k.L[0], k.nc[0]);
     const int cy = cell_coord(xw[3 * i + 1], k.L[1], k.nc[1]);
     const int cz = cell_coord(xw[3 * i + 2], k.L[2], k.nc[2]);
-    const int c = (cz * k.nc[1] + cy) * k.nc[0] + cx;
+    const int c = base + (cz * k.nc[1] + cy) * k.nc[0] + cx;
     cell_of[i] = c;
     atomicAdd(cell_count + c, 1);
 }
@@ -160,7 +162,9 @@ __device__ __forceinline__ void for_neighbours(int alpha, const double* __restri
                                                const int* __restrict__ cell_of, const int* __restrict__ cell_start,
                                                const int* __restrict__ cell_beads, int lane, F&& f) {
     const double x0 = xw[3 * alpha + 0], y0 = xw[3 * alpha + 1], z0 = xw[3 * alpha + 2];
-    const int c = cell_of[alpha];
+    const int ncell = k.nc[0] * k.nc[1] * k.nc[2];
+    const int base = (cell_of[alpha] / ncell) * ncell;   // first cell of the bead's configuration
+    const int c = cell_of[alpha] - base;
     const int cx = c % k.nc[0], cy = (c / k.nc[0]) % k.nc[1], cz = c / (k.nc[0] * k.nc[1]);
     for (int oz = k.lo[2]; oz <= k.hi[2]; ++oz)
         for (int oy = k.lo[1]; oy <= k.hi[1]; ++oy)
@@ -168,7 +172,7 @@ __device__ __forceinline__ void for_neighbours(int alpha, const double* __restri
                 const int nx = (cx + ox + k.nc[0]) % k.nc[0];
                 const int ny = (cy + oy + k.nc[1]) % k.nc[1];
                 const int nz = (cz + oz + k.nc[2]) % k.nc[2];
-                const int cell = (nz * k.nc[1] + ny) * k.nc[0] + nx;
+                const int cell = base + (nz * k.nc[1] + ny) * k.nc[0] + nx;
                 const int s = cell_start[cell], e = cell_start[cell + 1];
                 for (int t0 = s; t0 < e; t0 += 32) {
                     const int t = t0 + lane;
@@ -458,8 +462,8 @@ void near_build(ibpme_ctx* c, int n, const double* xw, bool need_grad) {
     int* bad = reinterpret_cast<int*>(fp + 1);
     IBP_CUDA(cudaMemsetAsync(fp, 0, 2 * sizeof(unsigned long long), s));
     if (n > 0) {
-        fingerprint_kernel<<<div_up(3LL * n, 256) < 256 ? div_up(3LL * n, 256) : 256, 256, 0, s>>>(3LL * n, xw, fp,
-                                                                                                  bad);
+        fingerprint_kernel<<<div_up(3LL * n, 256) < 256 ? div_up(3LL * n, 256) : 256, 256, 0, s>>>(3LL * n, xw,
+                                                                                                  c->bcfg, fp, bad);
         IBP_CHECK_LAUNCH();
     }
     unsigned long long* hfp = static_cast<unsigned long long*>(pinned_host(c, 2 * sizeof(unsigned long long)));
@@ -467,7 +471,7 @@ void near_build(ibpme_ctx* c, int n, const double* xw, bool need_grad) {
     IBP_CUDA(cudaStreamSynchronize(s));
     if (*reinterpret_cast<int*>(hfp + 1) != 0) fail(IBPME_ERR_NONFINITE, "non-finite bead position");
     const unsigned long long print = hfp[0];
-    if (nl.fp_valid && nl.n == n && nl.fp == print) return;
+    if (nl.fp_valid && nl.n == n && nl.fp == print && nl.ncfg == c->ncfg) return;
     nl.fp_valid = false;
     nl.n = n;
     nl.rc = c->rc;
@@ -480,6 +484,8 @@ void near_build(ibpme_ctx* c, int n, const double* xw, bool need_grad) {
         nl.nc[d] = m;
         ncells *= m;
     }
+    nl.ncfg = c->ncfg;
+    ncells *= c->ncfg;   // every configuration has its own cells
     const PairConst k = make_const(c);
     int* cell_of = static_cast<int*>(nl.cell_of.ensure(sizeof(int) * (n + 1)));
     int* cell_count = static_cast<int*>(nl.cell_count.ensure(sizeof(int) * (ncells + 1)));
@@ -489,7 +495,7 @@ void near_build(ibpme_ctx* c, int n, const double* xw, bool need_grad) {
     int* cell_beads = static_cast<int*>(nl.cell_beads.ensure(sizeof(int) * (n + 1)));
     IBP_CUDA(cudaMemsetAsync(cell_count, 0, sizeof(int) * (ncells + 1), s));
     if (n > 0) {
-        cell_count_kernel<<<div_up(n, 256), 256, 0, s>>>(n, xw, k, cell_of, cell_count);
+        cell_count_kernel<<<div_up(n, 256), 256, 0, s>>>(n, xw, k, c->bcfg, cell_of, cell_count);
         IBP_CHECK_LAUNCH();
     }
     scan_counts(cell_count, cell_start64, ncells, nl.scan_tmp, s);

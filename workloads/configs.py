@@ -121,10 +121,10 @@ def config3(n_ions: int = 100_000, per_side: int = 4, mesh=(256, 256, 256), seed
                     [[1.0, 0.0, 0.0]], mesh=tuple(mesh), tol=1e-6, precision="mixed")
 
 
-def _random_body(rng):
+def _random_body(rng, beads=(500, 5000)):
     """One anisotropic body: spherocylinder rod (aspect 2-6), cube, or ellipsoid
-    (semi-axis ratios in [1, 3]) with 500-5000 beads (log-uniform)."""
-    n = int(round(math.exp(rng.uniform(math.log(500), math.log(5000)))))
+    (semi-axis ratios in [1, 3]) with beads[0]-beads[1] beads (log-uniform)."""
+    n = int(round(math.exp(rng.uniform(math.log(beads[0]), math.log(beads[1])))))
     kind = rng.integers(3)
     if kind == 0:
         p = geo.spherocylinder(n, rng.uniform(2.0, 6.0))
@@ -135,10 +135,35 @@ def _random_body(rng):
     return p @ geo.random_rotation(rng).T
 
 
-def config4_batch(n_configs: int = 64, seed: int = 1003, max_bodies: int = 8) -> list[System]:
+def stack(systems: list[System], name: str = "batch") -> tuple[System, np.ndarray]:
+    """Concatenate independent configurations that share box, bead radius,
+    permittivity and fields into one bead list; returns the stacked System and
+    cfg_bodies, the body offsets of the configurations ([n_configs + 1])."""
+    s0 = systems[0]
+    for s in systems[1:]:
+        if not (np.array_equal(s.box, s0.box) and s.a == s0.a and s.eps == s0.eps
+                and np.array_equal(s.E0, s0.E0)):
+            raise ValueError("stacked configurations must share box, bead radius, eps and E0")
+    x = np.concatenate([s.x for s in systems])
+    offs, cfg, base = [0], [0], 0
+    for s in systems:
+        offs.extend((s.body_offsets[1:] + base).tolist())
+        base += s.n
+        cfg.append(cfg[-1] + s.n_bodies)
+    out = System(name=name, x=np.ascontiguousarray(x), body_offsets=np.asarray(offs, dtype=np.int32),
+                 X=np.concatenate([s.X for s in systems]), Q=np.concatenate([s.Q for s in systems]),
+                 E0=s0.E0.copy(), box=s0.box.copy(), a=s0.a, eps=s0.eps, mesh=s0.mesh, tol=s0.tol,
+                 precision=s0.precision)
+    return out, np.asarray(cfg, dtype=np.int32)
+
+
+def config4_batch(n_configs: int = 64, seed: int = 1003, max_bodies: int = 8,
+                  common_radius: bool = False, beads=(500, 5000)) -> list[System]:
     """Independent configurations of 1-max_bodies anisotropic bodies in L = 40,
     random orientations, non-overlapping bounding spheres, Q = 0, three field
-    directions; bead radius 0.45 x the configuration's minimum bead spacing."""
+    directions; bead radius 0.45 x the configuration's minimum bead spacing, or,
+    with common_radius, 0.45 x the smallest minimum spacing of the whole batch
+    (one radius for configurations solved in one batched call)."""
     rng = np.random.default_rng(seed)
     L = 40.0
     out = []
@@ -146,7 +171,7 @@ def config4_batch(n_configs: int = 64, seed: int = 1003, max_bodies: int = 8) ->
         nb = int(rng.integers(1, max_bodies + 1))
         bodies, centres, radii = [], [], []
         for _ in range(nb):
-            p = _random_body(rng)
+            p = _random_body(rng, beads)
             rad = float(np.sqrt((p * p).sum(axis=1)).max())
             for _try in range(1000):
                 cen = rng.uniform(rad, L - rad, size=3)
@@ -159,6 +184,11 @@ def config4_batch(n_configs: int = 64, seed: int = 1003, max_bodies: int = 8) ->
         out.append(assemble(f"polarizability_{c}", bodies, [], [], [0.0] * nb, [L] * 3,
                             0.45 * spacing, 1.0, np.eye(3), mesh=(128, 128, 128), tol=1e-6,
                             precision="mixed"))
+        out[-1].extra["min_spacing"] = spacing
+    if common_radius:
+        a = 0.45 * min(s.extra["min_spacing"] for s in out)
+        for s in out:
+            s.a = a
     return out
 
 
