@@ -282,19 +282,36 @@ void pme_apply(ibpme_ctx* c, int n, const double* xw, const double* q, int nrhs,
         er = static_cast<double*>(c->E_r.ensure(sizeof(double) * 3 * (m ? m : 1)));
         ek = static_cast<double*>(c->E_k.ensure(sizeof(double) * 3 * (m ? m : 1)));
     }
-    near_apply(c, n, q, nrhs, pr);
-    if (E) near_field(c, n, xw, q, nrhs, er);
+    // The real-space pass and the mesh pass are independent until they are
+    // combined: the near field runs on the context's second stream, forked from
+    // and joined back into the calling stream (two branches of a captured graph).
+    const cudaStream_t main = c->stream;
+    IBP_CUDA(cudaEventRecord(c->ev_fork, main));
+    IBP_CUDA(cudaStreamWaitEvent(c->aux, c->ev_fork, 0));
+    {
+        struct Restore {
+            ibpme_ctx* c;
+            cudaStream_t s;
+            ~Restore() { c->stream = s; }
+        } restore{c, main};
+        c->stream = c->aux;
+        near_apply(c, n, q, nrhs, pr);
+        if (E) near_field(c, n, xw, q, nrhs, er);
+    }
+    IBP_CUDA(cudaEventRecord(c->ev_join, c->aux));
     const int ch = nrhs * c->ncfg;
+    const StencilCache* sc = stencil_cache(c, n, xw);
     if (prec == IBPME_MIXED) {
         if (!c->have32) fail(IBPME_ERR_ARG, "mixed precision needs a context created with IBPME_MIXED");
-        c->mesh32.spread(n, xw, q, nrhs, c->bcfg, c->ncfg, c->stream);
+        c->mesh32.spread(n, xw, q, nrhs, c->bcfg, c->ncfg, c->stream, sc);
         c->mesh32.transform(ch, c->stream);
-        c->mesh32.gather(n, xw, nrhs, c->bcfg, pk, ek, c->stream);
+        c->mesh32.gather(n, xw, nrhs, c->bcfg, pk, ek, c->stream, sc);
     } else {
-        c->mesh64.spread(n, xw, q, nrhs, c->bcfg, c->ncfg, c->stream);
+        c->mesh64.spread(n, xw, q, nrhs, c->bcfg, c->ncfg, c->stream, sc);
         c->mesh64.transform(ch, c->stream);
-        c->mesh64.gather(n, xw, nrhs, c->bcfg, pk, ek, c->stream);
+        c->mesh64.gather(n, xw, nrhs, c->bcfg, pk, ek, c->stream, sc);
     }
+    IBP_CUDA(cudaStreamWaitEvent(c->stream, c->ev_join, 0));
     if (m) {
         double* qsum = static_cast<double*>(c->scalars.ensure(sizeof(double) * (size_t)ch));
         IBP_CUDA(cudaMemsetAsync(qsum, 0, sizeof(double) * ch, c->stream));
@@ -349,6 +366,9 @@ IBP_API ibpme_status pme_setup(ibpme_ctx** ctx, const ibpme_params* params, void
             IBP_CUDA(cudaStreamCreateWithFlags(&c->work, cudaStreamNonBlocking));
             IBP_CUDA(cudaEventCreateWithFlags(&c->ev_in, cudaEventDisableTiming));
             IBP_CUDA(cudaEventCreateWithFlags(&c->ev_out, cudaEventDisableTiming));
+            IBP_CUDA(cudaStreamCreateWithFlags(&c->aux, cudaStreamNonBlocking));
+            IBP_CUDA(cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming));
+            IBP_CUDA(cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming));
             near_setup(c);
             pinned_host(c, 4096);
             IBP_CUDA(cudaStreamSynchronize(c->stream));
@@ -369,6 +389,12 @@ IBP_API ibpme_status pme_destroy(ibpme_ctx* c) {
         cudaStreamSynchronize(c->work);
         cudaStreamDestroy(c->work);
     }
+    if (c->aux) {
+        cudaStreamSynchronize(c->aux);
+        cudaStreamDestroy(c->aux);
+    }
+    if (c->ev_fork) cudaEventDestroy(c->ev_fork);
+    if (c->ev_join) cudaEventDestroy(c->ev_join);
     if (c->ev_in) cudaEventDestroy(c->ev_in);
     if (c->ev_out) cudaEventDestroy(c->ev_out);
     c->mesh64.destroy();

@@ -107,6 +107,18 @@ template <> struct Cplx<double> { using type = cufftDoubleComplex; };
 constexpr int kMaxRhs = 8;
 constexpr int kMaxP = 32;
 
+// Stencils cached for a set of positions: each bead's first stencil node per
+// axis (and its configuration) and fractional offset (first node - x / h).
+// Built once per set of positions and shared by every spread and gather of a
+// solve in either precision.
+struct StencilCache {
+    bool valid = false;
+    unsigned long long fp = 0;   // position fingerprint the cache belongs to
+    int n = 0, ncfg = 0;
+    DevBuf start;                // int4 per bead: first node (x, y, z), configuration
+    DevBuf frac;                 // double4 per bead: (first node - x / h) per axis
+};
+
 // Spectral-Ewald mesh engine in one precision: grids, spectrum, Green's table, plans.
 // A grid "channel" holds one right-hand side of one configuration: channel
 // cfg * nrhs + r (a single system is configuration 0).
@@ -124,9 +136,12 @@ struct Mesh {
     void ensure_channels(int ch);
     void plans(int ch, cudaStream_t s);
     // bead_cfg (device, or NULL for one configuration) maps each bead to its configuration
-    void spread(int n, const double* xw, const double* q, int nrhs, const int* bead_cfg, int ncfg, cudaStream_t s);
+    // sc: cached stencils of these positions, or NULL to derive them in the kernels
+    void spread(int n, const double* xw, const double* q, int nrhs, const int* bead_cfg, int ncfg, cudaStream_t s,
+                const StencilCache* sc = nullptr);
     void transform(int ch, cudaStream_t s);   // R2C, scale, C2R over ch channels
-    void gather(int n, const double* xw, int nrhs, const int* bead_cfg, double* psi, double* E, cudaStream_t s);
+    void gather(int n, const double* xw, int nrhs, const int* bead_cfg, double* psi, double* E, cudaStream_t s,
+                const StencilCache* sc = nullptr);
 };
 
 // Cell list and real-space pair table (Sec. III.D.1, Sec. III.D.3 step 1).
@@ -141,6 +156,7 @@ struct NearList {
     DevBuf row_count, rowptr;
     DevBuf col, val, gfac;
     DevBuf scan_tmp, flag;
+    DevBuf xf;                     // FP32 positions (x, y, z, 0) for the candidate filter
     DevBuf table;                  // tabulated pair kernel (phi, phi', phi'') on [2a, r_c]
     DevBuf fp_dev;                 // fingerprint of the positions + non-finite flag
     unsigned long long fp = 0;     // fingerprint of the positions the table was built for
@@ -251,16 +267,26 @@ struct ibpme_ctx {
     const int* bcfg = nullptr;
     ibp::DevBuf ml_feat, ml_scratch, ml_scales, ml_y;   // learned warm start
     cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+    ibp::StencilCache stencils;               // stencils of the current positions
+    cudaStream_t aux = nullptr;               // second branch of a PME evaluation (near field)
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
 };
 
 namespace ibp {
 
 // ---- near.cu ----
+// exclusive scan of n int counts into n + 1 int64 offsets (out[n] = total)
+void scan_counts(const int* in, long long* out, int n, DevBuf& tmp, cudaStream_t s);
 void near_setup(ibpme_ctx* c);   // tabulates the pair kernel (once per context)
 void near_build(ibpme_ctx* c, int n, const double* xw, bool need_grad);
 void near_apply(ibpme_ctx* c, int n, const double* q, int nrhs, double* psi_r);    // overwrite
 void near_field(ibpme_ctx* c, int n, const double* xw, const double* q, int nrhs, double* E_r);  // overwrite
 double self_term(const ibpme_ctx* c);   // phi_self (without 1/eps)
+
+// ---- mesh.cu ----
+// Cached stencils for the current positions (rebuilt when the position
+// fingerprint of the last near_build changed), or NULL without a fingerprint.
+const StencilCache* stencil_cache(ibpme_ctx* c, int n, const double* xw);
 
 // ---- api.cu helpers ----
 void resolve_params(const ibpme_params* in, ibpme_params* out);   // rules of Sec. III.D.2; throws on bad input
@@ -318,6 +344,13 @@ __host__ __device__ __forceinline__ double wrap_coord(double x, double L) {
 
 __host__ __device__ __forceinline__ double min_image(double d, double L) {
     return d - L * floor(d / L + 0.5);
+}
+
+// Minimum image of a difference of two wrapped coordinates (both in [0, L)):
+// d lies in (-L, L), so one conditional shift suffices (no division).
+template <typename T>
+__host__ __device__ __forceinline__ T min_image_wrapped(T d, T L) {
+    return d > T(0.5) * L ? d - L : (d < T(-0.5) * L ? d + L : d);
 }
 
 inline int div_up(long long a, long long b) { return (int)((a + b - 1) / b); }

@@ -197,7 +197,9 @@ arnoldi_small_kernel(int nk, int m, int R, const int* __restrict__ uo, int* __re
                      const double* __restrict__ V, double* __restrict__ w, double* __restrict__ H,
                      double* __restrict__ cs, double* __restrict__ sn, double* __restrict__ g,
                      double* __restrict__ scal, const int* __restrict__ active, double* __restrict__ Vout) {
-    __shared__ double hc[130];
+    __shared__ double hc[130];      // this pass's projections
+    __shared__ double hcol[130];    // column j of H (both passes), rotated in place
+    __shared__ double c_s[130], s_s[130];
     __shared__ double sh[32];
     __shared__ double inv_h;
     const int j = *jdev;
@@ -208,8 +210,12 @@ arnoldi_small_kernel(int nk, int m, int R, const int* __restrict__ uo, int* __re
     const bool act = active[s] != 0;
     double* wr = w + (size_t)r * nk + base;
     const double* Vr = V + (size_t)r * (m + 1) * nk + base;
-    double* Hc = H + ((size_t)s * m + j) * (m + 1);
     if (act) {
+        // the earlier rotations, staged once so that the serial Givens sweep reads shared memory
+        for (int i = threadIdx.x; i < j; i += blockDim.x) {
+            c_s[i] = cs[(size_t)s * m + i];
+            s_s[i] = sn[(size_t)s * m + i];
+        }
         for (int pass = 0; pass < 2; ++pass) {
             for (int i = warp; i <= j; i += nwarp) {
                 const double* vi = Vr + (size_t)i * nk;
@@ -238,17 +244,45 @@ arnoldi_small_kernel(int nk, int m, int R, const int* __restrict__ uo, int* __re
                 for (; i <= j; ++i) v0 -= hc[i] * Vr[(size_t)i * nk + t];
                 wr[t] = (v0 + v1) + (v2 + v3);
             }
-            if (threadIdx.x <= j) Hc[threadIdx.x] = (pass == 0 ? 0.0 : Hc[threadIdx.x]) + hc[threadIdx.x];
+            if (threadIdx.x <= j) hcol[threadIdx.x] = (pass == 0 ? 0.0 : hcol[threadIdx.x]) + hc[threadIdx.x];
             __syncthreads();
         }
         double acc = 0.0;
         for (int t = threadIdx.x; t < len; t += blockDim.x) acc += wr[t] * wr[t];
         const double nrm2 = block_sum(acc, sh);
         if (threadIdx.x == 0) {
-            givens_column(m, j, s, sqrt(nrm2), H, cs, sn, g, scal);
-            inv_h = scal[(size_t)s * S_COUNT + S_INVH];
+            // Givens: apply rotations 0..j-1 to column j, then make the new one (as givens_column)
+            const double h = sqrt(nrm2);
+            hcol[j + 1] = h;
+            for (int i = 0; i < j; ++i) {
+                const double t = c_s[i] * hcol[i] + s_s[i] * hcol[i + 1];
+                hcol[i + 1] = -s_s[i] * hcol[i] + c_s[i] * hcol[i + 1];
+                hcol[i] = t;
+            }
+            const double den = hypot(hcol[j], hcol[j + 1]);
+            double cj = 1.0, sj = 0.0;
+            if (den > 0.0) {
+                cj = hcol[j] / den;
+                sj = hcol[j + 1] / den;
+            }
+            cs[(size_t)s * m + j] = cj;
+            sn[(size_t)s * m + j] = sj;
+            hcol[j] = den;
+            hcol[j + 1] = 0.0;
+            double* gr = g + (size_t)s * (m + 1);
+            const double gj = gr[j];
+            gr[j + 1] = -sj * gj;
+            gr[j] = cj * gj;
+            double* sc = scal + (size_t)s * S_COUNT;
+            sc[S_RES] = fabs(sj * gj);
+            // happy breakdown: the Krylov space is invariant, the estimate above is exact (0)
+            const double ih = (h > 1e-300 && h > 1e-14 * den) ? 1.0 / h : 0.0;
+            sc[S_INVH] = ih;
+            inv_h = ih;
         }
         __syncthreads();
+        double* Hc = H + ((size_t)s * m + j) * (m + 1);
+        for (int i = threadIdx.x; i <= j + 1; i += blockDim.x) Hc[i] = hcol[i];
         double* vn = Vout + ((size_t)r * (m + 1) + j + 1) * nk + base;
         for (int t = threadIdx.x; t < len; t += blockDim.x) vn[t] = wr[t] * inv_h;
     }
@@ -613,8 +647,10 @@ struct Solver {
         const BodyData& bd = c->bodies;
         const Mesh<float>& m32 = c->mesh32;
         const Mesh<double>& m64 = c->mesh64;
-        // make every lazily created resource exist before capture (this may grow the meshes)
+        // make every lazily created resource exist before capture (this may grow the meshes
+        // and build the stencil cache of these positions)
         if (prec == IBPME_MIXED) c->mesh32.plans(R * ncfg, s()); else c->mesh64.plans(R * ncfg, s());
+        stencil_cache(c, n, a.xw);
         auto P = [](const void* p) { return (long long)(size_t)p; };
         std::vector<long long> sig = {prec, R, S, ncfg, nk, n, m, nfree, nmb, (long long)prof_mask(),
                                       P(k->V.p), P(k->w.p), P(k->qop.p), P(k->psi.p), P(k->H.p), P(k->scal.p),
@@ -622,6 +658,7 @@ struct Solver {
                                       P(c->near.val.p), P(c->near.rowptr.p), P(a.xw), P(bd.free_idx.p),
                                       P(bd.free_unk.p), P(bd.bead_body.p), P(bd.body_unk.p), P(bd.mb_unk.p),
                                       P(bd.mb_first.p), P(bd.mb_cnt.p), P(bd.uo.p), P(c->bcfg),
+                                      (long long)c->stencils.valid, P(c->stencils.start.p), P(c->stencils.frac.p),
                                       P(prec == IBPME_MIXED ? m32.grid.p : m64.grid.p),
                                       P(prec == IBPME_MIXED ? m32.spec.p : m64.spec.p),
                                       P(prec == IBPME_MIXED ? m32.work.p : m64.work.p)};
@@ -807,6 +844,7 @@ struct Solver {
         // (possibly much larger) potentials of the guess itself.
         const bool mixed = a.prec == IBPME_MIXED;
         std::vector<double> res = residual(IBPME_FP64, true);
+        bool res64 = true;
         int fell_back = 0;
         if (a.learned && nk > 0) {
             // the learned guess must beat the zero guess, whose residual is |b| up to the ions' share
@@ -833,7 +871,13 @@ struct Solver {
                 if (!(res[i] <= tol_abs[i])) return false;
             return true;
         };
-        while (nk > 0 && !converged() && iters < a.max_iter && outer < 50) {
+        while (nk > 0 && iters < a.max_iter && outer < 50) {
+            if (converged()) {
+                if (res64) break;
+                res = residual(IBPME_FP64);   // a guess that looks converged: confirm with FP64
+                res64 = true;
+                if (converged()) break;
+            }
             ++outer;
             // FP64: plain restarted GMRES (one cycle per outer step, the same operator).
             // Mixed: the FP32-mesh solve aims below the target so that a single FP64
@@ -844,11 +888,14 @@ struct Solver {
             axpby_kernel<<<blocks_for(len), 256, 0, s()>>>(len, 1.0, D(k->x), 1.0, D(k->d), D(k->x));
             IBP_CHECK_LAUNCH();
             res = residual(IBPME_FP64);
+            res64 = true;
             if (verbose)
                 for (int i = 0; i < S; ++i)
                     std::fprintf(stderr, "[ibpme] outer %d system %d: iters %d  |r|/|b| = %.3e (fp64 matvecs %d)\n",
                                  outer, i, iters, relres(i), matvec64);
         }
+        // the reported residual and the ions' potentials come from an FP64 evaluation
+        if (!res64) res = residual(IBPME_FP64);
         // outputs
         extract_kernel<<<blocks_for((long long)std::max(n, nb) * R), 256, 0, s()>>>(
             n, nb, nk, R, I(bd.bead_body), I(bd.off), I(bd.bead_unk), I(bd.body_unk), D(k->x), bd.Q.as<double>(),

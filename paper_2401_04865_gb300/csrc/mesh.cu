@@ -260,6 +260,257 @@ void gather_dispatch(int n, const double* xw, int nrhs, const int* cfg, const Me
     }
 }
 
+// ---------------------------------------------------------------------------
+// Pair-lane spreading and gathering with cached stencils.
+//
+// For a fixed set of positions (a whole Krylov solve) every bead's first
+// stencil node and fractional offset are computed once (stencil_cache_kernel).
+// A warp sets up the bead's 3P one-dimensional windows once (lane l < P holds
+// node l of each axis); its lanes then own (x, y) column pairs (i, j) of the
+// stencil, taking their weights and node indices by shuffle, and walk the P
+// z-nodes of their column: per z-node one shuffle, one index update and one
+// atomic add (spread) or load (gather).  While the beads alone cannot fill the
+// GPU, the P^2 columns of a bead are split over several warps.
+// ---------------------------------------------------------------------------
+constexpr int kPairWarps = 4;   // warps per block
+
+__global__ void stencil_cache_kernel(int n, const double* __restrict__ xw, const int* __restrict__ bcfg, MeshGeom g,
+                                     int4* __restrict__ start, double4* __restrict__ frac) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= n) return;
+    int s0[3];
+    double f[3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        const double u = xw[3 * b + d] * g.inv_h[d];
+        const double sf = floor(u - 0.5 * g.P) + 1.0;
+        f[d] = sf - u;
+        int idx = (int)sf % g.N[d];
+        if (idx < 0) idx += g.N[d];
+        s0[d] = idx;
+    }
+    start[b] = make_int4(s0[0], s0[1], s0[2], bcfg ? bcfg[b] : 0);
+    frac[b] = make_double4(f[0], f[1], f[2], 0.0);
+}
+
+struct PairArgs {
+    MeshGeom g;
+    int wpb;            // warps per bead
+    int rounds;         // blocks of 32 (i, j) pairs per warp: wpb * rounds * 32 >= P^2
+    const int4* start;
+    const double4* frac;
+};
+
+template <typename T>
+__device__ __forceinline__ T window(T f, double kappa) { return dexp<T>(-(T)kappa * f * f); }
+
+// One-dimensional windows of a bead, lane l < P holding node l of each axis:
+// weight, distance (node - x) and periodic node index.
+template <typename T>
+struct Windows {
+    T wx, wy, wz, dx, dy, dz;
+    int ix, iy, iz;
+};
+
+template <typename T, bool DIST>
+__device__ __forceinline__ Windows<T> bead_windows(const PairArgs& A, int bead, int lane) {
+    const MeshGeom& g = A.g;
+    const int P = g.P;
+    const int4 st = A.start[bead];
+    const double4 fr = A.frac[bead];
+    Windows<T> W;
+    const T fx = (T)fr.x + (T)lane, fy = (T)fr.y + (T)lane, fz = (T)fr.z + (T)lane;
+    const bool in = lane < P;
+    W.wx = in ? window<T>(fx, g.kappa[0]) : (T)0;
+    W.wy = in ? window<T>(fy, g.kappa[1]) : (T)0;
+    W.wz = in ? window<T>(fz, g.kappa[2]) : (T)0;
+    if (DIST) {
+        W.dx = fx * (T)g.h[0];
+        W.dy = fy * (T)g.h[1];
+        W.dz = fz * (T)g.h[2];
+    }
+    W.ix = st.x + lane;
+    W.iy = st.y + lane;
+    W.iz = st.z + lane;
+    if (W.ix >= g.N[0]) W.ix -= g.N[0];   // P <= N: one wrap at most
+    if (W.iy >= g.N[1]) W.iy -= g.N[1];
+    if (W.iz >= g.N[2]) W.iz -= g.N[2];
+    return W;
+}
+
+template <typename T, int NR>
+__global__ void __launch_bounds__(32 * kPairWarps)
+spread_pairs_kernel(PairArgs A, int n, const double* __restrict__ q, T* __restrict__ grid) {
+    const int lane = threadIdx.x & 31;
+    const long long gw = (long long)blockIdx.x * kPairWarps + (threadIdx.x >> 5);
+    const long long slot = gw / A.wpb;
+    if (slot >= n) return;   // warp-uniform
+    const int part = (int)(gw - slot * A.wpb);
+    const int bead = (int)slot;
+    const MeshGeom& g = A.g;
+    const int P = g.P, P2 = P * P;
+    const Windows<T> W = bead_windows<T, false>(A, bead, lane);
+    T* gr = grid + (size_t)A.start[bead].w * NR * g.G;
+    T qc[NR];
+#pragma unroll
+    for (int r = 0; r < NR; ++r) qc[r] = (T)(g.c * q[(size_t)r * n + bead]);
+    const long long nxy = (long long)g.N[0] * g.N[1];
+    for (int rd = 0; rd < A.rounds; ++rd) {
+        const int first = (part * A.rounds + rd) * 32;
+        if (first >= P2) break;   // warp-uniform
+        const int pair = first + lane;
+        const bool on = pair < P2;
+        int j = pair / P, i = pair - j * P;
+        if (!on) i = j = 0;
+        const T wxy = __shfl_sync(0xffffffffu, W.wx, i) * __shfl_sync(0xffffffffu, W.wy, j);
+        const long long base = (long long)__shfl_sync(0xffffffffu, W.iy, j) * g.N[0] + __shfl_sync(0xffffffffu, W.ix, i);
+        T qw[NR];
+#pragma unroll
+        for (int r = 0; r < NR; ++r) qw[r] = qc[r] * wxy;
+        for (int k = 0; k < P; ++k) {
+            const T wz = __shfl_sync(0xffffffffu, W.wz, k);
+            const int iz = __shfl_sync(0xffffffffu, W.iz, k);
+            if (on) {
+                const size_t off = (size_t)iz * nxy + base;
+#pragma unroll
+                for (int r = 0; r < NR; ++r) atomicAdd(gr + (size_t)r * g.G + off, qw[r] * wz);
+            }
+        }
+    }
+}
+
+template <typename T, int NR, bool GRAD>
+__global__ void __launch_bounds__(32 * kPairWarps)
+gather_pairs_kernel(PairArgs A, int n, const T* __restrict__ grid, double* __restrict__ psi, double* __restrict__ E) {
+    const int lane = threadIdx.x & 31;
+    const long long gw = (long long)blockIdx.x * kPairWarps + (threadIdx.x >> 5);
+    const long long slot = gw / A.wpb;
+    if (slot >= n) return;   // warp-uniform
+    const int part = (int)(gw - slot * A.wpb);
+    const int bead = (int)slot;
+    const MeshGeom& g = A.g;
+    const int P = g.P, P2 = P * P;
+    const Windows<T> W = bead_windows<T, GRAD>(A, bead, lane);
+    const T* gr = grid + (size_t)A.start[bead].w * NR * g.G;
+    T sp[NR], ex[NR], ey[NR], ez[NR];
+#pragma unroll
+    for (int r = 0; r < NR; ++r) sp[r] = ex[r] = ey[r] = ez[r] = (T)0;
+    const long long nxy = (long long)g.N[0] * g.N[1];
+    for (int rd = 0; rd < A.rounds; ++rd) {
+        const int first = (part * A.rounds + rd) * 32;
+        if (first >= P2) break;   // warp-uniform
+        const int pair = first + lane;
+        const bool on = pair < P2;
+        int j = pair / P, i = pair - j * P;
+        if (!on) i = j = 0;
+        // every lane takes part in every shuffle (full mask); off lanes then drop their weight
+        const T wx = __shfl_sync(0xffffffffu, W.wx, i), wy = __shfl_sync(0xffffffffu, W.wy, j);
+        const T wxy = on ? wx * wy : (T)0;
+        T dx = (T)0, dy = (T)0;
+        if (GRAD) {
+            dx = __shfl_sync(0xffffffffu, W.dx, i);
+            dy = __shfl_sync(0xffffffffu, W.dy, j);
+        }
+        const long long base = (long long)__shfl_sync(0xffffffffu, W.iy, j) * g.N[0] + __shfl_sync(0xffffffffu, W.ix, i);
+        T a[NR], az[NR];
+#pragma unroll
+        for (int r = 0; r < NR; ++r) a[r] = az[r] = (T)0;
+        for (int k = 0; k < P; ++k) {
+            const T wz = __shfl_sync(0xffffffffu, W.wz, k);
+            const int iz = __shfl_sync(0xffffffffu, W.iz, k);
+            T dz = (T)0;
+            if (GRAD) dz = __shfl_sync(0xffffffffu, W.dz, k);
+            if (on) {
+                const size_t off = (size_t)iz * nxy + base;
+#pragma unroll
+                for (int r = 0; r < NR; ++r) {
+                    const T v = __ldg(gr + (size_t)r * g.G + off) * wz;
+                    a[r] += v;
+                    if (GRAD) az[r] += v * dz;
+                }
+            }
+        }
+#pragma unroll
+        for (int r = 0; r < NR; ++r) {
+            sp[r] += wxy * a[r];
+            if (GRAD) {
+                ex[r] += wxy * dx * a[r];
+                ey[r] += wxy * dy * a[r];
+                ez[r] += wxy * az[r];
+            }
+        }
+    }
+#pragma unroll
+    for (int r = 0; r < NR; ++r) {
+        const double s0 = warp_sum((double)sp[r]);
+        if (GRAD) {
+            const double e0 = warp_sum((double)ex[r]);
+            const double e1 = warp_sum((double)ey[r]);
+            const double e2 = warp_sum((double)ez[r]);
+            if (lane == 0) {
+                double* e = E + ((size_t)r * n + bead) * 3;
+                if (A.wpb == 1) {
+                    e[0] = -g.grad * e0;
+                    e[1] = -g.grad * e1;
+                    e[2] = -g.grad * e2;
+                } else {
+                    atomicAdd(e + 0, -g.grad * e0);
+                    atomicAdd(e + 1, -g.grad * e1);
+                    atomicAdd(e + 2, -g.grad * e2);
+                }
+            }
+        }
+        if (lane == 0) {
+            if (A.wpb == 1)
+                psi[(size_t)r * n + bead] = g.gather * s0;
+            else
+                atomicAdd(psi + (size_t)r * n + bead, g.gather * s0);
+        }
+    }
+}
+
+template <typename T, int NR>
+void launch_pairs(bool spread, bool grad, const PairArgs& A, int n, const double* q, T* grid, double* psi,
+                  double* E, cudaStream_t s) {
+    const int blocks = div_up((long long)n * A.wpb, kPairWarps);
+    if (spread)
+        spread_pairs_kernel<T, NR><<<blocks, 32 * kPairWarps, 0, s>>>(A, n, q, grid);
+    else if (grad)
+        gather_pairs_kernel<T, NR, true><<<blocks, 32 * kPairWarps, 0, s>>>(A, n, grid, psi, E);
+    else
+        gather_pairs_kernel<T, NR, false><<<blocks, 32 * kPairWarps, 0, s>>>(A, n, grid, psi, nullptr);
+}
+
+template <typename T>
+void pairs_dispatch(int nrhs, bool spread, bool grad, const PairArgs& A, int n, const double* q, T* grid,
+                    double* psi, double* E, cudaStream_t s) {
+    switch (nrhs) {
+        case 1: launch_pairs<T, 1>(spread, grad, A, n, q, grid, psi, E, s); break;
+        case 2: launch_pairs<T, 2>(spread, grad, A, n, q, grid, psi, E, s); break;
+        case 3: launch_pairs<T, 3>(spread, grad, A, n, q, grid, psi, E, s); break;
+        case 4: launch_pairs<T, 4>(spread, grad, A, n, q, grid, psi, E, s); break;
+        case 5: launch_pairs<T, 5>(spread, grad, A, n, q, grid, psi, E, s); break;
+        case 6: launch_pairs<T, 6>(spread, grad, A, n, q, grid, psi, E, s); break;
+        case 7: launch_pairs<T, 7>(spread, grad, A, n, q, grid, psi, E, s); break;
+        default: launch_pairs<T, 8>(spread, grad, A, n, q, grid, psi, E, s); break;
+    }
+}
+
+// Warps per bead: split a bead's P^2 columns over several warps while the bead
+// count alone cannot fill the GPU (about two waves of resident warps), else one
+// warp walks all of them and sets its window up once.
+PairArgs pair_args(const MeshGeom& g, const StencilCache& b, int n) {
+    PairArgs A{};
+    A.g = g;
+    const int blocks32 = (g.P * g.P + 31) / 32;
+    const bool split = (long long)n * blocks32 <= 152LL * 64 * 2;
+    A.wpb = split ? blocks32 : 1;
+    A.rounds = split ? 1 : blocks32;
+    A.start = b.start.as<int4>();
+    A.frac = b.frac.as<double4>();
+    return A;
+}
+
 // G(k)/(N_x N_y N_z) on the half spectrum, Eq. after H_hat:
 // j0^2(k a) e^{-(1 - eta) k^2 / (4 xi^2)} / k^2, zero at k = 0 (Sec. II, k = 0 removed).
 template <typename T>
@@ -377,12 +628,20 @@ void Mesh<T>::destroy() {
 
 template <typename T>
 void Mesh<T>::spread(int n, const double* xw, const double* q, int nrhs, const int* bead_cfg, int ncfg,
-                     cudaStream_t s) {
+                     cudaStream_t s, const StencilCache* sc) {
     ProfScope ps(mesh_stage<T>(ST_SPREAD), s);
     ensure_channels(nrhs * ncfg);
     IBP_CUDA(cudaMemsetAsync(grid.p, 0, sizeof(T) * (size_t)g.G * nrhs * ncfg, s));
     if (n == 0) return;
-    spread_dispatch<T>(n, xw, q, nrhs, bead_cfg, g, grid.as<T>(), s);
+    // Pair lanes while a bead's columns are split over warps (few beads); with one
+    // warp per bead the row-walking kernel keeps its atomics of consecutive
+    // instructions within one z-plane, which measured faster on dense surfaces.
+    const PairArgs A = sc ? pair_args(g, *sc, n) : PairArgs{};
+    if (sc && A.wpb > 1) {
+        pairs_dispatch<T>(nrhs, true, false, A, n, q, grid.as<T>(), nullptr, nullptr, s);
+    } else {
+        spread_dispatch<T>(n, xw, q, nrhs, bead_cfg, g, grid.as<T>(), s);
+    }
     IBP_CHECK_LAUNCH();
 }
 
@@ -414,9 +673,19 @@ void Mesh<T>::transform(int ch, cudaStream_t s) {
 
 template <typename T>
 void Mesh<T>::gather(int n, const double* xw, int nrhs, const int* bead_cfg, double* psi, double* E,
-                     cudaStream_t s) {
+                     cudaStream_t s, const StencilCache* sc) {
     if (n == 0) return;
     ProfScope ps(mesh_stage<T>(ST_GATHER), s);
+    if (sc) {   // several warps of a bead add their partial sums into zeroed outputs
+        const PairArgs A = pair_args(g, *sc, n);
+        if (A.wpb > 1) {
+            IBP_CUDA(cudaMemsetAsync(psi, 0, sizeof(double) * (size_t)nrhs * n, s));
+            if (E) IBP_CUDA(cudaMemsetAsync(E, 0, sizeof(double) * 3 * (size_t)nrhs * n, s));
+        }
+        pairs_dispatch<T>(nrhs, false, E != nullptr, A, n, nullptr, grid.as<T>(), psi, E, s);
+        IBP_CHECK_LAUNCH();
+        return;
+    }
     if (E)
         gather_dispatch<T, true>(n, xw, nrhs, bead_cfg, g, grid.as<T>(), psi, E, s);
     else
@@ -427,7 +696,25 @@ void Mesh<T>::gather(int n, const double* xw, int nrhs, const int* bead_cfg, dou
 template struct Mesh<float>;
 template struct Mesh<double>;
 
+const StencilCache* stencil_cache(ibpme_ctx* c, int n, const double* xw) {
+    const MeshGeom& g = c->mesh64.g;   // both meshes share N, h and P
+    if (n == 0 || !c->near.fp_valid) return nullptr;   // no fingerprint of these positions: no cache key
+    StencilCache& b = c->stencils;
+    if (b.valid && b.fp == c->near.fp && b.n == n && b.ncfg == c->ncfg) return &b;
+    b.valid = false;
+    int4* start = static_cast<int4*>(b.start.ensure(sizeof(int4) * n));
+    double4* frac = static_cast<double4*>(b.frac.ensure(sizeof(double4) * n));
+    stencil_cache_kernel<<<div_up(n, 256), 256, 0, c->stream>>>(n, xw, c->bcfg, g, start, frac);
+    IBP_CHECK_LAUNCH();
+    b.fp = c->near.fp;
+    b.n = n;
+    b.ncfg = c->ncfg;
+    b.valid = true;
+    return &b;
+}
+
 }  // namespace ibp
+
 
 // ---------------------------------------------------------------------------
 // Spreading for callers that cannot allocate device memory.

@@ -24,6 +24,7 @@ constexpr double kPi = 3.14159265358979323846264338327950288;
 
 struct PairConst {
     double a, xi, A, B, rc2, self;
+    float rc2_cand;     // FP32 screen: (r_c + delta)^2, delta above the FP32 rounding of positions in the box
     double L[3];
     int nc[3];
     int lo[3], hi[3];   // neighbour cell offsets per axis
@@ -154,14 +155,27 @@ __global__ void cell_fill_kernel(int n, const int* __restrict__ cell_of, int* __
     cell_beads[slot] = i;
 }
 
+// FP32 copy of the wrapped positions (x, y, z, 0) for the candidate filter.
+__global__ void pos32_kernel(int n, const double* __restrict__ xw, float4* __restrict__ xf) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) xf[i] = make_float4((float)xw[3 * i], (float)xw[3 * i + 1], (float)xw[3 * i + 2], 0.0f);
+}
+
 // Visits every bead beta != alpha of the neighbouring cells, lanes striding
 // over each cell; calls f(beta, dx, dy, dz, r2, within) for every lane slot
 // (within = false for idle lanes) so that warp-collective code can run in f.
+// Candidates are screened in FP32 with a margin far above its rounding, and
+// the pairs that pass are decided exactly in FP64 (GB300's FP64 rate makes the
+// FP64 test of every candidate the cost of the build).
 template <typename F>
-__device__ __forceinline__ void for_neighbours(int alpha, const double* __restrict__ xw, const PairConst& k,
+__device__ __forceinline__ void for_neighbours(int alpha, const double* __restrict__ xw,
+                                               const float4* __restrict__ xf, const PairConst& k,
                                                const int* __restrict__ cell_of, const int* __restrict__ cell_start,
                                                const int* __restrict__ cell_beads, int lane, F&& f) {
     const double x0 = xw[3 * alpha + 0], y0 = xw[3 * alpha + 1], z0 = xw[3 * alpha + 2];
+    const float4 p0 = xf[alpha];
+    const float Lx = (float)k.L[0], Ly = (float)k.L[1], Lz = (float)k.L[2];
+    const float rc2f = k.rc2_cand;
     const int ncell = k.nc[0] * k.nc[1] * k.nc[2];
     const int base = (cell_of[alpha] / ncell) * ncell;   // first cell of the bead's configuration
     const int c = cell_of[alpha] - base;
@@ -181,31 +195,39 @@ __device__ __forceinline__ void for_neighbours(int alpha, const double* __restri
                     double dx = 0, dy = 0, dz = 0, r2 = 0;
                     if (t < e) {
                         beta = cell_beads[t];
-                        dx = min_image(x0 - xw[3 * beta + 0], k.L[0]);
-                        dy = min_image(y0 - xw[3 * beta + 1], k.L[1]);
-                        dz = min_image(z0 - xw[3 * beta + 2], k.L[2]);
-                        r2 = dx * dx + dy * dy + dz * dz;
-                        within = (beta != alpha) && (r2 < k.rc2);
+                        const float4 pb = xf[beta];
+                        const float fx = min_image_wrapped(p0.x - pb.x, Lx);
+                        const float fy = min_image_wrapped(p0.y - pb.y, Ly);
+                        const float fz = min_image_wrapped(p0.z - pb.z, Lz);
+                        if (beta != alpha && fx * fx + fy * fy + fz * fz < rc2f) {
+                            dx = min_image_wrapped(x0 - xw[3 * beta + 0], k.L[0]);
+                            dy = min_image_wrapped(y0 - xw[3 * beta + 1], k.L[1]);
+                            dz = min_image_wrapped(z0 - xw[3 * beta + 2], k.L[2]);
+                            r2 = dx * dx + dy * dy + dz * dz;
+                            within = r2 < k.rc2;
+                        }
                     }
                     f(beta, dx, dy, dz, r2, within);
                 }
             }
 }
 
-__global__ void pair_count_kernel(int n, const double* __restrict__ xw, PairConst k, const int* __restrict__ cell_of,
+__global__ void pair_count_kernel(int n, const double* __restrict__ xw, const float4* __restrict__ xf, PairConst k,
+                                  const int* __restrict__ cell_of,
                                   const int* __restrict__ cell_start, const int* __restrict__ cell_beads,
                                   int* __restrict__ row_count) {
     const int alpha = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (alpha >= n) return;
     int cnt = 0;
-    for_neighbours(alpha, xw, k, cell_of, cell_start, cell_beads, lane,
+    for_neighbours(alpha, xw, xf, k, cell_of, cell_start, cell_beads, lane,
                    [&](int, double, double, double, double, bool within) { cnt += within ? 1 : 0; });
     cnt = warp_sum(cnt);
     if (lane == 0) row_count[alpha] = cnt;
 }
 
-__global__ void pair_fill_kernel(int n, const double* __restrict__ xw, PairConst k, const int* __restrict__ cell_of,
+__global__ void pair_fill_kernel(int n, const double* __restrict__ xw, const float4* __restrict__ xf, PairConst k,
+                                 const int* __restrict__ cell_of,
                                  const int* __restrict__ cell_start, const int* __restrict__ cell_beads,
                                  const long long* __restrict__ rowptr, int* __restrict__ col,
                                  double* __restrict__ val, double* __restrict__ gfac) {
@@ -214,7 +236,7 @@ __global__ void pair_fill_kernel(int n, const double* __restrict__ xw, PairConst
     if (alpha >= n) return;
     long long base = rowptr[alpha];
     const unsigned lt = (1u << lane) - 1u;
-    for_neighbours(alpha, xw, k, cell_of, cell_start, cell_beads, lane,
+    for_neighbours(alpha, xw, xf, k, cell_of, cell_start, cell_beads, lane,
                    [&](int beta, double, double, double, double r2, bool within) {
                        const unsigned m = __ballot_sync(0xffffffffu, within);
                        if (within) {
@@ -292,9 +314,9 @@ __global__ void near_field_kernel(int n, int nrhs, const double* __restrict__ xw
     for (long long p = s + lane; p < e; p += 32) {
         const int b = col[p];
         const double gf = gfac[p];
-        const double dx = min_image(x0 - xw[3 * b + 0], k.L[0]);
-        const double dy = min_image(y0 - xw[3 * b + 1], k.L[1]);
-        const double dz = min_image(z0 - xw[3 * b + 2], k.L[2]);
+        const double dx = min_image_wrapped(x0 - xw[3 * b + 0], k.L[0]);
+        const double dy = min_image_wrapped(y0 - xw[3 * b + 1], k.L[1]);
+        const double dz = min_image_wrapped(z0 - xw[3 * b + 2], k.L[2]);
 #pragma unroll
         for (int r = 0; r < kMaxRhs; ++r)
             if (r < nrhs) {
@@ -398,6 +420,8 @@ __global__ void narrow_kernel(const long long* __restrict__ a, int* __restrict__
     }
 }
 
+}  // namespace
+
 void scan_counts(const int* in, long long* out, int n, DevBuf& tmp, cudaStream_t s) {
     const int nblocks = div_up(n > 0 ? n : 1, kScanChunk);
     long long* sums = static_cast<long long*>(tmp.ensure(sizeof(long long) * (nblocks + 1)));
@@ -413,6 +437,8 @@ void scan_counts(const int* in, long long* out, int n, DevBuf& tmp, cudaStream_t
     }
 }
 
+namespace {
+
 PairConst make_const(const ibpme_ctx* c) {
     PairConst k{};
     k.a = c->a;
@@ -420,6 +446,13 @@ PairConst make_const(const ibpme_ctx* c) {
     k.A = 1.0 / (32.0 * pow(kPi, 1.5) * c->a * c->a * c->xi);
     k.B = 1.0 / (64.0 * kPi * c->a * c->a * c->xi * c->xi);
     k.rc2 = c->rc * c->rc;
+    {
+        // each FP32 coordinate is within 2^-24 L of its FP64 value; a difference within
+        // 2^-23 L per axis, the distance within sqrt(3) of that: delta = 8 L 2^-23 is ample
+        const double Lmax = fmax(c->p.box[0], fmax(c->p.box[1], c->p.box[2]));
+        const double delta = 8.0 * Lmax * 1.1920928955078125e-07;
+        k.rc2_cand = (float)((c->rc + delta) * (c->rc + delta) * (1.0 + 1e-5));
+    }
     k.self = (1.0 - exp(-4.0 * c->a * c->a * c->xi * c->xi)) / (8.0 * pow(kPi, 1.5) * c->a * c->a * c->xi) +
              erfc(2.0 * c->a * c->xi) / (4.0 * kPi * c->a);
     k.table = c->near.table.as<double>();
@@ -508,9 +541,12 @@ void near_build(ibpme_ctx* c, int n, const double* xw, bool need_grad) {
     // pair counts, offsets, fill
     int* row_count = static_cast<int*>(nl.row_count.ensure(sizeof(int) * (n + 1)));
     long long* rowptr = static_cast<long long*>(nl.rowptr.ensure(sizeof(long long) * (n + 1)));
+    float4* xf = static_cast<float4*>(nl.xf.ensure(sizeof(float4) * (n + 1)));
     if (n > 0) {
-        pair_count_kernel<<<div_up((long long)n * 32, 128), 128, 0, s>>>(n, xw, k, cell_of, cell_start, cell_beads,
-                                                                          row_count);
+        pos32_kernel<<<div_up(n, 256), 256, 0, s>>>(n, xw, xf);
+        IBP_CHECK_LAUNCH();
+        pair_count_kernel<<<div_up((long long)n * 32, 128), 128, 0, s>>>(n, xw, xf, k, cell_of, cell_start,
+                                                                          cell_beads, row_count);
         IBP_CHECK_LAUNCH();
     }
     scan_counts(row_count, rowptr, n, nl.scan_tmp, s);
@@ -524,8 +560,8 @@ void near_build(ibpme_ctx* c, int n, const double* xw, bool need_grad) {
     double* val = static_cast<double*>(nl.val.ensure(sizeof(double) * np));
     double* gfac = static_cast<double*>(nl.gfac.ensure(sizeof(double) * np));
     if (n > 0) {
-        pair_fill_kernel<<<div_up((long long)n * 32, 128), 128, 0, s>>>(n, xw, k, cell_of, cell_start, cell_beads,
-                                                                         rowptr, col, val, gfac);
+        pair_fill_kernel<<<div_up((long long)n * 32, 128), 128, 0, s>>>(n, xw, xf, k, cell_of, cell_start,
+                                                                         cell_beads, rowptr, col, val, gfac);
         IBP_CHECK_LAUNCH();
     }
     nl.fp = print;

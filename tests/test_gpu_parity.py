@@ -104,6 +104,43 @@ def test_pme_field_matches_oracle(cuda_lib, case, prec):
     ib.pme_destroy(ctx)
 
 
+@pytest.mark.parametrize("nrhs", [1, 2, 3, 4])
+def test_cached_stencil_mesh_kernels_match_fp64_and_oracle(cuda_lib, nrhs):
+    """pme_field runs the cached-stencil spread and gather in both precisions.  A
+    dense cluster straddling the periodic corner plus scattered beads, P = 9, one
+    to four fields; the FP32 mesh against the FP64 mesh to FP32 rounding and
+    against the oracle at the mixed bar, and a second call (cache reused) against
+    the first."""
+    ib = cuda_lib
+    rng = np.random.default_rng(40 + nrhs)
+    box = np.array([5.0, 6.0, 7.0])
+    mesh = (32, 40, 48)
+    d = rng.normal(size=(400, 3))
+    cluster = 0.6 * d / np.linalg.norm(d, axis=1, keepdims=True) * rng.uniform(0, 1, size=(400, 1)) ** (1 / 3)
+    x = np.concatenate([cluster + [0.1, 5.9, 3.5], rng.uniform(0, 1, size=(300, 3)) * box])
+    n = x.shape[0]
+    q = np.stack([random_neutral_charges(n, 100 + r) for r in range(nrhs)])
+    kw = dict(box=box, mesh=mesh, tol=1e-6, bead_radius=0.02, eps_f=0.8, max_rhs=4)
+    c64 = ib.pme_setup(ib.make_params(precision=ib.IBPME_FP64, **kw))
+    c32 = ib.pme_setup(ib.make_params(precision=ib.IBPME_MIXED, **kw))
+    try:
+        assert ib.ibpme_get_params(c32).P == 9
+        p64, e64 = _field(ib, c64, x, q, nrhs=nrhs)
+        p32, e32 = _field(ib, c32, x, q, nrhs=nrhs)
+        for r in range(nrhs):
+            assert rel_err(p32[r], p64[r]) < 2e-5, (r, rel_err(p32[r], p64[r]))
+            assert rel_err(e32[r], e64[r]) < 2e-5, (r, rel_err(e32[r], e64[r]))
+        # twice in a row: the cached bins and the graph-free path give the same result
+        p32b, e32b = _field(ib, c32, x, q, nrhs=nrhs)
+        assert rel_err(p32b, p32) < 1e-6 and rel_err(e32b, e32) < 1e-6
+        if nrhs == 1:
+            ref_psi, ref_E = o.potential(x, q[0], box, 0.02, 0.8, field=True)
+            assert rel_err(p32[0], ref_psi) < MIXED_RTOL and rel_err(e32[0], ref_E) < MIXED_RTOL
+    finally:
+        ib.pme_destroy(c64)
+        ib.pme_destroy(c32)
+
+
 def test_pme_field_multi_rhs_host_pointers_and_edge_cases(cuda_lib):
     ib = cuda_lib
     x, q0, box, a, eps, mesh, tol = _field_case("sphere162")
