@@ -271,7 +271,7 @@ void wrap_positions(ibpme_ctx* c, int n, const double* x, double* xw) {
 }
 
 void pme_apply(ibpme_ctx* c, int n, const double* xw, const double* q, int nrhs, int prec, double* psi,
-               double* E, bool near_ready) {
+               double* E, bool near_ready, bool near32) {
     if (!near_ready) near_build(c, n, xw, E != nullptr);
     const size_t m = (size_t)nrhs * n;
     double* pr = static_cast<double*>(c->psi_r.ensure(sizeof(double) * (m ? m : 1)));
@@ -295,7 +295,7 @@ void pme_apply(ibpme_ctx* c, int n, const double* xw, const double* q, int nrhs,
             ~Restore() { c->stream = s; }
         } restore{c, main};
         c->stream = c->aux;
-        near_apply(c, n, q, nrhs, pr);
+        near_apply(c, n, q, nrhs, pr, near32 && prec == IBPME_MIXED);
         if (E) near_field(c, n, xw, q, nrhs, er);
     }
     IBP_CUDA(cudaEventRecord(c->ev_join, c->aux));

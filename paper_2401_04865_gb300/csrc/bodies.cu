@@ -154,18 +154,21 @@ __device__ void normals6(unsigned entity, unsigned step, unsigned long long seed
 
 // f_tot = f_bead + Heyes-Melrose forces gamma/(2 dt) (2a - r) (x_a - x_b)/r for
 // r < 2a between beads of different bodies (Eq. hardsphereFD).
+// The pair table's rows and columns are in the cell-sorted order: row t is
+// bead order[t].
 __global__ void hard_sphere_kernel(int n, const double* __restrict__ xw, double L0, double L1, double L2,
                                    const long long* __restrict__ rowptr, const int* __restrict__ col,
-                                   const int* __restrict__ bead_body, double a, double coef,
-                                   const double* __restrict__ f_in, double* __restrict__ f_out) {
-    const int al = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+                                   const int* __restrict__ order, const int* __restrict__ bead_body, double a,
+                                   double coef, const double* __restrict__ f_in, double* __restrict__ f_out) {
+    const int t = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
-    if (al >= n) return;
+    if (t >= n) return;
+    const int al = order[t];
     const int ba = bead_body[al];
     const double x0 = xw[3 * al], y0 = xw[3 * al + 1], z0 = xw[3 * al + 2];
     double fx = 0, fy = 0, fz = 0;
-    for (long long p = rowptr[al] + lane; p < rowptr[al + 1]; p += 32) {
-        const int be = col[p];
+    for (long long p = rowptr[t] + lane; p < rowptr[t + 1]; p += 32) {
+        const int be = order[col[p]];
         if (bead_body[be] == ba) continue;
         const double dx = min_image(x0 - xw[3 * be], L0);
         const double dy = min_image(y0 - xw[3 * be + 1], L1);
@@ -432,7 +435,7 @@ void bd_step(ibpme_ctx* c, int n, const double* xw, const double* f, const ibpme
     double* Rm = ftot + 3 * (size_t)n;
     hard_sphere_kernel<<<div_up((long long)n * 32, 128), 128, 0, s>>>(
         n, xw, c->p.box[0], c->p.box[1], c->p.box[2], nl.rowptr.as<long long>(), nl.col.as<int>(),
-        bd.bead_body.as<int>(), c->a, p->gamma / (2.0 * p->dt), f, ftot);
+        nl.cell_beads.as<int>(), bd.bead_body.as<int>(), c->a, p->gamma / (2.0 * p->dt), f, ftot);
     IBP_CHECK_LAUNCH();
     BdConst bc{p->dt, p->gamma, p->kT, p->seed, (unsigned)(p->step & 0xffffffffLL)};
     bd_body_kernel<<<div_up((long long)bd.nb * 32, 128), 128, 0, s>>>(bd.nb, bd.off.as<int>(), bd.rel.as<double>(),

@@ -152,9 +152,13 @@ struct NearList {
     double L[3] = {0, 0, 0};
     double rc = 0;
     bool have_grad = false;
-    DevBuf cell_of, cell_count, cell_start64, cell_start, cell_beads, cursor;
+    DevBuf cell_of, cell_count, cell_start64, cell_start, cursor;
+    DevBuf cell_beads;             // beads sorted by cell: row t of the pair table is bead cell_beads[t]
     DevBuf row_count, rowptr;
     DevBuf col, val, gfac;
+    DevBuf pair32;                 // (col, FP32 val) per pair: inner operator of mixed-precision solves
+    DevBuf qf;                     // charges packed per bead (float4) for the FP32 pass
+    DevBuf qs;                     // charges [n][nrhs] in the sorted order for the FP64 pass
     DevBuf scan_tmp, flag;
     DevBuf xf;                     // FP32 positions (x, y, z, 0) for the candidate filter
     DevBuf table;                  // tabulated pair kernel (phi, phi', phi'') on [2a, r_c]
@@ -279,7 +283,8 @@ namespace ibp {
 void scan_counts(const int* in, long long* out, int n, DevBuf& tmp, cudaStream_t s);
 void near_setup(ibpme_ctx* c);   // tabulates the pair kernel (once per context)
 void near_build(ibpme_ctx* c, int n, const double* xw, bool need_grad);
-void near_apply(ibpme_ctx* c, int n, const double* q, int nrhs, double* psi_r);    // overwrite
+// overwrite; fp32: FP32 pair values and charges (the mixed solve's inner operator)
+void near_apply(ibpme_ctx* c, int n, const double* q, int nrhs, double* psi_r, bool fp32 = false);
 void near_field(ibpme_ctx* c, int n, const double* xw, const double* q, int nrhs, double* E_r);  // overwrite
 double self_term(const ibpme_ctx* c);   // phi_self (without 1/eps)
 
@@ -293,8 +298,9 @@ void resolve_params(const ibpme_params* in, ibpme_params* out);   // rules of Se
 MeshGeom make_geom(const ibpme_params& p);
 void wrap_positions(ibpme_ctx* c, int n, const double* x, double* xw);
 // psi = M q (real + self + wave) in the given precision; E optional
+// near32: real-space pass in FP32 too (only the inner operator of a mixed solve)
 void pme_apply(ibpme_ctx* c, int n, const double* xw, const double* q, int nrhs, int prec,
-               double* psi, double* E, bool near_ready);
+               double* psi, double* E, bool near_ready, bool near32 = false);
 void* pinned_host(ibpme_ctx* c, size_t bytes);
 
 // ---- bodies.cu ----

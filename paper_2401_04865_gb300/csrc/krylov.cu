@@ -592,7 +592,7 @@ struct Solver {
         scatter_kernel<<<blocks_for((long long)nfree * R), 256, 0, s()>>>(nfree, ustride, n, R, I(bd.free_idx),
                                                                           I(bd.free_unk), u, jdev, nk, D(k->qop));
         IBP_CHECK_LAUNCH();
-        pme_apply(c, n, a.xw, D(k->qop), R, prec, D(k->psi), nullptr, true);
+        pme_apply(c, n, a.xw, D(k->qop), R, prec, D(k->psi), nullptr, true, prec == IBPME_MIXED);
         const long long work = ((long long)nfree * R + 31) / 32 * 32 + 32LL * nmb * R;
         assemble_kernel<<<blocks_for(work), 256, 0, s()>>>(nfree, nmb, nk, ustride, n, R, I(bd.free_idx),
                                                            I(bd.free_unk), I(bd.bead_body), I(bd.body_unk),
@@ -655,7 +655,7 @@ struct Solver {
         std::vector<long long> sig = {prec, R, S, ncfg, nk, n, m, nfree, nmb, (long long)prof_mask(),
                                       P(k->V.p), P(k->w.p), P(k->qop.p), P(k->psi.p), P(k->H.p), P(k->scal.p),
                                       P(c->psi_r.p), P(c->psi_k.p), P(c->scalars.p), P(c->near.col.p),
-                                      P(c->near.val.p), P(c->near.rowptr.p), P(a.xw), P(bd.free_idx.p),
+                                      P(c->near.val.p), P(c->near.pair32.p), P(c->near.qf.p), P(c->near.qs.p), P(c->near.cell_beads.p), P(c->near.rowptr.p), P(a.xw), P(bd.free_idx.p),
                                       P(bd.free_unk.p), P(bd.bead_body.p), P(bd.body_unk.p), P(bd.mb_unk.p),
                                       P(bd.mb_first.p), P(bd.mb_cnt.p), P(bd.uo.p), P(c->bcfg),
                                       (long long)c->stencils.valid, P(c->stencils.start.p), P(c->stencils.frac.p),

@@ -162,8 +162,9 @@ __global__ void pos32_kernel(int n, const double* __restrict__ xw, float4* __res
 }
 
 // Visits every bead beta != alpha of the neighbouring cells, lanes striding
-// over each cell; calls f(beta, dx, dy, dz, r2, within) for every lane slot
-// (within = false for idle lanes) so that warp-collective code can run in f.
+// over each cell; calls f(beta, slot, dx, dy, dz, r2, within) for every lane
+// slot (within = false for idle lanes) so that warp-collective code can run in
+// f; slot is beta's position in the cell-sorted bead order.
 // Candidates are screened in FP32 with a margin far above its rounding, and
 // the pairs that pass are decided exactly in FP64 (GB300's FP64 rate makes the
 // FP64 test of every candidate the cost of the build).
@@ -207,37 +208,42 @@ __device__ __forceinline__ void for_neighbours(int alpha, const double* __restri
                             within = r2 < k.rc2;
                         }
                     }
-                    f(beta, dx, dy, dz, r2, within);
+                    f(beta, t, dx, dy, dz, r2, within);
                 }
             }
 }
 
+// The pair table is stored in the cell-sorted bead order: row t belongs to bead
+// cell_beads[t] and its columns are sorted positions too, so the rows a block
+// works on, and the charges they gather, sit close together in memory.
 __global__ void pair_count_kernel(int n, const double* __restrict__ xw, const float4* __restrict__ xf, PairConst k,
                                   const int* __restrict__ cell_of,
                                   const int* __restrict__ cell_start, const int* __restrict__ cell_beads,
                                   int* __restrict__ row_count) {
-    const int alpha = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int t = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
-    if (alpha >= n) return;
+    if (t >= n) return;
+    const int alpha = cell_beads[t];
     int cnt = 0;
     for_neighbours(alpha, xw, xf, k, cell_of, cell_start, cell_beads, lane,
-                   [&](int, double, double, double, double, bool within) { cnt += within ? 1 : 0; });
+                   [&](int, int, double, double, double, double, bool within) { cnt += within ? 1 : 0; });
     cnt = warp_sum(cnt);
-    if (lane == 0) row_count[alpha] = cnt;
+    if (lane == 0) row_count[t] = cnt;
 }
 
 __global__ void pair_fill_kernel(int n, const double* __restrict__ xw, const float4* __restrict__ xf, PairConst k,
                                  const int* __restrict__ cell_of,
                                  const int* __restrict__ cell_start, const int* __restrict__ cell_beads,
                                  const long long* __restrict__ rowptr, int* __restrict__ col,
-                                 double* __restrict__ val, double* __restrict__ gfac) {
-    const int alpha = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+                                 double* __restrict__ val, uint2* __restrict__ pair32, double* __restrict__ gfac) {
+    const int t = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
-    if (alpha >= n) return;
-    long long base = rowptr[alpha];
+    if (t >= n) return;
+    const int alpha = cell_beads[t];
+    long long base = rowptr[t];
     const unsigned lt = (1u << lane) - 1u;
     for_neighbours(alpha, xw, xf, k, cell_of, cell_start, cell_beads, lane,
-                   [&](int beta, double, double, double, double r2, bool within) {
+                   [&](int, int slot_b, double, double, double, double r2, bool within) {
                        const unsigned m = __ballot_sync(0xffffffffu, within);
                        if (within) {
                            const long long slot = base + __popc(m & lt);
@@ -251,8 +257,9 @@ __global__ void pair_fill_kernel(int n, const double* __restrict__ xw, const flo
                                phi = k.self;   // coincident beads: the r -> 0 limit
                                dphi = 0.0;
                            }
-                           col[slot] = beta;
+                           col[slot] = slot_b;
                            val[slot] = phi;
+                           pair32[slot] = make_uint2((unsigned)slot_b, __float_as_uint((float)phi));
                            if (gfac) gfac[slot] = (r > 0.0) ? -dphi / r : 0.0;
                        }
                        base += __popc(m);
@@ -261,15 +268,26 @@ __global__ void pair_fill_kernel(int n, const double* __restrict__ xw, const flo
 
 // psi_r[r][alpha] = (phi_self q_alpha + sum_pairs phi_r q_beta) / eps.
 // One warp per row for NR right-hand sides; four independent accumulation
-// chains per lane keep several gathers of q in flight on long rows.
+// chains per lane keep several gathers in flight on long rows.  The charges are
+// first packed in the sorted order with the right-hand sides interleaved, so a
+// pair gathers one NR-double run.
+__global__ void pack_q64_kernel(int n, int nrhs, const int* __restrict__ order, const double* __restrict__ q,
+                                double* __restrict__ qs) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n) return;
+    const int b = order[t];
+    for (int r = 0; r < nrhs; ++r) qs[(size_t)t * nrhs + r] = q[(size_t)r * n + b];
+}
+
 template <int NR>
 __global__ void near_apply_kernel(int n, const long long* __restrict__ rowptr, const int* __restrict__ col,
-                                  const double* __restrict__ val, double self, double inv_eps,
-                                  const double* __restrict__ q, double* __restrict__ psi) {
-    const int alpha = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+                                  const double* __restrict__ val, const int* __restrict__ order, double self,
+                                  double inv_eps, const double* __restrict__ qs, const double* __restrict__ q,
+                                  double* __restrict__ psi) {
+    const int t = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
-    if (alpha >= n) return;
-    const long long s = rowptr[alpha], e = rowptr[alpha + 1];
+    if (t >= n) return;
+    const long long s = rowptr[t], e = rowptr[t + 1];
     double acc[4][NR];
 #pragma unroll
     for (int u = 0; u < 4; ++u)
@@ -279,40 +297,104 @@ __global__ void near_apply_kernel(int n, const long long* __restrict__ rowptr, c
     for (; p + 96 < e; p += 128) {
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
-            const int b = col[p + 32 * u];
+            const double* qb = qs + (size_t)col[p + 32 * u] * NR;
             const double v = val[p + 32 * u];
 #pragma unroll
-            for (int r = 0; r < NR; ++r) acc[u][r] += v * q[(size_t)r * n + b];
+            for (int r = 0; r < NR; ++r) acc[u][r] += v * qb[r];
         }
     }
     for (; p < e; p += 32) {
-        const int b = col[p];
+        const double* qb = qs + (size_t)col[p] * NR;
         const double v = val[p];
 #pragma unroll
-        for (int r = 0; r < NR; ++r) acc[0][r] += v * q[(size_t)r * n + b];
+        for (int r = 0; r < NR; ++r) acc[0][r] += v * qb[r];
     }
+    const int alpha = order[t];
 #pragma unroll
     for (int r = 0; r < NR; ++r) {
-        const double t = warp_sum((acc[0][r] + acc[1][r]) + (acc[2][r] + acc[3][r]));
-        if (lane == 0) psi[(size_t)r * n + alpha] = (t + self * q[(size_t)r * n + alpha]) * inv_eps;
+        const double sum = warp_sum((acc[0][r] + acc[1][r]) + (acc[2][r] + acc[3][r]));
+        if (lane == 0) psi[(size_t)r * n + alpha] = (sum + self * q[(size_t)r * n + alpha]) * inv_eps;
+    }
+}
+
+// The inner operator of a mixed-precision solve: the same sum with the pair
+// values rounded to FP32 and stored with their column as one 8-byte word, the
+// charges of up to four right-hand sides packed per bead in one float4 (one
+// 16-byte gather per pair instead of NR 8-byte ones), FP32 partial sums per
+// lane, FP64 across the warp and for the self term.
+__global__ void pack_q32_kernel(int n, int nrhs, const int* __restrict__ order, const double* __restrict__ q,
+                                float4* __restrict__ qf) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n) return;
+    const int b = order[t];
+    float v[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+    for (int r = 0; r < nrhs; ++r) v[r] = (float)q[(size_t)r * n + b];
+    qf[t] = make_float4(v[0], v[1], v[2], v[3]);
+}
+
+constexpr int kChains32 = 8;   // pairs per lane in flight in the FP32 pass
+
+template <int NR>
+__global__ void near_apply32_kernel(int n, const long long* __restrict__ rowptr, const uint2* __restrict__ pair32,
+                                    const int* __restrict__ order, double self, double inv_eps,
+                                    const float4* __restrict__ qf, const double* __restrict__ q,
+                                    double* __restrict__ psi) {
+    const int t = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (t >= n) return;
+    const long long s = rowptr[t], e = rowptr[t + 1];
+    float acc[NR];
+#pragma unroll
+    for (int r = 0; r < NR; ++r) acc[r] = 0.0f;
+    long long p = s + lane;
+    // kChains32 independent (column, value) loads, then their charge gathers
+    for (; p + 32 * (kChains32 - 1) < e; p += 32 * kChains32) {
+        uint2 cv[kChains32];
+#pragma unroll
+        for (int u = 0; u < kChains32; ++u) cv[u] = pair32[p + 32 * u];
+        float4 b[kChains32];
+#pragma unroll
+        for (int u = 0; u < kChains32; ++u) b[u] = qf[cv[u].x];
+#pragma unroll
+        for (int u = 0; u < kChains32; ++u) {
+            const float v = __uint_as_float(cv[u].y);
+            const float qb[4] = {b[u].x, b[u].y, b[u].z, b[u].w};
+#pragma unroll
+            for (int r = 0; r < NR; ++r) acc[r] += v * qb[r];
+        }
+    }
+    for (; p < e; p += 32) {
+        const uint2 cv = pair32[p];
+        const float4 b = qf[cv.x];
+        const float v = __uint_as_float(cv.y);
+        const float qb[4] = {b.x, b.y, b.z, b.w};
+#pragma unroll
+        for (int r = 0; r < NR; ++r) acc[r] += v * qb[r];
+    }
+    const int alpha = order[t];
+#pragma unroll
+    for (int r = 0; r < NR; ++r) {
+        const double sum = warp_sum((double)acc[r]);
+        if (lane == 0) psi[(size_t)r * n + alpha] = (sum + self * q[(size_t)r * n + alpha]) * inv_eps;
     }
 }
 
 // E_r[r][alpha] = sum_pairs (-phi_r'(r)/r) (x_alpha - x_beta) q_beta / eps
 __global__ void near_field_kernel(int n, int nrhs, const double* __restrict__ xw, PairConst k,
                                   const long long* __restrict__ rowptr, const int* __restrict__ col,
-                                  const double* __restrict__ gfac, double inv_eps, const double* __restrict__ q,
-                                  double* __restrict__ E) {
-    const int alpha = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+                                  const int* __restrict__ order, const double* __restrict__ gfac, double inv_eps,
+                                  const double* __restrict__ q, double* __restrict__ E) {
+    const int t = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
-    if (alpha >= n) return;
-    const long long s = rowptr[alpha], e = rowptr[alpha + 1];
+    if (t >= n) return;
+    const int alpha = order[t];
+    const long long s = rowptr[t], e = rowptr[t + 1];
     const double x0 = xw[3 * alpha + 0], y0 = xw[3 * alpha + 1], z0 = xw[3 * alpha + 2];
     double ex[kMaxRhs], ey[kMaxRhs], ez[kMaxRhs];
 #pragma unroll
     for (int r = 0; r < kMaxRhs; ++r) ex[r] = ey[r] = ez[r] = 0.0;
     for (long long p = s + lane; p < e; p += 32) {
-        const int b = col[p];
+        const int b = order[col[p]];
         const double gf = gfac[p];
         const double dx = min_image_wrapped(x0 - xw[3 * b + 0], k.L[0]);
         const double dy = min_image_wrapped(y0 - xw[3 * b + 1], k.L[1]);
@@ -559,16 +641,20 @@ void near_build(ibpme_ctx* c, int n, const double* xw, bool need_grad) {
     int* col = static_cast<int*>(nl.col.ensure(sizeof(int) * np));
     double* val = static_cast<double*>(nl.val.ensure(sizeof(double) * np));
     double* gfac = static_cast<double*>(nl.gfac.ensure(sizeof(double) * np));
+    uint2* pair32 = static_cast<uint2*>(nl.pair32.ensure(sizeof(uint2) * np));
+    // packed charges of the two passes, allocated here, outside any graph capture
+    nl.qf.ensure(sizeof(float4) * (n + 1));
+    nl.qs.ensure(sizeof(double) * (size_t)(n + 1) * kMaxRhs);
     if (n > 0) {
         pair_fill_kernel<<<div_up((long long)n * 32, 128), 128, 0, s>>>(n, xw, xf, k, cell_of, cell_start,
-                                                                         cell_beads, rowptr, col, val, gfac);
+                                                                         cell_beads, rowptr, col, val, pair32, gfac);
         IBP_CHECK_LAUNCH();
     }
     nl.fp = print;
     nl.fp_valid = true;
 }
 
-void near_apply(ibpme_ctx* c, int n, const double* q, int nrhs, double* psi_r) {
+void near_apply(ibpme_ctx* c, int n, const double* q, int nrhs, double* psi_r, bool fp32) {
     if (n == 0) return;
     ProfScope ps(ST_NEAR_APPLY, c->stream);
     NearList& nl = c->near;
@@ -579,15 +665,33 @@ void near_apply(ibpme_ctx* c, int n, const double* q, int nrhs, double* psi_r) {
     const double* vl = nl.val.as<double>();
     const double ie = 1.0 / c->eps;
     cudaStream_t s = c->stream;
+    const int* od = nl.cell_beads.as<int>();
+    if (fp32 && nrhs <= 4) {
+        float4* qf = static_cast<float4*>(nl.qf.ensure(sizeof(float4) * n));
+        pack_q32_kernel<<<div_up(n, 256), 256, 0, s>>>(n, nrhs, od, q, qf);
+        IBP_CHECK_LAUNCH();
+        const uint2* pc = nl.pair32.as<uint2>();
+        switch (nrhs) {
+            case 1: near_apply32_kernel<1><<<blocks, 128, 0, s>>>(n, rp, pc, od, k.self, ie, qf, q, psi_r); break;
+            case 2: near_apply32_kernel<2><<<blocks, 128, 0, s>>>(n, rp, pc, od, k.self, ie, qf, q, psi_r); break;
+            case 3: near_apply32_kernel<3><<<blocks, 128, 0, s>>>(n, rp, pc, od, k.self, ie, qf, q, psi_r); break;
+            default: near_apply32_kernel<4><<<blocks, 128, 0, s>>>(n, rp, pc, od, k.self, ie, qf, q, psi_r); break;
+        }
+        IBP_CHECK_LAUNCH();
+        return;
+    }
+    double* qs = static_cast<double*>(nl.qs.ensure(sizeof(double) * (size_t)n * nrhs));
+    pack_q64_kernel<<<div_up(n, 256), 256, 0, s>>>(n, nrhs, od, q, qs);
+    IBP_CHECK_LAUNCH();
     switch (nrhs) {
-        case 1: near_apply_kernel<1><<<blocks, 128, 0, s>>>(n, rp, cl, vl, k.self, ie, q, psi_r); break;
-        case 2: near_apply_kernel<2><<<blocks, 128, 0, s>>>(n, rp, cl, vl, k.self, ie, q, psi_r); break;
-        case 3: near_apply_kernel<3><<<blocks, 128, 0, s>>>(n, rp, cl, vl, k.self, ie, q, psi_r); break;
-        case 4: near_apply_kernel<4><<<blocks, 128, 0, s>>>(n, rp, cl, vl, k.self, ie, q, psi_r); break;
-        case 5: near_apply_kernel<5><<<blocks, 128, 0, s>>>(n, rp, cl, vl, k.self, ie, q, psi_r); break;
-        case 6: near_apply_kernel<6><<<blocks, 128, 0, s>>>(n, rp, cl, vl, k.self, ie, q, psi_r); break;
-        case 7: near_apply_kernel<7><<<blocks, 128, 0, s>>>(n, rp, cl, vl, k.self, ie, q, psi_r); break;
-        default: near_apply_kernel<8><<<blocks, 128, 0, s>>>(n, rp, cl, vl, k.self, ie, q, psi_r); break;
+        case 1: near_apply_kernel<1><<<blocks, 128, 0, s>>>(n, rp, cl, vl, od, k.self, ie, qs, q, psi_r); break;
+        case 2: near_apply_kernel<2><<<blocks, 128, 0, s>>>(n, rp, cl, vl, od, k.self, ie, qs, q, psi_r); break;
+        case 3: near_apply_kernel<3><<<blocks, 128, 0, s>>>(n, rp, cl, vl, od, k.self, ie, qs, q, psi_r); break;
+        case 4: near_apply_kernel<4><<<blocks, 128, 0, s>>>(n, rp, cl, vl, od, k.self, ie, qs, q, psi_r); break;
+        case 5: near_apply_kernel<5><<<blocks, 128, 0, s>>>(n, rp, cl, vl, od, k.self, ie, qs, q, psi_r); break;
+        case 6: near_apply_kernel<6><<<blocks, 128, 0, s>>>(n, rp, cl, vl, od, k.self, ie, qs, q, psi_r); break;
+        case 7: near_apply_kernel<7><<<blocks, 128, 0, s>>>(n, rp, cl, vl, od, k.self, ie, qs, q, psi_r); break;
+        default: near_apply_kernel<8><<<blocks, 128, 0, s>>>(n, rp, cl, vl, od, k.self, ie, qs, q, psi_r); break;
     }
     IBP_CHECK_LAUNCH();
 }
@@ -599,7 +703,8 @@ void near_field(ibpme_ctx* c, int n, const double* xw, const double* q, int nrhs
     NearList& nl = c->near;
     const PairConst k = make_const(c);
     near_field_kernel<<<div_up((long long)n * 32, 128), 128, 0, c->stream>>>(
-        n, nrhs, xw, k, nl.rowptr.as<long long>(), nl.col.as<int>(), nl.gfac.as<double>(), 1.0 / c->eps, q, E_r);
+        n, nrhs, xw, k, nl.rowptr.as<long long>(), nl.col.as<int>(), nl.cell_beads.as<int>(), nl.gfac.as<double>(),
+        1.0 / c->eps, q, E_r);
     IBP_CHECK_LAUNCH();
 }
 

@@ -163,3 +163,30 @@ def test_polarizability_batch_is_symmetric_and_matches_oracle(cuda_lib):
             assert rel_err(q[r, lo:lo + p.n], qr[r]) < MIXED_RTOL, (r, rel_err(q[r, lo:lo + p.n], qr[r]))
     finally:
         ib.pme_destroy(ctx)
+
+
+def test_polarizability_driver_autotunes_and_matches_oracle(cuda_lib, tmp_path):
+    """The batched polarizability driver: buckets of at most three configurations,
+    the mesh of each bucket picked by the autotuner from two candidates (both
+    measured, the choice cached), and every body's 3x3 tensor of the smallest
+    configuration against the FP64 oracle solving that configuration alone."""
+    from paper_2401_04865_gb300 import batch as B
+    ib = cuda_lib
+    parts = C.config4_batch(n_configs=5, seed=78, max_bodies=2, common_radius=True, beads=(60, 150))
+    tuner = B.Autotuner(cache_path=str(tmp_path / "tune.json"), candidates=(64, 96), probe=(2, 5))
+    tensors, report = B.polarizability(ib, parts, tuner=tuner, rtol=1e-8, tol=1e-6, max_channels=9)
+    assert len(tensors) == 5 and all(t.shape == (p.n_bodies, 3, 3) for t, p in zip(tensors, parts))
+    assert sorted(i for rep in report for i in rep["configs"]) == list(range(5))
+    for rep in report:
+        assert len(rep["configs"]) <= 3 and rep["mesh"] in (64, 96) and rep["status"] == ib.IBPME_OK
+        assert {m["mesh"] for m in rep["tuning"]} == {64, 96}
+        assert all(m["per_iter_ms"] > 0 for m in rep["tuning"])
+    import os
+    assert os.path.exists(str(tmp_path / "tune.json"))
+    k = int(np.argmin([p.n for p in parts]))
+    p = parts[k]
+    E0 = np.eye(3)
+    qr, _ = o.solve_dense(p.x, p.body_offsets, p.X, p.Q, E0, p.box, p.a, p.eps)
+    for j in range(3):
+        Sr = o.dipoles(p.x, p.X, p.body_offsets, qr[j], p.box)    # [bodies][3] for E0 = e_j
+        assert rel_err(tensors[k][:, :, j], Sr) < MIXED_RTOL, (j, rel_err(tensors[k][:, :, j], Sr))
