@@ -52,8 +52,10 @@ typedef enum {
 } ibpme_status;
 
 enum { IBPME_FP64 = 0,            /* every step in FP64 */
-       IBPME_MIXED = 1 };         /* FP32 mesh (spread, FFT, scale, gather), FP64 near field,
-                                     FP64 Krylov; solves refine against the FP64 operator */
+       IBPME_MIXED = 1 };         /* FP32 mesh (spread, FFT, scale, gather), FP64 near field and
+                                     Krylov; inside a solve the corrections come from an inner
+                                     operator whose near field is FP32 too, refined against the
+                                     FP64 operator */
 
 /* Parameters of the spectral Ewald split (Sec. III.D).  A zero in a field
  * marked "auto" asks pme_setup to derive it with the rules of Sec. III.D.2:
@@ -310,7 +312,8 @@ long long ibpme_kernel_launches(void);
  * (real-space SpMV/field), 2 spread, 3 fft_forward, 4 scale, 5 fft_inverse,
  * 6 gather (2-6: FP32 mesh), 7 krylov (Arnoldi/Givens kernels of one iteration),
  * 8 bodies, 9-13 the FP64 mesh (spread64, fft_forward64, scale64, fft_inverse64,
- * gather64).
+ * gather64), 14 near_apply32 (the FP32 real-space pass of a mixed solve's inner
+ * operator).
  * ibpme_profile(mask) enables CUDA-event timing of the stages in the bit mask
  * (0 disables) and resets the totals; each enabled stage then records an event
  * pair on the stream it runs on. */

@@ -23,6 +23,8 @@
 // orthogonalisation) is captured once as a CUDA graph and replayed.
 #include "common.cuh"
 
+#include <cooperative_groups.h>
+
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
@@ -188,108 +190,153 @@ __global__ void normalize_kernel(int nk, int m, const int* __restrict__ jdev, in
 
 __global__ void advance_kernel(int* __restrict__ jdev) { *jdev += 1; }
 
-// ---- single-block Arnoldi: one block per system, any number of systems ----
-constexpr int kSmallThreads = 1024;
-constexpr int kSmallMaxNk = 32 * kSmallThreads;
+// ---- cluster Arnoldi: one thread-block cluster per system ----
+// GB300 executes FP64 at a small fraction of its FP32 rate on every SM, so the
+// orthogonalisation of even a few hundred unknowns is bound by the FP64 pipe of
+// the SM that runs it.  Each system is therefore spread over a cluster of
+// kClusterCtas CTAs (one slice of the unknowns each); partial projections and
+// norms are exchanged through distributed shared memory between hardware
+// cluster barriers, and every CTA repeats the short serial Givens sweep so that
+// no further exchange is needed.
+namespace cg = cooperative_groups;
+constexpr int kClusterCtas = 8;
+constexpr int kClusterThreads = 512;
+constexpr int kClusterMaxNk = 32768;
+constexpr size_t kStageSmem = 160 * 1024;   // dynamic shared memory of the staged variant (opt-in)
 
-__global__ void __launch_bounds__(kSmallThreads)
-arnoldi_small_kernel(int nk, int m, int R, const int* __restrict__ uo, int* __restrict__ jdev,
-                     const double* __restrict__ V, double* __restrict__ w, double* __restrict__ H,
-                     double* __restrict__ cs, double* __restrict__ sn, double* __restrict__ g,
-                     double* __restrict__ scal, const int* __restrict__ active, double* __restrict__ Vout) {
-    __shared__ double hc[130];      // this pass's projections
+// STAGE: the CTA's slice of V_0..V_j and of w is copied to shared memory once
+// (one round of independent loads), and both CGS passes run from there; used
+// when a slice of every Krylov vector fits (chunk <= threads, (m + 2) chunk
+// doubles of shared memory).
+template <bool STAGE>
+__global__ void __cluster_dims__(kClusterCtas, 1, 1) __launch_bounds__(kClusterThreads)
+arnoldi_cluster_kernel(int nk, int m, int R, int chunk_max, const int* __restrict__ uo,
+                       const int* __restrict__ jdev, const double* __restrict__ V, double* __restrict__ w,
+                       double* __restrict__ H, double* __restrict__ cs, double* __restrict__ sn,
+                       double* __restrict__ g, double* __restrict__ scal, const int* __restrict__ active,
+                       double* __restrict__ Vout) {
+    extern __shared__ double stage_buf[];   // STAGE: [j + 1][chunk_max] slice of V, then [chunk_max] of w
+    cg::cluster_group cl = cg::this_cluster();
+    __shared__ double part[130];    // this CTA's partial sums: projections, then |w|^2
+    __shared__ double hc[130];      // projections of this pass (whole system)
     __shared__ double hcol[130];    // column j of H (both passes), rotated in place
     __shared__ double c_s[130], s_s[130];
     __shared__ double sh[32];
     __shared__ double inv_h;
+    const int crank = (int)cl.block_rank();
+    const int s = blockIdx.x / kClusterCtas;
+    if (active[s] == 0) return;   // uniform over the cluster: no barrier is left waiting
     const int j = *jdev;
-    const int s = blockIdx.x;
     const int r = s % R, cfg = s / R;
     const int base = uo[cfg], len = uo[cfg + 1] - base;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarp = blockDim.x >> 5;
-    const bool act = active[s] != 0;
+    const int chunk = (len + kClusterCtas - 1) / kClusterCtas;
+    const int lo = min(len, crank * chunk), hi = min(len, lo + chunk);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarp = kClusterThreads / 32;
     double* wr = w + (size_t)r * nk + base;
     const double* Vr = V + (size_t)r * (m + 1) * nk + base;
-    if (act) {
-        // the earlier rotations, staged once so that the serial Givens sweep reads shared memory
-        for (int i = threadIdx.x; i < j; i += blockDim.x) {
-            c_s[i] = cs[(size_t)s * m + i];
-            s_s[i] = sn[(size_t)s * m + i];
+    // STAGE: the slice re-based at lo with row stride chunk_max, w after the V rows
+    double* vst = stage_buf;
+    double* wst = stage_buf + (size_t)(j + 1) * chunk_max;
+    const int cnt = hi - lo;
+    for (int i = threadIdx.x; i < j; i += kClusterThreads) {
+        c_s[i] = cs[(size_t)s * m + i];
+        s_s[i] = sn[(size_t)s * m + i];
+    }
+    if (STAGE) {
+        for (int e = threadIdx.x; e < (j + 1) * cnt; e += kClusterThreads) {
+            const int i = e / cnt, t = e - i * cnt;
+            vst[(size_t)i * chunk_max + t] = Vr[(size_t)i * nk + lo + t];
         }
-        for (int pass = 0; pass < 2; ++pass) {
-            for (int i = warp; i <= j; i += nwarp) {
-                const double* vi = Vr + (size_t)i * nk;
-                double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;   // independent chains for ILP
-                int t = lane;
-                for (; t + 96 < len; t += 128) {
-                    a0 += vi[t] * wr[t];
-                    a1 += vi[t + 32] * wr[t + 32];
-                    a2 += vi[t + 64] * wr[t + 64];
-                    a3 += vi[t + 96] * wr[t + 96];
-                }
-                for (; t < len; t += 32) a0 += vi[t] * wr[t];
-                const double acc = warp_sum((a0 + a1) + (a2 + a3));
-                if (lane == 0) hc[i] = acc;
+        if (threadIdx.x < cnt) wst[threadIdx.x] = wr[lo + threadIdx.x];
+        __syncthreads();
+    }
+    // element t of this CTA's slice of V_i and of w
+    auto vat = [&](int i, int t) -> double {
+        return STAGE ? vst[(size_t)i * chunk_max + (t - lo)] : Vr[(size_t)i * nk + t];
+    };
+    auto wat = [&](int t) -> double { return STAGE ? wst[t - lo] : wr[t]; };
+    for (int pass = 0; pass < 2; ++pass) {
+        for (int i = warp; i <= j; i += nwarp) {
+            double a0 = 0.0, a1 = 0.0;
+            int t = lo + lane;
+            for (; t + 32 < hi; t += 64) {
+                a0 += vat(i, t) * wat(t);
+                a1 += vat(i, t + 32) * wat(t + 32);
             }
-            __syncthreads();
-            for (int t = threadIdx.x; t < len; t += blockDim.x) {
-                double v0 = wr[t], v1 = 0.0, v2 = 0.0, v3 = 0.0;
-                int i = 0;
-                for (; i + 3 <= j; i += 4) {
-                    v0 -= hc[i] * Vr[(size_t)i * nk + t];
-                    v1 -= hc[i + 1] * Vr[(size_t)(i + 1) * nk + t];
-                    v2 -= hc[i + 2] * Vr[(size_t)(i + 2) * nk + t];
-                    v3 -= hc[i + 3] * Vr[(size_t)(i + 3) * nk + t];
-                }
-                for (; i <= j; ++i) v0 -= hc[i] * Vr[(size_t)i * nk + t];
-                wr[t] = (v0 + v1) + (v2 + v3);
-            }
-            if (threadIdx.x <= j) hcol[threadIdx.x] = (pass == 0 ? 0.0 : hcol[threadIdx.x]) + hc[threadIdx.x];
-            __syncthreads();
+            if (t < hi) a0 += vat(i, t) * wat(t);
+            const double acc = warp_sum(a0 + a1);
+            if (lane == 0) part[i] = acc;
         }
-        double acc = 0.0;
-        for (int t = threadIdx.x; t < len; t += blockDim.x) acc += wr[t] * wr[t];
-        const double nrm2 = block_sum(acc, sh);
-        if (threadIdx.x == 0) {
-            // Givens: apply rotations 0..j-1 to column j, then make the new one (as givens_column)
-            const double h = sqrt(nrm2);
-            hcol[j + 1] = h;
-            for (int i = 0; i < j; ++i) {
-                const double t = c_s[i] * hcol[i] + s_s[i] * hcol[i + 1];
-                hcol[i + 1] = -s_s[i] * hcol[i] + c_s[i] * hcol[i + 1];
-                hcol[i] = t;
+        cl.sync();
+        if (threadIdx.x <= j) {
+            double h = 0.0;
+            for (int c = 0; c < kClusterCtas; ++c) h += *cl.map_shared_rank(&part[threadIdx.x], c);
+            hc[threadIdx.x] = h;
+            hcol[threadIdx.x] = (pass == 0 ? 0.0 : hcol[threadIdx.x]) + h;
+        }
+        cl.sync();   // every CTA has read the partials (and sees hc) before part is reused
+        for (int t = lo + threadIdx.x; t < hi; t += kClusterThreads) {
+            double v0 = wat(t), v1 = 0.0;
+            int i = 0;
+            for (; i + 1 <= j; i += 2) {
+                v0 -= hc[i] * vat(i, t);
+                v1 -= hc[i + 1] * vat(i + 1, t);
             }
-            const double den = hypot(hcol[j], hcol[j + 1]);
-            double cj = 1.0, sj = 0.0;
-            if (den > 0.0) {
-                cj = hcol[j] / den;
-                sj = hcol[j + 1] / den;
-            }
+            if (i <= j) v0 -= hc[i] * vat(i, t);
+            if (STAGE)
+                wst[t - lo] = v0 + v1;
+            else
+                wr[t] = v0 + v1;
+        }
+        __syncthreads();
+    }
+    double acc = 0.0;
+    for (int t = lo + threadIdx.x; t < hi; t += kClusterThreads) acc += wat(t) * wat(t);
+    acc = block_sum(acc, sh);
+    if (threadIdx.x == 0) part[0] = acc;
+    cl.sync();
+    if (threadIdx.x == 0) {
+        double nrm2 = 0.0;
+        for (int c = 0; c < kClusterCtas; ++c) nrm2 += *cl.map_shared_rank(&part[0], c);
+        // Givens: apply rotations 0..j-1 to column j, then make the new one (as givens_column);
+        // every CTA computes the same values, CTA 0 stores them
+        const double h = sqrt(nrm2);
+        hcol[j + 1] = h;
+        for (int i = 0; i < j; ++i) {
+            const double t = c_s[i] * hcol[i] + s_s[i] * hcol[i + 1];
+            hcol[i + 1] = -s_s[i] * hcol[i] + c_s[i] * hcol[i + 1];
+            hcol[i] = t;
+        }
+        const double den = hypot(hcol[j], hcol[j + 1]);
+        double cj = 1.0, sj = 0.0;
+        if (den > 0.0) {
+            cj = hcol[j] / den;
+            sj = hcol[j + 1] / den;
+        }
+        hcol[j] = den;
+        hcol[j + 1] = 0.0;
+        // happy breakdown: the Krylov space is invariant, the estimate is exact (0)
+        const double ih = (h > 1e-300 && h > 1e-14 * den) ? 1.0 / h : 0.0;
+        inv_h = ih;
+        if (crank == 0) {
             cs[(size_t)s * m + j] = cj;
             sn[(size_t)s * m + j] = sj;
-            hcol[j] = den;
-            hcol[j + 1] = 0.0;
             double* gr = g + (size_t)s * (m + 1);
             const double gj = gr[j];
             gr[j + 1] = -sj * gj;
             gr[j] = cj * gj;
             double* sc = scal + (size_t)s * S_COUNT;
             sc[S_RES] = fabs(sj * gj);
-            // happy breakdown: the Krylov space is invariant, the estimate above is exact (0)
-            const double ih = (h > 1e-300 && h > 1e-14 * den) ? 1.0 / h : 0.0;
             sc[S_INVH] = ih;
-            inv_h = ih;
         }
-        __syncthreads();
-        double* Hc = H + ((size_t)s * m + j) * (m + 1);
-        for (int i = threadIdx.x; i <= j + 1; i += blockDim.x) Hc[i] = hcol[i];
-        double* vn = Vout + ((size_t)r * (m + 1) + j + 1) * nk + base;
-        for (int t = threadIdx.x; t < len; t += blockDim.x) vn[t] = wr[t] * inv_h;
     }
-    // with one block, every thread has read j by now: advance it here (with several
-    // systems a separate launch advances it, after all blocks are done)
-    __syncthreads();
-    if (gridDim.x == 1 && threadIdx.x == 0) *jdev = j + 1;
+    cl.sync();   // no CTA leaves while another may still read its partial norm
+    if (crank == 0) {
+        double* Hc = H + ((size_t)s * m + j) * (m + 1);
+        for (int i = threadIdx.x; i <= j + 1; i += kClusterThreads) Hc[i] = hcol[i];
+    }
+    double* vn = Vout + ((size_t)r * (m + 1) + j + 1) * nk + base;
+    for (int t = lo + threadIdx.x; t < hi; t += kClusterThreads) vn[t] = wat(t) * inv_h;
 }
 
 // Back substitution H(0:k,0:k) y = g(0:k) per system.
@@ -377,35 +424,33 @@ __global__ void scatter_kernel(int nfree, long long ustride, int n, int R, const
     qop[(size_t)r * n + free_idx[i]] = u[(size_t)r * ustride + free_unk[i]];
 }
 
-// y_bead = -psi_bead + Psi'(body); y_body = sum of the body's charges
-__global__ void assemble_kernel(int nfree, int nmb, int nk, long long ustride, int n, int R,
+// y_bead = -psi_bead + Psi'(body); y_body = sum of the body's charges.
+// Blocks [0, bead_blocks) take the bead rows; each later block sums the
+// charges of one (right-hand side, multi-bead body) pair, so that a body of
+// hundreds of beads is reduced by a whole block rather than a serial warp.
+__global__ void assemble_kernel(int nfree, int nmb, int nk, long long ustride, int n, int R, int bead_blocks,
                                 const int* __restrict__ free_idx, const int* __restrict__ free_unk,
                                 const int* __restrict__ bead_body, const int* __restrict__ body_unk,
                                 const int* __restrict__ mb_unk, const int* __restrict__ mb_first,
                                 const int* __restrict__ mb_cnt, const double* __restrict__ psi,
                                 const double* __restrict__ u, const int* __restrict__ jdev, double* __restrict__ y) {
+    __shared__ double sh[32];
     if (jdev) u += (size_t)(*jdev) * nk;
-    const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    const long long top = (long long)nfree * R;
-    if (t < top) {
+    if ((int)blockIdx.x < bead_blocks) {
+        const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+        if (t >= (long long)nfree * R) return;
         const int r = (int)(t / nfree), i = (int)(t % nfree);
         const int j = free_idx[i];
         y[(size_t)r * nk + free_unk[i]] = -psi[(size_t)r * n + j] + u[(size_t)r * ustride + body_unk[bead_body[j]]];
         return;
     }
-    // one warp per (rhs, body) for the constraint rows; the warp section starts on a
-    // 32-thread boundary so that every logical warp is one hardware warp
-    const long long top_pad = (top + 31) / 32 * 32;
-    if (t < top_pad) return;
-    const long long wt = t - top_pad;
-    const long long wid = wt >> 5;
-    const int lane = (int)(wt & 31);
-    if (wid >= (long long)nmb * R) return;
-    const int r = (int)(wid / nmb), b = (int)(wid % nmb);
-    double s = 0.0;
-    for (int i = lane; i < mb_cnt[b]; i += 32) s += u[(size_t)r * ustride + mb_first[b] + i];
-    s = warp_sum(s);
-    if (lane == 0) y[(size_t)r * nk + mb_unk[b]] = s;
+    const int wid = blockIdx.x - bead_blocks;
+    if (wid >= nmb * R) return;   // the one block of an empty launch
+    const int r = wid / nmb, b = wid % nmb;
+    double acc = 0.0;
+    for (int i = threadIdx.x; i < mb_cnt[b]; i += blockDim.x) acc += u[(size_t)r * ustride + mb_first[b] + i];
+    acc = block_sum(acc, sh);
+    if (threadIdx.x == 0) y[(size_t)r * nk + mb_unk[b]] = acc;
 }
 
 // all bead charges of the current iterate: free beads from x, ions fixed at Q
@@ -440,17 +485,19 @@ __global__ void fit_psi_kernel(int nmb, int nk, int n, int R, const int* __restr
 
 // residual of the full saddle system on the free rows (the ion rows hold exactly):
 //   r_bead = -r.E0 - (-(M q)_bead + Psi'_body),   r_body = Q - sum of the body's charges
-__global__ void residual_kernel(int nfree, int nmb, int nk, int n, int R, const int* __restrict__ free_idx,
-                                const int* __restrict__ free_unk, const int* __restrict__ bead_body,
-                                const int* __restrict__ body_unk, const int* __restrict__ mb_body,
-                                const int* __restrict__ mb_unk, const int* __restrict__ mb_first,
-                                const int* __restrict__ mb_cnt, const double* __restrict__ rel,
-                                const double* __restrict__ E0, const double* __restrict__ Q,
-                                const double* __restrict__ psi, const double* __restrict__ x,
-                                double* __restrict__ res) {
-    const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    const long long top = (long long)nfree * R;
-    if (t < top) {
+// (block roles as in assemble_kernel)
+__global__ void residual_kernel(int nfree, int nmb, int nk, int n, int R, int bead_blocks,
+                                const int* __restrict__ free_idx, const int* __restrict__ free_unk,
+                                const int* __restrict__ bead_body, const int* __restrict__ body_unk,
+                                const int* __restrict__ mb_body, const int* __restrict__ mb_unk,
+                                const int* __restrict__ mb_first, const int* __restrict__ mb_cnt,
+                                const double* __restrict__ rel, const double* __restrict__ E0,
+                                const double* __restrict__ Q, const double* __restrict__ psi,
+                                const double* __restrict__ x, double* __restrict__ res) {
+    __shared__ double sh[32];
+    if ((int)blockIdx.x < bead_blocks) {
+        const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+        if (t >= (long long)nfree * R) return;
         const int r = (int)(t / nfree), i = (int)(t % nfree);
         const int j = free_idx[i];
         const double* e = E0 + 3 * r;
@@ -458,17 +505,13 @@ __global__ void residual_kernel(int nfree, int nmb, int nk, int n, int R, const 
         res[(size_t)r * nk + free_unk[i]] = -rE + psi[(size_t)r * n + j] - x[(size_t)r * nk + body_unk[bead_body[j]]];
         return;
     }
-    const long long top_pad = (top + 31) / 32 * 32;   // warp section aligned to hardware warps
-    if (t < top_pad) return;
-    const long long wt = t - top_pad;
-    const long long wid = wt >> 5;
-    const int lane = (int)(wt & 31);
-    if (wid >= (long long)nmb * R) return;
-    const int r = (int)(wid / nmb), b = (int)(wid % nmb);
-    double sm = 0.0;
-    for (int i = lane; i < mb_cnt[b]; i += 32) sm += x[(size_t)r * nk + mb_first[b] + i];
-    sm = warp_sum(sm);
-    if (lane == 0) res[(size_t)r * nk + mb_unk[b]] = Q[mb_body[b]] - sm;
+    const int wid = blockIdx.x - bead_blocks;
+    if (wid >= nmb * R) return;   // the one block of an empty launch
+    const int r = wid / nmb, b = wid % nmb;
+    double acc = 0.0;
+    for (int i = threadIdx.x; i < mb_cnt[b]; i += blockDim.x) acc += x[(size_t)r * nk + mb_first[b] + i];
+    acc = block_sum(acc, sh);
+    if (threadIdx.x == 0) res[(size_t)r * nk + mb_unk[b]] = Q[mb_body[b]] - acc;
 }
 
 // |b_s|^2 = sum over the configuration's beads of (r.E0_r)^2 + sum over its bodies of Q^2
@@ -559,9 +602,12 @@ struct Solver {
     cudaStream_t s() const { return c->stream; }
     double* D(DevBuf& b) const { return b.as<double>(); }
     const int* I(const DevBuf& b) const { return b.as<int>(); }
-    bool single_block() const { return ncfg > 1 || nk <= kSmallMaxNk; }
+    bool clustered() const { return ncfg > 1 || nk <= kClusterMaxNk; }
 
     void alloc() {
+        // opt in to the staged Arnoldi's shared memory (on the current device; before any capture)
+        IBP_CUDA(cudaFuncSetAttribute(arnoldi_cluster_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)kStageSmem));
         k->nk = nk;
         k->R = R;
         k->S = S;
@@ -593,8 +639,8 @@ struct Solver {
                                                                           I(bd.free_unk), u, jdev, nk, D(k->qop));
         IBP_CHECK_LAUNCH();
         pme_apply(c, n, a.xw, D(k->qop), R, prec, D(k->psi), nullptr, true, prec == IBPME_MIXED);
-        const long long work = ((long long)nfree * R + 31) / 32 * 32 + 32LL * nmb * R;
-        assemble_kernel<<<blocks_for(work), 256, 0, s()>>>(nfree, nmb, nk, ustride, n, R, I(bd.free_idx),
+        const int bb = div_up((long long)nfree * R, 256);
+        assemble_kernel<<<std::max(1, bb + nmb * R), 256, 0, s()>>>(nfree, nmb, nk, ustride, n, R, bb, I(bd.free_idx),
                                                            I(bd.free_unk), I(bd.bead_body), I(bd.body_unk),
                                                            I(bd.mb_unk), I(bd.mb_first), I(bd.mb_cnt), D(k->psi), u,
                                                            jdev, y);
@@ -607,15 +653,24 @@ struct Solver {
         int* jd = k->jdev.as<int>();
         apply(prec, D(k->V), D(k->w), (long long)(m + 1) * nk, jd);
         ProfScope ps(ST_KRYLOV, s());
-        if (single_block()) {
-            arnoldi_small_kernel<<<S, kSmallThreads, 0, s()>>>(nk, m, R, I(c->bodies.uo), jd, D(k->V), D(k->w),
-                                                               D(k->H), D(k->cs), D(k->sn), D(k->g), D(k->scal),
-                                                               k->active.as<int>(), D(k->V));
-            IBP_CHECK_LAUNCH();
-            if (S > 1) {
-                advance_kernel<<<1, 1, 0, s()>>>(jd);
-                IBP_CHECK_LAUNCH();
+        if (clustered()) {
+            int max_len = 0;
+            const std::vector<int>& uo = c->bodies.uo_h;
+            for (size_t q = 0; q + 1 < uo.size(); ++q) max_len = std::max(max_len, uo[q + 1] - uo[q]);
+            const int chunk = std::max(1, div_up(max_len, kClusterCtas));
+            const size_t smem = sizeof(double) * (size_t)(m + 2) * chunk;
+            if (chunk <= kClusterThreads && smem <= kStageSmem) {
+                arnoldi_cluster_kernel<true><<<S * kClusterCtas, kClusterThreads, smem, s()>>>(
+                    nk, m, R, chunk, I(c->bodies.uo), jd, D(k->V), D(k->w), D(k->H), D(k->cs), D(k->sn), D(k->g),
+                    D(k->scal), k->active.as<int>(), D(k->V));
+            } else {
+                arnoldi_cluster_kernel<false><<<S * kClusterCtas, kClusterThreads, 0, s()>>>(
+                    nk, m, R, chunk, I(c->bodies.uo), jd, D(k->V), D(k->w), D(k->H), D(k->cs), D(k->sn), D(k->g),
+                    D(k->scal), k->active.as<int>(), D(k->V));
             }
+            IBP_CHECK_LAUNCH();
+            advance_kernel<<<1, 1, 0, s()>>>(jd);
+            IBP_CHECK_LAUNCH();
             return;
         }
         dim3 ag(k->nblk, R);
@@ -741,8 +796,9 @@ struct Solver {
                                                                         D(k->psi_tot), D(k->x));
             IBP_CHECK_LAUNCH();
         }
-        const long long work = ((long long)nfree * R + 31) / 32 * 32 + 32LL * nmb * R;
-        residual_kernel<<<blocks_for(work), 256, 0, s()>>>(nfree, nmb, nk, n, R, I(bd.free_idx), I(bd.free_unk),
+        const int bb = div_up((long long)nfree * R, 256);
+        residual_kernel<<<std::max(1, bb + nmb * R), 256, 0, s()>>>(nfree, nmb, nk, n, R, bb, I(bd.free_idx),
+                                                                    I(bd.free_unk),
                                                            I(bd.bead_body), I(bd.body_unk), I(bd.mb_body),
                                                            I(bd.mb_unk), I(bd.mb_first), I(bd.mb_cnt),
                                                            bd.rel.as<double>(), a.E0, bd.Q.as<double>(),

@@ -656,7 +656,8 @@ void near_build(ibpme_ctx* c, int n, const double* xw, bool need_grad) {
 
 void near_apply(ibpme_ctx* c, int n, const double* q, int nrhs, double* psi_r, bool fp32) {
     if (n == 0) return;
-    ProfScope ps(ST_NEAR_APPLY, c->stream);
+    fp32 = fp32 && nrhs <= 4;
+    ProfScope ps(fp32 ? ST_NEAR_APPLY32 : ST_NEAR_APPLY, c->stream);
     NearList& nl = c->near;
     const PairConst k = make_const(c);
     const int blocks = div_up((long long)n * 32, 128);
@@ -666,7 +667,7 @@ void near_apply(ibpme_ctx* c, int n, const double* q, int nrhs, double* psi_r, b
     const double ie = 1.0 / c->eps;
     cudaStream_t s = c->stream;
     const int* od = nl.cell_beads.as<int>();
-    if (fp32 && nrhs <= 4) {
+    if (fp32) {
         float4* qf = static_cast<float4*>(nl.qf.ensure(sizeof(float4) * n));
         pack_q32_kernel<<<div_up(n, 256), 256, 0, s>>>(n, nrhs, od, q, qf);
         IBP_CHECK_LAUNCH();
