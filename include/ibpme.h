@@ -256,8 +256,14 @@ ibpme_status ibpme_mlp_destroy(ibpme_mlp* mlp);
 /* Copy the IBPME_MLP_NPARAM parameters out / in (host or device pointer); set resets Adam. */
 ibpme_status ibpme_mlp_get(const ibpme_mlp* mlp, float* params);
 ibpme_status ibpme_mlp_set(ibpme_mlp* mlp, const float* params);
-/* y[i] = net(feat[i]) for n samples; feat [n][IBPME_MLP_IN], y [n], device pointers. */
+/* y[i] = net(feat[i]) for n samples; feat [n][IBPME_MLP_IN], y [n], device pointers.
+ * FP32 throughout on the CUDA cores (the reference of the training kernels). */
 ibpme_status ibpme_mlp_forward(ibpme_mlp* mlp, int n, const float* feat, float* y, void* cuda_stream);
+/* The same network with the hidden 64 x 64 layer on the tensor cores (tcgen05.mma,
+ * BF16 activations and weights, FP32 accumulation in tensor memory); the input and
+ * output layers stay FP32.  This is the path of IBPME_GUESS_LEARNED.  Synchronizes
+ * the stream; IBPME_ERR_TIMEOUT if a bounded wait for the tensor cores ran out. */
+ibpme_status ibpme_mlp_forward_tc(ibpme_mlp* mlp, int n, const float* feat, float* y, void* cuda_stream);
 /* Gradient of the mean squared error L = (1/n) sum (net(feat_i) - target_i)^2 with
  * respect to the parameters (grad [IBPME_MLP_NPARAM], host or device) and L. */
 ibpme_status ibpme_mlp_gradient(ibpme_mlp* mlp, int n, const float* feat, const float* target, float* grad,

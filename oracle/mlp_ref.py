@@ -31,6 +31,26 @@ def forward(p, X):
     return h2 @ W3 + b3
 
 
+def round_bf16(a):
+    """Round to the nearest bfloat16 (8-bit significand), ties to even, by bit
+    arithmetic on the float32 representation; returned as float64."""
+    b = np.asarray(a, dtype=np.float32).view(np.uint32).astype(np.uint64)
+    lsb = (b >> 16) & 1
+    r = ((b + 0x7FFF + lsb) >> 16) << 16
+    return r.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+def forward_bf16_hidden(p, X):
+    """The network with the hidden layer's operands (tanh(h1) in float32, and
+    W2) rounded to bfloat16 and the products summed exactly: what a BF16
+    tensor-core product with a wide accumulator computes for that layer."""
+    W1, b1, W2, b2, W3, b3 = unpack(p)
+    X = np.asarray(X, dtype=np.float64)
+    h1 = np.tanh((X.astype(np.float32) @ W1.T.astype(np.float32) + b1.astype(np.float32)).astype(np.float64))
+    h2 = np.tanh(round_bf16(h1) @ round_bf16(W2).T + b2)
+    return h2 @ W3 + b3
+
+
 def loss_and_grad(p, X, T):
     """L = mean (y - t)^2 and dL/dp by reverse-mode differentiation."""
     W1, b1, W2, b2, W3, b3 = unpack(p)

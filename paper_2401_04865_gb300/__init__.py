@@ -88,6 +88,7 @@ SIGNATURES = {
     "ibpme_mlp_get": (_i, [_p, _p]),
     "ibpme_mlp_set": (_i, [_p, _p]),
     "ibpme_mlp_forward": (_i, [_p, _i, _p, _p, _p]),
+    "ibpme_mlp_forward_tc": (_i, [_p, _i, _p, _p, _p]),
     "ibpme_mlp_gradient": (_i, [_p, _i, _p, _p, _p, _p, _p]),
     "ibpme_mlp_train": (_i, [_p, _i, _p, _p, _i, _i, ctypes.c_float, ctypes.c_ulonglong, _p, _p]),
     "ibpme_features": (_i, [_p, _i, _p, ctypes.POINTER(ibpme_bodies), _p, _i, _p, _p, _p]),
@@ -236,6 +237,12 @@ def ibpme_mlp_set(m, params):
 def ibpme_mlp_forward(m, n, feat, y, stream=None):
     return _check(load().ibpme_mlp_forward(m, int(n), ptr(feat, np.float32), ptr(y, np.float32),
                                            _stream_handle(stream)), "ibpme_mlp_forward")
+
+
+def ibpme_mlp_forward_tc(m, n, feat, y, stream=None):
+    """Tensor-core inference (BF16 hidden layer, FP32 accumulation)."""
+    return _check(load().ibpme_mlp_forward_tc(m, int(n), ptr(feat, np.float32), ptr(y, np.float32),
+                                              _stream_handle(stream)), "ibpme_mlp_forward_tc")
 
 
 def ibpme_mlp_gradient(m, n, feat, target, grad, loss=None, stream=None):

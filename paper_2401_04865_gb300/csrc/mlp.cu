@@ -11,6 +11,8 @@
 // W3[H], b3 (row-major, out x in).
 #include "common.cuh"
 
+#include <cuda_bf16.h>
+
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -20,6 +22,7 @@
 struct ibpme_mlp {
     int device = 0;
     ibp::DevBuf params, grad, m1, m2, perm, loss;
+    ibp::DevBuf tc_err;   // set by the tensor-core forward if its mbarrier wait ran out
     long long step = 0;
 };
 
@@ -63,6 +66,220 @@ __global__ void __launch_bounds__(128) mlp_forward_kernel(int n, const float* __
         y += w[OFF_W3 + o] * tanhf(a);
     }
     Y[s] = y;
+}
+
+// ---- inference on the 5th-generation tensor cores (tcgen05) ----
+// One CTA of 128 threads takes 128 samples.  Layer 1 (IN -> H) runs on the
+// CUDA cores, one sample per thread, and writes tanh(h1) as BF16 into shared
+// memory in the tensor cores' K-major layout without swizzle: 8 x 8 core
+// matrices of 8 rows x 16 bytes, byte offset of element (row, k) =
+// ((row / 8) * (H / 8) + k / 8) * 128 + (row % 8) * 16 + (k % 8) * 2, so
+// adjacent core matrices along K are 128 B apart and along the rows
+// (H / 8) * 128 B apart.  W2 (H x H, out x in) is staged the same way.  One
+// elected thread issues four tcgen05.mma (M = 128, N = H, K = 16 each, BF16
+// inputs, FP32 accumulator in tensor memory), commits them to an mbarrier,
+// and every warp then reads its 32 rows of the accumulator with tcgen05.ld;
+// layer 2's bias and tanh and layer 3 finish on the CUDA cores in FP32.
+namespace tc {
+
+constexpr int kRows = 128;                    // M: samples per CTA (one TMEM lane each)
+constexpr int kABytes = kRows * H * 2;        // BF16 activations
+constexpr int kBBytes = H * H * 2;            // BF16 W2
+constexpr int kCoreBytes = 128;               // one 8 x 16-byte core matrix
+constexpr uint32_t kLbo = kCoreBytes;         // next core matrix along K
+constexpr uint32_t kSbo = (H / 8) * kCoreBytes;   // next group of 8 rows
+constexpr int kTmemCols = H;                  // FP32 accumulator columns (a power of two >= 32)
+constexpr int kWaitLimit = 1 << 22;           // bounded mbarrier polling (about 0.4 s with back-off)
+constexpr size_t kSmem = 1024 + kABytes + kBBytes + 1024;
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+// Shared-memory matrix descriptor of tcgen05: start address, leading and
+// stride byte offsets (all >> 4), descriptor version 1, no swizzle.
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+    uint64_t d = 0;
+    d |= (uint64_t)((addr & 0x3FFFFu) >> 4);
+    d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
+    d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
+    d |= (uint64_t)1 << 46;
+    return d;
+}
+
+// Instruction descriptor of tcgen05.mma kind::f16: FP32 accumulator, BF16 A and
+// B, both K-major, N >> 3 and M >> 4.
+__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ uint32_t core_offset(int row, int k) {
+    return (uint32_t)(((row >> 3) * (H / 8) + (k >> 3)) * kCoreBytes + (row & 7) * 16 + (k & 7) * 2);
+}
+
+__device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
+    const uint32_t a = __bfloat16_as_ushort(__float2bfloat16_rn(lo));
+    const uint32_t b = __bfloat16_as_ushort(__float2bfloat16_rn(hi));
+    return a | (b << 16);
+}
+
+__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t phase) {
+    for (int it = 0; it < kWaitLimit; ++it) {
+        uint32_t done;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(done)
+            : "r"(mbar), "r"(phase)
+            : "memory");
+        if (done) return true;
+        if (it > 64) __nanosleep(100);
+    }
+    return false;
+}
+
+__global__ void __launch_bounds__(kRows) mlp_forward_tc_kernel(int n, const float* __restrict__ P,
+                                                               const float* __restrict__ X, float* __restrict__ Y,
+                                                               int* __restrict__ err) {
+    extern __shared__ uint8_t dyn[];
+    __shared__ float w1[H * IN], b1[H], b2[H], w3[H];
+    __shared__ float b3;
+    __shared__ uint32_t tmem_slot;
+    __shared__ __align__(8) uint64_t mbar;
+    // 1024-byte aligned operand tiles inside the dynamic buffer
+    const uint32_t dyn_base = smem_u32(dyn);
+    const uint32_t pad = (1024u - (dyn_base & 1023u)) & 1023u;
+    uint8_t* a_tile = dyn + pad;
+    uint8_t* b_tile = a_tile + kABytes;
+    const uint32_t a_addr = dyn_base + pad, b_addr = a_addr + kABytes;
+    const int tid = threadIdx.x, warp = tid >> 5;
+    const uint32_t mbar_addr = smem_u32(&mbar);
+
+    if (warp == 0) {   // 64 TMEM columns for the accumulator
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
+                     "r"(kTmemCols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mbar_addr) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    for (int i = tid; i < H * IN; i += kRows) w1[i] = P[OFF_W1 + i];
+    for (int i = tid; i < H; i += kRows) {
+        b1[i] = P[OFF_B1 + i];
+        b2[i] = P[OFF_B2 + i];
+        w3[i] = P[OFF_W3 + i];
+    }
+    if (tid == 0) b3 = P[OFF_B3];
+    // W2 -> BF16 core matrices: 8 consecutive inputs of one output per 16-byte store
+    for (int c = tid; c < H * (H / 8); c += kRows) {
+        const int o = c / (H / 8), kg = c % (H / 8);
+        const float* src = P + OFF_W2 + o * H + kg * 8;
+        uint4 v;
+        v.x = pack_bf16(src[0], src[1]);
+        v.y = pack_bf16(src[2], src[3]);
+        v.z = pack_bf16(src[4], src[5]);
+        v.w = pack_bf16(src[6], src[7]);
+        *reinterpret_cast<uint4*>(b_tile + core_offset(o, kg * 8)) = v;
+    }
+    __syncthreads();
+    // layer 1 on the CUDA cores, one sample per thread -> BF16 A tile
+    const int s = blockIdx.x * kRows + tid;
+    float x[IN];
+#pragma unroll
+    for (int f = 0; f < IN; ++f) x[f] = s < n ? X[(size_t)s * IN + f] : 0.0f;
+#pragma unroll
+    for (int kg = 0; kg < H / 8; ++kg) {
+        float h[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int o = kg * 8 + u;
+            float a = b1[o];
+#pragma unroll
+            for (int f = 0; f < IN; ++f) a += w1[o * IN + f] * x[f];
+            h[u] = tanhf(a);
+        }
+        uint4 v;
+        v.x = pack_bf16(h[0], h[1]);
+        v.y = pack_bf16(h[2], h[3]);
+        v.z = pack_bf16(h[4], h[5]);
+        v.w = pack_bf16(h[6], h[7]);
+        *reinterpret_cast<uint4*>(a_tile + core_offset(tid, kg * 8)) = v;
+    }
+    // generic-proxy writes of the tiles -> visible to the tensor cores' async proxy
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = tmem_slot;
+    if (tid == 0) {
+        const uint32_t idesc = idesc_bf16(kRows, H);
+#pragma unroll
+        for (int kk = 0; kk < H / 16; ++kk) {   // K = 16 per instruction: two core matrices along K
+            const uint64_t da = smem_desc(a_addr + kk * 2 * kCoreBytes, kLbo, kSbo);
+            const uint64_t db = smem_desc(b_addr + kk * 2 * kCoreBytes, kLbo, kSbo);
+            const uint32_t acc = kk > 0 ? 1u : 0u;
+            asm volatile(
+                "{\n\t.reg .pred p;\n\t"
+                "setp.ne.b32 p, %4, 0;\n\t"
+                "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem),
+                "l"(da), "l"(db), "r"(idesc), "r"(acc)
+                : "memory");
+        }
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar_addr)
+                     : "memory");
+    }
+    const bool ok = mbar_wait(mbar_addr, 0);
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (ok) {
+        // this warp's 32 accumulator rows (TMEM lanes 32 warp ..), 16 columns per load
+        float y = b3;
+        const uint32_t row_addr = tmem + ((uint32_t)(warp * 32) << 16);
+#pragma unroll
+        for (int c0 = 0; c0 < H; c0 += 16) {
+            uint32_t r[16];
+            asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
+                         : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+                           "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+                           "=r"(r[14]), "=r"(r[15])
+                         : "r"(row_addr + (uint32_t)c0)
+                         : "memory");
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+            for (int u = 0; u < 16; ++u) y += w3[c0 + u] * tanhf(__uint_as_float(r[u]) + b2[c0 + u]);
+        }
+        if (s < n) Y[s] = y;
+    } else if (tid == 0) {
+        atomicExch(err, 1);
+        mbar_wait(mbar_addr, 0);   // give the tensor cores a second bounded chance to finish
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols) : "memory");
+    }
+}
+
+}  // namespace tc
+
+// Tensor-core forward pass of n samples; returns IBPME_ERR_TIMEOUT (after the
+// kernel has freed its tensor memory) if a wait for the tensor cores ran out.
+void forward_tc(const ibpme_mlp* m, int n, const float* feat, float* out, cudaStream_t s) {
+    if (n <= 0) return;
+    int* err = static_cast<int*>(const_cast<ibpme_mlp*>(m)->tc_err.ensure(sizeof(int)));
+    IBP_CUDA(cudaMemsetAsync(err, 0, sizeof(int), s));
+    IBP_CUDA(cudaFuncSetAttribute(tc::mlp_forward_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)tc::kSmem));
+    tc::mlp_forward_tc_kernel<<<div_up(n, tc::kRows), tc::kRows, tc::kSmem, s>>>(n, m->params.as<float>(), feat,
+                                                                                    out, err);
+    IBP_CHECK_LAUNCH();
+    int h = 0;
+    IBP_CUDA(cudaMemcpyAsync(&h, err, sizeof(int), cudaMemcpyDeviceToHost, s));
+    IBP_CUDA(cudaStreamSynchronize(s));
+    if (h) fail(IBPME_ERR_TIMEOUT, "tensor-core MLP forward: the wait for the tensor cores ran out");
 }
 
 // ---- gradient of the mean squared error over a batch ----
@@ -369,8 +586,7 @@ void learned_guess(ibpme_ctx* c, const ibpme_mlp* mlp, int n, const double* xw, 
     float* f = static_cast<float*>(feat.ensure(sizeof(float) * IN * (size_t)n * nrhs));
     compute_features(c, n, xw, E0, nrhs, f, scratch, scales);
     float* yy = static_cast<float*>(y.ensure(sizeof(float) * (size_t)n * nrhs));
-    mlp_forward_kernel<<<div_up((long long)n * nrhs, 128), 128, 0, s>>>(n * nrhs, mlp->params.as<float>(), f, yy);
-    IBP_CHECK_LAUNCH();
+    forward_tc(mlp, n * nrhs, f, yy, s);
     guess_from_net_kernel<<<div_up((long long)n * nrhs, 256), 256, 0, s>>>(n, bd.nb, nrhs, bd.bead_body.as<int>(),
                                                                            bd.off.as<int>(), bd.Q.as<double>(),
                                                                            scales.as<double>(), yy, q);
@@ -464,6 +680,14 @@ IBP_API ibpme_status ibpme_mlp_forward(ibpme_mlp* m, int n, const float* feat, f
         cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
         mlp_forward_kernel<<<div_up(n, 128), 128, 0, s>>>(n, m->params.as<float>(), feat, out);
         IBP_CHECK_LAUNCH();
+        return IBPME_OK;
+    });
+}
+
+IBP_API ibpme_status ibpme_mlp_forward_tc(ibpme_mlp* m, int n, const float* feat, float* out, void* cuda_stream) {
+    return mlp_guard([&]() -> ibpme_status {
+        if (!m || n < 0 || (n > 0 && (!feat || !out))) fail(IBPME_ERR_ARG, "bad argument");
+        forward_tc(m, n, feat, out, static_cast<cudaStream_t>(cuda_stream));
         return IBPME_OK;
     });
 }

@@ -127,3 +127,33 @@ def test_learned_warm_start_gains_over_zero_guess(cuda_lib):
     finally:
         ib.ibpme_mlp_destroy(m)
         ib.pme_destroy(ctx)
+
+
+def test_mlp_tensor_core_forward_matches_bf16_reference(cuda_lib):
+    """ibpme_mlp_forward_tc (tcgen05.mma, BF16 hidden layer) against the FP64
+    network with the hidden layer's operands rounded to BF16 (tight: checks the
+    tensor-core operand layout and accumulation), and against the FP32 network
+    within BF16 accuracy; 777 samples = six full 128-row tiles and a ragged one."""
+    import torch
+    ib = cuda_lib
+    m = ib.ibpme_mlp_create(seed=11)
+    try:
+        rng = np.random.default_rng(4)
+        n = 777
+        X = rng.normal(size=(n, M.IN)).astype(np.float32)
+        p = _params(ib, m)
+        y = torch.zeros(n, dtype=torch.float32, device="cuda")
+        ib.ibpme_mlp_forward_tc(m, n, cuda(X), y)
+        torch.cuda.synchronize()
+        got = y.cpu().numpy().astype(np.float64)
+        ref_q = M.forward_bf16_hidden(p, X)
+        ref = M.forward(p, X)
+        scale = max(1.0, np.abs(ref).max())
+        assert np.max(np.abs(got - ref_q)) < 2e-4 * scale, np.max(np.abs(got - ref_q))
+        assert np.max(np.abs(got - ref)) < 3e-2 * scale
+        # no sample is skipped or duplicated across tiles: compare sample by sample
+        assert np.argmax(np.abs(got - ref_q)) >= 0 and np.all(np.isfinite(got))
+        # empty input
+        ib.ibpme_mlp_forward_tc(m, 0, None, None)
+    finally:
+        ib.ibpme_mlp_destroy(m)

@@ -375,3 +375,22 @@ def test_mlp_reference_gradient_by_finite_differences():
         pm = p.copy(); pm[i] -= h
         fd = (M.loss_and_grad(pp, X, T)[0] - M.loss_and_grad(pm, X, T)[0]) / (2 * h)
         assert abs(fd - g[i]) < 1e-7 * max(1.0, abs(g[i]))
+
+
+def test_bf16_rounding_pins():
+    """round_bf16: representable values are fixed, halfway cases go to the even
+    neighbour, and every result is within half an ulp (2^-8 relative)."""
+    from oracle import mlp_ref as M
+    exact = np.array([1.0, -2.5, 1.0 + 2 ** -7, 3 * 2.0 ** -20], dtype=np.float32)
+    assert np.array_equal(M.round_bf16(exact), exact.astype(np.float64))
+    ties = np.array([1.0 + 2 ** -8, 1.0 + 3 * 2 ** -8], dtype=np.float32)
+    assert np.array_equal(M.round_bf16(ties), [1.0, 1.0 + 2 ** -6])
+    rng = np.random.default_rng(0)
+    x = rng.normal(size=10000).astype(np.float32)
+    r = M.round_bf16(x)
+    assert np.all(np.abs(r - x) <= 2.0 ** -8 * np.abs(x) + 1e-45)
+    # the quantised network equals the exact one when the hidden operands are already BF16
+    p = rng.normal(size=M.NPARAM) * 0.1
+    W1, b1, W2, b2, W3, b3 = M.unpack(p)
+    X = rng.normal(size=(50, M.IN))
+    assert np.max(np.abs(M.forward_bf16_hidden(p, X) - M.forward(p, X))) < 2e-2
