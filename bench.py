@@ -52,6 +52,17 @@ def peaks():
         return HBM_FALLBACK_GBS, "fallback"
 
 
+def measured_traffic(stage):
+    """DRAM bytes (read + write) per launch of the stage's kernel on this workload,
+    as recorded from an ncu capture in profiles/traffic.json; None if absent."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
+            d = json.load(f)
+        return d["charged-sphere"][stage]["dram_bytes_per_launch"]
+    except (OSError, KeyError, ValueError, TypeError):
+        return None
+
+
 def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -341,6 +352,7 @@ def bench_ours(args, ib, torch, rank, world, local):
     e2e_s = time.perf_counter() - t0
 
     peak, peak_kind = peaks()
+    traffic = measured_traffic(dominant)
     launches_dom = dom[1]
     avg_ms = dom[0] / launches_dom if launches_dom else float("nan")
     alg = stage_bytes(dominant, s, npairs)
@@ -364,7 +376,7 @@ def bench_ours(args, ib, torch, rank, world, local):
         "roofline": {"kernel": dominant, "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": (achieved / peak) if achieved else None, "peak_source": peak_kind,
                      "alg_bytes_per_launch": alg, "avg_launch_ms": avg_ms, "launches": launches_dom,
-                     "traffic": None},
+                     "traffic": traffic},
         "pme_evals_per_s": pme["evals_per_s"],
         "pme_roofline": pme["roofline"],
         "fp64_gpu": fp64,
@@ -441,7 +453,7 @@ def bench_polarizability(args, ib, torch, rank, world, local):
     from paper_2401_04865_gb300 import batch as B
     from workloads import configs as C
     torch.cuda.set_device(local)
-    systems = C.config4_batch(n_configs=64, seed=1003 + 7919 * rank, common_radius=True)
+    systems = C.config4_batch(n_configs=args.configs, seed=1003 + 7919 * rank, common_radius=True)
     bucket = B.Bucket(ib, systems, np.eye(3))
     a, eps, tol = systems[0].a, systems[0].eps, 1e-6
     tuner = B.Autotuner(cache_path=os.path.join(_tf.mkdtemp(), "tune.json"), candidates=(96, 128, 160))
@@ -494,7 +506,9 @@ def bench_polarizability(args, ib, torch, rank, world, local):
         "value": value, "unit": "configurations/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32 mesh / f64 krylov", "data": "synthetic",
-        "config": {"workload": POL_WORKLOAD, "n_beads": bucket.n, "mesh": [mesh] * 3,
+        "config": {"workload": POL_WORKLOAD if args.configs == 64 else
+                   f"{args.configs}-configuration prefix of: {POL_WORKLOAD}", "n_configs": args.configs,
+                   "n_beads": bucket.n, "mesh": [mesh] * 3,
                    "l2": "inputs larger than L2; 256 MB flush before every step, outside its events",
                    "parallelism": f"replicas x{world} (independent batches, no collective)"},
         "autotune": [{k: v for k, v in m.items()} for m in report],
@@ -566,6 +580,8 @@ def main():
     ap.add_argument("--skip-cpu", action="store_true", help="do not time the oracle on the host")
     ap.add_argument("--workload", default="charged-sphere", choices=["charged-sphere", "polarizability"],
                     help="the headline charged-sphere step, or the batched polarizability solve")
+    ap.add_argument("--configs", type=int, default=64,
+                    help="configurations in the polarizability batch (64 = the full workload)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
