@@ -17,7 +17,9 @@ Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
                        [--workload charged-sphere|polarizability]
 For N > 1 launch with torchrun; every rank runs its own replica (weak scaling).
 --workload polarizability times the batched solve of 64 independent
-configurations (three fields each) on the autotuned mesh instead.
+configurations (three fields each) on the autotuned mesh instead; --workload
+trajectory times BD steps of eight spheres in 20,000 ions with the zero, the
+previous-step and the learned initial guess.
 """
 from __future__ import annotations
 
@@ -520,6 +522,108 @@ def bench_polarizability(args, ib, torch, rank, world, local):
 
 
 # ---------------------------------------------------------------------------
+# Brownian-dynamics trajectory with three initial guesses (--workload trajectory)
+# ---------------------------------------------------------------------------
+
+TRAJ_WORKLOAD = ("trajectory: 8 polarizable spheres (642 beads each) + 20,000 monovalent ions, L=30, l_B=0.7, "
+                 "bead radius 0.05, E0=z, mesh 192^3, tol 1e-6; step = mixed-precision solve to FP64 residual "
+                 "1e-6 + forces/torques + one BD step (dt=1e-3, kT=1); initial guess: zero, the previous "
+                 "step's charges, or the learned warm start trained on the first steps")
+
+
+def bench_trajectory(args, ib, torch, rank, world, local):
+    from workloads import configs as C
+    torch.cuda.set_device(local)
+    s = C.config5_trajectory(seed=1004 + 7919 * rank)
+    dev, f64 = "cuda", torch.float64
+    t = lambda a, dt=f64: torch.as_tensor(np.ascontiguousarray(a)).to(dt).to(dev)
+    stream = torch.cuda.current_stream()
+    ctx = ib.pme_setup(ib.make_params(box=s.box, mesh=s.mesh, tol=s.tol, bead_radius=s.a, eps_f=s.eps,
+                                      precision=ib.IBPME_MIXED, max_rhs=1), stream)
+    n, nb = s.n, s.n_bodies
+    off, Q, E0 = t(s.body_offsets, torch.int32), t(s.Q), t(s.E0[:1])
+    x, X = t(s.x), t(s.X)
+    xn, Xn = torch.empty_like(x), torch.empty_like(X)
+    q = torch.zeros((1, n), dtype=f64, device=dev)
+    fb = torch.zeros((n, 3), dtype=f64, device=dev)
+    F = torch.zeros((nb, 3), dtype=f64, device=dev)
+    L = torch.zeros((nb, 3), dtype=f64, device=dev)
+    sizes = np.diff(s.body_offsets)
+    body_beads = torch.as_tensor(np.repeat(sizes > 1, sizes), device=dev)
+
+    def step(x, X, xn, Xn, k, guess, mlp=None):
+        bodies = ib.Bodies(off, X, Q)
+        opts = ib.make_opts(rtol=1e-6, guess=guess, mlp=mlp)
+        status, st = ib.induced_charge_solve(ctx, n, x, bodies, E0, 1, opts, q)
+        if status != ib.IBPME_OK:
+            raise RuntimeError("trajectory solve did not converge")
+        ib.body_force_torque(ctx, n, x, q[0], bodies, E0[0], fb, F, L)
+        ib.ibpme_bd_step(ctx, n, x, bodies, fb, 1e-3, 1.0, 1.0, 4321, k, xn, Xn)
+        return st
+
+    # training segment: zero-guess steps; converged charges -> (features, targets) of body beads
+    feats, targs = [], []
+    k = 0
+    for _ in range(12):
+        q.zero_()
+        step(x, X, xn, Xn, k, ib.IBPME_GUESS_ZERO)
+        f = torch.zeros((1, n, ib.IBPME_MLP_IN), dtype=torch.float32, device=dev)
+        tg = torch.zeros((1, n), dtype=torch.float32, device=dev)
+        ib.ibpme_features(ctx, n, x, ib.Bodies(off, X, Q), E0, 1, f, q, tg)
+        feats.append(f[0][body_beads])
+        targs.append(tg[0][body_beads])
+        x, xn, X, Xn, k = xn, x, Xn, X, k + 1
+    mlp = ib.ibpme_mlp_create(seed=5)
+    feat = torch.cat(feats).contiguous()
+    targ = torch.cat(targs).contiguous()
+    loss = ib.ibpme_mlp_train(mlp, feat.shape[0], feat, targ, batch=2048, epochs=60, lr=2e-3, seed=1)
+    x0, X0, k0 = x.clone(), X.clone(), k
+
+    modes = {}
+    for name, guess in (("zero", ib.IBPME_GUESS_ZERO), ("previous", ib.IBPME_GUESS_USER),
+                        ("learned", ib.IBPME_GUESS_LEARNED)):
+        x.copy_(x0)
+        X.copy_(X0)
+        k = k0
+        q.zero_()
+        for _ in range(args.warmup):
+            if guess == ib.IBPME_GUESS_ZERO:
+                q.zero_()
+            step(x, X, xn, Xn, k, guess, mlp)
+            x, xn, X, Xn, k = xn, x, Xn, X, k + 1
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+        its, init = [], []
+        torch.cuda.synchronize()
+        for i in range(args.steps):
+            if guess == ib.IBPME_GUESS_ZERO:
+                q.zero_()
+            ev[i][0].record(stream)
+            st = step(x, X, xn, Xn, k, guess, mlp)
+            ev[i][1].record(stream)
+            its.append(st.iters)
+            init.append(st.init_rel_residual)
+            x, xn, X, Xn, k = xn, x, Xn, X, k + 1
+        torch.cuda.synchronize()
+        ms = float(np.sum([a.elapsed_time(b) for a, b in ev]))
+        modes[name] = {"steps_per_s": args.steps / (ms / 1e3), "ms_per_step": ms / args.steps,
+                       "iters_mean": float(np.mean(its)), "init_rel_residual_mean": float(np.mean(init))}
+    ib.ibpme_mlp_destroy(mlp)
+    ib.pme_destroy(ctx)
+    best = modes["learned"]
+    return {
+        "metric": "BD steps/s (induced-charge solve + forces + BD step)", "value": world * best["steps_per_s"],
+        "unit": "steps/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": best["ms_per_step"], "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32 mesh / f64 krylov", "data": "synthetic",
+        "config": {"workload": TRAJ_WORKLOAD, "n_beads": n, "mesh": list(s.mesh),
+                   "l2": "inputs resident; positions advance every step",
+                   "parallelism": f"replicas x{world} (independent trajectories, no collective)"},
+        "guess_modes": modes, "training": {"samples": int(feat.shape[0]), "final_loss": loss, "solves": 12},
+        "cpu_baseline": None,
+    }
+
+
+# ---------------------------------------------------------------------------
 # the oracle on the host cores
 # ---------------------------------------------------------------------------
 
@@ -578,8 +682,9 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--skip-fp64", action="store_true", help="do not time the plain FP64 path")
     ap.add_argument("--skip-cpu", action="store_true", help="do not time the oracle on the host")
-    ap.add_argument("--workload", default="charged-sphere", choices=["charged-sphere", "polarizability"],
-                    help="the headline charged-sphere step, or the batched polarizability solve")
+    ap.add_argument("--workload", default="charged-sphere", choices=["charged-sphere", "polarizability", "trajectory"],
+                    help="the headline charged-sphere step, the batched polarizability solve, or a BD "
+                         "trajectory comparing initial guesses")
     ap.add_argument("--configs", type=int, default=64,
                     help="configurations in the polarizability batch (64 = the full workload)")
     args = ap.parse_args()
@@ -597,8 +702,9 @@ def main():
     if world > 1:
         torch.cuda.set_device(local)
         torch.distributed.init_process_group("nccl", device_id=torch.device("cuda", local))
-    if args.workload == "polarizability":
-        out = bench_polarizability(args, ib, torch, rank, world, local)
+    if args.workload in ("polarizability", "trajectory"):
+        fn = bench_polarizability if args.workload == "polarizability" else bench_trajectory
+        out = fn(args, ib, torch, rank, world, local)
         if rank == 0:
             print(json.dumps(out), flush=True)
         if world > 1:
