@@ -138,7 +138,19 @@ typedef struct {
     const void* mlp;    /* trained ibpme_mlp (IBPME_GUESS_LEARNED), else NULL */
     int precision;      /* -1 = context precision, else IBPME_FP64 / IBPME_MIXED (mixed needs a
                            mixed context) */
+    int precond;        /* IBPME_PRECOND_BODY (0, the default) or IBPME_PRECOND_NONE */
 } ibpme_solve_opts;
+
+/* Right preconditioner of the Krylov iteration (not in the paper; the converged
+ * solution and its FP64 residual test are the same either way).  BODY applies,
+ * for every multi-bead body, the exact inverse of the body's own saddle block with
+ * the free-space kernel of Sec. II, [-M_b e; e^T 0]^{-1}, and the identity to the
+ * rest; a configuration with a body of more than 1,024 beads is left
+ * unpreconditioned.  M_b depends only on
+ * the distances between a rigid body's beads, so the inverses are computed once
+ * per body shape (FP64 Gauss-Jordan on the device, kept in FP32) and cached in
+ * the context; identical bodies share one. */
+enum { IBPME_PRECOND_BODY = 0, IBPME_PRECOND_NONE = 1 };
 
 typedef struct {
     int iters;              /* Krylov iterations (operator applications inside GMRES) */

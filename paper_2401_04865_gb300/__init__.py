@@ -31,6 +31,8 @@ IBPME_MIXED = 1
 IBPME_GUESS_ZERO = 0
 IBPME_GUESS_USER = 1
 IBPME_GUESS_LEARNED = 2
+IBPME_PRECOND_BODY = 0
+IBPME_PRECOND_NONE = 1
 
 _d, _i, _p = ctypes.c_double, ctypes.c_int, ctypes.c_void_p
 
@@ -45,7 +47,8 @@ class ibpme_bodies(ctypes.Structure):
 
 
 class ibpme_solve_opts(ctypes.Structure):
-    _fields_ = [("rtol", _d), ("restart", _i), ("max_iter", _i), ("guess", _i), ("mlp", _p), ("precision", _i)]
+    _fields_ = [("rtol", _d), ("restart", _i), ("max_iter", _i), ("guess", _i), ("mlp", _p), ("precision", _i),
+                ("precond", _i)]
 
 
 class ibpme_solve_stats(ctypes.Structure):
@@ -283,9 +286,11 @@ def pme_field(ctx, n, x, q, nrhs, psi, E=None):
     return _check(load().pme_field(ctx, int(n), ptr(x), ptr(q), int(nrhs), ptr(psi), ptr(E)), "pme_field")
 
 
-def make_opts(rtol=1e-6, restart=50, max_iter=3000, guess=IBPME_GUESS_ZERO, precision=-1, mlp=None) -> ibpme_solve_opts:
+def make_opts(rtol=1e-6, restart=50, max_iter=3000, guess=IBPME_GUESS_ZERO, precision=-1, mlp=None,
+              precond=IBPME_PRECOND_BODY) -> ibpme_solve_opts:
     handle = mlp.value if isinstance(mlp, ctypes.c_void_p) else mlp
-    return ibpme_solve_opts(float(rtol), int(restart), int(max_iter), int(guess), handle, int(precision))
+    return ibpme_solve_opts(float(rtol), int(restart), int(max_iter), int(guess), handle, int(precision),
+                            int(precond))
 
 
 def induced_charge_solve(ctx, n, x, bodies: Bodies, E0, nrhs, opts: ibpme_solve_opts | None, q_out, psi_out=None,

@@ -540,6 +540,8 @@ ibpme_status solve_entry(ibpme_ctx* c, int n, const double* x, const ibpme_bodie
     if (o.guess != IBPME_GUESS_ZERO && o.guess != IBPME_GUESS_USER && o.guess != IBPME_GUESS_LEARNED)
         fail(IBPME_ERR_ARG, "unknown guess mode");
     if (o.guess == IBPME_GUESS_LEARNED && cfg_bodies) fail(IBPME_ERR_ARG, "a batched solve takes no learned guess");
+    if (o.precond != IBPME_PRECOND_BODY && o.precond != IBPME_PRECOND_NONE) fail(IBPME_ERR_ARG, "unknown precond");
+    a.precond = o.precond == IBPME_PRECOND_BODY;
     a.user_guess = o.guess == IBPME_GUESS_USER || o.guess == IBPME_GUESS_LEARNED;
     a.learned = o.guess == IBPME_GUESS_LEARNED;
     const double* dx = static_cast<const double*>(stage_in(c, x, sizeof(double) * 3 * n, c->st_x));

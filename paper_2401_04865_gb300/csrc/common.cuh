@@ -79,6 +79,20 @@ struct DevBuf {
         }
         return p;
     }
+    // grow to b bytes keeping the content (stream-ordered copy)
+    void* grow(size_t b, cudaStream_t s) {
+        if (b <= bytes) return p;
+        void* q = nullptr;
+        IBP_CUDA(cudaMalloc(&q, b));
+        if (p) {
+            IBP_CUDA(cudaMemcpyAsync(q, p, bytes, cudaMemcpyDeviceToDevice, s));
+            IBP_CUDA(cudaStreamSynchronize(s));
+            cudaFree(p);
+        }
+        p = q;
+        bytes = b;
+        return p;
+    }
     template <typename T>
     T* as() const { return static_cast<T*>(p); }
 };
@@ -203,6 +217,24 @@ struct BodyData {
 
 struct Krylov;   // krylov.cu
 
+// Body-block preconditioner (precond.cu): inverses of the bodies' free-space
+// saddle blocks, cached per body shape for the life of the context.
+constexpr int kPrecondMaxBeads = 1024;                      // larger bodies are left unpreconditioned
+constexpr long long kPrecondCacheBytes = 2LL << 30;         // FP32 inverses kept at most
+struct Precond {
+    struct Shape {
+        int nb;
+        double m2, m4;        // rotation-invariant moments of the bead cloud
+        long long off, goff;  // element offsets of M^{-1} and of g in minv / gvec
+    };
+    std::vector<Shape> shapes;
+    long long used = 0, gused = 0;
+    DevBuf minv, gvec, sinv, shape_off, shape_goff;   // per shape
+    DevBuf pb_shape, pb_first, pb_psi, pb_n, plain;   // per solve: preconditioned bodies, identity unknowns
+    DevBuf moments, work, col;                        // set-up scratch
+    int npb = 0, nplain = 0, chunks = 0;
+};
+
 // Optional per-stage timing with CUDA events on the launching stream.
 enum Stage {
     ST_NEAR_BUILD = 0,   // cell list + pair table
@@ -273,6 +305,7 @@ struct ibpme_ctx {
     ibp::DevBuf ml_feat, ml_scratch, ml_scales, ml_y;   // learned warm start
     cudaEvent_t ev_in = nullptr, ev_out = nullptr;
     ibp::StencilCache stencils;               // stencils of the current positions
+    ibp::Precond pre;                         // body-block preconditioner
     cudaStream_t aux = nullptr;               // second branch of a PME evaluation (near field)
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
 };
@@ -332,8 +365,12 @@ struct SolveArgs {
     bool learned;       // the guess came from the learned model: fall back to zero if it is worse
     double rtol;
     int restart, max_iter;
+    bool precond;       // body-block right preconditioner
 };
 void solve(ibpme_ctx* c, const SolveArgs& a, ibpme_solve_stats* st);
+// precond.cu
+bool precond_prepare(ibpme_ctx* c);   // false: no body qualifies
+void precond_apply(ibpme_ctx* c, int R, const double* u, long long ustride, const int* jdev, int nk, double* out);
 void krylov_destroy(ibpme_ctx* c);
 
 // small device helpers

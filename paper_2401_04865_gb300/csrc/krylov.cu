@@ -36,6 +36,7 @@ namespace ibp {
 struct Krylov {
     int nk = 0, R = 0, S = 0, m = 0, nblk = 0;
     DevBuf V, H, cs, sn, g, y, w, x, d, r, rc, part, scal, active, qop, psi, psi_tot, qtot, Ax, norms, jdev;
+    DevBuf pu, pt, pz;   // preconditioned operand, cycle update before and after P^{-1}
     // one captured Arnoldi iteration per mesh precision, replayed for every j
     cudaGraphExec_t exec[2] = {nullptr, nullptr};
     std::vector<long long> sig[2];
@@ -585,6 +586,7 @@ struct Solver {
     const SolveArgs& a;
     int n, R, S, ncfg, nk, nfree, nmb, nb, m;
     int iters = 0, matvec64 = 0;
+    bool pre_on = false;         // body-block preconditioner active for this solve
     std::vector<double> bnorm;   // |b| per system
 
     Solver(ibpme_ctx* c_, const SolveArgs& a_) : c(c_), k(c_->kry), a(a_) {
@@ -620,7 +622,8 @@ struct Solver {
         k->sn.ensure(sizeof(double) * (size_t)S * m);
         k->g.ensure(sizeof(double) * (size_t)S * (m + 1));
         k->y.ensure(sizeof(double) * (size_t)S * m);
-        for (DevBuf* b : {&k->w, &k->x, &k->d, &k->r, &k->rc, &k->Ax}) b->ensure(sizeof(double) * v);
+        for (DevBuf* b : {&k->w, &k->x, &k->d, &k->r, &k->rc, &k->Ax, &k->pu, &k->pt, &k->pz})
+            b->ensure(sizeof(double) * v);
         k->part.ensure(sizeof(double) * (size_t)R * k->nblk * (m + 2));
         k->scal.ensure(sizeof(double) * (size_t)S * S_COUNT);
         k->active.ensure(sizeof(int) * S);
@@ -631,10 +634,17 @@ struct Solver {
     }
 
     // y = A(prec) u for the reduced saddle operator; u[r] starts at u + r * ustride
-    // (+ j * nk with j read on the device when jdev is given)
-    void apply(int prec, const double* u, double* y, long long ustride = -1, const int* jdev = nullptr) {
+    // (+ j * nk with j read on the device when jdev is given); with pre, y = A P^{-1} u
+    void apply(int prec, const double* u, double* y, long long ustride = -1, const int* jdev = nullptr,
+               bool pre = false) {
         const BodyData& bd = c->bodies;
         if (ustride < 0) ustride = nk;
+        if (pre && pre_on) {
+            precond_apply(c, R, u, ustride, jdev, nk, D(k->pu));
+            u = D(k->pu);
+            ustride = nk;
+            jdev = nullptr;
+        }
         scatter_kernel<<<blocks_for((long long)nfree * R), 256, 0, s()>>>(nfree, ustride, n, R, I(bd.free_idx),
                                                                           I(bd.free_unk), u, jdev, nk, D(k->qop));
         IBP_CHECK_LAUNCH();
@@ -651,7 +661,7 @@ struct Solver {
     // V_0..V_j, Givens on column j, V_{j+1} = w / h_{j+1,j}, j += 1 (every system).
     void iterate(int prec) {
         int* jd = k->jdev.as<int>();
-        apply(prec, D(k->V), D(k->w), (long long)(m + 1) * nk, jd);
+        apply(prec, D(k->V), D(k->w), (long long)(m + 1) * nk, jd, true);
         ProfScope ps(ST_KRYLOV, s());
         if (clustered()) {
             int max_len = 0;
@@ -714,6 +724,11 @@ struct Solver {
                                       P(bd.free_unk.p), P(bd.bead_body.p), P(bd.body_unk.p), P(bd.mb_unk.p),
                                       P(bd.mb_first.p), P(bd.mb_cnt.p), P(bd.uo.p), P(c->bcfg),
                                       (long long)c->stencils.valid, P(c->stencils.start.p), P(c->stencils.frac.p),
+                                      (long long)pre_on, (long long)c->pre.npb, (long long)c->pre.nplain,
+                                      (long long)c->pre.chunks, P(k->pu.p), P(c->pre.minv.p), P(c->pre.gvec.p),
+                                      P(c->pre.sinv.p), P(c->pre.pb_shape.p), P(c->pre.pb_first.p),
+                                      P(c->pre.pb_psi.p), P(c->pre.pb_n.p), P(c->pre.plain.p),
+                                      P(c->pre.shape_off.p), P(c->pre.shape_goff.p),
                                       P(prec == IBPME_MIXED ? m32.grid.p : m64.grid.p),
                                       P(prec == IBPME_MIXED ? m32.spec.p : m64.spec.p),
                                       P(prec == IBPME_MIXED ? m32.work.p : m64.work.p)};
@@ -857,9 +872,19 @@ struct Solver {
             }
             trisolve_kernel<<<S, 32, 0, s()>>>(m, kk, D(k->H), D(k->g), k->active.as<int>(), D(k->y));
             IBP_CHECK_LAUNCH();
-            xupdate_kernel<<<blocks_for(len), 256, 0, s()>>>(nk, m, kk, R, I(c->bodies.unk_cfg), D(k->V), D(k->y),
-                                                             dd);
-            IBP_CHECK_LAUNCH();
+            if (pre_on) {   // the cycle's correction is P^{-1} (V y)
+                IBP_CUDA(cudaMemsetAsync(k->pt.p, 0, sizeof(double) * len, s()));
+                xupdate_kernel<<<blocks_for(len), 256, 0, s()>>>(nk, m, kk, R, I(c->bodies.unk_cfg), D(k->V),
+                                                                 D(k->y), D(k->pt));
+                IBP_CHECK_LAUNCH();
+                precond_apply(c, R, D(k->pt), nk, nullptr, nk, D(k->pz));
+                axpby_kernel<<<blocks_for(len), 256, 0, s()>>>(len, 1.0, dd, 1.0, D(k->pz), dd);
+                IBP_CHECK_LAUNCH();
+            } else {
+                xupdate_kernel<<<blocks_for(len), 256, 0, s()>>>(nk, m, kk, R, I(c->bodies.unk_cfg), D(k->V),
+                                                                 D(k->y), dd);
+                IBP_CHECK_LAUNCH();
+            }
             // the estimate reached the target: the caller's full-system residual decides
             if (cycle_converged || iters >= a.max_iter) return;
             // restart: residual of this operator for the next cycle
@@ -875,6 +900,7 @@ struct Solver {
     void run(ibpme_solve_stats* st) {
         const BodyData& bd = c->bodies;
         alloc();
+        pre_on = a.precond && nk > 0 && precond_prepare(c);
         const long long len = (long long)nk * R;
         IBP_CUDA(cudaMemsetAsync(k->qop.p, 0, sizeof(double) * (size_t)R * n, s()));   // ions stay 0
         // |b| of the full system of Eq. saddle, b = [-r.E0 ; Q], per system

@@ -1,0 +1,345 @@
+// precond.cu -- body-block right preconditioner of the reduced saddle system
+// (Sec. III.B, Eq. saddle), a solver choice outside the paper.
+//
+// Within one rigid body the saddle operator is dominated by the body's own
+// interactions.  For every multi-bead body of at most kPrecondMaxBeads beads
+// the preconditioner applies the exact inverse of that body's free-space block
+//     P_b = [ -M_b  e ]      M_b(i, j) = M(|r_i - r_j|)   (Sec. II: 1/(4 pi eps r) for
+//           [  e^T  0 ]                                   r >= 2a, (4a - r)/(16 pi a^2 eps) below)
+// and the identity elsewhere.  With g = M_b^{-1} e and s = e^T g,
+//     P_b^{-1} [v; psi] = [ -M_b^{-1} v + g t ; t ],   t = (g . v + psi) / s.
+// M_b depends only on the distances between the body's beads, so it is the
+// same for every position and orientation of a rigid body: inverses are kept
+// per body shape (bead count and two rotation-invariant moments of the bead
+// cloud) for the life of the context, and identical bodies share one.  GMRES
+// then iterates on A P^{-1} (right preconditioning keeps the residual of the
+// original system); only the inter-body coupling and the periodic images are
+// left to the Krylov iteration.
+#include "common.cuh"
+
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+namespace ibp {
+
+namespace {
+
+constexpr double kPi = 3.14159265358979323846264338327950288;
+
+// moments of body b's bead cloud about its centroid: sum |d|^2, sum |d|^4 (rotation invariant)
+__global__ void shape_moments_kernel(int nmb, const int* __restrict__ mb_body, const int* __restrict__ off,
+                                     const double* __restrict__ rel, double* __restrict__ out) {
+    __shared__ double sh[3][32];
+    const int b = blockIdx.x;
+    if (b >= nmb) return;
+    const int body = mb_body[b];
+    const int j0 = off[body], j1 = off[body + 1];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    double c[3] = {0.0, 0.0, 0.0};
+    for (int j = j0 + threadIdx.x; j < j1; j += blockDim.x)
+        for (int d = 0; d < 3; ++d) c[d] += rel[3 * j + d];
+    for (int d = 0; d < 3; ++d) {
+        double v = warp_sum(c[d]);
+        if (lane == 0) sh[d][w] = v;
+    }
+    __syncthreads();
+    for (int d = 0; d < 3; ++d) {
+        double t = 0.0;
+        for (int q = 0; q < (int)(blockDim.x >> 5); ++q) t += sh[d][q];
+        c[d] = t / (double)(j1 - j0);
+    }
+    __syncthreads();
+    double m2 = 0.0, m4 = 0.0;
+    for (int j = j0 + threadIdx.x; j < j1; j += blockDim.x) {
+        const double dx = rel[3 * j] - c[0], dy = rel[3 * j + 1] - c[1], dz = rel[3 * j + 2] - c[2];
+        const double r2 = dx * dx + dy * dy + dz * dz;
+        m2 += r2;
+        m4 += r2 * r2;
+    }
+    m2 = warp_sum(m2);
+    m4 = warp_sum(m4);
+    if (lane == 0) {
+        sh[0][w] = m2;
+        sh[1][w] = m4;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double a = 0.0, bq = 0.0;
+        for (int q = 0; q < (int)(blockDim.x >> 5); ++q) {
+            a += sh[0][q];
+            bq += sh[1][q];
+        }
+        out[2 * b] = a;
+        out[2 * b + 1] = bq;
+    }
+}
+
+// M_b of one body from its beads' relative positions (row-major nb x nb)
+__global__ void block_matrix_kernel(int nb, const double* __restrict__ rel, double a, double eps,
+                                    double* __restrict__ A) {
+    const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (t >= (long long)nb * nb) return;
+    const int i = (int)(t / nb), j = (int)(t % nb);
+    const double dx = rel[3 * i] - rel[3 * j], dy = rel[3 * i + 1] - rel[3 * j + 1],
+                 dz = rel[3 * i + 2] - rel[3 * j + 2];
+    const double r = sqrt(dx * dx + dy * dy + dz * dz);
+    A[t] = r >= 2.0 * a ? 1.0 / (4.0 * kPi * eps * r) : (4.0 * a - r) / (16.0 * kPi * a * a * eps);
+}
+
+// Gauss-Jordan inversion in place without pivoting (M_b is symmetric positive
+// definite), step k: scale row k, keep column k for the elimination.
+__global__ void gj_pivot_kernel(int nb, int k, double* __restrict__ A, double* __restrict__ colk) {
+    const double p = A[(size_t)k * nb + k];
+    __syncthreads();   // every thread has read the pivot before row k changes
+    for (int i = threadIdx.x; i < nb; i += blockDim.x) colk[i] = A[(size_t)i * nb + k];
+    __syncthreads();
+    const double ip = 1.0 / p;
+    for (int j = threadIdx.x; j < nb; j += blockDim.x) {
+        const double v = j == k ? 1.0 : A[(size_t)k * nb + j];
+        A[(size_t)k * nb + j] = v * ip;
+    }
+}
+
+__global__ void gj_eliminate_kernel(int nb, int k, double* __restrict__ A, const double* __restrict__ colk) {
+    const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (t >= (long long)nb * nb) return;
+    const int i = (int)(t / nb), j = (int)(t % nb);
+    if (i == k) return;
+    const double f = colk[i];
+    const double rk = A[(size_t)k * nb + j];
+    A[t] = (j == k ? 0.0 : A[t]) - f * rk;
+}
+
+// g = M^{-1} e (row sums), M^{-1} rounded to FP32
+__global__ void finish_shape_kernel(int nb, const double* __restrict__ A, float* __restrict__ minv,
+                                    float* __restrict__ g) {
+    __shared__ double sh[32];
+    const int i = blockIdx.x;
+    double acc = 0.0;
+    for (int j = threadIdx.x; j < nb; j += blockDim.x) {
+        const double v = A[(size_t)i * nb + j];
+        minv[(size_t)i * nb + j] = (float)v;
+        acc += v;
+    }
+    acc = warp_sum(acc);
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int q = 0; q < (int)(blockDim.x >> 5); ++q) t += sh[q];
+        g[i] = (float)t;
+    }
+}
+
+__global__ void shape_s_kernel(int nb, const float* __restrict__ g, double* __restrict__ sinv) {
+    __shared__ double sh[32];
+    double acc = 0.0;
+    for (int i = threadIdx.x; i < nb; i += blockDim.x) acc += (double)g[i];
+    acc = warp_sum(acc);
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int q = 0; q < (int)(blockDim.x >> 5); ++q) t += sh[q];
+        *sinv = 1.0 / t;
+    }
+}
+
+constexpr int kRowsPerBlock = 32;
+constexpr int kApplyThreads = 256;
+
+// out = P^{-1} u on the preconditioned bodies (grid: bodies x row chunks, R) and
+// out = u on every other unknown (the trailing blocks of the grid).
+__global__ void __launch_bounds__(kApplyThreads)
+precond_apply_kernel(int npb, int chunks, int nk, long long ustride, const int* __restrict__ jdev,
+                     const int* __restrict__ pb_shape, const int* __restrict__ pb_first,
+                     const int* __restrict__ pb_psi, const int* __restrict__ pb_n,
+                     const long long* __restrict__ shape_off, const long long* __restrict__ shape_goff,
+                     const float* __restrict__ minv,
+                     const float* __restrict__ gvec, const double* __restrict__ sinv, int nplain,
+                     const int* __restrict__ plain, const double* __restrict__ u, double* __restrict__ out) {
+    __shared__ double v[kPrecondMaxBeads];
+    __shared__ double sh[32];
+    __shared__ double tpsi;
+    const int r = blockIdx.y;
+    if (jdev) u += (size_t)(*jdev) * nk;
+    const double* ur = u + (size_t)r * ustride;
+    double* orow = out + (size_t)r * nk;
+    const int body_blocks = npb * chunks;
+    if ((int)blockIdx.x >= body_blocks) {   // identity on the unknowns no block covers
+        const long long t = ((long long)blockIdx.x - body_blocks) * kApplyThreads + threadIdx.x;
+        if (t < nplain) orow[plain[t]] = ur[plain[t]];
+        return;
+    }
+    const int p = blockIdx.x / chunks, chunk = blockIdx.x % chunks;
+    const int nb = pb_n[p], first = pb_first[p], sh_id = pb_shape[p];
+    const float* M = minv + shape_off[sh_id];
+    const float* gv = gvec + shape_goff[sh_id];
+    for (int j = threadIdx.x; j < nb; j += kApplyThreads) v[j] = ur[first + j];
+    __syncthreads();
+    double acc = 0.0;
+    for (int j = threadIdx.x; j < nb; j += kApplyThreads) acc += (double)gv[j] * v[j];
+    acc = warp_sum(acc);
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int q = 0; q < kApplyThreads / 32; ++q) t += sh[q];
+        tpsi = (t + ur[pb_psi[p]]) * sinv[sh_id];
+    }
+    __syncthreads();
+    const double tp = tpsi;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int i0 = chunk * kRowsPerBlock;
+    for (int i = i0 + warp; i < min(nb, i0 + kRowsPerBlock); i += kApplyThreads / 32) {
+        const float* Mi = M + (size_t)i * nb;
+        double s = 0.0;
+        for (int j = lane; j < nb; j += 32) s += (double)Mi[j] * v[j];
+        s = warp_sum(s);
+        if (lane == 0) orow[first + i] = -s + (double)gv[i] * tp;
+    }
+    if (chunk == 0 && threadIdx.x == 0) orow[pb_psi[p]] = tp;
+}
+
+}  // namespace
+
+// Shapes of the current bodies: reuse cached inverses, build the missing ones,
+// and lay out the per-body tables of the apply kernel.  Returns false when no
+// body qualifies (the solve then runs unpreconditioned).
+bool precond_prepare(ibpme_ctx* c) {
+    Precond& P = c->pre;
+    const BodyData& bd = c->bodies;
+    cudaStream_t s = c->stream;
+    P.npb = 0;
+    if (bd.nmb == 0) return false;
+    std::vector<int> mb_body(bd.nmb), mb_first(bd.nmb), mb_cnt(bd.nmb), mb_unk(bd.nmb);
+    IBP_CUDA(cudaMemcpyAsync(mb_body.data(), bd.mb_body.p, sizeof(int) * bd.nmb, cudaMemcpyDeviceToHost, s));
+    IBP_CUDA(cudaMemcpyAsync(mb_first.data(), bd.mb_first.p, sizeof(int) * bd.nmb, cudaMemcpyDeviceToHost, s));
+    IBP_CUDA(cudaMemcpyAsync(mb_cnt.data(), bd.mb_cnt.p, sizeof(int) * bd.nmb, cudaMemcpyDeviceToHost, s));
+    IBP_CUDA(cudaMemcpyAsync(mb_unk.data(), bd.mb_unk.p, sizeof(int) * bd.nmb, cudaMemcpyDeviceToHost, s));
+    double* mom = static_cast<double*>(P.moments.ensure(sizeof(double) * 2 * bd.nmb));
+    shape_moments_kernel<<<bd.nmb, 256, 0, s>>>(bd.nmb, bd.mb_body.as<int>(), bd.off.as<int>(), bd.rel.as<double>(),
+                                                mom);
+    IBP_CHECK_LAUNCH();
+    std::vector<double> hm(2 * (size_t)bd.nmb);
+    IBP_CUDA(cudaMemcpyAsync(hm.data(), mom, sizeof(double) * 2 * bd.nmb, cudaMemcpyDeviceToHost, s));
+    IBP_CUDA(cudaStreamSynchronize(s));
+    const std::vector<int>& off = bd.host_off;
+
+    // A configuration is preconditioned only if every one of its multi-bead bodies
+    // qualifies: a system mixing P_b^{-1} blocks (eigenvalues near 1) with raw
+    // blocks of M (eigenvalues near the self term) converges slower than either.
+    const std::vector<int>& cb = bd.cfg_bodies_h;
+    auto cfg_of = [&](int body) {
+        return (int)(std::upper_bound(cb.begin(), cb.end(), body) - cb.begin()) - 1;
+    };
+    std::vector<char> cfg_ok(std::max(1, bd.ncfg), 1);
+    for (int b = 0; b < bd.nmb; ++b)
+        if (mb_cnt[b] > kPrecondMaxBeads) cfg_ok[cfg_of(mb_body[b])] = 0;
+    std::vector<int> pb_shape, pb_first, pb_psi, pb_n;
+    std::vector<char> covered(bd.nk, 0);
+    for (int b = 0; b < bd.nmb; ++b) {
+        const int nb = mb_cnt[b];
+        if (nb > kPrecondMaxBeads || !cfg_ok[cfg_of(mb_body[b])]) continue;
+        const double m2 = hm[2 * b], m4 = hm[2 * b + 1];
+        int id = -1;
+        for (size_t q = 0; q < P.shapes.size(); ++q) {
+            const Precond::Shape& sp = P.shapes[q];
+            if (sp.nb == nb && std::fabs(sp.m2 - m2) <= 1e-9 * std::fabs(m2) + 1e-300 &&
+                std::fabs(sp.m4 - m4) <= 1e-9 * std::fabs(m4) + 1e-300) {
+                id = (int)q;
+                break;
+            }
+        }
+        if (id < 0) {   // a new shape: build M_b from this body, invert, keep FP32 M^{-1}, g and 1/s
+            const long long need = P.used + (long long)nb * nb;
+            if (need * (long long)sizeof(float) > kPrecondCacheBytes) {   // cache full: start over
+                P.shapes.clear();
+                P.used = 0;
+                P.gused = 0;
+                pb_shape.clear();   // the bodies already listed refer to dropped shapes: redo them
+                pb_first.clear();
+                pb_psi.clear();
+                pb_n.clear();
+                std::fill(covered.begin(), covered.end(), 0);
+                b = -1;
+                continue;
+            }
+            Precond::Shape sp;
+            sp.nb = nb;
+            sp.m2 = m2;
+            sp.m4 = m4;
+            sp.off = P.used;
+            sp.goff = P.gused;
+            P.used += (long long)nb * nb;
+            P.gused += nb;
+            P.minv.grow(sizeof(float) * (size_t)P.used, s);
+            P.gvec.grow(sizeof(float) * (size_t)P.gused, s);
+            P.sinv.grow(sizeof(double) * (P.shapes.size() + 1), s);
+            double* A = static_cast<double*>(P.work.ensure(sizeof(double) * (size_t)nb * nb));
+            double* colk = static_cast<double*>(P.col.ensure(sizeof(double) * (size_t)nb));
+            const double* rel = bd.rel.as<double>() + 3 * (size_t)off[mb_body[b]];
+            const long long nn = (long long)nb * nb;
+            block_matrix_kernel<<<div_up(nn, 256), 256, 0, s>>>(nb, rel, c->a, c->eps, A);
+            IBP_CHECK_LAUNCH();
+            for (int k = 0; k < nb; ++k) {
+                gj_pivot_kernel<<<1, 256, 0, s>>>(nb, k, A, colk);
+                gj_eliminate_kernel<<<div_up(nn, 256), 256, 0, s>>>(nb, k, A, colk);
+            }
+            IBP_CHECK_LAUNCH();
+            finish_shape_kernel<<<nb, 128, 0, s>>>(nb, A, P.minv.as<float>() + sp.off, P.gvec.as<float>() + sp.goff);
+            IBP_CHECK_LAUNCH();
+            id = (int)P.shapes.size();
+            shape_s_kernel<<<1, 256, 0, s>>>(nb, P.gvec.as<float>() + sp.goff, P.sinv.as<double>() + id);
+            IBP_CHECK_LAUNCH();
+            P.shapes.push_back(sp);
+        }
+        pb_shape.push_back(id);
+        pb_first.push_back(mb_first[b]);
+        pb_psi.push_back(mb_unk[b]);
+        pb_n.push_back(nb);
+        for (int i = 0; i < nb; ++i) covered[mb_first[b] + i] = 1;
+        covered[mb_unk[b]] = 1;
+    }
+    if (pb_shape.empty()) return false;
+    std::vector<int> plain;
+    for (int u = 0; u < bd.nk; ++u)
+        if (!covered[u]) plain.push_back(u);
+    std::vector<long long> shape_off(P.shapes.size()), shape_goff(P.shapes.size());
+    for (size_t q = 0; q < P.shapes.size(); ++q) {
+        shape_off[q] = P.shapes[q].off;
+        shape_goff[q] = P.shapes[q].goff;
+    }
+    auto up = [&](DevBuf& dst, const void* src, size_t bytes) {
+        dst.ensure(bytes > 0 ? bytes : 4);
+        if (bytes) IBP_CUDA(cudaMemcpyAsync(dst.p, src, bytes, cudaMemcpyHostToDevice, s));
+    };
+    up(P.pb_shape, pb_shape.data(), sizeof(int) * pb_shape.size());
+    up(P.pb_first, pb_first.data(), sizeof(int) * pb_first.size());
+    up(P.pb_psi, pb_psi.data(), sizeof(int) * pb_psi.size());
+    up(P.pb_n, pb_n.data(), sizeof(int) * pb_n.size());
+    up(P.plain, plain.data(), sizeof(int) * plain.size());
+    up(P.shape_off, shape_off.data(), sizeof(long long) * shape_off.size());
+    up(P.shape_goff, shape_goff.data(), sizeof(long long) * shape_goff.size());
+    IBP_CUDA(cudaStreamSynchronize(s));   // host vectors go out of scope
+    P.npb = (int)pb_shape.size();
+    P.nplain = (int)plain.size();
+    int maxn = 0;
+    for (int v : pb_n) maxn = std::max(maxn, v);
+    P.chunks = div_up(maxn, kRowsPerBlock);
+    return true;
+}
+
+void precond_apply(ibpme_ctx* c, int R, const double* u, long long ustride, const int* jdev, int nk, double* out) {
+    const Precond& P = c->pre;
+    const int blocks = P.npb * P.chunks + div_up(P.nplain > 0 ? P.nplain : 1, kApplyThreads);
+    precond_apply_kernel<<<dim3(blocks, R), kApplyThreads, 0, c->stream>>>(
+        P.npb, P.chunks, nk, ustride, jdev, P.pb_shape.as<int>(), P.pb_first.as<int>(), P.pb_psi.as<int>(),
+        P.pb_n.as<int>(), P.shape_off.as<long long>(), P.shape_goff.as<long long>(), P.minv.as<float>(),
+        P.gvec.as<float>(),
+        P.sinv.as<double>(), P.nplain, P.plain.as<int>(), u, out);
+    IBP_CHECK_LAUNCH();
+}
+
+}  // namespace ibp
