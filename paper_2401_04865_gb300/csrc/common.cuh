@@ -252,6 +252,7 @@ enum Stage {
     ST_FFT_INV64,
     ST_GATHER64,
     ST_NEAR_APPLY32,     // real-space SpMV, FP32 pass (inner operator of mixed solves)
+    ST_NEAR_FIELD,       // real-space field (force pass)
     ST_COUNT
 };
 // stage of a mesh step for the mesh precision T

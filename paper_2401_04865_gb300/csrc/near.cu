@@ -699,7 +699,7 @@ void near_apply(ibpme_ctx* c, int n, const double* q, int nrhs, double* psi_r, b
 
 void near_field(ibpme_ctx* c, int n, const double* xw, const double* q, int nrhs, double* E_r) {
     if (n == 0) return;
-    ProfScope ps(ST_NEAR_APPLY, c->stream);
+    ProfScope ps(ST_NEAR_FIELD, c->stream);
     if (!c->near.have_grad) fail(IBPME_ERR_ARG, "internal: pair table built without gradients");
     NearList& nl = c->near;
     const PairConst k = make_const(c);
