@@ -145,10 +145,13 @@ struct Mesh {
     DevBuf green;   // [Gc] real: G(k) / (N_x N_y N_z), 0 at k = 0
     DevBuf work;    // cuFFT work area shared by the plans
     std::map<int, std::pair<cufftHandle, cufftHandle>> plan;   // R2C and C2R plans by channel count
+    // FP64 meshes of power-of-two sizes: double-float transforms instead of cuFFT (dffft.cu)
+    bool df = false;
+    DevBuf df_tw[3], df_buf;
     void init(const MeshGeom& geom, int channels, double xi, double eta, double a, cudaStream_t s);
     void destroy();
     void ensure_channels(int ch);
-    void plans(int ch, cudaStream_t s);
+    void plans(int ch, cudaStream_t s);   // every resource a transform of ch channels needs
     // bead_cfg (device, or NULL for one configuration) maps each bead to its configuration
     // sc: cached stencils of these positions, or NULL to derive them in the kernels
     void spread(int n, const double* xw, const double* q, int nrhs, const int* bead_cfg, int ncfg, cudaStream_t s,
@@ -322,6 +325,12 @@ void near_build(ibpme_ctx* c, int n, const double* xw, bool need_grad);
 void near_apply(ibpme_ctx* c, int n, const double* q, int nrhs, double* psi_r, bool fp32 = false);
 void near_field(ibpme_ctx* c, int n, const double* xw, const double* q, int nrhs, double* E_r);  // overwrite
 double self_term(const ibpme_ctx* c);   // phi_self (without 1/eps)
+
+// ---- dffft.cu ----
+bool df_fft_supported(const MeshGeom& g);
+void df_fft_init(const MeshGeom& g, DevBuf tw[3], cudaStream_t s);
+void df_fft_convolve(const MeshGeom& g, int ch, const double* green, double* grid, float4* S, DevBuf tw[3],
+                     cudaStream_t s);
 
 // ---- mesh.cu ----
 // Cached stencils for the current positions (rebuilt when the position

@@ -1,0 +1,292 @@
+// dffft.cu -- the FP64 mesh's 3-D transforms in double-float arithmetic.
+//
+// The true residual of a mixed-precision solve and every FP64-context PME
+// evaluation (Sec. III.D.3 steps 3-5) transform the FP64 grid.  GB300 executes
+// FP64 at a small fraction of its FP32 rate, and cuFFT's D2Z/Z2D of a 128^3 grid
+// is bound by that FP64 pipe.  Here each value is carried as an unevaluated sum
+// of two floats (hi + lo, about 48 significant bits; error-free transformations
+// of Dekker and Knuth: two-sum, and two-product with a fused multiply-add), so
+// the butterflies run on the FP32 pipes.  The transform is a radix-2 complex FFT
+// along x, y and z (power-of-two sizes), the Green's-function scaling of the
+// FP64 table is fused between the forward and inverse z passes, and the real
+// part comes back as FP64.  Sizes that are not powers of two use cuFFT.
+#include "common.cuh"
+
+#include <cmath>
+#include <vector>
+
+namespace ibp {
+
+namespace {
+
+constexpr int kDfPoints = 2048;   // points per block (lines x line length)
+constexpr int kDfThreads = 1024;  // one butterfly per thread per stage
+constexpr int kDfPad = 1;         // float4 of padding after each line in shared memory (bank spread)
+constexpr int kDfSmem = kDfPoints + kDfPoints / 16 * kDfPad;   // lines <= kDfPoints / 16
+
+// ---- double-float arithmetic (round-to-nearest intrinsics: no contraction) ----
+// Accuracy: each operation is exact to about 2^-44 of its operands' magnitude, so
+// a length-N transform keeps a normwise error near log2(N) 2^-44, far below the
+// FP32 mesh and the 1e-6 residual test it serves.
+struct df {
+    float hi, lo;
+};
+
+__device__ __forceinline__ df two_sum(float a, float b) {
+    const float s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    const float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+    return {s, e};
+}
+
+__device__ __forceinline__ df fast_two_sum(float a, float b) {   // |a| >= |b|
+    const float s = __fadd_rn(a, b);
+    return {s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+
+// Sum with one two-sum on the high parts: its error is bounded relative to
+// |a| + |b| (not to |a + b|), which is what a normwise FFT error bound needs.
+__device__ __forceinline__ df df_add(df a, df b) {
+    const df s = two_sum(a.hi, b.hi);
+    return fast_two_sum(s.hi, __fadd_rn(s.lo, __fadd_rn(a.lo, b.lo)));
+}
+
+__device__ __forceinline__ df df_neg(df a) { return {-a.hi, -a.lo}; }
+
+__device__ __forceinline__ df df_mul(df a, df b) {
+    const float p = __fmul_rn(a.hi, b.hi);
+    float e = __fmaf_rn(a.hi, b.hi, -p);
+    e = __fmaf_rn(a.hi, b.lo, e);
+    e = __fmaf_rn(a.lo, b.hi, e);
+    return fast_two_sum(p, e);
+}
+
+__device__ __forceinline__ df df_from_double(double v) {
+    const float h = (float)v;
+    return {h, (float)(v - (double)h)};
+}
+
+__device__ __forceinline__ double df_to_double(df a) { return (double)a.hi + (double)a.lo; }
+
+struct dfc {
+    df re, im;
+};
+
+__device__ __forceinline__ dfc load_c(const float4& v) { return {{v.x, v.y}, {v.z, v.w}}; }
+__device__ __forceinline__ float4 store_c(const dfc& c) { return make_float4(c.re.hi, c.re.lo, c.im.hi, c.im.lo); }
+
+// (a + ib) (c + id) with w = c + id; conj selects c - id
+__device__ __forceinline__ dfc cmul(const dfc& x, const dfc& w, bool conj) {
+    const df wi = conj ? df_neg(w.im) : w.im;
+    const df re = df_add(df_mul(x.re, w.re), df_neg(df_mul(x.im, wi)));
+    const df im = df_add(df_mul(x.re, wi), df_mul(x.im, w.re));
+    return {re, im};
+}
+
+__device__ __forceinline__ int bit_reverse(int i, int logn) { return (int)(__brev((unsigned)i) >> (32 - logn)); }
+
+// In-place radix-2 decimation-in-time FFT of `lines` lines of length n held in
+// shared memory in bit-reversed order (line l at buf[l * (n + kDfPad) ..]).  tw[k] =
+// exp(-2 pi i k / n), k < n/2; inverse uses the conjugates.  One butterfly per
+// thread per stage (lines * n / 2 = kDfThreads).
+__device__ void fft_lines(float4* buf, int n, int logn, const float4* __restrict__ tw, bool inverse) {
+    const int b = threadIdx.x;
+    const int half_n = n >> 1;
+    const int line = b / half_n, k = b % half_n;
+    float4* x = buf + line * (n + kDfPad);
+    for (int s = 1; s <= logn; ++s) {
+        const int half = 1 << (s - 1), len = half << 1;
+        const int group = k / half, pos = k % half;
+        const int i = group * len + pos, j = i + half;
+        const dfc w = load_c(tw[pos * (n / len)]);
+        const dfc a = load_c(x[i]);
+        const dfc t = cmul(load_c(x[j]), w, inverse);
+        __syncthreads();
+        x[i] = store_c({df_add(a.re, t.re), df_add(a.im, t.im)});
+        x[j] = store_c({df_add(a.re, df_neg(t.re)), df_add(a.im, df_neg(t.im))});
+        __syncthreads();
+    }
+}
+
+struct DfGeom {
+    int n[3], logn[3];
+    long long G;
+};
+
+// x pass, forward: FP64 real grid -> double-float complex lines
+__global__ void __launch_bounds__(kDfThreads)
+dfx_forward_kernel(DfGeom d, const double* __restrict__ grid, float4* __restrict__ S, const float4* __restrict__ tw) {
+    __shared__ float4 buf[kDfSmem];
+    const int n = d.n[0], lines = kDfPoints / n;
+    const size_t ch = blockIdx.y;
+    const long long line0 = (long long)blockIdx.x * lines;
+    const double* src = grid + ch * d.G + line0 * n;
+    for (int e = threadIdx.x; e < kDfPoints; e += kDfThreads) {
+        const int l = e / n, i = e % n;
+        const df v = df_from_double(src[(size_t)l * n + i]);
+        buf[l * (n + kDfPad) + bit_reverse(i, d.logn[0])] = make_float4(v.hi, v.lo, 0.0f, 0.0f);
+    }
+    __syncthreads();
+    fft_lines(buf, n, d.logn[0], tw, false);
+    float4* dst = S + ch * d.G + line0 * n;
+    for (int e = threadIdx.x; e < kDfPoints; e += kDfThreads) dst[e] = buf[(e / n) * (n + kDfPad) + e % n];
+}
+
+// x pass, inverse: double-float complex lines -> real part as FP64
+__global__ void __launch_bounds__(kDfThreads)
+dfx_inverse_kernel(DfGeom d, const float4* __restrict__ S, double* __restrict__ grid, const float4* __restrict__ tw) {
+    __shared__ float4 buf[kDfSmem];
+    const int n = d.n[0], lines = kDfPoints / n;
+    const size_t ch = blockIdx.y;
+    const long long line0 = (long long)blockIdx.x * lines;
+    const float4* src = S + ch * d.G + line0 * n;
+    for (int e = threadIdx.x; e < kDfPoints; e += kDfThreads) {
+        const int l = e / n, i = e % n;
+        buf[l * (n + kDfPad) + bit_reverse(i, d.logn[0])] = src[e];
+    }
+    __syncthreads();
+    fft_lines(buf, n, d.logn[0], tw, true);
+    double* dst = grid + ch * d.G + line0 * n;
+    for (int e = threadIdx.x; e < kDfPoints; e += kDfThreads) {
+        const float4 v = buf[(e / n) * (n + kDfPad) + e % n];
+        dst[e] = (double)v.x + (double)v.y;
+    }
+}
+
+// y pass (either direction): columns x0 .. x0 + cols of one z-plane
+__global__ void __launch_bounds__(kDfThreads)
+dfy_kernel(DfGeom d, float4* __restrict__ S, const float4* __restrict__ tw, int inverse) {
+    __shared__ float4 buf[kDfSmem];
+    const int n = d.n[1], cols = kDfPoints / n, nx = d.n[0];
+    const size_t ch = blockIdx.y;
+    const int blocks_x = nx / cols;
+    const int z = blockIdx.x / blocks_x, x0 = (blockIdx.x % blocks_x) * cols;
+    float4* plane = S + ch * d.G + (size_t)z * n * nx;
+    for (int e = threadIdx.x; e < kDfPoints; e += kDfThreads) {
+        const int y = e / cols, c = e % cols;   // consecutive threads: consecutive x (coalesced)
+        buf[c * (n + kDfPad) + bit_reverse(y, d.logn[1])] = plane[(size_t)y * nx + x0 + c];
+    }
+    __syncthreads();
+    fft_lines(buf, n, d.logn[1], tw, inverse != 0);
+    for (int e = threadIdx.x; e < kDfPoints; e += kDfThreads) {
+        const int y = e / cols, c = e % cols;
+        plane[(size_t)y * nx + x0 + c] = buf[c * (n + kDfPad) + y];
+    }
+}
+
+// z pass: forward FFT, Green's-function scaling (FP64 half-spectrum table,
+// k_x > N_x/2 by symmetry), inverse FFT, for columns x0 .. x0 + cols at one y
+__global__ void __launch_bounds__(kDfThreads)
+dfz_scale_kernel(DfGeom d, float4* __restrict__ S, const float4* __restrict__ tw, const double* __restrict__ green) {
+    __shared__ float4 buf[kDfSmem];
+    const int n = d.n[2], cols = kDfPoints / n, nx = d.n[0], ny = d.n[1];
+    const size_t ch = blockIdx.y;
+    const int blocks_x = nx / cols;
+    const int y = blockIdx.x / blocks_x, x0 = (blockIdx.x % blocks_x) * cols;
+    const size_t zstride = (size_t)nx * ny;
+    float4* col = S + ch * d.G + (size_t)y * nx + x0;
+    for (int e = threadIdx.x; e < kDfPoints; e += kDfThreads) {
+        const int z = e / cols, c = e % cols;
+        buf[c * (n + kDfPad) + bit_reverse(z, d.logn[2])] = col[(size_t)z * zstride + c];
+    }
+    __syncthreads();
+    fft_lines(buf, n, d.logn[2], tw, false);
+    const int nxh = nx / 2 + 1;
+    for (int e = threadIdx.x; e < kDfPoints; e += kDfThreads) {
+        const int c = e / n, z = e % n;
+        const int kx = x0 + c;
+        const int kxh = kx <= nx / 2 ? kx : nx - kx;   // G depends on k_x^2: fold onto the half table
+        const df gk = df_from_double(green[((size_t)z * ny + y) * nxh + kxh]);
+        float4& slot = buf[c * (n + kDfPad) + z];
+        dfc v = load_c(slot);
+        v.re = df_mul(v.re, gk);
+        v.im = df_mul(v.im, gk);
+        slot = store_c(v);
+    }
+    __syncthreads();
+    // back to bit-reversed order for the inverse transform
+    float4 mine[kDfPoints / kDfThreads];
+    for (int r = 0; r < kDfPoints / kDfThreads; ++r) {
+        const int e = threadIdx.x + r * kDfThreads;
+        mine[r] = buf[(e / n) * (n + kDfPad) + e % n];
+    }
+    __syncthreads();
+    for (int r = 0; r < kDfPoints / kDfThreads; ++r) {
+        const int e = threadIdx.x + r * kDfThreads;
+        const int c = e / n, z = e % n;
+        buf[c * (n + kDfPad) + bit_reverse(z, d.logn[2])] = mine[r];
+    }
+    __syncthreads();
+    fft_lines(buf, n, d.logn[2], tw, true);
+    for (int e = threadIdx.x; e < kDfPoints; e += kDfThreads) {
+        const int z = e / cols, c = e % cols;
+        col[(size_t)z * zstride + c] = buf[c * (n + kDfPad) + z];
+    }
+}
+
+int ilog2(int v) {
+    int l = 0;
+    while ((1 << l) < v) ++l;
+    return l;
+}
+
+}  // namespace
+
+bool df_fft_supported(const MeshGeom& g) {
+    for (int d = 0; d < 3; ++d) {
+        const int n = g.N[d];
+        if (n < 16 || n > 1024 || (n & (n - 1)) != 0) return false;
+    }
+    // the y and z passes take kDfPoints / N_d whole columns of x per block
+    return g.N[0] * g.N[1] >= kDfPoints && g.N[0] * g.N[2] >= kDfPoints;
+}
+
+// Twiddles exp(-2 pi i k / N_d), k < N_d / 2, per axis (double -> hi + lo floats).
+void df_fft_init(const MeshGeom& g, DevBuf tw[3], cudaStream_t s) {
+    for (int d = 0; d < 3; ++d) {
+        const int n = g.N[d];
+        std::vector<float4> h(n / 2);
+        for (int k = 0; k < n / 2; ++k) {
+            const double th = 2.0 * 3.14159265358979323846264338327950288 * k / n;
+            const double c = std::cos(th), sn = -std::sin(th);
+            const float ch = (float)c, sh = (float)sn;
+            h[k] = make_float4(ch, (float)(c - (double)ch), sh, (float)(sn - (double)sh));
+        }
+        tw[d].ensure(sizeof(float4) * h.size());
+        IBP_CUDA(cudaMemcpyAsync(tw[d].p, h.data(), sizeof(float4) * h.size(), cudaMemcpyHostToDevice, s));
+    }
+    IBP_CUDA(cudaStreamSynchronize(s));   // the host table goes out of scope
+}
+
+// grid (FP64, [ch][G]) -> inverse transform of G(k) times its transform, in place.
+void df_fft_convolve(const MeshGeom& g, int ch, const double* green, double* grid, float4* S, DevBuf tw[3],
+                     cudaStream_t s) {
+    DfGeom d;
+    for (int a = 0; a < 3; ++a) {
+        d.n[a] = g.N[a];
+        d.logn[a] = ilog2(g.N[a]);
+    }
+    d.G = g.G;
+    const dim3 gx((unsigned)(g.G / kDfPoints), ch);
+    const dim3 gy((unsigned)(g.N[2] * (g.N[0] / (kDfPoints / g.N[1]))), ch);
+    const dim3 gz((unsigned)(g.N[1] * (g.N[0] / (kDfPoints / g.N[2]))), ch);
+    {
+        ProfScope ps(ST_FFT_FWD64, s);
+        dfx_forward_kernel<<<gx, kDfThreads, 0, s>>>(d, grid, S, tw[0].as<float4>());
+        IBP_CHECK_LAUNCH();
+        dfy_kernel<<<gy, kDfThreads, 0, s>>>(d, S, tw[1].as<float4>(), 0);
+        IBP_CHECK_LAUNCH();
+    }
+    {
+        ProfScope ps(ST_SCALE64, s);
+        dfz_scale_kernel<<<gz, kDfThreads, 0, s>>>(d, S, tw[2].as<float4>(), green);
+        IBP_CHECK_LAUNCH();
+    }
+    ProfScope ps(ST_FFT_INV64, s);
+    dfy_kernel<<<gy, kDfThreads, 0, s>>>(d, S, tw[1].as<float4>(), 1);
+    IBP_CHECK_LAUNCH();
+    dfx_inverse_kernel<<<gx, kDfThreads, 0, s>>>(d, S, grid, tw[0].as<float4>());
+    IBP_CHECK_LAUNCH();
+}
+
+}  // namespace ibp

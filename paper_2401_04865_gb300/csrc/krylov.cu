@@ -731,7 +731,7 @@ struct Solver {
                                       P(c->pre.shape_off.p), P(c->pre.shape_goff.p),
                                       P(prec == IBPME_MIXED ? m32.grid.p : m64.grid.p),
                                       P(prec == IBPME_MIXED ? m32.spec.p : m64.spec.p),
-                                      P(prec == IBPME_MIXED ? m32.work.p : m64.work.p)};
+                                      P(prec == IBPME_MIXED ? m32.work.p : m64.work.p), P(m64.df_buf.p)};
         const int gi = prec == IBPME_MIXED ? 1 : 0;
         if (k->exec[gi] && k->sig[gi] == sig) return k->exec[gi];
         if (k->exec[gi]) {

@@ -564,6 +564,8 @@ template <typename T>
 void Mesh<T>::init(const MeshGeom& geom, int channels, double xi, double eta, double a, cudaStream_t s) {
     g = geom;
     rcap = 0;
+    df = sizeof(T) == 8 && df_fft_supported(g);
+    if (df) df_fft_init(g, df_tw, s);
     ensure_channels(channels);
     green.ensure(sizeof(T) * (size_t)g.Gc);
     green_kernel<T><<<grid_blocks(g.Gc, 256), 256, 0, s>>>(g, xi, eta, a, green.as<T>());
@@ -582,6 +584,10 @@ template <typename T>
 void Mesh<T>::plans(int ch, cudaStream_t s) {
     if (ch < 1) fail(IBPME_ERR_ARG, "channel count %d < 1", ch);
     ensure_channels(ch);
+    if (df) {   // double-float transforms: one complex float4 buffer, no cuFFT plan
+        df_buf.ensure(sizeof(float4) * (size_t)g.G * ch);
+        return;
+    }
     auto it = plan.find(ch);
     if (it == plan.end()) {
         int dims[3] = {g.N[2], g.N[1], g.N[0]};   // slowest to fastest: z, y, x
@@ -619,6 +625,8 @@ void Mesh<T>::destroy() {
         cufftDestroy(kv.second.second);
     }
     plan.clear();
+    df_buf.release();
+    for (auto& t : df_tw) t.release();
     grid.release();
     spec.release();
     green.release();
@@ -648,6 +656,12 @@ void Mesh<T>::spread(int n, const double* xw, const double* q, int nrhs, const i
 template <typename T>
 void Mesh<T>::transform(int ch, cudaStream_t s) {
     plans(ch, s);
+    if constexpr (sizeof(T) == 8) {
+        if (df) {
+            df_fft_convolve(g, ch, green.as<double>(), grid.as<double>(), df_buf.as<float4>(), df_tw, s);
+            return;
+        }
+    }
     const auto& pl = plan.at(ch);
     using C = typename Cplx<T>::type;
     {
