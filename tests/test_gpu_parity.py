@@ -348,3 +348,64 @@ def test_body_block_preconditioner_same_solution_fewer_iterations(cuda_lib, prec
         assert rel_err(res[ib.IBPME_PRECOND_BODY][1], res[ib.IBPME_PRECOND_NONE][1]) < (1e-6 if prec == "fp64" else 1e-4)
     finally:
         ib.pme_destroy(ctx)
+
+
+def test_fp64_mesh_double_float_transforms_reach_tight_tolerance(cuda_lib):
+    """On a power-of-two FP64 mesh the transforms run in double-float arithmetic
+    (about 48 significant bits); with the Ewald tolerance at 1e-10 (P = 15,
+    64^3; the truncation bounds of Sec. III.D.2 then leave a few 1e-9 over 400
+    charges in the potential, and about k_c times more in the field) the
+    potential matches the oracle below 1e-8 and the field below 1e-7, 1,000 and
+    100 times under the 1e-5 FP64 bar: the transforms are not the accuracy limit."""
+    ib = cuda_lib
+    rng = np.random.default_rng(61)
+    box = np.array([8.0, 8.0, 8.0])
+    n = 400
+    x = rng.uniform(0, 1, size=(n, 3)) * box
+    q = random_neutral_charges(n, 62)
+    ctx = ib.pme_setup(ib.make_params(box=box, mesh=(64, 64, 64), tol=1e-10, bead_radius=0.1, eps_f=0.9,
+                                      precision=ib.IBPME_FP64))
+    try:
+        assert ib.ibpme_get_params(ctx).P == 15
+        psi, E = _field(ib, ctx, x, q)
+        ref_psi, ref_E = o.potential(x, q, box, 0.1, 0.9, field=True)
+        assert rel_err(psi[0], ref_psi) < 1e-8, rel_err(psi[0], ref_psi)
+        assert rel_err(E[0], ref_E) < 1e-7, rel_err(E[0], ref_E)
+    finally:
+        ib.pme_destroy(ctx)
+
+
+def test_preconditioner_skips_configurations_with_large_bodies(cuda_lib):
+    """In a batch, a configuration holding a body above the block limit (1,024
+    beads) runs unpreconditioned while the others are preconditioned; every
+    configuration still matches its single-system solve."""
+    import torch
+    from workloads import geometry as geo
+    ib = cuda_lib
+    L = 12.0
+    big = geo.ellipsoid(1400, [1.0, 1.5, 2.0]) + L / 2
+    small = geo.icosphere(2) * 0.8 + L / 2
+    E0 = np.eye(3)
+    a = 0.45 * min(geo.min_spacing(big), geo.min_spacing(small))
+    parts = [C.assemble("big", [big], [], [], [0.0], [L] * 3, a, 1.0, E0, mesh=(64, 64, 64), tol=1e-6),
+             C.assemble("small", [small], [], [], [0.0], [L] * 3, a, 1.0, E0, mesh=(64, 64, 64), tol=1e-6)]
+    s, cfg = C.stack(parts)
+    ctx = context(ib, s, precision="fp64")
+    try:
+        bodies = ib.Bodies(cuda(s.body_offsets.astype(np.int32)), cuda(s.X), cuda(s.Q))
+        q = torch.zeros((3, s.n), dtype=torch.float64, device="cuda")
+        status, st = ib.induced_charge_solve_batch(ctx, s.n, cuda(s.x), bodies, cfg, cuda(s.E0), 3,
+                                                   ib.make_opts(rtol=1e-8), q)
+        assert status == ib.IBPME_OK
+        got = q.cpu().numpy()
+        lo = 0
+        for p in parts:
+            bp = ib.Bodies(cuda(p.body_offsets.astype(np.int32)), cuda(p.X), cuda(p.Q))
+            qs = torch.zeros((3, p.n), dtype=torch.float64, device="cuda")
+            status1, _ = ib.induced_charge_solve(ctx, p.n, cuda(p.x), bp, cuda(p.E0), 3,
+                                                 ib.make_opts(rtol=1e-8, precond=ib.IBPME_PRECOND_NONE), qs)
+            assert status1 == ib.IBPME_OK
+            assert rel_err(got[:, lo:lo + p.n], qs.cpu().numpy()) < 1e-6
+            lo += p.n
+    finally:
+        ib.pme_destroy(ctx)
