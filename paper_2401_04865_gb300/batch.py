@@ -35,19 +35,34 @@ MESH_CANDIDATES = (64, 96, 128, 160, 192)
 
 # ---------------------------------------------------------------- bucketing
 
-def buckets(sizes, ratio: float = 2.0, max_channels: int = 192, nrhs: int = 3) -> list[list[int]]:
+def buckets(sizes, ratio: float = 2.0, max_channels: int = 192, nrhs: int = 3, classes=None) -> list[list[int]]:
     """Indices of configurations grouped by bead count: sorted ascending, a new
     bucket starts when the count exceeds ``ratio`` x the bucket's first, or when
-    the bucket would hold more than max_channels / nrhs configurations."""
-    order = sorted(range(len(sizes)), key=lambda i: (sizes[i], i))
+    the bucket would hold more than max_channels / nrhs configurations.
+    Configurations of different ``classes`` (e.g. whether the body-block
+    preconditioner covers them, which sets how fast they converge) never share a
+    bucket: a batched solve iterates until its slowest system converges."""
+    cls = list(classes) if classes is not None else [0] * len(sizes)
+    order = sorted(range(len(sizes)), key=lambda i: (cls[i], sizes[i], i))
     per = max(1, max_channels // max(1, nrhs))
     out: list[list[int]] = []
     for i in order:
-        if out and sizes[i] <= ratio * sizes[out[-1][0]] and len(out[-1]) < per:
+        if (out and cls[i] == cls[out[-1][0]] and sizes[i] <= ratio * sizes[out[-1][0]]
+                and len(out[-1]) < per):
             out[-1].append(i)
         else:
             out.append([i])
     return out
+
+
+PRECOND_MAX_BEADS = 1024   # bodies the library's body-block preconditioner covers
+
+
+def preconditioned(system) -> int:
+    """1 if every multi-bead body of the configuration is small enough for the
+    body-block preconditioner (the whole configuration is then preconditioned)."""
+    sizes = np.diff(np.asarray(system.body_offsets))
+    return int(np.all(sizes[sizes > 1] <= PRECOND_MAX_BEADS))
 
 
 def cost_model(n_beads: int, mesh: int = 128, P: int = 9, nrhs: int = 3) -> float:
@@ -217,7 +232,8 @@ def polarizability(ib, systems, precision=None, rtol=1e-6, tol=1e-6, tuner: Auto
     a, eps = systems[0].a, systems[0].eps
     out = [None] * len(systems)
     report = []
-    for idx in buckets([s.n for s in systems], ratio=ratio, max_channels=max_channels, nrhs=3):
+    for idx in buckets([s.n for s in systems], ratio=ratio, max_channels=max_channels, nrhs=3,
+                       classes=[preconditioned(s) for s in systems]):
         bucket = Bucket(ib, [systems[i] for i in idx], E0)
         N = mesh
         tuned = None

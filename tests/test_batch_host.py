@@ -110,3 +110,18 @@ def test_autotuner_picks_the_cheapest_prediction_and_caches(tmp_path, monkeypatc
     monkeypatch.setattr(t2, "measure", fake_measure)
     t2.tune(None, _FakeBucket(40000, 4), 1e-6, 0.02, 1.0, 1)
     assert calls == [64, 96, 128]
+
+
+def test_buckets_never_mix_classes_and_preconditioned_flag():
+    sizes = [500, 600, 700, 800, 900, 1000]
+    classes = [1, 0, 1, 0, 1, 0]
+    out = B.buckets(sizes, ratio=1e9, max_channels=192, nrhs=3, classes=classes)
+    assert sorted(i for b in out for i in b) == list(range(6))
+    for b in out:
+        assert len({classes[i] for i in b}) == 1
+    assert len(out) == 2
+    S = type("S", (), {})
+    small, big = S(), S()
+    small.body_offsets = np.array([0, 642, 643, 644])      # a sphere and two ions
+    big.body_offsets = np.array([0, 642, 642 + 1500])      # a sphere and a 1,500-bead body
+    assert B.preconditioned(small) == 1 and B.preconditioned(big) == 0
