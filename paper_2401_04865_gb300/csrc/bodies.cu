@@ -139,18 +139,6 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k) {
     return c;
 }
 
-__device__ void normals6(unsigned entity, unsigned step, unsigned long long seed, double* z) {
-    const uint2 key = make_uint2((unsigned)(seed & 0xffffffffull), (unsigned)(seed >> 32));
-    const double two_pi = 6.283185307179586476925286766559;
-    for (unsigned t = 0; t < 3; ++t) {
-        const uint4 w = philox4x32_10(make_uint4(entity, step, t, 0x1B5EEDu), key);
-        const double u1 = ((double)w.x + 0.5) * 2.3283064365386963e-10;
-        const double u2 = ((double)w.y + 0.5) * 2.3283064365386963e-10;
-        const double rad = sqrt(-2.0 * log(u1));
-        z[2 * t] = rad * cos(two_pi * u2);
-        z[2 * t + 1] = rad * sin(two_pi * u2);
-    }
-}
 
 // f_tot = f_bead + Heyes-Melrose forces gamma/(2 dt) (2a - r) (x_a - x_b)/r for
 // r < 2a between beads of different bodies (Eq. hardsphereFD).
@@ -221,7 +209,43 @@ __global__ void bd_body_kernel(int nb, const int* __restrict__ off, const double
     const int b = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (b >= nb) return;
+    const int Ni = off[b + 1] - off[b];
+    // noise: Box-Muller pair t from Philox counter (body, step, t) on lane t, in
+    // parallel; an ion needs z0..z2 only (pairs 0 and 1, the cosine of pair 1)
+    double za = 0.0, zb = 0.0;
+    if (lane < (Ni > 1 ? 3 : 2)) {
+        const uint2 key = make_uint2((unsigned)(bc.seed & 0xffffffffull), (unsigned)(bc.seed >> 32));
+        const uint4 w = philox4x32_10(make_uint4((unsigned)b, bc.step, (unsigned)lane, 0x1B5EEDu), key);
+        const double u1 = ((double)w.x + 0.5) * 2.3283064365386963e-10;
+        const double u2 = ((double)w.y + 0.5) * 2.3283064365386963e-10;
+        const double rad = sqrt(-2.0 * log(u1));
+        const double ang = 6.283185307179586476925286766559 * u2;
+        if (Ni > 1 || lane == 0) {
+            double sn, cs;
+            sincos(ang, &sn, &cs);
+            za = rad * cs;
+            zb = rad * sn;
+        } else {
+            za = rad * cos(ang);
+        }
+    }
+    double z[6];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        z[2 * i] = __shfl_sync(0xffffffffu, za, i);
+        z[2 * i + 1] = __shfl_sync(0xffffffffu, zb, i);
+    }
     double F[3] = {0, 0, 0}, L[3] = {0, 0, 0}, J[6] = {0, 0, 0, 0, 0, 0};
+    if (Ni == 1) {   // an ion: its force, no torque (r = 0), no rotation
+        if (lane != 0) return;
+        const int j = off[b];
+        const double mt = 1.0 / bc.gamma;
+        const double st = sqrt(2.0 * bc.kT * bc.dt * mt);
+        for (int i = 0; i < 3; ++i) X_out[3 * b + i] = X[3 * b + i] + f[3 * j + i] * mt * bc.dt + st * z[i];
+        const double R[9] = {1, 0, 0, 0, 1, 0, 0, 0, 1};
+        for (int i = 0; i < 9; ++i) Rm[9 * b + i] = R[i];
+        return;
+    }
     for (int j = off[b] + lane; j < off[b + 1]; j += 32) {
         const double rx = rel[3 * j], ry = rel[3 * j + 1], rz = rel[3 * j + 2];
         const double ax = f[3 * j], ay = f[3 * j + 1], az = f[3 * j + 2];
@@ -236,9 +260,6 @@ __global__ void bd_body_kernel(int nb, const int* __restrict__ off, const double
     for (int i = 0; i < 3; ++i) { F[i] = warp_sum(F[i]); L[i] = warp_sum(L[i]); }
     for (int i = 0; i < 6; ++i) J[i] = warp_sum(J[i]);
     if (lane != 0) return;
-    const int Ni = off[b + 1] - off[b];
-    double z[6];
-    normals6((unsigned)b, bc.step, bc.seed, z);
     const double mt = 1.0 / (Ni * bc.gamma);
     const double st = sqrt(2.0 * bc.kT * bc.dt * mt);
     for (int i = 0; i < 3; ++i) X_out[3 * b + i] = X[3 * b + i] + F[i] * mt * bc.dt + st * z[i];

@@ -7,9 +7,10 @@
 // of two floats (hi + lo, about 48 significant bits; error-free transformations
 // of Dekker and Knuth: two-sum, and two-product with a fused multiply-add), so
 // the butterflies run on the FP32 pipes.  The transform is a radix-2 complex FFT
-// along x, y and z (power-of-two sizes), the Green's-function scaling of the
-// FP64 table is fused between the forward and inverse z passes, and the real
-// part comes back as FP64.  Sizes that are not powers of two use cuFFT.
+// along x (two real lines packed into one complex line), y and z on the half
+// spectrum (power-of-two sizes); the Green's-function scaling of the FP64 table
+// is fused between the forward and inverse z passes, and the real lines come
+// back as FP64.  Sizes that are not powers of two use cuFFT.
 #include "common.cuh"
 
 #include <cmath>
@@ -110,93 +111,122 @@ __device__ void fft_lines(float4* buf, int n, int logn, const float4* __restrict
 
 struct DfGeom {
     int n[3], logn[3];
-    long long G;
+    int h;          // half-spectrum row length N_x / 2 + 1
+    long long G;    // real points per channel
+    long long Gh;   // half-spectrum points per channel (N_y N_z h)
 };
 
-// x pass, forward: FP64 real grid -> double-float complex lines
+__device__ __forceinline__ df df_half(df a) { return {a.hi * 0.5f, a.lo * 0.5f}; }   // exact
+
+// x pass, forward.  Two real lines a, b travel as one complex line a + i b; after
+// its transform Z, A[k] = (Z[k] + conj Z[N-k]) / 2 and B[k] = (Z[k] - conj Z[N-k]) / 2i
+// are the spectra of a and b; their halves k = 0 .. N/2 go to S.
 __global__ void __launch_bounds__(kDfThreads)
 dfx_forward_kernel(DfGeom d, const double* __restrict__ grid, float4* __restrict__ S, const float4* __restrict__ tw) {
     __shared__ float4 buf[kDfSmem];
-    const int n = d.n[0], lines = kDfPoints / n;
+    const int n = d.n[0], pl = kDfPoints / n;   // packed lines per block
     const size_t ch = blockIdx.y;
-    const long long line0 = (long long)blockIdx.x * lines;
+    const long long line0 = (long long)blockIdx.x * 2 * pl;   // first real line
     const double* src = grid + ch * d.G + line0 * n;
     for (int e = threadIdx.x; e < kDfPoints; e += kDfThreads) {
-        const int l = e / n, i = e % n;
-        const df v = df_from_double(src[(size_t)l * n + i]);
-        buf[l * (n + kDfPad) + bit_reverse(i, d.logn[0])] = make_float4(v.hi, v.lo, 0.0f, 0.0f);
+        const int p = e / n, i = e % n;
+        const df a = df_from_double(src[(size_t)(2 * p) * n + i]);
+        const df b = df_from_double(src[(size_t)(2 * p + 1) * n + i]);
+        buf[p * (n + kDfPad) + bit_reverse(i, d.logn[0])] = make_float4(a.hi, a.lo, b.hi, b.lo);
     }
     __syncthreads();
     fft_lines(buf, n, d.logn[0], tw, false);
-    float4* dst = S + ch * d.G + line0 * n;
-    for (int e = threadIdx.x; e < kDfPoints; e += kDfThreads) dst[e] = buf[(e / n) * (n + kDfPad) + e % n];
+    float4* dst = S + ch * d.Gh + line0 * d.h;
+    for (int e = threadIdx.x; e < pl * d.h; e += kDfThreads) {
+        const int p = e / d.h, k = e % d.h;
+        const dfc zk = load_c(buf[p * (n + kDfPad) + k]);
+        const dfc zm = load_c(buf[p * (n + kDfPad) + ((n - k) & (n - 1))]);   // Z[N - k], conjugated below
+        const dfc A = {df_half(df_add(zk.re, zm.re)), df_half(df_add(zk.im, df_neg(zm.im)))};
+        // (Z[k] - conj Z[N-k]) / 2i: re = (zk.im + zm.im) / 2, im = -(zk.re - zm.re) / 2
+        const dfc B = {df_half(df_add(zk.im, zm.im)), df_half(df_add(zm.re, df_neg(zk.re)))};
+        dst[(size_t)(2 * p) * d.h + k] = store_c(A);
+        dst[(size_t)(2 * p + 1) * d.h + k] = store_c(B);
+    }
 }
 
-// x pass, inverse: double-float complex lines -> real part as FP64
+// x pass, inverse: the half spectra A, B of two lines rebuild Z = A + i B on all
+// N points (Z[N-k] = conj A[k] + i conj B[k]); the inverse transform's real and
+// imaginary parts are the two real lines, returned as FP64.
 __global__ void __launch_bounds__(kDfThreads)
 dfx_inverse_kernel(DfGeom d, const float4* __restrict__ S, double* __restrict__ grid, const float4* __restrict__ tw) {
     __shared__ float4 buf[kDfSmem];
-    const int n = d.n[0], lines = kDfPoints / n;
+    const int n = d.n[0], pl = kDfPoints / n;
     const size_t ch = blockIdx.y;
-    const long long line0 = (long long)blockIdx.x * lines;
-    const float4* src = S + ch * d.G + line0 * n;
-    for (int e = threadIdx.x; e < kDfPoints; e += kDfThreads) {
-        const int l = e / n, i = e % n;
-        buf[l * (n + kDfPad) + bit_reverse(i, d.logn[0])] = src[e];
+    const long long line0 = (long long)blockIdx.x * 2 * pl;
+    const float4* src = S + ch * d.Gh + line0 * d.h;
+    for (int e = threadIdx.x; e < pl * d.h; e += kDfThreads) {
+        const int p = e / d.h, k = e % d.h;
+        const dfc A = load_c(src[(size_t)(2 * p) * d.h + k]);
+        const dfc B = load_c(src[(size_t)(2 * p + 1) * d.h + k]);
+        // Z[k] = A + i B
+        const dfc zk = {df_add(A.re, df_neg(B.im)), df_add(A.im, B.re)};
+        buf[p * (n + kDfPad) + bit_reverse(k, d.logn[0])] = store_c(zk);
+        if (k > 0 && k < n / 2) {   // Z[N-k] = conj A + i conj B
+            const dfc zm = {df_add(A.re, B.im), df_add(df_neg(A.im), B.re)};
+            buf[p * (n + kDfPad) + bit_reverse(n - k, d.logn[0])] = store_c(zm);
+        }
     }
     __syncthreads();
     fft_lines(buf, n, d.logn[0], tw, true);
     double* dst = grid + ch * d.G + line0 * n;
     for (int e = threadIdx.x; e < kDfPoints; e += kDfThreads) {
-        const float4 v = buf[(e / n) * (n + kDfPad) + e % n];
-        dst[e] = (double)v.x + (double)v.y;
+        const int p = e / n, i = e % n;
+        const float4 v = buf[p * (n + kDfPad) + i];
+        dst[(size_t)(2 * p) * n + i] = (double)v.x + (double)v.y;
+        dst[(size_t)(2 * p + 1) * n + i] = (double)v.z + (double)v.w;
     }
 }
 
-// y pass (either direction): columns x0 .. x0 + cols of one z-plane
+// y pass (either direction) on the half spectrum: columns x0 .. x0 + cols of one
+// z-plane (the last group of columns may be partial)
 __global__ void __launch_bounds__(kDfThreads)
 dfy_kernel(DfGeom d, float4* __restrict__ S, const float4* __restrict__ tw, int inverse) {
     __shared__ float4 buf[kDfSmem];
-    const int n = d.n[1], cols = kDfPoints / n, nx = d.n[0];
+    const int n = d.n[1], cols = kDfPoints / n, h = d.h;
     const size_t ch = blockIdx.y;
-    const int blocks_x = nx / cols;
+    const int blocks_x = (h + cols - 1) / cols;
     const int z = blockIdx.x / blocks_x, x0 = (blockIdx.x % blocks_x) * cols;
-    float4* plane = S + ch * d.G + (size_t)z * n * nx;
+    float4* plane = S + ch * d.Gh + (size_t)z * n * h;
     for (int e = threadIdx.x; e < kDfPoints; e += kDfThreads) {
         const int y = e / cols, c = e % cols;   // consecutive threads: consecutive x (coalesced)
-        buf[c * (n + kDfPad) + bit_reverse(y, d.logn[1])] = plane[(size_t)y * nx + x0 + c];
+        buf[c * (n + kDfPad) + bit_reverse(y, d.logn[1])] =
+            x0 + c < h ? plane[(size_t)y * h + x0 + c] : make_float4(0.f, 0.f, 0.f, 0.f);
     }
     __syncthreads();
     fft_lines(buf, n, d.logn[1], tw, inverse != 0);
     for (int e = threadIdx.x; e < kDfPoints; e += kDfThreads) {
         const int y = e / cols, c = e % cols;
-        plane[(size_t)y * nx + x0 + c] = buf[c * (n + kDfPad) + y];
+        if (x0 + c < h) plane[(size_t)y * h + x0 + c] = buf[c * (n + kDfPad) + y];
     }
 }
 
-// z pass: forward FFT, Green's-function scaling (FP64 half-spectrum table,
-// k_x > N_x/2 by symmetry), inverse FFT, for columns x0 .. x0 + cols at one y
+// z pass on the half spectrum: forward FFT, Green's-function scaling (FP64
+// half-spectrum table), inverse FFT, for columns x0 .. x0 + cols at one y
 __global__ void __launch_bounds__(kDfThreads)
 dfz_scale_kernel(DfGeom d, float4* __restrict__ S, const float4* __restrict__ tw, const double* __restrict__ green) {
     __shared__ float4 buf[kDfSmem];
-    const int n = d.n[2], cols = kDfPoints / n, nx = d.n[0], ny = d.n[1];
+    const int n = d.n[2], cols = kDfPoints / n, ny = d.n[1], h = d.h;
     const size_t ch = blockIdx.y;
-    const int blocks_x = nx / cols;
+    const int blocks_x = (h + cols - 1) / cols;
     const int y = blockIdx.x / blocks_x, x0 = (blockIdx.x % blocks_x) * cols;
-    const size_t zstride = (size_t)nx * ny;
-    float4* col = S + ch * d.G + (size_t)y * nx + x0;
+    const size_t zstride = (size_t)h * ny;
+    float4* col = S + ch * d.Gh + (size_t)y * h + x0;
     for (int e = threadIdx.x; e < kDfPoints; e += kDfThreads) {
         const int z = e / cols, c = e % cols;
-        buf[c * (n + kDfPad) + bit_reverse(z, d.logn[2])] = col[(size_t)z * zstride + c];
+        buf[c * (n + kDfPad) + bit_reverse(z, d.logn[2])] =
+            x0 + c < h ? col[(size_t)z * zstride + c] : make_float4(0.f, 0.f, 0.f, 0.f);
     }
     __syncthreads();
     fft_lines(buf, n, d.logn[2], tw, false);
-    const int nxh = nx / 2 + 1;
     for (int e = threadIdx.x; e < kDfPoints; e += kDfThreads) {
         const int c = e / n, z = e % n;
-        const int kx = x0 + c;
-        const int kxh = kx <= nx / 2 ? kx : nx - kx;   // G depends on k_x^2: fold onto the half table
-        const df gk = df_from_double(green[((size_t)z * ny + y) * nxh + kxh]);
+        if (x0 + c >= h) continue;
+        const df gk = df_from_double(green[((size_t)z * ny + y) * h + x0 + c]);
         float4& slot = buf[c * (n + kDfPad) + z];
         dfc v = load_c(slot);
         v.re = df_mul(v.re, gk);
@@ -220,7 +250,7 @@ dfz_scale_kernel(DfGeom d, float4* __restrict__ S, const float4* __restrict__ tw
     fft_lines(buf, n, d.logn[2], tw, true);
     for (int e = threadIdx.x; e < kDfPoints; e += kDfThreads) {
         const int z = e / cols, c = e % cols;
-        col[(size_t)z * zstride + c] = buf[c * (n + kDfPad) + z];
+        if (x0 + c < h) col[(size_t)z * zstride + c] = buf[c * (n + kDfPad) + z];
     }
 }
 
@@ -237,8 +267,8 @@ bool df_fft_supported(const MeshGeom& g) {
         const int n = g.N[d];
         if (n < 16 || n > 1024 || (n & (n - 1)) != 0) return false;
     }
-    // the y and z passes take kDfPoints / N_d whole columns of x per block
-    return g.N[0] * g.N[1] >= kDfPoints && g.N[0] * g.N[2] >= kDfPoints;
+    // the x pass takes 2 kDfPoints / N_x whole real lines per block
+    return (long long)g.N[1] * g.N[2] % (2 * (kDfPoints / g.N[0])) == 0;
 }
 
 // Twiddles exp(-2 pi i k / N_d), k < N_d / 2, per axis (double -> hi + lo floats).
@@ -266,10 +296,14 @@ void df_fft_convolve(const MeshGeom& g, int ch, const double* green, double* gri
         d.n[a] = g.N[a];
         d.logn[a] = ilog2(g.N[a]);
     }
+    d.h = g.N[0] / 2 + 1;
     d.G = g.G;
-    const dim3 gx((unsigned)(g.G / kDfPoints), ch);
-    const dim3 gy((unsigned)(g.N[2] * (g.N[0] / (kDfPoints / g.N[1]))), ch);
-    const dim3 gz((unsigned)(g.N[1] * (g.N[0] / (kDfPoints / g.N[2]))), ch);
+    d.Gh = (long long)g.N[1] * g.N[2] * d.h;
+    const int pl = kDfPoints / g.N[0];
+    const dim3 gx((unsigned)((long long)g.N[1] * g.N[2] / (2 * pl)), ch);
+    const int cy = kDfPoints / g.N[1], cz = kDfPoints / g.N[2];
+    const dim3 gy((unsigned)(g.N[2] * ((d.h + cy - 1) / cy)), ch);
+    const dim3 gz((unsigned)(g.N[1] * ((d.h + cz - 1) / cz)), ch);
     {
         ProfScope ps(ST_FFT_FWD64, s);
         dfx_forward_kernel<<<gx, kDfThreads, 0, s>>>(d, grid, S, tw[0].as<float4>());

@@ -146,7 +146,7 @@ __global__ void shape_s_kernel(int nb, const float* __restrict__ g, double* __re
     }
 }
 
-constexpr int kRowsPerBlock = 32;
+constexpr int kRowsPerBlock = 8;   // rows of M^{-1} per block: a body spreads over n_b / 8 SMs
 constexpr int kApplyThreads = 256;
 
 // out = P^{-1} u on the preconditioned bodies (grid: bodies x row chunks, R) and
