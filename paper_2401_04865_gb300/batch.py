@@ -125,6 +125,24 @@ class Bucket:
         return self.ib.induced_charge_solve_batch(ctx, self.n, self.x, self.bodies, self.cfg, self.E0, self.R,
                                                   opts, self.q, None, self.S)
 
+    def shifted_positions(self, rng):
+        """(x, X) on the device with every configuration translated rigidly by its
+        own uniform random vector in the box.  In a periodic box a translation
+        changes no potential, charge or dipole, but every position-dependent table
+        (cells, pair table, stencils) has to be built again."""
+        import torch
+        x, X = [], []
+        for s in self.systems:
+            d = rng.uniform(0.0, 1.0, size=3) * np.asarray(s.box, dtype=np.float64)
+            x.append(np.mod(s.x + d, s.box))
+            X.append(np.mod(s.X + d, s.box))
+        return (torch.as_tensor(np.ascontiguousarray(np.concatenate(x)), device="cuda"),
+                torch.as_tensor(np.ascontiguousarray(np.concatenate(X)), device="cuda"))
+
+    def load_positions(self, x, X):
+        self.x.copy_(x)
+        self.X.copy_(X)
+
 
 def context_for(ib, box, mesh, tol, a, eps, precision, nrhs):
     return ib.pme_setup(ib.make_params(box=box, mesh=[mesh] * 3, tol=tol, bead_radius=a, eps_f=eps,
@@ -190,10 +208,15 @@ class Autotuner:
                 _, st = bucket.solve(ctx, ib.make_opts(max_iter=p))
                 runs.append((time.perf_counter() - t, st[0].iters))
             (ta, ia), (tb, ib_) = runs
-            per_iter = (tb - ta) / max(1, ib_ - ia)
             setup = max(0.0, t_first - ta)
+            if ib_ > ia:
+                per_iter = max(0.0, (tb - ta) / (ib_ - ia))
+                predicted = setup + ta + max(0, self.expected_iters - ia) * per_iter
+            else:   # converged within the shorter probe: that run is the whole solve
+                per_iter = ta / max(1, ia)
+                predicted = setup + ta
             return dict(mesh=mesh, per_iter_ms=1e3 * per_iter, setup_ms=1e3 * setup, base_ms=1e3 * ta,
-                        predicted_ms=1e3 * (setup + ta + self.expected_iters * per_iter))
+                        predicted_ms=1e3 * predicted)
         finally:
             ib.pme_destroy(ctx)
 

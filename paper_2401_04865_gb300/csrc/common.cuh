@@ -131,7 +131,17 @@ struct StencilCache {
     int n = 0, ncfg = 0;
     DevBuf start;                // int4 per bead: first node (x, y, z), configuration
     DevBuf frac;                 // double4 per bead: (first node - x / h) per axis
+    // Tile bins for spreading and gathering through shared memory (many beads
+    // only): beads sorted by (configuration, tile of kTileNodes^3 nodes holding
+    // their first stencil node).
+    bool tiles = false;
+    int tile_n[3] = {0, 0, 0};   // tiles per axis
+    DevBuf tile_count, tile_cursor, tile_off, tile_tmp, tile_bkey;
+    DevBuf tile_sorted;          // int per sorted position: bead
+    DevBuf tile_key;             // int per sorted position: configuration * tiles + tile
 };
+
+constexpr int kTileNodes = 8;    // tile edge in grid nodes
 
 // Spectral-Ewald mesh engine in one precision: grids, spectrum, Green's table, plans.
 // A grid "channel" holds one right-hand side of one configuration: channel

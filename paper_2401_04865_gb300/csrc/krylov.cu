@@ -724,6 +724,9 @@ struct Solver {
                                       P(bd.free_unk.p), P(bd.bead_body.p), P(bd.body_unk.p), P(bd.mb_unk.p),
                                       P(bd.mb_first.p), P(bd.mb_cnt.p), P(bd.uo.p), P(c->bcfg),
                                       (long long)c->stencils.valid, P(c->stencils.start.p), P(c->stencils.frac.p),
+                                      (long long)c->stencils.tiles, (long long)c->stencils.tile_n[0],
+                                      (long long)c->stencils.tile_n[1], (long long)c->stencils.tile_n[2],
+                                      P(c->stencils.tile_sorted.p), P(c->stencils.tile_key.p),
                                       (long long)pre_on, (long long)c->pre.npb, (long long)c->pre.nplain,
                                       (long long)c->pre.chunks, P(k->pu.p), P(c->pre.minv.p), P(c->pre.gvec.p),
                                       P(c->pre.sinv.p), P(c->pre.pb_shape.p), P(c->pre.pb_first.p),

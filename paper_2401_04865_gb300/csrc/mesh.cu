@@ -11,6 +11,7 @@
 #include "common.cuh"
 
 #include <cmath>
+#include <cstdlib>
 #include <mutex>
 
 namespace ibp {
@@ -511,6 +512,474 @@ PairArgs pair_args(const MeshGeom& g, const StencilCache& b, int n) {
     return A;
 }
 
+// ---------------------------------------------------------------------------
+// Tiled spreading and gathering through shared memory.
+//
+// On dense bead surfaces hundreds of beads share every grid node, and their
+// global atomics queue on the same L2 addresses.  Beads are binned (once per
+// set of positions) by configuration and by the tile of kTileNodes^3 nodes that
+// holds their first stencil node; every stencil of a tile then lies inside one
+// region of E^3 nodes, E = kTileNodes + P - 1.  A block takes kTileChunk
+// consecutive sorted beads and splits them into runs of one tile.  A run of at
+// least kTileMin beads is spread into the region in shared memory and the region
+// is added to the grid once (one atomic per non-zero node); a gather stages the
+// region in shared memory and reads every stencil from there.  Beads of
+// shorter runs (isolated ions) use the direct per-bead path.
+// ---------------------------------------------------------------------------
+constexpr int kTileChunk = 128;     // most sorted beads per block
+constexpr int kTileThreads = 256;
+constexpr int kTileWarps = kTileThreads / 32;
+constexpr int kTileMin = 8;         // beads of one tile that go through shared memory
+constexpr size_t kTileSmemMax = 192 * 1024;
+
+struct TileArgs {
+    PairArgs A;             // geometry and cached stencils (one warp per bead)
+    const int* sorted;      // bead at each sorted position
+    const int* key;         // configuration * ntiles + tile at each sorted position
+    int tn[3];              // tiles per axis
+    int ntiles;
+    int E;                  // region edge in nodes
+    int chunk;              // sorted beads per block (<= kTileChunk)
+};
+
+__global__ void tile_count_kernel(int n, const int4* __restrict__ start, int tn0, int tn1, int tn2,
+                                  int* __restrict__ count, int* __restrict__ key) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= n) return;
+    const int4 s = start[b];
+    const int k = ((s.w * tn2 + s.z / kTileNodes) * tn1 + s.y / kTileNodes) * tn0 + s.x / kTileNodes;
+    key[b] = k;
+    atomicAdd(count + k, 1);
+}
+
+__global__ void tile_fill_kernel(int n, const int* __restrict__ bead_key, const long long* __restrict__ off,
+                                 int* __restrict__ cursor, int* __restrict__ sorted, int* __restrict__ skey) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= n) return;
+    const int k = bead_key[b];
+    const long long p = off[k] + atomicAdd(cursor + k, 1);
+    sorted[p] = b;
+    skey[p] = k;
+}
+
+// Runs of equal keys among the block's sorted positions [p0, p0 + m): run r
+// covers [run_start[r], run_start[r + 1]); run_of[t] is the run of position t.
+struct TileRuns {
+    int start[kTileChunk + 1];
+    int of[kTileChunk];
+    int wcount[kTileChunk / 32];
+    int count;
+};
+
+__device__ void tile_runs(const int* __restrict__ key, int p0, int m, TileRuns& R) {
+    const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+    const bool in = t < m;   // m <= kTileChunk <= blockDim.x
+    const int k = in ? key[p0 + t] : -1;
+    const bool head = in && (t == 0 || key[p0 + t - 1] != k);
+    const unsigned bal = __ballot_sync(0xffffffffu, head);
+    if (lane == 0 && w < kTileChunk / 32) R.wcount[w] = __popc(bal);
+    __syncthreads();
+    int before = 0;
+    for (int u = 0; u < w && u < kTileChunk / 32; ++u) before += R.wcount[u];
+    if (head) R.start[before + __popc(bal & ((1u << lane) - 1u))] = t;
+    if (in) R.of[t] = before + __popc(bal & ((2u << lane) - 1u)) - 1;   // lane 31: mask wraps to all ones
+    if (t == 0) {
+        int tot = 0;
+        for (int u = 0; u < kTileChunk / 32; ++u) tot += R.wcount[u];
+        R.count = tot;
+        R.start[tot] = m;
+    }
+    __syncthreads();
+}
+
+__device__ __forceinline__ int wrap_once(int v, int N) { return v >= N ? v - N : v; }
+
+// Direct spreading of one bead (one warp, global atomics).
+template <typename T, int NR>
+__device__ __forceinline__ void spread_bead_direct(const PairArgs& A, int n, int bead, int lane,
+                                                   const double* __restrict__ q, T* __restrict__ grid) {
+    const MeshGeom& g = A.g;
+    const int P = g.P, P2 = P * P;
+    const Windows<T> W = bead_windows<T, false>(A, bead, lane);
+    T* gr = grid + (size_t)A.start[bead].w * NR * g.G;
+    T qc[NR];
+#pragma unroll
+    for (int r = 0; r < NR; ++r) qc[r] = (T)(g.c * q[(size_t)r * n + bead]);
+    const long long nxy = (long long)g.N[0] * g.N[1];
+    for (int first = 0; first < P2; first += 32) {
+        const int pair = first + lane;
+        const bool on = pair < P2;
+        int j = pair / P, i = pair - j * P;
+        if (!on) i = j = 0;
+        const T wxy = __shfl_sync(0xffffffffu, W.wx, i) * __shfl_sync(0xffffffffu, W.wy, j);
+        const long long base = (long long)__shfl_sync(0xffffffffu, W.iy, j) * g.N[0] + __shfl_sync(0xffffffffu, W.ix, i);
+        for (int k = 0; k < P; ++k) {
+            const T wz = __shfl_sync(0xffffffffu, W.wz, k);
+            const int iz = __shfl_sync(0xffffffffu, W.iz, k);
+            if (on) {
+                const size_t off = (size_t)iz * nxy + base;
+#pragma unroll
+                for (int r = 0; r < NR; ++r) atomicAdd(gr + (size_t)r * g.G + off, qc[r] * wxy * wz);
+            }
+        }
+    }
+}
+
+template <typename T, int NR>
+__global__ void __launch_bounds__(kTileThreads)
+spread_tiles_kernel(TileArgs TA, int n, const double* __restrict__ q, T* __restrict__ grid) {
+    extern __shared__ __align__(16) unsigned char tile_smem[];
+    T* reg = reinterpret_cast<T*>(tile_smem);
+    __shared__ TileRuns R;
+    const int p0 = blockIdx.x * TA.chunk;
+    const int m = min(TA.chunk, n - p0);
+    tile_runs(TA.key, p0, m, R);
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const PairArgs& A = TA.A;
+    const MeshGeom& g = A.g;
+    // isolated beads: direct atomics
+    for (int t = w; t < m; t += kTileWarps) {
+        const int r = R.of[t];
+        if (R.start[r + 1] - R.start[r] < kTileMin) spread_bead_direct<T, NR>(A, n, TA.sorted[p0 + t], lane, q, grid);
+    }
+    const int E = TA.E, E2 = E * E, E3 = E2 * E;
+    const int P = g.P, P2 = P * P;
+    for (int r = 0; r < R.count; ++r) {
+        const int a = R.start[r], b = R.start[r + 1];
+        if (b - a < kTileMin) continue;   // block-uniform
+        const int key = TA.key[p0 + a];
+        const int tile = key % TA.ntiles, cfg = key / TA.ntiles;
+        const int ox = (tile % TA.tn[0]) * kTileNodes;
+        const int oy = ((tile / TA.tn[0]) % TA.tn[1]) * kTileNodes;
+        const int oz = (tile / (TA.tn[0] * TA.tn[1])) * kTileNodes;
+        for (int u = threadIdx.x; u < NR * E3; u += kTileThreads) reg[u] = (T)0;
+        __syncthreads();
+        for (int t = a + w; t < b; t += kTileWarps) {
+            const int bead = TA.sorted[p0 + t];
+            const int4 st = A.start[bead];
+            const double4 fr = A.frac[bead];
+            const bool in = lane < P;
+            const T fx = (T)fr.x + (T)lane, fy = (T)fr.y + (T)lane, fz = (T)fr.z + (T)lane;
+            const T wx = in ? window<T>(fx, g.kappa[0]) : (T)0;
+            const T wy = in ? window<T>(fy, g.kappa[1]) : (T)0;
+            const T wz_l = in ? window<T>(fz, g.kappa[2]) : (T)0;
+            const int lx = st.x - ox, ly = st.y - oy, lz = st.z - oz;   // in [0, kTileNodes)
+            T qc[NR];
+#pragma unroll
+            for (int c = 0; c < NR; ++c) qc[c] = (T)(g.c * q[(size_t)c * n + bead]);
+            for (int first = 0; first < P2; first += 32) {
+                const int pair = first + lane;
+                const bool on = pair < P2;
+                int j = pair / P, i = pair - j * P;
+                if (!on) i = j = 0;
+                const T wxy = __shfl_sync(0xffffffffu, wx, i) * __shfl_sync(0xffffffffu, wy, j);
+                const int base = (lz * E + ly + j) * E + lx + i;
+                for (int k = 0; k < P; ++k) {
+                    const T wz = __shfl_sync(0xffffffffu, wz_l, k);
+                    if (on) {
+#pragma unroll
+                        for (int c = 0; c < NR; ++c) atomicAdd(reg + c * E3 + base + k * E2, qc[c] * wxy * wz);
+                    }
+                }
+            }
+        }
+        __syncthreads();
+        T* gr = grid + (size_t)cfg * NR * g.G;
+        for (int u = threadIdx.x; u < NR * E3; u += kTileThreads) {
+            const T v = reg[u];
+            if (v != (T)0) {
+                const int c = u / E3, rem = u - c * E3;
+                const int z = rem / E2, y = (rem / E) % E, x = rem % E;
+                const size_t off = ((size_t)wrap_once(oz + z, g.N[2]) * g.N[1] + wrap_once(oy + y, g.N[1])) * g.N[0] +
+                                   wrap_once(ox + x, g.N[0]);
+                atomicAdd(gr + (size_t)c * g.G + off, v);
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// Direct gather of one bead (one warp) into psi / E.
+template <typename T, int NR, bool GRAD>
+__device__ __forceinline__ void gather_bead_direct(const PairArgs& A, int n, int bead, int lane,
+                                                   const T* __restrict__ grid, double* __restrict__ psi,
+                                                   double* __restrict__ E) {
+    const MeshGeom& g = A.g;
+    const int P = g.P, P2 = P * P;
+    const Windows<T> W = bead_windows<T, GRAD>(A, bead, lane);
+    const T* gr = grid + (size_t)A.start[bead].w * NR * g.G;
+    T sp[NR], ex[NR], ey[NR], ez[NR];
+#pragma unroll
+    for (int r = 0; r < NR; ++r) sp[r] = ex[r] = ey[r] = ez[r] = (T)0;
+    const long long nxy = (long long)g.N[0] * g.N[1];
+    for (int first = 0; first < P2; first += 32) {
+        const int pair = first + lane;
+        const bool on = pair < P2;
+        int j = pair / P, i = pair - j * P;
+        if (!on) i = j = 0;
+        const T wx = __shfl_sync(0xffffffffu, W.wx, i), wy = __shfl_sync(0xffffffffu, W.wy, j);
+        const T wxy = on ? wx * wy : (T)0;
+        T dx = (T)0, dy = (T)0;
+        if (GRAD) {
+            dx = __shfl_sync(0xffffffffu, W.dx, i);
+            dy = __shfl_sync(0xffffffffu, W.dy, j);
+        }
+        const long long base = (long long)__shfl_sync(0xffffffffu, W.iy, j) * g.N[0] + __shfl_sync(0xffffffffu, W.ix, i);
+        T acc[NR], accz[NR];
+#pragma unroll
+        for (int r = 0; r < NR; ++r) acc[r] = accz[r] = (T)0;
+        for (int k = 0; k < P; ++k) {
+            const T wz = __shfl_sync(0xffffffffu, W.wz, k);
+            const int iz = __shfl_sync(0xffffffffu, W.iz, k);
+            T dz = (T)0;
+            if (GRAD) dz = __shfl_sync(0xffffffffu, W.dz, k);
+            if (on) {
+                const size_t off = (size_t)iz * nxy + base;
+#pragma unroll
+                for (int r = 0; r < NR; ++r) {
+                    const T v = __ldg(gr + (size_t)r * g.G + off) * wz;
+                    acc[r] += v;
+                    if (GRAD) accz[r] += v * dz;
+                }
+            }
+        }
+#pragma unroll
+        for (int r = 0; r < NR; ++r) {
+            sp[r] += wxy * acc[r];
+            if (GRAD) {
+                ex[r] += wxy * dx * acc[r];
+                ey[r] += wxy * dy * acc[r];
+                ez[r] += wxy * accz[r];
+            }
+        }
+    }
+#pragma unroll
+    for (int r = 0; r < NR; ++r) {
+        const double s0 = warp_sum((double)sp[r]);
+        if (GRAD) {
+            const double e0 = warp_sum((double)ex[r]);
+            const double e1 = warp_sum((double)ey[r]);
+            const double e2 = warp_sum((double)ez[r]);
+            if (lane == 0) {
+                double* e = E + ((size_t)r * n + bead) * 3;
+                e[0] = -g.grad * e0;
+                e[1] = -g.grad * e1;
+                e[2] = -g.grad * e2;
+            }
+        }
+        if (lane == 0) psi[(size_t)r * n + bead] = g.gather * s0;
+    }
+}
+
+template <typename T, int NR, bool GRAD>
+__global__ void __launch_bounds__(kTileThreads)
+gather_tiles_kernel(TileArgs TA, int n, const T* __restrict__ grid, double* __restrict__ psi, double* __restrict__ E) {
+    extern __shared__ __align__(16) unsigned char tile_smem[];
+    T* reg = reinterpret_cast<T*>(tile_smem);
+    __shared__ TileRuns R;
+    const int p0 = blockIdx.x * TA.chunk;
+    const int m = min(TA.chunk, n - p0);
+    tile_runs(TA.key, p0, m, R);
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const PairArgs& A = TA.A;
+    const MeshGeom& g = A.g;
+    for (int t = w; t < m; t += kTileWarps) {
+        const int r = R.of[t];
+        if (R.start[r + 1] - R.start[r] < kTileMin)
+            gather_bead_direct<T, NR, GRAD>(A, n, TA.sorted[p0 + t], lane, grid, psi, E);
+    }
+    const int Ee = TA.E, E2 = Ee * Ee, E3 = E2 * Ee;
+    const int P = g.P, P2 = P * P;
+    for (int r = 0; r < R.count; ++r) {
+        const int a = R.start[r], b = R.start[r + 1];
+        if (b - a < kTileMin) continue;   // block-uniform
+        const int key = TA.key[p0 + a];
+        const int tile = key % TA.ntiles, cfg = key / TA.ntiles;
+        const int ox = (tile % TA.tn[0]) * kTileNodes;
+        const int oy = ((tile / TA.tn[0]) % TA.tn[1]) * kTileNodes;
+        const int oz = (tile / (TA.tn[0] * TA.tn[1])) * kTileNodes;
+        const T* gr = grid + (size_t)cfg * NR * g.G;
+        for (int u = threadIdx.x; u < NR * E3; u += kTileThreads) {
+            const int c = u / E3, rem = u - c * E3;
+            const int z = rem / E2, y = (rem / Ee) % Ee, x = rem % Ee;
+            const size_t off = ((size_t)wrap_once(oz + z, g.N[2]) * g.N[1] + wrap_once(oy + y, g.N[1])) * g.N[0] +
+                               wrap_once(ox + x, g.N[0]);
+            reg[u] = __ldg(gr + (size_t)c * g.G + off);
+        }
+        __syncthreads();
+        for (int t = a + w; t < b; t += kTileWarps) {
+            const int bead = TA.sorted[p0 + t];
+            const int4 st = A.start[bead];
+            const double4 fr = A.frac[bead];
+            const bool in = lane < P;
+            const T fx = (T)fr.x + (T)lane, fy = (T)fr.y + (T)lane, fz = (T)fr.z + (T)lane;
+            const T wx_l = in ? window<T>(fx, g.kappa[0]) : (T)0;
+            const T wy_l = in ? window<T>(fy, g.kappa[1]) : (T)0;
+            const T wz_l = in ? window<T>(fz, g.kappa[2]) : (T)0;
+            const T dx_l = fx * (T)g.h[0], dy_l = fy * (T)g.h[1], dz_l = fz * (T)g.h[2];
+            const int lx = st.x - ox, ly = st.y - oy, lz = st.z - oz;
+            T sp[NR], ex[NR], ey[NR], ez[NR];
+#pragma unroll
+            for (int c = 0; c < NR; ++c) sp[c] = ex[c] = ey[c] = ez[c] = (T)0;
+            for (int first = 0; first < P2; first += 32) {
+                const int pair = first + lane;
+                const bool on = pair < P2;
+                int j = pair / P, i = pair - j * P;
+                if (!on) i = j = 0;
+                const T wx = __shfl_sync(0xffffffffu, wx_l, i), wy = __shfl_sync(0xffffffffu, wy_l, j);
+                const T wxy = on ? wx * wy : (T)0;
+                T dx = (T)0, dy = (T)0;
+                if (GRAD) {
+                    dx = __shfl_sync(0xffffffffu, dx_l, i);
+                    dy = __shfl_sync(0xffffffffu, dy_l, j);
+                }
+                const int base = (lz * Ee + ly + j) * Ee + lx + i;
+                T acc[NR], accz[NR];
+#pragma unroll
+                for (int c = 0; c < NR; ++c) acc[c] = accz[c] = (T)0;
+                for (int k = 0; k < P; ++k) {
+                    const T wz = __shfl_sync(0xffffffffu, wz_l, k);
+                    T dz = (T)0;
+                    if (GRAD) dz = __shfl_sync(0xffffffffu, dz_l, k);
+                    if (on) {
+#pragma unroll
+                        for (int c = 0; c < NR; ++c) {
+                            const T v = reg[c * E3 + base + k * E2] * wz;
+                            acc[c] += v;
+                            if (GRAD) accz[c] += v * dz;
+                        }
+                    }
+                }
+#pragma unroll
+                for (int c = 0; c < NR; ++c) {
+                    sp[c] += wxy * acc[c];
+                    if (GRAD) {
+                        ex[c] += wxy * dx * acc[c];
+                        ey[c] += wxy * dy * acc[c];
+                        ez[c] += wxy * accz[c];
+                    }
+                }
+            }
+#pragma unroll
+            for (int c = 0; c < NR; ++c) {
+                const double s0 = warp_sum((double)sp[c]);
+                if (GRAD) {
+                    const double e0 = warp_sum((double)ex[c]);
+                    const double e1 = warp_sum((double)ey[c]);
+                    const double e2 = warp_sum((double)ez[c]);
+                    if (lane == 0) {
+                        double* e = E + ((size_t)c * n + bead) * 3;
+                        e[0] = -g.grad * e0;
+                        e[1] = -g.grad * e1;
+                        e[2] = -g.grad * e2;
+                    }
+                }
+                if (lane == 0) psi[(size_t)c * n + bead] = g.gather * s0;
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// Blocks take fewer sorted beads when the beads are few, so that isolated
+// beads (one warp each) still give every SM several blocks.
+TileArgs tile_args(const MeshGeom& g, const StencilCache& b, int n) {
+    TileArgs TA{};
+    TA.chunk = n >= 152 * 4 * 128 ? 128 : (n >= 152 * 4 * 64 ? 64 : 32);
+    TA.A.g = g;
+    TA.A.wpb = 1;
+    TA.A.rounds = (g.P * g.P + 31) / 32;
+    TA.A.start = b.start.as<int4>();
+    TA.A.frac = b.frac.as<double4>();
+    TA.sorted = b.tile_sorted.as<int>();
+    TA.key = b.tile_key.as<int>();
+    for (int d = 0; d < 3; ++d) TA.tn[d] = b.tile_n[d];
+    TA.ntiles = b.tile_n[0] * b.tile_n[1] * b.tile_n[2];
+    TA.E = kTileNodes + g.P - 1;
+    return TA;
+}
+
+template <typename T>
+size_t tile_smem_bytes(const MeshGeom& g, int nrhs) {
+    const size_t E = kTileNodes + g.P - 1;
+    return sizeof(T) * (size_t)nrhs * E * E * E;
+}
+
+// Opt-in to more than 48 KB of dynamic shared memory for every tiled kernel,
+// once per device (outside any stream capture: called when bins are built).
+template <typename K>
+void tile_smem_attr(K kernel) {
+    IBP_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTileSmemMax));
+}
+
+template <typename T, int NR>
+void tile_attrs_nr() {
+    tile_smem_attr(spread_tiles_kernel<T, NR>);
+    tile_smem_attr(gather_tiles_kernel<T, NR, true>);
+    tile_smem_attr(gather_tiles_kernel<T, NR, false>);
+}
+
+template <typename T>
+void tile_attrs() {
+    tile_attrs_nr<T, 1>();
+    tile_attrs_nr<T, 2>();
+    tile_attrs_nr<T, 3>();
+    tile_attrs_nr<T, 4>();
+    tile_attrs_nr<T, 5>();
+    tile_attrs_nr<T, 6>();
+    tile_attrs_nr<T, 7>();
+    tile_attrs_nr<T, 8>();
+}
+
+void tile_attrs_once() {
+    constexpr int kMaxDev = 64;
+    static bool done[kMaxDev] = {};
+    static std::mutex mu;
+    int dev = 0;
+    IBP_CUDA(cudaGetDevice(&dev));
+    std::lock_guard<std::mutex> lock(mu);
+    if (dev < 0 || dev >= kMaxDev) fail(IBPME_ERR_CUDA, "device ordinal %d out of range", dev);
+    if (done[dev]) return;
+    tile_attrs<float>();
+    tile_attrs<double>();
+    done[dev] = true;
+}
+
+template <typename T, int NR>
+void launch_tiles(bool spread, bool grad, const TileArgs& TA, int n, const double* q, T* grid, double* psi,
+                  double* E, cudaStream_t s) {
+    const size_t bytes = tile_smem_bytes<T>(TA.A.g, NR);
+    const int blocks = div_up(n, TA.chunk);
+    if (spread)
+        spread_tiles_kernel<T, NR><<<blocks, kTileThreads, bytes, s>>>(TA, n, q, grid);
+    else if (grad)
+        gather_tiles_kernel<T, NR, true><<<blocks, kTileThreads, bytes, s>>>(TA, n, grid, psi, E);
+    else
+        gather_tiles_kernel<T, NR, false><<<blocks, kTileThreads, bytes, s>>>(TA, n, grid, psi, nullptr);
+}
+
+template <typename T>
+void tiles_dispatch(int nrhs, bool spread, bool grad, const TileArgs& TA, int n, const double* q, T* grid,
+                    double* psi, double* E, cudaStream_t s) {
+    switch (nrhs) {
+        case 1: launch_tiles<T, 1>(spread, grad, TA, n, q, grid, psi, E, s); break;
+        case 2: launch_tiles<T, 2>(spread, grad, TA, n, q, grid, psi, E, s); break;
+        case 3: launch_tiles<T, 3>(spread, grad, TA, n, q, grid, psi, E, s); break;
+        case 4: launch_tiles<T, 4>(spread, grad, TA, n, q, grid, psi, E, s); break;
+        case 5: launch_tiles<T, 5>(spread, grad, TA, n, q, grid, psi, E, s); break;
+        case 6: launch_tiles<T, 6>(spread, grad, TA, n, q, grid, psi, E, s); break;
+        case 7: launch_tiles<T, 7>(spread, grad, TA, n, q, grid, psi, E, s); break;
+        default: launch_tiles<T, 8>(spread, grad, TA, n, q, grid, psi, E, s); break;
+    }
+}
+
+// The tiled path serves a call when the cache holds tile bins and the region of
+// all its channels fits in shared memory.
+template <typename T>
+bool tiles_fit(const MeshGeom& g, const StencilCache* sc, int nrhs) {
+    return sc && sc->tiles && nrhs <= 8 && tile_smem_bytes<T>(g, nrhs) <= kTileSmemMax;
+}
+
 // G(k)/(N_x N_y N_z) on the half spectrum, Eq. after H_hat:
 // j0^2(k a) e^{-(1 - eta) k^2 / (4 xi^2)} / k^2, zero at k = 0 (Sec. II, k = 0 removed).
 template <typename T>
@@ -645,7 +1114,9 @@ void Mesh<T>::spread(int n, const double* xw, const double* q, int nrhs, const i
     // warp per bead the row-walking kernel keeps its atomics of consecutive
     // instructions within one z-plane, which measured faster on dense surfaces.
     const PairArgs A = sc ? pair_args(g, *sc, n) : PairArgs{};
-    if (sc && A.wpb > 1) {
+    if (tiles_fit<T>(g, sc, nrhs)) {
+        tiles_dispatch<T>(nrhs, true, false, tile_args(g, *sc, n), n, q, grid.as<T>(), nullptr, nullptr, s);
+    } else if (sc && A.wpb > 1) {
         pairs_dispatch<T>(nrhs, true, false, A, n, q, grid.as<T>(), nullptr, nullptr, s);
     } else {
         spread_dispatch<T>(n, xw, q, nrhs, bead_cfg, g, grid.as<T>(), s);
@@ -690,6 +1161,11 @@ void Mesh<T>::gather(int n, const double* xw, int nrhs, const int* bead_cfg, dou
                      cudaStream_t s, const StencilCache* sc) {
     if (n == 0) return;
     ProfScope ps(mesh_stage<T>(ST_GATHER), s);
+    if (tiles_fit<T>(g, sc, nrhs)) {
+        tiles_dispatch<T>(nrhs, false, E != nullptr, tile_args(g, *sc, n), n, nullptr, grid.as<T>(), psi, E, s);
+        IBP_CHECK_LAUNCH();
+        return;
+    }
     if (sc) {   // several warps of a bead add their partial sums into zeroed outputs
         const PairArgs A = pair_args(g, *sc, n);
         if (A.wpb > 1) {
@@ -720,6 +1196,36 @@ const StencilCache* stencil_cache(ibpme_ctx* c, int n, const double* xw) {
     double4* frac = static_cast<double4*>(b.frac.ensure(sizeof(double4) * n));
     stencil_cache_kernel<<<div_up(n, 256), 256, 0, c->stream>>>(n, xw, c->bcfg, g, start, frac);
     IBP_CHECK_LAUNCH();
+    // tile bins when one warp per bead already fills the GPU and a region of
+    // E^3 nodes does not wrap onto itself
+    const int E = kTileNodes + g.P - 1;
+    const long long blocks32 = (g.P * g.P + 31) / 32;
+    b.tiles = (long long)n * blocks32 > 152LL * 64 * 2 && g.N[0] >= E && g.N[1] >= E && g.N[2] >= E &&
+              std::getenv("IBPME_NO_TILES") == nullptr;   // the switch lets tests compare both paths
+    if (b.tiles) {
+        for (int d = 0; d < 3; ++d) b.tile_n[d] = div_up(g.N[d], kTileNodes);
+        const long long nkeys = (long long)b.tile_n[0] * b.tile_n[1] * b.tile_n[2] * c->ncfg;
+        if (nkeys > (1LL << 30)) {
+            b.tiles = false;
+        } else {
+            tile_attrs_once();
+            const int nk = (int)nkeys;
+            int* count = static_cast<int*>(b.tile_count.ensure(sizeof(int) * nk));
+            int* cursor = static_cast<int*>(b.tile_cursor.ensure(sizeof(int) * nk));
+            long long* off = static_cast<long long*>(b.tile_off.ensure(sizeof(long long) * (nk + 1)));
+            int* bkey = static_cast<int*>(b.tile_bkey.ensure(sizeof(int) * n));
+            int* sorted = static_cast<int*>(b.tile_sorted.ensure(sizeof(int) * n));
+            int* skey = static_cast<int*>(b.tile_key.ensure(sizeof(int) * n));
+            IBP_CUDA(cudaMemsetAsync(count, 0, sizeof(int) * nk, c->stream));
+            IBP_CUDA(cudaMemsetAsync(cursor, 0, sizeof(int) * nk, c->stream));
+            tile_count_kernel<<<div_up(n, 256), 256, 0, c->stream>>>(n, start, b.tile_n[0], b.tile_n[1], b.tile_n[2],
+                                                                     count, bkey);
+            IBP_CHECK_LAUNCH();
+            scan_counts(count, off, nk, b.tile_tmp, c->stream);
+            tile_fill_kernel<<<div_up(n, 256), 256, 0, c->stream>>>(n, bkey, off, cursor, sorted, skey);
+            IBP_CHECK_LAUNCH();
+        }
+    }
     b.fp = c->near.fp;
     b.n = n;
     b.ncfg = c->ncfg;

@@ -141,6 +141,59 @@ def test_cached_stencil_mesh_kernels_match_fp64_and_oracle(cuda_lib, nrhs):
         ib.pme_destroy(c32)
 
 
+def _dense_surfaces(seed, n_surf=6, per=1500, n_ions=1000, box=(5.0, 6.0, 7.0)):
+    """Beads packed on sphere surfaces (hundreds per grid cell, some straddling
+    the periodic faces) plus scattered ions."""
+    rng = np.random.default_rng(seed)
+    box = np.asarray(box)
+    parts = []
+    for k in range(n_surf):
+        d = rng.normal(size=(per, 3))
+        c = rng.uniform(0, 1, size=3) * box if k else np.array([0.2, 5.9, 3.5])   # one across the corner
+        parts.append(c + 0.8 * d / np.linalg.norm(d, axis=1, keepdims=True))
+    parts.append(rng.uniform(0, 1, size=(n_ions, 3)) * box)
+    return np.mod(np.concatenate(parts), box), box
+
+
+@pytest.mark.parametrize("nrhs", [1, 3])
+def test_tiled_mesh_path_matches_direct_path_and_oracle(cuda_lib, nrhs, monkeypatch):
+    """10,000 beads (9,000 on six sphere surfaces, 1,000 ions) take the tiled
+    spread and gather (shared-memory regions for dense tiles, direct atomics for
+    isolated ions); mesh sizes that are not multiples of the tile edge leave
+    ragged last tiles.  Against the same call with tiles switched off (FP64 to
+    rounding, FP32 to FP32 rounding) and against the oracle at sampled beads."""
+    ib = cuda_lib
+    x, box = _dense_surfaces(50 + nrhs)
+    n = x.shape[0]
+    q = np.stack([random_neutral_charges(n, 200 + r) for r in range(nrhs)])
+    kw = dict(box=box, mesh=(36, 44, 52), tol=1e-6, bead_radius=0.01, eps_f=0.8, max_rhs=4)
+    out = {}
+    for tiles in (True, False):
+        if tiles:
+            monkeypatch.delenv("IBPME_NO_TILES", raising=False)
+        else:
+            monkeypatch.setenv("IBPME_NO_TILES", "1")
+        for prec in (ib.IBPME_FP64, ib.IBPME_MIXED):
+            ctx = ib.pme_setup(ib.make_params(precision=prec, **kw))
+            try:
+                out[tiles, prec] = _field(ib, ctx, x, q, nrhs=nrhs)
+            finally:
+                ib.pme_destroy(ctx)
+    monkeypatch.delenv("IBPME_NO_TILES", raising=False)
+    for prec, bar in ((ib.IBPME_FP64, 1e-12), (ib.IBPME_MIXED, 2e-6)):
+        (pt, et), (pd, ed) = out[True, prec], out[False, prec]
+        for r in range(nrhs):
+            assert rel_err(pt[r], pd[r]) < bar, (prec, r, rel_err(pt[r], pd[r]))
+            assert rel_err(et[r], ed[r]) < bar, (prec, r, rel_err(et[r], ed[r]))
+    t = np.random.default_rng(1).choice(n, size=48, replace=False).astype(np.int32)
+    for r in range(nrhs):
+        ref_psi, ref_E = o.potential(x, q[r], box, 0.01, 0.8, targets=t, field=True)
+        for prec, bar in ((ib.IBPME_FP64, FP64_RTOL), (ib.IBPME_MIXED, MIXED_RTOL)):
+            p, e = out[True, prec]
+            assert rel_err(p[r][t], ref_psi) < bar, (prec, r, rel_err(p[r][t], ref_psi))
+            assert rel_err(e[r][t], ref_E) < bar, (prec, r, rel_err(e[r][t], ref_E))
+
+
 def test_pme_field_multi_rhs_host_pointers_and_edge_cases(cuda_lib):
     ib = cuda_lib
     x, q0, box, a, eps, mesh, tol = _field_case("sphere162")
