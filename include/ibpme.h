@@ -29,6 +29,11 @@
  *     ibpme_last_error() gives a message for the calling thread.  After an
  *     error the outputs are unspecified.
  *   - All beads share one radius a (Sec. III.A).
+ *   - Environment switches (read when the data they govern are built; for
+ *     diagnostics and tests, results agree to rounding either way):
+ *     IBPME_NO_GRAPHS (no captured iteration graphs), IBPME_NO_TILES (no
+ *     shared-memory tiles in spreading and gathering), IBPME_NO_COMPACT (every
+ *     intra-body pair in the real-space table), IBPME_VERBOSE (solver log).
  */
 #ifndef IBPME_H
 #define IBPME_H

@@ -434,6 +434,7 @@ IBP_API ibpme_status pme_spread(ibpme_ctx* c, int n, const double* x, const doub
         const double* dq = static_cast<const double*>(stage_in(c, q, sizeof(double) * (size_t)nrhs * n, c->st_q));
         double* xw = static_cast<double*>(c->xw.ensure(sizeof(double) * 3 * (n ? n : 1)));
         wrap_positions(c, n, dx, xw);
+        c->bodies_current = false;
         const bool mixed = c->p.precision == IBPME_MIXED;
         const size_t gb = (mixed ? sizeof(float) : sizeof(double)) * (size_t)c->geom.G * nrhs;
         if (mixed)
@@ -465,6 +466,7 @@ IBP_API ibpme_status pme_field(ibpme_ctx* c, int n, const double* x, const doubl
         if (n == 0) return IBPME_OK;
         double* xw = static_cast<double*>(c->xw.ensure(sizeof(double) * 3 * n));
         wrap_positions(c, n, dx, xw);
+        c->bodies_current = false;   // beads without bodies: every pair goes through the table
         pme_apply(c, n, xw, dq, nrhs, c->p.precision, static_cast<double*>(op.dev), static_cast<double*>(oe.dev),
                   false);
         finish_out(c, op);

@@ -400,6 +400,7 @@ void bodies_upload(ibpme_ctx* c, int n, const ibpme_bodies* b, const double* xw,
         bd.host_off = off;
         bd.host_cfg = cb;
         bd.host_n = n;
+        ++bd.version;
     }
     bd.X.ensure(sizeof(double) * 3 * nb);
     bd.Q.ensure(sizeof(double) * nb);
@@ -409,6 +410,7 @@ void bodies_upload(ibpme_ctx* c, int n, const ibpme_bodies* b, const double* xw,
     rel_kernel<<<div_up(n, 256), 256, 0, s>>>(n, xw, bd.bead_body.as<int>(), bd.X.as<double>(), c->p.box[0],
                                               c->p.box[1], c->p.box[2], bd.rel.as<double>());
     IBP_CHECK_LAUNCH();
+    c->bodies_current = true;
 }
 
 void body_dipoles(ibpme_ctx* c, int n, const double* q, int nrhs, double* S) {

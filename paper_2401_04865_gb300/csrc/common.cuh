@@ -193,6 +193,19 @@ struct NearList {
     unsigned long long fp = 0;     // fingerprint of the positions the table was built for
     bool fp_valid = false;
     int ncfg = 1;
+    // Compact bodies: multi-bead bodies within min(r_c, L/4) of their centre.
+    // Their intra-body pairs are left out of the table and evaluated directly
+    // by the compact kernels (FP32 for the inner operator, double-float for the
+    // FP64 operator and the field).
+    bool cb_on = false;            // the table was built with compact bodies taken out
+    unsigned long long cb_key = 0; // body structure the compact data belong to (0: none)
+    DevBuf cb_flag;                // [nb] 1 if the body is compact
+    DevBuf cb_hi, cb_lo;           // [n] float4: position relative to the body centre, hi + lo parts
+    DevBuf cb_tasks;               // int4 per block: (body, first target, first source, counts)
+    int cb_ntasks = 0;
+    unsigned long long cb_tasks_key = 0;
+    DevBuf tab32;                  // [nt] float4: FP32 cubic coefficients of phi per interval
+    DevBuf tab_df;                 // [nt][3] float4: double-float phi and phi' coefficients
 };
 
 // Body bookkeeping on the device for solves, forces and BD steps.
@@ -226,6 +239,7 @@ struct BodyData {
     std::vector<int> uo_h, cfg_beads_h, cfg_bodies_h;
     std::vector<int> host_off, host_cfg;   // structure of the last upload (to skip rebuilding the lists)
     int host_n = -1;
+    unsigned long long version = 0;        // changes whenever the body structure changes
 };
 
 struct Krylov;   // krylov.cu
@@ -316,6 +330,7 @@ struct ibpme_ctx {
     // bead b belongs to configuration bcfg[b]
     int ncfg = 1;
     const int* bcfg = nullptr;
+    bool bodies_current = false;   // the uploaded bodies belong to the running call
     ibp::DevBuf ml_feat, ml_scratch, ml_scales, ml_y;   // learned warm start
     cudaEvent_t ev_in = nullptr, ev_out = nullptr;
     ibp::StencilCache stencils;               // stencils of the current positions

@@ -12,6 +12,7 @@
 // is fused between the forward and inverse z passes, and the real lines come
 // back as FP64.  Sizes that are not powers of two use cuFFT.
 #include "common.cuh"
+#include "dfloat.cuh"
 
 #include <cmath>
 #include <vector>
@@ -25,50 +26,10 @@ constexpr int kDfThreads = 1024;  // one butterfly per thread per stage
 constexpr int kDfPad = 1;         // float4 of padding after each line in shared memory (bank spread)
 constexpr int kDfSmem = kDfPoints + kDfPoints / 16 * kDfPad;   // lines <= kDfPoints / 16
 
-// ---- double-float arithmetic (round-to-nearest intrinsics: no contraction) ----
-// Accuracy: each operation is exact to about 2^-44 of its operands' magnitude, so
-// a length-N transform keeps a normwise error near log2(N) 2^-44, far below the
-// FP32 mesh and the 1e-6 residual test it serves.
-struct df {
-    float hi, lo;
-};
-
-__device__ __forceinline__ df two_sum(float a, float b) {
-    const float s = __fadd_rn(a, b);
-    const float bb = __fsub_rn(s, a);
-    const float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
-    return {s, e};
-}
-
-__device__ __forceinline__ df fast_two_sum(float a, float b) {   // |a| >= |b|
-    const float s = __fadd_rn(a, b);
-    return {s, __fsub_rn(b, __fsub_rn(s, a))};
-}
-
-// Sum with one two-sum on the high parts: its error is bounded relative to
-// |a| + |b| (not to |a + b|), which is what a normwise FFT error bound needs.
-__device__ __forceinline__ df df_add(df a, df b) {
-    const df s = two_sum(a.hi, b.hi);
-    return fast_two_sum(s.hi, __fadd_rn(s.lo, __fadd_rn(a.lo, b.lo)));
-}
-
-__device__ __forceinline__ df df_neg(df a) { return {-a.hi, -a.lo}; }
-
-__device__ __forceinline__ df df_mul(df a, df b) {
-    const float p = __fmul_rn(a.hi, b.hi);
-    float e = __fmaf_rn(a.hi, b.hi, -p);
-    e = __fmaf_rn(a.hi, b.lo, e);
-    e = __fmaf_rn(a.lo, b.hi, e);
-    return fast_two_sum(p, e);
-}
-
-__device__ __forceinline__ df df_from_double(double v) {
-    const float h = (float)v;
-    return {h, (float)(v - (double)h)};
-}
-
-__device__ __forceinline__ double df_to_double(df a) { return (double)a.hi + (double)a.lo; }
-
+// Accuracy of the double-float operations (dfloat.cuh): each is exact to about
+// 2^-44 of its operands' magnitude, so a length-N transform keeps a normwise
+// error near log2(N) 2^-44, far below the FP32 mesh and the 1e-6 residual test
+// it serves.
 struct dfc {
     df re, im;
 };

@@ -727,6 +727,9 @@ struct Solver {
                                       (long long)c->stencils.tiles, (long long)c->stencils.tile_n[0],
                                       (long long)c->stencils.tile_n[1], (long long)c->stencils.tile_n[2],
                                       P(c->stencils.tile_sorted.p), P(c->stencils.tile_key.p),
+                                      (long long)c->near.cb_on, (long long)c->near.cb_ntasks,
+                                      P(c->near.cb_flag.p), P(c->near.cb_hi.p), P(c->near.cb_lo.p),
+                                      P(c->near.cb_tasks.p), P(c->near.tab32.p), P(c->near.tab_df.p),
                                       (long long)pre_on, (long long)c->pre.npb, (long long)c->pre.nplain,
                                       (long long)c->pre.chunks, P(k->pu.p), P(c->pre.minv.p), P(c->pre.gvec.p),
                                       P(c->pre.sinv.p), P(c->pre.pb_shape.p), P(c->pre.pb_first.p),

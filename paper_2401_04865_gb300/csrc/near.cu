@@ -15,6 +15,11 @@
 // with g'(u) = -2A e^{-u^2 xi^2} + 4 B xi^2 u erfc(u xi); three exp and three
 // erfc give both phi_r and phi_r'.
 #include "common.cuh"
+#include "dfloat.cuh"
+
+#include <cstdlib>
+#include <mutex>
+#include <vector>
 
 namespace ibp {
 
@@ -28,13 +33,20 @@ struct PairConst {
     double L[3];
     int nc[3];
     int lo[3], hi[3];   // neighbour cell offsets per axis
-    // tabulated kernel on [2a, r_c]: node i at r = t0 + i h holds (phi, phi', phi'')
+    // tabulated kernel on [2a, r_c] in u = r^2 / (2a)^2: octave e (u in [2^e, 2^(e+1)))
+    // holds kOctaveIntervals equal intervals; node j = e kOctaveIntervals + i sits at
+    // u = 2^e (1 + i / kOctaveIntervals) and holds (phi, dphi/du, G, dG/du) with
+    // G = -phi'(r) / r, the factor of the field
     const double* table;
-    double t0, h, inv_h;
-    int nt;
+    double inv4a2;      // 1 / (2a)^2
+    int K;              // octaves (0: no table, every pair takes the exact kernel)
+    // pairs inside one compact body are not tabulated (NULL: every pair is)
+    const int* bbody;   // body of each bead
+    const int* cflag;   // compact flag of each body
 };
 
-constexpr int kTableIntervals = 4096;
+constexpr int kOctaveIntervals = 128;   // intervals per octave of u (a power of two)
+constexpr int kMaxOctaves = 24;         // r_c / 2a up to 4096
 
 __device__ __forceinline__ void g_and_dg(double u, const PairConst& k, double& g, double& dg) {
     const double x2 = k.xi * k.xi;
@@ -75,30 +87,47 @@ __device__ void pair_kernel_d2(double r, const PairConst& k, double& phi, double
     d2phi = d2D / r - 2.0 * dD / (r * r) + 2.0 * D / (r * r * r);
 }
 
+// Node j of the table: u = 2^e (1 + i / M), r = 2a sqrt(u); with du/dr = r / (2 a^2),
+// dphi/du = phi' 2a^2 / r and dG/du = (phi' / r^2 - phi'' / r) 2a^2 / r.
 __global__ void table_kernel(PairConst k, double* __restrict__ table) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i > k.nt) return;
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j > k.K * kOctaveIntervals) return;
+    const int e = j / kOctaveIntervals, i = j % kOctaveIntervals;
+    const double u = ldexp(1.0 + (double)i / kOctaveIntervals, e);
+    const double r = 2.0 * k.a * sqrt(u);
     double p, d, d2;
-    pair_kernel_d2(k.t0 + i * k.h, k, p, d, d2);
-    table[3 * i + 0] = p;
-    table[3 * i + 1] = d;
-    table[3 * i + 2] = d2;
+    pair_kernel_d2(r, k, p, d, d2);
+    const double s = 2.0 * k.a * k.a / r;
+    table[4 * j + 0] = p;
+    table[4 * j + 1] = d * s;
+    table[4 * j + 2] = -d / r;
+    table[4 * j + 3] = (d / (r * r) - d2 / r) * s;
 }
 
-// Cubic Hermite interpolation of phi (from phi, phi') and of phi' (from phi', phi'')
-// between table nodes; r in [2a, r_c).
-__device__ __forceinline__ void pair_table(double r, const PairConst& k, double& phi, double& dphi) {
-    const double t = (r - k.t0) * k.inv_h;
-    int i = (int)t;
-    i = i < 0 ? 0 : (i >= k.nt ? k.nt - 1 : i);
-    const double s = t - i;
-    const double* a = k.table + 3 * i;
-    const double p0 = a[0], d0 = a[1], e0 = a[2], p1 = a[3], d1 = a[4], e1 = a[5];
+// Octave e, interval i and fraction s of u (>= about 1): u = 2^e (1 + (i + s) / M).
+__device__ __forceinline__ int table_interval(double u, const PairConst& k, double& s, double& hu) {
+    const long long bits = __double_as_longlong(u);
+    int e = (int)((bits >> 52) & 0x7FF) - 1023;   // floor(log2 u) for normal u
+    e = e < 0 ? 0 : (e > k.K - 1 ? k.K - 1 : e);
+    const double w = u * __longlong_as_double((long long)(1023 - e) << 52);   // u / 2^e, exact
+    const double t = (w - 1.0) * kOctaveIntervals;
+    int i = (int)floor(t);
+    i = i < 0 ? 0 : (i > kOctaveIntervals - 1 ? kOctaveIntervals - 1 : i);
+    s = t - i;
+    hu = __longlong_as_double((long long)(1023 + e) << 52) / kOctaveIntervals;   // interval width in u
+    return e * kOctaveIntervals + i;
+}
+
+// Cubic Hermite interpolation of phi and of G = -phi'/r in u, for r^2 in [(2a)^2, r_c^2).
+__device__ __forceinline__ void pair_table(double r2, const PairConst& k, double& phi, double& gfac) {
+    double s, hu;
+    const int j = table_interval(r2 * k.inv4a2, k, s, hu);
+    const double* a = k.table + 4 * j;
     const double s2 = s * s, s3 = s2 * s;
     const double h00 = 2.0 * s3 - 3.0 * s2 + 1.0, h10 = s3 - 2.0 * s2 + s;
     const double h01 = -2.0 * s3 + 3.0 * s2, h11 = s3 - s2;
-    phi = h00 * p0 + h10 * k.h * d0 + h01 * p1 + h11 * k.h * d1;
-    dphi = h00 * d0 + h10 * k.h * e0 + h01 * d1 + h11 * k.h * e1;
+    phi = h00 * a[0] + h10 * hu * a[1] + h01 * a[4] + h11 * hu * a[5];
+    gfac = h00 * a[2] + h10 * hu * a[3] + h01 * a[6] + h11 * hu * a[7];
 }
 
 __device__ __forceinline__ int cell_coord(double x, double L, int nc) {
@@ -179,6 +208,8 @@ __device__ __forceinline__ void for_neighbours(int alpha, const double* __restri
     const float rc2f = k.rc2_cand;
     const int ncell = k.nc[0] * k.nc[1] * k.nc[2];
     const int base = (cell_of[alpha] / ncell) * ncell;   // first cell of the bead's configuration
+    const int ba = k.cflag ? k.bbody[alpha] : -1;
+    const int skip_body = (ba >= 0 && k.cflag[ba]) ? ba : -1;   // alpha's compact body, or -1
     const int c = cell_of[alpha] - base;
     const int cx = c % k.nc[0], cy = (c / k.nc[0]) % k.nc[1], cz = c / (k.nc[0] * k.nc[1]);
     for (int oz = k.lo[2]; oz <= k.hi[2]; ++oz)
@@ -200,7 +231,8 @@ __device__ __forceinline__ void for_neighbours(int alpha, const double* __restri
                         const float fx = min_image_wrapped(p0.x - pb.x, Lx);
                         const float fy = min_image_wrapped(p0.y - pb.y, Ly);
                         const float fz = min_image_wrapped(p0.z - pb.z, Lz);
-                        if (beta != alpha && fx * fx + fy * fy + fz * fz < rc2f) {
+                        if (beta != alpha && fx * fx + fy * fy + fz * fz < rc2f &&
+                            (skip_body < 0 || k.bbody[beta] != skip_body)) {
                             dx = min_image_wrapped(x0 - xw[3 * beta + 0], k.L[0]);
                             dy = min_image_wrapped(y0 - xw[3 * beta + 1], k.L[1]);
                             dz = min_image_wrapped(z0 - xw[3 * beta + 2], k.L[2]);
@@ -247,20 +279,22 @@ __global__ void pair_fill_kernel(int n, const double* __restrict__ xw, const flo
                        const unsigned m = __ballot_sync(0xffffffffu, within);
                        if (within) {
                            const long long slot = base + __popc(m & lt);
-                           const double r = sqrt(r2);
-                           double phi, dphi;
-                           if (r >= 2.0 * k.a) {
-                               pair_table(r, k, phi, dphi);
-                           } else if (r > 0.0) {
+                           double phi, g;
+                           if (k.K > 0 && r2 * k.inv4a2 >= 1.0) {
+                               pair_table(r2, k, phi, g);
+                           } else if (r2 > 0.0) {
+                               const double r = sqrt(r2);
+                               double dphi;
                                pair_kernel(r, k, phi, dphi);   // overlapping beads: exact form
+                               g = -dphi / r;
                            } else {
-                               phi = k.self;   // coincident beads: the r -> 0 limit
-                               dphi = 0.0;
+                               phi = k.self;   // coincident beads: the r -> 0 limit, no field
+                               g = 0.0;
                            }
                            col[slot] = slot_b;
                            val[slot] = phi;
                            pair32[slot] = make_uint2((unsigned)slot_b, __float_as_uint((float)phi));
-                           if (gfac) gfac[slot] = (r > 0.0) ? -dphi / r : 0.0;
+                           if (gfac) gfac[slot] = g;
                        }
                        base += __popc(m);
                    });
@@ -421,6 +455,441 @@ __global__ void near_field_kernel(int n, int nrhs, const double* __restrict__ xw
     }
 }
 
+// ---------------------------------------------------------------------------
+// Compact bodies: intra-body pairs evaluated directly.
+//
+// Within a body whose beads all lie within min(r_c, L/4) of its centre, nearly
+// every pair is inside r_c; such pairs are most of the table of a tessellated
+// colloid (n_b^2 per body) and tabulating them needs FP64 per pair.  Instead,
+// blocks of kCbThreads targets sweep the body's beads staged in shared memory
+// and evaluate phi_r from cubic coefficients per table interval: FP32 for the
+// inner operator of a mixed solve, double-float (dfloat.cuh) for the FP64
+// operator and the field.  Positions are taken relative to the body centre, so
+// every intra-body difference is its minimum image (|difference| <= L/2).
+// Overlapping beads (r < 2a, rare within a tessellation) use the exact FP64
+// kernel; coincident beads the r -> 0 limit, as in the table.
+// ---------------------------------------------------------------------------
+constexpr int kCompactMin = 32;    // smaller bodies stay in the table
+constexpr int kCbThreads = 128;    // targets per task and sources staged per round
+constexpr int kCbBlocksPerSm = 6;  // resident blocks of the persistent compact kernels
+
+// Tables per interval j = e M + i of u (see PairConst), with s in [0, 1):
+//   tab32[j] = (p0, c1, c2, c3), phi = p0 + s (c1 + s (c2 + s c3))         (FP32)
+//   tabdf[3j..3j+2] = (p0 hi, p0 lo, c1 hi, c1 lo), (c2, c3, g0 hi, g0 lo), (f1 hi, f1 lo, f2, f3)
+// for phi and G = -phi'/r in double-float (linear terms) and FP32 (the smaller
+// quadratic and cubic ones).
+struct CbArgs {
+    const int* flag;       // [nb] compact
+    const int4* tasks;     // (body, first target bead, first source bead, target count << 20 | source count)
+    int ntasks;
+    const float4* hi;      // [n] position relative to the body centre, high parts
+    const float4* lo;      // low parts
+    const float4* tab32;
+    const float4* tabdf;
+    int nt;                // intervals (K M)
+    int K;                 // octaves
+    float rc2f, a2x4f, inv4a2f;
+    df rc2, inv4a2;
+    PairConst k;
+};
+
+// Interval and fraction of u = r^2 / (2a)^2 (FP32); u < 1 extrapolates the first interval.
+__device__ __forceinline__ int cb_interval32(float u, int K, float& s) {
+    int e = (__float_as_int(u) >> 23) - 127;
+    e = min(max(e, 0), K - 1);
+    const float w = __int_as_float(__float_as_int(u) - (e << 23));   // u / 2^e, exact
+    const float t = (w - 1.0f) * (float)kOctaveIntervals;
+    const int i = min(max((int)t, 0), kOctaveIntervals - 1);
+    s = t - (float)i;
+    return e * kOctaveIntervals + i;
+}
+
+// The same in double-float: w = u / 2^e scales both parts exactly, and the fraction
+// keeps the low part.
+__device__ __forceinline__ int cb_interval(df u, int K, df& s) {
+    int e = (__float_as_int(u.hi) >> 23) - 127;
+    e = min(max(e, 0), K - 1);
+    const float sc = __int_as_float((127 - e) << 23);   // 2^-e
+    const df w = {__fmul_rn(u.hi, sc), __fmul_rn(u.lo, sc)};
+    const df t0 = two_sum(w.hi, -1.0f);
+    const df t = fast_two_sum(__fmul_rn(t0.hi, (float)kOctaveIntervals),
+                              __fmul_rn(__fadd_rn(t0.lo, w.lo), (float)kOctaveIntervals));
+    int i = (int)floorf(t.hi);
+    i = min(max(i, 0), kOctaveIntervals - 1);
+    s = two_sum(__fsub_rn(t.hi, (float)i), t.lo);   // t.hi - i is exact
+    return e * kOctaveIntervals + i;
+}
+
+__device__ __forceinline__ df cb_poly(float4 a, float c2, float c3, df s) {
+    const df lin = df_add({a.x, a.y}, df_mul(s, {a.z, a.w}));
+    return df_add(lin, {__fmul_rn(__fmul_rn(s.hi, s.hi), __fmaf_rn(s.hi, c3, c2)), 0.0f});
+}
+
+__device__ __forceinline__ df cb_diff(float ah, float al, float bh, float bl) {
+    const df d = two_sum(ah, -bh);
+    return fast_two_sum(d.hi, __fadd_rn(d.lo, __fsub_rn(al, bl)));
+}
+
+// Exact FP64 pair kernel for overlapping or coincident beads (phi and G = -phi'/r).
+__device__ __noinline__ void cb_exact(const CbArgs& A, int ia, int ib, double& phi, double& g, double* d) {
+    const float4 ah = A.hi[ia], al = A.lo[ia], bh = A.hi[ib], bl = A.lo[ib];
+    d[0] = ((double)ah.x - (double)bh.x) + ((double)al.x - (double)bl.x);
+    d[1] = ((double)ah.y - (double)bh.y) + ((double)al.y - (double)bl.y);
+    d[2] = ((double)ah.z - (double)bh.z) + ((double)al.z - (double)bl.z);
+    const double r = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+    if (r > 0.0) {
+        double dphi;
+        pair_kernel(r, A.k, phi, dphi);
+        g = -dphi / r;
+    } else {
+        phi = A.k.self;
+        g = 0.0;
+    }
+}
+
+__device__ __forceinline__ void cb_task(const CbArgs& A, int task, int& body, int& t0, int& s0, int& tc, int& sc) {
+    const int4 w = A.tasks[task];
+    body = w.x;
+    t0 = w.y;
+    s0 = w.z;
+    tc = w.w >> 20;
+    sc = w.w & 0xFFFFF;
+}
+
+// Overlapping (r < 2a) and coincident sources of one target with the exact FP64
+// kernel: a rare second sweep over the task's sources, kept out of the main loop
+// so that it stays free of calls.  The test matches the main loop's.
+template <int NR, bool FIELD, bool DF>
+__device__ __noinline__ void cb_overlaps(const CbArgs& A, int n, int alpha, int s0, int sc,
+                                         const double* __restrict__ q, double* out) {
+    const float4 pa = A.hi[alpha];
+    for (int b = s0; b < s0 + sc; ++b) {
+        if (b == alpha) continue;
+        const float4 pb = A.hi[b];
+        const float dx = pa.x - pb.x, dy = pa.y - pb.y, dz = pa.z - pb.z;
+        const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+        if (!(r2 < A.a2x4f)) continue;
+        double phi, g, d[3];
+        cb_exact(A, alpha, b, phi, g, d);
+        if (!DF) phi = (double)(float)phi;
+#pragma unroll
+        for (int c = 0; c < NR; ++c) {
+            const double qb = q[(size_t)c * n + b];
+            if (FIELD) {
+                out[3 * c + 0] += g * qb * d[0];
+                out[3 * c + 1] += g * qb * d[1];
+                out[3 * c + 2] += g * qb * d[2];
+            } else {
+                out[c] += phi * qb;
+            }
+        }
+    }
+}
+
+// Copy n4 float4 of a table into shared memory.
+__device__ __forceinline__ void cb_stage_table(float4* dst, const float4* __restrict__ src, int n4) {
+    for (int i = threadIdx.x; i < n4; i += blockDim.x) dst[i] = src[i];
+    __syncthreads();
+}
+
+// Inner operator: psi_r[r][alpha] += sum over each task's sources, FP32 pairs from
+// the shared-memory table, FP32 sums per staged round, FP64 across rounds.
+// Persistent blocks stride over the tasks.
+template <int NR>
+__global__ void __launch_bounds__(kCbThreads)
+compact_apply32_kernel(CbArgs A, int n, const double* __restrict__ q, double inv_eps, double* __restrict__ psi) {
+    extern __shared__ float4 cb_tab[];
+    __shared__ float4 sp[kCbThreads];
+    __shared__ float4 sq[kCbThreads];   // charges of up to four fields
+    cb_stage_table(cb_tab, A.tab32, A.nt);
+    const int tid = threadIdx.x;
+    for (int task = blockIdx.x; task < A.ntasks; task += gridDim.x) {
+        int body, t0, s0, tc, sc;
+        cb_task(A, task, body, t0, s0, tc, sc);
+        if (!A.flag[body]) continue;   // block-uniform
+        const int alpha = t0 + tid;
+        const bool tin = tid < tc;
+        const float4 pa = tin ? A.hi[alpha] : make_float4(0.f, 0.f, 0.f, 0.f);
+        double accd[NR];
+#pragma unroll
+        for (int r = 0; r < NR; ++r) accd[r] = 0.0;
+        bool ov = false;
+        for (int u = 0; u < sc; u += kCbThreads) {
+            const int m = min(kCbThreads, sc - u);
+            __syncthreads();
+            if (tid < m) {
+                const int b = s0 + u + tid;
+                sp[tid] = A.hi[b];
+                float v[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+                for (int r = 0; r < NR; ++r) v[r] = (float)q[(size_t)r * n + b];
+                sq[tid] = make_float4(v[0], v[1], v[2], v[3]);
+            }
+            __syncthreads();
+            if (!tin) continue;
+            float acc[NR];
+#pragma unroll
+            for (int r = 0; r < NR; ++r) acc[r] = 0.0f;
+            const int self = alpha - (s0 + u);
+#pragma unroll 4
+            for (int j = 0; j < m; ++j) {
+                const float4 pb = sp[j];
+                const float dx = pa.x - pb.x, dy = pa.y - pb.y, dz = pa.z - pb.z;
+                const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+                const bool near = r2 < A.a2x4f;   // the target itself, or an overlap
+                ov |= near && j != self;
+                const bool use = r2 < A.rc2f && !near;
+                float s;
+                const int i = cb_interval32(r2 * A.inv4a2f, A.K, s);
+                const float4 c = cb_tab[use ? i : 0];
+                const float phi = use ? fmaf(s, fmaf(s, fmaf(s, c.w, c.z), c.y), c.x) : 0.0f;
+                const float4 qb = sq[j];
+                const float qv[4] = {qb.x, qb.y, qb.z, qb.w};
+#pragma unroll
+                for (int r = 0; r < NR; ++r) acc[r] = fmaf(phi, qv[r], acc[r]);
+            }
+#pragma unroll
+            for (int r = 0; r < NR; ++r) accd[r] += (double)acc[r];
+        }
+        if (tin) {
+            if (ov) cb_overlaps<NR, false, false>(A, n, alpha, s0, sc, q, accd);
+#pragma unroll
+            for (int r = 0; r < NR; ++r) atomicAdd(psi + (size_t)r * n + alpha, accd[r] * inv_eps);
+        }
+    }
+}
+
+// FP64 operator: the same sum in double-float arithmetic, the phi coefficients
+// (two float4 per interval) in shared memory.
+template <int NR>
+__global__ void __launch_bounds__(kCbThreads)
+compact_apply64_kernel(CbArgs A, int n, const double* __restrict__ q, double inv_eps, double* __restrict__ psi) {
+    extern __shared__ float4 cb_tab[];
+    __shared__ float4 sh[kCbThreads], sl[kCbThreads];
+    __shared__ float2 sq[NR][kCbThreads];
+    for (int i = threadIdx.x; i < A.nt; i += blockDim.x) {
+        cb_tab[2 * i] = A.tabdf[3 * i];
+        cb_tab[2 * i + 1] = A.tabdf[3 * i + 1];
+    }
+    __syncthreads();
+    const int tid = threadIdx.x;
+    for (int task = blockIdx.x; task < A.ntasks; task += gridDim.x) {
+        int body, t0, s0, tc, sc;
+        cb_task(A, task, body, t0, s0, tc, sc);
+        if (!A.flag[body]) continue;   // block-uniform
+        const int alpha = t0 + tid;
+        const bool tin = tid < tc;
+        const float4 ah = tin ? A.hi[alpha] : make_float4(0.f, 0.f, 0.f, 0.f);
+        const float4 al = tin ? A.lo[alpha] : make_float4(0.f, 0.f, 0.f, 0.f);
+        df acc[NR];
+#pragma unroll
+        for (int r = 0; r < NR; ++r) acc[r] = {0.0f, 0.0f};
+        bool ov = false;
+        for (int u = 0; u < sc; u += kCbThreads) {
+            const int m = min(kCbThreads, sc - u);
+            __syncthreads();
+            if (tid < m) {
+                const int b = s0 + u + tid;
+                sh[tid] = A.hi[b];
+                sl[tid] = A.lo[b];
+#pragma unroll
+                for (int r = 0; r < NR; ++r) {
+                    const df v = df_from_double(q[(size_t)r * n + b]);
+                    sq[r][tid] = make_float2(v.hi, v.lo);
+                }
+            }
+            __syncthreads();
+            if (!tin) continue;
+            const int self = alpha - (s0 + u);
+#pragma unroll 2
+            for (int j = 0; j < m; ++j) {
+                const float4 bh = sh[j];
+                const float fx = ah.x - bh.x, fy = ah.y - bh.y, fz = ah.z - bh.z;
+                const float r2f = fmaf(fx, fx, fmaf(fy, fy, fz * fz));   // the same test as the inner operator
+                const bool near = r2f < A.a2x4f;
+                ov |= near && j != self;
+                if (near) continue;
+                const float4 bl = sl[j];
+                const df dx = cb_diff(ah.x, al.x, bh.x, bl.x);
+                const df dy = cb_diff(ah.y, al.y, bh.y, bl.y);
+                const df dz = cb_diff(ah.z, al.z, bh.z, bl.z);
+                const df r2 = df_add(df_add(df_sqr(dx), df_sqr(dy)), df_sqr(dz));
+                if (!(r2.hi < A.rc2.hi || (r2.hi == A.rc2.hi && r2.lo < A.rc2.lo))) continue;
+                df s;
+                const int i = cb_interval(df_mul(r2, A.inv4a2), A.K, s);
+                const float4 a = cb_tab[2 * i], b = cb_tab[2 * i + 1];
+                const df phi = cb_poly(a, b.x, b.y, s);
+#pragma unroll
+                for (int r = 0; r < NR; ++r) {
+                    const float2 qb = sq[r][j];
+                    acc[r] = df_add(acc[r], df_mul(phi, {qb.x, qb.y}));
+                }
+            }
+        }
+        if (tin) {
+            double out[NR];
+#pragma unroll
+            for (int r = 0; r < NR; ++r) out[r] = df_to_double(acc[r]);
+            if (ov) cb_overlaps<NR, false, true>(A, n, alpha, s0, sc, q, out);
+#pragma unroll
+            for (int r = 0; r < NR; ++r) atomicAdd(psi + (size_t)r * n + alpha, out[r] * inv_eps);
+        }
+    }
+}
+
+// Field: E_r[r][alpha] += sum G(r) (x_alpha - x_beta) q_beta / eps, G = -phi'/r, double-float.
+template <int NR>
+__global__ void __launch_bounds__(kCbThreads)
+compact_field_kernel(CbArgs A, int n, const double* __restrict__ q, double inv_eps, double* __restrict__ E) {
+    extern __shared__ float4 cb_tab[];
+    __shared__ float4 sh[kCbThreads], sl[kCbThreads];
+    __shared__ float2 sq[NR][kCbThreads];
+    for (int i = threadIdx.x; i < A.nt; i += blockDim.x) {
+        cb_tab[2 * i] = A.tabdf[3 * i + 1];
+        cb_tab[2 * i + 1] = A.tabdf[3 * i + 2];
+    }
+    __syncthreads();
+    const int tid = threadIdx.x;
+    for (int task = blockIdx.x; task < A.ntasks; task += gridDim.x) {
+        int body, t0, s0, tc, sc;
+        cb_task(A, task, body, t0, s0, tc, sc);
+        if (!A.flag[body]) continue;   // block-uniform
+        const int alpha = t0 + tid;
+        const bool tin = tid < tc;
+        const float4 ah = tin ? A.hi[alpha] : make_float4(0.f, 0.f, 0.f, 0.f);
+        const float4 al = tin ? A.lo[alpha] : make_float4(0.f, 0.f, 0.f, 0.f);
+        df ex[NR], ey[NR], ez[NR];
+#pragma unroll
+        for (int r = 0; r < NR; ++r) ex[r] = ey[r] = ez[r] = {0.0f, 0.0f};
+        bool ov = false;
+        for (int u = 0; u < sc; u += kCbThreads) {
+            const int m = min(kCbThreads, sc - u);
+            __syncthreads();
+            if (tid < m) {
+                const int b = s0 + u + tid;
+                sh[tid] = A.hi[b];
+                sl[tid] = A.lo[b];
+#pragma unroll
+                for (int r = 0; r < NR; ++r) {
+                    const df v = df_from_double(q[(size_t)r * n + b]);
+                    sq[r][tid] = make_float2(v.hi, v.lo);
+                }
+            }
+            __syncthreads();
+            if (!tin) continue;
+            const int self = alpha - (s0 + u);
+            for (int j = 0; j < m; ++j) {
+                const float4 bh = sh[j];
+                const float fx = ah.x - bh.x, fy = ah.y - bh.y, fz = ah.z - bh.z;
+                const float r2f = fmaf(fx, fx, fmaf(fy, fy, fz * fz));
+                const bool near = r2f < A.a2x4f;
+                ov |= near && j != self;
+                if (near) continue;
+                const float4 bl = sl[j];
+                const df dx = cb_diff(ah.x, al.x, bh.x, bl.x);
+                const df dy = cb_diff(ah.y, al.y, bh.y, bl.y);
+                const df dz = cb_diff(ah.z, al.z, bh.z, bl.z);
+                const df r2 = df_add(df_add(df_sqr(dx), df_sqr(dy)), df_sqr(dz));
+                if (!(r2.hi < A.rc2.hi || (r2.hi == A.rc2.hi && r2.lo < A.rc2.lo))) continue;
+                df s;
+                const int i = cb_interval(df_mul(r2, A.inv4a2), A.K, s);
+                const float4 b4 = cb_tab[2 * i], c4 = cb_tab[2 * i + 1];
+                const df g = cb_poly(make_float4(b4.z, b4.w, c4.x, c4.y), c4.z, c4.w, s);
+#pragma unroll
+                for (int c = 0; c < NR; ++c) {
+                    const float2 qb = sq[c][j];
+                    const df gq = df_mul(g, {qb.x, qb.y});
+                    ex[c] = df_add(ex[c], df_mul(gq, dx));
+                    ey[c] = df_add(ey[c], df_mul(gq, dy));
+                    ez[c] = df_add(ez[c], df_mul(gq, dz));
+                }
+            }
+        }
+        if (tin) {
+            double o[3 * NR];
+#pragma unroll
+            for (int c = 0; c < NR; ++c) {
+                o[3 * c + 0] = df_to_double(ex[c]);
+                o[3 * c + 1] = df_to_double(ey[c]);
+                o[3 * c + 2] = df_to_double(ez[c]);
+            }
+            if (ov) cb_overlaps<NR, true, true>(A, n, alpha, s0, sc, q, o);
+#pragma unroll
+            for (int c = 0; c < NR; ++c) {
+                double* e = E + ((size_t)c * n + alpha) * 3;
+                atomicAdd(e + 0, o[3 * c + 0] * inv_eps);
+                atomicAdd(e + 1, o[3 * c + 1] * inv_eps);
+                atomicAdd(e + 2, o[3 * c + 2] * inv_eps);
+            }
+        }
+    }
+}
+
+// One warp per body: centre (mean of the minimum-image offsets from the first
+// bead), radius, the compact flag, and the positions relative to the centre as
+// hi + lo floats.
+__global__ void compact_bodies_kernel(int nb, const int* __restrict__ off, const double* __restrict__ xw, double L0,
+                                      double L1, double L2, double lim2, int* __restrict__ flag,
+                                      float4* __restrict__ hi, float4* __restrict__ lo) {
+    const int b = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (b >= nb) return;
+    const int o = off[b], m = off[b + 1] - o;
+    if (m < kCompactMin) {
+        if (lane == 0) flag[b] = 0;
+        return;
+    }
+    const double x0 = xw[3 * o], y0 = xw[3 * o + 1], z0 = xw[3 * o + 2];
+    double sx = 0.0, sy = 0.0, sz = 0.0;
+    for (int j = lane; j < m; j += 32) {
+        sx += min_image(xw[3 * (o + j)] - x0, L0);
+        sy += min_image(xw[3 * (o + j) + 1] - y0, L1);
+        sz += min_image(xw[3 * (o + j) + 2] - z0, L2);
+    }
+    const double cx = warp_sum(sx) / m, cy = warp_sum(sy) / m, cz = warp_sum(sz) / m;
+    double r2max = 0.0;
+    for (int j = lane; j < m; j += 32) {
+        const double dx = min_image(xw[3 * (o + j)] - x0, L0) - cx;
+        const double dy = min_image(xw[3 * (o + j) + 1] - y0, L1) - cy;
+        const double dz = min_image(xw[3 * (o + j) + 2] - z0, L2) - cz;
+        r2max = fmax(r2max, dx * dx + dy * dy + dz * dz);
+    }
+#pragma unroll
+    for (int s = 16; s > 0; s >>= 1) r2max = fmax(r2max, __shfl_xor_sync(0xffffffffu, r2max, s));
+    const int f = r2max <= lim2 ? 1 : 0;
+    if (lane == 0) flag[b] = f;
+    if (!f) return;
+    for (int j = lane; j < m; j += 32) {
+        const double dx = min_image(xw[3 * (o + j)] - x0, L0) - cx;
+        const double dy = min_image(xw[3 * (o + j) + 1] - y0, L1) - cy;
+        const double dz = min_image(xw[3 * (o + j) + 2] - z0, L2) - cz;
+        const float hx = (float)dx, hy = (float)dy, hz = (float)dz;
+        hi[o + j] = make_float4(hx, hy, hz, 0.0f);
+        lo[o + j] = make_float4((float)(dx - (double)hx), (float)(dy - (double)hy), (float)(dz - (double)hz), 0.0f);
+    }
+}
+
+// Cubic coefficients per interval j from the FP64 nodes (value and u-derivative of
+// phi and of G): on [node j, node j+1] with s in [0, 1] and width h = 2^e / M,
+//   phi = p0 + c1 s + c2 s^2 + c3 s^3,  c1 = h p'_0,  c2 = 3 (p1 - p0) - h (2 p'_0 + p'_1),
+//   c3 = h (p'_0 + p'_1) - 2 (p1 - p0)   (the cubic Hermite interpolant), and the same for G.
+__global__ void compact_table_kernel(int nt, const double* __restrict__ table, float4* __restrict__ tab32,
+                                     float4* __restrict__ tabdf) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= nt) return;
+    const double h = ldexp(1.0, j / kOctaveIntervals) / kOctaveIntervals;
+    const double* a = table + 4 * j;
+    const double p0 = a[0], d0 = a[1], g0 = a[2], e0 = a[3];
+    const double p1 = a[4], d1 = a[5], g1 = a[6], e1 = a[7];
+    const double c1 = h * d0, c2 = 3.0 * (p1 - p0) - h * (2.0 * d0 + d1), c3 = h * (d0 + d1) - 2.0 * (p1 - p0);
+    const double f1 = h * e0, f2 = 3.0 * (g1 - g0) - h * (2.0 * e0 + e1), f3 = h * (e0 + e1) - 2.0 * (g1 - g0);
+    tab32[j] = make_float4((float)p0, (float)c1, (float)c2, (float)c3);
+    const float ph = (float)p0, ch = (float)c1, gh = (float)g0, fh = (float)f1;
+    tabdf[3 * j] = make_float4(ph, (float)(p0 - (double)ph), ch, (float)(c1 - (double)ch));
+    tabdf[3 * j + 1] = make_float4((float)c2, (float)c3, gh, (float)(g0 - (double)gh));
+    tabdf[3 * j + 2] = make_float4(fh, (float)(f1 - (double)fh), (float)f2, (float)f3);
+}
+
 // ---- exclusive scan of int counts into 64-bit offsets (three passes) ----
 constexpr int kScanThreads = 1024;
 constexpr int kScanItems = 4;
@@ -521,6 +990,45 @@ void scan_counts(const int* in, long long* out, int n, DevBuf& tmp, cudaStream_t
 
 namespace {
 
+constexpr size_t kCbSmemMax = 2 * sizeof(float4) * kOctaveIntervals * kMaxOctaves;   // two float4 per interval
+
+template <typename K>
+void cb_attr(K kernel) {
+    IBP_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kCbSmemMax));
+}
+
+template <int NR>
+void cb_attrs_nr() {
+    cb_attr(compact_apply64_kernel<NR>);
+    cb_attr(compact_field_kernel<NR>);
+}
+
+// Opt-in to the shared-memory tables of the compact kernels, once per device
+// (called at set-up, outside any stream capture).
+void compact_attrs() {
+    constexpr int kMaxDev = 64;
+    static bool done[kMaxDev] = {};
+    static std::mutex mu;
+    int dev = 0;
+    IBP_CUDA(cudaGetDevice(&dev));
+    std::lock_guard<std::mutex> lock(mu);
+    if (dev < 0 || dev >= kMaxDev) fail(IBPME_ERR_CUDA, "device ordinal %d out of range", dev);
+    if (done[dev]) return;
+    cb_attr(compact_apply32_kernel<1>);
+    cb_attr(compact_apply32_kernel<2>);
+    cb_attr(compact_apply32_kernel<3>);
+    cb_attr(compact_apply32_kernel<4>);
+    cb_attrs_nr<1>();
+    cb_attrs_nr<2>();
+    cb_attrs_nr<3>();
+    cb_attrs_nr<4>();
+    cb_attrs_nr<5>();
+    cb_attrs_nr<6>();
+    cb_attrs_nr<7>();
+    cb_attrs_nr<8>();
+    done[dev] = true;
+}
+
 PairConst make_const(const ibpme_ctx* c) {
     PairConst k{};
     k.a = c->a;
@@ -538,10 +1046,13 @@ PairConst make_const(const ibpme_ctx* c) {
     k.self = (1.0 - exp(-4.0 * c->a * c->a * c->xi * c->xi)) / (8.0 * pow(kPi, 1.5) * c->a * c->a * c->xi) +
              erfc(2.0 * c->a * c->xi) / (4.0 * kPi * c->a);
     k.table = c->near.table.as<double>();
-    k.nt = kTableIntervals;
-    k.t0 = 2.0 * c->a;
-    k.h = (c->rc > k.t0 ? c->rc - k.t0 : 0.0) / kTableIntervals;
-    k.inv_h = k.h > 0.0 ? 1.0 / k.h : 0.0;
+    k.inv4a2 = 1.0 / (4.0 * c->a * c->a);
+    {
+        const double uc = c->rc * c->rc * k.inv4a2;   // u at the cut-off
+        k.K = 0;
+        while (k.K < kMaxOctaves && ldexp(1.0, k.K) < uc) ++k.K;
+        if (uc <= 1.0) k.K = 0;                        // r_c <= 2a: no tabulated range
+    }
     for (int d = 0; d < 3; ++d) {
         k.L[d] = c->p.box[d];
         k.nc[d] = c->near.nc[d];
@@ -558,14 +1069,154 @@ double self_term(const ibpme_ctx* c) { return make_const(c).self; }
 
 void near_setup(ibpme_ctx* c) {
     NearList& nl = c->near;
-    nl.table.ensure(sizeof(double) * 3 * (kTableIntervals + 1));
+    nl.table.ensure(sizeof(double) * 4 * (kMaxOctaves * kOctaveIntervals + 1));
     const PairConst k = make_const(c);
-    if (k.h > 0.0) {
-        table_kernel<<<div_up(kTableIntervals + 1, 128), 128, 0, c->stream>>>(k, nl.table.as<double>());
+    if (k.K > 0) {
+        const int nodes = k.K * kOctaveIntervals + 1;
+        table_kernel<<<div_up(nodes, 128), 128, 0, c->stream>>>(k, nl.table.as<double>());
+        IBP_CHECK_LAUNCH();
+        const int nt = k.K * kOctaveIntervals;
+        float4* t32 = static_cast<float4*>(nl.tab32.ensure(sizeof(float4) * nt));
+        float4* tdf = static_cast<float4*>(nl.tab_df.ensure(sizeof(float4) * 3 * nt));
+        compact_table_kernel<<<div_up(nt, 128), 128, 0, c->stream>>>(nt, nl.table.as<double>(), t32, tdf);
         IBP_CHECK_LAUNCH();
     }
+    compact_attrs();
     nl.fp_valid = false;
 }
+
+namespace {
+
+df host_df(double v) {
+    const float h = (float)v;
+    return {h, (float)(v - (double)h)};
+}
+
+CbArgs cb_args(const ibpme_ctx* c) {
+    const NearList& nl = c->near;
+    const PairConst k = make_const(c);
+    CbArgs A{};
+    A.flag = nl.cb_flag.as<int>();
+    A.tasks = nl.cb_tasks.as<int4>();
+    A.ntasks = nl.cb_ntasks;
+    A.hi = nl.cb_hi.as<float4>();
+    A.lo = nl.cb_lo.as<float4>();
+    A.tab32 = nl.tab32.as<float4>();
+    A.tabdf = nl.tab_df.as<float4>();
+    A.K = k.K;
+    A.nt = k.K * kOctaveIntervals;
+    A.rc2f = (float)k.rc2;
+    A.a2x4f = (float)(4.0 * k.a * k.a);
+    A.inv4a2f = (float)k.inv4a2;
+    A.rc2 = host_df(k.rc2);
+    A.inv4a2 = host_df(k.inv4a2);
+    A.k = k;
+    return A;
+}
+
+// Compact flags and relative positions of this set of positions, and the
+// block tasks of the body structure: (body, 128 targets, a range of sources).
+// Sources are split into ranges while the blocks would not give every SM
+// several of them.
+void compact_prepare(ibpme_ctx* c, int n, const double* xw) {
+    NearList& nl = c->near;
+    const BodyData& bd = c->bodies;
+    cudaStream_t s = c->stream;
+    const int nb = bd.nb;
+    int* flag = static_cast<int*>(nl.cb_flag.ensure(sizeof(int) * (nb + 1)));
+    float4* hi = static_cast<float4*>(nl.cb_hi.ensure(sizeof(float4) * (n + 1)));
+    float4* lo = static_cast<float4*>(nl.cb_lo.ensure(sizeof(float4) * (n + 1)));
+    const double* L = c->p.box;
+    const double lim = fmin(c->rc, 0.25 * fmin(L[0], fmin(L[1], L[2])));
+    compact_bodies_kernel<<<div_up((long long)nb * 32, 128), 128, 0, s>>>(nb, bd.off.as<int>(), xw, L[0], L[1], L[2],
+                                                                           lim * lim, flag, hi, lo);
+    IBP_CHECK_LAUNCH();
+    if (nl.cb_tasks_key == bd.version) return;
+    const std::vector<int>& off = bd.host_off;
+    auto blocks = [&](int S) {
+        long long t = 0;
+        for (int b = 0; b < nb; ++b) {
+            const int m = off[b + 1] - off[b];
+            if (m >= kCompactMin) t += (long long)div_up(m, kCbThreads) * div_up(m, S);
+        }
+        return t;
+    };
+    int S = 8;
+    for (int cand : {1024, 512, 256, 128, 64, 32, 16}) {
+        if (blocks(cand) >= 152LL * 8) {
+            S = cand;
+            break;
+        }
+    }
+    std::vector<int4> tasks;
+    for (int b = 0; b < nb; ++b) {
+        const int o = off[b], m = off[b + 1] - off[b];
+        if (m < kCompactMin) continue;
+        for (int t = 0; t < m; t += kCbThreads)
+            for (int u = 0; u < m; u += S)
+                tasks.push_back(make_int4(b, o + t, o + u, (std::min(kCbThreads, m - t) << 20) | std::min(S, m - u)));
+    }
+    nl.cb_ntasks = (int)tasks.size();
+    if (!tasks.empty()) {
+        nl.cb_tasks.ensure(sizeof(int4) * tasks.size());
+        IBP_CUDA(cudaMemcpyAsync(nl.cb_tasks.p, tasks.data(), sizeof(int4) * tasks.size(), cudaMemcpyHostToDevice, s));
+        IBP_CUDA(cudaStreamSynchronize(s));   // the host vector goes out of scope
+    }
+    nl.cb_tasks_key = bd.version;
+}
+
+int cb_grid(int ntasks) { return ntasks < 152 * kCbBlocksPerSm ? ntasks : 152 * kCbBlocksPerSm; }
+
+template <bool FP32>
+void compact_apply(ibpme_ctx* c, int n, const double* q, int nrhs, double* psi_r) {
+    const CbArgs A = cb_args(c);
+    const int g = cb_grid(A.ntasks);
+    const double ie = 1.0 / c->eps;
+    cudaStream_t s = c->stream;
+    if (FP32) {
+        const size_t sm = sizeof(float4) * A.nt;
+        switch (nrhs) {
+            case 1: compact_apply32_kernel<1><<<g, kCbThreads, sm, s>>>(A, n, q, ie, psi_r); break;
+            case 2: compact_apply32_kernel<2><<<g, kCbThreads, sm, s>>>(A, n, q, ie, psi_r); break;
+            case 3: compact_apply32_kernel<3><<<g, kCbThreads, sm, s>>>(A, n, q, ie, psi_r); break;
+            default: compact_apply32_kernel<4><<<g, kCbThreads, sm, s>>>(A, n, q, ie, psi_r); break;
+        }
+    } else {
+        const size_t sm = 2 * sizeof(float4) * A.nt;
+        switch (nrhs) {
+            case 1: compact_apply64_kernel<1><<<g, kCbThreads, sm, s>>>(A, n, q, ie, psi_r); break;
+            case 2: compact_apply64_kernel<2><<<g, kCbThreads, sm, s>>>(A, n, q, ie, psi_r); break;
+            case 3: compact_apply64_kernel<3><<<g, kCbThreads, sm, s>>>(A, n, q, ie, psi_r); break;
+            case 4: compact_apply64_kernel<4><<<g, kCbThreads, sm, s>>>(A, n, q, ie, psi_r); break;
+            case 5: compact_apply64_kernel<5><<<g, kCbThreads, sm, s>>>(A, n, q, ie, psi_r); break;
+            case 6: compact_apply64_kernel<6><<<g, kCbThreads, sm, s>>>(A, n, q, ie, psi_r); break;
+            case 7: compact_apply64_kernel<7><<<g, kCbThreads, sm, s>>>(A, n, q, ie, psi_r); break;
+            default: compact_apply64_kernel<8><<<g, kCbThreads, sm, s>>>(A, n, q, ie, psi_r); break;
+        }
+    }
+    IBP_CHECK_LAUNCH();
+}
+
+void compact_field(ibpme_ctx* c, int n, const double* q, int nrhs, double* E_r) {
+    const CbArgs A = cb_args(c);
+    const int g = cb_grid(A.ntasks);
+    const double ie = 1.0 / c->eps;
+    const size_t sm = 2 * sizeof(float4) * A.nt;
+    cudaStream_t s = c->stream;
+    switch (nrhs) {
+        case 1: compact_field_kernel<1><<<g, kCbThreads, sm, s>>>(A, n, q, ie, E_r); break;
+        case 2: compact_field_kernel<2><<<g, kCbThreads, sm, s>>>(A, n, q, ie, E_r); break;
+        case 3: compact_field_kernel<3><<<g, kCbThreads, sm, s>>>(A, n, q, ie, E_r); break;
+        case 4: compact_field_kernel<4><<<g, kCbThreads, sm, s>>>(A, n, q, ie, E_r); break;
+        case 5: compact_field_kernel<5><<<g, kCbThreads, sm, s>>>(A, n, q, ie, E_r); break;
+        case 6: compact_field_kernel<6><<<g, kCbThreads, sm, s>>>(A, n, q, ie, E_r); break;
+        case 7: compact_field_kernel<7><<<g, kCbThreads, sm, s>>>(A, n, q, ie, E_r); break;
+        default: compact_field_kernel<8><<<g, kCbThreads, sm, s>>>(A, n, q, ie, E_r); break;
+    }
+    IBP_CHECK_LAUNCH();
+}
+
+}  // namespace
 
 void near_build(ibpme_ctx* c, int n, const double* xw, bool need_grad) {
     (void)need_grad;   // the table always carries the gradient factors
@@ -586,8 +1237,15 @@ void near_build(ibpme_ctx* c, int n, const double* xw, bool need_grad) {
     IBP_CUDA(cudaStreamSynchronize(s));
     if (*reinterpret_cast<int*>(hfp + 1) != 0) fail(IBPME_ERR_NONFINITE, "non-finite bead position");
     const unsigned long long print = hfp[0];
-    if (nl.fp_valid && nl.n == n && nl.fp == print && nl.ncfg == c->ncfg) return;
+    // compact bodies whenever the call has bodies (their structure is part of the cache key)
+    const BodyData& bd = c->bodies;
+    const bool want_cb = c->bodies_current && bd.nmb > 0 && bd.host_n == n && make_const(c).K > 0 &&
+                         std::getenv("IBPME_NO_COMPACT") == nullptr;   // the switch lets tests compare both paths
+    const unsigned long long cb_key = want_cb ? bd.version : 0;
+    if (nl.fp_valid && nl.n == n && nl.fp == print && nl.ncfg == c->ncfg && nl.cb_key == cb_key) return;
     nl.fp_valid = false;
+    nl.cb_on = false;
+    nl.cb_key = cb_key;
     nl.n = n;
     nl.rc = c->rc;
     int ncells = 1;
@@ -601,7 +1259,13 @@ void near_build(ibpme_ctx* c, int n, const double* xw, bool need_grad) {
     }
     nl.ncfg = c->ncfg;
     ncells *= c->ncfg;   // every configuration has its own cells
-    const PairConst k = make_const(c);
+    PairConst k = make_const(c);
+    if (want_cb && n > 0) {
+        compact_prepare(c, n, xw);
+        k.bbody = bd.bead_body.as<int>();
+        k.cflag = nl.cb_flag.as<int>();
+        nl.cb_on = true;
+    }
     int* cell_of = static_cast<int*>(nl.cell_of.ensure(sizeof(int) * (n + 1)));
     int* cell_count = static_cast<int*>(nl.cell_count.ensure(sizeof(int) * (ncells + 1)));
     long long* cell_start64 = static_cast<long long*>(nl.cell_start64.ensure(sizeof(long long) * (ncells + 1)));
@@ -679,6 +1343,7 @@ void near_apply(ibpme_ctx* c, int n, const double* q, int nrhs, double* psi_r, b
             default: near_apply32_kernel<4><<<blocks, 128, 0, s>>>(n, rp, pc, od, k.self, ie, qf, q, psi_r); break;
         }
         IBP_CHECK_LAUNCH();
+        if (nl.cb_on && nl.cb_ntasks > 0) compact_apply<true>(c, n, q, nrhs, psi_r);
         return;
     }
     double* qs = static_cast<double*>(nl.qs.ensure(sizeof(double) * (size_t)n * nrhs));
@@ -695,6 +1360,7 @@ void near_apply(ibpme_ctx* c, int n, const double* q, int nrhs, double* psi_r, b
         default: near_apply_kernel<8><<<blocks, 128, 0, s>>>(n, rp, cl, vl, od, k.self, ie, qs, q, psi_r); break;
     }
     IBP_CHECK_LAUNCH();
+    if (nl.cb_on && nl.cb_ntasks > 0) compact_apply<false>(c, n, q, nrhs, psi_r);
 }
 
 void near_field(ibpme_ctx* c, int n, const double* xw, const double* q, int nrhs, double* E_r) {
@@ -707,6 +1373,7 @@ void near_field(ibpme_ctx* c, int n, const double* xw, const double* q, int nrhs
         n, nrhs, xw, k, nl.rowptr.as<long long>(), nl.col.as<int>(), nl.cell_beads.as<int>(), nl.gfac.as<double>(),
         1.0 / c->eps, q, E_r);
     IBP_CHECK_LAUNCH();
+    if (nl.cb_on && nl.cb_ntasks > 0) compact_field(c, n, q, nrhs, E_r);
 }
 
 }  // namespace ibp

@@ -259,6 +259,60 @@ def _check_solution(s, q, psi, S, bar, M=None):
     return qr, psr, Sr
 
 
+@pytest.mark.parametrize("a", [0.12, 0.2])
+def test_compact_bodies_match_the_table_path(cuda_lib, a, monkeypatch):
+    """Intra-body pairs of compact bodies evaluated directly (FP32 for the inner
+    operator, double-float for the FP64 operator and the field) against the same
+    calls with every pair in the table: solves in both precisions, bead forces,
+    body forces, torques and energy.  With a = 0.2 neighbouring beads of a body
+    overlap (r < 2a), which takes the exact kernel."""
+    import torch
+    ib = cuda_lib
+    s = C.small_system(seed=61, n_bodies=3, level=2, n_ions=40, L=9.0, a=a, mesh=(48, 48, 48), tol=1e-7, nrhs=2)
+    out = {}
+    q_common = None
+    for compact in (False, True):
+        if compact:
+            monkeypatch.delenv("IBPME_NO_COMPACT", raising=False)
+        else:
+            monkeypatch.setenv("IBPME_NO_COMPACT", "1")
+        for prec in ("fp64", "mixed"):
+            ctx = context(ib, s, precision=prec)
+            try:
+                bodies = ib.Bodies(cuda(s.body_offsets.astype(np.int32)), cuda(s.X), cuda(s.Q))
+                q = torch.zeros((2, s.n), dtype=torch.float64, device="cuda")
+                psi = torch.zeros((2, s.n_bodies), dtype=torch.float64, device="cuda")
+                S = torch.zeros((2, s.n_bodies, 3), dtype=torch.float64, device="cuda")
+                status, st = ib.induced_charge_solve(ctx, s.n, cuda(s.x), bodies, cuda(s.E0), 2,
+                                                     ib.make_opts(rtol=1e-10), q, psi, S)
+                torch.cuda.synchronize()
+                assert status == ib.IBPME_OK and st.rel_residual <= 1e-10
+                if q_common is None:
+                    q_common = q[0:1].clone()
+                f = torch.zeros((s.n, 3), dtype=torch.float64, device="cuda")
+                F = torch.zeros((s.n_bodies, 3), dtype=torch.float64, device="cuda")
+                L = torch.zeros((s.n_bodies, 3), dtype=torch.float64, device="cuda")
+                U = torch.zeros(1, dtype=torch.float64, device="cuda")
+                ib.body_force_torque(ctx, s.n, cuda(s.x), q_common, bodies, cuda(s.E0[:1]), f, F, L, U)
+                torch.cuda.synchronize()
+                out[compact, prec] = [t.cpu().numpy() for t in (q, psi, S, f, F, L, U)]
+            finally:
+                ib.pme_destroy(ctx)
+    monkeypatch.delenv("IBPME_NO_COMPACT", raising=False)
+    for prec in ("fp64", "mixed"):
+        t, d = out[True, prec], out[False, prec]
+        # forces only from the FP64 context: the mixed context's force pass runs its mesh
+        # in FP32, whose atomic sums vary from run to run near 1e-7
+        checks = (("q", 0, 1e-8), ("S", 2, 1e-8))
+        if prec == "fp64":
+            checks += (("f", 3, 1e-9), ("F", 4, 1e-9), ("L", 5, 1e-9), ("U", 6, 1e-10))
+        for name, i, bar in checks:
+            assert rel_err(t[i], d[i]) < bar, (prec, name, rel_err(t[i], d[i]))
+        assert np.abs(t[1] - d[1]).max() < 1e-8 * max(np.abs(d[1]).max(), 1.0), (prec, "psi")
+    q, psi, S = out[True, "fp64"][:3]
+    _check_solution(s, q, psi, S, FP64_RTOL)
+
+
 def test_solve_single_sphere_fp64(cuda_lib):
     ib = cuda_lib
     s = C.config1()
