@@ -463,7 +463,7 @@ def bench_polarizability(args, ib, torch, rank, world, local):
     a, eps, tol = systems[0].a, systems[0].eps, 1e-6
     tuner = B.Autotuner(cache_path=os.path.join(_tf.mkdtemp(), "tune.json"), candidates=(96, 128, 160))
     plan = []
-    for idx in B.buckets([s.n for s in systems], ratio=1e9, max_channels=192, nrhs=3,
+    for idx in B.buckets([s.n for s in systems], ratio=args.bucket_ratio, max_channels=192, nrhs=3,
                          classes=[B.preconditioned(s) for s in systems]):
         bucket = B.Bucket(ib, [systems[i] for i in idx], np.eye(3))
         mesh, report = tuner.tune(ib, bucket, tol, a, eps, ib.IBPME_MIXED)
@@ -545,7 +545,8 @@ def bench_polarizability(args, ib, torch, rank, world, local):
                    f"{args.configs}-configuration prefix of: {POL_WORKLOAD}", "n_configs": args.configs,
                    "n_beads": n_beads,
                    "l2": "inputs larger than L2; 256 MB flush before every step, outside its events",
-                   "parallelism": f"replicas x{world} (independent batches, no collective)"},
+                   "parallelism": f"replicas x{world} (independent batches, no collective)",
+                   "bucket_ratio": args.bucket_ratio},
         "buckets": [{"configs": len(p["idx"]), "beads": p["bucket"].n, "mesh": p["mesh"],
                      "preconditioned": bool(B.preconditioned(systems[p["idx"][0]])),
                      "iters": stats[-1][k][0].iters, "autotune": p["report"]} for k, p in enumerate(plan)],
@@ -722,6 +723,8 @@ def main():
     ap.add_argument("--workload", default="charged-sphere", choices=["charged-sphere", "polarizability", "trajectory"],
                     help="the headline charged-sphere step, the batched polarizability solve, or a BD "
                          "trajectory comparing initial guesses")
+    ap.add_argument("--bucket-ratio", type=float, default=1.6,
+                    help="polarizability: largest / smallest bead count within one batched call")
     ap.add_argument("--configs", type=int, default=64,
                     help="configurations in the polarizability batch (64 = the full workload)")
     args = ap.parse_args()

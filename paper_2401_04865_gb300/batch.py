@@ -210,7 +210,8 @@ class Autotuner:
             (ta, ia), (tb, ib_) = runs
             setup = max(0.0, t_first - ta)
             if ib_ > ia:
-                per_iter = max(0.0, (tb - ta) / (ib_ - ia))
+                # timing noise can make the longer probe no slower: then its own time per iteration
+                per_iter = (tb - ta) / (ib_ - ia) if tb > ta else tb / ib_
                 predicted = setup + ta + max(0, self.expected_iters - ia) * per_iter
             else:   # converged within the shorter probe: that run is the whole solve
                 per_iter = ta / max(1, ia)
@@ -240,7 +241,7 @@ class Autotuner:
 # ---------------------------------------------------------------- driver
 
 def polarizability(ib, systems, precision=None, rtol=1e-6, tol=1e-6, tuner: Autotuner | None = None,
-                   mesh: int | None = None, ratio=2.0, max_channels=192):
+                   mesh: int | None = None, ratio=1.6, max_channels=192):
     """Polarizability tensors of every body of every configuration.
 
     systems: configurations sharing box, bead radius and permittivity (their E0

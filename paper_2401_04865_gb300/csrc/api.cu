@@ -270,17 +270,29 @@ void wrap_positions(ibpme_ctx* c, int n, const double* x, double* xw) {
     IBP_CHECK_LAUNCH();
 }
 
+void pme_reserve(ibpme_ctx* c, int n, int nrhs, bool field) {
+    const size_t m = (size_t)nrhs * n;
+    c->psi_r.ensure(sizeof(double) * (m ? m : 1));
+    c->psi_k.ensure(sizeof(double) * (m ? m : 1));
+    if (field) {
+        c->E_r.ensure(sizeof(double) * 3 * (m ? m : 1));
+        c->E_k.ensure(sizeof(double) * 3 * (m ? m : 1));
+    }
+    c->scalars.ensure(sizeof(double) * (size_t)(nrhs * c->ncfg));
+}
+
 void pme_apply(ibpme_ctx* c, int n, const double* xw, const double* q, int nrhs, int prec, double* psi,
                double* E, bool near_ready, bool near32) {
     if (!near_ready) near_build(c, n, xw, E != nullptr);
     const size_t m = (size_t)nrhs * n;
-    double* pr = static_cast<double*>(c->psi_r.ensure(sizeof(double) * (m ? m : 1)));
-    double* pk = static_cast<double*>(c->psi_k.ensure(sizeof(double) * (m ? m : 1)));
+    pme_reserve(c, n, nrhs, E != nullptr);
+    double* pr = c->psi_r.as<double>();
+    double* pk = c->psi_k.as<double>();
     double* er = nullptr;
     double* ek = nullptr;
     if (E) {
-        er = static_cast<double*>(c->E_r.ensure(sizeof(double) * 3 * (m ? m : 1)));
-        ek = static_cast<double*>(c->E_k.ensure(sizeof(double) * 3 * (m ? m : 1)));
+        er = c->E_r.as<double>();
+        ek = c->E_k.as<double>();
     }
     // The real-space pass and the mesh pass are independent until they are
     // combined: the near field runs on the context's second stream, forked from

@@ -368,6 +368,8 @@ MeshGeom make_geom(const ibpme_params& p);
 void wrap_positions(ibpme_ctx* c, int n, const double* x, double* xw);
 // psi = M q (real + self + wave) in the given precision; E optional
 // near32: real-space pass in FP32 too (only the inner operator of a mixed solve)
+// every buffer pme_apply needs for n beads and nrhs fields (before a stream capture)
+void pme_reserve(ibpme_ctx* c, int n, int nrhs, bool field);
 void pme_apply(ibpme_ctx* c, int n, const double* xw, const double* q, int nrhs, int prec,
                double* psi, double* E, bool near_ready, bool near32 = false);
 void* pinned_host(ibpme_ctx* c, size_t bytes);

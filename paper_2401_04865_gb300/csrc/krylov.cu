@@ -716,6 +716,7 @@ struct Solver {
         // and build the stencil cache of these positions)
         if (prec == IBPME_MIXED) c->mesh32.plans(R * ncfg, s()); else c->mesh64.plans(R * ncfg, s());
         stencil_cache(c, n, a.xw);
+        pme_reserve(c, n, R, false);
         auto P = [](const void* p) { return (long long)(size_t)p; };
         std::vector<long long> sig = {prec, R, S, ncfg, nk, n, m, nfree, nmb, (long long)prof_mask(),
                                       P(k->V.p), P(k->w.p), P(k->qop.p), P(k->psi.p), P(k->H.p), P(k->scal.p),
@@ -804,13 +805,19 @@ struct Solver {
     // Leaves r, and psi_tot = M q_total for the ions' potentials.  Returns |r| per system.
     // With fit_psi the body potentials of x are first replaced by their
     // least-squares fit to the charges (initial guess).
-    std::vector<double> residual(int prec, bool fit_psi = false) {
+    // zero_charges: every bead charge of the current x is zero (x = 0 without ions), so
+    // the potentials are exactly zero and no evaluation is needed
+    std::vector<double> residual(int prec, bool fit_psi = false, bool zero_charges = false) {
         const BodyData& bd = c->bodies;
-        compose_kernel<<<blocks_for((long long)n * R), 256, 0, s()>>>(n, nk, R, I(bd.bead_unk), I(bd.bead_body),
-                                                                       bd.Q.as<double>(), D(k->x), D(k->qtot));
-        IBP_CHECK_LAUNCH();
-        pme_apply(c, n, a.xw, D(k->qtot), R, prec, D(k->psi_tot), nullptr, true);
-        if (prec == IBPME_FP64) ++matvec64;
+        if (zero_charges) {
+            IBP_CUDA(cudaMemsetAsync(k->psi_tot.p, 0, sizeof(double) * (size_t)R * n, s()));
+        } else {
+            compose_kernel<<<blocks_for((long long)n * R), 256, 0, s()>>>(n, nk, R, I(bd.bead_unk), I(bd.bead_body),
+                                                                           bd.Q.as<double>(), D(k->x), D(k->qtot));
+            IBP_CHECK_LAUNCH();
+            pme_apply(c, n, a.xw, D(k->qtot), R, prec, D(k->psi_tot), nullptr, true);
+            if (prec == IBPME_FP64) ++matvec64;
+        }
         if (fit_psi && nmb > 0) {
             fit_psi_kernel<<<blocks_for(32LL * nmb * R), 256, 0, s()>>>(nmb, nk, n, R, I(bd.mb_body), I(bd.mb_unk),
                                                                         I(bd.off), bd.rel.as<double>(), a.E0,
@@ -931,7 +938,9 @@ struct Solver {
         // operator, whose rounding then scales with the residual, not with the
         // (possibly much larger) potentials of the guess itself.
         const bool mixed = a.prec == IBPME_MIXED;
-        std::vector<double> res = residual(IBPME_FP64, true);
+        // the zero guess of a system without ions has no charge anywhere: r0 follows from b alone
+        const bool zero_start = nk > 0 && !a.user_guess && !a.learned && bd.nmb == bd.nb;
+        std::vector<double> res = residual(IBPME_FP64, true, zero_start);
         bool res64 = true;
         int fell_back = 0;
         if (a.learned && nk > 0) {
