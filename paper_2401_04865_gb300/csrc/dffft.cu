@@ -22,9 +22,12 @@ namespace ibp {
 namespace {
 
 constexpr int kDfPoints = 2048;   // points per block (lines x line length)
-constexpr int kDfThreads = 1024;  // one butterfly per thread per stage
-constexpr int kDfPad = 1;         // float4 of padding after each line in shared memory (bank spread)
-constexpr int kDfSmem = kDfPoints + kDfPoints / 16 * kDfPad;   // lines <= kDfPoints / 16
+constexpr int kDfThreads = 256;   // eight points per thread in each radix-8 pass
+// Shared memory: point i of a line at line * ls + i + i / 8 (a stride-8 store of the
+// first pass then spreads over the banks), ls = n + n / 8 + 1 (odd: column loads spread too)
+constexpr int kDfSmem = kDfPoints + kDfPoints / 8 + kDfPoints / 16;
+__host__ __device__ constexpr int df_ls(int n) { return n + n / 8 + 1; }
+__device__ __forceinline__ int sw(int i) { return i + (i >> 3); }
 
 // Accuracy of the double-float operations (dfloat.cuh): each is exact to about
 // 2^-44 of its operands' magnitude, so a length-N transform keeps a normwise
@@ -45,29 +48,105 @@ __device__ __forceinline__ dfc cmul(const dfc& x, const dfc& w, bool conj) {
     return {re, im};
 }
 
-__device__ __forceinline__ int bit_reverse(int i, int logn) { return (int)(__brev((unsigned)i) >> (32 - logn)); }
+// Multiplication by (1 -+ i) / sqrt(2) (forward / inverse) and by -+i.
+__device__ __forceinline__ dfc mul_w8(const dfc& x, bool inv) {
+    constexpr float ch = 0.70710677f;
+    constexpr float cl = (float)(0.70710678118654752440 - (double)ch);
+    const df c = {ch, cl};
+    // forward: (x + iy)(1 - i) = (x + y) + i (y - x); inverse: (x - y) + i (x + y)
+    const df a = df_add(x.re, inv ? df_neg(x.im) : x.im);
+    const df b = inv ? df_add(x.re, x.im) : df_add(x.im, df_neg(x.re));
+    return {df_mul(a, c), df_mul(b, c)};
+}
 
-// In-place radix-2 decimation-in-time FFT of `lines` lines of length n held in
-// shared memory in bit-reversed order (line l at buf[l * (n + kDfPad) ..]).  tw[k] =
-// exp(-2 pi i k / n), k < n/2; inverse uses the conjugates.  One butterfly per
-// thread per stage (lines * n / 2 = kDfThreads).
-__device__ void fft_lines(float4* buf, int n, int logn, const float4* __restrict__ tw, bool inverse) {
-    const int b = threadIdx.x;
-    const int half_n = n >> 1;
-    const int line = b / half_n, k = b % half_n;
-    float4* x = buf + line * (n + kDfPad);
-    for (int s = 1; s <= logn; ++s) {
-        const int half = 1 << (s - 1), len = half << 1;
-        const int group = k / half, pos = k % half;
-        const int i = group * len + pos, j = i + half;
-        const dfc w = load_c(tw[pos * (n / len)]);
-        const dfc a = load_c(x[i]);
-        const dfc t = cmul(load_c(x[j]), w, inverse);
-        __syncthreads();
-        x[i] = store_c({df_add(a.re, t.re), df_add(a.im, t.im)});
-        x[j] = store_c({df_add(a.re, df_neg(t.re)), df_add(a.im, df_neg(t.im))});
-        __syncthreads();
+__device__ __forceinline__ dfc mul_mi(const dfc& x, bool inv) {   // forward -i x, inverse +i x
+    return inv ? dfc{df_neg(x.im), x.re} : dfc{x.im, df_neg(x.re)};
+}
+
+__device__ __forceinline__ dfc cadd(const dfc& a, const dfc& b) { return {df_add(a.re, b.re), df_add(a.im, b.im)}; }
+__device__ __forceinline__ dfc csub(const dfc& a, const dfc& b) {
+    return {df_add(a.re, df_neg(b.re)), df_add(a.im, df_neg(b.im))};
+}
+
+// R-point DFTs in registers, y_q = sum_m v_m exp(-+2 pi i m q / R).
+template <bool INV>
+__device__ __forceinline__ void dft2(dfc* v) {
+    const dfc a = v[0], b = v[1];
+    v[0] = cadd(a, b);
+    v[1] = csub(a, b);
+}
+
+template <bool INV>
+__device__ __forceinline__ void dft4(dfc* v) {
+    const dfc a0 = cadd(v[0], v[2]), a1 = csub(v[0], v[2]);
+    const dfc a2 = cadd(v[1], v[3]), a3 = mul_mi(csub(v[1], v[3]), INV);
+    v[0] = cadd(a0, a2);
+    v[2] = csub(a0, a2);
+    v[1] = cadd(a1, a3);
+    v[3] = csub(a1, a3);
+}
+
+template <bool INV>
+__device__ __forceinline__ void dft8(dfc* v) {
+    dfc e[4] = {v[0], v[2], v[4], v[6]}, o[4] = {v[1], v[3], v[5], v[7]};
+    dft4<INV>(e);
+    dft4<INV>(o);
+    o[1] = mul_w8(o[1], INV);
+    o[2] = mul_mi(o[2], INV);
+    o[3] = mul_mi(mul_w8(o[3], INV), INV);   // w8^3 = w8 w4
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        v[q] = cadd(e[q], o[q]);
+        v[q + 4] = csub(e[q], o[q]);
     }
+}
+
+// One Stockham pass of radix R over the block's lines (lines x n = kDfPoints) in
+// shared memory, natural order in and out: butterfly j of a line takes the points
+// j + r n/R, applies the twiddles exp(-+2 pi i k r / (Ns R)), k = j mod Ns, and
+// writes its R outputs to (j - k) R + k + r Ns.  tw[t] = exp(-2 pi i t / n), t < n.
+template <int R, bool INV>
+__device__ __forceinline__ void stockham_pass(float4* buf, int ls, int n, int Ns, const float4* __restrict__ tw) {
+    constexpr int per = 8 / R;   // butterflies per thread: kDfPoints / R / kDfThreads
+    const int nb = n / R;
+    dfc v[per][R];
+    int out[per];
+#pragma unroll
+    for (int q = 0; q < per; ++q) {
+        const int b = threadIdx.x + q * kDfThreads;
+        const int line = b / nb, j = b - line * nb;
+        const int k = j % Ns;
+        const float4* x = buf + line * ls;
+#pragma unroll
+        for (int r = 0; r < R; ++r) v[q][r] = load_c(x[sw(j + r * nb)]);
+        const int step = k * (n / (Ns * R));
+#pragma unroll
+        for (int r = 1; r < R; ++r) v[q][r] = cmul(v[q][r], load_c(tw[r * step]), INV);
+        if (R == 8) dft8<INV>(v[q]);
+        else if (R == 4) dft4<INV>(v[q]);
+        else dft2<INV>(v[q]);
+        out[q] = line * ls + (j - k) * R + k;   // line offset + first output (before the swizzle)
+    }
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < per; ++q) {
+        const int b = threadIdx.x + q * kDfThreads;
+        const int line = b / nb;
+        const int o = out[q] - line * ls;
+#pragma unroll
+        for (int r = 0; r < R; ++r) buf[line * ls + sw(o + r * Ns)] = store_c(v[q][r]);
+    }
+    __syncthreads();
+}
+
+// Length-n transforms of every line of the block (natural order in and out).
+template <bool INV>
+__device__ void fft_lines(float4* buf, int n, int logn, const float4* __restrict__ tw) {
+    const int ls = df_ls(n);
+    int Ns = 1, l = logn;
+    for (; l >= 3; l -= 3, Ns *= 8) stockham_pass<8, INV>(buf, ls, n, Ns, tw);
+    if (l == 2) stockham_pass<4, INV>(buf, ls, n, Ns, tw);
+    else if (l == 1) stockham_pass<2, INV>(buf, ls, n, Ns, tw);
 }
 
 struct DfGeom {
@@ -85,7 +164,7 @@ __device__ __forceinline__ df df_half(df a) { return {a.hi * 0.5f, a.lo * 0.5f};
 __global__ void __launch_bounds__(kDfThreads)
 dfx_forward_kernel(DfGeom d, const double* __restrict__ grid, float4* __restrict__ S, const float4* __restrict__ tw) {
     __shared__ float4 buf[kDfSmem];
-    const int n = d.n[0], pl = kDfPoints / n;   // packed lines per block
+    const int n = d.n[0], pl = kDfPoints / n, ls = df_ls(n);   // packed lines per block
     const size_t ch = blockIdx.y;
     const long long line0 = (long long)blockIdx.x * 2 * pl;   // first real line
     const double* src = grid + ch * d.G + line0 * n;
@@ -93,15 +172,15 @@ dfx_forward_kernel(DfGeom d, const double* __restrict__ grid, float4* __restrict
         const int p = e / n, i = e % n;
         const df a = df_from_double(src[(size_t)(2 * p) * n + i]);
         const df b = df_from_double(src[(size_t)(2 * p + 1) * n + i]);
-        buf[p * (n + kDfPad) + bit_reverse(i, d.logn[0])] = make_float4(a.hi, a.lo, b.hi, b.lo);
+        buf[p * ls + sw(i)] = make_float4(a.hi, a.lo, b.hi, b.lo);
     }
     __syncthreads();
-    fft_lines(buf, n, d.logn[0], tw, false);
+    fft_lines<false>(buf, n, d.logn[0], tw);
     float4* dst = S + ch * d.Gh + line0 * d.h;
     for (int e = threadIdx.x; e < pl * d.h; e += kDfThreads) {
         const int p = e / d.h, k = e % d.h;
-        const dfc zk = load_c(buf[p * (n + kDfPad) + k]);
-        const dfc zm = load_c(buf[p * (n + kDfPad) + ((n - k) & (n - 1))]);   // Z[N - k], conjugated below
+        const dfc zk = load_c(buf[p * ls + sw(k)]);
+        const dfc zm = load_c(buf[p * ls + sw((n - k) & (n - 1))]);   // Z[N - k], conjugated below
         const dfc A = {df_half(df_add(zk.re, zm.re)), df_half(df_add(zk.im, df_neg(zm.im)))};
         // (Z[k] - conj Z[N-k]) / 2i: re = (zk.im + zm.im) / 2, im = -(zk.re - zm.re) / 2
         const dfc B = {df_half(df_add(zk.im, zm.im)), df_half(df_add(zm.re, df_neg(zk.re)))};
@@ -116,7 +195,7 @@ dfx_forward_kernel(DfGeom d, const double* __restrict__ grid, float4* __restrict
 __global__ void __launch_bounds__(kDfThreads)
 dfx_inverse_kernel(DfGeom d, const float4* __restrict__ S, double* __restrict__ grid, const float4* __restrict__ tw) {
     __shared__ float4 buf[kDfSmem];
-    const int n = d.n[0], pl = kDfPoints / n;
+    const int n = d.n[0], pl = kDfPoints / n, ls = df_ls(n);
     const size_t ch = blockIdx.y;
     const long long line0 = (long long)blockIdx.x * 2 * pl;
     const float4* src = S + ch * d.Gh + line0 * d.h;
@@ -126,18 +205,18 @@ dfx_inverse_kernel(DfGeom d, const float4* __restrict__ S, double* __restrict__ 
         const dfc B = load_c(src[(size_t)(2 * p + 1) * d.h + k]);
         // Z[k] = A + i B
         const dfc zk = {df_add(A.re, df_neg(B.im)), df_add(A.im, B.re)};
-        buf[p * (n + kDfPad) + bit_reverse(k, d.logn[0])] = store_c(zk);
+        buf[p * ls + sw(k)] = store_c(zk);
         if (k > 0 && k < n / 2) {   // Z[N-k] = conj A + i conj B
             const dfc zm = {df_add(A.re, B.im), df_add(df_neg(A.im), B.re)};
-            buf[p * (n + kDfPad) + bit_reverse(n - k, d.logn[0])] = store_c(zm);
+            buf[p * ls + sw(n - k)] = store_c(zm);
         }
     }
     __syncthreads();
-    fft_lines(buf, n, d.logn[0], tw, true);
+    fft_lines<true>(buf, n, d.logn[0], tw);
     double* dst = grid + ch * d.G + line0 * n;
     for (int e = threadIdx.x; e < kDfPoints; e += kDfThreads) {
         const int p = e / n, i = e % n;
-        const float4 v = buf[p * (n + kDfPad) + i];
+        const float4 v = buf[p * ls + sw(i)];
         dst[(size_t)(2 * p) * n + i] = (double)v.x + (double)v.y;
         dst[(size_t)(2 * p + 1) * n + i] = (double)v.z + (double)v.w;
     }
@@ -148,21 +227,23 @@ dfx_inverse_kernel(DfGeom d, const float4* __restrict__ S, double* __restrict__ 
 __global__ void __launch_bounds__(kDfThreads)
 dfy_kernel(DfGeom d, float4* __restrict__ S, const float4* __restrict__ tw, int inverse) {
     __shared__ float4 buf[kDfSmem];
-    const int n = d.n[1], cols = kDfPoints / n, h = d.h;
+    const int n = d.n[1], cols = kDfPoints / n, h = d.h, ls = df_ls(n);
     const size_t ch = blockIdx.y;
     const int blocks_x = (h + cols - 1) / cols;
     const int z = blockIdx.x / blocks_x, x0 = (blockIdx.x % blocks_x) * cols;
     float4* plane = S + ch * d.Gh + (size_t)z * n * h;
     for (int e = threadIdx.x; e < kDfPoints; e += kDfThreads) {
         const int y = e / cols, c = e % cols;   // consecutive threads: consecutive x (coalesced)
-        buf[c * (n + kDfPad) + bit_reverse(y, d.logn[1])] =
-            x0 + c < h ? plane[(size_t)y * h + x0 + c] : make_float4(0.f, 0.f, 0.f, 0.f);
+        buf[c * ls + sw(y)] = x0 + c < h ? plane[(size_t)y * h + x0 + c] : make_float4(0.f, 0.f, 0.f, 0.f);
     }
     __syncthreads();
-    fft_lines(buf, n, d.logn[1], tw, inverse != 0);
+    if (inverse)
+        fft_lines<true>(buf, n, d.logn[1], tw);
+    else
+        fft_lines<false>(buf, n, d.logn[1], tw);
     for (int e = threadIdx.x; e < kDfPoints; e += kDfThreads) {
         const int y = e / cols, c = e % cols;
-        if (x0 + c < h) plane[(size_t)y * h + x0 + c] = buf[c * (n + kDfPad) + y];
+        if (x0 + c < h) plane[(size_t)y * h + x0 + c] = buf[c * ls + sw(y)];
     }
 }
 
@@ -171,7 +252,7 @@ dfy_kernel(DfGeom d, float4* __restrict__ S, const float4* __restrict__ tw, int 
 __global__ void __launch_bounds__(kDfThreads)
 dfz_scale_kernel(DfGeom d, float4* __restrict__ S, const float4* __restrict__ tw, const double* __restrict__ green) {
     __shared__ float4 buf[kDfSmem];
-    const int n = d.n[2], cols = kDfPoints / n, ny = d.n[1], h = d.h;
+    const int n = d.n[2], cols = kDfPoints / n, ny = d.n[1], h = d.h, ls = df_ls(n);
     const size_t ch = blockIdx.y;
     const int blocks_x = (h + cols - 1) / cols;
     const int y = blockIdx.x / blocks_x, x0 = (blockIdx.x % blocks_x) * cols;
@@ -179,39 +260,25 @@ dfz_scale_kernel(DfGeom d, float4* __restrict__ S, const float4* __restrict__ tw
     float4* col = S + ch * d.Gh + (size_t)y * h + x0;
     for (int e = threadIdx.x; e < kDfPoints; e += kDfThreads) {
         const int z = e / cols, c = e % cols;
-        buf[c * (n + kDfPad) + bit_reverse(z, d.logn[2])] =
-            x0 + c < h ? col[(size_t)z * zstride + c] : make_float4(0.f, 0.f, 0.f, 0.f);
+        buf[c * ls + sw(z)] = x0 + c < h ? col[(size_t)z * zstride + c] : make_float4(0.f, 0.f, 0.f, 0.f);
     }
     __syncthreads();
-    fft_lines(buf, n, d.logn[2], tw, false);
+    fft_lines<false>(buf, n, d.logn[2], tw);
     for (int e = threadIdx.x; e < kDfPoints; e += kDfThreads) {
         const int c = e / n, z = e % n;
         if (x0 + c >= h) continue;
         const df gk = df_from_double(green[((size_t)z * ny + y) * h + x0 + c]);
-        float4& slot = buf[c * (n + kDfPad) + z];
+        float4& slot = buf[c * ls + sw(z)];
         dfc v = load_c(slot);
         v.re = df_mul(v.re, gk);
         v.im = df_mul(v.im, gk);
         slot = store_c(v);
     }
     __syncthreads();
-    // back to bit-reversed order for the inverse transform
-    float4 mine[kDfPoints / kDfThreads];
-    for (int r = 0; r < kDfPoints / kDfThreads; ++r) {
-        const int e = threadIdx.x + r * kDfThreads;
-        mine[r] = buf[(e / n) * (n + kDfPad) + e % n];
-    }
-    __syncthreads();
-    for (int r = 0; r < kDfPoints / kDfThreads; ++r) {
-        const int e = threadIdx.x + r * kDfThreads;
-        const int c = e / n, z = e % n;
-        buf[c * (n + kDfPad) + bit_reverse(z, d.logn[2])] = mine[r];
-    }
-    __syncthreads();
-    fft_lines(buf, n, d.logn[2], tw, true);
+    fft_lines<true>(buf, n, d.logn[2], tw);
     for (int e = threadIdx.x; e < kDfPoints; e += kDfThreads) {
         const int z = e / cols, c = e % cols;
-        if (x0 + c < h) col[(size_t)z * zstride + c] = buf[c * (n + kDfPad) + z];
+        if (x0 + c < h) col[(size_t)z * zstride + c] = buf[c * ls + sw(z)];
     }
 }
 
@@ -232,12 +299,12 @@ bool df_fft_supported(const MeshGeom& g) {
     return (long long)g.N[1] * g.N[2] % (2 * (kDfPoints / g.N[0])) == 0;
 }
 
-// Twiddles exp(-2 pi i k / N_d), k < N_d / 2, per axis (double -> hi + lo floats).
+// Twiddles exp(-2 pi i k / N_d), k < N_d, per axis (double -> hi + lo floats).
 void df_fft_init(const MeshGeom& g, DevBuf tw[3], cudaStream_t s) {
     for (int d = 0; d < 3; ++d) {
         const int n = g.N[d];
-        std::vector<float4> h(n / 2);
-        for (int k = 0; k < n / 2; ++k) {
+        std::vector<float4> h(n);
+        for (int k = 0; k < n; ++k) {
             const double th = 2.0 * 3.14159265358979323846264338327950288 * k / n;
             const double c = std::cos(th), sn = -std::sin(th);
             const float ch = (float)c, sh = (float)sn;
