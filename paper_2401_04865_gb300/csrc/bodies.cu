@@ -21,13 +21,16 @@ __global__ void bead_body_kernel(int nb, const int* __restrict__ off, int* __res
 }
 
 __global__ void rel_kernel(int n, const double* __restrict__ xw, const int* __restrict__ bead_body,
-                           const double* __restrict__ X, double L0, double L1, double L2, double* __restrict__ rel) {
+                           const double* __restrict__ X, double L0, double L1, double L2, double iL0, double iL1,
+                           double iL2, double* __restrict__ rel) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const int b = bead_body[i];
-    rel[3 * i + 0] = min_image(xw[3 * i + 0] - X[3 * b + 0], L0);
-    rel[3 * i + 1] = min_image(xw[3 * i + 1] - X[3 * b + 1], L1);
-    rel[3 * i + 2] = min_image(xw[3 * i + 2] - X[3 * b + 2], L2);
+    // minimum image with a multiplication by 1/L (the reference points need not be wrapped)
+    const double d0 = xw[3 * i + 0] - X[3 * b + 0], d1 = xw[3 * i + 1] - X[3 * b + 1], d2 = xw[3 * i + 2] - X[3 * b + 2];
+    rel[3 * i + 0] = d0 - L0 * floor(d0 * iL0 + 0.5);
+    rel[3 * i + 1] = d1 - L1 * floor(d1 * iL1 + 0.5);
+    rel[3 * i + 2] = d2 - L2 * floor(d2 * iL2 + 0.5);
 }
 
 __global__ void dipole_kernel(int nb, int n, int nrhs, const int* __restrict__ off, const double* __restrict__ rel,
@@ -158,11 +161,12 @@ __global__ void hard_sphere_kernel(int n, const double* __restrict__ xw, double 
     for (long long p = rowptr[t] + lane; p < rowptr[t + 1]; p += 32) {
         const int be = order[col[p]];
         if (bead_body[be] == ba) continue;
-        const double dx = min_image(x0 - xw[3 * be], L0);
-        const double dy = min_image(y0 - xw[3 * be + 1], L1);
-        const double dz = min_image(z0 - xw[3 * be + 2], L2);
-        const double r = sqrt(dx * dx + dy * dy + dz * dz);
-        if (r < 2.0 * a && r > 0.0) {
+        const double dx = min_image_wrapped(x0 - xw[3 * be], L0);
+        const double dy = min_image_wrapped(y0 - xw[3 * be + 1], L1);
+        const double dz = min_image_wrapped(z0 - xw[3 * be + 2], L2);
+        const double r2 = dx * dx + dy * dy + dz * dz;
+        if (r2 < 4.0 * a * a && r2 > 0.0) {   // overlap: the only pairs that need r
+            const double r = sqrt(r2);
             const double m = coef * (2.0 * a - r) / r;
             fx += m * dx;
             fy += m * dy;
@@ -408,7 +412,8 @@ void bodies_upload(ibpme_ctx* c, int n, const ibpme_bodies* b, const double* xw,
     IBP_CUDA(cudaMemcpyAsync(bd.Q.p, b->Q, sizeof(double) * nb, cudaMemcpyDeviceToDevice, s));
     bd.rel.ensure(sizeof(double) * 3 * n);
     rel_kernel<<<div_up(n, 256), 256, 0, s>>>(n, xw, bd.bead_body.as<int>(), bd.X.as<double>(), c->p.box[0],
-                                              c->p.box[1], c->p.box[2], bd.rel.as<double>());
+                                              c->p.box[1], c->p.box[2], 1.0 / c->p.box[0], 1.0 / c->p.box[1],
+                                              1.0 / c->p.box[2], bd.rel.as<double>());
     IBP_CHECK_LAUNCH();
     c->bodies_current = true;
 }

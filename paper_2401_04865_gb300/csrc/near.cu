@@ -825,44 +825,64 @@ compact_field_kernel(CbArgs A, int n, const double* __restrict__ q, double inv_e
     }
 }
 
-// One warp per body: centre (mean of the minimum-image offsets from the first
+// One block per body: centre (mean of the minimum-image offsets from the first
 // bead), radius, the compact flag, and the positions relative to the centre as
-// hi + lo floats.
-__global__ void compact_bodies_kernel(int nb, const int* __restrict__ off, const double* __restrict__ xw, double L0,
-                                      double L1, double L2, double lim2, int* __restrict__ flag,
-                                      float4* __restrict__ hi, float4* __restrict__ lo) {
-    const int b = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int lane = threadIdx.x & 31;
-    if (b >= nb) return;
+// hi + lo floats.  Bodies below kCompactMin beads leave at once.
+constexpr int kCbBodyThreads = 256;
+
+__device__ __forceinline__ double block_sum_256(double v, double* sh) {
+    v = warp_sum(v);
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
+    __syncthreads();
+    double t = 0.0;
+#pragma unroll
+    for (int w = 0; w < kCbBodyThreads / 32; ++w) t += sh[w];
+    return t;
+}
+
+__global__ void __launch_bounds__(kCbBodyThreads)
+compact_bodies_kernel(const int* __restrict__ off, const double* __restrict__ xw, double L0, double L1, double L2,
+                      double lim2, int* __restrict__ flag, float4* __restrict__ hi, float4* __restrict__ lo) {
+    __shared__ double sh[kCbBodyThreads / 32];
+    const int b = blockIdx.x;
     const int o = off[b], m = off[b + 1] - o;
-    if (m < kCompactMin) {
-        if (lane == 0) flag[b] = 0;
+    if (m < kCompactMin) {   // block-uniform
+        if (threadIdx.x == 0) flag[b] = 0;
         return;
     }
     const double x0 = xw[3 * o], y0 = xw[3 * o + 1], z0 = xw[3 * o + 2];
     double sx = 0.0, sy = 0.0, sz = 0.0;
-    for (int j = lane; j < m; j += 32) {
-        sx += min_image(xw[3 * (o + j)] - x0, L0);
-        sy += min_image(xw[3 * (o + j) + 1] - y0, L1);
-        sz += min_image(xw[3 * (o + j) + 2] - z0, L2);
+    for (int j = threadIdx.x; j < m; j += kCbBodyThreads) {
+        sx += min_image_wrapped(xw[3 * (o + j)] - x0, L0);
+        sy += min_image_wrapped(xw[3 * (o + j) + 1] - y0, L1);
+        sz += min_image_wrapped(xw[3 * (o + j) + 2] - z0, L2);
     }
-    const double cx = warp_sum(sx) / m, cy = warp_sum(sy) / m, cz = warp_sum(sz) / m;
+    const double cx = block_sum_256(sx, sh) / m;
+    const double cy = block_sum_256(sy, sh) / m;
+    const double cz = block_sum_256(sz, sh) / m;
     double r2max = 0.0;
-    for (int j = lane; j < m; j += 32) {
-        const double dx = min_image(xw[3 * (o + j)] - x0, L0) - cx;
-        const double dy = min_image(xw[3 * (o + j) + 1] - y0, L1) - cy;
-        const double dz = min_image(xw[3 * (o + j) + 2] - z0, L2) - cz;
+    for (int j = threadIdx.x; j < m; j += kCbBodyThreads) {
+        const double dx = min_image_wrapped(xw[3 * (o + j)] - x0, L0) - cx;
+        const double dy = min_image_wrapped(xw[3 * (o + j) + 1] - y0, L1) - cy;
+        const double dz = min_image_wrapped(xw[3 * (o + j) + 2] - z0, L2) - cz;
         r2max = fmax(r2max, dx * dx + dy * dy + dz * dz);
     }
 #pragma unroll
     for (int s = 16; s > 0; s >>= 1) r2max = fmax(r2max, __shfl_xor_sync(0xffffffffu, r2max, s));
-    const int f = r2max <= lim2 ? 1 : 0;
-    if (lane == 0) flag[b] = f;
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = r2max;
+    __syncthreads();
+    double rm = 0.0;
+#pragma unroll
+    for (int w = 0; w < kCbBodyThreads / 32; ++w) rm = fmax(rm, sh[w]);
+    const int f = rm <= lim2 ? 1 : 0;
+    if (threadIdx.x == 0) flag[b] = f;
     if (!f) return;
-    for (int j = lane; j < m; j += 32) {
-        const double dx = min_image(xw[3 * (o + j)] - x0, L0) - cx;
-        const double dy = min_image(xw[3 * (o + j) + 1] - y0, L1) - cy;
-        const double dz = min_image(xw[3 * (o + j) + 2] - z0, L2) - cz;
+    for (int j = threadIdx.x; j < m; j += kCbBodyThreads) {
+        const double dx = min_image_wrapped(xw[3 * (o + j)] - x0, L0) - cx;
+        const double dy = min_image_wrapped(xw[3 * (o + j) + 1] - y0, L1) - cy;
+        const double dz = min_image_wrapped(xw[3 * (o + j) + 2] - z0, L2) - cz;
         const float hx = (float)dx, hy = (float)dy, hz = (float)dz;
         hi[o + j] = make_float4(hx, hy, hz, 0.0f);
         lo[o + j] = make_float4((float)(dx - (double)hx), (float)(dy - (double)hy), (float)(dz - (double)hz), 0.0f);
@@ -1128,8 +1148,8 @@ void compact_prepare(ibpme_ctx* c, int n, const double* xw) {
     float4* lo = static_cast<float4*>(nl.cb_lo.ensure(sizeof(float4) * (n + 1)));
     const double* L = c->p.box;
     const double lim = fmin(c->rc, 0.25 * fmin(L[0], fmin(L[1], L[2])));
-    compact_bodies_kernel<<<div_up((long long)nb * 32, 128), 128, 0, s>>>(nb, bd.off.as<int>(), xw, L[0], L[1], L[2],
-                                                                           lim * lim, flag, hi, lo);
+    compact_bodies_kernel<<<nb, kCbBodyThreads, 0, s>>>(bd.off.as<int>(), xw, L[0], L[1], L[2], lim * lim, flag, hi,
+                                                        lo);
     IBP_CHECK_LAUNCH();
     if (nl.cb_tasks_key == bd.version) return;
     const std::vector<int>& off = bd.host_off;
