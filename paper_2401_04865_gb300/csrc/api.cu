@@ -413,6 +413,8 @@ IBP_API ibpme_status pme_destroy(ibpme_ctx* c) {
     c->mesh32.destroy();
     if (c->pinned) cudaFreeHost(c->pinned);
     c->pinned = nullptr;
+    if (c->pre.hm_pin) cudaFreeHost(c->pre.hm_pin);
+    c->pre.hm_pin = nullptr;
     delete c;
     return IBPME_OK;
 }

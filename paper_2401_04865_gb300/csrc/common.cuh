@@ -260,6 +260,14 @@ struct Precond {
     DevBuf pb_shape, pb_first, pb_psi, pb_n, plain;   // per solve: preconditioned bodies, identity unknowns
     DevBuf moments, work, col;                        // set-up scratch
     int npb = 0, nplain = 0, chunks = 0;
+    // steady state: the body structure the tables were laid out for, the shape of
+    // every multi-bead body (-1: identity), and the moments of the last positions
+    // (copied asynchronously into pinned memory, checked at the next solve)
+    unsigned long long prep_version = 0;
+    bool prep_valid = false;
+    std::vector<int> assign;
+    double* hm_pin = nullptr;
+    size_t hm_cap = 0;
 };
 
 // Optional per-stage timing with CUDA events on the launching stream.

@@ -21,8 +21,9 @@ namespace ibp {
 
 namespace {
 
-constexpr int kDfPoints = 2048;   // points per block (lines x line length)
-constexpr int kDfThreads = 256;   // eight points per thread in each radix-8 pass
+constexpr int kDfPoints = 1024;   // points per block (lines x line length)
+constexpr int kDfThreads = 128;   // eight points per thread in each radix-8 pass
+constexpr int kDfMinBlocks = 8;   // resident blocks per SM the register budget is set for
 // Shared memory: point i of a line at line * ls + i + i / 8 (a stride-8 store of the
 // first pass then spreads over the banks), ls = n + n / 8 + 1 (odd: column loads spread too)
 constexpr int kDfSmem = kDfPoints + kDfPoints / 8 + kDfPoints / 16;
@@ -161,7 +162,7 @@ __device__ __forceinline__ df df_half(df a) { return {a.hi * 0.5f, a.lo * 0.5f};
 // x pass, forward.  Two real lines a, b travel as one complex line a + i b; after
 // its transform Z, A[k] = (Z[k] + conj Z[N-k]) / 2 and B[k] = (Z[k] - conj Z[N-k]) / 2i
 // are the spectra of a and b; their halves k = 0 .. N/2 go to S.
-__global__ void __launch_bounds__(kDfThreads)
+__global__ void __launch_bounds__(kDfThreads, kDfMinBlocks)
 dfx_forward_kernel(DfGeom d, const double* __restrict__ grid, float4* __restrict__ S, const float4* __restrict__ tw) {
     __shared__ float4 buf[kDfSmem];
     const int n = d.n[0], pl = kDfPoints / n, ls = df_ls(n);   // packed lines per block
@@ -192,7 +193,7 @@ dfx_forward_kernel(DfGeom d, const double* __restrict__ grid, float4* __restrict
 // x pass, inverse: the half spectra A, B of two lines rebuild Z = A + i B on all
 // N points (Z[N-k] = conj A[k] + i conj B[k]); the inverse transform's real and
 // imaginary parts are the two real lines, returned as FP64.
-__global__ void __launch_bounds__(kDfThreads)
+__global__ void __launch_bounds__(kDfThreads, kDfMinBlocks)
 dfx_inverse_kernel(DfGeom d, const float4* __restrict__ S, double* __restrict__ grid, const float4* __restrict__ tw) {
     __shared__ float4 buf[kDfSmem];
     const int n = d.n[0], pl = kDfPoints / n, ls = df_ls(n);
@@ -224,7 +225,7 @@ dfx_inverse_kernel(DfGeom d, const float4* __restrict__ S, double* __restrict__ 
 
 // y pass (either direction) on the half spectrum: columns x0 .. x0 + cols of one
 // z-plane (the last group of columns may be partial)
-__global__ void __launch_bounds__(kDfThreads)
+__global__ void __launch_bounds__(kDfThreads, kDfMinBlocks)
 dfy_kernel(DfGeom d, float4* __restrict__ S, const float4* __restrict__ tw, int inverse) {
     __shared__ float4 buf[kDfSmem];
     const int n = d.n[1], cols = kDfPoints / n, h = d.h, ls = df_ls(n);
@@ -249,7 +250,7 @@ dfy_kernel(DfGeom d, float4* __restrict__ S, const float4* __restrict__ tw, int 
 
 // z pass on the half spectrum: forward FFT, Green's-function scaling (FP64
 // half-spectrum table), inverse FFT, for columns x0 .. x0 + cols at one y
-__global__ void __launch_bounds__(kDfThreads)
+__global__ void __launch_bounds__(kDfThreads, kDfMinBlocks)
 dfz_scale_kernel(DfGeom d, float4* __restrict__ S, const float4* __restrict__ tw, const double* __restrict__ green) {
     __shared__ float4 buf[kDfSmem];
     const int n = d.n[2], cols = kDfPoints / n, ny = d.n[1], h = d.h, ls = df_ls(n);

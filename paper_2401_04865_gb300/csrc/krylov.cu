@@ -588,6 +588,7 @@ struct Solver {
     int iters = 0, matvec64 = 0;
     bool pre_on = false;         // body-block preconditioner active for this solve
     std::vector<double> bnorm;   // |b| per system
+    bool want_b = false;         // the next norms() call also fetches |b|
 
     Solver(ibpme_ctx* c_, const SolveArgs& a_) : c(c_), k(c_->kry), a(a_) {
         n = a.n;
@@ -627,7 +628,7 @@ struct Solver {
         k->part.ensure(sizeof(double) * (size_t)R * k->nblk * (m + 2));
         k->scal.ensure(sizeof(double) * (size_t)S * S_COUNT);
         k->active.ensure(sizeof(int) * S);
-        k->norms.ensure(sizeof(double) * S);
+        k->norms.ensure(sizeof(double) * 2 * S);   // |v|^2 per system, then |b|^2 per system
         k->jdev.ensure(sizeof(int));
         const size_t full = (size_t)R * n;
         for (DevBuf* b : {&k->qop, &k->psi, &k->psi_tot, &k->qtot}) b->ensure(sizeof(double) * full);
@@ -788,8 +789,14 @@ struct Solver {
         const int chunks = std::max(1, std::min(blocks_for(per), 608 / S + 1));
         norm2_kernel<<<dim3(chunks, S), 256, 0, s()>>>(nk, R, I(c->bodies.uo), v, D(k->norms));
         IBP_CHECK_LAUNCH();
-        std::vector<double> h = fetch(D(k->norms), S);
+        // the first fetch of a solve also brings |b|^2 (second half), saving one synchronisation
+        std::vector<double> h = fetch(D(k->norms), want_b ? 2 * S : S);
         for (double& e : h) e = std::sqrt(e);
+        if (want_b) {
+            bnorm.assign(h.begin() + S, h.end());
+            h.resize(S);
+            want_b = false;
+        }
         return h;
     }
 
@@ -917,15 +924,12 @@ struct Solver {
         const long long len = (long long)nk * R;
         IBP_CUDA(cudaMemsetAsync(k->qop.p, 0, sizeof(double) * (size_t)R * n, s()));   // ions stay 0
         // |b| of the full system of Eq. saddle, b = [-r.E0 ; Q], per system
-        IBP_CUDA(cudaMemsetAsync(k->norms.p, 0, sizeof(double) * S, s()));
+        IBP_CUDA(cudaMemsetAsync(D(k->norms) + S, 0, sizeof(double) * S, s()));
         const int per = (n + nb) / ncfg + 1;
         bfull_kernel<<<dim3(std::max(1, std::min(blocks_for(per), 608 / S + 1)), S), 256, 0, s()>>>(
-            R, I(bd.cfg_beads), I(bd.cfg_bodies), bd.rel.as<double>(), a.E0, bd.Q.as<double>(), D(k->norms));
+            R, I(bd.cfg_beads), I(bd.cfg_bodies), bd.rel.as<double>(), a.E0, bd.Q.as<double>(), D(k->norms) + S);
         IBP_CHECK_LAUNCH();
-        bnorm = fetch(D(k->norms), S);
-        for (double& e : bnorm) e = std::sqrt(e);
-        std::vector<double> tol_abs(S);
-        for (int i = 0; i < S; ++i) tol_abs[i] = a.rtol * bnorm[i];
+        want_b = true;   // fetched with the initial residual
 
         if (nk > 0) IBP_CUDA(cudaMemsetAsync(k->x.p, 0, sizeof(double) * len, s()));
         if (nk > 0 && a.user_guess) {
@@ -941,6 +945,8 @@ struct Solver {
         // the zero guess of a system without ions has no charge anywhere: r0 follows from b alone
         const bool zero_start = nk > 0 && !a.user_guess && !a.learned && bd.nmb == bd.nb;
         std::vector<double> res = residual(IBPME_FP64, true, zero_start);
+        std::vector<double> tol_abs(S);
+        for (int i = 0; i < S; ++i) tol_abs[i] = a.rtol * bnorm[i];
         bool res64 = true;
         int fell_back = 0;
         if (a.learned && nk > 0) {

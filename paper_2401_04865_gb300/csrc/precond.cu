@@ -207,12 +207,62 @@ precond_apply_kernel(int npb, int chunks, int nk, long long ustride, const int* 
 // Shapes of the current bodies: reuse cached inverses, build the missing ones,
 // and lay out the per-body tables of the apply kernel.  Returns false when no
 // body qualifies (the solve then runs unpreconditioned).
+namespace {
+
+bool shape_matches(const Precond::Shape& sp, int nb, double m2, double m4) {
+    return sp.nb == nb && std::fabs(sp.m2 - m2) <= 1e-9 * std::fabs(m2) + 1e-300 &&
+           std::fabs(sp.m4 - m4) <= 1e-9 * std::fabs(m4) + 1e-300;
+}
+
+// Moments of the current positions into pinned memory, without waiting (the
+// solve synchronises before it returns, so the next call can read them).
+void queue_moments(ibpme_ctx* c) {
+    Precond& P = c->pre;
+    const BodyData& bd = c->bodies;
+    const size_t bytes = sizeof(double) * 2 * bd.nmb;
+    if (P.hm_cap < bytes) {
+        if (P.hm_pin) cudaFreeHost(P.hm_pin);
+        P.hm_pin = nullptr;
+        P.hm_cap = 0;
+        IBP_CUDA(cudaMallocHost(&P.hm_pin, bytes));
+        P.hm_cap = bytes;
+    }
+    double* mom = static_cast<double*>(P.moments.ensure(bytes));
+    shape_moments_kernel<<<bd.nmb, 256, 0, c->stream>>>(bd.nmb, bd.mb_body.as<int>(), bd.off.as<int>(),
+                                                        bd.rel.as<double>(), mom);
+    IBP_CHECK_LAUNCH();
+    IBP_CUDA(cudaMemcpyAsync(P.hm_pin, mom, bytes, cudaMemcpyDeviceToHost, c->stream));
+}
+
+}  // namespace
+
 bool precond_prepare(ibpme_ctx* c) {
     Precond& P = c->pre;
     const BodyData& bd = c->bodies;
     cudaStream_t s = c->stream;
+    if (bd.nmb == 0) {
+        P.npb = 0;
+        return false;
+    }
+    // Steady state (a rigid-body trajectory): the same body structure as the last
+    // preparation, and the moments of the previous call's positions still match
+    // every assigned shape.  The tables stay; this call's moments are queued for
+    // the next check.  A body that changed shape is caught one solve late, which
+    // costs iterations, not accuracy (a right preconditioner does not change the
+    // solution).
+    if (P.prep_valid && P.prep_version == bd.version && P.hm_pin && (int)P.assign.size() == bd.nmb) {
+        bool same = true;
+        for (int b = 0; b < bd.nmb && same; ++b) {
+            const int id = P.assign[b];
+            if (id >= 0) same = shape_matches(P.shapes[id], P.shapes[id].nb, P.hm_pin[2 * b], P.hm_pin[2 * b + 1]);
+        }
+        if (same) {
+            queue_moments(c);
+            return P.npb > 0;
+        }
+    }
+    P.prep_valid = false;
     P.npb = 0;
-    if (bd.nmb == 0) return false;
     std::vector<int> mb_body(bd.nmb), mb_first(bd.nmb), mb_cnt(bd.nmb), mb_unk(bd.nmb);
     IBP_CUDA(cudaMemcpyAsync(mb_body.data(), bd.mb_body.p, sizeof(int) * bd.nmb, cudaMemcpyDeviceToHost, s));
     IBP_CUDA(cudaMemcpyAsync(mb_first.data(), bd.mb_first.p, sizeof(int) * bd.nmb, cudaMemcpyDeviceToHost, s));
@@ -239,15 +289,14 @@ bool precond_prepare(ibpme_ctx* c) {
         if (mb_cnt[b] > kPrecondMaxBeads) cfg_ok[cfg_of(mb_body[b])] = 0;
     std::vector<int> pb_shape, pb_first, pb_psi, pb_n;
     std::vector<char> covered(bd.nk, 0);
+    std::vector<int> assign(bd.nmb, -1);
     for (int b = 0; b < bd.nmb; ++b) {
         const int nb = mb_cnt[b];
         if (nb > kPrecondMaxBeads || !cfg_ok[cfg_of(mb_body[b])]) continue;
         const double m2 = hm[2 * b], m4 = hm[2 * b + 1];
         int id = -1;
         for (size_t q = 0; q < P.shapes.size(); ++q) {
-            const Precond::Shape& sp = P.shapes[q];
-            if (sp.nb == nb && std::fabs(sp.m2 - m2) <= 1e-9 * std::fabs(m2) + 1e-300 &&
-                std::fabs(sp.m4 - m4) <= 1e-9 * std::fabs(m4) + 1e-300) {
+            if (shape_matches(P.shapes[q], nb, m2, m4)) {
                 id = (int)q;
                 break;
             }
@@ -263,6 +312,7 @@ bool precond_prepare(ibpme_ctx* c) {
                 pb_psi.clear();
                 pb_n.clear();
                 std::fill(covered.begin(), covered.end(), 0);
+                std::fill(assign.begin(), assign.end(), -1);
                 b = -1;
                 continue;
             }
@@ -295,6 +345,7 @@ bool precond_prepare(ibpme_ctx* c) {
             IBP_CHECK_LAUNCH();
             P.shapes.push_back(sp);
         }
+        assign[b] = id;
         pb_shape.push_back(id);
         pb_first.push_back(mb_first[b]);
         pb_psi.push_back(mb_unk[b]);
@@ -302,7 +353,13 @@ bool precond_prepare(ibpme_ctx* c) {
         for (int i = 0; i < nb; ++i) covered[mb_first[b] + i] = 1;
         covered[mb_unk[b]] = 1;
     }
-    if (pb_shape.empty()) return false;
+    P.assign = assign;
+    P.prep_version = bd.version;
+    if (pb_shape.empty()) {
+        P.prep_valid = true;   // the structure is known to leave every body unpreconditioned
+        queue_moments(c);
+        return false;
+    }
     std::vector<int> plain;
     for (int u = 0; u < bd.nk; ++u)
         if (!covered[u]) plain.push_back(u);
@@ -328,6 +385,8 @@ bool precond_prepare(ibpme_ctx* c) {
     int maxn = 0;
     for (int v : pb_n) maxn = std::max(maxn, v);
     P.chunks = div_up(maxn, kRowsPerBlock);
+    P.prep_valid = true;
+    queue_moments(c);
     return true;
 }
 
