@@ -54,6 +54,13 @@ def peaks():
         return HBM_FALLBACK_GBS, "fallback"
 
 
+# the kernel behind each single-kernel stage of the library's profiler
+STAGE_KERNEL = {"spread": "spread_pairs_kernel<float>", "gather": "gather_pairs_kernel<float>",
+                "scale": "scale_kernel<float>", "near_apply": "near_apply_kernel", "near_apply32": "near_apply32_kernel",
+                "spread64": "spread_pairs_kernel<double>", "gather64": "gather_pairs_kernel<double>",
+                "scale64": "dfz_scale_kernel"}
+
+
 def measured_traffic(stage):
     """DRAM bytes (read + write) per launch of the stage's kernel on this workload,
     as recorded from an ncu capture in profiles/traffic.json; None if absent."""
@@ -243,6 +250,52 @@ class HostStep:
 
 
 # algorithmic bytes per launch of each timed stage (mesh w = 4 or 8 bytes, R = 1)
+# FP32 operations of the double-float primitives (dfloat.cuh, dffft.cu): two_sum 6,
+# fast_two_sum 3, df_add 11, df_mul 7, complex multiply 4 df_mul + 2 df_add = 50, complex
+# add 22, radix-2 DFT 2 x 22 = 44, radix-4 DFT 4 x 22 = 88, multiply by w8 2 x 11 + 2 x 7 = 36,
+# radix-8 DFT 2 x 88 + 2 x 36 + 8 x 22 = 424.
+DF_CMUL, DF_DFT = 50, {2: 44, 4: 88, 8: 424}
+
+
+def df_transform_ops(n):
+    """FP32 operations per point of one length-n double-float Stockham transform:
+    radix-8 passes, then one radix-4 or radix-2 pass; the twiddles of a pass with
+    sub-transform length Ns are trivial for the 1/Ns of its butterflies with k = 0
+    and are not counted."""
+    passes, l = [], int(round(np.log2(n)))
+    while l >= 3:
+        passes.append(8)
+        l -= 3
+    if l:
+        passes.append(2 ** l)
+    ops, ns = 0.0, 1
+    for r in passes:
+        ops += ((1.0 - 1.0 / ns) * (r - 1) * DF_CMUL + DF_DFT[r]) / r
+        ns *= r
+    return ops
+
+
+def stage_work(stage, s, npairs, df_mesh):
+    """(bound, algorithmic work per launch, unit) of a stage's kernel."""
+    if stage == "scale64" and df_mesh:
+        # forward z transform, Green's-function scaling (2 df_mul), inverse z transform,
+        # over the half spectrum (N_z N_y (N_x/2+1) points; the padded columns are not counted)
+        pts = s.mesh[2] * s.mesh[1] * (s.mesh[0] // 2 + 1)
+        return "alu", pts * (2 * df_transform_ops(s.mesh[2]) + 14), "Gop/s"
+    b = stage_bytes(stage, s, npairs)
+    return ("hbm", b, "GB/s") if b is not None else (None, None, None)
+
+
+def alu_peak():
+    """FP32 operations per second: 152 SMs x 128 FP32 lanes x the maximum SM clock."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            mhz = float(json.load(f)["sm_max_mhz"])
+    except (OSError, KeyError, ValueError):
+        mhz = 2070.0
+    return 152 * 128 * mhz * 1e6 / 1e9, f"derived: 152 SMs x 128 FP32 lanes x {mhz:.0f} MHz"
+
+
 def stage_bytes(stage, s, npairs):
     G = int(np.prod(s.mesh))
     Gc = s.mesh[2] * s.mesh[1] * (s.mesh[0] // 2 + 1)
@@ -285,14 +338,21 @@ def bench_ours(args, ib, torch, rank, world, local):
     # candidates: the library's own memory-bound kernels (cuFFT is a library; the pair-table
     # build, the Krylov group and the body reductions are reported in warmup_stage_ms)
     # the FP64 mesh stages (double-float transforms, FP64 pipe) are compute paths, not HBM-bound ones
-    own = {k: v for k, v in prof.items() if stage_bytes(k, s, 1) is not None and not k.startswith("fft")
-           and not k.endswith("64") and v[1] > 0}
+    # candidates: stages of the calling stream that are one own kernel each with a work model
+    # (cuFFT is a library; the table build, the Krylov group and the body reductions are
+    # composite; the near-field stages run on the second stream, where their events also
+    # time the wait for the mesh pass they overlap)
+    df_mesh = all(int(m) & (int(m) - 1) == 0 for m in s.mesh)   # FP64 mesh in double-float transforms
+    cand = ("spread", "gather", "scale", "spread64", "gather64", "scale64")
+    own = {k: v for k, v in prof.items() if k in cand and v[1] > 0}
     dominant = max(own, key=lambda k: own[k][0]) if own else "spread"
+    hbm_own = {k: v for k, v in own.items() if stage_work(k, s, 1, df_mesh)[0] == "hbm"}
+    hbm_dominant = max(hbm_own, key=lambda k: hbm_own[k][0]) if hbm_own else dominant
     dom_idx = ib.STAGES.index(dominant)
     warm_profile = {k: {"ms": round(v[0], 4), "launches": v[1]} for k, v in prof.items() if v[1]}
 
-    # timed region: only the dominant stage carries events
-    ib.ibpme_profile(1 << dom_idx)
+    # timed region: only the two reported stages carry events
+    ib.ibpme_profile((1 << dom_idx) | (1 << ib.STAGES.index(hbm_dominant)))
     launches0 = ib.ibpme_kernel_launches()
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     iters = []
@@ -310,7 +370,9 @@ def bench_ours(args, ib, torch, rank, world, local):
     launches = ib.ibpme_kernel_launches() - launches0
     step_ms = [a.elapsed_time(b) for a, b in ev]
     total_ms = float(np.sum(step_ms))
-    dom = ib.ibpme_profile_read()[dominant]
+    timed_prof = ib.ibpme_profile_read()
+    dom = timed_prof[dominant]
+    hdom = timed_prof[hbm_dominant]
     ib.ibpme_profile(0)
     if world > 1:
         t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
@@ -355,11 +417,18 @@ def bench_ours(args, ib, torch, rank, world, local):
     e2e_s = time.perf_counter() - t0
 
     peak, peak_kind = peaks()
-    traffic = measured_traffic(dominant)
-    launches_dom = dom[1]
-    avg_ms = dom[0] / launches_dom if launches_dom else float("nan")
-    alg = stage_bytes(dominant, s, npairs)
-    achieved = alg / (avg_ms / 1e3) / 1e9 if alg and launches_dom else None
+
+    def roof(stage, prof_entry):
+        bound, work, unit = stage_work(stage, s, npairs, df_mesh)
+        launches_k = prof_entry[1]
+        avg = prof_entry[0] / launches_k if launches_k else float("nan")
+        ach = work / (avg / 1e3) / 1e9 if work and launches_k else None
+        pk, pk_kind = alu_peak() if bound == "alu" else (peak, peak_kind)
+        out = {"kernel": STAGE_KERNEL.get(stage, stage), "stage": stage, "bound": bound, "achieved": ach,
+               "peak": pk, "unit": unit, "frac": (ach / pk) if ach else None, "peak_source": pk_kind,
+               ("alg_ops_per_launch" if bound == "alu" else "alg_bytes_per_launch"): work,
+               "avg_launch_ms": avg, "launches": launches_k, "traffic": measured_traffic(stage)}
+        return out
     out = {
         "metric": METRIC,
         "value": value,
@@ -376,10 +445,8 @@ def bench_ours(args, ib, torch, rank, world, local):
         "config": {"workload": WORKLOAD, "n_beads": s.n, "n_bodies": s.n_bodies, "mesh": list(s.mesh),
                    "l2": "L2 flushed (256 MB write) before every timed step, outside its events",
                    "parallelism": f"replicas x{world} (independent systems, no collective)"},
-        "roofline": {"kernel": dominant, "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": (achieved / peak) if achieved else None, "peak_source": peak_kind,
-                     "alg_bytes_per_launch": alg, "avg_launch_ms": avg_ms, "launches": launches_dom,
-                     "traffic": traffic},
+        "roofline": roof(dominant, dom),
+        "roofline_hbm_kernel": roof(hbm_dominant, hdom),
         "pme_evals_per_s": pme["evals_per_s"],
         "pme_roofline": pme["roofline"],
         "fp64_gpu": fp64,
