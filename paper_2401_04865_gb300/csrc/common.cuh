@@ -131,6 +131,7 @@ struct StencilCache {
     int n = 0, ncfg = 0;
     DevBuf start;                // int4 per bead: first node (x, y, z), configuration
     DevBuf frac;                 // double4 per bead: (first node - x / h) per axis
+    DevBuf w64;                  // FP64 window weights [n][3][P] (GB300's FP64 exp is slow: once per positions)
     // Tile bins for spreading and gathering through shared memory (many beads
     // only): beads sorted by (configuration, tile of kTileNodes^3 nodes holding
     // their first stencil node).

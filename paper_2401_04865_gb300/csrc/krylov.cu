@@ -728,7 +728,7 @@ struct Solver {
                                       (long long)c->stencils.valid, P(c->stencils.start.p), P(c->stencils.frac.p),
                                       (long long)c->stencils.tiles, (long long)c->stencils.tile_n[0],
                                       (long long)c->stencils.tile_n[1], (long long)c->stencils.tile_n[2],
-                                      P(c->stencils.tile_sorted.p), P(c->stencils.tile_key.p),
+                                      P(c->stencils.tile_sorted.p), P(c->stencils.tile_key.p), P(c->stencils.w64.p),
                                       (long long)c->near.cb_on, (long long)c->near.cb_ntasks,
                                       P(c->near.cb_flag.p), P(c->near.cb_hi.p), P(c->near.cb_lo.p),
                                       P(c->near.cb_tasks.p), P(c->near.tab32.p), P(c->near.tab_df.p),

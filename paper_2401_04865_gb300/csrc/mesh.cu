@@ -276,7 +276,7 @@ void gather_dispatch(int n, const double* xw, int nrhs, const int* cfg, const Me
 constexpr int kPairWarps = 4;   // warps per block
 
 __global__ void stencil_cache_kernel(int n, const double* __restrict__ xw, const int* __restrict__ bcfg, MeshGeom g,
-                                     int4* __restrict__ start, double4* __restrict__ frac) {
+                                     int4* __restrict__ start, double4* __restrict__ frac, double* __restrict__ w64) {
     const int b = blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= n) return;
     int s0[3];
@@ -292,6 +292,13 @@ __global__ void stencil_cache_kernel(int n, const double* __restrict__ xw, const
     }
     start[b] = make_int4(s0[0], s0[1], s0[2], bcfg ? bcfg[b] : 0);
     frac[b] = make_double4(f[0], f[1], f[2], 0.0);
+    // the FP64 windows exp(-kappa (f + l)^2), l < P, exactly as the kernels evaluate them
+    double* w = w64 + (size_t)b * 3 * g.P;
+    for (int d = 0; d < 3; ++d)
+        for (int l = 0; l < g.P; ++l) {
+            const double t = f[d] + (double)l;
+            w[d * g.P + l] = exp(-g.kappa[d] * t * t);
+        }
 }
 
 struct PairArgs {
@@ -300,10 +307,20 @@ struct PairArgs {
     int rounds;         // blocks of 32 (i, j) pairs per warp: wpb * rounds * 32 >= P^2
     const int4* start;
     const double4* frac;
+    const double* w64;  // cached FP64 windows [n][3][P] (NULL: evaluate them)
 };
 
 template <typename T>
 __device__ __forceinline__ T window(T f, double kappa) { return dexp<T>(-(T)kappa * f * f); }
+
+// Window l of axis d of a bead: the cached FP64 value (FP64 meshes), else evaluated.
+template <typename T>
+__device__ __forceinline__ T bead_window(const PairArgs& A, int bead, int d, T f, int l, bool in) {
+    if constexpr (sizeof(T) == 8) {
+        if (A.w64) return in ? A.w64[((size_t)bead * 3 + d) * A.g.P + l] : 0.0;
+    }
+    return in ? window<T>(f, A.g.kappa[d]) : (T)0;
+}
 
 // One-dimensional windows of a bead, lane l < P holding node l of each axis:
 // weight, distance (node - x) and periodic node index.
@@ -322,9 +339,9 @@ __device__ __forceinline__ Windows<T> bead_windows(const PairArgs& A, int bead, 
     Windows<T> W;
     const T fx = (T)fr.x + (T)lane, fy = (T)fr.y + (T)lane, fz = (T)fr.z + (T)lane;
     const bool in = lane < P;
-    W.wx = in ? window<T>(fx, g.kappa[0]) : (T)0;
-    W.wy = in ? window<T>(fy, g.kappa[1]) : (T)0;
-    W.wz = in ? window<T>(fz, g.kappa[2]) : (T)0;
+    W.wx = bead_window<T>(A, bead, 0, fx, lane, in);
+    W.wy = bead_window<T>(A, bead, 1, fy, lane, in);
+    W.wz = bead_window<T>(A, bead, 2, fz, lane, in);
     if (DIST) {
         W.dx = fx * (T)g.h[0];
         W.dy = fy * (T)g.h[1];
@@ -509,6 +526,7 @@ PairArgs pair_args(const MeshGeom& g, const StencilCache& b, int n) {
     A.rounds = split ? 1 : blocks32;
     A.start = b.start.as<int4>();
     A.frac = b.frac.as<double4>();
+    A.w64 = b.w64.as<double>();
     return A;
 }
 
@@ -660,9 +678,9 @@ spread_tiles_kernel(TileArgs TA, int n, const double* __restrict__ q, T* __restr
             const double4 fr = A.frac[bead];
             const bool in = lane < P;
             const T fx = (T)fr.x + (T)lane, fy = (T)fr.y + (T)lane, fz = (T)fr.z + (T)lane;
-            const T wx = in ? window<T>(fx, g.kappa[0]) : (T)0;
-            const T wy = in ? window<T>(fy, g.kappa[1]) : (T)0;
-            const T wz_l = in ? window<T>(fz, g.kappa[2]) : (T)0;
+            const T wx = bead_window<T>(A, bead, 0, fx, lane, in);
+            const T wy = bead_window<T>(A, bead, 1, fy, lane, in);
+            const T wz_l = bead_window<T>(A, bead, 2, fz, lane, in);
             const int lx = st.x - ox, ly = st.y - oy, lz = st.z - oz;   // in [0, kTileNodes)
             T qc[NR];
 #pragma unroll
@@ -813,9 +831,9 @@ gather_tiles_kernel(TileArgs TA, int n, const T* __restrict__ grid, double* __re
             const double4 fr = A.frac[bead];
             const bool in = lane < P;
             const T fx = (T)fr.x + (T)lane, fy = (T)fr.y + (T)lane, fz = (T)fr.z + (T)lane;
-            const T wx_l = in ? window<T>(fx, g.kappa[0]) : (T)0;
-            const T wy_l = in ? window<T>(fy, g.kappa[1]) : (T)0;
-            const T wz_l = in ? window<T>(fz, g.kappa[2]) : (T)0;
+            const T wx_l = bead_window<T>(A, bead, 0, fx, lane, in);
+            const T wy_l = bead_window<T>(A, bead, 1, fy, lane, in);
+            const T wz_l = bead_window<T>(A, bead, 2, fz, lane, in);
             const T dx_l = fx * (T)g.h[0], dy_l = fy * (T)g.h[1], dz_l = fz * (T)g.h[2];
             const int lx = st.x - ox, ly = st.y - oy, lz = st.z - oz;
             T sp[NR], ex[NR], ey[NR], ez[NR];
@@ -891,6 +909,7 @@ TileArgs tile_args(const MeshGeom& g, const StencilCache& b, int n) {
     TA.A.rounds = (g.P * g.P + 31) / 32;
     TA.A.start = b.start.as<int4>();
     TA.A.frac = b.frac.as<double4>();
+    TA.A.w64 = b.w64.as<double>();
     TA.sorted = b.tile_sorted.as<int>();
     TA.key = b.tile_key.as<int>();
     for (int d = 0; d < 3; ++d) TA.tn[d] = b.tile_n[d];
@@ -1194,7 +1213,8 @@ const StencilCache* stencil_cache(ibpme_ctx* c, int n, const double* xw) {
     b.valid = false;
     int4* start = static_cast<int4*>(b.start.ensure(sizeof(int4) * n));
     double4* frac = static_cast<double4*>(b.frac.ensure(sizeof(double4) * n));
-    stencil_cache_kernel<<<div_up(n, 256), 256, 0, c->stream>>>(n, xw, c->bcfg, g, start, frac);
+    double* w64 = static_cast<double*>(b.w64.ensure(sizeof(double) * 3 * (size_t)g.P * n));
+    stencil_cache_kernel<<<div_up(n, 256), 256, 0, c->stream>>>(n, xw, c->bcfg, g, start, frac, w64);
     IBP_CHECK_LAUNCH();
     // tile bins when one warp per bead already fills the GPU and a region of
     // E^3 nodes does not wrap onto itself
