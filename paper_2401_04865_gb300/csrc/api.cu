@@ -449,6 +449,7 @@ IBP_API ibpme_status pme_spread(ibpme_ctx* c, int n, const double* x, const doub
         double* xw = static_cast<double*>(c->xw.ensure(sizeof(double) * 3 * (n ? n : 1)));
         wrap_positions(c, n, dx, xw);
         c->bodies_current = false;
+        c->near.fp_pre_valid = false;
         const bool mixed = c->p.precision == IBPME_MIXED;
         const size_t gb = (mixed ? sizeof(float) : sizeof(double)) * (size_t)c->geom.G * nrhs;
         if (mixed)
@@ -481,6 +482,7 @@ IBP_API ibpme_status pme_field(ibpme_ctx* c, int n, const double* x, const doubl
         double* xw = static_cast<double*>(c->xw.ensure(sizeof(double) * 3 * n));
         wrap_positions(c, n, dx, xw);
         c->bodies_current = false;   // beads without bodies: every pair goes through the table
+        c->near.fp_pre_valid = false;
         pme_apply(c, n, xw, dq, nrhs, c->p.precision, static_cast<double*>(op.dev), static_cast<double*>(oe.dev),
                   false);
         finish_out(c, op);
@@ -508,7 +510,9 @@ void prepare_bodies(ibpme_ctx* c, int n, const ibpme_bodies* bodies, const doubl
     d.body_offsets = static_cast<const int*>(stage_in(c, bodies->body_offsets, sizeof(int) * (nb + 1), c->st_off));
     d.X = static_cast<const double*>(stage_in(c, bodies->X, sizeof(double) * 3 * nb, c->st_X));
     d.Q = static_cast<const double*>(stage_in(c, bodies->Q, sizeof(double) * nb, c->st_Q));
-    bodies_upload(c, n, &d, xw, ncfg, nullptr, cfg_bodies);
+    // one synchronisation for the body structure and the position fingerprint
+    const unsigned long long h = near_prefetch(c, n, xw, d.body_offsets, nb + 1);
+    bodies_upload(c, n, &d, xw, ncfg, nullptr, cfg_bodies, &h);
 }
 
 // The configuration split of a batched call, undone when the call ends so that

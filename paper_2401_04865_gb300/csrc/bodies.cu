@@ -314,16 +314,25 @@ __global__ void bd_bead_kernel(int n, const int* __restrict__ bead_body, const d
 }  // namespace
 
 void bodies_upload(ibpme_ctx* c, int n, const ibpme_bodies* b, const double* xw, int ncfg, const int* cfg_beads,
-                   const int* cfg_bodies) {
+                   const int* cfg_bodies, const unsigned long long* off_hash) {
     BodyData& bd = c->bodies;
     cudaStream_t s = c->stream;
     const int nb = b->n_bodies;
-    std::vector<int> off(nb + 1);
-    IBP_CUDA(cudaMemcpyAsync(off.data(), b->body_offsets, sizeof(int) * (nb + 1), cudaMemcpyDeviceToHost, s));
-    IBP_CUDA(cudaStreamSynchronize(s));
-    if (off[0] != 0 || off[nb] != n) fail(IBPME_ERR_ARG, "body_offsets must start at 0 and end at n = %d", n);
-    for (int i = 0; i < nb; ++i)
-        if (off[i + 1] <= off[i]) fail(IBPME_ERR_ARG, "body %d is empty or offsets decrease", i);
+    // the same offsets as the last (validated) upload, by their hash: no read-back
+    const bool known = off_hash && bd.off_hash != 0 && *off_hash == bd.off_hash && bd.host_n == n &&
+                       (int)bd.host_off.size() == nb + 1;
+    std::vector<int> off;
+    if (known) {
+        off = bd.host_off;
+    } else {
+        off.resize(nb + 1);
+        IBP_CUDA(cudaMemcpyAsync(off.data(), b->body_offsets, sizeof(int) * (nb + 1), cudaMemcpyDeviceToHost, s));
+        IBP_CUDA(cudaStreamSynchronize(s));
+        if (off[0] != 0 || off[nb] != n) fail(IBPME_ERR_ARG, "body_offsets must start at 0 and end at n = %d", n);
+        for (int i = 0; i < nb; ++i)
+            if (off[i + 1] <= off[i]) fail(IBPME_ERR_ARG, "body %d is empty or offsets decrease", i);
+        bd.off_hash = 0;   // set below once the structure is recorded
+    }
     // configurations: contiguous ranges of bodies (and hence of beads)
     std::vector<int> cb(ncfg + 1), cbe(ncfg + 1);
     if (ncfg == 1 && !cfg_bodies) {
@@ -406,6 +415,7 @@ void bodies_upload(ibpme_ctx* c, int n, const ibpme_bodies* b, const double* xw,
         bd.host_n = n;
         ++bd.version;
     }
+    bd.off_hash = off_hash ? *off_hash : 0;
     bd.X.ensure(sizeof(double) * 3 * nb);
     bd.Q.ensure(sizeof(double) * nb);
     IBP_CUDA(cudaMemcpyAsync(bd.X.p, b->X, sizeof(double) * 3 * nb, cudaMemcpyDeviceToDevice, s));

@@ -193,6 +193,12 @@ struct NearList {
     DevBuf fp_dev;                 // fingerprint of the positions + non-finite flag
     unsigned long long fp = 0;     // fingerprint of the positions the table was built for
     bool fp_valid = false;
+    // fingerprint already fetched by the entry point (with the body-structure hash, one
+    // synchronisation for both), consumed by the next near_build for these positions
+    bool fp_pre_valid = false;
+    unsigned long long fp_pre[2] = {0, 0};
+    int fp_pre_n = -1;
+    const double* fp_pre_xw = nullptr;
     int ncfg = 1;
     // Compact bodies: multi-bead bodies within min(r_c, L/4) of their centre.
     // Their intra-body pairs are left out of the table and evaluated directly
@@ -241,6 +247,7 @@ struct BodyData {
     std::vector<int> host_off, host_cfg;   // structure of the last upload (to skip rebuilding the lists)
     int host_n = -1;
     unsigned long long version = 0;        // changes whenever the body structure changes
+    unsigned long long off_hash = 0;       // hash of the offsets of the last upload (0: unknown)
 };
 
 struct Krylov;   // krylov.cu
@@ -355,6 +362,10 @@ namespace ibp {
 void scan_counts(const int* in, long long* out, int n, DevBuf& tmp, cudaStream_t s);
 void near_setup(ibpme_ctx* c);   // tabulates the pair kernel (once per context)
 void near_build(ibpme_ctx* c, int n, const double* xw, bool need_grad);
+// Position fingerprint of xw and a hash of the noff body offsets (device), fetched with one
+// synchronisation; the fingerprint is kept for the next near_build of these positions.
+// Returns the offsets hash.
+unsigned long long near_prefetch(ibpme_ctx* c, int n, const double* xw, const int* off, int noff);
 // overwrite; fp32: FP32 pair values and charges (the mixed solve's inner operator)
 void near_apply(ibpme_ctx* c, int n, const double* q, int nrhs, double* psi_r, bool fp32 = false);
 void near_field(ibpme_ctx* c, int n, const double* xw, const double* q, int nrhs, double* E_r);  // overwrite
@@ -385,8 +396,10 @@ void* pinned_host(ibpme_ctx* c, size_t bytes);
 
 // ---- bodies.cu ----
 // cfg_beads / cfg_bodies: host [ncfg+1] offsets of the configurations (NULL for one)
+// off_hash: hash of the body offsets from near_prefetch, or NULL (read the offsets back)
 void bodies_upload(ibpme_ctx* c, int n, const ibpme_bodies* b, const double* xw, int ncfg = 1,
-                   const int* cfg_beads = nullptr, const int* cfg_bodies = nullptr);
+                   const int* cfg_beads = nullptr, const int* cfg_bodies = nullptr,
+                   const unsigned long long* off_hash = nullptr);
 void body_dipoles(ibpme_ctx* c, int n, const double* q, int nrhs, double* S);
 void bead_forces(ibpme_ctx* c, int n, const double* q, const double* E0, const double* E, double* f);
 void body_reduce_force_torque(ibpme_ctx* c, int n, const double* f, double* F, double* L);

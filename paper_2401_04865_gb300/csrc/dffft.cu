@@ -120,9 +120,11 @@ __device__ __forceinline__ void stockham_pass(float4* buf, int ls, int n, int Ns
         const float4* x = buf + line * ls;
 #pragma unroll
         for (int r = 0; r < R; ++r) v[q][r] = load_c(x[sw(j + r * nb)]);
-        const int step = k * (n / (Ns * R));
+        if (Ns > 1) {   // the first pass (Ns = 1) has k = 0: every twiddle is 1
+            const int step = k * (n / (Ns * R));
 #pragma unroll
-        for (int r = 1; r < R; ++r) v[q][r] = cmul(v[q][r], load_c(tw[r * step]), INV);
+            for (int r = 1; r < R; ++r) v[q][r] = cmul(v[q][r], load_c(tw[r * step]), INV);
+        }
         if (R == 8) dft8<INV>(v[q]);
         else if (R == 4) dft4<INV>(v[q]);
         else dft2<INV>(v[q]);

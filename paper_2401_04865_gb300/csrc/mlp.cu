@@ -765,6 +765,7 @@ IBP_API ibpme_status ibpme_features(ibpme_ctx* c, int n, const double* x, const 
         if (!dev_ok) fail(IBPME_ERR_ARG, "ibpme_features takes device pointers");
         double* xw = static_cast<double*>(c->xw.ensure(sizeof(double) * 3 * n));
         wrap_positions(c, n, x, xw);
+        c->near.fp_pre_valid = false;
         bodies_upload(c, n, bodies, xw);
         compute_features(c, n, xw, E0, nrhs, feat, c->ml_scratch, c->ml_scales);
         if (q && target) {

@@ -163,6 +163,23 @@ __global__ void fingerprint_kernel(long long m, const double* __restrict__ xw, c
     }
 }
 
+// Order-dependent 64-bit hash of m ints (one block): sum of mix64(value ^ mix64(index)).
+__global__ void hash_ints_kernel(const int* __restrict__ a, int m, unsigned long long* __restrict__ out) {
+    __shared__ unsigned long long sh[32];
+    unsigned long long acc = 0;
+    for (int i = threadIdx.x; i < m; i += blockDim.x)
+        acc += mix64((unsigned long long)(unsigned)a[i] ^ mix64(0xA24BAED4963EE407ull + (unsigned long long)i));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned long long t = mix64((unsigned long long)m);
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += sh[w];
+        *out = t | 1ull;   // never 0 (0 means unknown)
+    }
+}
+
 __global__ void cell_count_kernel(int n, const double* __restrict__ xw, PairConst k, const int* __restrict__ bcfg,
                                   int* __restrict__ cell_of, int* __restrict__ cell_count) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -1238,25 +1255,56 @@ void compact_field(ibpme_ctx* c, int n, const double* q, int nrhs, double* E_r) 
 
 }  // namespace
 
+unsigned long long near_prefetch(ibpme_ctx* c, int n, const double* xw, const int* off, int noff) {
+    NearList& nl = c->near;
+    cudaStream_t s = c->stream;
+    unsigned long long* fp = static_cast<unsigned long long*>(nl.fp_dev.ensure(3 * sizeof(unsigned long long)));
+    IBP_CUDA(cudaMemsetAsync(fp, 0, 3 * sizeof(unsigned long long), s));
+    if (n > 0) {
+        fingerprint_kernel<<<div_up(3LL * n, 256) < 256 ? div_up(3LL * n, 256) : 256, 256, 0, s>>>(
+            3LL * n, xw, nullptr, fp, reinterpret_cast<int*>(fp + 1));
+        IBP_CHECK_LAUNCH();
+    }
+    hash_ints_kernel<<<1, 256, 0, s>>>(off, noff, fp + 2);
+    IBP_CHECK_LAUNCH();
+    unsigned long long* h = static_cast<unsigned long long*>(pinned_host(c, 3 * sizeof(unsigned long long)));
+    IBP_CUDA(cudaMemcpyAsync(h, fp, 3 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
+    IBP_CUDA(cudaStreamSynchronize(s));
+    nl.fp_pre[0] = h[0];
+    nl.fp_pre[1] = (unsigned long long)*reinterpret_cast<int*>(h + 1);
+    nl.fp_pre_n = n;
+    nl.fp_pre_xw = xw;
+    nl.fp_pre_valid = true;
+    return h[2];
+}
+
 void near_build(ibpme_ctx* c, int n, const double* xw, bool need_grad) {
     (void)need_grad;   // the table always carries the gradient factors
     NearList& nl = c->near;
     cudaStream_t s = c->stream;
     ProfScope ps(ST_NEAR_BUILD, s);
     // positions unchanged since the last build (solve -> forces -> BD step): reuse the table
-    unsigned long long* fp = static_cast<unsigned long long*>(nl.fp_dev.ensure(2 * sizeof(unsigned long long)));
-    int* bad = reinterpret_cast<int*>(fp + 1);
-    IBP_CUDA(cudaMemsetAsync(fp, 0, 2 * sizeof(unsigned long long), s));
-    if (n > 0) {
-        fingerprint_kernel<<<div_up(3LL * n, 256) < 256 ? div_up(3LL * n, 256) : 256, 256, 0, s>>>(3LL * n, xw,
-                                                                                                  c->bcfg, fp, bad);
-        IBP_CHECK_LAUNCH();
+    unsigned long long print = 0;
+    if (nl.fp_pre_valid && nl.fp_pre_n == n && nl.fp_pre_xw == xw) {   // fetched by the entry point
+        nl.fp_pre_valid = false;
+        if (nl.fp_pre[1] != 0) fail(IBPME_ERR_NONFINITE, "non-finite bead position");
+        print = nl.fp_pre[0];
+    } else {
+        nl.fp_pre_valid = false;
+        unsigned long long* fp = static_cast<unsigned long long*>(nl.fp_dev.ensure(3 * sizeof(unsigned long long)));
+        int* bad = reinterpret_cast<int*>(fp + 1);
+        IBP_CUDA(cudaMemsetAsync(fp, 0, 2 * sizeof(unsigned long long), s));
+        if (n > 0) {
+            fingerprint_kernel<<<div_up(3LL * n, 256) < 256 ? div_up(3LL * n, 256) : 256, 256, 0, s>>>(
+                3LL * n, xw, c->bcfg, fp, bad);
+            IBP_CHECK_LAUNCH();
+        }
+        unsigned long long* hfp = static_cast<unsigned long long*>(pinned_host(c, 2 * sizeof(unsigned long long)));
+        IBP_CUDA(cudaMemcpyAsync(hfp, fp, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
+        IBP_CUDA(cudaStreamSynchronize(s));
+        if (*reinterpret_cast<int*>(hfp + 1) != 0) fail(IBPME_ERR_NONFINITE, "non-finite bead position");
+        print = hfp[0];
     }
-    unsigned long long* hfp = static_cast<unsigned long long*>(pinned_host(c, 2 * sizeof(unsigned long long)));
-    IBP_CUDA(cudaMemcpyAsync(hfp, fp, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
-    IBP_CUDA(cudaStreamSynchronize(s));
-    if (*reinterpret_cast<int*>(hfp + 1) != 0) fail(IBPME_ERR_NONFINITE, "non-finite bead position");
-    const unsigned long long print = hfp[0];
     // compact bodies whenever the call has bodies (their structure is part of the cache key)
     const BodyData& bd = c->bodies;
     const bool want_cb = c->bodies_current && bd.nmb > 0 && bd.host_n == n && make_const(c).K > 0 &&
