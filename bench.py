@@ -571,9 +571,11 @@ def bench_polarizability(args, ib, torch, rank, world, local):
         torch.cuda.synchronize()
         for i in range(args.steps):
             step(args.warmup + i)          # new positions and the L2 flush, outside the events
+            torch.cuda.nvtx.range_push("pol_timed")   # lets ncu capture exactly the timed batches
             ev[i][0].record(stream)
             stats.append(solve_all())
             ev[i][1].record(stream)
+            torch.cuda.nvtx.range_pop()
         torch.cuda.synchronize()
     launches = ib.ibpme_kernel_launches() - launches0
     total_ms = float(np.sum([e0.elapsed_time(e1) for e0, e1 in ev]))

@@ -33,11 +33,51 @@ __global__ void rel_kernel(int n, const double* __restrict__ xw, const int* __re
     rel[3 * i + 2] = d2 - L2 * floor(d2 * iL2 + 0.5);
 }
 
-__global__ void dipole_kernel(int nb, int n, int nrhs, const int* __restrict__ off, const double* __restrict__ rel,
+// Block roles of the per-body kernels (kBodyThreads threads per block): the first
+// body_ion_blocks(nb) blocks take one body per thread and handle the single-bead bodies
+// (ions, most of the bodies of an electrolyte); the others take one multi-bead body per
+// warp from the list mb_body.  Returns false for threads without work; the warp role
+// returns warp-uniformly.
+constexpr int kBodyThreads = 256;
+
+__host__ __device__ __forceinline__ int body_ion_blocks(int nb) { return (nb + kBodyThreads - 1) / kBodyThreads; }
+
+__device__ __forceinline__ bool body_role(int nb, int nmb, const int* __restrict__ mb_body, const int* __restrict__ off,
+                                          int& body, int& lane, bool& ion) {
+    const int ib = body_ion_blocks(nb);
+    if ((int)blockIdx.x < ib) {
+        ion = true;
+        lane = 0;
+        body = (int)blockIdx.x * kBodyThreads + (int)threadIdx.x;
+        return body < nb && off[body + 1] - off[body] == 1;
+    }
+    ion = false;
+    lane = threadIdx.x & 31;
+    const int w = (((int)blockIdx.x - ib) * kBodyThreads + (int)threadIdx.x) >> 5;
+    if (w >= nmb) return false;
+    body = mb_body[w];
+    return true;
+}
+
+int body_grid(int nb, int nmb) { return body_ion_blocks(nb) + div_up((long long)nmb * 32, kBodyThreads); }
+
+__global__ void dipole_kernel(int nb, int nmb, const int* __restrict__ mb_body, int n, int nrhs,
+                              const int* __restrict__ off, const double* __restrict__ rel,
                               const double* __restrict__ q, double* __restrict__ S) {
-    const int b = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int lane = threadIdx.x & 31;
-    if (b >= nb) return;
+    int b, lane;
+    bool ion;
+    if (!body_role(nb, nmb, mb_body, off, b, lane, ion)) return;
+    if (ion) {
+        const int j = off[b];
+        for (int r = 0; r < nrhs; ++r) {
+            const double qq = q[(size_t)r * n + j];
+            double* o = S + ((size_t)r * nb + b) * 3;
+            o[0] = rel[3 * j + 0] * qq;
+            o[1] = rel[3 * j + 1] * qq;
+            o[2] = rel[3 * j + 2] * qq;
+        }
+        return;
+    }
     for (int r = 0; r < nrhs; ++r) {
         double sx = 0, sy = 0, sz = 0;
         for (int j = off[b] + lane; j < off[b + 1]; j += 32) {
@@ -65,11 +105,22 @@ __global__ void force_kernel(int n, const double* __restrict__ q, const double* 
     f[i] = q[i / 3] * (E0[i % 3] + E[i]);
 }
 
-__global__ void force_torque_kernel(int nb, const int* __restrict__ off, const double* __restrict__ rel,
-                                    const double* __restrict__ f, double* __restrict__ F, double* __restrict__ L) {
-    const int b = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int lane = threadIdx.x & 31;
-    if (b >= nb) return;
+__global__ void force_torque_kernel(int nb, int nmb, const int* __restrict__ mb_body, const int* __restrict__ off,
+                                    const double* __restrict__ rel, const double* __restrict__ f,
+                                    double* __restrict__ F, double* __restrict__ L) {
+    int b, lane;
+    bool ion;
+    if (!body_role(nb, nmb, mb_body, off, b, lane, ion)) return;
+    if (ion) {
+        const int j = off[b];
+        const double ax = f[3 * j], ay = f[3 * j + 1], az = f[3 * j + 2];
+        const double rx = rel[3 * j], ry = rel[3 * j + 1], rz = rel[3 * j + 2];
+        F[3 * b] = ax; F[3 * b + 1] = ay; F[3 * b + 2] = az;
+        L[3 * b] = ry * az - rz * ay;
+        L[3 * b + 1] = rz * ax - rx * az;
+        L[3 * b + 2] = rx * ay - ry * ax;
+        return;
+    }
     double fx = 0, fy = 0, fz = 0, lx = 0, ly = 0, lz = 0;
     for (int j = off[b] + lane; j < off[b + 1]; j += 32) {
         const double ax = f[3 * j], ay = f[3 * j + 1], az = f[3 * j + 2];
@@ -89,14 +140,22 @@ __global__ void force_torque_kernel(int nb, const int* __restrict__ off, const d
 
 // Per-body energy contribution Q_i Psi_i - S_i . E0 with
 // Psi_i - Psi_0,i = mean_j (psi_ij - r_ij . E0) (Eq. beadpot1) and Psi_0,i = -X_i . E0.
-__global__ void energy_body_kernel(int nb, const int* __restrict__ off, const double* __restrict__ rel,
+__global__ void energy_body_kernel(int nb, int nmb, const int* __restrict__ mb_body, const int* __restrict__ off,
+                                   const double* __restrict__ rel,
                                    const double* __restrict__ q, const double* __restrict__ psi,
                                    const double* __restrict__ E0, const double* __restrict__ X,
                                    const double* __restrict__ Q, double* __restrict__ contrib) {
-    const int b = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int lane = threadIdx.x & 31;
-    if (b >= nb) return;
+    int b, lane;
+    bool ion;
+    if (!body_role(nb, nmb, mb_body, off, b, lane, ion)) return;
     const double e0 = E0[0], e1 = E0[1], e2 = E0[2];
+    if (ion) {
+        const int j = off[b];
+        const double rE = rel[3 * j] * e0 + rel[3 * j + 1] * e1 + rel[3 * j + 2] * e2;
+        const double Psi = (psi[j] - rE) / 1.0 - (X[3 * b] * e0 + X[3 * b + 1] * e1 + X[3 * b + 2] * e2);
+        contrib[b] = Q[b] * Psi - q[j] * rE;
+        return;
+    }
     double pr = 0, sE = 0;
     for (int j = off[b] + lane; j < off[b + 1]; j += 32) {
         const double rE = rel[3 * j] * e0 + rel[3 * j + 1] * e1 + rel[3 * j + 2] * e2;
@@ -207,41 +266,29 @@ __device__ void rotation_matrix(const double* th, double* R) {
 }
 
 // One warp per body: F, L, J; lane 0 draws the noise and forms U, Omega, R.
-__global__ void bd_body_kernel(int nb, const int* __restrict__ off, const double* __restrict__ rel,
+// Box-Muller pair t of body b: Philox counter (body, step, t); (rad cos, rad sin).
+__device__ __forceinline__ void bd_normals(int b, const BdConst& bc, unsigned t, double& rad, double& ang) {
+    const uint2 key = make_uint2((unsigned)(bc.seed & 0xffffffffull), (unsigned)(bc.seed >> 32));
+    const uint4 w = philox4x32_10(make_uint4((unsigned)b, bc.step, t, 0x1B5EEDu), key);
+    const double u1 = ((double)w.x + 0.5) * 2.3283064365386963e-10;
+    const double u2 = ((double)w.y + 0.5) * 2.3283064365386963e-10;
+    rad = sqrt(-2.0 * log(u1));
+    ang = 6.283185307179586476925286766559 * u2;
+}
+
+__global__ void bd_body_kernel(int nb, int nmb, const int* __restrict__ mb_body, const int* __restrict__ off,
+                               const double* __restrict__ rel,
                                const double* __restrict__ f, const double* __restrict__ X, BdConst bc,
                                double* __restrict__ X_out, double* __restrict__ Rm) {
-    const int b = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int lane = threadIdx.x & 31;
-    if (b >= nb) return;
-    const int Ni = off[b + 1] - off[b];
-    // noise: Box-Muller pair t from Philox counter (body, step, t) on lane t, in
-    // parallel; an ion needs z0..z2 only (pairs 0 and 1, the cosine of pair 1)
-    double za = 0.0, zb = 0.0;
-    if (lane < (Ni > 1 ? 3 : 2)) {
-        const uint2 key = make_uint2((unsigned)(bc.seed & 0xffffffffull), (unsigned)(bc.seed >> 32));
-        const uint4 w = philox4x32_10(make_uint4((unsigned)b, bc.step, (unsigned)lane, 0x1B5EEDu), key);
-        const double u1 = ((double)w.x + 0.5) * 2.3283064365386963e-10;
-        const double u2 = ((double)w.y + 0.5) * 2.3283064365386963e-10;
-        const double rad = sqrt(-2.0 * log(u1));
-        const double ang = 6.283185307179586476925286766559 * u2;
-        if (Ni > 1 || lane == 0) {
-            double sn, cs;
-            sincos(ang, &sn, &cs);
-            za = rad * cs;
-            zb = rad * sn;
-        } else {
-            za = rad * cos(ang);
-        }
-    }
-    double z[6];
-#pragma unroll
-    for (int i = 0; i < 3; ++i) {
-        z[2 * i] = __shfl_sync(0xffffffffu, za, i);
-        z[2 * i + 1] = __shfl_sync(0xffffffffu, zb, i);
-    }
-    double F[3] = {0, 0, 0}, L[3] = {0, 0, 0}, J[6] = {0, 0, 0, 0, 0, 0};
-    if (Ni == 1) {   // an ion: its force, no torque (r = 0), no rotation
-        if (lane != 0) return;
+    int b, lane;
+    bool ion;
+    if (!body_role(nb, nmb, mb_body, off, b, lane, ion)) return;
+    if (ion) {   // translation only (r = 0, no rotation): z0, z1 from pair 0, z2 the cosine of pair 1
+        double rad0, ang0, rad1, ang1, sn, cs;
+        bd_normals(b, bc, 0u, rad0, ang0);
+        bd_normals(b, bc, 1u, rad1, ang1);
+        sincos(ang0, &sn, &cs);
+        const double z[3] = {rad0 * cs, rad0 * sn, rad1 * cos(ang1)};
         const int j = off[b];
         const double mt = 1.0 / bc.gamma;
         const double st = sqrt(2.0 * bc.kT * bc.dt * mt);
@@ -250,6 +297,24 @@ __global__ void bd_body_kernel(int nb, const int* __restrict__ off, const double
         for (int i = 0; i < 9; ++i) Rm[9 * b + i] = R[i];
         return;
     }
+    const int Ni = off[b + 1] - off[b];
+    // noise: Box-Muller pair t from Philox counter (body, step, t) on lane t, in
+    // parallel; an ion needs z0..z2 only (pairs 0 and 1, the cosine of pair 1)
+    double za = 0.0, zb = 0.0;
+    if (lane < 3) {   // pair t on lane t
+        double rad, ang, sn, cs;
+        bd_normals(b, bc, (unsigned)lane, rad, ang);
+        sincos(ang, &sn, &cs);
+        za = rad * cs;
+        zb = rad * sn;
+    }
+    double z[6];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        z[2 * i] = __shfl_sync(0xffffffffu, za, i);
+        z[2 * i + 1] = __shfl_sync(0xffffffffu, zb, i);
+    }
+    double F[3] = {0, 0, 0}, L[3] = {0, 0, 0}, J[6] = {0, 0, 0, 0, 0, 0};
     for (int j = off[b] + lane; j < off[b + 1]; j += 32) {
         const double rx = rel[3 * j], ry = rel[3 * j + 1], rz = rel[3 * j + 2];
         const double ax = f[3 * j], ay = f[3 * j + 1], az = f[3 * j + 2];
@@ -431,8 +496,8 @@ void bodies_upload(ibpme_ctx* c, int n, const ibpme_bodies* b, const double* xw,
 void body_dipoles(ibpme_ctx* c, int n, const double* q, int nrhs, double* S) {
     ProfScope ps(ST_BODIES, c->stream);
     BodyData& bd = c->bodies;
-    dipole_kernel<<<div_up((long long)bd.nb * 32, 128), 128, 0, c->stream>>>(bd.nb, n, nrhs, bd.off.as<int>(),
-                                                                              bd.rel.as<double>(), q, S);
+    dipole_kernel<<<body_grid(bd.nb, bd.nmb), kBodyThreads, 0, c->stream>>>(
+        bd.nb, bd.nmb, bd.mb_body.as<int>(), n, nrhs, bd.off.as<int>(), bd.rel.as<double>(), q, S);
     IBP_CHECK_LAUNCH();
 }
 
@@ -446,8 +511,8 @@ void body_reduce_force_torque(ibpme_ctx* c, int n, const double* f, double* F, d
     ProfScope ps(ST_BODIES, c->stream);
     (void)n;
     BodyData& bd = c->bodies;
-    force_torque_kernel<<<div_up((long long)bd.nb * 32, 128), 128, 0, c->stream>>>(bd.nb, bd.off.as<int>(),
-                                                                                    bd.rel.as<double>(), f, F, L);
+    force_torque_kernel<<<body_grid(bd.nb, bd.nmb), kBodyThreads, 0, c->stream>>>(
+        bd.nb, bd.nmb, bd.mb_body.as<int>(), bd.off.as<int>(), bd.rel.as<double>(), f, F, L);
     IBP_CHECK_LAUNCH();
 }
 
@@ -456,8 +521,9 @@ void body_energy(ibpme_ctx* c, int n, const double* q, const double* psi, const 
     (void)n;
     BodyData& bd = c->bodies;
     double* contrib = static_cast<double*>(bd.scratch.ensure(sizeof(double) * (bd.nb + 1)));
-    energy_body_kernel<<<div_up((long long)bd.nb * 32, 128), 128, 0, c->stream>>>(
-        bd.nb, bd.off.as<int>(), bd.rel.as<double>(), q, psi, E0, bd.X.as<double>(), bd.Q.as<double>(), contrib);
+    energy_body_kernel<<<body_grid(bd.nb, bd.nmb), kBodyThreads, 0, c->stream>>>(
+        bd.nb, bd.nmb, bd.mb_body.as<int>(), bd.off.as<int>(), bd.rel.as<double>(), q, psi, E0, bd.X.as<double>(),
+        bd.Q.as<double>(), contrib);
     IBP_CHECK_LAUNCH();
     half_sum_kernel<<<1, 1024, 0, c->stream>>>(bd.nb, contrib, U);
     IBP_CHECK_LAUNCH();
@@ -476,8 +542,9 @@ void bd_step(ibpme_ctx* c, int n, const double* xw, const double* f, const ibpme
         nl.cell_beads.as<int>(), bd.bead_body.as<int>(), c->a, p->gamma / (2.0 * p->dt), f, ftot);
     IBP_CHECK_LAUNCH();
     BdConst bc{p->dt, p->gamma, p->kT, p->seed, (unsigned)(p->step & 0xffffffffLL)};
-    bd_body_kernel<<<div_up((long long)bd.nb * 32, 128), 128, 0, s>>>(bd.nb, bd.off.as<int>(), bd.rel.as<double>(),
-                                                                       ftot, bd.X.as<double>(), bc, X_out, Rm);
+    bd_body_kernel<<<body_grid(bd.nb, bd.nmb), kBodyThreads, 0, s>>>(bd.nb, bd.nmb, bd.mb_body.as<int>(),
+                                                                     bd.off.as<int>(), bd.rel.as<double>(), ftot,
+                                                                     bd.X.as<double>(), bc, X_out, Rm);
     IBP_CHECK_LAUNCH();
     bd_bead_kernel<<<div_up(n, 256), 256, 0, s>>>(n, bd.bead_body.as<int>(), bd.rel.as<double>(), X_out, Rm, x_out);
     IBP_CHECK_LAUNCH();

@@ -6,11 +6,12 @@
 // is bound by that FP64 pipe.  Here each value is carried as an unevaluated sum
 // of two floats (hi + lo, about 48 significant bits; error-free transformations
 // of Dekker and Knuth: two-sum, and two-product with a fused multiply-add), so
-// the butterflies run on the FP32 pipes.  The transform is a radix-2 complex FFT
+// the butterflies run on the FP32 pipes.  The transforms are Stockham passes
+// (radix 3 when 3 divides the size, radix 8, then radix 4 or 2) in shared memory
 // along x (two real lines packed into one complex line), y and z on the half
-// spectrum (power-of-two sizes); the Green's-function scaling of the FP64 table
-// is fused between the forward and inverse z passes, and the real lines come
-// back as FP64.  Sizes that are not powers of two use cuFFT.
+// spectrum; the Green's-function scaling of the FP64 table is fused between the
+// forward and inverse z passes, and the real lines come back as FP64.  Sizes
+// 2^k and 3 2^k (16 to 1024); other sizes use cuFFT.
 #include "common.cuh"
 #include "dfloat.cuh"
 
@@ -102,19 +103,40 @@ __device__ __forceinline__ void dft8(dfc* v) {
     }
 }
 
-// One Stockham pass of radix R over the block's lines (lines x n = kDfPoints) in
+// Radix-3 DFT: t1 = v1 + v2, t2 = v0 - t1/2, t3 = -+i (sqrt(3)/2)(v1 - v2);
+// y0 = v0 + t1, y1 = t2 + t3, y2 = t2 - t3.
+template <bool INV>
+__device__ __forceinline__ void dft3(dfc* v) {
+    constexpr float ch = 0.86602540f;
+    constexpr float cl = (float)(0.86602540378443864676 - (double)ch);
+    const df c = {ch, cl};
+    const dfc t1 = cadd(v[1], v[2]);
+    const dfc t2 = {df_add(v[0].re, df_neg(df_half(t1.re))), df_add(v[0].im, df_neg(df_half(t1.im)))};
+    const dfc d = csub(v[1], v[2]);
+    // forward: -i c d = c (d.im, -d.re); inverse: +i c d = c (-d.im, d.re)
+    const dfc t3 = INV ? dfc{df_neg(df_mul(d.im, c)), df_mul(d.re, c)} : dfc{df_mul(d.im, c), df_neg(df_mul(d.re, c))};
+    v[0] = cadd(v[0], t1);
+    v[1] = cadd(t2, t3);
+    v[2] = csub(t2, t3);
+}
+
+// One Stockham pass of radix R over the block's lines (pts = lines x n points) in
 // shared memory, natural order in and out: butterfly j of a line takes the points
 // j + r n/R, applies the twiddles exp(-+2 pi i k r / (Ns R)), k = j mod Ns, and
 // writes its R outputs to (j - k) R + k + r Ns.  tw[t] = exp(-2 pi i t / n), t < n.
+// A thread holds all its butterflies in registers between the loads and the stores.
 template <int R, bool INV>
-__device__ __forceinline__ void stockham_pass(float4* buf, int ls, int n, int Ns, const float4* __restrict__ tw) {
-    constexpr int per = 8 / R;   // butterflies per thread: kDfPoints / R / kDfThreads
-    const int nb = n / R;
+__device__ __forceinline__ void stockham_pass(float4* buf, int ls, int n, int pts, int Ns,
+                                              const float4* __restrict__ tw) {
+    constexpr int per = (kDfPoints / R + kDfThreads - 1) / kDfThreads;   // butterflies per thread at most
+    const int nb = n / R, nbf = pts / R;
     dfc v[per][R];
     int out[per];
 #pragma unroll
     for (int q = 0; q < per; ++q) {
         const int b = threadIdx.x + q * kDfThreads;
+        out[q] = -1;
+        if (b >= nbf) continue;
         const int line = b / nb, j = b - line * nb;
         const int k = j % Ns;
         const float4* x = buf + line * ls;
@@ -127,12 +149,14 @@ __device__ __forceinline__ void stockham_pass(float4* buf, int ls, int n, int Ns
         }
         if (R == 8) dft8<INV>(v[q]);
         else if (R == 4) dft4<INV>(v[q]);
+        else if (R == 3) dft3<INV>(v[q]);
         else dft2<INV>(v[q]);
         out[q] = line * ls + (j - k) * R + k;   // line offset + first output (before the swizzle)
     }
     __syncthreads();
 #pragma unroll
     for (int q = 0; q < per; ++q) {
+        if (out[q] < 0) continue;
         const int b = threadIdx.x + q * kDfThreads;
         const int line = b / nb;
         const int o = out[q] - line * ls;
@@ -142,24 +166,30 @@ __device__ __forceinline__ void stockham_pass(float4* buf, int ls, int n, int Ns
     __syncthreads();
 }
 
-// Length-n transforms of every line of the block (natural order in and out).
+// Length-n transforms (n = 2^m or 3 2^m) of every line of the block (natural order in
+// and out): a radix-3 pass first when 3 divides n, then radix-8 passes, then one
+// radix-4 or radix-2 pass.
 template <bool INV>
-__device__ void fft_lines(float4* buf, int n, int logn, const float4* __restrict__ tw) {
+__device__ void fft_lines(float4* buf, int n, int logm, int pts, const float4* __restrict__ tw) {
     const int ls = df_ls(n);
-    int Ns = 1, l = logn;
-    for (; l >= 3; l -= 3, Ns *= 8) stockham_pass<8, INV>(buf, ls, n, Ns, tw);
-    if (l == 2) stockham_pass<4, INV>(buf, ls, n, Ns, tw);
-    else if (l == 1) stockham_pass<2, INV>(buf, ls, n, Ns, tw);
+    int Ns = 1, l = logm;
+    if (n % 3 == 0) {
+        stockham_pass<3, INV>(buf, ls, n, pts, Ns, tw);
+        Ns = 3;
+    }
+    for (; l >= 3; l -= 3, Ns *= 8) stockham_pass<8, INV>(buf, ls, n, pts, Ns, tw);
+    if (l == 2) stockham_pass<4, INV>(buf, ls, n, pts, Ns, tw);
+    else if (l == 1) stockham_pass<2, INV>(buf, ls, n, pts, Ns, tw);
 }
 
 struct DfGeom {
-    int n[3], logn[3];
+    int n[3], logn[3];   // size and log2 of its power-of-two factor per axis
+    int pl[3];           // lines (x) or columns (y, z) per block: lines x n <= kDfPoints
     int h;          // half-spectrum row length N_x / 2 + 1
     long long G;    // real points per channel
     long long Gh;   // half-spectrum points per channel (N_y N_z h)
 };
 
-__device__ __forceinline__ df df_half(df a) { return {a.hi * 0.5f, a.lo * 0.5f}; }   // exact
 
 // x pass, forward.  Two real lines a, b travel as one complex line a + i b; after
 // its transform Z, A[k] = (Z[k] + conj Z[N-k]) / 2 and B[k] = (Z[k] - conj Z[N-k]) / 2i
@@ -167,23 +197,23 @@ __device__ __forceinline__ df df_half(df a) { return {a.hi * 0.5f, a.lo * 0.5f};
 __global__ void __launch_bounds__(kDfThreads, kDfMinBlocks)
 dfx_forward_kernel(DfGeom d, const double* __restrict__ grid, float4* __restrict__ S, const float4* __restrict__ tw) {
     __shared__ float4 buf[kDfSmem];
-    const int n = d.n[0], pl = kDfPoints / n, ls = df_ls(n);   // packed lines per block
+    const int n = d.n[0], pl = d.pl[0], ls = df_ls(n), pts = pl * n;   // packed lines per block
     const size_t ch = blockIdx.y;
     const long long line0 = (long long)blockIdx.x * 2 * pl;   // first real line
     const double* src = grid + ch * d.G + line0 * n;
-    for (int e = threadIdx.x; e < kDfPoints; e += kDfThreads) {
+    for (int e = threadIdx.x; e < pts; e += kDfThreads) {
         const int p = e / n, i = e % n;
         const df a = df_from_double(src[(size_t)(2 * p) * n + i]);
         const df b = df_from_double(src[(size_t)(2 * p + 1) * n + i]);
         buf[p * ls + sw(i)] = make_float4(a.hi, a.lo, b.hi, b.lo);
     }
     __syncthreads();
-    fft_lines<false>(buf, n, d.logn[0], tw);
+    fft_lines<false>(buf, n, d.logn[0], pts, tw);
     float4* dst = S + ch * d.Gh + line0 * d.h;
     for (int e = threadIdx.x; e < pl * d.h; e += kDfThreads) {
         const int p = e / d.h, k = e % d.h;
         const dfc zk = load_c(buf[p * ls + sw(k)]);
-        const dfc zm = load_c(buf[p * ls + sw((n - k) & (n - 1))]);   // Z[N - k], conjugated below
+        const dfc zm = load_c(buf[p * ls + sw(k == 0 ? 0 : n - k)]);   // Z[N - k], conjugated below
         const dfc A = {df_half(df_add(zk.re, zm.re)), df_half(df_add(zk.im, df_neg(zm.im)))};
         // (Z[k] - conj Z[N-k]) / 2i: re = (zk.im + zm.im) / 2, im = -(zk.re - zm.re) / 2
         const dfc B = {df_half(df_add(zk.im, zm.im)), df_half(df_add(zm.re, df_neg(zk.re)))};
@@ -198,7 +228,7 @@ dfx_forward_kernel(DfGeom d, const double* __restrict__ grid, float4* __restrict
 __global__ void __launch_bounds__(kDfThreads, kDfMinBlocks)
 dfx_inverse_kernel(DfGeom d, const float4* __restrict__ S, double* __restrict__ grid, const float4* __restrict__ tw) {
     __shared__ float4 buf[kDfSmem];
-    const int n = d.n[0], pl = kDfPoints / n, ls = df_ls(n);
+    const int n = d.n[0], pl = d.pl[0], ls = df_ls(n), pts = pl * n;
     const size_t ch = blockIdx.y;
     const long long line0 = (long long)blockIdx.x * 2 * pl;
     const float4* src = S + ch * d.Gh + line0 * d.h;
@@ -215,9 +245,9 @@ dfx_inverse_kernel(DfGeom d, const float4* __restrict__ S, double* __restrict__ 
         }
     }
     __syncthreads();
-    fft_lines<true>(buf, n, d.logn[0], tw);
+    fft_lines<true>(buf, n, d.logn[0], pts, tw);
     double* dst = grid + ch * d.G + line0 * n;
-    for (int e = threadIdx.x; e < kDfPoints; e += kDfThreads) {
+    for (int e = threadIdx.x; e < pts; e += kDfThreads) {
         const int p = e / n, i = e % n;
         const float4 v = buf[p * ls + sw(i)];
         dst[(size_t)(2 * p) * n + i] = (double)v.x + (double)v.y;
@@ -230,21 +260,21 @@ dfx_inverse_kernel(DfGeom d, const float4* __restrict__ S, double* __restrict__ 
 __global__ void __launch_bounds__(kDfThreads, kDfMinBlocks)
 dfy_kernel(DfGeom d, float4* __restrict__ S, const float4* __restrict__ tw, int inverse) {
     __shared__ float4 buf[kDfSmem];
-    const int n = d.n[1], cols = kDfPoints / n, h = d.h, ls = df_ls(n);
+    const int n = d.n[1], cols = d.pl[1], h = d.h, ls = df_ls(n), pts = cols * n;
     const size_t ch = blockIdx.y;
     const int blocks_x = (h + cols - 1) / cols;
     const int z = blockIdx.x / blocks_x, x0 = (blockIdx.x % blocks_x) * cols;
     float4* plane = S + ch * d.Gh + (size_t)z * n * h;
-    for (int e = threadIdx.x; e < kDfPoints; e += kDfThreads) {
+    for (int e = threadIdx.x; e < pts; e += kDfThreads) {
         const int y = e / cols, c = e % cols;   // consecutive threads: consecutive x (coalesced)
         buf[c * ls + sw(y)] = x0 + c < h ? plane[(size_t)y * h + x0 + c] : make_float4(0.f, 0.f, 0.f, 0.f);
     }
     __syncthreads();
     if (inverse)
-        fft_lines<true>(buf, n, d.logn[1], tw);
+        fft_lines<true>(buf, n, d.logn[1], pts, tw);
     else
-        fft_lines<false>(buf, n, d.logn[1], tw);
-    for (int e = threadIdx.x; e < kDfPoints; e += kDfThreads) {
+        fft_lines<false>(buf, n, d.logn[1], pts, tw);
+    for (int e = threadIdx.x; e < pts; e += kDfThreads) {
         const int y = e / cols, c = e % cols;
         if (x0 + c < h) plane[(size_t)y * h + x0 + c] = buf[c * ls + sw(y)];
     }
@@ -255,19 +285,19 @@ dfy_kernel(DfGeom d, float4* __restrict__ S, const float4* __restrict__ tw, int 
 __global__ void __launch_bounds__(kDfThreads, kDfMinBlocks)
 dfz_scale_kernel(DfGeom d, float4* __restrict__ S, const float4* __restrict__ tw, const double* __restrict__ green) {
     __shared__ float4 buf[kDfSmem];
-    const int n = d.n[2], cols = kDfPoints / n, ny = d.n[1], h = d.h, ls = df_ls(n);
+    const int n = d.n[2], cols = d.pl[2], ny = d.n[1], h = d.h, ls = df_ls(n), pts = cols * n;
     const size_t ch = blockIdx.y;
     const int blocks_x = (h + cols - 1) / cols;
     const int y = blockIdx.x / blocks_x, x0 = (blockIdx.x % blocks_x) * cols;
     const size_t zstride = (size_t)h * ny;
     float4* col = S + ch * d.Gh + (size_t)y * h + x0;
-    for (int e = threadIdx.x; e < kDfPoints; e += kDfThreads) {
+    for (int e = threadIdx.x; e < pts; e += kDfThreads) {
         const int z = e / cols, c = e % cols;
         buf[c * ls + sw(z)] = x0 + c < h ? col[(size_t)z * zstride + c] : make_float4(0.f, 0.f, 0.f, 0.f);
     }
     __syncthreads();
-    fft_lines<false>(buf, n, d.logn[2], tw);
-    for (int e = threadIdx.x; e < kDfPoints; e += kDfThreads) {
+    fft_lines<false>(buf, n, d.logn[2], pts, tw);
+    for (int e = threadIdx.x; e < pts; e += kDfThreads) {
         const int c = e / n, z = e % n;
         if (x0 + c >= h) continue;
         const df gk = df_from_double(green[((size_t)z * ny + y) * h + x0 + c]);
@@ -278,8 +308,8 @@ dfz_scale_kernel(DfGeom d, float4* __restrict__ S, const float4* __restrict__ tw
         slot = store_c(v);
     }
     __syncthreads();
-    fft_lines<true>(buf, n, d.logn[2], tw);
-    for (int e = threadIdx.x; e < kDfPoints; e += kDfThreads) {
+    fft_lines<true>(buf, n, d.logn[2], pts, tw);
+    for (int e = threadIdx.x; e < pts; e += kDfThreads) {
         const int z = e / cols, c = e % cols;
         if (x0 + c < h) col[(size_t)z * zstride + c] = buf[c * ls + sw(z)];
     }
@@ -293,13 +323,29 @@ int ilog2(int v) {
 
 }  // namespace
 
+namespace {
+
+bool pow2(int v) { return v > 0 && (v & (v - 1)) == 0; }
+
+// power-of-two factor of a supported size: n itself, or n / 3
+int pow2_part(int n) { return n % 3 == 0 ? n / 3 : n; }
+
+// lines (or columns) per block: the largest power of two p with p n <= kDfPoints
+int df_lines(int n) {
+    int p = 1;
+    while (2 * p * n <= kDfPoints) p *= 2;
+    return p;
+}
+
+}  // namespace
+
 bool df_fft_supported(const MeshGeom& g) {
     for (int d = 0; d < 3; ++d) {
-        const int n = g.N[d];
-        if (n < 16 || n > 1024 || (n & (n - 1)) != 0) return false;
+        const int n = g.N[d], m = pow2_part(n);
+        if (!pow2(m) || n < 16 || n > kDfPoints || (m != n && m < 8)) return false;   // 2^k or 3 2^k
     }
-    // the x pass takes 2 kDfPoints / N_x whole real lines per block
-    return (long long)g.N[1] * g.N[2] % (2 * (kDfPoints / g.N[0])) == 0;
+    // the x pass takes 2 df_lines(N_x) whole real lines per block
+    return (long long)g.N[1] * g.N[2] % (2 * df_lines(g.N[0])) == 0;
 }
 
 // Twiddles exp(-2 pi i k / N_d), k < N_d, per axis (double -> hi + lo floats).
@@ -325,14 +371,15 @@ void df_fft_convolve(const MeshGeom& g, int ch, const double* green, double* gri
     DfGeom d;
     for (int a = 0; a < 3; ++a) {
         d.n[a] = g.N[a];
-        d.logn[a] = ilog2(g.N[a]);
+        d.logn[a] = ilog2(pow2_part(g.N[a]));
+        d.pl[a] = df_lines(g.N[a]);
     }
     d.h = g.N[0] / 2 + 1;
     d.G = g.G;
     d.Gh = (long long)g.N[1] * g.N[2] * d.h;
-    const int pl = kDfPoints / g.N[0];
+    const int pl = d.pl[0];
     const dim3 gx((unsigned)((long long)g.N[1] * g.N[2] / (2 * pl)), ch);
-    const int cy = kDfPoints / g.N[1], cz = kDfPoints / g.N[2];
+    const int cy = d.pl[1], cz = d.pl[2];
     const dim3 gy((unsigned)(g.N[2] * ((d.h + cy - 1) / cy)), ch);
     const dim3 gz((unsigned)(g.N[1] * ((d.h + cz - 1) / cz)), ch);
     {

@@ -39,6 +39,8 @@ __device__ __forceinline__ df df_add(df a, df b) {
 
 __device__ __forceinline__ df df_neg(df a) { return {-a.hi, -a.lo}; }
 
+__device__ __forceinline__ df df_half(df a) { return {a.hi * 0.5f, a.lo * 0.5f}; }   // exact
+
 __device__ __forceinline__ df df_sub(df a, df b) { return df_add(a, df_neg(b)); }
 
 __device__ __forceinline__ df df_mul(df a, df b) {
