@@ -356,7 +356,7 @@ __device__ __forceinline__ Windows<T> bead_windows(const PairArgs& A, int bead, 
     return W;
 }
 
-template <typename T, int NR>
+template <typename T, int NR, int PC>
 __global__ void __launch_bounds__(32 * kPairWarps)
 spread_pairs_kernel(PairArgs A, int n, const double* __restrict__ q, T* __restrict__ grid) {
     const int lane = threadIdx.x & 31;
@@ -366,7 +366,7 @@ spread_pairs_kernel(PairArgs A, int n, const double* __restrict__ q, T* __restri
     const int part = (int)(gw - slot * A.wpb);
     const int bead = (int)slot;
     const MeshGeom& g = A.g;
-    const int P = g.P, P2 = P * P;
+    const int P = PC ? PC : g.P, P2 = P * P;
     const Windows<T> W = bead_windows<T, false>(A, bead, lane);
     T* gr = grid + (size_t)A.start[bead].w * NR * g.G;
     T qc[NR];
@@ -385,6 +385,7 @@ spread_pairs_kernel(PairArgs A, int n, const double* __restrict__ q, T* __restri
         T qw[NR];
 #pragma unroll
         for (int r = 0; r < NR; ++r) qw[r] = qc[r] * wxy;
+        #pragma unroll
         for (int k = 0; k < P; ++k) {
             const T wz = __shfl_sync(0xffffffffu, W.wz, k);
             const int iz = __shfl_sync(0xffffffffu, W.iz, k);
@@ -397,7 +398,7 @@ spread_pairs_kernel(PairArgs A, int n, const double* __restrict__ q, T* __restri
     }
 }
 
-template <typename T, int NR, bool GRAD>
+template <typename T, int NR, bool GRAD, int PC>
 __global__ void __launch_bounds__(32 * kPairWarps)
 gather_pairs_kernel(PairArgs A, int n, const T* __restrict__ grid, double* __restrict__ psi, double* __restrict__ E) {
     const int lane = threadIdx.x & 31;
@@ -407,7 +408,7 @@ gather_pairs_kernel(PairArgs A, int n, const T* __restrict__ grid, double* __res
     const int part = (int)(gw - slot * A.wpb);
     const int bead = (int)slot;
     const MeshGeom& g = A.g;
-    const int P = g.P, P2 = P * P;
+    const int P = PC ? PC : g.P, P2 = P * P;
     const Windows<T> W = bead_windows<T, GRAD>(A, bead, lane);
     const T* gr = grid + (size_t)A.start[bead].w * NR * g.G;
     T sp[NR], ex[NR], ey[NR], ez[NR];
@@ -433,6 +434,7 @@ gather_pairs_kernel(PairArgs A, int n, const T* __restrict__ grid, double* __res
         T a[NR], az[NR];
 #pragma unroll
         for (int r = 0; r < NR; ++r) a[r] = az[r] = (T)0;
+        #pragma unroll
         for (int k = 0; k < P; ++k) {
             const T wz = __shfl_sync(0xffffffffu, W.wz, k);
             const int iz = __shfl_sync(0xffffffffu, W.iz, k);
@@ -491,12 +493,34 @@ template <typename T, int NR>
 void launch_pairs(bool spread, bool grad, const PairArgs& A, int n, const double* q, T* grid, double* psi,
                   double* E, cudaStream_t s) {
     const int blocks = div_up((long long)n * A.wpb, kPairWarps);
-    if (spread)
-        spread_pairs_kernel<T, NR><<<blocks, 32 * kPairWarps, 0, s>>>(A, n, q, grid);
-    else if (grad)
-        gather_pairs_kernel<T, NR, true><<<blocks, 32 * kPairWarps, 0, s>>>(A, n, grid, psi, E);
-    else
-        gather_pairs_kernel<T, NR, false><<<blocks, 32 * kPairWarps, 0, s>>>(A, n, grid, psi, nullptr);
+    // compile-time P = 9 (tolerance 1e-6) for the usual field counts: the z walk unrolls
+    bool p9 = false;
+    if constexpr (NR <= 3) p9 = A.g.P == 9;
+    if (spread) {
+        if constexpr (NR <= 3) {
+            if (p9) {
+                spread_pairs_kernel<T, NR, 9><<<blocks, 32 * kPairWarps, 0, s>>>(A, n, q, grid);
+                return;
+            }
+        }
+        spread_pairs_kernel<T, NR, 0><<<blocks, 32 * kPairWarps, 0, s>>>(A, n, q, grid);
+    } else if (grad) {
+        if constexpr (NR <= 3) {
+            if (p9) {
+                gather_pairs_kernel<T, NR, true, 9><<<blocks, 32 * kPairWarps, 0, s>>>(A, n, grid, psi, E);
+                return;
+            }
+        }
+        gather_pairs_kernel<T, NR, true, 0><<<blocks, 32 * kPairWarps, 0, s>>>(A, n, grid, psi, E);
+    } else {
+        if constexpr (NR <= 3) {
+            if (p9) {
+                gather_pairs_kernel<T, NR, false, 9><<<blocks, 32 * kPairWarps, 0, s>>>(A, n, grid, psi, nullptr);
+                return;
+            }
+        }
+        gather_pairs_kernel<T, NR, false, 0><<<blocks, 32 * kPairWarps, 0, s>>>(A, n, grid, psi, nullptr);
+    }
 }
 
 template <typename T>
@@ -613,17 +637,18 @@ __device__ void tile_runs(const int* __restrict__ key, int p0, int m, TileRuns& 
 __device__ __forceinline__ int wrap_once(int v, int N) { return v >= N ? v - N : v; }
 
 // Direct spreading of one bead (one warp, global atomics).
-template <typename T, int NR>
+template <typename T, int NR, int PC>
 __device__ __forceinline__ void spread_bead_direct(const PairArgs& A, int n, int bead, int lane,
                                                    const double* __restrict__ q, T* __restrict__ grid) {
     const MeshGeom& g = A.g;
-    const int P = g.P, P2 = P * P;
+    const int P = PC ? PC : g.P, P2 = P * P;
     const Windows<T> W = bead_windows<T, false>(A, bead, lane);
     T* gr = grid + (size_t)A.start[bead].w * NR * g.G;
     T qc[NR];
 #pragma unroll
     for (int r = 0; r < NR; ++r) qc[r] = (T)(g.c * q[(size_t)r * n + bead]);
     const long long nxy = (long long)g.N[0] * g.N[1];
+    #pragma unroll
     for (int first = 0; first < P2; first += 32) {
         const int pair = first + lane;
         const bool on = pair < P2;
@@ -631,6 +656,7 @@ __device__ __forceinline__ void spread_bead_direct(const PairArgs& A, int n, int
         if (!on) i = j = 0;
         const T wxy = __shfl_sync(0xffffffffu, W.wx, i) * __shfl_sync(0xffffffffu, W.wy, j);
         const long long base = (long long)__shfl_sync(0xffffffffu, W.iy, j) * g.N[0] + __shfl_sync(0xffffffffu, W.ix, i);
+        #pragma unroll
         for (int k = 0; k < P; ++k) {
             const T wz = __shfl_sync(0xffffffffu, W.wz, k);
             const int iz = __shfl_sync(0xffffffffu, W.iz, k);
@@ -643,7 +669,7 @@ __device__ __forceinline__ void spread_bead_direct(const PairArgs& A, int n, int
     }
 }
 
-template <typename T, int NR>
+template <typename T, int NR, int PC>
 __global__ void __launch_bounds__(kTileThreads)
 spread_tiles_kernel(TileArgs TA, int n, const double* __restrict__ q, T* __restrict__ grid) {
     extern __shared__ __align__(16) unsigned char tile_smem[];
@@ -658,10 +684,10 @@ spread_tiles_kernel(TileArgs TA, int n, const double* __restrict__ q, T* __restr
     // isolated beads: direct atomics
     for (int t = w; t < m; t += kTileWarps) {
         const int r = R.of[t];
-        if (R.start[r + 1] - R.start[r] < kTileMin) spread_bead_direct<T, NR>(A, n, TA.sorted[p0 + t], lane, q, grid);
+        if (R.start[r + 1] - R.start[r] < kTileMin) spread_bead_direct<T, NR, PC>(A, n, TA.sorted[p0 + t], lane, q, grid);
     }
     const int E = TA.E, E2 = E * E, E3 = E2 * E;
-    const int P = g.P, P2 = P * P;
+    const int P = PC ? PC : g.P, P2 = P * P;
     for (int r = 0; r < R.count; ++r) {
         const int a = R.start[r], b = R.start[r + 1];
         if (b - a < kTileMin) continue;   // block-uniform
@@ -685,14 +711,16 @@ spread_tiles_kernel(TileArgs TA, int n, const double* __restrict__ q, T* __restr
             T qc[NR];
 #pragma unroll
             for (int c = 0; c < NR; ++c) qc[c] = (T)(g.c * q[(size_t)c * n + bead]);
-            for (int first = 0; first < P2; first += 32) {
+            #pragma unroll
+    for (int first = 0; first < P2; first += 32) {
                 const int pair = first + lane;
                 const bool on = pair < P2;
                 int j = pair / P, i = pair - j * P;
                 if (!on) i = j = 0;
                 const T wxy = __shfl_sync(0xffffffffu, wx, i) * __shfl_sync(0xffffffffu, wy, j);
                 const int base = (lz * E + ly + j) * E + lx + i;
-                for (int k = 0; k < P; ++k) {
+                #pragma unroll
+        for (int k = 0; k < P; ++k) {
                     const T wz = __shfl_sync(0xffffffffu, wz_l, k);
                     if (on) {
 #pragma unroll
@@ -718,18 +746,19 @@ spread_tiles_kernel(TileArgs TA, int n, const double* __restrict__ q, T* __restr
 }
 
 // Direct gather of one bead (one warp) into psi / E.
-template <typename T, int NR, bool GRAD>
+template <typename T, int NR, bool GRAD, int PC>
 __device__ __forceinline__ void gather_bead_direct(const PairArgs& A, int n, int bead, int lane,
                                                    const T* __restrict__ grid, double* __restrict__ psi,
                                                    double* __restrict__ E) {
     const MeshGeom& g = A.g;
-    const int P = g.P, P2 = P * P;
+    const int P = PC ? PC : g.P, P2 = P * P;
     const Windows<T> W = bead_windows<T, GRAD>(A, bead, lane);
     const T* gr = grid + (size_t)A.start[bead].w * NR * g.G;
     T sp[NR], ex[NR], ey[NR], ez[NR];
 #pragma unroll
     for (int r = 0; r < NR; ++r) sp[r] = ex[r] = ey[r] = ez[r] = (T)0;
     const long long nxy = (long long)g.N[0] * g.N[1];
+    #pragma unroll
     for (int first = 0; first < P2; first += 32) {
         const int pair = first + lane;
         const bool on = pair < P2;
@@ -746,6 +775,7 @@ __device__ __forceinline__ void gather_bead_direct(const PairArgs& A, int n, int
         T acc[NR], accz[NR];
 #pragma unroll
         for (int r = 0; r < NR; ++r) acc[r] = accz[r] = (T)0;
+        #pragma unroll
         for (int k = 0; k < P; ++k) {
             const T wz = __shfl_sync(0xffffffffu, W.wz, k);
             const int iz = __shfl_sync(0xffffffffu, W.iz, k);
@@ -789,7 +819,7 @@ __device__ __forceinline__ void gather_bead_direct(const PairArgs& A, int n, int
     }
 }
 
-template <typename T, int NR, bool GRAD>
+template <typename T, int NR, bool GRAD, int PC>
 __global__ void __launch_bounds__(kTileThreads)
 gather_tiles_kernel(TileArgs TA, int n, const T* __restrict__ grid, double* __restrict__ psi, double* __restrict__ E) {
     extern __shared__ __align__(16) unsigned char tile_smem[];
@@ -804,10 +834,10 @@ gather_tiles_kernel(TileArgs TA, int n, const T* __restrict__ grid, double* __re
     for (int t = w; t < m; t += kTileWarps) {
         const int r = R.of[t];
         if (R.start[r + 1] - R.start[r] < kTileMin)
-            gather_bead_direct<T, NR, GRAD>(A, n, TA.sorted[p0 + t], lane, grid, psi, E);
+            gather_bead_direct<T, NR, GRAD, PC>(A, n, TA.sorted[p0 + t], lane, grid, psi, E);
     }
     const int Ee = TA.E, E2 = Ee * Ee, E3 = E2 * Ee;
-    const int P = g.P, P2 = P * P;
+    const int P = PC ? PC : g.P, P2 = P * P;
     for (int r = 0; r < R.count; ++r) {
         const int a = R.start[r], b = R.start[r + 1];
         if (b - a < kTileMin) continue;   // block-uniform
@@ -839,7 +869,8 @@ gather_tiles_kernel(TileArgs TA, int n, const T* __restrict__ grid, double* __re
             T sp[NR], ex[NR], ey[NR], ez[NR];
 #pragma unroll
             for (int c = 0; c < NR; ++c) sp[c] = ex[c] = ey[c] = ez[c] = (T)0;
-            for (int first = 0; first < P2; first += 32) {
+            #pragma unroll
+    for (int first = 0; first < P2; first += 32) {
                 const int pair = first + lane;
                 const bool on = pair < P2;
                 int j = pair / P, i = pair - j * P;
@@ -855,7 +886,8 @@ gather_tiles_kernel(TileArgs TA, int n, const T* __restrict__ grid, double* __re
                 T acc[NR], accz[NR];
 #pragma unroll
                 for (int c = 0; c < NR; ++c) acc[c] = accz[c] = (T)0;
-                for (int k = 0; k < P; ++k) {
+                #pragma unroll
+        for (int k = 0; k < P; ++k) {
                     const T wz = __shfl_sync(0xffffffffu, wz_l, k);
                     T dz = (T)0;
                     if (GRAD) dz = __shfl_sync(0xffffffffu, dz_l, k);
@@ -933,9 +965,14 @@ void tile_smem_attr(K kernel) {
 
 template <typename T, int NR>
 void tile_attrs_nr() {
-    tile_smem_attr(spread_tiles_kernel<T, NR>);
-    tile_smem_attr(gather_tiles_kernel<T, NR, true>);
-    tile_smem_attr(gather_tiles_kernel<T, NR, false>);
+    tile_smem_attr(spread_tiles_kernel<T, NR, 0>);
+    tile_smem_attr(gather_tiles_kernel<T, NR, true, 0>);
+    tile_smem_attr(gather_tiles_kernel<T, NR, false, 0>);
+    if constexpr (NR <= 3) {
+        tile_smem_attr(spread_tiles_kernel<T, NR, 9>);
+        tile_smem_attr(gather_tiles_kernel<T, NR, true, 9>);
+        tile_smem_attr(gather_tiles_kernel<T, NR, false, 9>);
+    }
 }
 
 template <typename T>
@@ -969,12 +1006,33 @@ void launch_tiles(bool spread, bool grad, const TileArgs& TA, int n, const doubl
                   double* E, cudaStream_t s) {
     const size_t bytes = tile_smem_bytes<T>(TA.A.g, NR);
     const int blocks = div_up(n, TA.chunk);
-    if (spread)
-        spread_tiles_kernel<T, NR><<<blocks, kTileThreads, bytes, s>>>(TA, n, q, grid);
-    else if (grad)
-        gather_tiles_kernel<T, NR, true><<<blocks, kTileThreads, bytes, s>>>(TA, n, grid, psi, E);
-    else
-        gather_tiles_kernel<T, NR, false><<<blocks, kTileThreads, bytes, s>>>(TA, n, grid, psi, nullptr);
+    bool p9 = false;
+    if constexpr (NR <= 3) p9 = TA.A.g.P == 9;
+    if (spread) {
+        if constexpr (NR <= 3) {
+            if (p9) {
+                spread_tiles_kernel<T, NR, 9><<<blocks, kTileThreads, bytes, s>>>(TA, n, q, grid);
+                return;
+            }
+        }
+        spread_tiles_kernel<T, NR, 0><<<blocks, kTileThreads, bytes, s>>>(TA, n, q, grid);
+    } else if (grad) {
+        if constexpr (NR <= 3) {
+            if (p9) {
+                gather_tiles_kernel<T, NR, true, 9><<<blocks, kTileThreads, bytes, s>>>(TA, n, grid, psi, E);
+                return;
+            }
+        }
+        gather_tiles_kernel<T, NR, true, 0><<<blocks, kTileThreads, bytes, s>>>(TA, n, grid, psi, E);
+    } else {
+        if constexpr (NR <= 3) {
+            if (p9) {
+                gather_tiles_kernel<T, NR, false, 9><<<blocks, kTileThreads, bytes, s>>>(TA, n, grid, psi, nullptr);
+                return;
+            }
+        }
+        gather_tiles_kernel<T, NR, false, 0><<<blocks, kTileThreads, bytes, s>>>(TA, n, grid, psi, nullptr);
+    }
 }
 
 template <typename T>
