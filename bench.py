@@ -383,7 +383,7 @@ def bench_ours(args, ib, torch, rank, world, local):
     # PME evaluations alone on the same system (potential of the current charges)
     npairs = pair_count(ib, st)
     pme = pme_rate(ib, torch, st, flush, max(10, args.steps))
-    pme_big = pme_at_scale(ib, torch, flush, 10)
+    pme_big = None if args.skip_scale else pme_at_scale(ib, torch, flush, 10)
 
     # plain FP64 GPU path: the same step with every mesh step in FP64
     fp64 = None
@@ -833,6 +833,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--skip-fp64", action="store_true", help="do not time the plain FP64 path")
     ap.add_argument("--skip-cpu", action="store_true", help="do not time the oracle on the host")
+    ap.add_argument("--skip-scale", action="store_true", help="do not time the PME evaluation on the lattice")
     ap.add_argument("--workload", default="charged-sphere", choices=["charged-sphere", "polarizability", "trajectory"],
                     help="the headline charged-sphere step, the batched polarizability solve, or a BD "
                          "trajectory comparing initial guesses")
