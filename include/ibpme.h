@@ -60,7 +60,9 @@ enum { IBPME_FP64 = 0,            /* every step in FP64 */
        IBPME_MIXED = 1 };         /* FP32 mesh (spread, FFT, scale, gather), FP64 near field and
                                      Krylov; inside a solve the corrections come from an inner
                                      operator whose near field is FP32 too, refined against the
-                                     FP64 operator */
+                                     FP64 operator.  At rtol >= 1e-7 the first residual of a
+                                     nonzero guess takes the FP32 mesh; every residual that
+                                     decides convergence takes the FP64 operator */
 
 /* Parameters of the spectral Ewald split (Sec. III.D).  A zero in a field
  * marked "auto" asks pme_setup to derive it with the rules of Sec. III.D.2:
@@ -162,9 +164,10 @@ typedef struct {
     int outer;              /* refinement steps (mixed precision), 1 for FP64 */
     int matvecs_fp64;       /* FP64 operator applications (true residuals, RHS) */
     double rel_residual;    /* final ||b - A u||_2 / ||b||_2 with the FP64 operator, worst RHS */
-    double time_ms;         /* wall time of the call */
+    double time_ms;         /* host wall time of the call (device outputs complete in stream order) */
     int fell_back;          /* 1 if the learned guess was rejected for the zero guess */
-    double init_rel_residual;   /* ||b - A u0|| / ||b|| of the initial guess actually used (FP64 operator) */
+    double init_rel_residual;   /* ||b - A u0|| / ||b|| of the initial guess actually used (FP64
+                                   operator; FP32 mesh where the first residual takes it) */
 } ibpme_solve_stats;
 
 /* Induced-charge solve, Sec. III.B Eq. saddle:

@@ -131,6 +131,7 @@ struct StencilCache {
     int n = 0, ncfg = 0;
     DevBuf start;                // int4 per bead: first node (x, y, z), configuration
     DevBuf frac;                 // double4 per bead: (first node - x / h) per axis
+    DevBuf frac32;               // float4 per bead: the same offsets in FP32 (FP32 kernels)
     DevBuf w64;                  // FP64 window weights [n][3][P] (GB300's FP64 exp is slow: once per positions)
     // Tile bins for spreading and gathering through shared memory (many beads
     // only): beads sorted by (configuration, tile of kTileNodes^3 nodes holding
@@ -159,6 +160,7 @@ struct Mesh {
     // FP64 meshes of power-of-two sizes: double-float transforms instead of cuFFT (dffft.cu)
     bool df = false;
     DevBuf df_tw[3], df_buf;
+    DevBuf green_df;   // the Green's table as (hi, lo) float pairs for the double-float transforms
     void init(const MeshGeom& geom, int channels, double xi, double eta, double a, cudaStream_t s);
     void destroy();
     void ensure_channels(int ch);
@@ -347,6 +349,9 @@ struct ibpme_ctx {
     int ncfg = 1;
     const int* bcfg = nullptr;
     bool bodies_current = false;   // the uploaded bodies belong to the running call
+    // mixed solves whose first residual takes the FP64 operator after an FP32-mesh start
+    // missed the tolerance at the first FP64 check (counts down once per solve)
+    int start32_skip = 0;
     ibp::DevBuf ml_feat, ml_scratch, ml_scales, ml_y;   // learned warm start
     cudaEvent_t ev_in = nullptr, ev_out = nullptr;
     ibp::StencilCache stencils;               // stencils of the current positions
@@ -374,7 +379,7 @@ double self_term(const ibpme_ctx* c);   // phi_self (without 1/eps)
 // ---- dffft.cu ----
 bool df_fft_supported(const MeshGeom& g);
 void df_fft_init(const MeshGeom& g, DevBuf tw[3], cudaStream_t s);
-void df_fft_convolve(const MeshGeom& g, int ch, const double* green, double* grid, float4* S, DevBuf tw[3],
+void df_fft_convolve(const MeshGeom& g, int ch, const float2* green, double* grid, float4* S, DevBuf tw[3],
                      cudaStream_t s);
 
 // ---- mesh.cu ----

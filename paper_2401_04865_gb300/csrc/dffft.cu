@@ -280,10 +280,11 @@ dfy_kernel(DfGeom d, float4* __restrict__ S, const float4* __restrict__ tw, int 
     }
 }
 
-// z pass on the half spectrum: forward FFT, Green's-function scaling (FP64
-// half-spectrum table), inverse FFT, for columns x0 .. x0 + cols at one y
+// z pass on the half spectrum: forward FFT, Green's-function scaling (the FP64
+// half-spectrum table split into hi + lo floats), inverse FFT, for columns
+// x0 .. x0 + cols at one y
 __global__ void __launch_bounds__(kDfThreads, kDfMinBlocks)
-dfz_scale_kernel(DfGeom d, float4* __restrict__ S, const float4* __restrict__ tw, const double* __restrict__ green) {
+dfz_scale_kernel(DfGeom d, float4* __restrict__ S, const float4* __restrict__ tw, const float2* __restrict__ green) {
     __shared__ float4 buf[kDfSmem];
     const int n = d.n[2], cols = d.pl[2], ny = d.n[1], h = d.h, ls = df_ls(n), pts = cols * n;
     const size_t ch = blockIdx.y;
@@ -300,7 +301,8 @@ dfz_scale_kernel(DfGeom d, float4* __restrict__ S, const float4* __restrict__ tw
     for (int e = threadIdx.x; e < pts; e += kDfThreads) {
         const int c = e / n, z = e % n;
         if (x0 + c >= h) continue;
-        const df gk = df_from_double(green[((size_t)z * ny + y) * h + x0 + c]);
+        const float2 gv = green[((size_t)z * ny + y) * h + x0 + c];
+        const df gk = {gv.x, gv.y};
         float4& slot = buf[c * ls + sw(z)];
         dfc v = load_c(slot);
         v.re = df_mul(v.re, gk);
@@ -366,7 +368,7 @@ void df_fft_init(const MeshGeom& g, DevBuf tw[3], cudaStream_t s) {
 }
 
 // grid (FP64, [ch][G]) -> inverse transform of G(k) times its transform, in place.
-void df_fft_convolve(const MeshGeom& g, int ch, const double* green, double* grid, float4* S, DevBuf tw[3],
+void df_fft_convolve(const MeshGeom& g, int ch, const float2* green, double* grid, float4* S, DevBuf tw[3],
                      cudaStream_t s) {
     DfGeom d;
     for (int a = 0; a < 3; ++a) {

@@ -41,9 +41,17 @@ struct Krylov {
     cudaGraphExec_t exec[2] = {nullptr, nullptr};
     std::vector<long long> sig[2];
     long long nodes[2] = {0, 0};   // library kernels captured in each graph (counted per replay)
+    // host mirror of the device flags in `active` (uploaded only when they change) and
+    // the pinned staging the uploads read; every upload is followed by a synchronising
+    // fetch before the staging is written again
+    std::vector<int> act_mirror;
+    const void* act_buf = nullptr;
+    int* act_pin = nullptr;
+    int act_cap = 0;
     ~Krylov() {
         for (auto& e : exec)
             if (e) cudaGraphExecDestroy(e);
+        if (act_pin) cudaFreeHost(act_pin);
     }
 };
 
@@ -725,7 +733,7 @@ struct Solver {
                                       P(c->near.val.p), P(c->near.pair32.p), P(c->near.qf.p), P(c->near.qs.p), P(c->near.cell_beads.p), P(c->near.rowptr.p), P(a.xw), P(bd.free_idx.p),
                                       P(bd.free_unk.p), P(bd.bead_body.p), P(bd.body_unk.p), P(bd.mb_unk.p),
                                       P(bd.mb_first.p), P(bd.mb_cnt.p), P(bd.uo.p), P(c->bcfg),
-                                      (long long)c->stencils.valid, P(c->stencils.start.p), P(c->stencils.frac.p),
+                                      (long long)c->stencils.valid, P(c->stencils.start.p), P(c->stencils.frac.p), P(c->stencils.frac32.p),
                                       (long long)c->stencils.tiles, (long long)c->stencils.tile_n[0],
                                       (long long)c->stencils.tile_n[1], (long long)c->stencils.tile_n[2],
                                       P(c->stencils.tile_sorted.p), P(c->stencils.tile_key.p), P(c->stencils.w64.p),
@@ -739,7 +747,9 @@ struct Solver {
                                       P(c->pre.shape_off.p), P(c->pre.shape_goff.p),
                                       P(prec == IBPME_MIXED ? m32.grid.p : m64.grid.p),
                                       P(prec == IBPME_MIXED ? m32.spec.p : m64.spec.p),
-                                      P(prec == IBPME_MIXED ? m32.work.p : m64.work.p), P(m64.df_buf.p)};
+                                      P(prec == IBPME_MIXED ? m32.work.p : m64.work.p), P(m64.df_buf.p),
+                                      P(m32.green.p), P(m64.green.p), P(m64.green_df.p), P(m64.df_tw[0].p),
+                                      P(m64.df_tw[1].p), P(m64.df_tw[2].p)};
         const int gi = prec == IBPME_MIXED ? 1 : 0;
         if (k->exec[gi] && k->sig[gi] == sig) return k->exec[gi];
         if (k->exec[gi]) {
@@ -801,10 +811,18 @@ struct Solver {
     }
 
     void set_active(const std::vector<int>& act) {
-        int* h = static_cast<int*>(pinned_host(c, sizeof(int) * S));
-        for (int i = 0; i < S; ++i) h[i] = act[i];
-        IBP_CUDA(cudaMemcpyAsync(k->active.p, h, sizeof(int) * S, cudaMemcpyHostToDevice, s()));
-        IBP_CUDA(cudaStreamSynchronize(s()));   // the pinned scratch is reused right after
+        if (k->act_buf == k->active.p && k->act_mirror == act) return;   // the device already holds them
+        if (k->act_cap < S) {
+            if (k->act_pin) IBP_CUDA(cudaFreeHost(k->act_pin));
+            k->act_pin = nullptr;
+            k->act_cap = 0;
+            IBP_CUDA(cudaHostAlloc(reinterpret_cast<void**>(&k->act_pin), sizeof(int) * S, cudaHostAllocDefault));
+            k->act_cap = S;
+        }
+        for (int i = 0; i < S; ++i) k->act_pin[i] = act[i];
+        IBP_CUDA(cudaMemcpyAsync(k->active.p, k->act_pin, sizeof(int) * S, cudaMemcpyHostToDevice, s()));
+        k->act_mirror = act;
+        k->act_buf = k->active.p;
     }
 
     // Residual of the full saddle system at the iterate x with the operator of the
@@ -844,11 +862,13 @@ struct Solver {
 
     // GMRES on A(prec) d = rhs (d = 0 on entry) for every system, cycles of at most m
     // iterations, until |rhs - A d| <= target per system or the iteration budget is spent.
-    void gmres(int prec, const double* rhs, double* dd, const std::vector<double>& target) {
+    // rn0: |rhs| per system, from the norms() call that left |rhs|^2 in k->norms
+    void gmres(int prec, const double* rhs, double* dd, const std::vector<double>& target,
+               const std::vector<double>& rn0) {
         const long long len = (long long)nk * R;
         IBP_CUDA(cudaMemsetAsync(dd, 0, sizeof(double) * len, s()));
         const double* res_vec = rhs;   // residual the next cycle starts from
-        std::vector<double> rn = norms(rhs);
+        std::vector<double> rn = rn0;
         for (;;) {
             std::vector<int> act(S);
             bool any = false;
@@ -937,17 +957,30 @@ struct Solver {
                                                                             I(bd.free_unk), a.q, D(k->x));
             IBP_CHECK_LAUNCH();
         }
-        // Iterative refinement on the full system.  Every residual uses the FP64
-        // operator; in mixed precision the corrections come from the FP32-mesh
-        // operator, whose rounding then scales with the residual, not with the
-        // (possibly much larger) potentials of the guess itself.
+        // Iterative refinement on the full system.  Every residual that decides
+        // convergence uses the FP64 operator; in mixed precision the corrections come
+        // from the FP32-mesh operator, whose rounding then scales with the residual,
+        // not with the (possibly much larger) potentials of the guess itself.
         const bool mixed = a.prec == IBPME_MIXED;
         // the zero guess of a system without ions has no charge anywhere: r0 follows from b alone
         const bool zero_start = nk > 0 && !a.user_guess && !a.learned && bd.nmb == bd.nb;
-        std::vector<double> res = residual(IBPME_FP64, true, zero_start);
+        // Mixed precision at tolerances of 1e-7 and looser: the first residual takes the
+        // FP32-mesh operator.  Its rounding enters the correction once and the FP64
+        // residual after it still decides convergence, so a step usually needs one FP64
+        // evaluation instead of two.  Where that rounding is not small against |b| (many
+        // ions around a weakly charged body) the first FP64 check fails; the context then
+        // starts the next 32 solves from the FP64 residual.
+        bool start32 = mixed && !zero_start && a.rtol >= 1e-7;
+        if (start32 && c->start32_skip > 0) {
+            --c->start32_skip;
+            start32 = false;
+        }
+        bool judge32 = start32;   // the first FP64 check still has to judge the FP32 start
+        const int prec0 = start32 ? IBPME_MIXED : IBPME_FP64;
+        std::vector<double> res = residual(prec0, true, zero_start);
         std::vector<double> tol_abs(S);
         for (int i = 0; i < S; ++i) tol_abs[i] = a.rtol * bnorm[i];
-        bool res64 = true;
+        bool res64 = !start32;
         int fell_back = 0;
         if (a.learned && nk > 0) {
             // the learned guess must beat the zero guess, whose residual is |b| up to the ions' share
@@ -956,7 +989,7 @@ struct Solver {
                 if (!(res[i] < bnorm[i])) worse = true;
             if (worse) {
                 IBP_CUDA(cudaMemsetAsync(k->x.p, 0, sizeof(double) * len, s()));
-                res = residual(IBPME_FP64, true);
+                res = residual(prec0, true);
                 fell_back = 1;
             }
         }
@@ -979,6 +1012,10 @@ struct Solver {
                 if (res64) break;
                 res = residual(IBPME_FP64);   // a guess that looks converged: confirm with FP64
                 res64 = true;
+                if (judge32) {
+                    c->start32_skip = converged() ? 0 : 32;
+                    judge32 = false;
+                }
                 if (converged()) break;
             }
             ++outer;
@@ -987,11 +1024,15 @@ struct Solver {
             // check usually confirms it.
             std::vector<double> tgt(S);
             for (int i = 0; i < S; ++i) tgt[i] = (mixed ? 0.25 : 0.9) * tol_abs[i];
-            gmres(a.prec, D(k->r), D(k->d), tgt);
+            gmres(a.prec, D(k->r), D(k->d), tgt, res);   // res: norms of k->r, the last norms() call
             axpby_kernel<<<blocks_for(len), 256, 0, s()>>>(len, 1.0, D(k->x), 1.0, D(k->d), D(k->x));
             IBP_CHECK_LAUNCH();
             res = residual(IBPME_FP64);
             res64 = true;
+            if (judge32) {
+                c->start32_skip = converged() ? 0 : 32;
+                judge32 = false;
+            }
             if (verbose)
                 for (int i = 0; i < S; ++i)
                     std::fprintf(stderr, "[ibpme] outer %d system %d: iters %d  |r|/|b| = %.3e (fp64 matvecs %d)\n",

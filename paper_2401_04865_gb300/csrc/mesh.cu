@@ -276,7 +276,8 @@ void gather_dispatch(int n, const double* xw, int nrhs, const int* cfg, const Me
 constexpr int kPairWarps = 4;   // warps per block
 
 __global__ void stencil_cache_kernel(int n, const double* __restrict__ xw, const int* __restrict__ bcfg, MeshGeom g,
-                                     int4* __restrict__ start, double4* __restrict__ frac, double* __restrict__ w64) {
+                                     int4* __restrict__ start, double4* __restrict__ frac, float4* __restrict__ frac32,
+                                     double* __restrict__ w64) {
     const int b = blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= n) return;
     int s0[3];
@@ -292,6 +293,7 @@ __global__ void stencil_cache_kernel(int n, const double* __restrict__ xw, const
     }
     start[b] = make_int4(s0[0], s0[1], s0[2], bcfg ? bcfg[b] : 0);
     frac[b] = make_double4(f[0], f[1], f[2], 0.0);
+    frac32[b] = make_float4((float)f[0], (float)f[1], (float)f[2], 0.0f);
     // the FP64 windows exp(-kappa (f + l)^2), l < P, exactly as the kernels evaluate them
     double* w = w64 + (size_t)b * 3 * g.P;
     for (int d = 0; d < 3; ++d)
@@ -301,17 +303,29 @@ __global__ void stencil_cache_kernel(int n, const double* __restrict__ xw, const
         }
 }
 
+// FP32 kernels take every constant and offset in FP32: GB300 issues FP64
+// instructions (conversions included) at a small fraction of the FP32 rate, and
+// a handful per bead made the FP64 pipe the busiest unit of the FP32 gather.
 struct PairArgs {
     MeshGeom g;
     int wpb;            // warps per bead
     int rounds;         // blocks of 32 (i, j) pairs per warp: wpb * rounds * 32 >= P^2
     const int4* start;
     const double4* frac;
+    const float4* frac32;   // the same offsets rounded to FP32
     const double* w64;  // cached FP64 windows [n][3][P] (NULL: evaluate them)
+    float kappa32[3], h32[3], c32, gather32, grad32;   // MeshGeom's constants in FP32
 };
 
+// A mesh constant in the kernel's precision.
 template <typename T>
-__device__ __forceinline__ T window(T f, double kappa) { return dexp<T>(-(T)kappa * f * f); }
+__device__ __forceinline__ T cst(double v64, float v32) {
+    if constexpr (sizeof(T) == 4) return v32;
+    else return v64;
+}
+
+template <typename T>
+__device__ __forceinline__ T window(T f, T kappa) { return dexp<T>(-kappa * f * f); }
 
 // Window l of axis d of a bead: the cached FP64 value (FP64 meshes), else evaluated.
 template <typename T>
@@ -319,7 +333,23 @@ __device__ __forceinline__ T bead_window(const PairArgs& A, int bead, int d, T f
     if constexpr (sizeof(T) == 8) {
         if (A.w64) return in ? A.w64[((size_t)bead * 3 + d) * A.g.P + l] : 0.0;
     }
-    return in ? window<T>(f, A.g.kappa[d]) : (T)0;
+    return in ? window<T>(f, cst<T>(A.g.kappa[d], A.kappa32[d])) : (T)0;
+}
+
+// (node l - x) / h per axis for lane l of a bead's stencil.
+template <typename T>
+__device__ __forceinline__ void bead_offsets(const PairArgs& A, int bead, int lane, T& fx, T& fy, T& fz) {
+    if constexpr (sizeof(T) == 4) {
+        const float4 fr = A.frac32[bead];
+        fx = fr.x + (float)lane;
+        fy = fr.y + (float)lane;
+        fz = fr.z + (float)lane;
+    } else {
+        const double4 fr = A.frac[bead];
+        fx = fr.x + (double)lane;
+        fy = fr.y + (double)lane;
+        fz = fr.z + (double)lane;
+    }
 }
 
 // One-dimensional windows of a bead, lane l < P holding node l of each axis:
@@ -335,17 +365,17 @@ __device__ __forceinline__ Windows<T> bead_windows(const PairArgs& A, int bead, 
     const MeshGeom& g = A.g;
     const int P = g.P;
     const int4 st = A.start[bead];
-    const double4 fr = A.frac[bead];
     Windows<T> W;
-    const T fx = (T)fr.x + (T)lane, fy = (T)fr.y + (T)lane, fz = (T)fr.z + (T)lane;
+    T fx, fy, fz;
+    bead_offsets<T>(A, bead, lane, fx, fy, fz);
     const bool in = lane < P;
     W.wx = bead_window<T>(A, bead, 0, fx, lane, in);
     W.wy = bead_window<T>(A, bead, 1, fy, lane, in);
     W.wz = bead_window<T>(A, bead, 2, fz, lane, in);
     if (DIST) {
-        W.dx = fx * (T)g.h[0];
-        W.dy = fy * (T)g.h[1];
-        W.dz = fz * (T)g.h[2];
+        W.dx = fx * cst<T>(g.h[0], A.h32[0]);
+        W.dy = fy * cst<T>(g.h[1], A.h32[1]);
+        W.dz = fz * cst<T>(g.h[2], A.h32[2]);
     }
     W.ix = st.x + lane;
     W.iy = st.y + lane;
@@ -371,7 +401,7 @@ spread_pairs_kernel(PairArgs A, int n, const double* __restrict__ q, T* __restri
     T* gr = grid + (size_t)A.start[bead].w * NR * g.G;
     T qc[NR];
 #pragma unroll
-    for (int r = 0; r < NR; ++r) qc[r] = (T)(g.c * q[(size_t)r * n + bead]);
+    for (int r = 0; r < NR; ++r) qc[r] = cst<T>(g.c, A.c32) * (T)q[(size_t)r * n + bead];
     const long long nxy = (long long)g.N[0] * g.N[1];
     for (int rd = 0; rd < A.rounds; ++rd) {
         const int first = (part * A.rounds + rd) * 32;
@@ -462,29 +492,29 @@ gather_pairs_kernel(PairArgs A, int n, const T* __restrict__ grid, double* __res
     }
 #pragma unroll
     for (int r = 0; r < NR; ++r) {
-        const double s0 = warp_sum((double)sp[r]);
+        const T s0 = warp_sum(sp[r]);
         if (GRAD) {
-            const double e0 = warp_sum((double)ex[r]);
-            const double e1 = warp_sum((double)ey[r]);
-            const double e2 = warp_sum((double)ez[r]);
+            const T e0 = warp_sum(ex[r]);
+            const T e1 = warp_sum(ey[r]);
+            const T e2 = warp_sum(ez[r]);
             if (lane == 0) {
                 double* e = E + ((size_t)r * n + bead) * 3;
                 if (A.wpb == 1) {
-                    e[0] = -g.grad * e0;
-                    e[1] = -g.grad * e1;
-                    e[2] = -g.grad * e2;
+                    e[0] = (double)(-cst<T>(g.grad, A.grad32) * e0);
+                    e[1] = (double)(-cst<T>(g.grad, A.grad32) * e1);
+                    e[2] = (double)(-cst<T>(g.grad, A.grad32) * e2);
                 } else {
-                    atomicAdd(e + 0, -g.grad * e0);
-                    atomicAdd(e + 1, -g.grad * e1);
-                    atomicAdd(e + 2, -g.grad * e2);
+                    atomicAdd(e + 0, (double)(-cst<T>(g.grad, A.grad32) * e0));
+                    atomicAdd(e + 1, (double)(-cst<T>(g.grad, A.grad32) * e1));
+                    atomicAdd(e + 2, (double)(-cst<T>(g.grad, A.grad32) * e2));
                 }
             }
         }
         if (lane == 0) {
             if (A.wpb == 1)
-                psi[(size_t)r * n + bead] = g.gather * s0;
+                psi[(size_t)r * n + bead] = (double)(cst<T>(g.gather, A.gather32) * s0);
             else
-                atomicAdd(psi + (size_t)r * n + bead, g.gather * s0);
+                atomicAdd(psi + (size_t)r * n + bead, (double)(cst<T>(g.gather, A.gather32) * s0));
         }
     }
 }
@@ -541,16 +571,28 @@ void pairs_dispatch(int nrhs, bool spread, bool grad, const PairArgs& A, int n, 
 // Warps per bead: split a bead's P^2 columns over several warps while the bead
 // count alone cannot fill the GPU (about two waves of resident warps), else one
 // warp walks all of them and sets its window up once.
+void pair_consts(PairArgs& A, const MeshGeom& g, const StencilCache& b) {
+    A.g = g;
+    A.start = b.start.as<int4>();
+    A.frac = b.frac.as<double4>();
+    A.frac32 = b.frac32.as<float4>();
+    A.w64 = b.w64.as<double>();
+    for (int d = 0; d < 3; ++d) {
+        A.kappa32[d] = (float)g.kappa[d];
+        A.h32[d] = (float)g.h[d];
+    }
+    A.c32 = (float)g.c;
+    A.gather32 = (float)g.gather;
+    A.grad32 = (float)g.grad;
+}
+
 PairArgs pair_args(const MeshGeom& g, const StencilCache& b, int n) {
     PairArgs A{};
-    A.g = g;
+    pair_consts(A, g, b);
     const int blocks32 = (g.P * g.P + 31) / 32;
     const bool split = (long long)n * blocks32 <= 152LL * 64 * 2;
     A.wpb = split ? blocks32 : 1;
     A.rounds = split ? 1 : blocks32;
-    A.start = b.start.as<int4>();
-    A.frac = b.frac.as<double4>();
-    A.w64 = b.w64.as<double>();
     return A;
 }
 
@@ -646,7 +688,7 @@ __device__ __forceinline__ void spread_bead_direct(const PairArgs& A, int n, int
     T* gr = grid + (size_t)A.start[bead].w * NR * g.G;
     T qc[NR];
 #pragma unroll
-    for (int r = 0; r < NR; ++r) qc[r] = (T)(g.c * q[(size_t)r * n + bead]);
+    for (int r = 0; r < NR; ++r) qc[r] = cst<T>(g.c, A.c32) * (T)q[(size_t)r * n + bead];
     const long long nxy = (long long)g.N[0] * g.N[1];
     #pragma unroll
     for (int first = 0; first < P2; first += 32) {
@@ -701,16 +743,16 @@ spread_tiles_kernel(TileArgs TA, int n, const double* __restrict__ q, T* __restr
         for (int t = a + w; t < b; t += kTileWarps) {
             const int bead = TA.sorted[p0 + t];
             const int4 st = A.start[bead];
-            const double4 fr = A.frac[bead];
             const bool in = lane < P;
-            const T fx = (T)fr.x + (T)lane, fy = (T)fr.y + (T)lane, fz = (T)fr.z + (T)lane;
+            T fx, fy, fz;
+            bead_offsets<T>(A, bead, lane, fx, fy, fz);
             const T wx = bead_window<T>(A, bead, 0, fx, lane, in);
             const T wy = bead_window<T>(A, bead, 1, fy, lane, in);
             const T wz_l = bead_window<T>(A, bead, 2, fz, lane, in);
             const int lx = st.x - ox, ly = st.y - oy, lz = st.z - oz;   // in [0, kTileNodes)
             T qc[NR];
 #pragma unroll
-            for (int c = 0; c < NR; ++c) qc[c] = (T)(g.c * q[(size_t)c * n + bead]);
+            for (int c = 0; c < NR; ++c) qc[c] = cst<T>(g.c, A.c32) * (T)q[(size_t)c * n + bead];
             #pragma unroll
     for (int first = 0; first < P2; first += 32) {
                 const int pair = first + lane;
@@ -803,19 +845,19 @@ __device__ __forceinline__ void gather_bead_direct(const PairArgs& A, int n, int
     }
 #pragma unroll
     for (int r = 0; r < NR; ++r) {
-        const double s0 = warp_sum((double)sp[r]);
+        const T s0 = warp_sum(sp[r]);
         if (GRAD) {
-            const double e0 = warp_sum((double)ex[r]);
-            const double e1 = warp_sum((double)ey[r]);
-            const double e2 = warp_sum((double)ez[r]);
+            const T e0 = warp_sum(ex[r]);
+            const T e1 = warp_sum(ey[r]);
+            const T e2 = warp_sum(ez[r]);
             if (lane == 0) {
                 double* e = E + ((size_t)r * n + bead) * 3;
-                e[0] = -g.grad * e0;
-                e[1] = -g.grad * e1;
-                e[2] = -g.grad * e2;
+                e[0] = (double)(-cst<T>(g.grad, A.grad32) * e0);
+                e[1] = (double)(-cst<T>(g.grad, A.grad32) * e1);
+                e[2] = (double)(-cst<T>(g.grad, A.grad32) * e2);
             }
         }
-        if (lane == 0) psi[(size_t)r * n + bead] = g.gather * s0;
+        if (lane == 0) psi[(size_t)r * n + bead] = (double)(cst<T>(g.gather, A.gather32) * s0);
     }
 }
 
@@ -858,13 +900,14 @@ gather_tiles_kernel(TileArgs TA, int n, const T* __restrict__ grid, double* __re
         for (int t = a + w; t < b; t += kTileWarps) {
             const int bead = TA.sorted[p0 + t];
             const int4 st = A.start[bead];
-            const double4 fr = A.frac[bead];
             const bool in = lane < P;
-            const T fx = (T)fr.x + (T)lane, fy = (T)fr.y + (T)lane, fz = (T)fr.z + (T)lane;
+            T fx, fy, fz;
+            bead_offsets<T>(A, bead, lane, fx, fy, fz);
             const T wx_l = bead_window<T>(A, bead, 0, fx, lane, in);
             const T wy_l = bead_window<T>(A, bead, 1, fy, lane, in);
             const T wz_l = bead_window<T>(A, bead, 2, fz, lane, in);
-            const T dx_l = fx * (T)g.h[0], dy_l = fy * (T)g.h[1], dz_l = fz * (T)g.h[2];
+            const T dx_l = fx * cst<T>(g.h[0], A.h32[0]), dy_l = fy * cst<T>(g.h[1], A.h32[1]),
+                    dz_l = fz * cst<T>(g.h[2], A.h32[2]);
             const int lx = st.x - ox, ly = st.y - oy, lz = st.z - oz;
             T sp[NR], ex[NR], ey[NR], ez[NR];
 #pragma unroll
@@ -912,19 +955,19 @@ gather_tiles_kernel(TileArgs TA, int n, const T* __restrict__ grid, double* __re
             }
 #pragma unroll
             for (int c = 0; c < NR; ++c) {
-                const double s0 = warp_sum((double)sp[c]);
+                const T s0 = warp_sum(sp[c]);
                 if (GRAD) {
-                    const double e0 = warp_sum((double)ex[c]);
-                    const double e1 = warp_sum((double)ey[c]);
-                    const double e2 = warp_sum((double)ez[c]);
+                    const T e0 = warp_sum(ex[c]);
+                    const T e1 = warp_sum(ey[c]);
+                    const T e2 = warp_sum(ez[c]);
                     if (lane == 0) {
                         double* e = E + ((size_t)c * n + bead) * 3;
-                        e[0] = -g.grad * e0;
-                        e[1] = -g.grad * e1;
-                        e[2] = -g.grad * e2;
+                        e[0] = (double)(-cst<T>(g.grad, A.grad32) * e0);
+                        e[1] = (double)(-cst<T>(g.grad, A.grad32) * e1);
+                        e[2] = (double)(-cst<T>(g.grad, A.grad32) * e2);
                     }
                 }
-                if (lane == 0) psi[(size_t)c * n + bead] = g.gather * s0;
+                if (lane == 0) psi[(size_t)c * n + bead] = (double)(cst<T>(g.gather, A.gather32) * s0);
             }
         }
         __syncthreads();
@@ -936,12 +979,9 @@ gather_tiles_kernel(TileArgs TA, int n, const T* __restrict__ grid, double* __re
 TileArgs tile_args(const MeshGeom& g, const StencilCache& b, int n) {
     TileArgs TA{};
     TA.chunk = n >= 152 * 4 * 128 ? 128 : (n >= 152 * 4 * 64 ? 64 : 32);
-    TA.A.g = g;
+    pair_consts(TA.A, g, b);
     TA.A.wpb = 1;
     TA.A.rounds = (g.P * g.P + 31) / 32;
-    TA.A.start = b.start.as<int4>();
-    TA.A.frac = b.frac.as<double4>();
-    TA.A.w64 = b.w64.as<double>();
     TA.sorted = b.tile_sorted.as<int>();
     TA.key = b.tile_key.as<int>();
     for (int d = 0; d < 3; ++d) TA.tn[d] = b.tile_n[d];
@@ -1084,6 +1124,15 @@ __global__ void green_kernel(MeshGeom g, double xi, double eta, double a, T* __r
     }
 }
 
+// The FP64 Green's table as unevaluated sums hi + lo of floats.
+__global__ void green_split_kernel(long long Gc, const double* __restrict__ green, float2* __restrict__ out) {
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < Gc; t += (long long)gridDim.x * blockDim.x) {
+        const double v = green[t];
+        const float hi = (float)v;
+        out[t] = make_float2(hi, (float)(v - (double)hi));
+    }
+}
+
 // Scaling of the half spectrum by the Green's table; blockIdx.y is the
 // right-hand side, so the table index needs no division.
 template <typename T>
@@ -1116,6 +1165,13 @@ void Mesh<T>::init(const MeshGeom& geom, int channels, double xi, double eta, do
     green.ensure(sizeof(T) * (size_t)g.Gc);
     green_kernel<T><<<grid_blocks(g.Gc, 256), 256, 0, s>>>(g, xi, eta, a, green.as<T>());
     IBP_CHECK_LAUNCH();
+    if constexpr (sizeof(T) == 8) {
+        if (df) {
+            green_df.ensure(sizeof(float2) * (size_t)g.Gc);
+            green_split_kernel<<<grid_blocks(g.Gc, 256), 256, 0, s>>>(g.Gc, green.as<double>(), green_df.as<float2>());
+            IBP_CHECK_LAUNCH();
+        }
+    }
 }
 
 template <typename T>
@@ -1176,6 +1232,7 @@ void Mesh<T>::destroy() {
     grid.release();
     spec.release();
     green.release();
+    green_df.release();
     work.release();
     rcap = 0;
 }
@@ -1206,7 +1263,7 @@ void Mesh<T>::transform(int ch, cudaStream_t s) {
     plans(ch, s);
     if constexpr (sizeof(T) == 8) {
         if (df) {
-            df_fft_convolve(g, ch, green.as<double>(), grid.as<double>(), df_buf.as<float4>(), df_tw, s);
+            df_fft_convolve(g, ch, green_df.as<float2>(), grid.as<double>(), df_buf.as<float4>(), df_tw, s);
             return;
         }
     }
@@ -1271,8 +1328,9 @@ const StencilCache* stencil_cache(ibpme_ctx* c, int n, const double* xw) {
     b.valid = false;
     int4* start = static_cast<int4*>(b.start.ensure(sizeof(int4) * n));
     double4* frac = static_cast<double4*>(b.frac.ensure(sizeof(double4) * n));
+    float4* frac32 = static_cast<float4*>(b.frac32.ensure(sizeof(float4) * n));
     double* w64 = static_cast<double*>(b.w64.ensure(sizeof(double) * 3 * (size_t)g.P * n));
-    stencil_cache_kernel<<<div_up(n, 256), 256, 0, c->stream>>>(n, xw, c->bcfg, g, start, frac, w64);
+    stencil_cache_kernel<<<div_up(n, 256), 256, 0, c->stream>>>(n, xw, c->bcfg, g, start, frac, frac32, w64);
     IBP_CHECK_LAUNCH();
     // tile bins when one warp per bead already fills the GPU and a region of
     // E^3 nodes does not wrap onto itself

@@ -386,6 +386,38 @@ def test_solve_charged_sphere_with_ions_full_size_mixed(cuda_lib):
     ib.pme_destroy(ctx)
 
 
+def test_mixed_warm_start_checks_once_in_fp64(cuda_lib):
+    """A mixed solve from a nearby guess (the previous step's charges, perturbed):
+    the first residual takes the FP32 mesh, one FP64 residual after the correction
+    confirms convergence, and the charges still match the dense FP64 oracle.  A
+    second context then solves the 2,050-ion system from the uniform guess, where
+    the FP32 start is too coarse for the first FP64 check: the solve refines on and
+    converges all the same."""
+    ib = cuda_lib
+    s = C.small_system(seed=13, n_bodies=3, level=2, n_ions=25, L=9.0, a=0.12, mesh=(48, 48, 48), tol=1e-7)
+    ctx = context(ib, s, precision="mixed")
+    try:
+        status, st, q, psi, S = _solve(ib, ctx, s, rtol=1e-9)
+        assert status == ib.IBPME_OK
+        rng = np.random.default_rng(5)
+        guess = q[0] * (1.0 + 1e-4 * rng.standard_normal(s.n))
+        status, st, q, psi, S = _solve(ib, ctx, s, rtol=1e-6, guess=guess)
+        assert status == ib.IBPME_OK and st.rel_residual <= 1e-6
+        assert st.matvecs_fp64 == 1 and st.outer == 1, (st.matvecs_fp64, st.outer)
+        _check_solution(s, q, psi, S, MIXED_RTOL)
+    finally:
+        ib.pme_destroy(ctx)
+    s2 = C.config2()
+    ctx = context(ib, s2)
+    try:
+        for _ in range(2):   # the second solve starts from the FP64 residual
+            status, st, q, psi, S = _solve(ib, ctx, s2, guess=s2.q_guess)
+            assert status == ib.IBPME_OK and st.rel_residual <= 1e-6
+        _check_solution(s2, q, psi, S, MIXED_RTOL)
+    finally:
+        ib.pme_destroy(ctx)
+
+
 def test_forces_torques_energy_fp64(cuda_lib):
     import torch
     ib = cuda_lib
