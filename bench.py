@@ -180,14 +180,12 @@ class Step:
         ib = self.ib
         bodies = ib.Bodies(self.off, self.X, self.Q)
         self.q.copy_(self.q0)
-        status, st = ib.induced_charge_solve(self.ctx, self.n, self.x, bodies, self.E0, 1, self.opts, self.q,
-                                             self.psi, self.S)
+        # solve + forces/torques/energy + BD step: one library call
+        status, st = ib.ibpme_bd_advance(self.ctx, self.n, self.x, bodies, self.E0[0], self.opts, self.q[0], DT,
+                                         1.0, 1.0, 1234, self.step_no, self.F, self.L, self.x_next, self.X_next,
+                                         psi_out=self.psi[0], f_bead=self.f, U=self.U)
         if status != ib.IBPME_OK:
             raise RuntimeError(f"solve did not converge: residual {st.rel_residual:.3e}")
-        ib.body_force_torque(self.ctx, self.n, self.x, self.q[0], bodies, self.E0[0], self.f, self.F, self.L,
-                             self.U)
-        ib.ibpme_bd_step(self.ctx, self.n, self.x, bodies, self.f, DT, 1.0, 1.0, 1234, self.step_no,
-                         self.x_next, self.X_next)
         self.x, self.x_next = self.x_next, self.x
         self.X, self.X_next = self.X_next, self.X
         self.step_no += 1
@@ -223,27 +221,20 @@ class HostStep:
         self.opts = ib.make_opts(rtol=1e-6, guess=ib.IBPME_GUESS_USER, precision=ib.IBPME_MIXED)
         self.step_no = 0
         body = self.off.nbytes + self.X.nbytes + self.Q.nbytes
-        # bytes copied per step, counted from the arrays each call stages
-        self.h2d = (self.x.nbytes + body + self.E0.nbytes + self.q.nbytes           # solve (q_out read as guess)
-                    + self.x.nbytes + self.q.nbytes + body + 24                     # forces
-                    + self.x.nbytes + body + self.f.nbytes)                         # BD step
-        self.d2h = (self.q.nbytes + self.psi.nbytes + self.S.nbytes
-                    + self.f.nbytes + self.F.nbytes + self.L.nbytes + self.U.nbytes
-                    + self.x_next.nbytes + self.X_next.nbytes)
+        # bytes copied per step, counted from the arrays the one call stages
+        self.h2d = self.x.nbytes + body + 24 + self.q.nbytes                  # q_io read as the guess
+        self.d2h = (self.q.nbytes + self.psi.nbytes + self.f.nbytes + self.F.nbytes + self.L.nbytes
+                    + self.U.nbytes + self.x_next.nbytes + self.X_next.nbytes)
 
     def run(self):
         ib = self.ib
         bodies = ib.Bodies(self.off, self.X, self.Q)
         self.q[:] = self.q0
-        status, st = ib.induced_charge_solve(self.ctx, self.s.n, self.x, bodies, self.E0, 1, self.opts, self.q,
-                                             self.psi, self.S)
+        status, st = ib.ibpme_bd_advance(self.ctx, self.s.n, self.x, bodies, self.E0[0], self.opts, self.q[0], DT,
+                                         1.0, 1.0, 1234, self.step_no, self.F, self.L, self.x_next, self.X_next,
+                                         psi_out=self.psi[0], f_bead=self.f, U=self.U)
         if status != ib.IBPME_OK:
             raise RuntimeError("host-buffer solve did not converge")
-        q0 = np.ascontiguousarray(self.q[0])
-        ib.body_force_torque(self.ctx, self.s.n, self.x, q0, bodies, np.ascontiguousarray(self.E0[0]), self.f,
-                             self.F, self.L, self.U)
-        ib.ibpme_bd_step(self.ctx, self.s.n, self.x, bodies, self.f, DT, 1.0, 1.0, 1234, self.step_no,
-                         self.x_next, self.X_next)
         self.x, self.x_next = self.x_next, self.x
         self.X, self.X_next = self.X_next, self.X
         self.step_no += 1
@@ -705,11 +696,10 @@ def bench_trajectory(args, ib, torch, rank, world, local):
     def step(x, X, xn, Xn, k, guess, mlp=None):
         bodies = ib.Bodies(off, X, Q)
         opts = ib.make_opts(rtol=1e-6, guess=guess, mlp=mlp)
-        status, st = ib.induced_charge_solve(ctx, n, x, bodies, E0, 1, opts, q)
+        status, st = ib.ibpme_bd_advance(ctx, n, x, bodies, E0[0], opts, q[0], 1e-3, 1.0, 1.0, 4321, k, F, L, xn, Xn,
+                                         f_bead=fb)
         if status != ib.IBPME_OK:
             raise RuntimeError("trajectory solve did not converge")
-        ib.body_force_torque(ctx, n, x, q[0], bodies, E0[0], fb, F, L)
-        ib.ibpme_bd_step(ctx, n, x, bodies, fb, 1e-3, 1.0, 1.0, 4321, k, xn, Xn)
         return st
 
     # training segment: zero-guess steps; converged charges -> (features, targets) of body beads

@@ -247,6 +247,32 @@ ibpme_status ibpme_bd_step(ibpme_ctx* ctx, int n, const double* x, const ibpme_b
                            const double* f_bead, const ibpme_bd_params* bd,
                            double* x_out, double* X_out);
 
+/* One step of the Brownian dynamics of Sec. V.A in one call: the induced-charge
+ * solve of Eq. saddle at the positions x for one field E0 [3] (options as
+ * induced_charge_solve), the bead forces of Eq. beadforce with the body forces,
+ * torques and energy of body_force_torque, and the Euler-Maruyama step of
+ * ibpme_bd_step with those bead forces.  The positions are checked, the bodies
+ * uploaded and the real-space pair table built once for the three parts.  The
+ * field of the forces is the gradient gathered from the FP64 mesh of the solve's
+ * final FP64 residual (which already holds the transformed potential of the final
+ * charges) plus the FP64 near field, and the energy takes that residual's FP64
+ * potentials: in an FP64 context the results equal the three separate calls up to
+ * rounding; in a mixed context the forces carry the FP64 mesh where
+ * body_force_torque takes the FP32 mesh.
+ *   q_io     [n] bead charges: the initial guess on input when opts->guess = USER,
+ *            the solution on output
+ *   psi_out  [N_b] Psi - Psi_0 per body, or NULL
+ *   f_bead   [n][3] bead forces without the hard-sphere part, or NULL
+ *   F, L     [N_b][3] body forces and torques;  U [1] energy, or NULL
+ *   x_out, X_out, bd  as ibpme_bd_step
+ *   stats    the solve's statistics, or NULL
+ * Returns IBPME_ERR_NOT_CONVERGED (charges and psi written, forces and positions
+ * not) if the solve hits max_iter. */
+ibpme_status ibpme_bd_advance(ibpme_ctx* ctx, int n, const double* x, const ibpme_bodies* bodies,
+                              const double* E0, const ibpme_solve_opts* opts, const ibpme_bd_params* bd,
+                              double* q_io, double* psi_out, double* f_bead, double* F, double* L, double* U,
+                              double* x_out, double* X_out, ibpme_solve_stats* stats);
+
 /* ---- Learned warm start (not in the paper) ----
  *
  * A small network (IBPME_MLP_IN features -> 64 -> 64 -> 1, tanh, FP32) maps

@@ -85,6 +85,9 @@ SIGNATURES = {
     "body_force_torque": (_i, [_p, _i, _p, _p, ctypes.POINTER(ibpme_bodies), _p, _p, _p, _p, _p]),
     "ibpme_bd_step": (_i, [_p, _i, _p, ctypes.POINTER(ibpme_bodies), _p, ctypes.POINTER(ibpme_bd_params),
                            _p, _p]),
+    "ibpme_bd_advance": (_i, [_p, _i, _p, ctypes.POINTER(ibpme_bodies), _p, ctypes.POINTER(ibpme_solve_opts),
+                              ctypes.POINTER(ibpme_bd_params), _p, _p, _p, _p, _p, _p, _p, _p,
+                              ctypes.POINTER(ibpme_solve_stats)]),
     "pme_spread_noalloc": (_i, [ctypes.POINTER(ibpme_params), _i, _p, _p, _i, _p, _p]),
     "ibpme_mlp_create": (_i, [ctypes.POINTER(_p), ctypes.c_ulonglong]),
     "ibpme_mlp_destroy": (_i, [_p]),
@@ -329,6 +332,20 @@ def ibpme_bd_step(ctx, n, x, bodies: Bodies, f_bead, dt, gamma=1.0, kT=1.0, seed
     bd = ibpme_bd_params(float(dt), float(gamma), float(kT), int(seed), int(step))
     return _check(load().ibpme_bd_step(ctx, int(n), ptr(x), ctypes.byref(bodies.c), ptr(f_bead),
                                        ctypes.byref(bd), ptr(x_out), ptr(X_out)), "ibpme_bd_step")
+
+
+def ibpme_bd_advance(ctx, n, x, bodies: Bodies, E0, opts: ibpme_solve_opts | None, q_io, dt, gamma=1.0, kT=1.0,
+                     seed=0, step=0, F=None, L=None, x_out=None, X_out=None, psi_out=None, f_bead=None, U=None):
+    """Solve, forces and one BD step in one call.  Returns (status, stats); raises on
+    any status other than OK / NOT_CONVERGED."""
+    bd = ibpme_bd_params(float(dt), float(gamma), float(kT), int(seed), int(step))
+    st = ibpme_solve_stats()
+    status = load().ibpme_bd_advance(ctx, int(n), ptr(x), ctypes.byref(bodies.c), ptr(E0),
+                                     ctypes.byref(opts) if opts is not None else None, ctypes.byref(bd), ptr(q_io),
+                                     ptr(psi_out), ptr(f_bead), ptr(F), ptr(L), ptr(U), ptr(x_out), ptr(X_out),
+                                     ctypes.byref(st))
+    _check(status, "ibpme_bd_advance", ok=(IBPME_OK, IBPME_ERR_NOT_CONVERGED))
+    return status, st
 
 
 def ibpme_kernel_launches() -> int:

@@ -283,6 +283,7 @@ void pme_reserve(ibpme_ctx* c, int n, int nrhs, bool field) {
 
 void pme_apply(ibpme_ctx* c, int n, const double* xw, const double* q, int nrhs, int prec, double* psi,
                double* E, bool near_ready, bool near32) {
+    c->grid64_final = false;   // the meshes are about to hold other charges
     if (!near_ready) near_build(c, n, xw, E != nullptr);
     const size_t m = (size_t)nrhs * n;
     pme_reserve(c, n, nrhs, E != nullptr);
@@ -529,13 +530,17 @@ struct ConfigScope {
     }
 };
 
-// Shared by induced_charge_solve (one configuration) and induced_charge_solve_batch.
-ibpme_status solve_entry(ibpme_ctx* c, int n, const double* x, const ibpme_bodies* bodies, int ncfg,
-                         const int* cfg_bodies, const double* E0, int nrhs, const ibpme_solve_opts* opts,
-                         double* q_out, double* psi_out, double* S_out, ibpme_solve_stats* stats) {
-    if (!c) fail(IBPME_ERR_ARG, "ctx is NULL");
-    DeviceScope ds(c->device);
-    const auto t0 = std::chrono::steady_clock::now();
+// One solve call up to its device outputs (shared by induced_charge_solve,
+// induced_charge_solve_batch and ibpme_bd_advance); the caller finishes the outputs.
+struct SolveCall {
+    SolveArgs a{};
+    OutArg oq, op, os;
+    std::vector<ibpme_solve_stats> st;
+};
+
+void solve_run(ibpme_ctx* c, int n, const double* x, const ibpme_bodies* bodies, int ncfg, const int* cfg_bodies,
+               const double* E0, int nrhs, const ibpme_solve_opts* opts, double* q_out, double* psi_out,
+               double* S_out, SolveCall& call) {
     check_n(n);
     if (n == 0) fail(IBPME_ERR_ARG, "a solve needs at least one bead");
     if (nrhs < 1 || nrhs > c->p.max_rhs) fail(IBPME_ERR_ARG, "nrhs %d outside 1..%d", nrhs, c->p.max_rhs);
@@ -546,7 +551,7 @@ ibpme_status solve_entry(ibpme_ctx* c, int n, const double* x, const ibpme_bodie
     ibpme_solve_opts o{};
     o.precision = -1;
     if (opts) o = *opts;
-    SolveArgs a{};
+    SolveArgs& a = call.a;
     a.n = n;
     a.nrhs = nrhs;
     a.prec = o.precision < 0 ? c->p.precision : o.precision;
@@ -572,37 +577,89 @@ ibpme_status solve_entry(ibpme_ctx* c, int n, const double* x, const ibpme_bodie
     prepare_bodies(c, n, bodies, xw, ncfg, cfg_bodies);
     ConfigScope scope(c, ncfg);
     const int nb = bodies->n_bodies;
-    OutArg oq = stage_out(c, q_out, sizeof(double) * (size_t)nrhs * n, c->st_out1, a.user_guess);
-    OutArg op = stage_out(c, psi_out, sizeof(double) * (size_t)nrhs * nb, c->st_out2);
-    OutArg os = stage_out(c, S_out, sizeof(double) * 3 * (size_t)nrhs * nb, c->st_out3);
-    a.q = static_cast<double*>(oq.dev);
-    a.psi = static_cast<double*>(op.dev);
+    call.oq = stage_out(c, q_out, sizeof(double) * (size_t)nrhs * n, c->st_out1, a.user_guess);
+    call.op = stage_out(c, psi_out, sizeof(double) * (size_t)nrhs * nb, c->st_out2);
+    call.os = stage_out(c, S_out, sizeof(double) * 3 * (size_t)nrhs * nb, c->st_out3);
+    a.q = static_cast<double*>(call.oq.dev);
+    a.psi = static_cast<double*>(call.op.dev);
     if (a.learned) learned_guess(c, static_cast<const ibpme_mlp*>(o.mlp), n, xw, a.E0, nrhs, a.q);
-    std::vector<ibpme_solve_stats> st(ncfg);
-    solve(c, a, st.data());
-    if (S_out) body_dipoles(c, n, a.q, nrhs, static_cast<double*>(os.dev));
-    finish_out(c, oq);
-    finish_out(c, op);
-    finish_out(c, os);
-    // the last convergence check has synchronised; device outputs are stream-ordered,
-    // host outputs must have arrived before the call returns
-    if (oq.host || op.host || os.host) IBP_CUDA(cudaStreamSynchronize(c->stream));
+    call.st.assign(ncfg, ibpme_solve_stats{});
+    solve(c, a, call.st.data());
+    if (S_out) body_dipoles(c, n, a.q, nrhs, static_cast<double*>(call.os.dev));
+}
+
+// Statistics of a finished solve call into stats[ncfg]; the call's status.
+ibpme_status solve_status(SolveCall& call, std::chrono::steady_clock::time_point t0, ibpme_solve_stats* stats) {
     const double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
     double worst = 0.0;
     bool finite = true;
-    for (auto& e : st) {
+    for (auto& e : call.st) {
         e.time_ms = ms;
         finite = finite && std::isfinite(e.rel_residual);
         worst = std::max(worst, e.rel_residual);
     }
     if (stats)
-        for (int k = 0; k < ncfg; ++k) stats[k] = st[k];
+        for (size_t k = 0; k < call.st.size(); ++k) stats[k] = call.st[k];
     if (!finite) fail(IBPME_ERR_NONFINITE, "non-finite residual in the solve");
-    if (!(worst <= a.rtol)) {
-        set_error("not converged: relative residual %.3e after %d iterations", worst, st[0].iters);
+    if (!(worst <= call.a.rtol)) {
+        set_error("not converged: relative residual %.3e after %d iterations", worst, call.st[0].iters);
         return IBPME_ERR_NOT_CONVERGED;
     }
     return IBPME_OK;
+}
+
+ibpme_status solve_entry(ibpme_ctx* c, int n, const double* x, const ibpme_bodies* bodies, int ncfg,
+                         const int* cfg_bodies, const double* E0, int nrhs, const ibpme_solve_opts* opts,
+                         double* q_out, double* psi_out, double* S_out, ibpme_solve_stats* stats) {
+    if (!c) fail(IBPME_ERR_ARG, "ctx is NULL");
+    DeviceScope ds(c->device);
+    const auto t0 = std::chrono::steady_clock::now();
+    SolveCall call;
+    solve_run(c, n, x, bodies, ncfg, cfg_bodies, E0, nrhs, opts, q_out, psi_out, S_out, call);
+    finish_out(c, call.oq);
+    finish_out(c, call.op);
+    finish_out(c, call.os);
+    // the last convergence check has synchronised; device outputs are stream-ordered,
+    // host outputs must have arrived before the call returns
+    if (call.oq.host || call.op.host || call.os.host) IBP_CUDA(cudaStreamSynchronize(c->stream));
+    return solve_status(call, t0, stats);
+}
+
+// Potential psi [n] and field E [n][3] of the charges q at the positions of the
+// solve that just produced them (near table and stencils current).  The FP64 mesh
+// grid of the solve's final residual already holds these charges' transformed
+// potential and the Krylov state their FP64 potentials: the field is one gradient
+// gather of that grid plus the near field, and the potentials are taken as they are.
+// Without that evaluation (the solve skipped it) one full evaluation.
+const double* solution_field(ibpme_ctx* c, int n, const double* xw, const double* q, double* psi, double* E) {
+    const double* psi64 = solve_potentials(c);
+    if (!psi64) {
+        pme_apply(c, n, xw, q, 1, c->p.precision, psi, E, true);
+        return psi;
+    }
+    pme_reserve(c, n, 1, true);
+    double* er = c->E_r.as<double>();
+    double* ek = c->E_k.as<double>();
+    const cudaStream_t main = c->stream;
+    IBP_CUDA(cudaEventRecord(c->ev_fork, main));
+    IBP_CUDA(cudaStreamWaitEvent(c->aux, c->ev_fork, 0));
+    {
+        struct Restore {
+            ibpme_ctx* c;
+            cudaStream_t s;
+            ~Restore() { c->stream = s; }
+        } restore{c, main};
+        c->stream = c->aux;
+        near_field(c, n, xw, q, 1, er);
+    }
+    IBP_CUDA(cudaEventRecord(c->ev_join, c->aux));
+    const StencilCache* sc = stencil_cache(c, n, xw);
+    c->mesh64.gather(n, xw, 1, nullptr, c->psi_k.as<double>(), ek, c->stream, sc);
+    IBP_CUDA(cudaStreamWaitEvent(c->stream, c->ev_join, 0));
+    add_kernel<<<div_up(3LL * n, 256), 256, 0, c->stream>>>(3LL * n, er, ek, E);
+    IBP_CHECK_LAUNCH();
+    c->grid64_final = false;
+    return psi64;
 }
 
 }  // namespace
@@ -657,6 +714,55 @@ IBP_API ibpme_status body_force_torque(ibpme_ctx* c, int n, const double* x, con
         finish_out(c, oL);
         finish_out(c, oU);
         if (of.host || oF.host || oL.host || oU.host) IBP_CUDA(cudaStreamSynchronize(c->stream));
+        return IBPME_OK;
+    });
+}
+
+IBP_API ibpme_status ibpme_bd_advance(ibpme_ctx* c, int n, const double* x, const ibpme_bodies* bodies,
+                                      const double* E0, const ibpme_solve_opts* opts, const ibpme_bd_params* bd,
+                                      double* q_io, double* psi_out, double* f_bead, double* F, double* L,
+                                      double* U, double* x_out, double* X_out, ibpme_solve_stats* stats) {
+    return guard([&]() -> ibpme_status {
+        if (!c) fail(IBPME_ERR_ARG, "ctx is NULL");
+        DeviceScope ds(c->device);
+        const auto t0 = std::chrono::steady_clock::now();
+        if (!bd || !F || !L || !x_out || !X_out) fail(IBPME_ERR_ARG, "bd, F, L, x_out and X_out are required");
+        if (!(bd->dt > 0) || !(bd->gamma > 0) || !(bd->kT >= 0)) fail(IBPME_ERR_ARG, "need dt > 0, gamma > 0, kT >= 0");
+        // the solve: positions staged and wrapped, bodies uploaded and the near table
+        // built once for the whole step
+        SolveCall call;
+        solve_run(c, n, x, bodies, 1, nullptr, E0, 1, opts, q_io, psi_out, nullptr, call);
+        const ibpme_status status = solve_status(call, t0, stats);
+        if (status != IBPME_OK) {   // not converged: charges written, nothing moves
+            finish_out(c, call.oq);
+            finish_out(c, call.op);
+            IBP_CUDA(cudaStreamSynchronize(c->stream));
+            return status;
+        }
+        const int nb = bodies->n_bodies;
+        const double* xw = call.a.xw;
+        const double* q = call.a.q;
+        const double* dE0 = call.a.E0;
+        OutArg of = stage_out(c, f_bead, sizeof(double) * 3 * n, c->st_out5);
+        OutArg oF = stage_out(c, F, sizeof(double) * 3 * nb, c->st_out3);
+        OutArg oL = stage_out(c, L, sizeof(double) * 3 * nb, c->st_out4);
+        OutArg oU = stage_out(c, U, sizeof(double), c->st_out6);
+        OutArg ox = stage_out(c, x_out, sizeof(double) * 3 * n, c->st_out7);
+        OutArg oX = stage_out(c, X_out, sizeof(double) * 3 * nb, c->st_out8);
+        // forces, torques and energy of the solution (Eq. beadforce, Sec. III.C, Eq. pot_syst)
+        double* buf = static_cast<double*>(c->qfull.ensure(sizeof(double) * 4 * n));   // psi [n] then E [n][3]
+        double* E = buf + n;
+        const double* psi = solution_field(c, n, xw, q, buf, E);
+        double* f = of.dev ? static_cast<double*>(of.dev) : static_cast<double*>(c->st_f.ensure(sizeof(double) * 3 * n));
+        bead_forces(c, n, q, dE0, E, f);
+        body_reduce_force_torque(c, n, f, static_cast<double*>(oF.dev), static_cast<double*>(oL.dev));
+        if (U) body_energy(c, n, q, psi, dE0, static_cast<double*>(oU.dev));
+        // the Euler-Maruyama step (Eq. forward) with the hard-sphere forces of Eq. hardsphereFD
+        bd_step(c, n, xw, f, bd, static_cast<double*>(ox.dev), static_cast<double*>(oX.dev));
+        for (const OutArg* o : {&call.oq, &call.op, &of, &oF, &oL, &oU, &ox, &oX}) finish_out(c, *o);
+        bool host = false;
+        for (const OutArg* o : {&call.oq, &call.op, &of, &oF, &oL, &oU, &ox, &oX}) host = host || o->host;
+        if (host) IBP_CUDA(cudaStreamSynchronize(c->stream));
         return IBPME_OK;
     });
 }

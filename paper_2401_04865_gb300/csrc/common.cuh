@@ -339,7 +339,8 @@ struct ibpme_ctx {
     ibp::DevBuf psi_r, psi_k, E_r, E_k;   // [R][n], [R][n][3]
     ibp::DevBuf qfull;       // [R][n]
     // staging of host arrays
-    ibp::DevBuf st_x, st_q, st_out1, st_out2, st_out3, st_out4, st_E0, st_off, st_X, st_Q, st_f;
+    ibp::DevBuf st_x, st_q, st_out1, st_out2, st_out3, st_out4, st_out5, st_out6, st_out7, st_out8, st_E0, st_off, st_X,
+        st_Q, st_f;
     ibp::DevBuf scalars;     // small device scratch
     void* pinned = nullptr;  // small pinned host scratch
     size_t pinned_bytes = 0;
@@ -352,6 +353,9 @@ struct ibpme_ctx {
     // mixed solves whose first residual takes the FP64 operator after an FP32-mesh start
     // missed the tolerance at the first FP64 check (counts down once per solve)
     int start32_skip = 0;
+    // the FP64 mesh grid and the Krylov potentials hold the last solve's final FP64
+    // residual evaluation (the field of the solution charges can be gathered from it)
+    bool grid64_final = false;
     ibp::DevBuf ml_feat, ml_scratch, ml_scales, ml_y;   // learned warm start
     cudaEvent_t ev_in = nullptr, ev_out = nullptr;
     ibp::StencilCache stencils;               // stencils of the current positions
@@ -432,6 +436,9 @@ struct SolveArgs {
     bool precond;       // body-block right preconditioner
 };
 void solve(ibpme_ctx* c, const SolveArgs& a, ibpme_solve_stats* st);
+// FP64 potentials [nrhs][n] of the last solve's final residual evaluation (its FP64
+// mesh grid still holds the same charges), or NULL when that evaluation was skipped
+const double* solve_potentials(ibpme_ctx* c);
 // precond.cu
 bool precond_prepare(ibpme_ctx* c);   // false: no body qualifies
 void precond_apply(ibpme_ctx* c, int R, const double* u, long long ustride, const int* jdev, int nk, double* out);

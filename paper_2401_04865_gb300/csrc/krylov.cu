@@ -836,12 +836,14 @@ struct Solver {
         const BodyData& bd = c->bodies;
         if (zero_charges) {
             IBP_CUDA(cudaMemsetAsync(k->psi_tot.p, 0, sizeof(double) * (size_t)R * n, s()));
+            c->grid64_final = false;   // no evaluation: the grid holds other charges
         } else {
             compose_kernel<<<blocks_for((long long)n * R), 256, 0, s()>>>(n, nk, R, I(bd.bead_unk), I(bd.bead_body),
                                                                            bd.Q.as<double>(), D(k->x), D(k->qtot));
             IBP_CHECK_LAUNCH();
             pme_apply(c, n, a.xw, D(k->qtot), R, prec, D(k->psi_tot), nullptr, true);
             if (prec == IBPME_FP64) ++matvec64;
+            c->grid64_final = prec == IBPME_FP64;
         }
         if (fit_psi && nmb > 0) {
             fit_psi_kernel<<<blocks_for(32LL * nmb * R), 256, 0, s()>>>(nmb, nk, n, R, I(bd.mb_body), I(bd.mb_unk),
@@ -1067,8 +1069,13 @@ struct Solver {
 
 }  // namespace
 
+const double* solve_potentials(ibpme_ctx* c) {
+    return c->kry && c->grid64_final ? c->kry->psi_tot.as<double>() : nullptr;
+}
+
 void solve(ibpme_ctx* c, const SolveArgs& a, ibpme_solve_stats* st) {
     if (!c->kry) c->kry = new Krylov();
+    c->grid64_final = false;
     // The solve runs on the context's own non-blocking stream (graph capture is not
     // possible on the legacy default stream), ordered after and before the caller's.
     cudaStream_t user = c->stream;

@@ -275,32 +275,35 @@ void gather_dispatch(int n, const double* xw, int nrhs, const int* cfg, const Me
 // ---------------------------------------------------------------------------
 constexpr int kPairWarps = 4;   // warps per block
 
+// One thread per (bead, axis, stencil node l < P): the first node of the axis, the
+// fractional offset and the FP64 window of node l (GB300 evaluates FP64 exp at a small
+// fraction of its FP32 rate, so the windows are spread over the whole GPU).  The
+// thread of node 0 writes the axis's start and offsets; axis 0 also the configuration.
 __global__ void stencil_cache_kernel(int n, const double* __restrict__ xw, const int* __restrict__ bcfg, MeshGeom g,
                                      int4* __restrict__ start, double4* __restrict__ frac, float4* __restrict__ frac32,
                                      double* __restrict__ w64) {
-    const int b = blockIdx.x * blockDim.x + threadIdx.x;
-    if (b >= n) return;
-    int s0[3];
-    double f[3];
-#pragma unroll
-    for (int d = 0; d < 3; ++d) {
-        const double u = xw[3 * b + d] * g.inv_h[d];
-        const double sf = floor(u - 0.5 * g.P) + 1.0;
-        f[d] = sf - u;
-        int idx = (int)sf % g.N[d];
-        if (idx < 0) idx += g.N[d];
-        s0[d] = idx;
+    const int P = g.P;
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= 3LL * P * n) return;
+    const int b = (int)(t / (3 * P));
+    const int rem = (int)(t - (long long)b * 3 * P);
+    const int d = rem / P, l = rem - d * P;
+    const double u = xw[3 * b + d] * g.inv_h[d];
+    const double sf = floor(u - 0.5 * P) + 1.0;
+    const double f = sf - u;
+    const double tt = f + (double)l;
+    w64[((size_t)b * 3 + d) * P + l] = exp(-g.kappa[d] * tt * tt);   // exactly as the kernels evaluate them
+    if (l != 0) return;
+    int idx = (int)sf % g.N[d];
+    if (idx < 0) idx += g.N[d];
+    reinterpret_cast<int*>(start + b)[d] = idx;
+    reinterpret_cast<double*>(frac + b)[d] = f;
+    reinterpret_cast<float*>(frac32 + b)[d] = (float)f;
+    if (d == 0) {
+        reinterpret_cast<int*>(start + b)[3] = bcfg ? bcfg[b] : 0;
+        reinterpret_cast<double*>(frac + b)[3] = 0.0;
+        reinterpret_cast<float*>(frac32 + b)[3] = 0.0f;
     }
-    start[b] = make_int4(s0[0], s0[1], s0[2], bcfg ? bcfg[b] : 0);
-    frac[b] = make_double4(f[0], f[1], f[2], 0.0);
-    frac32[b] = make_float4((float)f[0], (float)f[1], (float)f[2], 0.0f);
-    // the FP64 windows exp(-kappa (f + l)^2), l < P, exactly as the kernels evaluate them
-    double* w = w64 + (size_t)b * 3 * g.P;
-    for (int d = 0; d < 3; ++d)
-        for (int l = 0; l < g.P; ++l) {
-            const double t = f[d] + (double)l;
-            w[d * g.P + l] = exp(-g.kappa[d] * t * t);
-        }
 }
 
 // FP32 kernels take every constant and offset in FP32: GB300 issues FP64
@@ -1330,7 +1333,8 @@ const StencilCache* stencil_cache(ibpme_ctx* c, int n, const double* xw) {
     double4* frac = static_cast<double4*>(b.frac.ensure(sizeof(double4) * n));
     float4* frac32 = static_cast<float4*>(b.frac32.ensure(sizeof(float4) * n));
     double* w64 = static_cast<double*>(b.w64.ensure(sizeof(double) * 3 * (size_t)g.P * n));
-    stencil_cache_kernel<<<div_up(n, 256), 256, 0, c->stream>>>(n, xw, c->bcfg, g, start, frac, frac32, w64);
+    stencil_cache_kernel<<<div_up(3LL * g.P * n, 256), 256, 0, c->stream>>>(n, xw, c->bcfg, g, start, frac, frac32,
+                                                                             w64);
     IBP_CHECK_LAUNCH();
     // tile bins when one warp per bead already fills the GPU and a region of
     // E^3 nodes does not wrap onto itself

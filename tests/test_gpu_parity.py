@@ -472,6 +472,67 @@ def test_bd_step_matches_oracle(cuda_lib):
     ib.pme_destroy(ctx)
 
 
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_bd_advance_matches_oracle_and_the_three_calls(cuda_lib, prec):
+    """ibpme_bd_advance (solve + forces + BD step in one call) against the dense FP64
+    oracle (charges, bead forces, body forces, torques, energy; then the BD step of
+    the oracle from the oracle's forces) and against induced_charge_solve,
+    body_force_torque and ibpme_bd_step called in sequence.  Its forces gather the
+    field from the FP64 mesh of the solve's final residual, so they meet the FP64
+    bar also in a mixed context."""
+    import torch
+    ib = cuda_lib
+    s = C.small_system(seed=23, n_bodies=2, level=2, n_ions=12, L=8.0, a=0.14, mesh=(48, 48, 48), tol=1e-8)
+    n, nb = s.n, s.n_bodies
+    dt, gamma, kT, seed, step = 1e-3, 1.1, 0.8, 777, 3
+    qr, psr = o.solve_dense(s.x, s.body_offsets, s.X, s.Q, s.E0[0], s.box, s.a, s.eps)
+    f_ref = o.bead_forces(s.x, qr, s.E0[0], s.box, s.a, s.eps)
+    F_ref, L_ref = o.body_force_torque(s.x, s.X, s.body_offsets, f_ref, s.box)
+    U_ref = o.energy(s.X, s.Q, psr, o.dipoles(s.x, s.X, s.body_offsets, qr, s.box), s.E0[0])
+    f_tot = f_ref + o.hard_sphere_forces(s.x, s.body_offsets, s.box, s.a, gamma, dt)
+    xr, Xr = o.bd_step(s.x, s.X, s.body_offsets, f_tot, s.box, s.a, dt, gamma=gamma, kT=kT, seed=seed, step=step)
+    z = lambda *shape: torch.zeros(shape, dtype=torch.float64, device="cuda")
+    ctx = context(ib, s, precision=prec)
+    try:
+        bodies = ib.Bodies(cuda(s.body_offsets.astype(np.int32)), cuda(s.X), cuda(s.Q))
+        opts = ib.make_opts(rtol=1e-10)
+        # one call
+        q, psi, f, F, L, U, xo, Xo = z(1, n), z(1, nb), z(n, 3), z(nb, 3), z(nb, 3), z(1), z(n, 3), z(nb, 3)
+        status, st = ib.ibpme_bd_advance(ctx, n, cuda(s.x), bodies, cuda(s.E0[0]), opts, q, dt, gamma, kT, seed,
+                                         step, F, L, xo, Xo, psi_out=psi, f_bead=f, U=U)
+        torch.cuda.synchronize()
+        assert status == ib.IBPME_OK and st.rel_residual <= 1e-10
+        one = [t.cpu().numpy() for t in (q, psi, f, F, L, U, xo, Xo)]
+        # three calls
+        q3, psi3, f3, F3, L3, U3, xo3, Xo3 = z(1, n), z(1, nb), z(n, 3), z(nb, 3), z(nb, 3), z(1), z(n, 3), z(nb, 3)
+        status, st = ib.induced_charge_solve(ctx, n, cuda(s.x), bodies, cuda(s.E0[:1]), 1, opts, q3, psi3)
+        assert status == ib.IBPME_OK
+        ib.body_force_torque(ctx, n, cuda(s.x), q3[0], bodies, cuda(s.E0[0]), f3, F3, L3, U3)
+        ib.ibpme_bd_step(ctx, n, cuda(s.x), bodies, f3, dt, gamma, kT, seed, step, xo3, Xo3)
+        torch.cuda.synchronize()
+        three = [t.cpu().numpy() for t in (q3, psi3, f3, F3, L3, U3, xo3, Xo3)]
+    finally:
+        ib.pme_destroy(ctx)
+    q, psi, f, F, L, U, xo, Xo = one
+    assert rel_err(q[0], qr) < FP64_RTOL
+    assert rel_err(f, f_ref) < FP64_RTOL and rel_err(F, F_ref) < FP64_RTOL
+    r = o.relative_positions(s.x, s.X, s.body_offsets, s.box)
+    moment = np.add.reduceat(np.linalg.norm(r, axis=1) * np.linalg.norm(f_ref, axis=1), s.body_offsets[:-1])
+    assert np.max(np.abs(L - L_ref)) < FP64_RTOL * moment.max()
+    assert abs(U[0] - U_ref) < FP64_RTOL * abs(U_ref)
+    # the step moves by F dt / gamma + noise: compare the displacement with the oracle's
+    disp_ref = o.min_image(xr - s.x, s.box)
+    assert np.max(np.abs(o.min_image(xo - xr, s.box))) < FP64_RTOL * np.abs(disp_ref).max()
+    assert np.max(np.abs(o.min_image(Xo - Xr, s.box))) < FP64_RTOL * np.abs(disp_ref).max()
+    # against the three calls: the same solve; the forces agree to the three-call
+    # path's mesh precision
+    bar = 1e-9 if prec == "fp64" else MIXED_RTOL
+    assert rel_err(q[0], three[0][0]) < 1e-9 and rel_err(psi[0], three[1][0]) < 1e-7
+    assert rel_err(f, three[2]) < bar and rel_err(F, three[3]) < bar
+    assert abs(U[0] - three[5][0]) < bar * abs(U[0])
+    assert np.max(np.abs(o.min_image(xo - three[6], s.box))) < bar * np.abs(disp_ref).max()
+
+
 def test_full_size_lattice_field_sampled(cuda_lib):
     """64 spheres + 100,000 ions on 256^3 in mixed precision: the potential at a
     seeded sample of beads against the oracle's exact Ewald sum at those beads."""
