@@ -34,13 +34,15 @@ __global__ void rel_kernel(int n, const double* __restrict__ xw, const int* __re
 }
 
 // Block roles of the per-body kernels (kBodyThreads threads per block): the first
-// body_ion_blocks(nb) blocks take one body per thread and handle the single-bead bodies
-// (ions, most of the bodies of an electrolyte); the others take one multi-bead body per
-// warp from the list mb_body.  Returns false for threads without work; the warp role
-// returns warp-uniformly.
+// body_ion_blocks(nb) blocks take one body per thread of their first kIonsPerBlock
+// threads and handle the single-bead bodies (ions, most of the bodies of an
+// electrolyte; few per block, so that the FP64 noise of the BD step spreads over
+// many SMs); the others take one multi-bead body per warp from the list mb_body.
+// Returns false for threads without work; the warp role returns warp-uniformly.
 constexpr int kBodyThreads = 256;
+constexpr int kIonsPerBlock = 32;
 
-__host__ __device__ __forceinline__ int body_ion_blocks(int nb) { return (nb + kBodyThreads - 1) / kBodyThreads; }
+__host__ __device__ __forceinline__ int body_ion_blocks(int nb) { return (nb + kIonsPerBlock - 1) / kIonsPerBlock; }
 
 __device__ __forceinline__ bool body_role(int nb, int nmb, const int* __restrict__ mb_body, const int* __restrict__ off,
                                           int& body, int& lane, bool& ion) {
@@ -48,8 +50,8 @@ __device__ __forceinline__ bool body_role(int nb, int nmb, const int* __restrict
     if ((int)blockIdx.x < ib) {
         ion = true;
         lane = 0;
-        body = (int)blockIdx.x * kBodyThreads + (int)threadIdx.x;
-        return body < nb && off[body + 1] - off[body] == 1;
+        body = (int)blockIdx.x * kIonsPerBlock + (int)threadIdx.x;
+        return (int)threadIdx.x < kIonsPerBlock && body < nb && off[body + 1] - off[body] == 1;
     }
     ion = false;
     lane = threadIdx.x & 31;
@@ -206,20 +208,29 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k) {
 // r < 2a between beads of different bodies (Eq. hardsphereFD).
 // The pair table's rows and columns are in the cell-sorted order: row t is
 // bead order[t].
-__global__ void hard_sphere_kernel(int n, const double* __restrict__ xw, double L0, double L1, double L2,
-                                   const long long* __restrict__ rowptr, const int* __restrict__ col,
-                                   const int* __restrict__ order, const int* __restrict__ bead_body, double a,
-                                   double coef, const double* __restrict__ f_in, double* __restrict__ f_out) {
+// Pairs are screened with the FP32 positions (a margin far above their rounding);
+// the few that may overlap are decided in FP64.
+__global__ void hard_sphere_kernel(int n, const double* __restrict__ xw, const float4* __restrict__ xf, double L0,
+                                   double L1, double L2, const long long* __restrict__ rowptr,
+                                   const int* __restrict__ col, const int* __restrict__ order,
+                                   const int* __restrict__ bead_body, double a, double coef,
+                                   const double* __restrict__ f_in, double* __restrict__ f_out) {
     const int t = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (t >= n) return;
     const int al = order[t];
-    const int ba = bead_body[al];
-    const double x0 = xw[3 * al], y0 = xw[3 * al + 1], z0 = xw[3 * al + 2];
+    const float4 pa = xf[al];
+    const float Lx = (float)L0, Ly = (float)L1, Lz = (float)L2;
+    const float lim = (float)(4.0 * a * a * (1.0 + 1e-3)) + 1e-5f;
     double fx = 0, fy = 0, fz = 0;
     for (long long p = rowptr[t] + lane; p < rowptr[t + 1]; p += 32) {
         const int be = order[col[p]];
-        if (bead_body[be] == ba) continue;
+        const float4 pb = xf[be];
+        const float ex = min_image_wrapped(pa.x - pb.x, Lx), ey = min_image_wrapped(pa.y - pb.y, Ly);
+        const float ez = min_image_wrapped(pa.z - pb.z, Lz);
+        if (ex * ex + ey * ey + ez * ez >= lim) continue;
+        if (bead_body[be] == bead_body[al]) continue;
+        const double x0 = xw[3 * al], y0 = xw[3 * al + 1], z0 = xw[3 * al + 2];
         const double dx = min_image_wrapped(x0 - xw[3 * be], L0);
         const double dy = min_image_wrapped(y0 - xw[3 * be + 1], L1);
         const double dz = min_image_wrapped(z0 - xw[3 * be + 2], L2);
@@ -538,7 +549,7 @@ void bd_step(ibpme_ctx* c, int n, const double* xw, const double* f, const ibpme
     double* ftot = static_cast<double*>(bd.scratch.ensure(sizeof(double) * (3 * (size_t)n + 9 * (size_t)bd.nb)));
     double* Rm = ftot + 3 * (size_t)n;
     hard_sphere_kernel<<<div_up((long long)n * 32, 128), 128, 0, s>>>(
-        n, xw, c->p.box[0], c->p.box[1], c->p.box[2], nl.rowptr.as<long long>(), nl.col.as<int>(),
+        n, xw, nl.xf.as<float4>(), c->p.box[0], c->p.box[1], c->p.box[2], nl.rowptr.as<long long>(), nl.col.as<int>(),
         nl.cell_beads.as<int>(), bd.bead_body.as<int>(), c->a, p->gamma / (2.0 * p->dt), f, ftot);
     IBP_CHECK_LAUNCH();
     BdConst bc{p->dt, p->gamma, p->kT, p->seed, (unsigned)(p->step & 0xffffffffLL)};

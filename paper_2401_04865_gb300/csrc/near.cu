@@ -207,8 +207,8 @@ __global__ void pos32_kernel(int n, const double* __restrict__ xw, float4* __res
     if (i < n) xf[i] = make_float4((float)xw[3 * i], (float)xw[3 * i + 1], (float)xw[3 * i + 2], 0.0f);
 }
 
-// Visits every bead beta != alpha of the neighbouring cells, lanes striding
-// over each cell; calls f(beta, slot, dx, dy, dz, r2, within) for every lane
+// Visits every bead beta != alpha of the neighbouring cells, 32 candidates per
+// round across the cells; calls f(beta, slot, dx, dy, dz, r2, within) for every lane
 // slot (within = false for idle lanes) so that warp-collective code can run in
 // f; slot is beta's position in the cell-sorted bead order.
 // Candidates are screened in FP32 with a margin far above its rounding, and
@@ -219,6 +219,7 @@ __device__ __forceinline__ void for_neighbours(int alpha, const double* __restri
                                                const float4* __restrict__ xf, const PairConst& k,
                                                const int* __restrict__ cell_of, const int* __restrict__ cell_start,
                                                const int* __restrict__ cell_beads, int lane, F&& f) {
+    const unsigned full = 0xffffffffu;
     const double x0 = xw[3 * alpha + 0], y0 = xw[3 * alpha + 1], z0 = xw[3 * alpha + 2];
     const float4 p0 = xf[alpha];
     const float Lx = (float)k.L[0], Ly = (float)k.L[1], Lz = (float)k.L[2];
@@ -229,37 +230,65 @@ __device__ __forceinline__ void for_neighbours(int alpha, const double* __restri
     const int skip_body = (ba >= 0 && k.cflag[ba]) ? ba : -1;   // alpha's compact body, or -1
     const int c = cell_of[alpha] - base;
     const int cx = c % k.nc[0], cy = (c / k.nc[0]) % k.nc[1], cz = c / (k.nc[0] * k.nc[1]);
-    for (int oz = k.lo[2]; oz <= k.hi[2]; ++oz)
-        for (int oy = k.lo[1]; oy <= k.hi[1]; ++oy)
-            for (int ox = k.lo[0]; ox <= k.hi[0]; ++ox) {
-                const int nx = (cx + ox + k.nc[0]) % k.nc[0];
-                const int ny = (cy + oy + k.nc[1]) % k.nc[1];
-                const int nz = (cz + oz + k.nc[2]) % k.nc[2];
-                const int cell = base + (nz * k.nc[1] + ny) * k.nc[0] + nx;
-                const int s = cell_start[cell], e = cell_start[cell + 1];
-                for (int t0 = s; t0 < e; t0 += 32) {
-                    const int t = t0 + lane;
-                    bool within = false;
-                    int beta = -1;
-                    double dx = 0, dy = 0, dz = 0, r2 = 0;
-                    if (t < e) {
-                        beta = cell_beads[t];
-                        const float4 pb = xf[beta];
-                        const float fx = min_image_wrapped(p0.x - pb.x, Lx);
-                        const float fy = min_image_wrapped(p0.y - pb.y, Ly);
-                        const float fz = min_image_wrapped(p0.z - pb.z, Lz);
-                        if (beta != alpha && fx * fx + fy * fy + fz * fz < rc2f &&
-                            (skip_body < 0 || k.bbody[beta] != skip_body)) {
-                            dx = min_image_wrapped(x0 - xw[3 * beta + 0], k.L[0]);
-                            dy = min_image_wrapped(y0 - xw[3 * beta + 1], k.L[1]);
-                            dz = min_image_wrapped(z0 - xw[3 * beta + 2], k.L[2]);
-                            r2 = dx * dx + dy * dy + dz * dz;
-                            within = r2 < k.rc2;
-                        }
-                    }
-                    f(beta, t, dx, dy, dz, r2, within);
+    const int wx = k.hi[0] - k.lo[0] + 1, wy = k.hi[1] - k.lo[1] + 1, wz = k.hi[2] - k.lo[2] + 1;
+    const int nnb = wx * wy * wz;
+    // Neighbour cells 32 at a time, lane l holding cell g0 + l of the (z, y, x)
+    // offset order and its bead range; their candidates, concatenated in that
+    // order, are then taken 32 per round.  A warp's dependent loads per row are
+    // one round for the cell ranges plus one per 32 candidates, instead of one
+    // chain per neighbour cell.
+    for (int g0 = 0; g0 < nnb; g0 += 32) {
+        const int g = g0 + lane;
+        int s = 0, cnt = 0;
+        if (g < nnb) {
+            const int ox = k.lo[0] + g % wx, oy = k.lo[1] + (g / wx) % wy, oz = k.lo[2] + g / (wx * wy);
+            const int nx = (cx + ox + k.nc[0]) % k.nc[0];
+            const int ny = (cy + oy + k.nc[1]) % k.nc[1];
+            const int nz = (cz + oz + k.nc[2]) % k.nc[2];
+            const int cell = base + (nz * k.nc[1] + ny) * k.nc[0] + nx;
+            s = cell_start[cell];
+            cnt = cell_start[cell + 1] - s;
+        }
+        int incl = cnt;   // inclusive prefix of the counts over the lanes
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const int v = __shfl_up_sync(full, incl, d);
+            if (lane >= d) incl += v;
+        }
+        const int excl = incl - cnt;
+        const int total = __shfl_sync(full, incl, 31);
+        for (int i0 = 0; i0 < total; i0 += 32) {
+            const int i = i0 + lane;
+            // the lane whose range holds candidate i: the largest j with excl_j <= i
+            // (its count is then non-zero); j + step never passes lane 31
+            int j = 0;
+#pragma unroll
+            for (int step = 16; step > 0; step >>= 1) {
+                const int e = __shfl_sync(full, excl, j + step);
+                if (e <= i) j += step;
+            }
+            const int t = __shfl_sync(full, s, j) + (i - __shfl_sync(full, excl, j));
+            bool within = false;
+            int beta = -1;
+            double dx = 0, dy = 0, dz = 0, r2 = 0;
+            if (i < total) {
+                beta = cell_beads[t];
+                const float4 pb = xf[beta];
+                const float fx = min_image_wrapped(p0.x - pb.x, Lx);
+                const float fy = min_image_wrapped(p0.y - pb.y, Ly);
+                const float fz = min_image_wrapped(p0.z - pb.z, Lz);
+                if (beta != alpha && fx * fx + fy * fy + fz * fz < rc2f &&
+                    (skip_body < 0 || k.bbody[beta] != skip_body)) {
+                    dx = min_image_wrapped(x0 - xw[3 * beta + 0], k.L[0]);
+                    dy = min_image_wrapped(y0 - xw[3 * beta + 1], k.L[1]);
+                    dz = min_image_wrapped(z0 - xw[3 * beta + 2], k.L[2]);
+                    r2 = dx * dx + dy * dy + dz * dz;
+                    within = r2 < k.rc2;
                 }
             }
+            f(beta, t, dx, dy, dz, r2, within);
+        }
+    }
 }
 
 // The pair table is stored in the cell-sorted bead order: row t belongs to bead
@@ -486,7 +515,6 @@ __global__ void near_field_kernel(int n, int nrhs, const double* __restrict__ xw
 // Overlapping beads (r < 2a, rare within a tessellation) use the exact FP64
 // kernel; coincident beads the r -> 0 limit, as in the table.
 // ---------------------------------------------------------------------------
-constexpr int kCompactMin = 32;    // smaller bodies stay in the table
 constexpr int kCbThreads = 128;    // targets per task and sources staged per round
 constexpr int kCbBlocksPerSm = 6;  // resident blocks of the persistent compact kernels
 
@@ -842,68 +870,33 @@ compact_field_kernel(CbArgs A, int n, const double* __restrict__ q, double inv_e
     }
 }
 
-// One block per body: centre (mean of the minimum-image offsets from the first
-// bead), radius, the compact flag, and the positions relative to the centre as
-// hi + lo floats.  Bodies below kCompactMin beads leave at once.
-constexpr int kCbBodyThreads = 256;
+// Compact bodies: every bead within lim of the body's first bead (so that every
+// intra-body difference of the relative positions below is its minimum image).
+// Flags first (bodies of at least kCompactMin beads start compact), then one
+// thread per bead: its position relative to the body's first bead as hi + lo
+// floats, and a bead beyond lim clears its body's flag.
+constexpr int kCompactMin = 32;    // smaller bodies stay in the table
 
-__device__ __forceinline__ double block_sum_256(double v, double* sh) {
-    v = warp_sum(v);
-    __syncthreads();
-    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
-    __syncthreads();
-    double t = 0.0;
-#pragma unroll
-    for (int w = 0; w < kCbBodyThreads / 32; ++w) t += sh[w];
-    return t;
+__global__ void compact_flags_kernel(int nb, const int* __restrict__ off, int* __restrict__ flag) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b < nb) flag[b] = off[b + 1] - off[b] >= kCompactMin ? 1 : 0;
 }
 
-__global__ void __launch_bounds__(kCbBodyThreads)
-compact_bodies_kernel(const int* __restrict__ off, const double* __restrict__ xw, double L0, double L1, double L2,
-                      double lim2, int* __restrict__ flag, float4* __restrict__ hi, float4* __restrict__ lo) {
-    __shared__ double sh[kCbBodyThreads / 32];
-    const int b = blockIdx.x;
-    const int o = off[b], m = off[b + 1] - o;
-    if (m < kCompactMin) {   // block-uniform
-        if (threadIdx.x == 0) flag[b] = 0;
-        return;
-    }
-    const double x0 = xw[3 * o], y0 = xw[3 * o + 1], z0 = xw[3 * o + 2];
-    double sx = 0.0, sy = 0.0, sz = 0.0;
-    for (int j = threadIdx.x; j < m; j += kCbBodyThreads) {
-        sx += min_image_wrapped(xw[3 * (o + j)] - x0, L0);
-        sy += min_image_wrapped(xw[3 * (o + j) + 1] - y0, L1);
-        sz += min_image_wrapped(xw[3 * (o + j) + 2] - z0, L2);
-    }
-    const double cx = block_sum_256(sx, sh) / m;
-    const double cy = block_sum_256(sy, sh) / m;
-    const double cz = block_sum_256(sz, sh) / m;
-    double r2max = 0.0;
-    for (int j = threadIdx.x; j < m; j += kCbBodyThreads) {
-        const double dx = min_image_wrapped(xw[3 * (o + j)] - x0, L0) - cx;
-        const double dy = min_image_wrapped(xw[3 * (o + j) + 1] - y0, L1) - cy;
-        const double dz = min_image_wrapped(xw[3 * (o + j) + 2] - z0, L2) - cz;
-        r2max = fmax(r2max, dx * dx + dy * dy + dz * dz);
-    }
-#pragma unroll
-    for (int s = 16; s > 0; s >>= 1) r2max = fmax(r2max, __shfl_xor_sync(0xffffffffu, r2max, s));
-    __syncthreads();
-    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = r2max;
-    __syncthreads();
-    double rm = 0.0;
-#pragma unroll
-    for (int w = 0; w < kCbBodyThreads / 32; ++w) rm = fmax(rm, sh[w]);
-    const int f = rm <= lim2 ? 1 : 0;
-    if (threadIdx.x == 0) flag[b] = f;
-    if (!f) return;
-    for (int j = threadIdx.x; j < m; j += kCbBodyThreads) {
-        const double dx = min_image_wrapped(xw[3 * (o + j)] - x0, L0) - cx;
-        const double dy = min_image_wrapped(xw[3 * (o + j) + 1] - y0, L1) - cy;
-        const double dz = min_image_wrapped(xw[3 * (o + j) + 2] - z0, L2) - cz;
-        const float hx = (float)dx, hy = (float)dy, hz = (float)dz;
-        hi[o + j] = make_float4(hx, hy, hz, 0.0f);
-        lo[o + j] = make_float4((float)(dx - (double)hx), (float)(dy - (double)hy), (float)(dz - (double)hz), 0.0f);
-    }
+__global__ void compact_rel_kernel(int n, const int* __restrict__ bead_body, const int* __restrict__ off,
+                                   const double* __restrict__ xw, double L0, double L1, double L2, double lim2,
+                                   int* __restrict__ flag, float4* __restrict__ hi, float4* __restrict__ lo) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n) return;
+    const int b = bead_body[j];
+    const int o = off[b];
+    if (off[b + 1] - o < kCompactMin) return;
+    const double dx = min_image_wrapped(xw[3 * j] - xw[3 * o], L0);
+    const double dy = min_image_wrapped(xw[3 * j + 1] - xw[3 * o + 1], L1);
+    const double dz = min_image_wrapped(xw[3 * j + 2] - xw[3 * o + 2], L2);
+    const float hx = (float)dx, hy = (float)dy, hz = (float)dz;
+    hi[j] = make_float4(hx, hy, hz, 0.0f);
+    lo[j] = make_float4((float)(dx - (double)hx), (float)(dy - (double)hy), (float)(dz - (double)hz), 0.0f);
+    if (dx * dx + dy * dy + dz * dz > lim2) flag[b] = 0;   // every writer stores 0
 }
 
 // Cubic coefficients per interval j from the FP64 nodes (value and u-derivative of
@@ -1164,9 +1157,13 @@ void compact_prepare(ibpme_ctx* c, int n, const double* xw) {
     float4* hi = static_cast<float4*>(nl.cb_hi.ensure(sizeof(float4) * (n + 1)));
     float4* lo = static_cast<float4*>(nl.cb_lo.ensure(sizeof(float4) * (n + 1)));
     const double* L = c->p.box;
-    const double lim = fmin(c->rc, 0.25 * fmin(L[0], fmin(L[1], L[2])));
-    compact_bodies_kernel<<<nb, kCbBodyThreads, 0, s>>>(bd.off.as<int>(), xw, L[0], L[1], L[2], lim * lim, flag, hi,
-                                                        lo);
+    // a body spanning at most 2 r_c (every bead within 2 r_c of the first bead), and
+    // at most a quarter box so that intra-body differences are minimum images
+    const double lim = fmin(2.0 * c->rc, 0.25 * fmin(L[0], fmin(L[1], L[2])));
+    compact_flags_kernel<<<div_up(nb, 256), 256, 0, s>>>(nb, bd.off.as<int>(), flag);
+    IBP_CHECK_LAUNCH();
+    compact_rel_kernel<<<div_up(n, 256), 256, 0, s>>>(n, bd.bead_body.as<int>(), bd.off.as<int>(), xw, L[0], L[1], L[2],
+                                                      lim * lim, flag, hi, lo);
     IBP_CHECK_LAUNCH();
     if (nl.cb_tasks_key == bd.version) return;
     const std::vector<int>& off = bd.host_off;
