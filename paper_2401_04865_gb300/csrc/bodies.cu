@@ -37,8 +37,10 @@ __global__ void rel_kernel(int n, const double* __restrict__ xw, const int* __re
 // body_ion_blocks(nb) blocks take one body per thread of their first kIonsPerBlock
 // threads and handle the single-bead bodies (ions, most of the bodies of an
 // electrolyte; few per block, so that the FP64 noise of the BD step spreads over
-// many SMs); the others take one multi-bead body per warp from the list mb_body.
-// Returns false for threads without work; the warp role returns warp-uniformly.
+// many SMs); the others take one multi-bead body per block from the list mb_body
+// (GB300 runs FP64 at a small fraction of its FP32 rate: a body's sums spread over
+// the four schedulers of an SM instead of one warp).  Returns false for threads
+// without work; a body block returns true for all its threads (block barriers).
 constexpr int kBodyThreads = 256;
 constexpr int kIonsPerBlock = 32;
 
@@ -54,14 +56,31 @@ __device__ __forceinline__ bool body_role(int nb, int nmb, const int* __restrict
         return (int)threadIdx.x < kIonsPerBlock && body < nb && off[body + 1] - off[body] == 1;
     }
     ion = false;
-    lane = threadIdx.x & 31;
-    const int w = (((int)blockIdx.x - ib) * kBodyThreads + (int)threadIdx.x) >> 5;
-    if (w >= nmb) return false;
-    body = mb_body[w];
+    lane = threadIdx.x;
+    body = mb_body[(int)blockIdx.x - ib];
     return true;
 }
 
-int body_grid(int nb, int nmb) { return body_ion_blocks(nb) + div_up((long long)nmb * 32, kBodyThreads); }
+int body_grid(int nb, int nmb) { return body_ion_blocks(nb) + nmb; }
+
+// Sums v[0..NV) over a body block (every thread takes part); thread 0 gets the totals.
+template <int NV>
+__device__ __forceinline__ void body_block_sum(double (&v)[NV], double (*sh)[NV]) {
+#pragma unroll
+    for (int i = 0; i < NV; ++i) v[i] = warp_sum(v[i]);
+    __syncthreads();   // the previous sum's reads of sh are done
+    if ((threadIdx.x & 31) == 0)
+#pragma unroll
+        for (int i = 0; i < NV; ++i) sh[threadIdx.x >> 5][i] = v[i];
+    __syncthreads();
+    if (threadIdx.x == 0)
+#pragma unroll
+        for (int i = 0; i < NV; ++i) {
+            double t = 0.0;
+            for (int w = 0; w < kBodyThreads / 32; ++w) t += sh[w][i];
+            v[i] = t;
+        }
+}
 
 __global__ void dipole_kernel(int nb, int nmb, const int* __restrict__ mb_body, int n, int nrhs,
                               const int* __restrict__ off, const double* __restrict__ rel,
@@ -80,22 +99,21 @@ __global__ void dipole_kernel(int nb, int nmb, const int* __restrict__ mb_body, 
         }
         return;
     }
+    __shared__ double sh[kBodyThreads / 32][3];
     for (int r = 0; r < nrhs; ++r) {
-        double sx = 0, sy = 0, sz = 0;
-        for (int j = off[b] + lane; j < off[b + 1]; j += 32) {
+        double v[3] = {0, 0, 0};
+        for (int j = off[b] + lane; j < off[b + 1]; j += kBodyThreads) {
             const double qq = q[(size_t)r * n + j];
-            sx += rel[3 * j + 0] * qq;
-            sy += rel[3 * j + 1] * qq;
-            sz += rel[3 * j + 2] * qq;
+            v[0] += rel[3 * j + 0] * qq;
+            v[1] += rel[3 * j + 1] * qq;
+            v[2] += rel[3 * j + 2] * qq;
         }
-        sx = warp_sum(sx);
-        sy = warp_sum(sy);
-        sz = warp_sum(sz);
+        body_block_sum<3>(v, sh);
         if (lane == 0) {
             double* o = S + ((size_t)r * nb + b) * 3;
-            o[0] = sx;
-            o[1] = sy;
-            o[2] = sz;
+            o[0] = v[0];
+            o[1] = v[1];
+            o[2] = v[2];
         }
     }
 }
@@ -123,20 +141,20 @@ __global__ void force_torque_kernel(int nb, int nmb, const int* __restrict__ mb_
         L[3 * b + 2] = rx * ay - ry * ax;
         return;
     }
-    double fx = 0, fy = 0, fz = 0, lx = 0, ly = 0, lz = 0;
-    for (int j = off[b] + lane; j < off[b + 1]; j += 32) {
+    __shared__ double sh[kBodyThreads / 32][6];
+    double v[6] = {0, 0, 0, 0, 0, 0};   // F, then L
+    for (int j = off[b] + lane; j < off[b + 1]; j += kBodyThreads) {
         const double ax = f[3 * j], ay = f[3 * j + 1], az = f[3 * j + 2];
         const double rx = rel[3 * j], ry = rel[3 * j + 1], rz = rel[3 * j + 2];
-        fx += ax; fy += ay; fz += az;
-        lx += ry * az - rz * ay;
-        ly += rz * ax - rx * az;
-        lz += rx * ay - ry * ax;
+        v[0] += ax; v[1] += ay; v[2] += az;
+        v[3] += ry * az - rz * ay;
+        v[4] += rz * ax - rx * az;
+        v[5] += rx * ay - ry * ax;
     }
-    fx = warp_sum(fx); fy = warp_sum(fy); fz = warp_sum(fz);
-    lx = warp_sum(lx); ly = warp_sum(ly); lz = warp_sum(lz);
+    body_block_sum<6>(v, sh);
     if (lane == 0) {
-        F[3 * b] = fx; F[3 * b + 1] = fy; F[3 * b + 2] = fz;
-        L[3 * b] = lx; L[3 * b + 1] = ly; L[3 * b + 2] = lz;
+        F[3 * b] = v[0]; F[3 * b + 1] = v[1]; F[3 * b + 2] = v[2];
+        L[3 * b] = v[3]; L[3 * b + 1] = v[4]; L[3 * b + 2] = v[5];
     }
 }
 
@@ -158,18 +176,18 @@ __global__ void energy_body_kernel(int nb, int nmb, const int* __restrict__ mb_b
         contrib[b] = Q[b] * Psi - q[j] * rE;
         return;
     }
-    double pr = 0, sE = 0;
-    for (int j = off[b] + lane; j < off[b + 1]; j += 32) {
+    __shared__ double sh[kBodyThreads / 32][2];
+    double v[2] = {0, 0};   // sum (psi - r.E0), sum q r.E0
+    for (int j = off[b] + lane; j < off[b + 1]; j += kBodyThreads) {
         const double rE = rel[3 * j] * e0 + rel[3 * j + 1] * e1 + rel[3 * j + 2] * e2;
-        pr += psi[j] - rE;
-        sE += q[j] * rE;
+        v[0] += psi[j] - rE;
+        v[1] += q[j] * rE;
     }
-    pr = warp_sum(pr);
-    sE = warp_sum(sE);
+    body_block_sum<2>(v, sh);
     if (lane == 0) {
         const double cnt = (double)(off[b + 1] - off[b]);
-        const double Psi = pr / cnt - (X[3 * b] * e0 + X[3 * b + 1] * e1 + X[3 * b + 2] * e2);
-        contrib[b] = Q[b] * Psi - sE;
+        const double Psi = v[0] / cnt - (X[3 * b] * e0 + X[3 * b + 1] * e1 + X[3 * b + 2] * e2);
+        contrib[b] = Q[b] * Psi - v[1];
     }
 }
 
@@ -325,21 +343,23 @@ __global__ void bd_body_kernel(int nb, int nmb, const int* __restrict__ mb_body,
         z[2 * i] = __shfl_sync(0xffffffffu, za, i);
         z[2 * i + 1] = __shfl_sync(0xffffffffu, zb, i);
     }
-    double F[3] = {0, 0, 0}, L[3] = {0, 0, 0}, J[6] = {0, 0, 0, 0, 0, 0};
-    for (int j = off[b] + lane; j < off[b + 1]; j += 32) {
+    __shared__ double sh[kBodyThreads / 32][12];
+    double v[12] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};   // F, L, J (upper triangle)
+    for (int j = off[b] + lane; j < off[b + 1]; j += kBodyThreads) {
         const double rx = rel[3 * j], ry = rel[3 * j + 1], rz = rel[3 * j + 2];
         const double ax = f[3 * j], ay = f[3 * j + 1], az = f[3 * j + 2];
-        F[0] += ax; F[1] += ay; F[2] += az;
-        L[0] += ry * az - rz * ay;
-        L[1] += rz * ax - rx * az;
-        L[2] += rx * ay - ry * ax;
+        v[0] += ax; v[1] += ay; v[2] += az;
+        v[3] += ry * az - rz * ay;
+        v[4] += rz * ax - rx * az;
+        v[5] += rx * ay - ry * ax;
         const double rr = rx * rx + ry * ry + rz * rz;
-        J[0] += rr - rx * rx; J[1] += -rx * ry; J[2] += -rx * rz;
-        J[3] += rr - ry * ry; J[4] += -ry * rz; J[5] += rr - rz * rz;
+        v[6] += rr - rx * rx; v[7] += -rx * ry; v[8] += -rx * rz;
+        v[9] += rr - ry * ry; v[10] += -ry * rz; v[11] += rr - rz * rz;
     }
-    for (int i = 0; i < 3; ++i) { F[i] = warp_sum(F[i]); L[i] = warp_sum(L[i]); }
-    for (int i = 0; i < 6; ++i) J[i] = warp_sum(J[i]);
+    body_block_sum<12>(v, sh);
     if (lane != 0) return;
+    const double F[3] = {v[0], v[1], v[2]}, L[3] = {v[3], v[4], v[5]};
+    const double J[6] = {v[6], v[7], v[8], v[9], v[10], v[11]};
     const double mt = 1.0 / (Ni * bc.gamma);
     const double st = sqrt(2.0 * bc.kT * bc.dt * mt);
     for (int i = 0; i < 3; ++i) X_out[3 * b + i] = X[3 * b + i] + F[i] * mt * bc.dt + st * z[i];

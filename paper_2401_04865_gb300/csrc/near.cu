@@ -30,6 +30,7 @@ constexpr double kPi = 3.14159265358979323846264338327950288;
 struct PairConst {
     double a, xi, A, B, rc2, self;
     float rc2_cand;     // FP32 screen: (r_c + delta)^2, delta above the FP32 rounding of positions in the box
+    float rc2_in;       // FP32 screen: below (r_c - delta)^2 a pair is inside r_c without the FP64 test
     double L[3];
     int nc[3];
     int lo[3], hi[3];   // neighbour cell offsets per axis
@@ -214,7 +215,9 @@ __global__ void pos32_kernel(int n, const double* __restrict__ xw, float4* __res
 // Candidates are screened in FP32 with a margin far above its rounding, and
 // the pairs that pass are decided exactly in FP64 (GB300's FP64 rate makes the
 // FP64 test of every candidate the cost of the build).
-template <typename F>
+// NEED_R = false (counting): a candidate inside the inner FP32 bound is a pair
+// without the FP64 test, which then runs only in the thin shell around r_c.
+template <bool NEED_R, typename F>
 __device__ __forceinline__ void for_neighbours(int alpha, const double* __restrict__ xw,
                                                const float4* __restrict__ xf, const PairConst& k,
                                                const int* __restrict__ cell_of, const int* __restrict__ cell_start,
@@ -277,13 +280,17 @@ __device__ __forceinline__ void for_neighbours(int alpha, const double* __restri
                 const float fx = min_image_wrapped(p0.x - pb.x, Lx);
                 const float fy = min_image_wrapped(p0.y - pb.y, Ly);
                 const float fz = min_image_wrapped(p0.z - pb.z, Lz);
-                if (beta != alpha && fx * fx + fy * fy + fz * fz < rc2f &&
-                    (skip_body < 0 || k.bbody[beta] != skip_body)) {
-                    dx = min_image_wrapped(x0 - xw[3 * beta + 0], k.L[0]);
-                    dy = min_image_wrapped(y0 - xw[3 * beta + 1], k.L[1]);
-                    dz = min_image_wrapped(z0 - xw[3 * beta + 2], k.L[2]);
-                    r2 = dx * dx + dy * dy + dz * dz;
-                    within = r2 < k.rc2;
+                const float r2f = fx * fx + fy * fy + fz * fz;
+                if (beta != alpha && r2f < rc2f && (skip_body < 0 || k.bbody[beta] != skip_body)) {
+                    if (!NEED_R && r2f < k.rc2_in) {
+                        within = true;
+                    } else {
+                        dx = min_image_wrapped(x0 - xw[3 * beta + 0], k.L[0]);
+                        dy = min_image_wrapped(y0 - xw[3 * beta + 1], k.L[1]);
+                        dz = min_image_wrapped(z0 - xw[3 * beta + 2], k.L[2]);
+                        r2 = dx * dx + dy * dy + dz * dz;
+                        within = r2 < k.rc2;
+                    }
                 }
             }
             f(beta, t, dx, dy, dz, r2, within);
@@ -303,8 +310,8 @@ __global__ void pair_count_kernel(int n, const double* __restrict__ xw, const fl
     if (t >= n) return;
     const int alpha = cell_beads[t];
     int cnt = 0;
-    for_neighbours(alpha, xw, xf, k, cell_of, cell_start, cell_beads, lane,
-                   [&](int, int, double, double, double, double, bool within) { cnt += within ? 1 : 0; });
+    for_neighbours<false>(alpha, xw, xf, k, cell_of, cell_start, cell_beads, lane,
+                          [&](int, int, double, double, double, double, bool within) { cnt += within ? 1 : 0; });
     cnt = warp_sum(cnt);
     if (lane == 0) row_count[t] = cnt;
 }
@@ -320,7 +327,7 @@ __global__ void pair_fill_kernel(int n, const double* __restrict__ xw, const flo
     const int alpha = cell_beads[t];
     long long base = rowptr[t];
     const unsigned lt = (1u << lane) - 1u;
-    for_neighbours(alpha, xw, xf, k, cell_of, cell_start, cell_beads, lane,
+    for_neighbours<true>(alpha, xw, xf, k, cell_of, cell_start, cell_beads, lane,
                    [&](int, int slot_b, double, double, double, double r2, bool within) {
                        const unsigned m = __ballot_sync(0xffffffffu, within);
                        if (within) {
@@ -504,14 +511,14 @@ __global__ void near_field_kernel(int n, int nrhs, const double* __restrict__ xw
 // ---------------------------------------------------------------------------
 // Compact bodies: intra-body pairs evaluated directly.
 //
-// Within a body whose beads all lie within min(r_c, L/4) of its centre, nearly
+// Within a body whose beads all lie within min(2 r_c, L/4) of its first bead, nearly
 // every pair is inside r_c; such pairs are most of the table of a tessellated
 // colloid (n_b^2 per body) and tabulating them needs FP64 per pair.  Instead,
 // blocks of kCbThreads targets sweep the body's beads staged in shared memory
 // and evaluate phi_r from cubic coefficients per table interval: FP32 for the
 // inner operator of a mixed solve, double-float (dfloat.cuh) for the FP64
-// operator and the field.  Positions are taken relative to the body centre, so
-// every intra-body difference is its minimum image (|difference| <= L/2).
+// operator and the field.  Positions are taken relative to the body's first bead,
+// so every intra-body difference is its minimum image (|difference| <= L/2).
 // Overlapping beads (r < 2a, rare within a tessellation) use the exact FP64
 // kernel; coincident beads the r -> 0 limit, as in the table.
 // ---------------------------------------------------------------------------
@@ -527,7 +534,7 @@ struct CbArgs {
     const int* flag;       // [nb] compact
     const int4* tasks;     // (body, first target bead, first source bead, target count << 20 | source count)
     int ntasks;
-    const float4* hi;      // [n] position relative to the body centre, high parts
+    const float4* hi;      // [n] position relative to the body's first bead, high parts
     const float4* lo;      // low parts
     const float4* tab32;
     const float4* tabdf;
@@ -1072,6 +1079,7 @@ PairConst make_const(const ibpme_ctx* c) {
         const double Lmax = fmax(c->p.box[0], fmax(c->p.box[1], c->p.box[2]));
         const double delta = 8.0 * Lmax * 1.1920928955078125e-07;
         k.rc2_cand = (float)((c->rc + delta) * (c->rc + delta) * (1.0 + 1e-5));
+        k.rc2_in = c->rc > delta ? (float)((c->rc - delta) * (c->rc - delta) * (1.0 - 1e-5)) : 0.0f;
     }
     k.self = (1.0 - exp(-4.0 * c->a * c->a * c->xi * c->xi)) / (8.0 * pow(kPi, 1.5) * c->a * c->a * c->xi) +
              erfc(2.0 * c->a * c->xi) / (4.0 * kPi * c->a);
