@@ -185,6 +185,7 @@ struct NearList {
     DevBuf cell_of, cell_count, cell_start64, cell_start, cursor;
     DevBuf cell_beads;             // beads sorted by cell: row t of the pair table is bead cell_beads[t]
     DevBuf row_count, rowptr;
+    DevBuf prow;                   // row (sorted position) of every pair
     DevBuf col, val, gfac;
     DevBuf pair32;                 // (col, FP32 val) per pair: inner operator of mixed-precision solves
     DevBuf qf;                     // charges packed per bead (float4) for the FP32 pass

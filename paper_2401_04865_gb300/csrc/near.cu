@@ -209,15 +209,15 @@ __global__ void pos32_kernel(int n, const double* __restrict__ xw, float4* __res
 }
 
 // Visits every bead beta != alpha of the neighbouring cells, 32 candidates per
-// round across the cells; calls f(beta, slot, dx, dy, dz, r2, within) for every lane
-// slot (within = false for idle lanes) so that warp-collective code can run in
-// f; slot is beta's position in the cell-sorted bead order.
-// Candidates are screened in FP32 with a margin far above its rounding, and
-// the pairs that pass are decided exactly in FP64 (GB300's FP64 rate makes the
-// FP64 test of every candidate the cost of the build).
-// NEED_R = false (counting): a candidate inside the inner FP32 bound is a pair
-// without the FP64 test, which then runs only in the thin shell around r_c.
-template <bool NEED_R, typename F>
+// round across the cells; calls f(beta, slot, within) for every lane slot
+// (within = false for idle lanes) so that warp-collective code can run in f;
+// slot is beta's position in the cell-sorted bead order.  Candidates are
+// screened in FP32 between an outer and an inner bound, each a margin far above
+// the FP32 rounding of positions in the box away from r_c: outside the outer
+// one a candidate is no pair, inside the inner one it is, and only the thin
+// shell between them takes the exact FP64 test (GB300's FP64 rate made the FP64
+// test of every candidate the cost of the build).
+template <typename F>
 __device__ __forceinline__ void for_neighbours(int alpha, const double* __restrict__ xw,
                                                const float4* __restrict__ xf, const PairConst& k,
                                                const int* __restrict__ cell_of, const int* __restrict__ cell_start,
@@ -273,7 +273,6 @@ __device__ __forceinline__ void for_neighbours(int alpha, const double* __restri
             const int t = __shfl_sync(full, s, j) + (i - __shfl_sync(full, excl, j));
             bool within = false;
             int beta = -1;
-            double dx = 0, dy = 0, dz = 0, r2 = 0;
             if (i < total) {
                 beta = cell_beads[t];
                 const float4 pb = xf[beta];
@@ -282,18 +281,17 @@ __device__ __forceinline__ void for_neighbours(int alpha, const double* __restri
                 const float fz = min_image_wrapped(p0.z - pb.z, Lz);
                 const float r2f = fx * fx + fy * fy + fz * fz;
                 if (beta != alpha && r2f < rc2f && (skip_body < 0 || k.bbody[beta] != skip_body)) {
-                    if (!NEED_R && r2f < k.rc2_in) {
+                    if (r2f < k.rc2_in) {
                         within = true;
                     } else {
-                        dx = min_image_wrapped(x0 - xw[3 * beta + 0], k.L[0]);
-                        dy = min_image_wrapped(y0 - xw[3 * beta + 1], k.L[1]);
-                        dz = min_image_wrapped(z0 - xw[3 * beta + 2], k.L[2]);
-                        r2 = dx * dx + dy * dy + dz * dz;
-                        within = r2 < k.rc2;
+                        const double dx = min_image_wrapped(x0 - xw[3 * beta + 0], k.L[0]);
+                        const double dy = min_image_wrapped(y0 - xw[3 * beta + 1], k.L[1]);
+                        const double dz = min_image_wrapped(z0 - xw[3 * beta + 2], k.L[2]);
+                        within = dx * dx + dy * dy + dz * dz < k.rc2;
                     }
                 }
             }
-            f(beta, t, dx, dy, dz, r2, within);
+            f(beta, t, within);
         }
     }
 }
@@ -310,47 +308,67 @@ __global__ void pair_count_kernel(int n, const double* __restrict__ xw, const fl
     if (t >= n) return;
     const int alpha = cell_beads[t];
     int cnt = 0;
-    for_neighbours<false>(alpha, xw, xf, k, cell_of, cell_start, cell_beads, lane,
-                          [&](int, int, double, double, double, double, bool within) { cnt += within ? 1 : 0; });
+    for_neighbours(alpha, xw, xf, k, cell_of, cell_start, cell_beads, lane,
+                   [&](int, int, bool within) { cnt += within ? 1 : 0; });
     cnt = warp_sum(cnt);
     if (lane == 0) row_count[t] = cnt;
 }
 
+// The columns of each row (the same walk and decisions as the count) and the row of
+// every pair; the FP64 values follow in pair_values_kernel, one thread per pair, so
+// that the rows of beads beside a dense body (hundreds of real pairs each) do not
+// hold one warp per row through their FP64 work.
 __global__ void pair_fill_kernel(int n, const double* __restrict__ xw, const float4* __restrict__ xf, PairConst k,
                                  const int* __restrict__ cell_of,
                                  const int* __restrict__ cell_start, const int* __restrict__ cell_beads,
                                  const long long* __restrict__ rowptr, int* __restrict__ col,
-                                 double* __restrict__ val, uint2* __restrict__ pair32, double* __restrict__ gfac) {
+                                 int* __restrict__ prow) {
     const int t = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (t >= n) return;
     const int alpha = cell_beads[t];
     long long base = rowptr[t];
     const unsigned lt = (1u << lane) - 1u;
-    for_neighbours<true>(alpha, xw, xf, k, cell_of, cell_start, cell_beads, lane,
-                   [&](int, int slot_b, double, double, double, double r2, bool within) {
-                       const unsigned m = __ballot_sync(0xffffffffu, within);
-                       if (within) {
-                           const long long slot = base + __popc(m & lt);
-                           double phi, g;
-                           if (k.K > 0 && r2 * k.inv4a2 >= 1.0) {
-                               pair_table(r2, k, phi, g);
-                           } else if (r2 > 0.0) {
-                               const double r = sqrt(r2);
-                               double dphi;
-                               pair_kernel(r, k, phi, dphi);   // overlapping beads: exact form
-                               g = -dphi / r;
-                           } else {
-                               phi = k.self;   // coincident beads: the r -> 0 limit, no field
-                               g = 0.0;
-                           }
-                           col[slot] = slot_b;
-                           val[slot] = phi;
-                           pair32[slot] = make_uint2((unsigned)slot_b, __float_as_uint((float)phi));
-                           if (gfac) gfac[slot] = g;
-                       }
-                       base += __popc(m);
-                   });
+    for_neighbours(alpha, xw, xf, k, cell_of, cell_start, cell_beads, lane,
+                          [&](int, int slot_b, bool within) {
+                              const unsigned m = __ballot_sync(0xffffffffu, within);
+                              if (within) {
+                                  const long long slot = base + __popc(m & lt);
+                                  col[slot] = slot_b;
+                                  prow[slot] = t;
+                              }
+                              base += __popc(m);
+                          });
+}
+
+// phi_r and -phi_r'/r of every pair from its FP64 distance: the octave table at
+// r >= 2a, the exact form for overlapping beads, the r -> 0 limit for coincident ones.
+__global__ void pair_values_kernel(long long np, const double* __restrict__ xw, PairConst k,
+                                   const int* __restrict__ prow, const int* __restrict__ col,
+                                   const int* __restrict__ order, double* __restrict__ val,
+                                   uint2* __restrict__ pair32, double* __restrict__ gfac) {
+    const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= np) return;
+    const int a = order[prow[p]], cb = col[p], b = order[cb];
+    const double dx = min_image_wrapped(xw[3 * a + 0] - xw[3 * b + 0], k.L[0]);
+    const double dy = min_image_wrapped(xw[3 * a + 1] - xw[3 * b + 1], k.L[1]);
+    const double dz = min_image_wrapped(xw[3 * a + 2] - xw[3 * b + 2], k.L[2]);
+    const double r2 = dx * dx + dy * dy + dz * dz;
+    double phi, g;
+    if (k.K > 0 && r2 * k.inv4a2 >= 1.0) {
+        pair_table(r2, k, phi, g);
+    } else if (r2 > 0.0) {
+        const double r = sqrt(r2);
+        double dphi;
+        pair_kernel(r, k, phi, dphi);   // overlapping beads: exact form
+        g = -dphi / r;
+    } else {
+        phi = k.self;   // coincident beads: the r -> 0 limit, no field
+        g = 0.0;
+    }
+    val[p] = phi;
+    pair32[p] = make_uint2((unsigned)cb, __float_as_uint((float)phi));
+    if (gfac) gfac[p] = g;
 }
 
 // psi_r[r][alpha] = (phi_self q_alpha + sum_pairs phi_r q_beta) / eps.
@@ -466,44 +484,51 @@ __global__ void near_apply32_kernel(int n, const long long* __restrict__ rowptr,
     }
 }
 
-// E_r[r][alpha] = sum_pairs (-phi_r'(r)/r) (x_alpha - x_beta) q_beta / eps
-__global__ void near_field_kernel(int n, int nrhs, const double* __restrict__ xw, PairConst k,
-                                  const long long* __restrict__ rowptr, const int* __restrict__ col,
+// E_r[r][alpha] += sum_pairs (-phi_r'(r)/r) (x_alpha - x_beta) q_beta / eps, one
+// thread per pair (E_r zeroed first).  Pairs are stored row by row: a warp sums the
+// runs of equal rows among its lanes (segmented doubling) and the first lane of each
+// run adds the run's sum to its row, one atomic per component.  The rows beside a
+// dense body hold hundreds of pairs; one warp per row left most of the GPU idle.
+__global__ void near_field_kernel(long long np, int n, int nrhs, const double* __restrict__ xw, PairConst k,
+                                  const int* __restrict__ prow, const int* __restrict__ col,
                                   const int* __restrict__ order, const double* __restrict__ gfac, double inv_eps,
                                   const double* __restrict__ q, double* __restrict__ E) {
-    const int t = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const unsigned full = 0xffffffffu;
+    const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const int lane = threadIdx.x & 31;
-    if (t >= n) return;
-    const int alpha = order[t];
-    const long long s = rowptr[t], e = rowptr[t + 1];
-    const double x0 = xw[3 * alpha + 0], y0 = xw[3 * alpha + 1], z0 = xw[3 * alpha + 2];
-    double ex[kMaxRhs], ey[kMaxRhs], ez[kMaxRhs];
-#pragma unroll
-    for (int r = 0; r < kMaxRhs; ++r) ex[r] = ey[r] = ez[r] = 0.0;
-    for (long long p = s + lane; p < e; p += 32) {
-        const int b = order[col[p]];
-        const double gf = gfac[p];
-        const double dx = min_image_wrapped(x0 - xw[3 * b + 0], k.L[0]);
-        const double dy = min_image_wrapped(y0 - xw[3 * b + 1], k.L[1]);
-        const double dz = min_image_wrapped(z0 - xw[3 * b + 2], k.L[2]);
-#pragma unroll
-        for (int r = 0; r < kMaxRhs; ++r)
-            if (r < nrhs) {
-                const double w = gf * q[(size_t)r * n + b];
-                ex[r] += w * dx;
-                ey[r] += w * dy;
-                ez[r] += w * dz;
-            }
+    const bool on = p < np;
+    const int t = on ? prow[p] : -1;   // idle lanes (the grid's tail) only follow on lanes
+    int a = 0, b = 0;
+    double gf = 0.0, d[3] = {0.0, 0.0, 0.0};
+    if (on) {
+        a = order[t];
+        b = order[col[p]];
+        gf = gfac[p];
+        d[0] = min_image_wrapped(xw[3 * a + 0] - xw[3 * b + 0], k.L[0]);
+        d[1] = min_image_wrapped(xw[3 * a + 1] - xw[3 * b + 1], k.L[1]);
+        d[2] = min_image_wrapped(xw[3 * a + 2] - xw[3 * b + 2], k.L[2]);
     }
+    const int tprev = __shfl_up_sync(full, t, 1);
+    const bool head = on && (lane == 0 || tprev != t);
+    for (int r = 0; r < nrhs; ++r) {
+        const double wq = on ? gf * q[(size_t)r * n + b] : 0.0;
+        double v[3] = {wq * d[0], wq * d[1], wq * d[2]};
+        // after the step of width w, lane l holds the sum over lanes [l, l + 2w) of its run
 #pragma unroll
-    for (int r = 0; r < kMaxRhs; ++r) {
-        if (r >= nrhs) break;
-        const double a0 = warp_sum(ex[r]), a1 = warp_sum(ey[r]), a2 = warp_sum(ez[r]);
-        if (lane == 0) {
-            double* o = E + ((size_t)r * n + alpha) * 3;
-            o[0] = a0 * inv_eps;
-            o[1] = a1 * inv_eps;
-            o[2] = a2 * inv_eps;
+        for (int w = 1; w < 32; w <<= 1) {
+            const int ot = __shfl_down_sync(full, t, w);
+            double o[3];
+#pragma unroll
+            for (int c = 0; c < 3; ++c) o[c] = __shfl_down_sync(full, v[c], w);
+            if (lane + w < 32 && ot == t)
+#pragma unroll
+                for (int c = 0; c < 3; ++c) v[c] += o[c];
+        }
+        if (head) {
+            double* e = E + ((size_t)r * n + a) * 3;
+            atomicAdd(e + 0, v[0] * inv_eps);
+            atomicAdd(e + 1, v[1] * inv_eps);
+            atomicAdd(e + 2, v[2] * inv_eps);
         }
     }
 }
@@ -1383,9 +1408,15 @@ void near_build(ibpme_ctx* c, int n, const double* xw, bool need_grad) {
     nl.qf.ensure(sizeof(float4) * (n + 1));
     nl.qs.ensure(sizeof(double) * (size_t)(n + 1) * kMaxRhs);
     if (n > 0) {
+        int* prow = static_cast<int*>(nl.prow.ensure(sizeof(int) * np));
         pair_fill_kernel<<<div_up((long long)n * 32, 128), 128, 0, s>>>(n, xw, xf, k, cell_of, cell_start,
-                                                                         cell_beads, rowptr, col, val, pair32, gfac);
+                                                                         cell_beads, rowptr, col, prow);
         IBP_CHECK_LAUNCH();
+        if (nl.npairs > 0) {
+            pair_values_kernel<<<div_up(nl.npairs, 256), 256, 0, s>>>(nl.npairs, xw, k, prow, col, cell_beads, val,
+                                                                     pair32, gfac);
+            IBP_CHECK_LAUNCH();
+        }
     }
     nl.fp = print;
     nl.fp_valid = true;
@@ -1442,10 +1473,13 @@ void near_field(ibpme_ctx* c, int n, const double* xw, const double* q, int nrhs
     if (!c->near.have_grad) fail(IBPME_ERR_ARG, "internal: pair table built without gradients");
     NearList& nl = c->near;
     const PairConst k = make_const(c);
-    near_field_kernel<<<div_up((long long)n * 32, 128), 128, 0, c->stream>>>(
-        n, nrhs, xw, k, nl.rowptr.as<long long>(), nl.col.as<int>(), nl.cell_beads.as<int>(), nl.gfac.as<double>(),
-        1.0 / c->eps, q, E_r);
-    IBP_CHECK_LAUNCH();
+    IBP_CUDA(cudaMemsetAsync(E_r, 0, sizeof(double) * 3 * (size_t)nrhs * n, c->stream));
+    if (nl.npairs > 0) {
+        near_field_kernel<<<div_up(nl.npairs, 256), 256, 0, c->stream>>>(
+            nl.npairs, n, nrhs, xw, k, nl.prow.as<int>(), nl.col.as<int>(), nl.cell_beads.as<int>(),
+            nl.gfac.as<double>(), 1.0 / c->eps, q, E_r);
+        IBP_CHECK_LAUNCH();
+    }
     if (nl.cb_on && nl.cb_ntasks > 0) compact_field(c, n, q, nrhs, E_r);
 }
 
