@@ -203,8 +203,8 @@ dfx_forward_kernel(DfGeom d, const double* __restrict__ grid, float4* __restrict
     const double* src = grid + ch * d.G + line0 * n;
     for (int e = threadIdx.x; e < pts; e += kDfThreads) {
         const int p = e / n, i = e % n;
-        const df a = df_from_double(src[(size_t)(2 * p) * n + i]);
-        const df b = df_from_double(src[(size_t)(2 * p + 1) * n + i]);
+        const df a = df_split(src[(size_t)(2 * p) * n + i]);
+        const df b = df_split(src[(size_t)(2 * p + 1) * n + i]);
         buf[p * ls + sw(i)] = make_float4(a.hi, a.lo, b.hi, b.lo);
     }
     __syncthreads();
@@ -250,8 +250,8 @@ dfx_inverse_kernel(DfGeom d, const float4* __restrict__ S, double* __restrict__ 
     for (int e = threadIdx.x; e < pts; e += kDfThreads) {
         const int p = e / n, i = e % n;
         const float4 v = buf[p * ls + sw(i)];
-        dst[(size_t)(2 * p) * n + i] = (double)v.x + (double)v.y;
-        dst[(size_t)(2 * p + 1) * n + i] = (double)v.z + (double)v.w;
+        dst[(size_t)(2 * p) * n + i] = df_join({v.x, v.y});
+        dst[(size_t)(2 * p + 1) * n + i] = df_join({v.z, v.w});
     }
 }
 

@@ -83,4 +83,37 @@ __device__ __forceinline__ df df_from_double(double v) {
 
 __device__ __forceinline__ double df_to_double(df a) { return (double)a.hi + (double)a.lo; }
 
+// Conversions with integer operations on the bits instead of FP64 conversions
+// (GB300 issues those at its FP64 rate).
+//
+// df_split: hi = v with its significand cut to 24 bits, lo = the remaining 29
+// significand bits rounded to FP32, so hi + lo = v to a relative 2^-47.  Zero
+// gives (0, 0); exponents outside [-74, 127] (FP32 could not hold lo or hi) take
+// df_from_double.
+__device__ __forceinline__ df df_split(double v) {
+    const unsigned hw = (unsigned)__double2hiint(v), lw = (unsigned)__double2loint(v);
+    if (((hw & 0x7FFFFFFFu) | lw) == 0u) return {0.0f, 0.0f};
+    const int e = (int)((hw >> 20) & 0x7FFu) - 1023;
+    if (e < -74 || e > 127) return df_from_double(v);
+    const unsigned sign = hw & 0x80000000u;
+    const float hi = __uint_as_float(sign | ((unsigned)(e + 127) << 23) | ((hw & 0xFFFFFu) << 3) | (lw >> 29));
+    const float scale = __uint_as_float((unsigned)(e - 52 + 127) << 23);   // 2^(e - 52)
+    const float lo = __fmul_rn(__uint2float_rn(lw & 0x1FFFFFFFu), scale);
+    return {hi, __uint_as_float(__float_as_uint(lo) | sign)};
+}
+
+// The double with the value of f (exact): sign, exponent and significand moved
+// into place; subnormal and non-finite f take the FP64 conversion.
+__device__ __forceinline__ double widen(float f) {
+    const unsigned u = __float_as_uint(f);
+    if ((u & 0x7FFFFFFFu) == 0u) return __hiloint2double((int)(u & 0x80000000u), 0);
+    const unsigned ef = (u >> 23) & 0xFFu;
+    if (ef == 0u || ef == 0xFFu) return (double)f;
+    const unsigned hw = (u & 0x80000000u) | ((ef - 127u + 1023u) << 20) | ((u & 0x7FFFFFu) >> 3);
+    return __hiloint2double((int)hw, (int)((u & 0x7u) << 29));
+}
+
+// hi + lo in FP64 with one FP64 addition
+__device__ __forceinline__ double df_join(df a) { return widen(a.hi) + widen(a.lo); }
+
 }  // namespace ibp
