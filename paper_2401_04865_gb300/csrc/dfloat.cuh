@@ -51,6 +51,24 @@ __device__ __forceinline__ df df_mul(df a, df b) {
     return fast_two_sum(p, e);
 }
 
+// b a for a float a: the exact product of a and b.hi plus a b.lo.
+__device__ __forceinline__ df df_mul_f(df b, float a) {
+    const float p = __fmul_rn(a, b.hi);
+    float e = __fmaf_rn(a, b.hi, -p);
+    e = __fmaf_rn(a, b.lo, e);
+    return fast_two_sum(p, e);
+}
+
+// Sum over the warp (every lane receives it).
+__device__ __forceinline__ df df_warp_sum(df v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const df w = {__shfl_xor_sync(0xffffffffu, v.hi, o), __shfl_xor_sync(0xffffffffu, v.lo, o)};
+        v = df_add(v, w);
+    }
+    return v;
+}
+
 __device__ __forceinline__ df df_sqr(df a) {
     const float p = __fmul_rn(a.hi, a.hi);
     float e = __fmaf_rn(a.hi, a.hi, -p);

@@ -16,6 +16,7 @@
 // original system); only the inter-body coupling and the periodic images are
 // left to the Krylov iteration.
 #include "common.cuh"
+#include "dfloat.cuh"
 
 #include <algorithm>
 #include <cmath>
@@ -159,8 +160,11 @@ precond_apply_kernel(int npb, int chunks, int nk, long long ustride, const int* 
                      const float* __restrict__ minv,
                      const float* __restrict__ gvec, const double* __restrict__ sinv, int nplain,
                      const int* __restrict__ plain, const double* __restrict__ u, double* __restrict__ out) {
-    __shared__ double v[kPrecondMaxBeads];
-    __shared__ double sh[32];
+    // u of the body as double-float: the FP32 inverse times it accumulates on the FP32
+    // pipes (an FP64 multiply-add and a conversion per entry made this kernel wait on
+    // GB300's FP64 rate), to about 2^-44 of each row's magnitude
+    __shared__ float2 v[kPrecondMaxBeads];
+    __shared__ df sh[32];
     __shared__ double tpsi;
     const int r = blockIdx.y;
     if (jdev) u += (size_t)(*jdev) * nk;
@@ -176,17 +180,19 @@ precond_apply_kernel(int npb, int chunks, int nk, long long ustride, const int* 
     const int nb = pb_n[p], first = pb_first[p], sh_id = pb_shape[p];
     const float* M = minv + shape_off[sh_id];
     const float* gv = gvec + shape_goff[sh_id];
-    for (int j = threadIdx.x; j < nb; j += kApplyThreads) v[j] = ur[first + j];
-    __syncthreads();
-    double acc = 0.0;
-    for (int j = threadIdx.x; j < nb; j += kApplyThreads) acc += (double)gv[j] * v[j];
-    acc = warp_sum(acc);
+    df acc = {0.0f, 0.0f};
+    for (int j = threadIdx.x; j < nb; j += kApplyThreads) {
+        const df d = df_split(ur[first + j]);
+        v[j] = make_float2(d.hi, d.lo);
+        acc = df_add(acc, df_mul_f(d, gv[j]));
+    }
+    acc = df_warp_sum(acc);
     if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = acc;
     __syncthreads();
     if (threadIdx.x == 0) {
-        double t = 0.0;
-        for (int q = 0; q < kApplyThreads / 32; ++q) t += sh[q];
-        tpsi = (t + ur[pb_psi[p]]) * sinv[sh_id];
+        df t = {0.0f, 0.0f};
+        for (int q = 0; q < kApplyThreads / 32; ++q) t = df_add(t, sh[q]);
+        tpsi = (df_join(t) + ur[pb_psi[p]]) * sinv[sh_id];
     }
     __syncthreads();
     const double tp = tpsi;
@@ -194,10 +200,13 @@ precond_apply_kernel(int npb, int chunks, int nk, long long ustride, const int* 
     const int i0 = chunk * kRowsPerBlock;
     for (int i = i0 + warp; i < min(nb, i0 + kRowsPerBlock); i += kApplyThreads / 32) {
         const float* Mi = M + (size_t)i * nb;
-        double s = 0.0;
-        for (int j = lane; j < nb; j += 32) s += (double)Mi[j] * v[j];
-        s = warp_sum(s);
-        if (lane == 0) orow[first + i] = -s + (double)gv[i] * tp;
+        df s = {0.0f, 0.0f};
+        for (int j = lane; j < nb; j += 32) {
+            const float2 vj = v[j];
+            s = df_add(s, df_mul_f({vj.x, vj.y}, Mi[j]));
+        }
+        s = df_warp_sum(s);
+        if (lane == 0) orow[first + i] = -df_join(s) + (double)gv[i] * tp;
     }
     if (chunk == 0 && threadIdx.x == 0) orow[pb_psi[p]] = tp;
 }
