@@ -161,6 +161,8 @@ struct Mesh {
     bool df = false;
     DevBuf df_tw[3], df_buf;
     DevBuf green_df;   // the Green's table as (hi, lo) float pairs for the double-float transforms
+    DevBuf grid_df;    // [rcap][G] (hi, lo) floats: the transformed grid of the double-float transforms
+    bool potential_df = false;   // the last transform left the potential in grid_df (gathers read it)
     void init(const MeshGeom& geom, int channels, double xi, double eta, double a, cudaStream_t s);
     void destroy();
     void ensure_channels(int ch);
@@ -384,8 +386,8 @@ double self_term(const ibpme_ctx* c);   // phi_self (without 1/eps)
 // ---- dffft.cu ----
 bool df_fft_supported(const MeshGeom& g);
 void df_fft_init(const MeshGeom& g, DevBuf tw[3], cudaStream_t s);
-void df_fft_convolve(const MeshGeom& g, int ch, const float2* green, double* grid, float4* S, DevBuf tw[3],
-                     cudaStream_t s);
+void df_fft_convolve(const MeshGeom& g, int ch, const float2* green, const double* grid, float2* out, float4* S,
+                     DevBuf tw[3], cudaStream_t s);
 
 // ---- mesh.cu ----
 // Cached stencils for the current positions (rebuilt when the position

@@ -224,9 +224,10 @@ dfx_forward_kernel(DfGeom d, const double* __restrict__ grid, float4* __restrict
 
 // x pass, inverse: the half spectra A, B of two lines rebuild Z = A + i B on all
 // N points (Z[N-k] = conj A[k] + i conj B[k]); the inverse transform's real and
-// imaginary parts are the two real lines, returned as FP64.
+// imaginary parts are the two real lines, returned as hi + lo floats (the gathers
+// read them in double-float arithmetic).
 __global__ void __launch_bounds__(kDfThreads, kDfMinBlocks)
-dfx_inverse_kernel(DfGeom d, const float4* __restrict__ S, double* __restrict__ grid, const float4* __restrict__ tw) {
+dfx_inverse_kernel(DfGeom d, const float4* __restrict__ S, float2* __restrict__ grid, const float4* __restrict__ tw) {
     __shared__ float4 buf[kDfSmem];
     const int n = d.n[0], pl = d.pl[0], ls = df_ls(n), pts = pl * n;
     const size_t ch = blockIdx.y;
@@ -246,12 +247,12 @@ dfx_inverse_kernel(DfGeom d, const float4* __restrict__ S, double* __restrict__ 
     }
     __syncthreads();
     fft_lines<true>(buf, n, d.logn[0], pts, tw);
-    double* dst = grid + ch * d.G + line0 * n;
+    float2* dst = grid + ch * d.G + line0 * n;
     for (int e = threadIdx.x; e < pts; e += kDfThreads) {
         const int p = e / n, i = e % n;
         const float4 v = buf[p * ls + sw(i)];
-        dst[(size_t)(2 * p) * n + i] = df_join({v.x, v.y});
-        dst[(size_t)(2 * p + 1) * n + i] = df_join({v.z, v.w});
+        dst[(size_t)(2 * p) * n + i] = make_float2(v.x, v.y);
+        dst[(size_t)(2 * p + 1) * n + i] = make_float2(v.z, v.w);
     }
 }
 
@@ -367,9 +368,10 @@ void df_fft_init(const MeshGeom& g, DevBuf tw[3], cudaStream_t s) {
     IBP_CUDA(cudaStreamSynchronize(s));   // the host table goes out of scope
 }
 
-// grid (FP64, [ch][G]) -> inverse transform of G(k) times its transform, in place.
-void df_fft_convolve(const MeshGeom& g, int ch, const float2* green, double* grid, float4* S, DevBuf tw[3],
-                     cudaStream_t s) {
+// grid (FP64, [ch][G]) -> out ([ch][G], hi + lo floats): the inverse transform of G(k)
+// times the grid's transform.
+void df_fft_convolve(const MeshGeom& g, int ch, const float2* green, const double* grid, float2* out, float4* S,
+                     DevBuf tw[3], cudaStream_t s) {
     DfGeom d;
     for (int a = 0; a < 3; ++a) {
         d.n[a] = g.N[a];
@@ -399,7 +401,7 @@ void df_fft_convolve(const MeshGeom& g, int ch, const float2* green, double* gri
     ProfScope ps(ST_FFT_INV64, s);
     dfy_kernel<<<gy, kDfThreads, 0, s>>>(d, S, tw[1].as<float4>(), 1);
     IBP_CHECK_LAUNCH();
-    dfx_inverse_kernel<<<gx, kDfThreads, 0, s>>>(d, S, grid, tw[0].as<float4>());
+    dfx_inverse_kernel<<<gx, kDfThreads, 0, s>>>(d, S, out, tw[0].as<float4>());
     IBP_CHECK_LAUNCH();
 }
 

@@ -747,7 +747,7 @@ struct Solver {
                                       P(c->pre.shape_off.p), P(c->pre.shape_goff.p),
                                       P(prec == IBPME_MIXED ? m32.grid.p : m64.grid.p),
                                       P(prec == IBPME_MIXED ? m32.spec.p : m64.spec.p),
-                                      P(prec == IBPME_MIXED ? m32.work.p : m64.work.p), P(m64.df_buf.p),
+                                      P(prec == IBPME_MIXED ? m32.work.p : m64.work.p), P(m64.df_buf.p), P(m64.grid_df.p),
                                       P(m32.green.p), P(m64.green.p), P(m64.green_df.p), P(m64.df_tw[0].p),
                                       P(m64.df_tw[1].p), P(m64.df_tw[2].p)};
         const int gi = prec == IBPME_MIXED ? 1 : 0;

@@ -9,6 +9,7 @@
 // (i, row) owns one x offset i of the stencil and walks the (j, k) rows, so
 // the addresses of neighbouring lanes are contiguous along x.
 #include "common.cuh"
+#include "dfloat.cuh"
 
 #include <cmath>
 #include <cstdlib>
@@ -94,7 +95,8 @@ spread_kernel(int n, const double* __restrict__ xw, const double* __restrict__ q
 template <typename T, int NR, int WPB, bool GRAD>
 __global__ void __launch_bounds__(32 * kWarpsPerBlock)
 gather_kernel(int n, const double* __restrict__ xw, const int* __restrict__ bead_cfg, MeshGeom g,
-              const T* __restrict__ grid, double* __restrict__ psi, double* __restrict__ E) {
+              const T* __restrict__ grid, const float2* __restrict__ gdf, double* __restrict__ psi,
+              double* __restrict__ E) {
     __shared__ T s_w[kWarpsPerBlock][3][kMaxP];
     __shared__ T s_d[kWarpsPerBlock][3][kMaxP];
     __shared__ int s_idx[kWarpsPerBlock][3][kMaxP];
@@ -116,7 +118,10 @@ gather_kernel(int n, const double* __restrict__ xw, const int* __restrict__ bead
         wx = s_w[wib][0][i];
         if (GRAD) dx = s_d[wib][0][i];
         const int ix = s_idx[wib][0][i];
-        if (bead_cfg) grid += (size_t)bead_cfg[bead] * NR * g.G;
+        if (bead_cfg) {
+            grid += (size_t)bead_cfg[bead] * NR * g.G;
+            if (gdf) gdf += (size_t)bead_cfg[bead] * NR * g.G;
+        }
         const int P2 = P * P;
         const int step = rows_per * WPB;
         int row = rsub + rows_per * part;
@@ -128,7 +133,18 @@ gather_kernel(int n, const double* __restrict__ xw, const int* __restrict__ bead
             const int off = s_idx[wib][2][k] * nxy + s_idx[wib][1][j] * g.N[0] + ix;
 #pragma unroll
             for (int r = 0; r < NR; ++r) {
-                const T v = __ldg(grid + (size_t)r * g.G + off) * wyz;
+                T gv;
+                if constexpr (sizeof(T) == 8) {
+                    if (gdf) {
+                        const float2 t = __ldg(gdf + (size_t)r * g.G + off);
+                        gv = df_join(df{t.x, t.y});
+                    } else {
+                        gv = __ldg(grid + (size_t)r * g.G + off);
+                    }
+                } else {
+                    gv = __ldg(grid + (size_t)r * g.G + off);
+                }
+                const T v = gv * wyz;
                 acc[r] += v;
                 if (GRAD) {
                     accy[r] += v * s_d[wib][1][j];
@@ -230,34 +246,34 @@ void spread_dispatch(int n, const double* xw, const double* q, int nrhs, const i
 }
 
 template <typename T, int NR, int WPB, bool GRAD>
-void launch_gather(int n, const double* xw, const int* cfg, const MeshGeom& g, const T* grid, double* psi, double* E,
-                   cudaStream_t s) {
+void launch_gather(int n, const double* xw, const int* cfg, const MeshGeom& g, const T* grid, const float2* gdf, double* psi,
+                   double* E, cudaStream_t s) {
     const int blocks = div_up((long long)n * WPB, kWarpsPerBlock);
-    gather_kernel<T, NR, WPB, GRAD><<<blocks, 32 * kWarpsPerBlock, 0, s>>>(n, xw, cfg, g, grid, psi, E);
+    gather_kernel<T, NR, WPB, GRAD><<<blocks, 32 * kWarpsPerBlock, 0, s>>>(n, xw, cfg, g, grid, gdf, psi, E);
 }
 
 template <typename T, int NR, bool GRAD>
-void launch_gather_w(int n, const double* xw, const int* cfg, const MeshGeom& g, const T* grid, double* psi,
-                     double* E, cudaStream_t s) {
+void launch_gather_w(int n, const double* xw, const int* cfg, const MeshGeom& g, const T* grid, const float2* gdf,
+                     double* psi, double* E, cudaStream_t s) {
     switch (warps_per_bead(n)) {
-        case 1: launch_gather<T, NR, 1, GRAD>(n, xw, cfg, g, grid, psi, E, s); break;
-        case 2: launch_gather<T, NR, 2, GRAD>(n, xw, cfg, g, grid, psi, E, s); break;
-        default: launch_gather<T, NR, 4, GRAD>(n, xw, cfg, g, grid, psi, E, s); break;
+        case 1: launch_gather<T, NR, 1, GRAD>(n, xw, cfg, g, grid, gdf, psi, E, s); break;
+        case 2: launch_gather<T, NR, 2, GRAD>(n, xw, cfg, g, grid, gdf, psi, E, s); break;
+        default: launch_gather<T, NR, 4, GRAD>(n, xw, cfg, g, grid, gdf, psi, E, s); break;
     }
 }
 
 template <typename T, bool GRAD>
 void gather_dispatch(int n, const double* xw, int nrhs, const int* cfg, const MeshGeom& g, const T* grid,
-                     double* psi, double* E, cudaStream_t s) {
+                     const float2* gdf, double* psi, double* E, cudaStream_t s) {
     switch (nrhs) {
-        case 1: launch_gather_w<T, 1, GRAD>(n, xw, cfg, g, grid, psi, E, s); break;
-        case 2: launch_gather_w<T, 2, GRAD>(n, xw, cfg, g, grid, psi, E, s); break;
-        case 3: launch_gather_w<T, 3, GRAD>(n, xw, cfg, g, grid, psi, E, s); break;
-        case 4: launch_gather_w<T, 4, GRAD>(n, xw, cfg, g, grid, psi, E, s); break;
-        case 5: launch_gather_w<T, 5, GRAD>(n, xw, cfg, g, grid, psi, E, s); break;
-        case 6: launch_gather_w<T, 6, GRAD>(n, xw, cfg, g, grid, psi, E, s); break;
-        case 7: launch_gather_w<T, 7, GRAD>(n, xw, cfg, g, grid, psi, E, s); break;
-        default: launch_gather_w<T, 8, GRAD>(n, xw, cfg, g, grid, psi, E, s); break;
+        case 1: launch_gather_w<T, 1, GRAD>(n, xw, cfg, g, grid, gdf, psi, E, s); break;
+        case 2: launch_gather_w<T, 2, GRAD>(n, xw, cfg, g, grid, gdf, psi, E, s); break;
+        case 3: launch_gather_w<T, 3, GRAD>(n, xw, cfg, g, grid, gdf, psi, E, s); break;
+        case 4: launch_gather_w<T, 4, GRAD>(n, xw, cfg, g, grid, gdf, psi, E, s); break;
+        case 5: launch_gather_w<T, 5, GRAD>(n, xw, cfg, g, grid, gdf, psi, E, s); break;
+        case 6: launch_gather_w<T, 6, GRAD>(n, xw, cfg, g, grid, gdf, psi, E, s); break;
+        case 7: launch_gather_w<T, 7, GRAD>(n, xw, cfg, g, grid, gdf, psi, E, s); break;
+        default: launch_gather_w<T, 8, GRAD>(n, xw, cfg, g, grid, gdf, psi, E, s); break;
     }
 }
 
@@ -318,6 +334,7 @@ struct PairArgs {
     const float4* frac32;   // the same offsets rounded to FP32
     const double* w64;  // cached FP64 windows [n][3][P] (NULL: evaluate them)
     float kappa32[3], h32[3], c32, gather32, grad32;   // MeshGeom's constants in FP32
+    const float2* gdf;  // FP64 gathers: the transformed grid as hi + lo floats, or NULL (FP64 grid)
 };
 
 // A mesh constant in the kernel's precision.
@@ -433,6 +450,44 @@ spread_pairs_kernel(PairArgs A, int n, const double* __restrict__ q, T* __restri
     }
 }
 
+// The z walk of one (x, y) column of a gather from the double-float grid (FP64
+// meshes with double-float transforms): products and sums on the FP32 pipes, one
+// FP64 addition per column and field to join the result (GB300 runs FP64 at a small
+// fraction of its FP32 rate).  wzl, wdzl: this lane's window and window x distance
+// as hi + lo floats; lane k supplies node k of the column.
+template <int NR, bool GRAD, int PC>
+__device__ __forceinline__ void column_walk_df(const float2* __restrict__ gr, long long G, long long nxy,
+                                               long long base, bool on, int P_rt, df wzl, df wdzl, int izl,
+                                               double (&a)[NR], double (&az)[NR]) {
+    const unsigned full = 0xffffffffu;
+    const int P = PC ? PC : P_rt;
+    df sa[NR], sz[NR];
+#pragma unroll
+    for (int r = 0; r < NR; ++r) sa[r] = sz[r] = df{0.0f, 0.0f};
+#pragma unroll
+    for (int k = 0; k < P; ++k) {
+        const df wz = {__shfl_sync(full, wzl.hi, k), __shfl_sync(full, wzl.lo, k)};
+        const int iz = __shfl_sync(full, izl, k);
+        df wdz = {0.0f, 0.0f};
+        if (GRAD) wdz = df{__shfl_sync(full, wdzl.hi, k), __shfl_sync(full, wdzl.lo, k)};
+        if (on) {
+            const size_t off = (size_t)iz * nxy + base;
+#pragma unroll
+            for (int r = 0; r < NR; ++r) {
+                const float2 v = __ldg(gr + (size_t)r * G + off);
+                const df vd = {v.x, v.y};
+                sa[r] = df_add(sa[r], df_mul(vd, wz));
+                if (GRAD) sz[r] = df_add(sz[r], df_mul(vd, wdz));
+            }
+        }
+    }
+#pragma unroll
+    for (int r = 0; r < NR; ++r) {
+        a[r] = df_join(sa[r]);
+        az[r] = GRAD ? df_join(sz[r]) : 0.0;
+    }
+}
+
 template <typename T, int NR, bool GRAD, int PC>
 __global__ void __launch_bounds__(32 * kPairWarps)
 gather_pairs_kernel(PairArgs A, int n, const T* __restrict__ grid, double* __restrict__ psi, double* __restrict__ E) {
@@ -450,6 +505,13 @@ gather_pairs_kernel(PairArgs A, int n, const T* __restrict__ grid, double* __res
 #pragma unroll
     for (int r = 0; r < NR; ++r) sp[r] = ex[r] = ey[r] = ez[r] = (T)0;
     const long long nxy = (long long)g.N[0] * g.N[1];
+    df wz_df = {0.0f, 0.0f}, wdz_df = {0.0f, 0.0f};   // this lane's z window as hi + lo (double-float grid)
+    if constexpr (sizeof(T) == 8) {
+        if (A.gdf) {
+            wz_df = df_split(W.wz);
+            if (GRAD) wdz_df = df_split(W.wdz);
+        }
+    }
     for (int rd = 0; rd < A.rounds; ++rd) {
         const int first = (part * A.rounds + rd) * 32;
         if (first >= P2) break;   // warp-uniform
@@ -467,21 +529,31 @@ gather_pairs_kernel(PairArgs A, int n, const T* __restrict__ grid, double* __res
         }
         const long long base = (long long)__shfl_sync(0xffffffffu, W.iy, j) * g.N[0] + __shfl_sync(0xffffffffu, W.ix, i);
         T a[NR], az[NR];
+        bool walked = false;
+        if constexpr (sizeof(T) == 8) {
+            if (A.gdf) {
+                column_walk_df<NR, GRAD, PC>(A.gdf + (size_t)A.start[bead].w * NR * g.G, g.G, nxy, base, on, P,
+                                             wz_df, wdz_df, W.iz, a, az);
+                walked = true;
+            }
+        }
+        if (!walked) {
 #pragma unroll
-        for (int r = 0; r < NR; ++r) a[r] = az[r] = (T)0;
-        #pragma unroll
-        for (int k = 0; k < P; ++k) {
-            const T wz = __shfl_sync(0xffffffffu, W.wz, k);
-            const int iz = __shfl_sync(0xffffffffu, W.iz, k);
-            T wdz = (T)0;
-            if (GRAD) wdz = __shfl_sync(0xffffffffu, W.wdz, k);
-            if (on) {
-                const size_t off = (size_t)iz * nxy + base;
+            for (int r = 0; r < NR; ++r) a[r] = az[r] = (T)0;
 #pragma unroll
-                for (int r = 0; r < NR; ++r) {
-                    const T v = __ldg(gr + (size_t)r * g.G + off);
-                    a[r] = fma(v, wz, a[r]);
-                    if (GRAD) az[r] = fma(v, wdz, az[r]);
+            for (int k = 0; k < P; ++k) {
+                const T wz = __shfl_sync(0xffffffffu, W.wz, k);
+                const int iz = __shfl_sync(0xffffffffu, W.iz, k);
+                T wdz = (T)0;
+                if (GRAD) wdz = __shfl_sync(0xffffffffu, W.wdz, k);
+                if (on) {
+                    const size_t off = (size_t)iz * nxy + base;
+#pragma unroll
+                    for (int r = 0; r < NR; ++r) {
+                        const T v = __ldg(gr + (size_t)r * g.G + off);
+                        a[r] = fma(v, wz, a[r]);
+                        if (GRAD) az[r] = fma(v, wdz, az[r]);
+                    }
                 }
             }
         }
@@ -805,6 +877,13 @@ __device__ __forceinline__ void gather_bead_direct(const PairArgs& A, int n, int
 #pragma unroll
     for (int r = 0; r < NR; ++r) sp[r] = ex[r] = ey[r] = ez[r] = (T)0;
     const long long nxy = (long long)g.N[0] * g.N[1];
+    df wz_df = {0.0f, 0.0f}, wdz_df = {0.0f, 0.0f};   // this lane's z window as hi + lo (double-float grid)
+    if constexpr (sizeof(T) == 8) {
+        if (A.gdf) {
+            wz_df = df_split(W.wz);
+            if (GRAD) wdz_df = df_split(W.wdz);
+        }
+    }
     #pragma unroll
     for (int first = 0; first < P2; first += 32) {
         const int pair = first + lane;
@@ -820,21 +899,31 @@ __device__ __forceinline__ void gather_bead_direct(const PairArgs& A, int n, int
         }
         const long long base = (long long)__shfl_sync(0xffffffffu, W.iy, j) * g.N[0] + __shfl_sync(0xffffffffu, W.ix, i);
         T acc[NR], accz[NR];
+        bool walked = false;
+        if constexpr (sizeof(T) == 8) {
+            if (A.gdf) {
+                column_walk_df<NR, GRAD, PC>(A.gdf + (size_t)A.start[bead].w * NR * g.G, g.G, nxy, base, on, P,
+                                             wz_df, wdz_df, W.iz, acc, accz);
+                walked = true;
+            }
+        }
+        if (!walked) {
 #pragma unroll
-        for (int r = 0; r < NR; ++r) acc[r] = accz[r] = (T)0;
-        #pragma unroll
-        for (int k = 0; k < P; ++k) {
-            const T wz = __shfl_sync(0xffffffffu, W.wz, k);
-            const int iz = __shfl_sync(0xffffffffu, W.iz, k);
-            T wdz = (T)0;
-            if (GRAD) wdz = __shfl_sync(0xffffffffu, W.wdz, k);
-            if (on) {
-                const size_t off = (size_t)iz * nxy + base;
+            for (int r = 0; r < NR; ++r) acc[r] = accz[r] = (T)0;
 #pragma unroll
-                for (int r = 0; r < NR; ++r) {
-                    const T v = __ldg(gr + (size_t)r * g.G + off);
-                    acc[r] = fma(v, wz, acc[r]);
-                    if (GRAD) accz[r] = fma(v, wdz, accz[r]);
+            for (int k = 0; k < P; ++k) {
+                const T wz = __shfl_sync(0xffffffffu, W.wz, k);
+                const int iz = __shfl_sync(0xffffffffu, W.iz, k);
+                T wdz = (T)0;
+                if (GRAD) wdz = __shfl_sync(0xffffffffu, W.wdz, k);
+                if (on) {
+                    const size_t off = (size_t)iz * nxy + base;
+#pragma unroll
+                    for (int r = 0; r < NR; ++r) {
+                        const T v = __ldg(gr + (size_t)r * g.G + off);
+                        acc[r] = fma(v, wz, acc[r]);
+                        if (GRAD) accz[r] = fma(v, wdz, accz[r]);
+                    }
                 }
             }
         }
@@ -899,7 +988,18 @@ gather_tiles_kernel(TileArgs TA, int n, const T* __restrict__ grid, double* __re
             const int z = rem / E2, y = (rem / Ee) % Ee, x = rem % Ee;
             const size_t off = ((size_t)wrap_once(oz + z, g.N[2]) * g.N[1] + wrap_once(oy + y, g.N[1])) * g.N[0] +
                                wrap_once(ox + x, g.N[0]);
-            reg[u] = __ldg(gr + (size_t)c * g.G + off);
+            T v;
+            if constexpr (sizeof(T) == 8) {
+                if (A.gdf) {
+                    const float2 t = __ldg(A.gdf + (size_t)(cfg * NR + c) * g.G + off);
+                    v = df_join(df{t.x, t.y});
+                } else {
+                    v = __ldg(gr + (size_t)c * g.G + off);
+                }
+            } else {
+                v = __ldg(gr + (size_t)c * g.G + off);
+            }
+            reg[u] = v;
         }
         __syncthreads();
         for (int t = a + w; t < b; t += kTileWarps) {
@@ -1183,6 +1283,7 @@ template <typename T>
 void Mesh<T>::ensure_channels(int ch) {
     if (ch <= rcap) return;
     grid.ensure(sizeof(T) * (size_t)g.G * ch);
+    if (df) grid_df.ensure(sizeof(float2) * (size_t)g.G * ch);
     spec.ensure(sizeof(typename Cplx<T>::type) * (size_t)g.Gc * ch);
     rcap = ch;
 }
@@ -1238,6 +1339,8 @@ void Mesh<T>::destroy() {
     spec.release();
     green.release();
     green_df.release();
+    grid_df.release();
+    potential_df = false;
     work.release();
     rcap = 0;
 }
@@ -1247,6 +1350,7 @@ void Mesh<T>::spread(int n, const double* xw, const double* q, int nrhs, const i
                      cudaStream_t s, const StencilCache* sc) {
     ProfScope ps(mesh_stage<T>(ST_SPREAD), s);
     ensure_channels(nrhs * ncfg);
+    potential_df = false;
     IBP_CUDA(cudaMemsetAsync(grid.p, 0, sizeof(T) * (size_t)g.G * nrhs * ncfg, s));
     if (n == 0) return;
     // Pair lanes while a bead's columns are split over warps (few beads); with one
@@ -1268,10 +1372,13 @@ void Mesh<T>::transform(int ch, cudaStream_t s) {
     plans(ch, s);
     if constexpr (sizeof(T) == 8) {
         if (df) {
-            df_fft_convolve(g, ch, green_df.as<float2>(), grid.as<double>(), df_buf.as<float4>(), df_tw, s);
+            df_fft_convolve(g, ch, green_df.as<float2>(), grid.as<double>(), grid_df.as<float2>(), df_buf.as<float4>(),
+                            df_tw, s);
+            potential_df = true;
             return;
         }
     }
+    potential_df = false;
     const auto& pl = plan.at(ch);
     using C = typename Cplx<T>::type;
     {
@@ -1300,13 +1407,18 @@ void Mesh<T>::gather(int n, const double* xw, int nrhs, const int* bead_cfg, dou
                      cudaStream_t s, const StencilCache* sc) {
     if (n == 0) return;
     ProfScope ps(mesh_stage<T>(ST_GATHER), s);
+    // the double-float transforms leave the potential as hi + lo floats
+    const float2* gdf = sizeof(T) == 8 && potential_df ? grid_df.as<float2>() : nullptr;
     if (tiles_fit<T>(g, sc, nrhs)) {
-        tiles_dispatch<T>(nrhs, false, E != nullptr, tile_args(g, *sc, n), n, nullptr, grid.as<T>(), psi, E, s);
+        TileArgs TA = tile_args(g, *sc, n);
+        TA.A.gdf = gdf;
+        tiles_dispatch<T>(nrhs, false, E != nullptr, TA, n, nullptr, grid.as<T>(), psi, E, s);
         IBP_CHECK_LAUNCH();
         return;
     }
     if (sc) {   // several warps of a bead add their partial sums into zeroed outputs
-        const PairArgs A = pair_args(g, *sc, n);
+        PairArgs A = pair_args(g, *sc, n);
+        A.gdf = gdf;
         if (A.wpb > 1) {
             IBP_CUDA(cudaMemsetAsync(psi, 0, sizeof(double) * (size_t)nrhs * n, s));
             if (E) IBP_CUDA(cudaMemsetAsync(E, 0, sizeof(double) * 3 * (size_t)nrhs * n, s));
@@ -1316,9 +1428,9 @@ void Mesh<T>::gather(int n, const double* xw, int nrhs, const int* bead_cfg, dou
         return;
     }
     if (E)
-        gather_dispatch<T, true>(n, xw, nrhs, bead_cfg, g, grid.as<T>(), psi, E, s);
+        gather_dispatch<T, true>(n, xw, nrhs, bead_cfg, g, grid.as<T>(), gdf, psi, E, s);
     else
-        gather_dispatch<T, false>(n, xw, nrhs, bead_cfg, g, grid.as<T>(), psi, nullptr, s);
+        gather_dispatch<T, false>(n, xw, nrhs, bead_cfg, g, grid.as<T>(), gdf, psi, nullptr, s);
     IBP_CHECK_LAUNCH();
 }
 
