@@ -2,7 +2,8 @@
 // contiguous bead ranges of the summation tensor Sigma (Appendix): dipoles
 // (Eq. rigid_dipole), bead forces (Eq. beadforce), body forces and torques
 // (Sec. III.C), the energy (Eq. pot_syst) and the Brownian-dynamics step of
-// Sec. V.A (Eq. forward, Eq. hardsphereFD).  One warp per body.
+// Sec. V.A (Eq. forward, Eq. hardsphereFD).  Ions one per thread, multi-bead bodies
+// one per block (body_role).
 #include "common.cuh"
 
 #include <cmath>
@@ -294,7 +295,8 @@ __device__ void rotation_matrix(const double* th, double* R) {
         }
 }
 
-// One warp per body: F, L, J; lane 0 draws the noise and forms U, Omega, R.
+// One body per thread (ions) or per block: F, L, J summed over the body; threads 0-2
+// draw the noise, thread 0 forms U, Omega, R.
 // Box-Muller pair t of body b: Philox counter (body, step, t); (rad cos, rad sin).
 __device__ __forceinline__ void bd_normals(int b, const BdConst& bc, unsigned t, double& rad, double& ang) {
     const uint2 key = make_uint2((unsigned)(bc.seed & 0xffffffffull), (unsigned)(bc.seed >> 32));

@@ -212,7 +212,7 @@ struct NearList {
     bool cb_on = false;            // the table was built with compact bodies taken out
     unsigned long long cb_key = 0; // body structure the compact data belong to (0: none)
     DevBuf cb_flag;                // [nb] 1 if the body is compact
-    DevBuf cb_hi, cb_lo;           // [n] float4: position relative to the body centre, hi + lo parts
+    DevBuf cb_hi, cb_lo;           // [n] float4: position relative to the body's first bead, hi + lo parts
     DevBuf cb_tasks;               // int4 per block: (body, first target, first source, counts)
     int cb_ntasks = 0;
     unsigned long long cb_tasks_key = 0;
