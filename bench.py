@@ -243,9 +243,10 @@ class HostStep:
 # algorithmic bytes per launch of each timed stage (mesh w = 4 or 8 bytes, R = 1)
 # FP32 operations of the double-float primitives (dfloat.cuh, dffft.cu): two_sum 6,
 # fast_two_sum 3, df_add 11, df_mul 7, complex multiply 4 df_mul + 2 df_add = 50, complex
-# add 22, radix-2 DFT 2 x 22 = 44, radix-4 DFT 4 x 22 = 88, multiply by w8 2 x 11 + 2 x 7 = 36,
-# radix-8 DFT 2 x 88 + 2 x 36 + 8 x 22 = 424.
-DF_CMUL, DF_DFT = 50, {2: 44, 4: 88, 8: 424}
+# add 22; an r-point DFT of radix-2 butterflies takes r log2(r) complex additions: radix-2
+# 2 x 22 = 44, radix-4 8 x 22 = 176 (its -i is free), radix-8 24 x 22 plus two multiplies by
+# w8 (2 x 11 + 2 x 7 = 36 each; w8^2 = -i is free) = 600.
+DF_CMUL, DF_DFT = 50, {2: 44, 4: 176, 8: 600}
 
 
 def df_transform_ops(n):

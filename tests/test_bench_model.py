@@ -1,0 +1,71 @@
+"""The benchmark's algorithmic work model (the numerator of its roofline) against
+counts derived here from first principles.
+
+Double-float primitives (two_sum, fast_two_sum, df_add, df_mul) are counted from their
+definitions as FP32 operations; a length-n power-of-two transform built from radix-8
+passes and one radix-4 or radix-2 pass is counted butterfly by butterfly, with an
+r-point radix-2 DFT taking r log2(r) complex additions and the k = 0 twiddles of each
+pass free.
+"""
+import math
+import os
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+
+import bench  # noqa: E402
+
+TWO_SUM = 6          # s, bb, and four operations for the error term
+FAST_TWO_SUM = 3
+DF_ADD = TWO_SUM + 2 + FAST_TWO_SUM          # two-sum of the highs, two adds of the lows, renormalise
+DF_MUL = 1 + 3 + FAST_TWO_SUM                # product, three fused multiply-adds, renormalise
+CADD = 2 * DF_ADD
+CMUL = 4 * DF_MUL + 2 * DF_ADD
+MUL_W8 = 2 * DF_ADD + 2 * DF_MUL             # (re +- im) / sqrt(2)
+
+
+def dft_ops(r):
+    adds = r * int(math.log2(r))
+    extra = 2 * MUL_W8 if r == 8 else 0      # w8 and w8^3 (w8^2 = -i costs nothing)
+    return adds * CADD + extra
+
+
+def transform_ops_per_point(n):
+    """Walk the passes of a length-n transform point by point."""
+    l = int(round(math.log2(n)))
+    radices = [8] * (l // 3) + ([2 ** (l % 3)] if l % 3 else [])
+    total, ns = 0, 1
+    for r in radices:
+        butterflies = n // r
+        nontrivial = butterflies - butterflies // ns          # k = 0 butterflies have unit twiddles
+        total += nontrivial * (r - 1) * CMUL + butterflies * dft_ops(r)
+        ns *= r
+    return total / n
+
+
+def test_primitive_counts_match_the_model():
+    assert DF_ADD == 11 and DF_MUL == 7 and CMUL == bench.DF_CMUL == 50
+    for r in (2, 4, 8):
+        assert bench.DF_DFT[r] == dft_ops(r), r
+
+
+@pytest.mark.parametrize("n", [16, 32, 64, 128, 256, 512, 1024])
+def test_transform_ops_per_point(n):
+    assert bench.df_transform_ops(n) == pytest.approx(transform_ops_per_point(n), rel=1e-12)
+
+
+def test_z_pass_work_of_the_headline_mesh():
+    """Forward and inverse z transforms plus the Green's scaling (two df_mul per point)
+    on the half spectrum of the 128^3 mesh: 515.2 M FP32 operations per launch."""
+
+    class S:
+        mesh = (128, 128, 128)
+
+    bound, work, unit = bench.stage_work("scale64", S, 0, True)
+    pts = 128 * 128 * 65
+    assert bound == "alu" and unit == "Gop/s"
+    assert work == pytest.approx(pts * (2 * transform_ops_per_point(128) + 2 * DF_MUL), rel=1e-12)
+    assert work == pytest.approx(515.2e6, rel=1e-3)
