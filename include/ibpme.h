@@ -175,7 +175,7 @@ typedef struct {
  *   [Sigma    0 ] [Psi - Psi_0] = [   Q   ],   r_ij = x_ij - X_i (minimum image)
  * by restarted GMRES with every vector and scalar on the device.  Single-bead
  * bodies (ions) have q = Q fixed; they are eliminated exactly and their
- * Psi - Psi_0 is recovered with one FP64 evaluation.  Convergence is judged
+ * Psi - Psi_0 is recovered with one FP64 evaluation.  Convergence is decided
  * on the full system with the FP64 operator.
  *   E0       [nrhs][3] external field per right-hand side
  *   q_out    [nrhs][n] bead charges (initial guess on input when guess = USER)

@@ -977,7 +977,7 @@ struct Solver {
             --c->start32_skip;
             start32 = false;
         }
-        bool judge32 = start32;   // the first FP64 check still has to judge the FP32 start
+        bool check32 = start32;   // the first FP64 check still has to decide on the FP32 start
         const int prec0 = start32 ? IBPME_MIXED : IBPME_FP64;
         std::vector<double> res = residual(prec0, true, zero_start);
         std::vector<double> tol_abs(S);
@@ -1014,9 +1014,9 @@ struct Solver {
                 if (res64) break;
                 res = residual(IBPME_FP64);   // a guess that looks converged: confirm with FP64
                 res64 = true;
-                if (judge32) {
+                if (check32) {
                     c->start32_skip = converged() ? 0 : 32;
-                    judge32 = false;
+                    check32 = false;
                 }
                 if (converged()) break;
             }
@@ -1031,9 +1031,9 @@ struct Solver {
             IBP_CHECK_LAUNCH();
             res = residual(IBPME_FP64);
             res64 = true;
-            if (judge32) {
+            if (check32) {
                 c->start32_skip = converged() ? 0 : 32;
-                judge32 = false;
+                check32 = false;
             }
             if (verbose)
                 for (int i = 0; i < S; ++i)

@@ -1,6 +1,6 @@
 """Learned warm start: the library's MLP kernels against the FP64 reference
 network, training, and the gain of the trained network over the zero guess
-(the converged solve is the judge)."""
+(the converged solve decides)."""
 import numpy as np
 import pytest
 
