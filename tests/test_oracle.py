@@ -394,3 +394,208 @@ def test_bf16_rounding_pins():
     W1, b1, W2, b2, W3, b3 = M.unpack(p)
     X = rng.normal(size=(50, M.IN))
     assert np.max(np.abs(M.forward_bf16_hidden(p, X) - M.forward(p, X))) < 2e-2
+
+
+# ---------------------------------------------------------------------------
+# Philox4x32-10 against its published known-answer vectors
+# ---------------------------------------------------------------------------
+
+def test_philox_known_answer_vectors():
+    """Catches a wrong multiplier, Weyl constant, round count or word order in the
+    generator: three published 128-bit outputs (all-zero, all-one and pi-digit inputs)."""
+    kat = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "philox_kat.json")))
+    for v in kat["vectors"]:
+        ctr = tuple(int(w, 16) for w in v["ctr"])
+        key = tuple(int(w, 16) for w in v["key"])
+        assert o.philox4x32_10(ctr, key) == tuple(int(w, 16) for w in v["out"])
+
+
+# ---------------------------------------------------------------------------
+# Spread grid of Eq. H_hat: fixed by what the window must be, not by its formula
+# ---------------------------------------------------------------------------
+
+_ANISO_BOX = np.array([3.0, 4.0, 5.0])
+_ANISO_MESH = (16, 20, 24)
+
+
+def _grid_dft(H, box, m):
+    """h_x h_y h_z sum_g H(x_g) e^{-i k.x_g} at k = 2 pi m / L (grid stored [z, y, x])."""
+    Nz, Ny, Nx = H.shape
+    h = box / np.array([Nx, Ny, Nz])
+    k = 2 * math.pi * np.asarray(m, dtype=np.float64) / box
+    ph = (np.exp(-1j * k[2] * h[2] * np.arange(Nz))[:, None, None]
+          * np.exp(-1j * k[1] * h[1] * np.arange(Ny))[None, :, None]
+          * np.exp(-1j * k[0] * h[0] * np.arange(Nx))[None, None, :])
+    return (H * ph).sum() * np.prod(h), k
+
+
+@pytest.mark.parametrize("P", [4, 5, 9])
+def test_spread_stencil_is_the_P_nearest_nodes(P):
+    """Catches a stencil shifted by a node or an axis mix-up: for one bead the nodes
+    that receive charge are, per axis, the P nodes nearest to it in periodic distance
+    (Sec. III.D.2), found here by sorting every node of the axis by its distance."""
+    rng = np.random.default_rng(P)
+    N = list(_ANISO_MESH)
+    h = _ANISO_BOX / np.array(N)
+    for _ in range(6):
+        x = rng.uniform(-2.0, 7.0, size=3)
+        H = o.spread_grid(x[None, :], np.array([1.0]), _ANISO_BOX, N, 1.5, 0.4, P)
+        hit = np.nonzero(H)
+        for d, axis in ((0, 2), (1, 1), (2, 0)):          # H is [z, y, x]
+            nodes = np.arange(N[d])
+            dist = np.abs((nodes * h[d] - x[d] + _ANISO_BOX[d] / 2) % _ANISO_BOX[d] - _ANISO_BOX[d] / 2)
+            nearest = set(np.argsort(dist)[:P].tolist())
+            assert set(hit[axis].tolist()) == nearest
+
+
+@pytest.mark.parametrize("tol", [1e-8, 1e-10])
+def test_spread_grid_carries_the_total_charge(tol):
+    """Catches a wrong normalisation constant (the printed (2 xi / pi eta^2)^{3/2} included):
+    the grid integrates to the total charge, sum_g H(x_g) h_x h_y h_z = sum q, to the
+    window's truncation and quadrature error e^{-pi P/2} (Sec. III.D.2), bounded by tol."""
+    p = o.auto_params(_ANISO_BOX, _ANISO_MESH, tol, 0.05)
+    rng = np.random.default_rng(3)
+    x = rng.uniform(-1.0, 6.0, size=(7, 3))
+    q = rng.uniform(0.5, 1.5, size=7)
+    H = o.spread_grid(x, q, _ANISO_BOX, _ANISO_MESH, p["xi"], p["eta"], p["P"])
+    h = _ANISO_BOX / np.array(_ANISO_MESH)
+    assert abs(H.sum() * np.prod(h) / q.sum() - 1.0) < 100 * tol
+
+
+@pytest.mark.parametrize("tol", [1e-8, 1e-10])
+def test_spread_grid_transform_is_the_filtered_structure_factor(tol):
+    """Catches a wrong window width, a transposed grid axis or a wrong node position.
+    By Poisson summation the grid's Fourier coefficients are the structure factor times
+    the window's transform e^{-eta k^2/(8 xi^2)} (Sec. III.D.2, the transform pair stated
+    with Eq. H_hat), summed over the aliases k' = k + 2 pi (m_x/h_x, m_y/h_y, m_z/h_z):
+    h^3 sum_g H(x_g) e^{-i k.x_g} = sum_k' e^{-eta k'^2/(8 xi^2)} sum_b q_b e^{-i k'.x_b},
+    to the window's truncation error e^{-pi P/2}, bounded by tol; checked at wave vectors
+    along every axis and mixed ones up to k_c."""
+    p = o.auto_params(_ANISO_BOX, _ANISO_MESH, tol, 0.05)
+    rng = np.random.default_rng(5)
+    x = rng.uniform(-1.0, 6.0, size=(9, 3))
+    q = rng.uniform(-1.0, 1.0, size=9)
+    H = o.spread_grid(x, q, _ANISO_BOX, _ANISO_MESH, p["xi"], p["eta"], p["P"])
+    two_pi_h = 2 * math.pi * np.array(_ANISO_MESH) / _ANISO_BOX
+    aliases = np.array([(i, j, l) for i in range(-2, 3) for j in range(-2, 3) for l in range(-2, 3)])
+    for m in [(1, 0, 0), (0, 2, 0), (0, 0, 3), (2, -1, 1), (-3, 2, -2), (4, 3, -5), (6, 0, 0), (0, 0, -11)]:
+        got, k = _grid_dft(H, _ANISO_BOX, m)
+        assert np.linalg.norm(k) <= p["k_c"]
+        want = 0.0
+        for al in aliases:
+            kp = k + al * two_pi_h
+            want += math.exp(-p["eta"] * float(kp @ kp) / (8 * p["xi"] ** 2)) * np.sum(q * np.exp(-1j * (x @ kp)))
+        assert abs(got - want) < 100 * tol * np.abs(q).sum()
+        # the first alias matters near k_c (it is what a mesh too coarse for the window would show)
+        direct = math.exp(-p["eta"] * float(k @ k) / (8 * p["xi"] ** 2)) * np.sum(q * np.exp(-1j * (x @ k)))
+        if np.linalg.norm(k) > 0.85 * p["k_c"]:
+            assert abs(direct - want) > 100 * tol * np.abs(q).sum()
+
+
+# ---------------------------------------------------------------------------
+# Rigid-body Brownian step (Sec. V.A): rotation and noise of multi-bead bodies
+# ---------------------------------------------------------------------------
+
+def _rotation_vectors(r, rn):
+    """Rotation vectors of the rotations taking each body's r[b] onto rn[b]
+    (least-squares rotation from the SVD of sum_j rn_j r_j^T, then its axis-angle)."""
+    Hm = np.einsum("bji,bjk->bik", rn, r)
+    U, _, Vt = np.linalg.svd(Hm)
+    D = np.tile(np.eye(3), (len(r), 1, 1))
+    D[:, 2, 2] = np.sign(np.linalg.det(U @ Vt))
+    R = U @ D @ Vt
+    ang = np.arccos(np.clip((np.trace(R, axis1=1, axis2=2) - 1) / 2, -1, 1))
+    w = np.stack([R[:, 2, 1] - R[:, 1, 2], R[:, 0, 2] - R[:, 2, 0], R[:, 1, 0] - R[:, 0, 1]], axis=1)
+    s = np.where(ang > 1e-12, ang / (2 * np.sin(np.maximum(ang, 1e-300))), 0.5)
+    return w * s[:, None]
+
+
+def _ring(n, radius):
+    t = 2 * math.pi * np.arange(n) / n
+    return np.stack([radius * np.cos(t), radius * np.sin(t), np.zeros(n)], axis=1)
+
+
+def test_bd_rotation_under_torque_closed_form_inertia():
+    """Catches a wrong rotational friction J (a transposed r r^T, |r|^2 dropped) or a
+    missing 1/gamma: with kT = 0 the body turns by Omega dt, Omega = (gamma J)^{-1} L,
+    where J has a closed form: a ring of n beads of radius R in the xy plane has
+    J = n R^2 diag(1/2, 1/2, 1); a regular icosahedron of circumradius R has J = 8 R^2 I.
+    The torque comes from two opposite forces on a pair of beads (no net force)."""
+    box = np.array([12.0, 12.0, 12.0])
+    Xc = np.array([6.0, 5.0, 7.0])
+    gamma, dt, Fm = 1.7, 1e-3, 3.0
+    ring = _ring(8, 1.3)                     # beads at 45 degree steps: +-y are beads 2 and 6
+    ico = G.icosphere(0, 0.9)
+    assert ico.shape == (12, 3)
+    cases = []
+    # ring: forces +-F z on the beads at +-y give L = 2 R F x; and +-F y on the beads at +-x give L = 2 R F z
+    f = np.zeros((8, 3)); f[2, 2], f[6, 2] = Fm, -Fm
+    f[0, 1], f[4, 1] = Fm, -Fm
+    L = np.array([2 * 1.3 * Fm, 0.0, 2 * 1.3 * Fm])
+    J = 8 * 1.3 ** 2 * np.diag([0.5, 0.5, 1.0])
+    cases.append((ring, f, L, J))
+    # icosahedron: +-F e on two opposite vertices n, -n give L = 2 R F (n x e)
+    n_hat = ico[0] / np.linalg.norm(ico[0])
+    opp = int(np.argmin(ico @ n_hat))
+    e = np.cross(n_hat, [0.3, -0.5, 0.8]); e /= np.linalg.norm(e)
+    f = np.zeros((12, 3)); f[0], f[opp] = Fm * e, -Fm * e
+    cases.append((ico, f, 2 * 0.9 * Fm * np.cross(n_hat, e), 8 * 0.9 ** 2 * np.eye(3)))
+    for shape, f, L, J in cases:
+        x = Xc + shape
+        off = np.array([0, len(shape)])
+        xn, Xn = o.bd_step(x, Xc[None, :], off, f, box, 0.05, dt=dt, gamma=gamma, kT=0.0)
+        assert np.allclose(Xn[0], Xc, atol=1e-15)              # no net force, no noise
+        theta = _rotation_vectors(shape[None], (xn - Xn[0])[None])[0]
+        want = np.linalg.solve(gamma * J, L) * dt
+        assert np.linalg.norm(theta - want) < 1e-9 * np.linalg.norm(want)
+
+
+def test_bd_rigid_drag_force_gives_back_its_angular_velocity():
+    """Catches a torque or inertia of the wrong sign or handedness, for any body shape:
+    bead forces equal to the free-draining drag of a rigid rotation, f_j = gamma w x r_j,
+    make the body turn at Omega = w (L = gamma J w is an identity of the cross product)."""
+    rng = np.random.default_rng(11)
+    box = np.array([9.0, 9.0, 9.0])
+    shape = rng.normal(size=(17, 3))
+    shape -= shape.mean(axis=0)
+    X = np.array([[4.0, 4.5, 5.0]])
+    w = np.array([0.4, -1.1, 0.7])
+    gamma, dt = 2.5, 1e-3
+    f = gamma * np.cross(w, shape)
+    xn, Xn = o.bd_step(X + shape, X, np.array([0, 17]), f, box, 0.05, dt=dt, gamma=gamma, kT=0.0)
+    theta = _rotation_vectors(shape[None], (xn - Xn[0])[None])[0]
+    assert np.linalg.norm(theta - w * dt) < 1e-9 * np.linalg.norm(w * dt)
+
+
+def test_bd_body_noise_covariance():
+    """Catches a wrong noise amplitude (a lost factor 2 or square root, the translational
+    1/N_i, or the Cholesky factor of J in place of that of J^{-1}): over 10,000 draws of
+    force-free 8-bead rings, the body displacement has variance 2 kT dt/(N_i gamma) per
+    axis and the rotation vector has covariance 2 kT dt (gamma J)^{-1}, J = n R^2 diag(1/2, 1/2, 1)
+    (fluctuation-dissipation with the free-draining mobility of Sec. V.A)."""
+    box = np.array([10.0, 10.0, 10.0])
+    n, R = 8, 1.0
+    ring = _ring(n, R)
+    nb = 2000
+    X = np.tile([5.0, 5.0, 5.0], (nb, 1))
+    x = (X[:, None, :] + ring[None]).reshape(-1, 3)
+    off = np.arange(nb + 1) * n
+    kT, dt, gamma = 1.3, 1e-3, 2.0
+    th, dX = [], []
+    for step in range(5):
+        xn, Xn = o.bd_step(x, X, off, np.zeros_like(x), box, 0.05, dt=dt, gamma=gamma, kT=kT, seed=99, step=step)
+        th.append(_rotation_vectors(np.repeat(ring[None], nb, 0), xn.reshape(nb, n, 3) - Xn[:, None, :]))
+        dX.append(Xn - X)
+    th = np.concatenate(th)
+    dX = np.concatenate(dX)
+    m = th.shape[0]
+    sd = 5 * math.sqrt(2.0 / m)                     # five standard errors of a variance ratio
+    var_t = 2 * kT * dt / (n * gamma)
+    assert np.all(np.abs(dX.var(axis=0) / var_t - 1) < sd)
+    assert np.all(np.abs(dX.mean(axis=0)) < 5 * math.sqrt(var_t / m))
+    C = 2 * kT * dt * np.linalg.inv(gamma * n * R * R * np.diag([0.5, 0.5, 1.0]))
+    cov = np.cov(th.T)
+    d = np.sqrt(np.diag(C))
+    corr = cov / np.outer(d, d)
+    assert np.all(np.abs(np.diag(corr) - 1) < sd)
+    assert np.all(np.abs(corr - np.diag(np.diag(corr))) < 5 / math.sqrt(m))
