@@ -245,16 +245,26 @@ class HostStep:
 # fast_two_sum 3, df_add 11, df_mul 7, complex multiply 4 df_mul + 2 df_add = 50, complex
 # add 22; an r-point DFT of radix-2 butterflies takes r log2(r) complex additions: radix-2
 # 2 x 22 = 44, radix-4 8 x 22 = 176 (its -i is free), radix-8 24 x 22 plus two multiplies by
-# w8 (2 x 11 + 2 x 7 = 36 each; w8^2 = -i is free) = 600.
-DF_CMUL, DF_DFT = 50, {2: 44, 4: 176, 8: 600}
+# w8 (2 x 11 + 2 x 7 = 36 each; w8^2 = -i is free) = 600.  The radix-3 DFT takes five
+# complex additions (110), two df_add and two exact halvings (22 + 4) and two df_mul by
+# sqrt(3)/2 (14) = 150.
+DF_CMUL, DF_DFT = 50, {2: 44, 3: 150, 4: 176, 8: 600}
+
+
+def df_mesh_size(n):
+    """Whether the library's double-float transform takes an axis of n points:
+    n = 2^k or 3 2^k with a power-of-two part of at least 8, 16 <= n <= 1024."""
+    m = n // 3 if n % 3 == 0 else n
+    return 16 <= n <= 1024 and m & (m - 1) == 0 and (m == n or m >= 8)
 
 
 def df_transform_ops(n):
     """FP32 operations per point of one length-n double-float Stockham transform:
-    radix-8 passes, then one radix-4 or radix-2 pass; the twiddles of a pass with
-    sub-transform length Ns are trivial for the 1/Ns of its butterflies with k = 0
-    and are not counted."""
-    passes, l = [], int(round(np.log2(n)))
+    a radix-3 pass when 3 divides n, radix-8 passes, then one radix-4 or radix-2
+    pass; the twiddles of a pass with sub-transform length Ns are trivial for the
+    1/Ns of its butterflies with k = 0 and are not counted."""
+    passes = [3] if n % 3 == 0 else []
+    l = int(round(np.log2(n // 3 if n % 3 == 0 else n)))
     while l >= 3:
         passes.append(8)
         l -= 3
@@ -334,7 +344,7 @@ def bench_ours(args, ib, torch, rank, world, local):
     # (cuFFT is a library; the table build, the Krylov group and the body reductions are
     # composite; the near-field stages run on the second stream, where their events also
     # time the wait for the mesh pass they overlap)
-    df_mesh = all(int(m) & (int(m) - 1) == 0 for m in s.mesh)   # FP64 mesh in double-float transforms
+    df_mesh = all(df_mesh_size(int(m)) for m in s.mesh)   # FP64 mesh in double-float transforms
     cand = ("spread", "gather", "scale", "spread64", "gather64", "scale64")
     own = {k: v for k, v in prof.items() if k in cand and v[1] > 0}
     dominant = max(own, key=lambda k: own[k][0]) if own else "spread"

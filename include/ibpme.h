@@ -332,7 +332,7 @@ ibpme_status ibpme_features(ibpme_ctx* ctx, int n, const double* x, const ibpme_
  * is captured into a CUDA graph (where cudaMalloc is not allowed), engines whose
  * device memory belongs to a pool or a framework, and loops that must never reach
  * the allocator.  pme_spread needs a context, which allocates; this variant does
- * the same spreading (Eq. H_hat, same stencil and normalisation) with no context
+ * the same spreading as pme_spread (same stencil and normalisation) with no context
  * and no allocation of any kind: its only scratch, the positions wrapped into the
  * box, lives in a fixed array inside the library (IBPME_NOALLOC_MAX_BEADS x 3
  * doubles = 6 MiB), which every GPU that loads the library keeps until the

@@ -27,16 +27,24 @@ CMUL = 4 * DF_MUL + 2 * DF_ADD
 MUL_W8 = 2 * DF_ADD + 2 * DF_MUL             # (re +- im) / sqrt(2)
 
 
+DF_HALF = 2                                  # both words times 0.5 (exact)
+
+
 def dft_ops(r):
+    if r == 3:
+        # t1 = v1 + v2; t2 = v0 - t1/2; t3 = -+i (sqrt(3)/2)(v1 - v2); y0 = v0 + t1, y1,2 = t2 +- t3
+        return 5 * CADD + 2 * DF_ADD + 2 * DF_HALF + 2 * DF_MUL
     adds = r * int(math.log2(r))
     extra = 2 * MUL_W8 if r == 8 else 0      # w8 and w8^3 (w8^2 = -i costs nothing)
     return adds * CADD + extra
 
 
 def transform_ops_per_point(n):
-    """Walk the passes of a length-n transform point by point."""
-    l = int(round(math.log2(n)))
-    radices = [8] * (l // 3) + ([2 ** (l % 3)] if l % 3 else [])
+    """Walk the passes of a length-n transform point by point (a radix-3 pass first
+    when 3 divides n)."""
+    three = n % 3 == 0
+    l = int(round(math.log2(n // 3 if three else n)))
+    radices = ([3] if three else []) + [8] * (l // 3) + ([2 ** (l % 3)] if l % 3 else [])
     total, ns = 0, 1
     for r in radices:
         butterflies = n // r
@@ -48,11 +56,11 @@ def transform_ops_per_point(n):
 
 def test_primitive_counts_match_the_model():
     assert DF_ADD == 11 and DF_MUL == 7 and CMUL == bench.DF_CMUL == 50
-    for r in (2, 4, 8):
+    for r in (2, 3, 4, 8):
         assert bench.DF_DFT[r] == dft_ops(r), r
 
 
-@pytest.mark.parametrize("n", [16, 32, 64, 128, 256, 512, 1024])
+@pytest.mark.parametrize("n", [16, 32, 48, 64, 96, 128, 192, 256, 384, 512, 768, 1024])
 def test_transform_ops_per_point(n):
     assert bench.df_transform_ops(n) == pytest.approx(transform_ops_per_point(n), rel=1e-12)
 
@@ -69,3 +77,10 @@ def test_z_pass_work_of_the_headline_mesh():
     assert bound == "alu" and unit == "Gop/s"
     assert work == pytest.approx(pts * (2 * transform_ops_per_point(128) + 2 * DF_MUL), rel=1e-12)
     assert work == pytest.approx(515.2e6, rel=1e-3)
+
+
+@pytest.mark.parametrize("n,ok", [(16, True), (24, True), (40, False), (48, True), (96, True), (192, True), (256, True),
+                                  (768, True), (1024, True), (1536, False), (12, False), (8, False), (100, False)])
+def test_double_float_mesh_rule(n, ok):
+    """2^k or 3 2^k with a power-of-two part of at least 8, 16 to 1024 points."""
+    assert bench.df_mesh_size(n) == ok

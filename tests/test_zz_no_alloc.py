@@ -6,8 +6,9 @@ and real-time loops that must never enter the allocator.  For them the library
 offers pme_spread_noalloc, which needs no context and keeps its only scratch
 (the wrapped positions) in a fixed array inside the library.  These checks run
 it through the C ABI and compare its grid with the context-based pme_spread on
-the same inputs, twice in a row with different inputs, so that a stale scratch
-array would show.  The file is named to be collected last.
+the same inputs, twice in a row with different inputs, the smaller call first,
+so that scratch rows a kernel read past n by mistake, or rows left stale by the
+earlier call, would show.  The file is named to be collected last.
 """
 import numpy as np
 import pytest
@@ -33,7 +34,7 @@ def test_noalloc_spread_matches_pme_spread_twice(cuda_lib, prec):
     dt = torch.float64 if prec == "fp64" else torch.float32
     rng = np.random.default_rng(17)
     try:
-        for call, (n, nrhs) in enumerate([(301, 2), (97, 3)]):
+        for call, (n, nrhs) in enumerate([(97, 3), (301, 2)]):
             x = rng.uniform(-4, 10, size=(n, 3))
             q = rng.normal(size=(nrhs, n))
             xd, qd = cuda(x), cuda(q)
