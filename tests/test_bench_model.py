@@ -65,18 +65,32 @@ def test_transform_ops_per_point(n):
     assert bench.df_transform_ops(n) == pytest.approx(transform_ops_per_point(n), rel=1e-12)
 
 
-def test_z_pass_work_of_the_headline_mesh():
+def test_z_pass_work_of_the_charged_sphere_mesh():
     """Forward and inverse z transforms plus the Green's scaling (two df_mul per point)
-    on the half spectrum of the 128^3 mesh: 515.2 M FP32 operations per launch."""
+    on the half spectrum of the 128^3 mesh: 515.2 M FP32 operations per launch; its
+    algorithmic bytes: the double-float half spectrum (16 B per point) read and written
+    and the double-float Green's table (8 B per point) read, 34.1 MB + 5.3 MB."""
 
     class S:
         mesh = (128, 128, 128)
+        n = 0
 
-    bound, work, unit = bench.stage_work("scale64", S, 0, True)
     pts = 128 * 128 * 65
-    assert bound == "alu" and unit == "Gop/s"
-    assert work == pytest.approx(pts * (2 * transform_ops_per_point(128) + 2 * DF_MUL), rel=1e-12)
-    assert work == pytest.approx(515.2e6, rel=1e-3)
+    ops = bench.alu_work(S)
+    assert ops == pytest.approx(pts * (2 * transform_ops_per_point(128) + 2 * DF_MUL), rel=1e-12)
+    assert ops == pytest.approx(515.2e6, rel=1e-3)
+    bound, work, unit = bench.stage_work("scale64", S, 0, True)
+    assert bound == "hbm" and unit == "GB/s" and work == pts * (2 * 16 + 8)
+
+
+def test_pme_bytes_of_the_lattice():
+    """6 G w R + N (32 + 8 R) for the 256^3 FP32 mesh and 141,088 beads, one field."""
+
+    class S:
+        mesh = (256, 256, 256)
+        n = 141_088
+
+    assert bench.pme_bytes(S) == 6 * 256 ** 3 * 4 + 141_088 * 40
 
 
 @pytest.mark.parametrize("n,ok", [(16, True), (24, True), (40, False), (48, True), (96, True), (192, True), (256, True),
