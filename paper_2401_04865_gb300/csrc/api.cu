@@ -343,6 +343,65 @@ void pme_apply(ibpme_ctx* c, int n, const double* xw, const double* q, int nrhs,
     }
 }
 
+bool free_prepare(ibpme_ctx* c, const double* xw, int nrhs) {
+    if (std::getenv("IBPME_FULL_OPERATOR")) return false;   // the switch lets tests compare both paths
+    if (!near_free_build(c, xw)) return false;
+    if (!free_stencil_cache(c)) return false;
+    FreeSet& fs = c->fs;
+    const size_t m = (size_t)nrhs * fs.nfree;
+    fs.psi_r.ensure(sizeof(double) * (m ? m : 1));
+    fs.psi_k.ensure(sizeof(double) * (m ? m : 1));
+    fs.qsum.ensure(sizeof(double) * (size_t)(nrhs * c->ncfg));
+    return true;
+}
+
+void pme_apply_free(ibpme_ctx* c, const double* qc, int nrhs, int prec, double* psi_f, bool near32) {
+    FreeSet& fs = c->fs;
+    const int n = fs.nfree;
+    c->grid64_final = false;   // the meshes are about to hold other charges
+    if (n == 0) return;
+    double* pr = fs.psi_r.as<double>();
+    double* pk = fs.psi_k.as<double>();
+    const double* xf = fs.xf.as<double>();
+    const int* fcfg = c->ncfg > 1 ? c->bodies.free_cfg.as<int>() : nullptr;
+    // near field on the second stream, as in pme_apply
+    const cudaStream_t main = c->stream;
+    IBP_CUDA(cudaEventRecord(c->ev_fork, main));
+    IBP_CUDA(cudaStreamWaitEvent(c->aux, c->ev_fork, 0));
+    {
+        struct Restore {
+            ibpme_ctx* c;
+            cudaStream_t s;
+            ~Restore() { c->stream = s; }
+        } restore{c, main};
+        c->stream = c->aux;
+        near_apply_free(c, qc, nrhs, pr, near32 && prec == IBPME_MIXED);
+    }
+    IBP_CUDA(cudaEventRecord(c->ev_join, c->aux));
+    const int ch = nrhs * c->ncfg;
+    const StencilCache* sc = free_stencil_cache(c);
+    if (prec == IBPME_MIXED) {
+        if (!c->have32) fail(IBPME_ERR_ARG, "mixed precision needs a context created with IBPME_MIXED");
+        c->mesh32.spread(n, xf, qc, nrhs, fcfg, c->ncfg, c->stream, sc);
+        c->mesh32.transform(ch, c->stream);
+        c->mesh32.gather(n, xf, nrhs, fcfg, pk, nullptr, c->stream, sc);
+    } else {
+        c->mesh64.spread(n, xf, qc, nrhs, fcfg, c->ncfg, c->stream, sc);
+        c->mesh64.transform(ch, c->stream);
+        c->mesh64.gather(n, xf, nrhs, fcfg, pk, nullptr, c->stream, sc);
+    }
+    IBP_CUDA(cudaStreamWaitEvent(c->stream, c->ev_join, 0));
+    double* qsum = fs.qsum.as<double>();
+    IBP_CUDA(cudaMemsetAsync(qsum, 0, sizeof(double) * ch, c->stream));
+    qsum_kernel<<<dim3(div_up(n, 256) < 64 ? div_up(n, 256) : 64, nrhs), 256, 0, c->stream>>>(n, nrhs, qc, fcfg, qsum);
+    IBP_CHECK_LAUNCH();
+    const double V = c->p.box[0] * c->p.box[1] * c->p.box[2];
+    const double k0 = 1.0 / (4.0 * c->xi * c->xi * V * c->eps);
+    const long long m = (long long)nrhs * n;
+    combine_kernel<<<div_up(m, 256), 256, 0, c->stream>>>(m, n, nrhs, pr, pk, qsum, fcfg, k0, psi_f);
+    IBP_CHECK_LAUNCH();
+}
+
 }  // namespace ibp
 
 using namespace ibp;

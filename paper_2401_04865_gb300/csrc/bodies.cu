@@ -452,7 +452,7 @@ void bodies_upload(ibpme_ctx* c, int n, const ibpme_bodies* b, const double* xw,
     if (!same) {
         // unknowns of configuration k: its free beads (beads of multi-bead bodies), then its multi-bead bodies
         std::vector<int> free_idx, free_unk, mb_body, mb_unk, mb_first, mb_cnt, bead_unk(n, -1), body_unk(nb, -1),
-            unk_cfg, bead_cfg(n), uo(ncfg + 1, 0);
+            unk_cfg, bead_cfg(n), uo(ncfg + 1, 0), free_pos(n, -1), free_cfg;
         int u = 0;
         for (int k = 0; k < ncfg; ++k) {
             uo[k] = u;
@@ -461,6 +461,8 @@ void bodies_upload(ibpme_ctx* c, int n, const ibpme_bodies* b, const double* xw,
                 if (off[i + 1] - off[i] < 2) continue;
                 for (int j = off[i]; j < off[i + 1]; ++j) {
                     bead_unk[j] = u;
+                    free_pos[j] = (int)free_idx.size();
+                    free_cfg.push_back(k);
                     free_idx.push_back(j);
                     free_unk.push_back(u++);
                     unk_cfg.push_back(k);
@@ -490,8 +492,14 @@ void bodies_upload(ibpme_ctx* c, int n, const ibpme_bodies* b, const double* xw,
             if (!v.empty())
                 IBP_CUDA(cudaMemcpyAsync(dst.p, v.data(), sizeof(int) * v.size(), cudaMemcpyHostToDevice, s));
         };
+        std::vector<int> iota(free_idx.size());
+        for (size_t f = 0; f < iota.size(); ++f) iota[f] = (int)f;
         up(bd.free_idx, free_idx);
         up(bd.free_unk, free_unk);
+        up(bd.free_pos, free_pos);
+        up(bd.free_cfg, free_cfg);
+        up(bd.iota, iota);
+        bd.free_pos_h = free_pos;
         up(bd.mb_body, mb_body);
         up(bd.mb_unk, mb_unk);
         up(bd.mb_first, mb_first);

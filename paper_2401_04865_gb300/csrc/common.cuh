@@ -214,6 +214,7 @@ struct NearList {
     DevBuf cb_flag;                // [nb] 1 if the body is compact
     DevBuf cb_hi, cb_lo;           // [n] float4: position relative to the body's first bead, hi + lo parts
     DevBuf cb_tasks;               // int4 per block: (body, first target, first source, counts)
+    std::vector<int4> cb_tasks_h;  // host copy of the tasks
     int cb_ntasks = 0;
     unsigned long long cb_tasks_key = 0;
     DevBuf tab32;                  // [nt] float4: FP32 cubic coefficients of phi per interval
@@ -248,6 +249,10 @@ struct BodyData {
     DevBuf cfg_bodies;  // [ncfg+1] body offsets of the configurations
     DevBuf rel;         // [n][3] r_ij = minimum image of x_ij - X_i
     DevBuf scratch;     // reductions and BD temporaries
+    DevBuf free_pos;    // [n] position of a bead in the free-bead list, -1 for ions
+    DevBuf free_cfg;    // [nfree] configuration of each free bead
+    DevBuf iota;        // [nfree] 0, 1, ..., nfree - 1 (identity order of the free-bead list)
+    std::vector<int> free_pos_h;   // host copy of free_pos
     std::vector<int> uo_h, cfg_beads_h, cfg_bodies_h;
     std::vector<int> host_off, host_cfg;   // structure of the last upload (to skip rebuilding the lists)
     int host_n = -1;
@@ -256,6 +261,32 @@ struct BodyData {
 };
 
 struct Krylov;   // krylov.cu
+
+// The free beads (beads of multi-bead bodies) on their own.  A Krylov vector
+// carries charges on these beads only (ion charges are fixed and eliminated) and
+// only their potentials enter the reduced saddle operator, so the operator of
+// the Krylov iterations evaluates sources and targets of this list alone: the
+// mesh pass spreads and gathers the free beads through their own stencil cache,
+// the real-space pass takes the table's pairs between two free beads (re-indexed
+// into the list) and the compact bodies' pairs.  Everything is indexed by the
+// position f in the list (bodies.free_idx[f] is the bead).
+struct FreeSet {
+    bool valid = false;
+    unsigned long long fp = 0;        // position fingerprint the data belong to
+    unsigned long long version = 0;   // body structure they belong to
+    int nfree = 0;
+    DevBuf xf;                        // [nfree][3] wrapped positions
+    StencilCache sc;                  // their stencils (and tile bins)
+    DevBuf sorted_of;                 // [n] pair-table row (cell-sorted position) of each bead
+    long long npairs = 0;             // pairs between two free beads outside the compact bodies
+    DevBuf row_count, rowptr, col, val, pair32, scan_tmp;   // that table in list indices
+    DevBuf qf, qs;                    // packed charges of its FP32 and FP64 passes
+    DevBuf cb_hi, cb_lo;              // [nfree] compact-body relative positions in list order
+    DevBuf cb_tasks;                  // compact-body tasks in list indices
+    int cb_ntasks = 0;
+    unsigned long long cb_tasks_key = 0;
+    DevBuf psi_r, psi_k, qsum;        // [R][nfree] partial potentials, [channels] charge sums
+};
 
 // Body-block preconditioner (precond.cu): inverses of the bodies' free-space
 // saddle blocks, cached per body shape for the life of the context.
@@ -362,6 +393,7 @@ struct ibpme_ctx {
     ibp::DevBuf ml_feat, ml_scratch, ml_scales, ml_y;   // learned warm start
     cudaEvent_t ev_in = nullptr, ev_out = nullptr;
     ibp::StencilCache stencils;               // stencils of the current positions
+    ibp::FreeSet fs;                          // the free beads on their own (Krylov operator)
     ibp::Precond pre;                         // body-block preconditioner
     cudaStream_t aux = nullptr;               // second branch of a PME evaluation (near field)
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
@@ -383,6 +415,15 @@ void near_apply(ibpme_ctx* c, int n, const double* q, int nrhs, double* psi_r, b
 void near_field(ibpme_ctx* c, int n, const double* xw, const double* q, int nrhs, double* E_r);  // overwrite
 double self_term(const ibpme_ctx* c);   // phi_self (without 1/eps)
 
+// The free-bead data of the current positions and body structure (call after
+// near_build, outside any stream capture): positions, stencils, the free-free pair
+// table and the compact-body tasks in list indices.  False when the free-bead
+// operator cannot be used (no free beads, or the table was built without bodies).
+bool near_free_build(ibpme_ctx* c, const double* xw);
+// psi_r [nrhs][nfree] = real-space potential at the free beads of the charges qc
+// [nrhs][nfree] on the free beads (self term, free-free table, compact bodies)
+void near_apply_free(ibpme_ctx* c, const double* qc, int nrhs, double* psi_r, bool fp32);
+
 // ---- dffft.cu ----
 bool df_fft_supported(const MeshGeom& g);
 void df_fft_init(const MeshGeom& g, DevBuf tw[3], cudaStream_t s);
@@ -393,6 +434,8 @@ void df_fft_convolve(const MeshGeom& g, int ch, const float2* green, const doubl
 // Cached stencils for the current positions (rebuilt when the position
 // fingerprint of the last near_build changed), or NULL without a fingerprint.
 const StencilCache* stencil_cache(ibpme_ctx* c, int n, const double* xw);
+// Stencils of the free beads (c->fs.xf), keyed like stencil_cache.
+const StencilCache* free_stencil_cache(ibpme_ctx* c);
 
 // ---- api.cu helpers ----
 void resolve_params(const ibpme_params* in, ibpme_params* out);   // rules of Sec. III.D.2; throws on bad input
@@ -404,6 +447,12 @@ void wrap_positions(ibpme_ctx* c, int n, const double* x, double* xw);
 void pme_reserve(ibpme_ctx* c, int n, int nrhs, bool field);
 void pme_apply(ibpme_ctx* c, int n, const double* xw, const double* q, int nrhs, int prec,
                double* psi, double* E, bool near_ready, bool near32 = false);
+// Prepare the free-bead operator for the positions xw of the last near_build and nrhs
+// fields (after near_build, before any capture); false if it cannot serve this call.
+bool free_prepare(ibpme_ctx* c, const double* xw, int nrhs);
+// psi_f = M q restricted to the free beads: charges qc [nrhs][nfree] on the free beads
+// (every other charge zero), potentials psi_f [nrhs][nfree] at the free beads.
+void pme_apply_free(ibpme_ctx* c, const double* qc, int nrhs, int prec, double* psi_f, bool near32);
 void* pinned_host(ibpme_ctx* c, size_t bytes);
 
 // ---- bodies.cu ----

@@ -37,6 +37,7 @@ struct Krylov {
     int nk = 0, R = 0, S = 0, m = 0, nblk = 0;
     DevBuf V, H, cs, sn, g, y, w, x, d, r, rc, part, scal, active, qop, psi, psi_tot, qtot, Ax, norms, jdev;
     DevBuf pu, pt, pz;   // preconditioned operand, cycle update before and after P^{-1}
+    DevBuf qc, psif;     // [R][nfree] charges and potentials of the free beads (free-bead operator)
     // one captured Arnoldi iteration per mesh precision, replayed for every j
     cudaGraphExec_t exec[2] = {nullptr, nullptr};
     std::vector<long long> sig[2];
@@ -433,15 +434,28 @@ __global__ void scatter_kernel(int nfree, long long ustride, int n, int R, const
     qop[(size_t)r * n + free_idx[i]] = u[(size_t)r * ustride + free_unk[i]];
 }
 
+// Free-bead charges of u in list order: qc[r][i] = u[r][free_unk[i]].
+__global__ void gather_free_kernel(int nfree, long long ustride, int R, const int* __restrict__ free_unk,
+                                   const double* __restrict__ u, const int* __restrict__ jdev, int nk,
+                                   double* __restrict__ qc) {
+    const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (t >= (long long)nfree * R) return;
+    if (jdev) u += (size_t)(*jdev) * nk;
+    const int r = (int)(t / nfree), i = (int)(t % nfree);
+    qc[t] = u[(size_t)r * ustride + free_unk[i]];
+}
+
 // y_bead = -psi_bead + Psi'(body); y_body = sum of the body's charges.
 // Blocks [0, bead_blocks) take the bead rows; each later block sums the
 // charges of one (right-hand side, multi-bead body) pair, so that a body of
 // hundreds of beads is reduced by a whole block rather than a serial warp.
+// psi holds [R][n] bead potentials (list == false) or [R][nfree] free-bead
+// potentials in list order (list == true).
 __global__ void assemble_kernel(int nfree, int nmb, int nk, long long ustride, int n, int R, int bead_blocks,
                                 const int* __restrict__ free_idx, const int* __restrict__ free_unk,
                                 const int* __restrict__ bead_body, const int* __restrict__ body_unk,
                                 const int* __restrict__ mb_unk, const int* __restrict__ mb_first,
-                                const int* __restrict__ mb_cnt, const double* __restrict__ psi,
+                                const int* __restrict__ mb_cnt, const double* __restrict__ psi, bool list,
                                 const double* __restrict__ u, const int* __restrict__ jdev, double* __restrict__ y) {
     __shared__ double sh[32];
     if (jdev) u += (size_t)(*jdev) * nk;
@@ -450,7 +464,8 @@ __global__ void assemble_kernel(int nfree, int nmb, int nk, long long ustride, i
         if (t >= (long long)nfree * R) return;
         const int r = (int)(t / nfree), i = (int)(t % nfree);
         const int j = free_idx[i];
-        y[(size_t)r * nk + free_unk[i]] = -psi[(size_t)r * n + j] + u[(size_t)r * ustride + body_unk[bead_body[j]]];
+        const double p = list ? psi[t] : psi[(size_t)r * n + j];
+        y[(size_t)r * nk + free_unk[i]] = -p + u[(size_t)r * ustride + body_unk[bead_body[j]]];
         return;
     }
     const int wid = blockIdx.x - bead_blocks;
@@ -595,6 +610,7 @@ struct Solver {
     int n, R, S, ncfg, nk, nfree, nmb, nb, m;
     int iters = 0, matvec64 = 0;
     bool pre_on = false;         // body-block preconditioner active for this solve
+    bool use_free = false;       // the Krylov operator evaluates the free beads alone
     std::vector<double> bnorm;   // |b| per system
     bool want_b = false;         // the next norms() call also fetches |b|
 
@@ -640,6 +656,8 @@ struct Solver {
         k->jdev.ensure(sizeof(int));
         const size_t full = (size_t)R * n;
         for (DevBuf* b : {&k->qop, &k->psi, &k->psi_tot, &k->qtot}) b->ensure(sizeof(double) * full);
+        const size_t fr = (size_t)R * (nfree > 0 ? nfree : 1);
+        for (DevBuf* b : {&k->qc, &k->psif}) b->ensure(sizeof(double) * fr);
     }
 
     // y = A(prec) u for the reduced saddle operator; u[r] starts at u + r * ustride
@@ -654,15 +672,27 @@ struct Solver {
             ustride = nk;
             jdev = nullptr;
         }
-        scatter_kernel<<<blocks_for((long long)nfree * R), 256, 0, s()>>>(nfree, ustride, n, R, I(bd.free_idx),
-                                                                          I(bd.free_unk), u, jdev, nk, D(k->qop));
-        IBP_CHECK_LAUNCH();
-        pme_apply(c, n, a.xw, D(k->qop), R, prec, D(k->psi), nullptr, true, prec == IBPME_MIXED);
+        const double* psi_op;
+        if (use_free) {
+            // the Krylov vector's charges sit on the free beads only, and only their
+            // potentials enter the reduced operator: evaluate the free beads alone
+            gather_free_kernel<<<blocks_for((long long)nfree * R), 256, 0, s()>>>(nfree, ustride, R, I(bd.free_unk),
+                                                                                  u, jdev, nk, D(k->qc));
+            IBP_CHECK_LAUNCH();
+            pme_apply_free(c, D(k->qc), R, prec, D(k->psif), prec == IBPME_MIXED);
+            psi_op = D(k->psif);
+        } else {
+            scatter_kernel<<<blocks_for((long long)nfree * R), 256, 0, s()>>>(nfree, ustride, n, R, I(bd.free_idx),
+                                                                              I(bd.free_unk), u, jdev, nk, D(k->qop));
+            IBP_CHECK_LAUNCH();
+            pme_apply(c, n, a.xw, D(k->qop), R, prec, D(k->psi), nullptr, true, prec == IBPME_MIXED);
+            psi_op = D(k->psi);
+        }
         const int bb = div_up((long long)nfree * R, 256);
         assemble_kernel<<<std::max(1, bb + nmb * R), 256, 0, s()>>>(nfree, nmb, nk, ustride, n, R, bb, I(bd.free_idx),
                                                            I(bd.free_unk), I(bd.bead_body), I(bd.body_unk),
-                                                           I(bd.mb_unk), I(bd.mb_first), I(bd.mb_cnt), D(k->psi), u,
-                                                           jdev, y);
+                                                           I(bd.mb_unk), I(bd.mb_first), I(bd.mb_cnt), psi_op,
+                                                           use_free, u, jdev, y);
         IBP_CHECK_LAUNCH();
     }
 
@@ -750,6 +780,18 @@ struct Solver {
                                       P(prec == IBPME_MIXED ? m32.work.p : m64.work.p), P(m64.df_buf.p), P(m64.grid_df.p),
                                       P(m32.green.p), P(m64.green.p), P(m64.green_df.p), P(m64.df_tw[0].p),
                                       P(m64.df_tw[1].p), P(m64.df_tw[2].p)};
+        if (use_free) {
+            const FreeSet& fs = c->fs;
+            const StencilCache& fc = fs.sc;
+            for (long long v : {1LL, (long long)fs.nfree, (long long)fs.cb_ntasks, P(fs.xf.p), P(fs.rowptr.p),
+                                P(fs.col.p), P(fs.val.p), P(fs.pair32.p), P(fs.qf.p), P(fs.qs.p), P(fs.cb_hi.p),
+                                P(fs.cb_lo.p), P(fs.cb_tasks.p), P(fs.psi_r.p), P(fs.psi_k.p), P(fs.qsum.p),
+                                (long long)fc.valid, (long long)fc.tiles, (long long)fc.tile_n[0],
+                                (long long)fc.tile_n[1], (long long)fc.tile_n[2], P(fc.start.p), P(fc.frac.p),
+                                P(fc.frac32.p), P(fc.w64.p), P(fc.tile_sorted.p), P(fc.tile_key.p), P(bd.iota.p),
+                                P(bd.free_cfg.p), P(k->qc.p), P(k->psif.p)})
+                sig.push_back(v);
+        }
         const int gi = prec == IBPME_MIXED ? 1 : 0;
         if (k->exec[gi] && k->sig[gi] == sig) return k->exec[gi];
         if (k->exec[gi]) {
@@ -943,6 +985,7 @@ struct Solver {
         const BodyData& bd = c->bodies;
         alloc();
         pre_on = a.precond && nk > 0 && precond_prepare(c);
+        use_free = nk > 0 && nfree > 0 && free_prepare(c, a.xw, R);
         const long long len = (long long)nk * R;
         IBP_CUDA(cudaMemsetAsync(k->qop.p, 0, sizeof(double) * (size_t)R * n, s()));   // ions stay 0
         // |b| of the full system of Eq. saddle, b = [-r.E0 ; Q], per system

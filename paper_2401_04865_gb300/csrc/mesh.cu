@@ -1437,17 +1437,17 @@ void Mesh<T>::gather(int n, const double* xw, int nrhs, const int* bead_cfg, dou
 template struct Mesh<float>;
 template struct Mesh<double>;
 
-const StencilCache* stencil_cache(ibpme_ctx* c, int n, const double* xw) {
+namespace {
+
+// Stencils (and tile bins) of n beads at xw, bead b of configuration bcfg[b], into b.
+void build_stencils(ibpme_ctx* c, StencilCache& b, int n, const double* xw, const int* bcfg) {
     const MeshGeom& g = c->mesh64.g;   // both meshes share N, h and P
-    if (n == 0 || !c->near.fp_valid) return nullptr;   // no fingerprint of these positions: no cache key
-    StencilCache& b = c->stencils;
-    if (b.valid && b.fp == c->near.fp && b.n == n && b.ncfg == c->ncfg) return &b;
     b.valid = false;
     int4* start = static_cast<int4*>(b.start.ensure(sizeof(int4) * n));
     double4* frac = static_cast<double4*>(b.frac.ensure(sizeof(double4) * n));
     float4* frac32 = static_cast<float4*>(b.frac32.ensure(sizeof(float4) * n));
     double* w64 = static_cast<double*>(b.w64.ensure(sizeof(double) * 3 * (size_t)g.P * n));
-    stencil_cache_kernel<<<div_up(3LL * g.P * n, 256), 256, 0, c->stream>>>(n, xw, c->bcfg, g, start, frac, frac32,
+    stencil_cache_kernel<<<div_up(3LL * g.P * n, 256), 256, 0, c->stream>>>(n, xw, bcfg, g, start, frac, frac32,
                                                                              w64);
     IBP_CHECK_LAUNCH();
     // tile bins when one warp per bead already fills the GPU and a region of
@@ -1484,6 +1484,25 @@ const StencilCache* stencil_cache(ibpme_ctx* c, int n, const double* xw) {
     b.n = n;
     b.ncfg = c->ncfg;
     b.valid = true;
+}
+
+}  // namespace
+
+const StencilCache* stencil_cache(ibpme_ctx* c, int n, const double* xw) {
+    if (n == 0 || !c->near.fp_valid) return nullptr;   // no fingerprint of these positions: no cache key
+    StencilCache& b = c->stencils;
+    if (b.valid && b.fp == c->near.fp && b.n == n && b.ncfg == c->ncfg) return &b;
+    build_stencils(c, b, n, xw, c->bcfg);
+    return &b;
+}
+
+const StencilCache* free_stencil_cache(ibpme_ctx* c) {
+    const FreeSet& fs = c->fs;
+    const int n = fs.nfree;
+    if (n == 0 || !fs.valid) return nullptr;
+    StencilCache& b = c->fs.sc;
+    if (b.valid && b.fp == c->near.fp && b.n == n && b.ncfg == c->ncfg) return &b;
+    build_stencils(c, b, n, fs.xf.as<double>(), c->ncfg > 1 ? c->bodies.free_cfg.as<int>() : nullptr);
     return &b;
 }
 

@@ -1227,16 +1227,16 @@ void compact_prepare(ibpme_ctx* c, int n, const double* xw) {
     if (!tasks.empty()) {
         nl.cb_tasks.ensure(sizeof(int4) * tasks.size());
         IBP_CUDA(cudaMemcpyAsync(nl.cb_tasks.p, tasks.data(), sizeof(int4) * tasks.size(), cudaMemcpyHostToDevice, s));
-        IBP_CUDA(cudaStreamSynchronize(s));   // the host vector goes out of scope
+        IBP_CUDA(cudaStreamSynchronize(s));   // the host vector is replaced below
     }
+    nl.cb_tasks_h = std::move(tasks);
     nl.cb_tasks_key = bd.version;
 }
 
 int cb_grid(int ntasks) { return ntasks < 152 * kCbBlocksPerSm ? ntasks : 152 * kCbBlocksPerSm; }
 
 template <bool FP32>
-void compact_apply(ibpme_ctx* c, int n, const double* q, int nrhs, double* psi_r) {
-    const CbArgs A = cb_args(c);
+void compact_apply(ibpme_ctx* c, const CbArgs& A, int n, const double* q, int nrhs, double* psi_r) {
     const int g = cb_grid(A.ntasks);
     const double ie = 1.0 / c->eps;
     cudaStream_t s = c->stream;
@@ -1447,7 +1447,7 @@ void near_apply(ibpme_ctx* c, int n, const double* q, int nrhs, double* psi_r, b
             default: near_apply32_kernel<4><<<blocks, 128, 0, s>>>(n, rp, pc, od, k.self, ie, qf, q, psi_r); break;
         }
         IBP_CHECK_LAUNCH();
-        if (nl.cb_on && nl.cb_ntasks > 0) compact_apply<true>(c, n, q, nrhs, psi_r);
+        if (nl.cb_on && nl.cb_ntasks > 0) compact_apply<true>(c, cb_args(c), n, q, nrhs, psi_r);
         return;
     }
     double* qs = static_cast<double*>(nl.qs.ensure(sizeof(double) * (size_t)n * nrhs));
@@ -1464,7 +1464,7 @@ void near_apply(ibpme_ctx* c, int n, const double* q, int nrhs, double* psi_r, b
         default: near_apply_kernel<8><<<blocks, 128, 0, s>>>(n, rp, cl, vl, od, k.self, ie, qs, q, psi_r); break;
     }
     IBP_CHECK_LAUNCH();
-    if (nl.cb_on && nl.cb_ntasks > 0) compact_apply<false>(c, n, q, nrhs, psi_r);
+    if (nl.cb_on && nl.cb_ntasks > 0) compact_apply<false>(c, cb_args(c), n, q, nrhs, psi_r);
 }
 
 void near_field(ibpme_ctx* c, int n, const double* xw, const double* q, int nrhs, double* E_r) {
@@ -1481,6 +1481,198 @@ void near_field(ibpme_ctx* c, int n, const double* xw, const double* q, int nrhs
         IBP_CHECK_LAUNCH();
     }
     if (nl.cb_on && nl.cb_ntasks > 0) compact_field(c, n, q, nrhs, E_r);
+}
+
+namespace {
+
+// ---- the free beads on their own (the Krylov operator's sources and targets) ----
+
+// Pair-table row (cell-sorted position) of every bead.
+__global__ void invert_order_kernel(int n, const int* __restrict__ order, int* __restrict__ inv) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < n) inv[order[t]] = t;
+}
+
+// Wrapped positions of the free beads in list order.
+__global__ void free_positions_kernel(int nfree, const int* __restrict__ free_idx, const double* __restrict__ xw,
+                                      double* __restrict__ xf) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= 3 * nfree) return;
+    const int f = i / 3, d = i - 3 * f;
+    xf[i] = xw[3 * free_idx[f] + d];
+}
+
+// Compact-body relative positions in list order.
+__global__ void free_rel_kernel(int nfree, const int* __restrict__ free_idx, const float4* __restrict__ hi,
+                                const float4* __restrict__ lo, float4* __restrict__ fhi, float4* __restrict__ flo) {
+    const int f = blockIdx.x * blockDim.x + threadIdx.x;
+    if (f >= nfree) return;
+    fhi[f] = hi[free_idx[f]];
+    flo[f] = lo[free_idx[f]];
+}
+
+// Pairs of free bead f's table row whose other bead is free too (one thread per row).
+__global__ void ff_count_kernel(int nfree, const int* __restrict__ free_idx, const int* __restrict__ sorted_of,
+                                const long long* __restrict__ rowptr, const int* __restrict__ col,
+                                const int* __restrict__ order, const int* __restrict__ free_pos,
+                                int* __restrict__ count) {
+    const int f = blockIdx.x * blockDim.x + threadIdx.x;
+    if (f >= nfree) return;
+    const int t = sorted_of[free_idx[f]];
+    int k = 0;
+    for (long long p = rowptr[t]; p < rowptr[t + 1]; ++p) k += free_pos[order[col[p]]] >= 0 ? 1 : 0;
+    count[f] = k;
+}
+
+// Those pairs in list indices: column, FP64 value and the (column, FP32 value) word.
+__global__ void ff_fill_kernel(int nfree, const int* __restrict__ free_idx, const int* __restrict__ sorted_of,
+                               const long long* __restrict__ rowptr, const int* __restrict__ col,
+                               const int* __restrict__ order, const int* __restrict__ free_pos,
+                               const double* __restrict__ val, const uint2* __restrict__ pair32,
+                               const long long* __restrict__ fptr, int* __restrict__ fcol, double* __restrict__ fval,
+                               uint2* __restrict__ fpair32) {
+    const int f = blockIdx.x * blockDim.x + threadIdx.x;
+    if (f >= nfree) return;
+    const int t = sorted_of[free_idx[f]];
+    long long k = fptr[f];
+    for (long long p = rowptr[t]; p < rowptr[t + 1]; ++p) {
+        const int g = free_pos[order[col[p]]];
+        if (g < 0) continue;
+        fcol[k] = g;
+        fval[k] = val[p];
+        fpair32[k] = make_uint2((unsigned)g, pair32[p].y);
+        ++k;
+    }
+}
+
+CbArgs cb_args_free(const ibpme_ctx* c) {
+    CbArgs A = cb_args(c);
+    A.tasks = c->fs.cb_tasks.as<int4>();
+    A.ntasks = c->fs.cb_ntasks;
+    A.hi = c->fs.cb_hi.as<float4>();
+    A.lo = c->fs.cb_lo.as<float4>();
+    return A;
+}
+
+}  // namespace
+
+bool near_free_build(ibpme_ctx* c, const double* xw) {
+    NearList& nl = c->near;
+    FreeSet& fs = c->fs;
+    const BodyData& bd = c->bodies;
+    const int n = nl.n, nf = bd.nfree;
+    if (!nl.fp_valid || !c->bodies_current || bd.host_n != n || nf == 0) return false;
+    if (fs.valid && fs.fp == nl.fp && fs.version == bd.version && fs.nfree == nf) return true;
+    cudaStream_t s = c->stream;
+    fs.valid = false;
+    fs.nfree = nf;
+    const int* fidx = bd.free_idx.as<int>();
+    double* xf = static_cast<double*>(fs.xf.ensure(sizeof(double) * 3 * (size_t)nf));
+    free_positions_kernel<<<div_up(3LL * nf, 256), 256, 0, s>>>(nf, fidx, xw, xf);
+    IBP_CHECK_LAUNCH();
+    // the table's pairs between two free beads, re-indexed into the list
+    int* sorted_of = static_cast<int*>(fs.sorted_of.ensure(sizeof(int) * (n + 1)));
+    invert_order_kernel<<<div_up(n, 256), 256, 0, s>>>(n, nl.cell_beads.as<int>(), sorted_of);
+    IBP_CHECK_LAUNCH();
+    int* cnt = static_cast<int*>(fs.row_count.ensure(sizeof(int) * (nf + 1)));
+    long long* fptr = static_cast<long long*>(fs.rowptr.ensure(sizeof(long long) * (nf + 1)));
+    ff_count_kernel<<<div_up(nf, 128), 128, 0, s>>>(nf, fidx, sorted_of, nl.rowptr.as<long long>(), nl.col.as<int>(),
+                                                    nl.cell_beads.as<int>(), bd.free_pos.as<int>(), cnt);
+    IBP_CHECK_LAUNCH();
+    scan_counts(cnt, fptr, nf, fs.scan_tmp, s);
+    long long* host_total = static_cast<long long*>(pinned_host(c, sizeof(long long)));
+    IBP_CUDA(cudaMemcpyAsync(host_total, fptr + nf, sizeof(long long), cudaMemcpyDeviceToHost, s));
+    IBP_CUDA(cudaStreamSynchronize(s));
+    fs.npairs = *host_total;
+    const size_t np = (size_t)(fs.npairs > 0 ? fs.npairs : 1);
+    int* fcol = static_cast<int*>(fs.col.ensure(sizeof(int) * np));
+    double* fval = static_cast<double*>(fs.val.ensure(sizeof(double) * np));
+    uint2* fp32 = static_cast<uint2*>(fs.pair32.ensure(sizeof(uint2) * np));
+    if (fs.npairs > 0) {
+        ff_fill_kernel<<<div_up(nf, 128), 128, 0, s>>>(nf, fidx, sorted_of, nl.rowptr.as<long long>(), nl.col.as<int>(),
+                                                       nl.cell_beads.as<int>(), bd.free_pos.as<int>(),
+                                                       nl.val.as<double>(), nl.pair32.as<uint2>(), fptr, fcol, fval,
+                                                       fp32);
+        IBP_CHECK_LAUNCH();
+    }
+    fs.qf.ensure(sizeof(float4) * (nf + 1));
+    fs.qs.ensure(sizeof(double) * (size_t)(nf + 1) * kMaxRhs);
+    // compact bodies: relative positions in list order, tasks in list indices (a task's
+    // targets and sources lie in one body, whose free beads are consecutive in the list)
+    if (nl.cb_on && nl.cb_ntasks > 0) {
+        float4* fhi = static_cast<float4*>(fs.cb_hi.ensure(sizeof(float4) * (nf + 1)));
+        float4* flo = static_cast<float4*>(fs.cb_lo.ensure(sizeof(float4) * (nf + 1)));
+        free_rel_kernel<<<div_up(nf, 256), 256, 0, s>>>(nf, fidx, nl.cb_hi.as<float4>(), nl.cb_lo.as<float4>(), fhi,
+                                                         flo);
+        IBP_CHECK_LAUNCH();
+        if (fs.cb_tasks_key != nl.cb_tasks_key || fs.cb_ntasks != nl.cb_ntasks) {
+            std::vector<int4> t(nl.cb_tasks_h);
+            for (int4& w : t) {
+                w.y = bd.free_pos_h[w.y];
+                w.z = bd.free_pos_h[w.z];
+                if (w.y < 0 || w.z < 0) fail(IBPME_ERR_ARG, "internal: compact-body task outside the free beads");
+            }
+            fs.cb_tasks.ensure(sizeof(int4) * t.size());
+            IBP_CUDA(cudaMemcpyAsync(fs.cb_tasks.p, t.data(), sizeof(int4) * t.size(), cudaMemcpyHostToDevice, s));
+            IBP_CUDA(cudaStreamSynchronize(s));   // the host vector goes out of scope
+            fs.cb_ntasks = (int)t.size();
+            fs.cb_tasks_key = nl.cb_tasks_key;
+        }
+    } else {
+        fs.cb_ntasks = 0;
+        fs.cb_tasks_key = 0;
+    }
+    fs.fp = nl.fp;
+    fs.version = bd.version;
+    fs.valid = true;
+    return true;
+}
+
+void near_apply_free(ibpme_ctx* c, const double* qc, int nrhs, double* psi_r, bool fp32) {
+    FreeSet& fs = c->fs;
+    const int n = fs.nfree;
+    if (n == 0) return;
+    fp32 = fp32 && nrhs <= 4;
+    ProfScope ps(fp32 ? ST_NEAR_APPLY32 : ST_NEAR_APPLY, c->stream);
+    const PairConst k = make_const(c);
+    const int blocks = div_up((long long)n * 32, 128);
+    const long long* rp = fs.rowptr.as<long long>();
+    const double ie = 1.0 / c->eps;
+    cudaStream_t s = c->stream;
+    const int* od = c->bodies.iota.as<int>();   // rows are list positions already
+    const bool cb = c->near.cb_on && fs.cb_ntasks > 0;
+    if (fp32) {
+        float4* qf = fs.qf.as<float4>();
+        pack_q32_kernel<<<div_up(n, 256), 256, 0, s>>>(n, nrhs, od, qc, qf);
+        IBP_CHECK_LAUNCH();
+        const uint2* pc = fs.pair32.as<uint2>();
+        switch (nrhs) {
+            case 1: near_apply32_kernel<1><<<blocks, 128, 0, s>>>(n, rp, pc, od, k.self, ie, qf, qc, psi_r); break;
+            case 2: near_apply32_kernel<2><<<blocks, 128, 0, s>>>(n, rp, pc, od, k.self, ie, qf, qc, psi_r); break;
+            case 3: near_apply32_kernel<3><<<blocks, 128, 0, s>>>(n, rp, pc, od, k.self, ie, qf, qc, psi_r); break;
+            default: near_apply32_kernel<4><<<blocks, 128, 0, s>>>(n, rp, pc, od, k.self, ie, qf, qc, psi_r); break;
+        }
+        IBP_CHECK_LAUNCH();
+        if (cb) compact_apply<true>(c, cb_args_free(c), n, qc, nrhs, psi_r);
+        return;
+    }
+    double* qs = fs.qs.as<double>();
+    pack_q64_kernel<<<div_up(n, 256), 256, 0, s>>>(n, nrhs, od, qc, qs);
+    IBP_CHECK_LAUNCH();
+    const int* cl = fs.col.as<int>();
+    const double* vl = fs.val.as<double>();
+    switch (nrhs) {
+        case 1: near_apply_kernel<1><<<blocks, 128, 0, s>>>(n, rp, cl, vl, od, k.self, ie, qs, qc, psi_r); break;
+        case 2: near_apply_kernel<2><<<blocks, 128, 0, s>>>(n, rp, cl, vl, od, k.self, ie, qs, qc, psi_r); break;
+        case 3: near_apply_kernel<3><<<blocks, 128, 0, s>>>(n, rp, cl, vl, od, k.self, ie, qs, qc, psi_r); break;
+        case 4: near_apply_kernel<4><<<blocks, 128, 0, s>>>(n, rp, cl, vl, od, k.self, ie, qs, qc, psi_r); break;
+        case 5: near_apply_kernel<5><<<blocks, 128, 0, s>>>(n, rp, cl, vl, od, k.self, ie, qs, qc, psi_r); break;
+        case 6: near_apply_kernel<6><<<blocks, 128, 0, s>>>(n, rp, cl, vl, od, k.self, ie, qs, qc, psi_r); break;
+        case 7: near_apply_kernel<7><<<blocks, 128, 0, s>>>(n, rp, cl, vl, od, k.self, ie, qs, qc, psi_r); break;
+        default: near_apply_kernel<8><<<blocks, 128, 0, s>>>(n, rp, cl, vl, od, k.self, ie, qs, qc, psi_r); break;
+    }
+    IBP_CHECK_LAUNCH();
+    if (cb) compact_apply<false>(c, cb_args_free(c), n, qc, nrhs, psi_r);
 }
 
 }  // namespace ibp

@@ -190,3 +190,31 @@ def test_polarizability_driver_autotunes_and_matches_oracle(cuda_lib, tmp_path):
     for j in range(3):
         Sr = o.dipoles(p.x, p.X, p.body_offsets, qr[j], p.box)    # [bodies][3] for E0 = e_j
         assert rel_err(tensors[k][:, :, j], Sr) < MIXED_RTOL, (j, rel_err(tensors[k][:, :, j], Sr))
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_batch_free_bead_operator_matches_full_operator(cuda_lib, prec, monkeypatch):
+    """Batched configurations through the free-bead operator (each free bead carries
+    its configuration) give the solves of the operator over every bead."""
+    ib = cuda_lib
+    rng = np.random.default_rng(8)
+    parts = _configs(rng.normal(size=(2, 3)))
+    s, cfg = C.stack(parts)
+    res = {}
+    for full in (True, False):
+        if full:
+            monkeypatch.setenv("IBPME_FULL_OPERATOR", "1")
+        else:
+            monkeypatch.delenv("IBPME_FULL_OPERATOR", raising=False)
+        ctx = context(ib, s, precision=prec)
+        try:
+            status, st, q, psi, S = _batch_solve(ib, ctx, s, cfg, prec=ib.IBPME_FP64 if prec == "fp64" else -1,
+                                                 rtol=1e-10)
+            assert status == ib.IBPME_OK and all(e.rel_residual <= 1e-10 for e in st)
+            res[full] = (q, psi, S)
+        finally:
+            ib.pme_destroy(ctx)
+    monkeypatch.delenv("IBPME_FULL_OPERATOR", raising=False)
+    assert rel_err(res[False][0], res[True][0]) < 1e-8
+    assert rel_err(res[False][2], res[True][2]) < 1e-8
+    assert np.abs(res[False][1] - res[True][1]).max() < 1e-8 * max(np.abs(res[True][1]).max(), 1.0)

@@ -640,3 +640,50 @@ def test_preconditioner_skips_configurations_with_large_bodies(cuda_lib):
             lo += p.n
     finally:
         ib.pme_destroy(ctx)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_free_bead_operator_matches_full_operator(cuda_lib, prec, monkeypatch):
+    """The Krylov operator evaluates the free beads (beads of multi-bead bodies) alone:
+    their own stencils, the table's pairs between two free beads and the compact bodies.
+    Against the same solves with every bead in every evaluation (ions at zero charge):
+    bodies close enough for pairs between bodies inside r_c, ions, two fields, and the
+    oracle's dense solution; iteration counts stay within one of each other."""
+    import torch
+    ib = cuda_lib
+    s = C.small_system(seed=62, n_bodies=4, level=2, n_ions=40, L=8.0, a=0.12, mesh=(48, 48, 48), tol=1e-7, nrhs=2)
+    # pairs of beads of different multi-bead bodies inside r_c exist (the free-free table is used)
+    ctx = context(ib, s, precision=prec)
+    rc = ib.ibpme_get_params(ctx).r_cut
+    ib.pme_destroy(ctx)
+    bid = o.body_index(s.body_offsets)
+    body = np.diff(s.body_offsets)[bid] > 1
+    xb, bb = s.x[body], bid[body]
+    d = o.min_image(xb[:, None, :] - xb[None, :, :], s.box)
+    inside = (np.sqrt((d * d).sum(axis=2)) < rc) & (bb[:, None] != bb[None, :])
+    assert inside.sum() > 100
+    out = {}
+    for full in (True, False):
+        if full:
+            monkeypatch.setenv("IBPME_FULL_OPERATOR", "1")
+        else:
+            monkeypatch.delenv("IBPME_FULL_OPERATOR", raising=False)
+        ctx = context(ib, s, precision=prec)
+        try:
+            bodies = ib.Bodies(cuda(s.body_offsets.astype(np.int32)), cuda(s.X), cuda(s.Q))
+            q = torch.zeros((2, s.n), dtype=torch.float64, device="cuda")
+            psi = torch.zeros((2, s.n_bodies), dtype=torch.float64, device="cuda")
+            S = torch.zeros((2, s.n_bodies, 3), dtype=torch.float64, device="cuda")
+            status, st = ib.induced_charge_solve(ctx, s.n, cuda(s.x), bodies, cuda(s.E0), 2,
+                                                 ib.make_opts(rtol=1e-10, precond=ib.IBPME_PRECOND_NONE), q, psi, S)
+            torch.cuda.synchronize()
+            assert status == ib.IBPME_OK and st.rel_residual <= 1e-10
+            out[full] = (st.iters, q.cpu().numpy(), psi.cpu().numpy(), S.cpu().numpy())
+        finally:
+            ib.pme_destroy(ctx)
+    monkeypatch.delenv("IBPME_FULL_OPERATOR", raising=False)
+    (it_f, qf, pf, Sf), (it_s, qs, ps, Ss) = out[True], out[False]
+    assert abs(it_f - it_s) <= 1, (it_f, it_s)
+    assert rel_err(qs, qf) < 1e-8 and rel_err(Ss, Sf) < 1e-8
+    assert np.abs(ps - pf).max() < 1e-8 * max(np.abs(pf).max(), 1.0)
+    _check_solution(s, qs, ps, Ss, FP64_RTOL)
