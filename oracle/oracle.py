@@ -13,6 +13,8 @@ What it computes, each function citing the passage it follows:
   part as C diag(G) C^T + S diag(G) S^T with C = cos(K x), S = sin(K x)).
 * The saddle system of Eq. saddle, solved by dense LU (numpy.linalg.solve)
   or by textbook restarted GMRES (Saad) on the matrix-free operator.
+* The grand capacitance tensor C = Sigma' M^{-1} Sigma'^T (Eq. QS_capacitance)
+  by dense LU.
 * Dipoles (Eq. rigid_dipole), energy (Eq. pot_syst), bead forces
   (Eq. beadforce: f = q (E0 + E) with E the field of all other charges),
   body forces and torques (Sec. III.C), the Brownian-dynamics step of
@@ -377,6 +379,33 @@ def solve_gmres(x, body_offsets, X, Q, E0, box, a, eps, rtol=1e-10, restart=50, 
     return u[:n], u[n:], it, res
 
 
+def sigma_prime(x, X, body_offsets, box):
+    """Sigma' of Eq. QS_capacitance (Appendix): 4 N_b x N; rows 0..N_b-1 are Sigma,
+    row N_b + 3 i + d holds r_ij,d on the beads of body i (body-major)."""
+    x = _c(x).reshape(-1, 3)
+    n = x.shape[0]
+    off = np.asarray(body_offsets, dtype=np.int64)
+    nb = len(off) - 1
+    r = relative_positions(x, X, off, box)
+    Sp = np.zeros((4 * nb, n))
+    for i in range(nb):
+        Sp[i, off[i]:off[i + 1]] = 1.0
+        for d in range(3):
+            Sp[nb + 3 * i + d, off[i]:off[i + 1]] = r[off[i]:off[i + 1], d]
+    return Sp
+
+
+def grand_capacitance(x, X, body_offsets, box, a, eps, M=None, xi=None):
+    """Grand capacitance tensor C = Sigma' M^{-1} Sigma'^T (Sec. III.B, Eq. QS_capacitance):
+    [Q; S] = C [Psi - Psi_0; E0], with the 3 N_b field rows and columns body-major
+    (the field E0 of each body's own bead rows).  M^{-1} Sigma'^T by dense LU."""
+    x = _c(x).reshape(-1, 3)
+    if M is None:
+        M = M_dense(x, box, a, eps, xi=xi)
+    Sp = sigma_prime(x, X, body_offsets, box)
+    return Sp @ np.linalg.solve(M, Sp.T)
+
+
 # ---------------------------------------------------------------------------
 # Derived quantities: Eq. rigid_dipole, Eq. pot_syst, Eq. beadforce, Sec. III.C
 # ---------------------------------------------------------------------------
@@ -589,7 +618,8 @@ def reference_solution(x, body_offsets, X, Q, E0, box, a, eps, dense=None, xi=No
 __all__ = [
     "lib", "num_threads", "k0_term", "M_free", "phi_real", "dphi_real", "phi_self", "ewald_split",
     "potential", "wave_vectors", "M_dense", "spread_grid", "min_image", "body_index", "sigma_matrix",
-    "relative_positions", "saddle_rhs", "saddle_matrix", "solve_dense", "gmres",
+    "relative_positions", "saddle_rhs", "saddle_matrix", "solve_dense", "gmres", "sigma_prime",
+    "grand_capacitance",
     "saddle_operator", "solve_gmres", "dipoles", "energy", "bead_forces",
     "body_force_torque", "auto_params", "philox4x32_10", "normals",
     "hard_sphere_forces", "bd_step", "reference_solution",

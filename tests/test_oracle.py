@@ -599,3 +599,79 @@ def test_bd_body_noise_covariance():
     corr = cov / np.outer(d, d)
     assert np.all(np.abs(np.diag(corr) - 1) < sd)
     assert np.all(np.abs(corr - np.diag(np.diag(corr))) < 5 / math.sqrt(m))
+
+
+# ---------------------------------------------------------------------------
+# Grand capacitance tensor, Eq. QS_capacitance
+# ---------------------------------------------------------------------------
+
+def _sphere_in_box(L, a=0.1, eps=1.0, level=2):
+    x = G.icosphere(level) + L / 2
+    return C.assemble("sphere", [x], [], [], [0.0], [L] * 3, a, eps, [[0.0, 0.0, 1.0]])
+
+
+def test_grand_capacitance_reproduces_the_saddle_solution():
+    """Catches a transposed Sigma', a wrong sign or a missing r_ij: by Eq. QS_capacitance the
+    saddle solution of Eq. saddle for given Q and E0 has [Q; S] = C [Psi - Psi_0; E0] (the
+    same field on every body), and C is symmetric positive definite."""
+    s = C.small_system(seed=12, n_bodies=3, level=1, n_ions=0, L=7.0, a=0.2, charged=True)
+    Cm = o.grand_capacitance(s.x, s.X, s.body_offsets, s.box, s.a, s.eps)
+    nb = s.n_bodies
+    assert Cm.shape == (4 * nb, 4 * nb)
+    assert np.allclose(Cm, Cm.T, rtol=0, atol=1e-9 * np.abs(Cm).max())
+    assert np.linalg.eigvalsh(0.5 * (Cm + Cm.T)).min() > 0
+    rng = np.random.default_rng(3)
+    for _ in range(3):
+        E0 = rng.normal(size=3)
+        Q = rng.normal(size=nb)
+        q, psi = o.solve_dense(s.x, s.body_offsets, s.X, Q, E0, s.box, s.a, s.eps)
+        S = o.dipoles(s.x, s.X, s.body_offsets, q, s.box)
+        lhs = np.concatenate([Q, S.ravel()])
+        rhs = Cm @ np.concatenate([psi, np.tile(E0, nb)])
+        assert np.max(np.abs(lhs - rhs)) < 1e-8 * np.abs(lhs).max()
+
+
+def test_sphere_charge_capacitance_in_a_periodic_box():
+    """Catches a wrong k = 0 treatment or charge block: a charged conducting sphere in a
+    cubic box with the uniform neutralizing background of Sec. II has
+    1/C_QPsi(L) = 1/C_isolated - w/(4 pi eps L) + a_s^2/(3 eps L^3), w the simple-cubic
+    Wigner constant (its images) and the last term the background inside the sphere
+    (mean |r_i - r_j|^2 = 2 a_s^2 over its surface); differences between boxes cancel
+    the tessellation's C_isolated."""
+    w = GOLDEN["wigner_constant_simple_cubic"]["value"]
+    eps = 1.0
+    inv = {L: 1.0 / o.grand_capacitance(*(lambda s: (s.x, s.X, s.body_offsets, s.box, s.a, s.eps))(
+        _sphere_in_box(L, eps=eps)))[0, 0] for L in (6.0, 8.0, 12.0, 16.0)}
+    for L1, L2 in ((6.0, 12.0), (8.0, 16.0)):
+        want = -w / (4 * math.pi * eps) * (1 / L1 - 1 / L2) + (1 / (3 * eps)) * (1 / L1 ** 3 - 1 / L2 ** 3)
+        got = inv[L1] - inv[L2]
+        assert abs(got / want - 1) < 2e-3, (L1, L2, got, want)
+        # without the Wigner term the difference would be off by far more
+        assert abs(inv[L1] - inv[L2]) > 10 * abs((1 / (3 * eps)) * (1 / L1 ** 3 - 1 / L2 ** 3))
+
+
+def test_sphere_polarizability_in_a_cubic_lattice_is_clausius_mossotti():
+    """Catches a wrong field block or lattice sum: one sphere per cubic cell (a simple
+    cubic lattice) has the dipole response C_SE = alpha / (1 - alpha/(3 eps V)) with the
+    isolated polarizability alpha (Lorentz local field), the charge-dipole blocks vanish
+    by symmetry, and eps_eff = eps (1 + C_SE/(eps V)) is Clausius-Mossotti's
+    (1 + 2 phi)/(1 - phi) with phi = alpha/(4 pi eps) (4 pi/3)/V (Sec. IV.C at low phi)."""
+    eps = 1.3
+    caps = {}
+    for L in (6.0, 16.0):
+        s = _sphere_in_box(L, eps=eps)
+        Cm = o.grand_capacitance(s.x, s.X, s.body_offsets, s.box, s.a, s.eps)
+        assert np.abs(Cm[0, 1:]).max() < 1e-10 * Cm[0, 0]
+        d = np.diag(Cm)[1:]
+        assert np.ptp(d) < 1e-8 * d.mean()                       # isotropic
+        assert np.abs(Cm[1:, 1:] - np.diag(d)).max() < 1e-8 * d.mean()
+        caps[L] = d.mean()
+    V16, V6 = 16.0 ** 3, 6.0 ** 3
+    alpha = caps[16.0] / (1 + caps[16.0] / (3 * eps * V16))      # invert the same relation at L = 16
+    want = alpha / (1 - alpha / (3 * eps * V6))
+    assert abs(caps[6.0] / want - 1) < 1e-4, (caps[6.0], want)
+    phi = alpha / (4 * math.pi * eps) * (4 * math.pi / 3) / V6
+    eps_eff = eps * (1 + caps[6.0] / (eps * V6))
+    assert abs(eps_eff / (eps * (1 + 2 * phi) / (1 - phi)) - 1) < 1e-4
+    # the lattice raises the dipole above the isolated sphere's by the factor 1/(1 - phi)
+    assert caps[6.0] > alpha * (1 + 0.9 * phi)
