@@ -21,7 +21,9 @@ kernel launches.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
                        [--workload lattice|charged-sphere|polarizability|trajectory]
-For N > 1 launch with torchrun; every rank runs its own replica (weak scaling).
+For N > 1 launch with torchrun: the lattice, charged-sphere and trajectory workloads run one
+independent replica per rank (weak scaling); the polarizability batch is split across
+the ranks (strong scaling).
 --workload charged-sphere times the 2,692-bead charged sphere alone;
 --workload polarizability times the batched solve of 64 independent
 configurations (three fields each) on the autotuned mesh; --workload
@@ -649,32 +651,36 @@ def bench_polarizability(args, ib, torch, rank, world, local):
     from paper_2401_04865_gb300 import batch as B
     from workloads import configs as C
     torch.cuda.set_device(local)
-    systems = C.config4_batch(n_configs=args.configs, seed=1003 + 7919 * rank, common_radius=True)
+    batch = C.config4_batch(n_configs=args.configs, seed=1003, common_radius=True)
+    # one batch for the whole job: each rank solves its longest-processing-time share
+    plan = B.shard_lpt([B.cost_model(s.n) for s in batch], world)
+    mine = plan[rank]
+    systems = [batch[i] for i in mine]
     a, eps, tol = systems[0].a, systems[0].eps, 1e-6
     tuner = B.Autotuner(cache_path=os.path.join(_tf.mkdtemp(), "tune.json"), candidates=(96, 128, 160))
-    plan = []
+    plan_buckets = []
     for idx in B.buckets([s.n for s in systems], ratio=args.bucket_ratio, max_channels=192, nrhs=3,
                          classes=[B.preconditioned(s) for s in systems]):
         bucket = B.Bucket(ib, [systems[i] for i in idx], np.eye(3))
         mesh, report = tuner.tune(ib, bucket, tol, a, eps, ib.IBPME_MIXED)
         ctx = B.context_for(ib, systems[0].box, mesh, tol, a, eps, ib.IBPME_MIXED, 3)
-        plan.append({"idx": idx, "bucket": bucket, "ctx": ctx, "mesh": mesh, "report": report})
+        plan_buckets.append({"idx": idx, "bucket": bucket, "ctx": ctx, "mesh": mesh, "report": report})
     opts = ib.make_opts(rtol=1e-6)
     stream = torch.cuda.current_stream()
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
     # every step solves the batch at new positions (each configuration shifted
     # rigidly), so the cells, pair tables and stencils are built inside the step
     rng = np.random.default_rng(2024 + rank)
-    positions = [[p["bucket"].shifted_positions(rng) for p in plan] for _ in range(args.warmup + args.steps)]
+    positions = [[p["bucket"].shifted_positions(rng) for p in plan_buckets] for _ in range(args.warmup + args.steps)]
 
     def step(k):
-        for p, (x, X) in zip(plan, positions[k]):
+        for p, (x, X) in zip(plan_buckets, positions[k]):
             p["bucket"].load_positions(x, X)
         flush.zero_()
 
     def solve_all():
         out = []
-        for p in plan:
+        for p in plan_buckets:
             status, st = p["bucket"].solve(p["ctx"], opts)
             if status != ib.IBPME_OK:
                 raise RuntimeError("batched solve did not converge")
@@ -706,10 +712,23 @@ def bench_polarizability(args, ib, torch, rank, world, local):
         t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
         total_ms = float(t.item())
-    value = world * len(systems) * args.steps / (total_ms / 1e3)
+    value = len(batch) * args.steps / (total_ms / 1e3)
+    # the last step's tensors of every configuration, gathered on rank 0 in batch order
+    # (host objects, after the timed region)
+    mine_tensors = {}
+    for p in plan_buckets:
+        S = p["bucket"].S.cpu().numpy()
+        for k, i in enumerate(p["idx"]):
+            lo, hi = p["bucket"].cfg[k], p["bucket"].cfg[k + 1]
+            mine_tensors[mine[i]] = np.transpose(S[:, lo:hi, :], (1, 2, 0))
+    gathered = [mine_tensors]
+    if world > 1:
+        gathered = [None] * world if rank == 0 else None
+        torch.distributed.gather_object(mine_tensors, gathered, dst=0)
+    n_gathered = sum(len(g) for g in gathered) if rank == 0 else None
     # the same configurations one call each (context of their bucket), each at
     # new positions, timed the same way
-    where = {i: p for p in plan for i in p["idx"]}
+    where = {i: p for p in plan_buckets for i in p["idx"]}
     t_seq = 0.0
     for i in range(len(systems)):
         one = B.Bucket(ib, [systems[i]], np.eye(3))
@@ -725,23 +744,26 @@ def bench_polarizability(args, ib, torch, rank, world, local):
         if status != ib.IBPME_OK:
             raise RuntimeError("single-configuration solve did not converge")
         t_seq += e0.elapsed_time(e1) / 1e3
-    for p in plan:
+    for p in plan_buckets:
         ib.pme_destroy(p["ctx"])
     n_beads = int(sum(s.n for s in systems))
     return {
         "metric": "polarizability configurations/s (batched induced-charge solves, 3 fields each)",
         "value": value, "unit": "configurations/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "strong", "vs_baseline": None,
         "dtype": "f32 mesh / f64 krylov", "data": "synthetic",
         "config": {"workload": POL_WORKLOAD if args.configs == 64 else
                    f"{args.configs}-configuration prefix of: {POL_WORKLOAD}", "n_configs": args.configs,
-                   "n_beads": n_beads,
+                   "n_beads": int(sum(s.n for s in batch)),
                    "l2": "inputs larger than L2; 256 MB flush before every step, outside its events",
-                   "parallelism": f"replicas x{world} (independent batches, no collective)",
+                   "parallelism": f"one batch over {world} rank(s): longest-processing-time shares, tensors "
+                                  f"gathered on rank 0 over the host (no device collective)",
                    "bucket_ratio": args.bucket_ratio},
         "buckets": [{"configs": len(p["idx"]), "beads": p["bucket"].n, "mesh": p["mesh"],
                      "preconditioned": bool(B.preconditioned(systems[p["idx"][0]])),
-                     "iters": stats[-1][k][0].iters, "autotune": p["report"]} for k, p in enumerate(plan)],
+                     "iters": stats[-1][k][0].iters, "autotune": p["report"]} for k, p in enumerate(plan_buckets)],
+        "gathered_configurations": n_gathered,
+        "rank_share": {"configurations": len(systems), "beads": n_beads},
         "one_call_per_configuration": {"value": len(systems) / t_seq, "unit": "configurations/s",
                                        "sample": len(systems),
                                        "note": "every configuration of the batch solved one call each, at new "

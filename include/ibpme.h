@@ -233,6 +233,28 @@ typedef struct {
     long long step;               /* step counter (part of the Philox counter) */
 } ibpme_bd_params;
 
+/* Grand capacitance tensor of Sec. III.B, Eq. QS_capacitance:
+ *     [Q; S] = C [Psi - Psi_0; E0],   C = Sigma' M^{-1} Sigma'^T,
+ * for the bodies at x, with E0 the field of each body's own bead rows.  C is
+ * 4 N_b x 4 N_b, rows and columns ordered [Q_1 .. Q_Nb, S_1x, S_1y, S_1z, S_2x, ...]
+ * (body-major dipole rows).  Column k holds the body charges and dipoles of the
+ * charges q = M^{-1} psi_k, where psi_k (column k of Sigma'^T) is 1 on the beads of
+ * body k (k < N_b) or r_ij,d on the beads of body i (k = N_b + 3 i + d) and 0
+ * elsewhere; the 4 N_b systems M q = psi_k are solved by the Krylov solver of
+ * induced_charge_solve (options as there: rtol on ||psi_k - M q|| / ||psi_k||,
+ * precision, body-block preconditioner) in groups of at most max_rhs right-hand
+ * sides, from the zero guess.  C is symmetric positive definite up to the
+ * tolerance.  With one sphere per periodic cell, C_SE / (eps_f V) gives the
+ * lattice's effective permittivity eps_eff / eps_f - 1 (Sec. IV.C).
+ *   bodies   every body needs two beads or more (IBPME_ERR_ARG otherwise: single
+ *            beads are not conductors here); bodies->Q is not used and may be NULL
+ *   opts     NULL = defaults; guess must be IBPME_GUESS_ZERO
+ *   C_out    [4 N_b][4 N_b] row-major, device or host
+ *   stats    the worst residual and most iterations over the groups, or NULL
+ * Returns IBPME_ERR_NOT_CONVERGED (C written) if a group misses rtol. */
+ibpme_status ibpme_capacitance(ibpme_ctx* ctx, int n, const double* x, const ibpme_bodies* bodies,
+                               const ibpme_solve_opts* opts, double* C_out, ibpme_solve_stats* stats);
+
 /* One Euler-Maruyama step (Eq. forward) with free-draining mobility M^H = I/gamma.
  * The bead forces f_bead [n][3] are augmented by the Heyes-Melrose hard-sphere
  * pair forces of Eq. hardsphereFD (beads of different bodies closer than 2a).

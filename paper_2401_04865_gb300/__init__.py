@@ -89,6 +89,8 @@ SIGNATURES = {
                               ctypes.POINTER(ibpme_bd_params), _p, _p, _p, _p, _p, _p, _p, _p,
                               ctypes.POINTER(ibpme_solve_stats)]),
     "pme_spread_noalloc": (_i, [ctypes.POINTER(ibpme_params), _i, _p, _p, _i, _p, _p]),
+    "ibpme_capacitance": (_i, [_p, _i, _p, ctypes.POINTER(ibpme_bodies), ctypes.POINTER(ibpme_solve_opts), _p,
+                               ctypes.POINTER(ibpme_solve_stats)]),
     "ibpme_mlp_create": (_i, [ctypes.POINTER(_p), ctypes.c_ulonglong]),
     "ibpme_mlp_destroy": (_i, [_p]),
     "ibpme_mlp_get": (_i, [_p, _p]),
@@ -345,6 +347,17 @@ def ibpme_bd_advance(ctx, n, x, bodies: Bodies, E0, opts: ibpme_solve_opts | Non
                                      ptr(psi_out), ptr(f_bead), ptr(F), ptr(L), ptr(U), ptr(x_out), ptr(X_out),
                                      ctypes.byref(st))
     _check(status, "ibpme_bd_advance", ok=(IBPME_OK, IBPME_ERR_NOT_CONVERGED))
+    return status, st
+
+
+def ibpme_capacitance(ctx, n, x, bodies: Bodies, C_out, opts: ibpme_solve_opts | None = None):
+    """Grand capacitance tensor C [4 N_b][4 N_b] into C_out.  Returns (status, stats);
+    raises on any status other than OK / NOT_CONVERGED."""
+    st = ibpme_solve_stats()
+    status = load().ibpme_capacitance(ctx, int(n), ptr(x), ctypes.byref(bodies.c),
+                                      ctypes.byref(opts) if opts is not None else None, ptr(C_out),
+                                      ctypes.byref(st))
+    _check(status, "ibpme_capacitance", ok=(IBPME_OK, IBPME_ERR_NOT_CONVERGED))
     return status, st
 
 

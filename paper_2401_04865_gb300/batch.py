@@ -281,6 +281,26 @@ def polarizability(ib, systems, precision=None, rtol=1e-6, tol=1e-6, tuner: Auto
     return out, report
 
 
+def polarizability_sharded(ib, systems, group=None, solve=None, **kw):
+    """Polarizability tensors of one batch split across the ranks of a
+    torch.distributed group: configurations are assigned longest processing time
+    first on cost_model (shard_lpt), every rank solves its share with
+    polarizability(ib, share, **kw) (bucketed and autotuned on its own GPU), and the
+    tensors are gathered on rank 0 in configuration order over the host (no device
+    collective).  solve(share) -> (tensors, report) replaces that call (tests).
+    Returns (tensors, this rank's bucket report) on rank 0, (None, report) elsewhere."""
+    solve = solve or (lambda part: polarizability(ib, part, **kw))
+    report = []
+
+    def solve_share(part):
+        out, rep = solve(part)
+        report.extend(rep)
+        return out
+
+    tensors = run_sharded(systems, [cost_model(s.n) for s in systems], solve_share, group=group)
+    return tensors, report
+
+
 def run_sharded(items, costs, solve_fn, group=None):
     """Solve independent items on every rank of a torch.distributed group and
     gather the results on rank 0 (host objects; no device collective).

@@ -852,3 +852,143 @@ IBP_API ibpme_status ibpme_bd_step(ibpme_ctx* c, int n, const double* x, const i
         return IBPME_OK;
     });
 }
+
+// ---------------------------------------------------------------------------
+// Grand capacitance tensor (Sec. III.B, Eq. QS_capacitance)
+// ---------------------------------------------------------------------------
+namespace ibp {
+namespace {
+
+// Column k0 + r of Sigma'^T as bead potentials (r < R): column k < nb puts 1 on the
+// beads of body k, column nb + 3 i + d puts r_ij,d on the beads of body i.
+__global__ void cap_rhs_kernel(int n, int R, int k0, int nb, const int* __restrict__ bead_body,
+                               const double* __restrict__ rel, double* __restrict__ psi) {
+    const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (t >= (long long)n * R) return;
+    const int r = (int)(t / n), j = (int)(t % n);
+    const int k = k0 + r, b = bead_body[j];
+    double v = 0.0;
+    if (k < nb) {
+        v = b == k ? 1.0 : 0.0;
+    } else {
+        const int i = (k - nb) / 3, d = (k - nb) % 3;
+        v = b == i ? rel[3 * j + d] : 0.0;
+    }
+    psi[t] = v;
+}
+
+// Rows of C for columns k0 .. k0 + R - 1: C[i][k] = sum over body i of q, C[nb + 3 i + d][k] =
+// sum over body i of r_d q (Sigma' q).  One block per (column, body).
+__global__ void cap_columns_kernel(int n, int nb, int R, int k0, const int* __restrict__ off,
+                                   const double* __restrict__ rel, const double* __restrict__ q,
+                                   double* __restrict__ C) {
+    __shared__ double sh[4][32];
+    const int r = blockIdx.y, i = blockIdx.x;
+    double v[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int j = off[i] + threadIdx.x; j < off[i + 1]; j += blockDim.x) {
+        const double qj = q[(size_t)r * n + j];
+        v[0] += qj;
+        v[1] += rel[3 * j] * qj;
+        v[2] += rel[3 * j + 1] * qj;
+        v[3] += rel[3 * j + 2] * qj;
+    }
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+        v[c] = warp_sum(v[c]);
+        if (lane == 0) sh[c][w] = v[c];
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const long long ld = 4LL * nb, k = k0 + r;
+        double tot[4] = {0.0, 0.0, 0.0, 0.0};
+        for (int u = 0; u < (int)(blockDim.x >> 5); ++u)
+            for (int c = 0; c < 4; ++c) tot[c] += sh[c][u];
+        C[(size_t)i * ld + k] = tot[0];
+        for (int d = 0; d < 3; ++d) C[(size_t)(nb + 3 * i + d) * ld + k] = tot[1 + d];
+    }
+}
+
+}  // namespace
+}  // namespace ibp
+
+IBP_API ibpme_status ibpme_capacitance(ibpme_ctx* c, int n, const double* x, const ibpme_bodies* bodies,
+                                       const ibpme_solve_opts* opts, double* C_out, ibpme_solve_stats* stats) {
+    return guard([&]() -> ibpme_status {
+        if (!c) fail(IBPME_ERR_ARG, "ctx is NULL");
+        DeviceScope ds(c->device);
+        const auto t0 = std::chrono::steady_clock::now();
+        check_n(n);
+        if (n == 0) fail(IBPME_ERR_ARG, "the capacitance needs at least one body");
+        if (!x || !bodies || !C_out) fail(IBPME_ERR_ARG, "x, bodies and C_out are required");
+        const int nb = bodies->n_bodies;
+        if (nb < 1) fail(IBPME_ERR_ARG, "n_bodies must be >= 1");
+        ibpme_solve_opts o{};
+        o.precision = -1;
+        if (opts) o = *opts;
+        if (o.guess != IBPME_GUESS_ZERO) fail(IBPME_ERR_ARG, "the capacitance solves start from the zero guess");
+        if (o.precond != IBPME_PRECOND_BODY && o.precond != IBPME_PRECOND_NONE) fail(IBPME_ERR_ARG, "unknown precond");
+        SolveArgs a{};
+        a.n = n;
+        a.prec = o.precision < 0 ? c->p.precision : o.precision;
+        if (a.prec != IBPME_FP64 && a.prec != IBPME_MIXED) fail(IBPME_ERR_ARG, "unknown solve precision");
+        if (a.prec == IBPME_MIXED && !c->have32) fail(IBPME_ERR_ARG, "mixed solve needs a mixed context");
+        a.rtol = o.rtol > 0 ? o.rtol : 1e-6;
+        a.restart = o.restart > 0 ? o.restart : 50;
+        if (a.restart > 128) fail(IBPME_ERR_ARG, "restart must be <= 128");
+        a.max_iter = o.max_iter > 0 ? o.max_iter : 3000;
+        a.precond = o.precond == IBPME_PRECOND_BODY;
+        const double* dx = static_cast<const double*>(stage_in(c, x, sizeof(double) * 3 * n, c->st_x));
+        double* xw = static_cast<double*>(c->xw.ensure(sizeof(double) * 3 * n));
+        wrap_positions(c, n, dx, xw);
+        a.xw = xw;
+        // the net charges play no part (the body potentials are given): zeros where none are passed
+        const int R = std::min(c->p.max_rhs, 4 * nb);
+        double* zero = static_cast<double*>(c->cap_zero.ensure(sizeof(double) * (size_t)std::max(nb, 3 * R)));
+        IBP_CUDA(cudaMemsetAsync(zero, 0, sizeof(double) * (size_t)std::max(nb, 3 * R), c->stream));
+        ibpme_bodies b = *bodies;
+        if (!b.Q) b.Q = zero;
+        prepare_bodies(c, n, &b, xw);
+        if (c->bodies.nmb != nb)
+            fail(IBPME_ERR_ARG, "every body needs two beads or more (single-bead bodies are not conductors here)");
+        a.E0 = zero;
+        OutArg oc = stage_out(c, C_out, sizeof(double) * 16 * (size_t)nb * nb, c->st_out1);
+        double* psi = static_cast<double*>(c->cap_psi.ensure(sizeof(double) * (size_t)R * n));
+        double* q = static_cast<double*>(c->cap_q.ensure(sizeof(double) * (size_t)R * n));
+        ibpme_solve_stats agg{};
+        agg.outer = 0;
+        for (int k0 = 0; k0 < 4 * nb; k0 += R) {
+            const int r = std::min(R, 4 * nb - k0);
+            cap_rhs_kernel<<<div_up((long long)n * r, 256), 256, 0, c->stream>>>(n, r, k0, nb,
+                                                                              c->bodies.bead_body.as<int>(),
+                                                                              c->bodies.rel.as<double>(), psi);
+            IBP_CHECK_LAUNCH();
+            a.nrhs = r;
+            a.q = q;
+            a.psi = nullptr;
+            a.bead_psi = psi;
+            ibpme_solve_stats st{};
+            solve(c, a, &st);
+            cap_columns_kernel<<<dim3(nb, r), 256, 0, c->stream>>>(n, nb, r, k0, c->bodies.off.as<int>(),
+                                                                  c->bodies.rel.as<double>(), q,
+                                                                  static_cast<double*>(oc.dev));
+            IBP_CHECK_LAUNCH();
+            agg.iters = std::max(agg.iters, st.iters);
+            agg.outer = std::max(agg.outer, st.outer);
+            agg.matvecs_fp64 += st.matvecs_fp64;
+            agg.rel_residual = std::isfinite(st.rel_residual) && std::isfinite(agg.rel_residual)
+                                   ? std::max(agg.rel_residual, st.rel_residual) : NAN;
+            agg.init_rel_residual = std::max(agg.init_rel_residual, st.init_rel_residual);
+        }
+        finish_out(c, oc);
+        IBP_CUDA(cudaStreamSynchronize(c->stream));
+        agg.time_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+        if (stats) *stats = agg;
+        if (!std::isfinite(agg.rel_residual)) fail(IBPME_ERR_NONFINITE, "non-finite residual in the solve");
+        if (!(agg.rel_residual <= a.rtol)) {
+            set_error("not converged: relative residual %.3e after %d iterations", agg.rel_residual, agg.iters);
+            return IBPME_ERR_NOT_CONVERGED;
+        }
+        return IBPME_OK;
+    });
+}

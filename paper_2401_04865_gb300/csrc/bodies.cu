@@ -229,6 +229,34 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k) {
 // bead order[t].
 // Pairs are screened with the FP32 positions (a margin far above their rounding);
 // the few that may overlap are decided in FP64.
+// The same forces from the table's list of overlapping pairs (r < 2a, listed when the
+// pair values were built), one thread per ordered pair adding the force on its row bead
+// (the table holds both orders of a pair); f_out starts as a copy of f_bead.  A walk of
+// every pair of the table to find the few overlapping ones was the cost of this pass.
+__global__ void hard_sphere_list_kernel(const int* __restrict__ ov_count, const int* __restrict__ ov_list,
+                                        const double* __restrict__ xw, double L0, double L1, double L2,
+                                        const int* __restrict__ prow, const int* __restrict__ col,
+                                        const int* __restrict__ order, const int* __restrict__ bead_body, double a,
+                                        double coef, double* __restrict__ f_out) {
+    const int m = *ov_count;
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < m; t += gridDim.x * blockDim.x) {
+        const long long p = ov_list[t];
+        const int al = order[prow[p]], be = order[col[p]];
+        if (bead_body[al] == bead_body[be]) continue;
+        const double dx = min_image_wrapped(xw[3 * al] - xw[3 * be], L0);
+        const double dy = min_image_wrapped(xw[3 * al + 1] - xw[3 * be + 1], L1);
+        const double dz = min_image_wrapped(xw[3 * al + 2] - xw[3 * be + 2], L2);
+        const double r2 = dx * dx + dy * dy + dz * dz;
+        if (r2 < 4.0 * a * a && r2 > 0.0) {
+            const double r = sqrt(r2);
+            const double mag = coef * (2.0 * a - r) / r;
+            atomicAdd(f_out + 3 * al, mag * dx);
+            atomicAdd(f_out + 3 * al + 1, mag * dy);
+            atomicAdd(f_out + 3 * al + 2, mag * dz);
+        }
+    }
+}
+
 __global__ void hard_sphere_kernel(int n, const double* __restrict__ xw, const float4* __restrict__ xf, double L0,
                                    double L1, double L2, const long long* __restrict__ rowptr,
                                    const int* __restrict__ col, const int* __restrict__ order,
@@ -578,9 +606,17 @@ void bd_step(ibpme_ctx* c, int n, const double* xw, const double* f, const ibpme
     ProfScope ps(ST_BODIES, s);
     double* ftot = static_cast<double*>(bd.scratch.ensure(sizeof(double) * (3 * (size_t)n + 9 * (size_t)bd.nb)));
     double* Rm = ftot + 3 * (size_t)n;
-    hard_sphere_kernel<<<div_up((long long)n * 32, 128), 128, 0, s>>>(
-        n, xw, nl.xf.as<float4>(), c->p.box[0], c->p.box[1], c->p.box[2], nl.rowptr.as<long long>(), nl.col.as<int>(),
-        nl.cell_beads.as<int>(), bd.bead_body.as<int>(), c->a, p->gamma / (2.0 * p->dt), f, ftot);
+    if (nl.ov_valid) {
+        IBP_CUDA(cudaMemcpyAsync(ftot, f, sizeof(double) * 3 * (size_t)n, cudaMemcpyDeviceToDevice, s));
+        hard_sphere_list_kernel<<<152 * 4, 128, 0, s>>>(nl.ov_count.as<int>(), nl.ov_list.as<int>(), xw, c->p.box[0],
+                                                        c->p.box[1], c->p.box[2], nl.prow.as<int>(), nl.col.as<int>(),
+                                                        nl.cell_beads.as<int>(), bd.bead_body.as<int>(), c->a,
+                                                        p->gamma / (2.0 * p->dt), ftot);
+    } else {
+        hard_sphere_kernel<<<div_up((long long)n * 32, 128), 128, 0, s>>>(
+            n, xw, nl.xf.as<float4>(), c->p.box[0], c->p.box[1], c->p.box[2], nl.rowptr.as<long long>(),
+            nl.col.as<int>(), nl.cell_beads.as<int>(), bd.bead_body.as<int>(), c->a, p->gamma / (2.0 * p->dt), f, ftot);
+    }
     IBP_CHECK_LAUNCH();
     BdConst bc{p->dt, p->gamma, p->kT, p->seed, (unsigned)(p->step & 0xffffffffLL)};
     bd_body_kernel<<<body_grid(bd.nb, bd.nmb), kBodyThreads, 0, s>>>(bd.nb, bd.nmb, bd.mb_body.as<int>(),

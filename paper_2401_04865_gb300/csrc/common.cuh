@@ -133,6 +133,8 @@ struct StencilCache {
     DevBuf frac;                 // double4 per bead: (first node - x / h) per axis
     DevBuf frac32;               // float4 per bead: the same offsets in FP32 (FP32 kernels)
     DevBuf w64;                  // FP64 window weights [n][3][P] (GB300's FP64 exp is slow: once per positions)
+    DevBuf wdf;                  // the same windows as hi + lo floats [n][3][P] (double-float gathers)
+    DevBuf frac_df;              // float4 pairs per bead: the offsets of frac as hi + lo floats
     // Tile bins for spreading and gathering through shared memory (many beads
     // only): beads sorted by (configuration, tile of kTileNodes^3 nodes holding
     // their first stencil node).
@@ -194,6 +196,10 @@ struct NearList {
     DevBuf qs;                     // charges [n][nrhs] in the sorted order for the FP64 pass
     DevBuf scan_tmp, flag;
     DevBuf xf;                     // FP32 positions (x, y, z, 0) for the candidate filter
+    DevBuf xdf;                    // positions as hi, lo float4 pairs per bead (double-float pair values)
+    DevBuf ov_list;                // pairs of overlapping beads (r < 2a), valued exactly in FP64
+    DevBuf ov_count;
+    bool ov_valid = false;         // ov_list holds every overlapping pair of the current table
     DevBuf table;                  // tabulated pair kernel (phi, phi', phi'') on [2a, r_c]
     DevBuf fp_dev;                 // fingerprint of the positions + non-finite flag
     unsigned long long fp = 0;     // fingerprint of the positions the table was built for
@@ -394,6 +400,7 @@ struct ibpme_ctx {
     cudaEvent_t ev_in = nullptr, ev_out = nullptr;
     ibp::StencilCache stencils;               // stencils of the current positions
     ibp::FreeSet fs;                          // the free beads on their own (Krylov operator)
+    ibp::DevBuf cap_psi, cap_q, cap_zero;     // grand capacitance: bead potentials, charges, zeros
     ibp::Precond pre;                         // body-block preconditioner
     cudaStream_t aux = nullptr;               // second branch of a PME evaluation (near field)
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
@@ -486,6 +493,11 @@ struct SolveArgs {
     double rtol;
     int restart, max_iter;
     bool precond;       // body-block right preconditioner
+    // Prescribed bead potentials [nrhs][n] (device), or NULL for Eq. saddle.  Given,
+    // the solve finds the charges of M q = bead_psi instead: the body potentials are
+    // no unknowns (their rows become the identity with zero right-hand side), every
+    // body must have two beads or more, and E0, Q and psi are not used.
+    const double* bead_psi = nullptr;
 };
 void solve(ibpme_ctx* c, const SolveArgs& a, ibpme_solve_stats* st);
 // FP64 potentials [nrhs][n] of the last solve's final residual evaluation (its FP64
@@ -493,7 +505,9 @@ void solve(ibpme_ctx* c, const SolveArgs& a, ibpme_solve_stats* st);
 const double* solve_potentials(ibpme_ctx* c);
 // precond.cu
 bool precond_prepare(ibpme_ctx* c);   // false: no body qualifies
-void precond_apply(ibpme_ctx* c, int R, const double* u, long long ustride, const int* jdev, int nk, double* out);
+// dir: the block [-M_b 0; 0 1] of the prescribed-potential problem (SolveArgs::bead_psi)
+void precond_apply(ibpme_ctx* c, int R, const double* u, long long ustride, const int* jdev, int nk, double* out,
+                   bool dir = false);
 void krylov_destroy(ibpme_ctx* c);
 
 // small device helpers

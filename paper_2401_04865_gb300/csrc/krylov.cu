@@ -456,7 +456,8 @@ __global__ void assemble_kernel(int nfree, int nmb, int nk, long long ustride, i
                                 const int* __restrict__ bead_body, const int* __restrict__ body_unk,
                                 const int* __restrict__ mb_unk, const int* __restrict__ mb_first,
                                 const int* __restrict__ mb_cnt, const double* __restrict__ psi, bool list,
-                                const double* __restrict__ u, const int* __restrict__ jdev, double* __restrict__ y) {
+                                bool dir, const double* __restrict__ u, const int* __restrict__ jdev,
+                                double* __restrict__ y) {
     __shared__ double sh[32];
     if (jdev) u += (size_t)(*jdev) * nk;
     if ((int)blockIdx.x < bead_blocks) {
@@ -465,12 +466,16 @@ __global__ void assemble_kernel(int nfree, int nmb, int nk, long long ustride, i
         const int r = (int)(t / nfree), i = (int)(t % nfree);
         const int j = free_idx[i];
         const double p = list ? psi[t] : psi[(size_t)r * n + j];
-        y[(size_t)r * nk + free_unk[i]] = -p + u[(size_t)r * ustride + body_unk[bead_body[j]]];
+        y[(size_t)r * nk + free_unk[i]] = -p + (dir ? 0.0 : u[(size_t)r * ustride + body_unk[bead_body[j]]]);
         return;
     }
     const int wid = blockIdx.x - bead_blocks;
     if (wid >= nmb * R) return;   // the one block of an empty launch
     const int r = wid / nmb, b = wid % nmb;
+    if (dir) {   // prescribed potentials: the body rows are the identity
+        if (threadIdx.x == 0) y[(size_t)r * nk + mb_unk[b]] = u[(size_t)r * ustride + mb_unk[b]];
+        return;
+    }
     double acc = 0.0;
     for (int i = threadIdx.x; i < mb_cnt[b]; i += blockDim.x) acc += u[(size_t)r * ustride + mb_first[b] + i];
     acc = block_sum(acc, sh);
@@ -516,14 +521,20 @@ __global__ void residual_kernel(int nfree, int nmb, int nk, int n, int R, int be
                                 const int* __restrict__ mb_body, const int* __restrict__ mb_unk,
                                 const int* __restrict__ mb_first, const int* __restrict__ mb_cnt,
                                 const double* __restrict__ rel, const double* __restrict__ E0,
-                                const double* __restrict__ Q, const double* __restrict__ psi,
-                                const double* __restrict__ x, double* __restrict__ res) {
+                                const double* __restrict__ bead_psi, const double* __restrict__ Q,
+                                const double* __restrict__ psi, const double* __restrict__ x,
+                                double* __restrict__ res) {
     __shared__ double sh[32];
+    const bool dir = bead_psi != nullptr;
     if ((int)blockIdx.x < bead_blocks) {
         const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
         if (t >= (long long)nfree * R) return;
         const int r = (int)(t / nfree), i = (int)(t % nfree);
         const int j = free_idx[i];
+        if (dir) {   // M q = bead_psi: r_bead = -bead_psi + (M q)_bead
+            res[(size_t)r * nk + free_unk[i]] = -bead_psi[(size_t)r * n + j] + psi[(size_t)r * n + j];
+            return;
+        }
         const double* e = E0 + 3 * r;
         const double rE = rel[3 * j] * e[0] + rel[3 * j + 1] * e[1] + rel[3 * j + 2] * e[2];
         res[(size_t)r * nk + free_unk[i]] = -rE + psi[(size_t)r * n + j] - x[(size_t)r * nk + body_unk[bead_body[j]]];
@@ -532,6 +543,10 @@ __global__ void residual_kernel(int nfree, int nmb, int nk, int n, int R, int be
     const int wid = blockIdx.x - bead_blocks;
     if (wid >= nmb * R) return;   // the one block of an empty launch
     const int r = wid / nmb, b = wid % nmb;
+    if (dir) {
+        if (threadIdx.x == 0) res[(size_t)r * nk + mb_unk[b]] = -x[(size_t)r * nk + mb_unk[b]];
+        return;
+    }
     double acc = 0.0;
     for (int i = threadIdx.x; i < mb_cnt[b]; i += blockDim.x) acc += x[(size_t)r * nk + mb_first[b] + i];
     acc = block_sum(acc, sh);
@@ -540,9 +555,11 @@ __global__ void residual_kernel(int nfree, int nmb, int nk, int n, int R, int be
 
 // |b_s|^2 = sum over the configuration's beads of (r.E0_r)^2 + sum over its bodies of Q^2
 // (Eq. saddle right-hand side), grid: chunks x S
-__global__ void bfull_kernel(int R, const int* __restrict__ cfg_beads, const int* __restrict__ cfg_bodies,
+// (with bead_psi, the prescribed-potential problem: sum of bead_psi^2 over the beads)
+__global__ void bfull_kernel(int R, int n, const int* __restrict__ cfg_beads, const int* __restrict__ cfg_bodies,
                              const double* __restrict__ rel, const double* __restrict__ E0,
-                             const double* __restrict__ Q, double* __restrict__ norms) {
+                             const double* __restrict__ bead_psi, const double* __restrict__ Q,
+                             double* __restrict__ norms) {
     __shared__ double sh[32];
     const int s = blockIdx.y;
     const int r = s % R, cfg = s / R;
@@ -554,9 +571,10 @@ __global__ void bfull_kernel(int R, const int* __restrict__ cfg_beads, const int
     for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < len; t += (long long)gridDim.x * blockDim.x) {
         if (t < nb1 - nb0) {
             const long long j = nb0 + t;
-            const double v = rel[3 * j] * e[0] + rel[3 * j + 1] * e[1] + rel[3 * j + 2] * e[2];
+            const double v = bead_psi ? bead_psi[(size_t)r * n + j]
+                                      : rel[3 * j] * e[0] + rel[3 * j + 1] * e[1] + rel[3 * j + 2] * e[2];
             acc += v * v;
-        } else {
+        } else if (!bead_psi) {
             const double v = Q[q0 + t - (nb1 - nb0)];
             acc += v * v;
         }
@@ -611,6 +629,7 @@ struct Solver {
     int iters = 0, matvec64 = 0;
     bool pre_on = false;         // body-block preconditioner active for this solve
     bool use_free = false;       // the Krylov operator evaluates the free beads alone
+    bool dir = false;            // prescribed bead potentials (M q = a.bead_psi), not Eq. saddle
     std::vector<double> bnorm;   // |b| per system
     bool want_b = false;         // the next norms() call also fetches |b|
 
@@ -624,6 +643,7 @@ struct Solver {
         nb = c->bodies.nb;
         nk = c->bodies.nk;
         m = a.restart;
+        dir = a.bead_psi != nullptr;
     }
 
     cudaStream_t s() const { return c->stream; }
@@ -667,7 +687,7 @@ struct Solver {
         const BodyData& bd = c->bodies;
         if (ustride < 0) ustride = nk;
         if (pre && pre_on) {
-            precond_apply(c, R, u, ustride, jdev, nk, D(k->pu));
+            precond_apply(c, R, u, ustride, jdev, nk, D(k->pu), dir);
             u = D(k->pu);
             ustride = nk;
             jdev = nullptr;
@@ -692,7 +712,7 @@ struct Solver {
         assemble_kernel<<<std::max(1, bb + nmb * R), 256, 0, s()>>>(nfree, nmb, nk, ustride, n, R, bb, I(bd.free_idx),
                                                            I(bd.free_unk), I(bd.bead_body), I(bd.body_unk),
                                                            I(bd.mb_unk), I(bd.mb_first), I(bd.mb_cnt), psi_op,
-                                                           use_free, u, jdev, y);
+                                                           use_free, dir, u, jdev, y);
         IBP_CHECK_LAUNCH();
     }
 
@@ -757,7 +777,7 @@ struct Solver {
         stencil_cache(c, n, a.xw);
         pme_reserve(c, n, R, false);
         auto P = [](const void* p) { return (long long)(size_t)p; };
-        std::vector<long long> sig = {prec, R, S, ncfg, nk, n, m, nfree, nmb, (long long)prof_mask(),
+        std::vector<long long> sig = {prec, R, S, ncfg, nk, n, m, nfree, nmb, (long long)prof_mask(), (long long)dir,
                                       P(k->V.p), P(k->w.p), P(k->qop.p), P(k->psi.p), P(k->H.p), P(k->scal.p),
                                       P(c->psi_r.p), P(c->psi_k.p), P(c->scalars.p), P(c->near.col.p),
                                       P(c->near.val.p), P(c->near.pair32.p), P(c->near.qf.p), P(c->near.qs.p), P(c->near.cell_beads.p), P(c->near.rowptr.p), P(a.xw), P(bd.free_idx.p),
@@ -887,7 +907,7 @@ struct Solver {
             if (prec == IBPME_FP64) ++matvec64;
             c->grid64_final = prec == IBPME_FP64;
         }
-        if (fit_psi && nmb > 0) {
+        if (fit_psi && nmb > 0 && !dir) {
             fit_psi_kernel<<<blocks_for(32LL * nmb * R), 256, 0, s()>>>(nmb, nk, n, R, I(bd.mb_body), I(bd.mb_unk),
                                                                         I(bd.off), bd.rel.as<double>(), a.E0,
                                                                         D(k->psi_tot), D(k->x));
@@ -898,8 +918,8 @@ struct Solver {
                                                                     I(bd.free_unk),
                                                            I(bd.bead_body), I(bd.body_unk), I(bd.mb_body),
                                                            I(bd.mb_unk), I(bd.mb_first), I(bd.mb_cnt),
-                                                           bd.rel.as<double>(), a.E0, bd.Q.as<double>(),
-                                                           D(k->psi_tot), D(k->x), D(k->r));
+                                                           bd.rel.as<double>(), a.E0, a.bead_psi,
+                                                           bd.Q.as<double>(), D(k->psi_tot), D(k->x), D(k->r));
         IBP_CHECK_LAUNCH();
         return norms(D(k->r));
     }
@@ -961,7 +981,7 @@ struct Solver {
                 xupdate_kernel<<<blocks_for(len), 256, 0, s()>>>(nk, m, kk, R, I(c->bodies.unk_cfg), D(k->V),
                                                                  D(k->y), D(k->pt));
                 IBP_CHECK_LAUNCH();
-                precond_apply(c, R, D(k->pt), nk, nullptr, nk, D(k->pz));
+                precond_apply(c, R, D(k->pt), nk, nullptr, nk, D(k->pz), dir);
                 axpby_kernel<<<blocks_for(len), 256, 0, s()>>>(len, 1.0, dd, 1.0, D(k->pz), dd);
                 IBP_CHECK_LAUNCH();
             } else {
@@ -992,7 +1012,8 @@ struct Solver {
         IBP_CUDA(cudaMemsetAsync(D(k->norms) + S, 0, sizeof(double) * S, s()));
         const int per = (n + nb) / ncfg + 1;
         bfull_kernel<<<dim3(std::max(1, std::min(blocks_for(per), 608 / S + 1)), S), 256, 0, s()>>>(
-            R, I(bd.cfg_beads), I(bd.cfg_bodies), bd.rel.as<double>(), a.E0, bd.Q.as<double>(), D(k->norms) + S);
+            R, n, I(bd.cfg_beads), I(bd.cfg_bodies), bd.rel.as<double>(), a.E0, a.bead_psi, bd.Q.as<double>(),
+            D(k->norms) + S);
         IBP_CHECK_LAUNCH();
         want_b = true;   // fetched with the initial residual
 

@@ -297,7 +297,7 @@ constexpr int kPairWarps = 4;   // warps per block
 // thread of node 0 writes the axis's start and offsets; axis 0 also the configuration.
 __global__ void stencil_cache_kernel(int n, const double* __restrict__ xw, const int* __restrict__ bcfg, MeshGeom g,
                                      int4* __restrict__ start, double4* __restrict__ frac, float4* __restrict__ frac32,
-                                     double* __restrict__ w64) {
+                                     double* __restrict__ w64, float2* __restrict__ wdf, float4* __restrict__ frac_df) {
     const int P = g.P;
     const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= 3LL * P * n) return;
@@ -308,8 +308,14 @@ __global__ void stencil_cache_kernel(int n, const double* __restrict__ xw, const
     const double sf = floor(u - 0.5 * P) + 1.0;
     const double f = sf - u;
     const double tt = f + (double)l;
-    w64[((size_t)b * 3 + d) * P + l] = exp(-g.kappa[d] * tt * tt);   // exactly as the kernels evaluate them
+    const double w = exp(-g.kappa[d] * tt * tt);   // exactly as the kernels evaluate them
+    w64[((size_t)b * 3 + d) * P + l] = w;
+    const df wd = df_split(w);
+    wdf[((size_t)b * 3 + d) * P + l] = make_float2(wd.hi, wd.lo);
     if (l != 0) return;
+    const df fd = df_split(f);
+    reinterpret_cast<float*>(frac_df + 2 * b)[d] = fd.hi;
+    reinterpret_cast<float*>(frac_df + 2 * b + 1)[d] = fd.lo;
     int idx = (int)sf % g.N[d];
     if (idx < 0) idx += g.N[d];
     reinterpret_cast<int*>(start + b)[d] = idx;
@@ -319,6 +325,8 @@ __global__ void stencil_cache_kernel(int n, const double* __restrict__ xw, const
         reinterpret_cast<int*>(start + b)[3] = bcfg ? bcfg[b] : 0;
         reinterpret_cast<double*>(frac + b)[3] = 0.0;
         reinterpret_cast<float*>(frac32 + b)[3] = 0.0f;
+        reinterpret_cast<float*>(frac_df + 2 * b)[3] = 0.0f;
+        reinterpret_cast<float*>(frac_df + 2 * b + 1)[3] = 0.0f;
     }
 }
 
@@ -333,6 +341,9 @@ struct PairArgs {
     const double4* frac;
     const float4* frac32;   // the same offsets rounded to FP32
     const double* w64;  // cached FP64 windows [n][3][P] (NULL: evaluate them)
+    const float2* wdf;  // the same as hi + lo floats
+    const float4* frac_df;   // per bead two float4: the offsets as hi, lo floats
+    float hdf[3][2];    // h per axis as hi, lo floats
     float kappa32[3], h32[3], c32, gather32, grad32;   // MeshGeom's constants in FP32
     const float2* gdf;  // FP64 gathers: the transformed grid as hi + lo floats, or NULL (FP64 grid)
 };
@@ -406,6 +417,162 @@ __device__ __forceinline__ Windows<T> bead_windows(const PairArgs& A, int bead, 
     if (W.iy >= g.N[1]) W.iy -= g.N[1];
     if (W.iz >= g.N[2]) W.iz -= g.N[2];
     return W;
+}
+
+// ---- FP64 gathers in double-float arithmetic ----
+// The double-float transforms leave the FP64 potential as hi + lo floats.  A gather
+// from it keeps every product and sum on the FP32 pipes: the bead's windows are split
+// into hi + lo floats once per lane, each column's walk, its weight and the bead's
+// running sums are double-float, and each result is joined to FP64 once (GB300
+// issues FP64 instructions at 1/64 of its FP32 rate, and an FP64 multiply-add per
+// column or per node made the FP64 pipe the limit of these gathers).
+
+// One-dimensional windows of a bead as double-float, lane l < P holding node l.
+struct DfWindows {
+    df wx, wy, wz, dx, dy, wdz;
+    int ix, iy, iz;
+};
+
+template <bool GRAD>
+__device__ __forceinline__ DfWindows df_bead_windows(const PairArgs& A, int bead, int lane) {
+    const MeshGeom& g = A.g;
+    const int P = g.P;
+    const bool in = lane < P;
+    const float2* wb = A.wdf + (size_t)bead * 3 * P;
+    DfWindows D;
+    const float2 zero = make_float2(0.0f, 0.0f);
+    const float2 wx = in ? wb[lane] : zero, wy = in ? wb[P + lane] : zero, wz = in ? wb[2 * P + lane] : zero;
+    D.wx = df{wx.x, wx.y};
+    D.wy = df{wy.x, wy.y};
+    D.wz = df{wz.x, wz.y};
+    if (GRAD) {   // distance (node l - x) = (f + l) h per axis, f the bead's offset
+        const float4 fh = A.frac_df[2 * bead], fl = A.frac_df[2 * bead + 1];
+        const float lf = (float)lane;
+        D.dx = df_mul(df_add(df{fh.x, fl.x}, df{lf, 0.0f}), df{A.hdf[0][0], A.hdf[0][1]});
+        D.dy = df_mul(df_add(df{fh.y, fl.y}, df{lf, 0.0f}), df{A.hdf[1][0], A.hdf[1][1]});
+        const df dz = df_mul(df_add(df{fh.z, fl.z}, df{lf, 0.0f}), df{A.hdf[2][0], A.hdf[2][1]});
+        D.wdz = df_mul(D.wz, dz);
+    } else {
+        D.dx = D.dy = D.wdz = df{0.0f, 0.0f};
+    }
+    const int4 st = A.start[bead];
+    D.ix = st.x + lane;
+    D.iy = st.y + lane;
+    D.iz = st.z + lane;
+    if (D.ix >= g.N[0]) D.ix -= g.N[0];   // P <= N: one wrap at most
+    if (D.iy >= g.N[1]) D.iy -= g.N[1];
+    if (D.iz >= g.N[2]) D.iz -= g.N[2];
+    return D;
+}
+
+__device__ __forceinline__ df df_shfl(df v, int src) {
+    return {__shfl_sync(0xffffffffu, v.hi, src), __shfl_sync(0xffffffffu, v.lo, src)};
+}
+
+// Adds one column's walk (sa = sum of node w_z, sz = sum of node w_z dz) with the
+// column's weight w_x w_y (and distances dx, dy for the gradient) to the bead's sums.
+template <int NR, bool GRAD>
+__device__ __forceinline__ void df_column_add(df wxy, df dx, df dy, const df (&sa)[NR], const df (&sz)[NR],
+                                              df (&sp)[NR], df (&ex)[NR], df (&ey)[NR], df (&ez)[NR]) {
+#pragma unroll
+    for (int r = 0; r < NR; ++r) {
+        const df t = df_mul(wxy, sa[r]);
+        sp[r] = df_add(sp[r], t);
+        if (GRAD) {
+            ex[r] = df_add(ex[r], df_mul(t, dx));
+            ey[r] = df_add(ey[r], df_mul(t, dy));
+            ez[r] = df_add(ez[r], df_mul(wxy, sz[r]));
+        }
+    }
+}
+
+// The bead's columns pair = first .. first + 31 (lane: first + lane) of its P^2 (x, y)
+// columns, read from the global hi + lo grid of its configuration (gr: channel 0).
+template <int NR, bool GRAD, int PC>
+__device__ __forceinline__ void df_round_global(const DfWindows& D, int P_rt, int lane, int first, int n0,
+                                                long long nxy, long long G, const float2* __restrict__ gr,
+                                                df (&sp)[NR], df (&ex)[NR], df (&ey)[NR], df (&ez)[NR]) {
+    const int P = PC ? PC : P_rt, P2 = P * P;
+    const int pair = first + lane;
+    const bool on = pair < P2;
+    int j = pair / P, i = pair - j * P;
+    if (!on) i = j = 0;
+    const df wx = df_shfl(D.wx, i), wy = df_shfl(D.wy, j);
+    const df wxy = on ? df_mul(wx, wy) : df{0.0f, 0.0f};
+    df dx = {0.0f, 0.0f}, dy = {0.0f, 0.0f};
+    if (GRAD) {
+        dx = df_shfl(D.dx, i);
+        dy = df_shfl(D.dy, j);
+    }
+    const long long base = (long long)__shfl_sync(0xffffffffu, D.iy, j) * n0 + __shfl_sync(0xffffffffu, D.ix, i);
+    df sa[NR], sz[NR];
+#pragma unroll
+    for (int r = 0; r < NR; ++r) sa[r] = sz[r] = df{0.0f, 0.0f};
+#pragma unroll
+    for (int k = 0; k < P; ++k) {
+        const df wz = df_shfl(D.wz, k);
+        const int iz = __shfl_sync(0xffffffffu, D.iz, k);
+        df wdz = {0.0f, 0.0f};
+        if (GRAD) wdz = df_shfl(D.wdz, k);
+        if (on) {
+            const size_t off = (size_t)iz * nxy + base;
+#pragma unroll
+            for (int r = 0; r < NR; ++r) {
+                const float2 v = __ldg(gr + (size_t)r * G + off);
+                const df vd = {v.x, v.y};
+                sa[r] = df_add(sa[r], df_mul(vd, wz));
+                if (GRAD) sz[r] = df_add(sz[r], df_mul(vd, wdz));
+            }
+        }
+    }
+    df_column_add<NR, GRAD>(wxy, dx, dy, sa, sz, sp, ex, ey, ez);
+}
+
+// Sums of the lanes of a warp into psi (and E) for bead `bead`, scaled by the gather and
+// gradient constants; accumulate adds (several warps share a bead), else it stores.
+template <int NR, bool GRAD>
+__device__ __forceinline__ void df_bead_store(const MeshGeom& g, int n, int bead, int lane, bool accumulate,
+                                              df (&sp)[NR], df (&ex)[NR], df (&ey)[NR], df (&ez)[NR],
+                                              double* __restrict__ psi, double* __restrict__ E) {
+    // the constants as double-float (a float pair is exact to 2^-48 of them)
+    const float gh = (float)g.gather, dh = (float)(-g.grad);
+    const df cg = {gh, (float)(g.gather - (double)gh)}, cd = {dh, (float)(-g.grad - (double)dh)};
+#pragma unroll
+    for (int r = 0; r < NR; ++r) {
+        // every lane holds every sum after the shuffles; lane k < 4 joins result k
+        // (one FP64 addition per bead for the potential and the three field components)
+        const df s0 = df_mul(df_warp_sum(sp[r]), cg);
+        df v = s0;
+        if (GRAD) {
+            const df e0 = df_mul(df_warp_sum(ex[r]), cd);
+            const df e1 = df_mul(df_warp_sum(ey[r]), cd);
+            const df e2 = df_mul(df_warp_sum(ez[r]), cd);
+            v = lane == 1 ? e0 : (lane == 2 ? e1 : (lane == 3 ? e2 : s0));
+        }
+        if (lane > (GRAD ? 3 : 0)) continue;
+        const double x = df_join(v);
+        double* dst = lane == 0 ? psi + (size_t)r * n + bead : E + ((size_t)r * n + bead) * 3 + (lane - 1);
+        if (accumulate) atomicAdd(dst, x);
+        else *dst = x;
+    }
+}
+
+// Direct FP64 gather of one bead (one warp) from the hi + lo grid.
+template <int NR, bool GRAD, int PC>
+__device__ __forceinline__ void gather_bead_df(const PairArgs& A, int n, int bead, int lane, double* __restrict__ psi,
+                                               double* __restrict__ E) {
+    const MeshGeom& g = A.g;
+    const int P = PC ? PC : g.P, P2 = P * P;
+    const DfWindows D = df_bead_windows<GRAD>(A, bead, lane);
+    const float2* gr = A.gdf + (size_t)A.start[bead].w * NR * g.G;
+    const long long nxy = (long long)g.N[0] * g.N[1];
+    df sp[NR], ex[NR], ey[NR], ez[NR];
+#pragma unroll
+    for (int r = 0; r < NR; ++r) sp[r] = ex[r] = ey[r] = ez[r] = df{0.0f, 0.0f};
+#pragma unroll
+    for (int first = 0; first < P2; first += 32)
+        df_round_global<NR, GRAD, PC>(D, P, lane, first, g.N[0], nxy, g.G, gr, sp, ex, ey, ez);
+    df_bead_store<NR, GRAD>(g, n, bead, lane, false, sp, ex, ey, ez, psi, E);
 }
 
 template <typename T, int NR, int PC>
@@ -499,6 +666,23 @@ gather_pairs_kernel(PairArgs A, int n, const T* __restrict__ grid, double* __res
     const int bead = (int)slot;
     const MeshGeom& g = A.g;
     const int P = PC ? PC : g.P, P2 = P * P;
+    if constexpr (sizeof(T) == 8) {
+        if (A.gdf) {   // FP64 potential as hi + lo floats: double-float throughout
+            const DfWindows D = df_bead_windows<GRAD>(A, bead, lane);
+            const float2* gr2 = A.gdf + (size_t)A.start[bead].w * NR * g.G;
+            const long long nxy2 = (long long)g.N[0] * g.N[1];
+            df dsp[NR], dex[NR], dey[NR], dez[NR];
+#pragma unroll
+            for (int r = 0; r < NR; ++r) dsp[r] = dex[r] = dey[r] = dez[r] = df{0.0f, 0.0f};
+            for (int rd = 0; rd < A.rounds; ++rd) {
+                const int first = (part * A.rounds + rd) * 32;
+                if (first >= P2) break;   // warp-uniform
+                df_round_global<NR, GRAD, PC>(D, P, lane, first, g.N[0], nxy2, g.G, gr2, dsp, dex, dey, dez);
+            }
+            df_bead_store<NR, GRAD>(g, n, bead, lane, A.wpb > 1, dsp, dex, dey, dez, psi, E);
+            return;
+        }
+    }
     const Windows<T> W = bead_windows<T, GRAD>(A, bead, lane);
     const T* gr = grid + (size_t)A.start[bead].w * NR * g.G;
     T sp[NR], ex[NR], ey[NR], ez[NR];
@@ -654,6 +838,13 @@ void pair_consts(PairArgs& A, const MeshGeom& g, const StencilCache& b) {
     A.frac = b.frac.as<double4>();
     A.frac32 = b.frac32.as<float4>();
     A.w64 = b.w64.as<double>();
+    A.wdf = b.wdf.as<float2>();
+    A.frac_df = b.frac_df.as<float4>();
+    for (int d = 0; d < 3; ++d) {
+        const float hi = (float)g.h[d];
+        A.hdf[d][0] = hi;
+        A.hdf[d][1] = (float)(g.h[d] - (double)hi);
+    }
     for (int d = 0; d < 3; ++d) {
         A.kappa32[d] = (float)g.kappa[d];
         A.h32[d] = (float)g.h[d];
@@ -775,6 +966,9 @@ __device__ __forceinline__ void spread_bead_direct(const PairArgs& A, int n, int
         if (!on) i = j = 0;
         const T wxy = __shfl_sync(0xffffffffu, W.wx, i) * __shfl_sync(0xffffffffu, W.wy, j);
         const long long base = (long long)__shfl_sync(0xffffffffu, W.iy, j) * g.N[0] + __shfl_sync(0xffffffffu, W.ix, i);
+        T qw[NR];   // the column's weight: one multiplication per node below
+#pragma unroll
+        for (int r = 0; r < NR; ++r) qw[r] = qc[r] * wxy;
         #pragma unroll
         for (int k = 0; k < P; ++k) {
             const T wz = __shfl_sync(0xffffffffu, W.wz, k);
@@ -782,7 +976,7 @@ __device__ __forceinline__ void spread_bead_direct(const PairArgs& A, int n, int
             if (on) {
                 const size_t off = (size_t)iz * nxy + base;
 #pragma unroll
-                for (int r = 0; r < NR; ++r) atomicAdd(gr + (size_t)r * g.G + off, qc[r] * wxy * wz);
+                for (int r = 0; r < NR; ++r) atomicAdd(gr + (size_t)r * g.G + off, qw[r] * wz);
             }
         }
     }
@@ -838,12 +1032,15 @@ spread_tiles_kernel(TileArgs TA, int n, const double* __restrict__ q, T* __restr
                 if (!on) i = j = 0;
                 const T wxy = __shfl_sync(0xffffffffu, wx, i) * __shfl_sync(0xffffffffu, wy, j);
                 const int base = (lz * E + ly + j) * E + lx + i;
-                #pragma unroll
-        for (int k = 0; k < P; ++k) {
+                T qw[NR];   // the column's weight: one multiplication per node below
+#pragma unroll
+                for (int c = 0; c < NR; ++c) qw[c] = qc[c] * wxy;
+#pragma unroll
+                for (int k = 0; k < P; ++k) {
                     const T wz = __shfl_sync(0xffffffffu, wz_l, k);
                     if (on) {
 #pragma unroll
-                        for (int c = 0; c < NR; ++c) atomicAdd(reg + c * E3 + base + k * E2, qc[c] * wxy * wz);
+                        for (int c = 0; c < NR; ++c) atomicAdd(reg + c * E3 + base + k * E2, qw[c] * wz);
                     }
                 }
             }
@@ -955,6 +1152,82 @@ __device__ __forceinline__ void gather_bead_direct(const PairArgs& A, int n, int
     }
 }
 
+// Dense tiles of an FP64 gather from the hi + lo grid: the region is staged in shared
+// memory as hi + lo floats and every bead of the run is gathered from it in
+// double-float arithmetic.
+template <int NR, bool GRAD, int PC>
+__device__ void gather_tiles_df(const TileArgs& TA, const TileRuns& R, int p0, int n, float2* __restrict__ reg,
+                                double* __restrict__ psi, double* __restrict__ E) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const PairArgs& A = TA.A;
+    const MeshGeom& g = A.g;
+    const int Ee = TA.E, E2 = Ee * Ee, E3 = E2 * Ee;
+    const int P = PC ? PC : g.P, P2 = P * P;
+    for (int r = 0; r < R.count; ++r) {
+        const int a = R.start[r], b = R.start[r + 1];
+        if (b - a < kTileMin) continue;   // block-uniform
+        const int key = TA.key[p0 + a];
+        const int tile = key % TA.ntiles, cfg = key / TA.ntiles;
+        const int ox = (tile % TA.tn[0]) * kTileNodes;
+        const int oy = ((tile / TA.tn[0]) % TA.tn[1]) * kTileNodes;
+        const int oz = (tile / (TA.tn[0] * TA.tn[1])) * kTileNodes;
+        const float2* gr = A.gdf + (size_t)cfg * NR * g.G;
+        for (int u = threadIdx.x; u < NR * E3; u += kTileThreads) {
+            const int c = u / E3, rem = u - c * E3;
+            const int z = rem / E2, y = (rem / Ee) % Ee, x = rem % Ee;
+            const size_t off = ((size_t)wrap_once(oz + z, g.N[2]) * g.N[1] + wrap_once(oy + y, g.N[1])) * g.N[0] +
+                               wrap_once(ox + x, g.N[0]);
+            reg[u] = __ldg(gr + (size_t)c * g.G + off);
+        }
+        __syncthreads();
+        for (int t = a + w; t < b; t += kTileWarps) {
+            const int bead = TA.sorted[p0 + t];
+            const int4 st = A.start[bead];
+            const DfWindows D = df_bead_windows<GRAD>(A, bead, lane);
+            const int lx = st.x - ox, ly = st.y - oy, lz = st.z - oz;
+            df sp[NR], ex[NR], ey[NR], ez[NR];
+#pragma unroll
+            for (int c = 0; c < NR; ++c) sp[c] = ex[c] = ey[c] = ez[c] = df{0.0f, 0.0f};
+#pragma unroll
+            for (int first = 0; first < P2; first += 32) {
+                const int pair = first + lane;
+                const bool on = pair < P2;
+                int j = pair / P, i = pair - j * P;
+                if (!on) i = j = 0;
+                const df wx = df_shfl(D.wx, i), wy = df_shfl(D.wy, j);
+                const df wxy = on ? df_mul(wx, wy) : df{0.0f, 0.0f};
+                df dx = {0.0f, 0.0f}, dy = {0.0f, 0.0f};
+                if (GRAD) {
+                    dx = df_shfl(D.dx, i);
+                    dy = df_shfl(D.dy, j);
+                }
+                const int base = (lz * Ee + ly + j) * Ee + lx + i;
+                df sa[NR], sz[NR];
+#pragma unroll
+                for (int c = 0; c < NR; ++c) sa[c] = sz[c] = df{0.0f, 0.0f};
+#pragma unroll
+                for (int k = 0; k < P; ++k) {
+                    const df wz = df_shfl(D.wz, k);
+                    df wdz = {0.0f, 0.0f};
+                    if (GRAD) wdz = df_shfl(D.wdz, k);
+                    if (on) {
+#pragma unroll
+                        for (int c = 0; c < NR; ++c) {
+                            const float2 v = reg[c * E3 + base + k * E2];
+                            const df vd = {v.x, v.y};
+                            sa[c] = df_add(sa[c], df_mul(vd, wz));
+                            if (GRAD) sz[c] = df_add(sz[c], df_mul(vd, wdz));
+                        }
+                    }
+                }
+                df_column_add<NR, GRAD>(wxy, dx, dy, sa, sz, sp, ex, ey, ez);
+            }
+            df_bead_store<NR, GRAD>(g, n, bead, lane, false, sp, ex, ey, ez, psi, E);
+        }
+        __syncthreads();
+    }
+}
+
 template <typename T, int NR, bool GRAD, int PC>
 __global__ void __launch_bounds__(kTileThreads)
 gather_tiles_kernel(TileArgs TA, int n, const T* __restrict__ grid, double* __restrict__ psi, double* __restrict__ E) {
@@ -967,13 +1240,28 @@ gather_tiles_kernel(TileArgs TA, int n, const T* __restrict__ grid, double* __re
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const PairArgs& A = TA.A;
     const MeshGeom& g = A.g;
+    bool dfg = false;   // FP64 potential as hi + lo floats: double-float throughout
+    if constexpr (sizeof(T) == 8) dfg = A.gdf != nullptr;
     for (int t = w; t < m; t += kTileWarps) {
         const int r = R.of[t];
-        if (R.start[r + 1] - R.start[r] < kTileMin)
+        if (R.start[r + 1] - R.start[r] < kTileMin) {
+            if constexpr (sizeof(T) == 8) {
+                if (dfg) {
+                    gather_bead_df<NR, GRAD, PC>(A, n, TA.sorted[p0 + t], lane, psi, E);
+                    continue;
+                }
+            }
             gather_bead_direct<T, NR, GRAD, PC>(A, n, TA.sorted[p0 + t], lane, grid, psi, E);
+        }
     }
     const int Ee = TA.E, E2 = Ee * Ee, E3 = E2 * Ee;
     const int P = PC ? PC : g.P, P2 = P * P;
+    if constexpr (sizeof(T) == 8) {
+        if (dfg) {
+            gather_tiles_df<NR, GRAD, PC>(TA, R, p0, n, reinterpret_cast<float2*>(tile_smem), psi, E);
+            return;
+        }
+    }
     for (int r = 0; r < R.count; ++r) {
         const int a = R.start[r], b = R.start[r + 1];
         if (b - a < kTileMin) continue;   // block-uniform
@@ -1447,8 +1735,10 @@ void build_stencils(ibpme_ctx* c, StencilCache& b, int n, const double* xw, cons
     double4* frac = static_cast<double4*>(b.frac.ensure(sizeof(double4) * n));
     float4* frac32 = static_cast<float4*>(b.frac32.ensure(sizeof(float4) * n));
     double* w64 = static_cast<double*>(b.w64.ensure(sizeof(double) * 3 * (size_t)g.P * n));
+    float2* wdf = static_cast<float2*>(b.wdf.ensure(sizeof(float2) * 3 * (size_t)g.P * n));
+    float4* frac_df = static_cast<float4*>(b.frac_df.ensure(sizeof(float4) * 2 * (size_t)n));
     stencil_cache_kernel<<<div_up(3LL * g.P * n, 256), 256, 0, c->stream>>>(n, xw, bcfg, g, start, frac, frac32,
-                                                                             w64);
+                                                                             w64, wdf, frac_df);
     IBP_CHECK_LAUNCH();
     // tile bins when one warp per bead already fills the GPU and a region of
     // E^3 nodes does not wrap onto itself

@@ -164,20 +164,22 @@ __global__ void fingerprint_kernel(long long m, const double* __restrict__ xw, c
     }
 }
 
-// Order-dependent 64-bit hash of m ints (one block): sum of mix64(value ^ mix64(index)).
+// Order-dependent 64-bit hash of m ints: mix64(m) + sum of mix64(value ^ mix64(index)),
+// added into *out (zeroed by the caller) by every block; the caller sets bit 0 so that
+// a hash is never 0 (0 means unknown).
 __global__ void hash_ints_kernel(const int* __restrict__ a, int m, unsigned long long* __restrict__ out) {
     __shared__ unsigned long long sh[32];
     unsigned long long acc = 0;
-    for (int i = threadIdx.x; i < m; i += blockDim.x)
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < m; i += (long long)gridDim.x * blockDim.x)
         acc += mix64((unsigned long long)(unsigned)a[i] ^ mix64(0xA24BAED4963EE407ull + (unsigned long long)i));
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
     if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = acc;
     __syncthreads();
     if (threadIdx.x == 0) {
-        unsigned long long t = mix64((unsigned long long)m);
+        unsigned long long t = blockIdx.x == 0 ? mix64((unsigned long long)m) : 0ull;
         for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += sh[w];
-        *out = t | 1ull;   // never 0 (0 means unknown)
+        atomicAdd(out, t);
     }
 }
 
@@ -952,6 +954,148 @@ __global__ void compact_table_kernel(int nt, const double* __restrict__ table, f
     tabdf[3 * j + 2] = make_float4(fh, (float)(f1 - (double)fh), (float)f2, (float)f3);
 }
 
+// ---- pair values in double-float arithmetic ----
+// GB300 issues FP64 at 1/64 of its FP32 rate, and the FP64 Hermite interpolation of
+// every pair made the FP64 pipe the limit of the table build.  Pairs at r >= 2a take
+// the table's per-interval coefficients in double-float arithmetic (linear terms hi +
+// lo, quadratic and cubic terms FP32, as the compact-body kernels) from double-float
+// positions, and join to FP64 once per value.  Overlapping beads (r < 2a) need the
+// exact kernel (three exp and three erfc in FP64); they are rare, and within a warp of
+// table pairs one of them stalled every lane, so they are listed and valued by a
+// second kernel of one thread per such pair.
+
+// Positions as hi, lo float4 per bead.
+__global__ void pos_df_kernel(int n, const double* __restrict__ xw, float4* __restrict__ xdf) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const df x = df_split(xw[3 * i]), y = df_split(xw[3 * i + 1]), z = df_split(xw[3 * i + 2]);
+    xdf[2 * i] = make_float4(x.hi, y.hi, z.hi, 0.0f);
+    xdf[2 * i + 1] = make_float4(x.lo, y.lo, z.lo, 0.0f);
+}
+
+struct DfPairArgs {
+    const float4* xdf;
+    const float4* tabdf;
+    int K;
+    df inv4a2;
+    df L[3];
+    float halfL[3];
+};
+
+// Minimum image of a difference of two wrapped coordinates (in (-L, L)): one shift.
+__device__ __forceinline__ df df_min_image(df d, df L, float halfL) {
+    if (d.hi > halfL) return df_sub(d, L);
+    if (d.hi < -halfL) return df_add(d, L);
+    return d;
+}
+
+__global__ void pair_values_df_kernel(long long np, DfPairArgs A, const int* __restrict__ prow,
+                                      const int* __restrict__ col, const int* __restrict__ order,
+                                      double* __restrict__ val, uint2* __restrict__ pair32, double* __restrict__ gfac,
+                                      int* __restrict__ ov_list, int* __restrict__ ov_count) {
+    const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= np) return;
+    const int a = order[prow[p]], cb = col[p], b = order[cb];
+    const float4 ah = A.xdf[2 * a], al = A.xdf[2 * a + 1], bh = A.xdf[2 * b], bl = A.xdf[2 * b + 1];
+    const df dx = df_min_image(df_sub(df{ah.x, al.x}, df{bh.x, bl.x}), A.L[0], A.halfL[0]);
+    const df dy = df_min_image(df_sub(df{ah.y, al.y}, df{bh.y, bl.y}), A.L[1], A.halfL[1]);
+    const df dz = df_min_image(df_sub(df{ah.z, al.z}, df{bh.z, bl.z}), A.L[2], A.halfL[2]);
+    const df r2 = df_add(df_add(df_sqr(dx), df_sqr(dy)), df_sqr(dz));
+    const df u = df_mul(r2, A.inv4a2);
+    if (!(u.hi > 1.0f || (u.hi == 1.0f && u.lo >= 0.0f))) {   // r < 2a: the exact kernel, below
+        ov_list[atomicAdd(ov_count, 1)] = (int)p;   // np < 2^31 (the table's pair count)
+        return;
+    }
+    df s;
+    const int j = cb_interval(u, A.K, s);
+    const float4 t0 = A.tabdf[3 * j], t1 = A.tabdf[3 * j + 1], t2 = A.tabdf[3 * j + 2];
+    const df phi = cb_poly(t0, t1.x, t1.y, s);
+    const df g = cb_poly(make_float4(t1.z, t1.w, t2.x, t2.y), t2.z, t2.w, s);
+    val[p] = df_join(phi);
+    pair32[p] = make_uint2((unsigned)cb, __float_as_uint(__fadd_rn(phi.hi, phi.lo)));
+    if (gfac) gfac[p] = df_join(g);
+}
+
+// The listed pairs of overlapping beads with the exact FP64 kernel (the r -> 0 limit
+// for coincident ones); the grid strides over the list, whose length is on the device.
+__global__ void pair_values_exact_kernel(const int* __restrict__ ov_count, const int* __restrict__ ov_list,
+                                         const double* __restrict__ xw, PairConst k, const int* __restrict__ prow,
+                                         const int* __restrict__ col, const int* __restrict__ order,
+                                         double* __restrict__ val, uint2* __restrict__ pair32,
+                                         double* __restrict__ gfac) {
+    const int m = *ov_count;
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < m; t += gridDim.x * blockDim.x) {
+        const long long p = ov_list[t];
+        const int a = order[prow[p]], cb = col[p], b = order[cb];
+        const double dx = min_image_wrapped(xw[3 * a + 0] - xw[3 * b + 0], k.L[0]);
+        const double dy = min_image_wrapped(xw[3 * a + 1] - xw[3 * b + 1], k.L[1]);
+        const double dz = min_image_wrapped(xw[3 * a + 2] - xw[3 * b + 2], k.L[2]);
+        const double r2 = dx * dx + dy * dy + dz * dz;
+        double phi, g;
+        if (r2 > 0.0) {
+            const double r = sqrt(r2);
+            double dphi;
+            pair_kernel(r, k, phi, dphi);
+            g = -dphi / r;
+        } else {
+            phi = k.self;   // coincident beads: the r -> 0 limit, no field
+            g = 0.0;
+        }
+        val[p] = phi;
+        pair32[p] = make_uint2((unsigned)cb, __float_as_uint((float)phi));
+        if (gfac) gfac[p] = g;
+    }
+}
+
+// The real-space field of near_field_kernel in double-float arithmetic: differences
+// from the double-float positions, products and the segmented warp sums on the FP32
+// pipes, one FP64 addition per component of each run's sum (the FP64 differences,
+// products and 15 FP64 additions of the segmented sums per pair made the FP64 pipe the
+// limit of the force pass).
+__global__ void near_field_df_kernel(long long np, int n, int nrhs, DfPairArgs A, const int* __restrict__ prow,
+                                     const int* __restrict__ col, const int* __restrict__ order,
+                                     const double* __restrict__ gfac, df inv_eps, const double* __restrict__ q,
+                                     double* __restrict__ E) {
+    const unsigned full = 0xffffffffu;
+    const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const int lane = threadIdx.x & 31;
+    const bool on = p < np;
+    const int t = on ? prow[p] : -1;   // idle lanes (the grid's tail) only follow on lanes
+    int a = 0, b = 0;
+    df gf = {0.0f, 0.0f}, d[3] = {{0.0f, 0.0f}, {0.0f, 0.0f}, {0.0f, 0.0f}};
+    if (on) {
+        a = order[t];
+        b = order[col[p]];
+        gf = df_split(gfac[p]);
+        const float4 ah = A.xdf[2 * a], al = A.xdf[2 * a + 1], bh = A.xdf[2 * b], bl = A.xdf[2 * b + 1];
+        d[0] = df_min_image(df_sub(df{ah.x, al.x}, df{bh.x, bl.x}), A.L[0], A.halfL[0]);
+        d[1] = df_min_image(df_sub(df{ah.y, al.y}, df{bh.y, bl.y}), A.L[1], A.halfL[1]);
+        d[2] = df_min_image(df_sub(df{ah.z, al.z}, df{bh.z, bl.z}), A.L[2], A.halfL[2]);
+    }
+    const int tprev = __shfl_up_sync(full, t, 1);
+    const bool head = on && (lane == 0 || tprev != t);
+    for (int r = 0; r < nrhs; ++r) {
+        const df wq = on ? df_mul(gf, df_split(q[(size_t)r * n + b])) : df{0.0f, 0.0f};
+        df v[3] = {df_mul(wq, d[0]), df_mul(wq, d[1]), df_mul(wq, d[2])};
+        // after the step of width w, lane l holds the sum over lanes [l, l + 2w) of its run
+#pragma unroll
+        for (int w = 1; w < 32; w <<= 1) {
+            const int ot = __shfl_down_sync(full, t, w);
+            df o[3];
+#pragma unroll
+            for (int c = 0; c < 3; ++c) o[c] = df{__shfl_down_sync(full, v[c].hi, w), __shfl_down_sync(full, v[c].lo, w)};
+            if (lane + w < 32 && ot == t)
+#pragma unroll
+                for (int c = 0; c < 3; ++c) v[c] = df_add(v[c], o[c]);
+        }
+        if (head) {
+            double* e = E + ((size_t)r * n + a) * 3;
+#pragma unroll
+            for (int c = 0; c < 3; ++c) atomicAdd(e + c, df_join(df_mul(v[c], inv_eps)));
+        }
+    }
+}
+
 // ---- exclusive scan of int counts into 64-bit offsets (three passes) ----
 constexpr int kScanThreads = 1024;
 constexpr int kScanItems = 4;
@@ -1295,7 +1439,7 @@ unsigned long long near_prefetch(ibpme_ctx* c, int n, const double* xw, const in
             3LL * n, xw, nullptr, fp, reinterpret_cast<int*>(fp + 1));
         IBP_CHECK_LAUNCH();
     }
-    hash_ints_kernel<<<1, 256, 0, s>>>(off, noff, fp + 2);
+    hash_ints_kernel<<<std::max(1, std::min(div_up(noff, 256), 152)), 256, 0, s>>>(off, noff, fp + 2);
     IBP_CHECK_LAUNCH();
     unsigned long long* h = static_cast<unsigned long long*>(pinned_host(c, 3 * sizeof(unsigned long long)));
     IBP_CUDA(cudaMemcpyAsync(h, fp, 3 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
@@ -1305,7 +1449,7 @@ unsigned long long near_prefetch(ibpme_ctx* c, int n, const double* xw, const in
     nl.fp_pre_n = n;
     nl.fp_pre_xw = xw;
     nl.fp_pre_valid = true;
-    return h[2];
+    return h[2] | 1ull;
 }
 
 void near_build(ibpme_ctx* c, int n, const double* xw, bool need_grad) {
@@ -1342,6 +1486,7 @@ void near_build(ibpme_ctx* c, int n, const double* xw, bool need_grad) {
     const unsigned long long cb_key = want_cb ? bd.version : 0;
     if (nl.fp_valid && nl.n == n && nl.fp == print && nl.ncfg == c->ncfg && nl.cb_key == cb_key) return;
     nl.fp_valid = false;
+    nl.ov_valid = false;
     nl.cb_on = false;
     nl.cb_key = cb_key;
     nl.n = n;
@@ -1412,7 +1557,31 @@ void near_build(ibpme_ctx* c, int n, const double* xw, bool need_grad) {
         pair_fill_kernel<<<div_up((long long)n * 32, 128), 128, 0, s>>>(n, xw, xf, k, cell_of, cell_start,
                                                                          cell_beads, rowptr, col, prow);
         IBP_CHECK_LAUNCH();
-        if (nl.npairs > 0) {
+        if (nl.npairs > 0 && k.K > 0 && nl.npairs < (1LL << 31)) {
+            // table pairs in double-float arithmetic, overlapping beads listed and valued exactly
+            float4* xdf = static_cast<float4*>(nl.xdf.ensure(sizeof(float4) * 2 * (size_t)(n + 1)));
+            pos_df_kernel<<<div_up(n, 256), 256, 0, s>>>(n, xw, xdf);
+            IBP_CHECK_LAUNCH();
+            int* ov_list = static_cast<int*>(nl.ov_list.ensure(sizeof(int) * np));
+            int* ov_count = static_cast<int*>(nl.ov_count.ensure(sizeof(int)));
+            IBP_CUDA(cudaMemsetAsync(ov_count, 0, sizeof(int), s));
+            DfPairArgs A{};
+            A.xdf = xdf;
+            A.tabdf = nl.tab_df.as<float4>();
+            A.K = k.K;
+            A.inv4a2 = host_df(k.inv4a2);
+            for (int d = 0; d < 3; ++d) {
+                A.L[d] = host_df(k.L[d]);
+                A.halfL[d] = (float)(0.5 * k.L[d]);
+            }
+            pair_values_df_kernel<<<div_up(nl.npairs, 256), 256, 0, s>>>(nl.npairs, A, prow, col, cell_beads, val,
+                                                                        pair32, gfac, ov_list, ov_count);
+            IBP_CHECK_LAUNCH();
+            pair_values_exact_kernel<<<152 * 4, 128, 0, s>>>(ov_count, ov_list, xw, k, prow, col, cell_beads, val,
+                                                             pair32, gfac);
+            IBP_CHECK_LAUNCH();
+            nl.ov_valid = true;
+        } else if (nl.npairs > 0) {
             pair_values_kernel<<<div_up(nl.npairs, 256), 256, 0, s>>>(nl.npairs, xw, k, prow, col, cell_beads, val,
                                                                      pair32, gfac);
             IBP_CHECK_LAUNCH();
@@ -1474,7 +1643,18 @@ void near_field(ibpme_ctx* c, int n, const double* xw, const double* q, int nrhs
     NearList& nl = c->near;
     const PairConst k = make_const(c);
     IBP_CUDA(cudaMemsetAsync(E_r, 0, sizeof(double) * 3 * (size_t)nrhs * n, c->stream));
-    if (nl.npairs > 0) {
+    if (nl.npairs > 0 && nl.ov_valid) {   // double-float positions of this table are current
+        DfPairArgs A{};
+        A.xdf = nl.xdf.as<float4>();
+        for (int d = 0; d < 3; ++d) {
+            A.L[d] = host_df(k.L[d]);
+            A.halfL[d] = (float)(0.5 * k.L[d]);
+        }
+        near_field_df_kernel<<<div_up(nl.npairs, 256), 256, 0, c->stream>>>(
+            nl.npairs, n, nrhs, A, nl.prow.as<int>(), nl.col.as<int>(), nl.cell_beads.as<int>(), nl.gfac.as<double>(),
+            host_df(1.0 / c->eps), q, E_r);
+        IBP_CHECK_LAUNCH();
+    } else if (nl.npairs > 0) {
         near_field_kernel<<<div_up(nl.npairs, 256), 256, 0, c->stream>>>(
             nl.npairs, n, nrhs, xw, k, nl.prow.as<int>(), nl.col.as<int>(), nl.cell_beads.as<int>(),
             nl.gfac.as<double>(), 1.0 / c->eps, q, E_r);

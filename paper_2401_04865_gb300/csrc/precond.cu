@@ -151,9 +151,11 @@ constexpr int kRowsPerBlock = 8;   // rows of M^{-1} per block: a body spreads o
 constexpr int kApplyThreads = 256;
 
 // out = P^{-1} u on the preconditioned bodies (grid: bodies x row chunks, R) and
-// out = u on every other unknown (the trailing blocks of the grid).
+// out = u on every other unknown (the trailing blocks of the grid).  With dir (the
+// problem of prescribed bead potentials, whose operator is [-M 0; 0 I]) the block is
+// [-M_b 0; 0 1] and its inverse -M_b^{-1} on the beads, the identity on the body row.
 __global__ void __launch_bounds__(kApplyThreads)
-precond_apply_kernel(int npb, int chunks, int nk, long long ustride, const int* __restrict__ jdev,
+precond_apply_kernel(bool dir, int npb, int chunks, int nk, long long ustride, const int* __restrict__ jdev,
                      const int* __restrict__ pb_shape, const int* __restrict__ pb_first,
                      const int* __restrict__ pb_psi, const int* __restrict__ pb_n,
                      const long long* __restrict__ shape_off, const long long* __restrict__ shape_goff,
@@ -192,7 +194,7 @@ precond_apply_kernel(int npb, int chunks, int nk, long long ustride, const int* 
     if (threadIdx.x == 0) {
         df t = {0.0f, 0.0f};
         for (int q = 0; q < kApplyThreads / 32; ++q) t = df_add(t, sh[q]);
-        tpsi = (df_join(t) + ur[pb_psi[p]]) * sinv[sh_id];
+        tpsi = dir ? ur[pb_psi[p]] : (df_join(t) + ur[pb_psi[p]]) * sinv[sh_id];
     }
     __syncthreads();
     const double tp = tpsi;
@@ -206,7 +208,7 @@ precond_apply_kernel(int npb, int chunks, int nk, long long ustride, const int* 
             s = df_add(s, df_mul_f({vj.x, vj.y}, Mi[j]));
         }
         s = df_warp_sum(s);
-        if (lane == 0) orow[first + i] = -df_join(s) + (double)gv[i] * tp;
+        if (lane == 0) orow[first + i] = -df_join(s) + (dir ? 0.0 : (double)gv[i] * tp);
     }
     if (chunk == 0 && threadIdx.x == 0) orow[pb_psi[p]] = tp;
 }
@@ -399,11 +401,12 @@ bool precond_prepare(ibpme_ctx* c) {
     return true;
 }
 
-void precond_apply(ibpme_ctx* c, int R, const double* u, long long ustride, const int* jdev, int nk, double* out) {
+void precond_apply(ibpme_ctx* c, int R, const double* u, long long ustride, const int* jdev, int nk, double* out,
+                   bool dir) {
     const Precond& P = c->pre;
     const int blocks = P.npb * P.chunks + div_up(P.nplain > 0 ? P.nplain : 1, kApplyThreads);
     precond_apply_kernel<<<dim3(blocks, R), kApplyThreads, 0, c->stream>>>(
-        P.npb, P.chunks, nk, ustride, jdev, P.pb_shape.as<int>(), P.pb_first.as<int>(), P.pb_psi.as<int>(),
+        dir, P.npb, P.chunks, nk, ustride, jdev, P.pb_shape.as<int>(), P.pb_first.as<int>(), P.pb_psi.as<int>(),
         P.pb_n.as<int>(), P.shape_off.as<long long>(), P.shape_goff.as<long long>(), P.minv.as<float>(),
         P.gvec.as<float>(),
         P.sinv.as<double>(), P.nplain, P.plain.as<int>(), u, out);

@@ -75,6 +75,62 @@ def test_run_sharded_gathers_every_item_in_order_over_two_gloo_ranks(tmp_path):
         assert sorted(np.nonzero(res[:, 2] == r)[0].tolist()) == plan[r]
 
 
+def _moment_tensors(systems):
+    """A stand-in for the solve of each configuration: per body, the second moment
+    sum_j r_j r_j^T of its beads about their centroid (geometry only)."""
+    out = []
+    for s in systems:
+        off = s.body_offsets
+        T = np.zeros((s.n_bodies, 3, 3))
+        for b in range(s.n_bodies):
+            r = s.x[off[b]:off[b + 1]] - s.X[b]
+            T[b] = r.T @ r
+        out.append(T)
+    return out
+
+
+def _pol_rank_main(rank, world, port, out_path):
+    import torch.distributed as dist
+    from workloads import configs as C
+    dist.init_process_group("gloo", init_method=f"tcp://127.0.0.1:{port}", rank=rank, world_size=world)
+    try:
+        systems = C.config4_batch(n_configs=8, seed=1003, common_radius=True)
+        solved = []
+
+        def stub(part):
+            solved.extend(s.name for s in part)
+            return _moment_tensors(part), [dict(configs=len(part), beads=int(sum(s.n for s in part)))]
+
+        tensors, report = B.polarizability_sharded(None, systems, solve=stub)
+        names = [None] * world
+        dist.all_gather_object(names, solved)
+        if rank == 0:
+            np.save(out_path, np.concatenate([t.ravel() for t in tensors]))
+            np.save(out_path + ".plan.npy", np.array([len(n) for n in names]))
+        else:
+            assert tensors is None
+        assert report and report[0]["configs"] == len(solved)
+    finally:
+        dist.destroy_process_group()
+
+
+def test_polarizability_batch_sharded_over_two_gloo_ranks_equals_one_rank(tmp_path):
+    """The 8-configuration prefix of the batched polarizability workload (real
+    configurations of rods, cubes and ellipsoids) split over two gloo ranks with
+    shard_lpt and gathered with run_sharded: rank 0 receives every configuration's
+    tensors in configuration order, equal to one rank solving all of them, and the
+    split follows the LPT plan of the cost model."""
+    import torch.multiprocessing as mp
+    from workloads import configs as C
+    out = str(tmp_path / "pol.npy")
+    mp.spawn(_pol_rank_main, args=(2, _free_port(), out), nprocs=2, join=True)
+    systems = C.config4_batch(n_configs=8, seed=1003, common_radius=True)
+    want = np.concatenate([t.ravel() for t in _moment_tensors(systems)])
+    assert np.array_equal(np.load(out), want)
+    plan = B.shard_lpt([B.cost_model(s.n) for s in systems], 2)
+    assert list(np.load(out + ".plan.npy")) == [len(p) for p in plan]
+
+
 class _FakeBucket:
     def __init__(self, n, nconf):
         self.n = n

@@ -88,6 +88,8 @@ def test_batch_reports_not_converged_when_one_configuration_misses(cuda_lib):
     ib = cuda_lib
     parts = [C.small_system(seed=42, n_bodies=1, level=1, n_ions=0, L=8.0, a=0.14, mesh=(48, 48, 48), tol=1e-8),
              _system()]
+    for p in parts:
+        p.E0 = np.array([[0.3, -0.2, 1.0]])
     s, cfg = C.stack(parts)
     ctx = context(ib, s, precision="fp64")
     try:
