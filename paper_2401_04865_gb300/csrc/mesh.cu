@@ -946,6 +946,140 @@ __device__ void tile_runs(const int* __restrict__ key, int p0, int m, TileRuns& 
 
 __device__ __forceinline__ int wrap_once(int v, int N) { return v >= N ? v - N : v; }
 
+// ---- FP32 direct paths with 16-byte accesses ----
+// With N_x a multiple of four and the stencil width known at compile time, a lane
+// takes one (y, z) row of a bead's stencil; the row's P x-nodes lie in G4 aligned
+// groups of four consecutive nodes (periodic wrap at a group boundary), which are
+// added with float4 atomics (spread) or read with float4 loads (gather), zeros in
+// the slots outside the stencil: for P = 9 three vector accesses per row instead of
+// nine scalar ones.  Every lane holds the 4 G4 slot weights of the x axis (the same for
+// all rows of the bead).
+template <int P>
+struct V4 {
+    static constexpr int G4 = (P + 6) / 4;   // groups covering offsets sh .. sh + P - 1, sh < 4
+};
+
+template <int P>
+__device__ __forceinline__ void x_slots(float wl, int sh, float (&w)[4 * V4<P>::G4]) {
+#pragma unroll
+    for (int m = 0; m < 4 * V4<P>::G4; ++m) {
+        const int idx = m - sh;   // warp-uniform
+        const float v = __shfl_sync(0xffffffffu, wl, idx < 0 ? 0 : (idx >= P ? 0 : idx));
+        w[m] = (idx >= 0 && idx < P) ? v : 0.0f;
+    }
+}
+
+template <int NR, int P>
+__device__ __forceinline__ void spread_bead_v4(const PairArgs& A, int n, int bead, int lane,
+                                               const double* __restrict__ q, float* __restrict__ grid) {
+    constexpr int G4 = V4<P>::G4, P2 = P * P;
+    const MeshGeom& g = A.g;
+    const Windows<float> W = bead_windows<float, false>(A, bead, lane);
+    const int ix0 = __shfl_sync(0xffffffffu, W.ix, 0);
+    const int sh = ix0 & 3, gx0 = ix0 >> 2, ngx = g.N[0] >> 2;
+    float wx[4 * G4];
+    x_slots<P>(W.wx, sh, wx);
+    float* gr = grid + (size_t)A.start[bead].w * NR * g.G;
+    float qc[NR];
+#pragma unroll
+    for (int r = 0; r < NR; ++r) qc[r] = A.c32 * (float)q[(size_t)r * n + bead];
+#pragma unroll
+    for (int first = 0; first < P2; first += 32) {
+        const int row = first + lane;
+        const bool on = row < P2;
+        int k = row / P, j = row - k * P;
+        if (!on) j = k = 0;
+        const float wyz = __shfl_sync(0xffffffffu, W.wy, j) * __shfl_sync(0xffffffffu, W.wz, k);
+        const int iy = __shfl_sync(0xffffffffu, W.iy, j), iz = __shfl_sync(0xffffffffu, W.iz, k);
+        if (on) {
+            float4* row4 = reinterpret_cast<float4*>(gr + ((size_t)iz * g.N[1] + iy) * g.N[0]);
+#pragma unroll
+            for (int r = 0; r < NR; ++r) {
+                const float s = qc[r] * wyz;
+                float4* rp = row4 + (size_t)r * (g.G >> 2);
+#pragma unroll
+                for (int t = 0; t < G4; ++t) {
+                    int gx = gx0 + t;
+                    if (gx >= ngx) gx -= ngx;
+                    atomicAdd(rp + gx, make_float4(s * wx[4 * t], s * wx[4 * t + 1], s * wx[4 * t + 2],
+                                                   s * wx[4 * t + 3]));
+                }
+            }
+        }
+    }
+}
+
+template <int NR, bool GRAD, int P>
+__device__ __forceinline__ void gather_bead_v4(const PairArgs& A, int n, int bead, int lane,
+                                               const float* __restrict__ grid, double* __restrict__ psi,
+                                               double* __restrict__ E) {
+    constexpr int G4 = V4<P>::G4, P2 = P * P;
+    const MeshGeom& g = A.g;
+    const Windows<float> W = bead_windows<float, GRAD>(A, bead, lane);
+    const int ix0 = __shfl_sync(0xffffffffu, W.ix, 0);
+    const int sh = ix0 & 3, gx0 = ix0 >> 2, ngx = g.N[0] >> 2;
+    float wx[4 * G4], wxd[4 * G4];
+    x_slots<P>(W.wx, sh, wx);
+    if (GRAD) x_slots<P>(W.wx * W.dx, sh, wxd);
+    const float* gr = grid + (size_t)A.start[bead].w * NR * g.G;
+    float sp[NR], ex[NR], ey[NR], ez[NR];
+#pragma unroll
+    for (int r = 0; r < NR; ++r) sp[r] = ex[r] = ey[r] = ez[r] = 0.0f;
+#pragma unroll
+    for (int first = 0; first < P2; first += 32) {
+        const int row = first + lane;
+        const bool on = row < P2;
+        int k = row / P, j = row - k * P;
+        if (!on) j = k = 0;
+        const float wy = __shfl_sync(0xffffffffu, W.wy, j), wz = __shfl_sync(0xffffffffu, W.wz, k);
+        float wyz = wy * wz, wdy = 0.0f, wdz = 0.0f;
+        if (GRAD) {
+            wdy = wy * __shfl_sync(0xffffffffu, W.dy, j) * wz;
+            wdz = wy * __shfl_sync(0xffffffffu, W.wdz, k);
+        }
+        const int iy = __shfl_sync(0xffffffffu, W.iy, j), iz = __shfl_sync(0xffffffffu, W.iz, k);
+        if (!on) wyz = wdy = wdz = 0.0f;
+        if (on) {
+            const float4* row4 = reinterpret_cast<const float4*>(gr + ((size_t)iz * g.N[1] + iy) * g.N[0]);
+#pragma unroll
+            for (int r = 0; r < NR; ++r) {
+                const float4* rp = row4 + (size_t)r * (g.G >> 2);
+                float a = 0.0f, ax = 0.0f;
+#pragma unroll
+                for (int t = 0; t < G4; ++t) {
+                    int gx = gx0 + t;
+                    if (gx >= ngx) gx -= ngx;
+                    const float4 v = __ldg(rp + gx);
+                    a = fmaf(v.x, wx[4 * t], fmaf(v.y, wx[4 * t + 1], fmaf(v.z, wx[4 * t + 2], fmaf(v.w, wx[4 * t + 3], a))));
+                    if (GRAD)
+                        ax = fmaf(v.x, wxd[4 * t], fmaf(v.y, wxd[4 * t + 1],
+                                  fmaf(v.z, wxd[4 * t + 2], fmaf(v.w, wxd[4 * t + 3], ax))));
+                }
+                sp[r] = fmaf(wyz, a, sp[r]);
+                if (GRAD) {
+                    ex[r] = fmaf(wyz, ax, ex[r]);
+                    ey[r] = fmaf(wdy, a, ey[r]);
+                    ez[r] = fmaf(wdz, a, ez[r]);
+                }
+            }
+        }
+    }
+#pragma unroll
+    for (int r = 0; r < NR; ++r) {
+        const float s0 = warp_sum(sp[r]);
+        if (GRAD) {
+            const float e0 = warp_sum(ex[r]), e1 = warp_sum(ey[r]), e2 = warp_sum(ez[r]);
+            if (lane == 0) {
+                double* e = E + ((size_t)r * n + bead) * 3;
+                e[0] = (double)(-A.grad32 * e0);
+                e[1] = (double)(-A.grad32 * e1);
+                e[2] = (double)(-A.grad32 * e2);
+            }
+        }
+        if (lane == 0) psi[(size_t)r * n + bead] = (double)(A.gather32 * s0);
+    }
+}
+
 // Direct spreading of one bead (one warp, global atomics).
 template <typename T, int NR, int PC>
 __device__ __forceinline__ void spread_bead_direct(const PairArgs& A, int n, int bead, int lane,
@@ -994,10 +1128,19 @@ spread_tiles_kernel(TileArgs TA, int n, const double* __restrict__ q, T* __restr
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const PairArgs& A = TA.A;
     const MeshGeom& g = A.g;
-    // isolated beads: direct atomics
+    // isolated beads: direct atomics (FP32 rows as float4 groups when the stencil width is fixed)
+    const bool v4x = (g.N[0] & 3) == 0;
     for (int t = w; t < m; t += kTileWarps) {
         const int r = R.of[t];
-        if (R.start[r + 1] - R.start[r] < kTileMin) spread_bead_direct<T, NR, PC>(A, n, TA.sorted[p0 + t], lane, q, grid);
+        if (R.start[r + 1] - R.start[r] < kTileMin) {
+            if constexpr (sizeof(T) == 4 && PC > 0) {
+                if (v4x) {
+                    spread_bead_v4<NR, PC>(A, n, TA.sorted[p0 + t], lane, q, reinterpret_cast<float*>(grid));
+                    continue;
+                }
+            }
+            spread_bead_direct<T, NR, PC>(A, n, TA.sorted[p0 + t], lane, q, grid);
+        }
     }
     const int E = TA.E, E2 = E * E, E3 = E2 * E;
     const int P = PC ? PC : g.P, P2 = P * P;
@@ -1047,14 +1190,33 @@ spread_tiles_kernel(TileArgs TA, int n, const double* __restrict__ q, T* __restr
         }
         __syncthreads();
         T* gr = grid + (size_t)cfg * NR * g.G;
-        for (int u = threadIdx.x; u < NR * E3; u += kTileThreads) {
-            const T v = reg[u];
-            if (v != (T)0) {
-                const int c = u / E3, rem = u - c * E3;
-                const int z = rem / E2, y = (rem / E) % E, x = rem % E;
-                const size_t off = ((size_t)wrap_once(oz + z, g.N[2]) * g.N[1] + wrap_once(oy + y, g.N[1])) * g.N[0] +
-                                   wrap_once(ox + x, g.N[0]);
-                atomicAdd(gr + (size_t)c * g.G + off, v);
+        bool flushed = false;
+        if constexpr (sizeof(T) == 4) {
+            if (v4x && (E & 3) == 0) {   // groups of four x-nodes: float4 atomics (a group never wraps)
+                const int E4 = E >> 2;
+                for (int u = threadIdx.x; u < NR * (E3 >> 2); u += kTileThreads) {
+                    const float4 v = reinterpret_cast<const float4*>(reg)[u];
+                    if (v.x != 0.0f || v.y != 0.0f || v.z != 0.0f || v.w != 0.0f) {
+                        const int c = u / (E3 >> 2), rem = u - c * (E3 >> 2);
+                        const int z = rem / (E2 >> 2), y = (rem / E4) % E, x = 4 * (rem % E4);
+                        const size_t off = ((size_t)wrap_once(oz + z, g.N[2]) * g.N[1] + wrap_once(oy + y, g.N[1])) *
+                                               g.N[0] + wrap_once(ox + x, g.N[0]);
+                        atomicAdd(reinterpret_cast<float4*>(gr + (size_t)c * g.G + off), v);
+                    }
+                }
+                flushed = true;
+            }
+        }
+        if (!flushed) {
+            for (int u = threadIdx.x; u < NR * E3; u += kTileThreads) {
+                const T v = reg[u];
+                if (v != (T)0) {
+                    const int c = u / E3, rem = u - c * E3;
+                    const int z = rem / E2, y = (rem / E) % E, x = rem % E;
+                    const size_t off = ((size_t)wrap_once(oz + z, g.N[2]) * g.N[1] + wrap_once(oy + y, g.N[1])) *
+                                           g.N[0] + wrap_once(ox + x, g.N[0]);
+                    atomicAdd(gr + (size_t)c * g.G + off, v);
+                }
             }
         }
         __syncthreads();
@@ -1242,12 +1404,20 @@ gather_tiles_kernel(TileArgs TA, int n, const T* __restrict__ grid, double* __re
     const MeshGeom& g = A.g;
     bool dfg = false;   // FP64 potential as hi + lo floats: double-float throughout
     if constexpr (sizeof(T) == 8) dfg = A.gdf != nullptr;
+    const bool v4x = (g.N[0] & 3) == 0;
     for (int t = w; t < m; t += kTileWarps) {
         const int r = R.of[t];
         if (R.start[r + 1] - R.start[r] < kTileMin) {
             if constexpr (sizeof(T) == 8) {
                 if (dfg) {
                     gather_bead_df<NR, GRAD, PC>(A, n, TA.sorted[p0 + t], lane, psi, E);
+                    continue;
+                }
+            }
+            if constexpr (sizeof(T) == 4 && PC > 0) {
+                if (v4x) {
+                    gather_bead_v4<NR, GRAD, PC>(A, n, TA.sorted[p0 + t], lane, reinterpret_cast<const float*>(grid),
+                                                 psi, E);
                     continue;
                 }
             }

@@ -155,12 +155,14 @@ def _dense_surfaces(seed, n_surf=6, per=1500, n_ions=1000, box=(5.0, 6.0, 7.0)):
     return np.mod(np.concatenate(parts), box), box
 
 
-@pytest.mark.parametrize("nrhs,mesh", [(1, (36, 44, 52)), (3, (36, 44, 52)), (1, (40, 48, 56)), (3, (40, 48, 56))])
+@pytest.mark.parametrize("nrhs,mesh", [(1, (36, 44, 52)), (3, (36, 44, 52)), (1, (40, 48, 56)), (3, (40, 48, 56)),
+                                       (2, (38, 44, 50))])
 def test_tiled_mesh_path_matches_direct_path_and_oracle(cuda_lib, nrhs, mesh, monkeypatch):
     """10,000 beads (9,000 on six sphere surfaces, 1,000 ions) take the tiled
     spread and gather (shared-memory regions for dense tiles, direct atomics for
     isolated ions), on meshes whose edges are and are not multiples of the tile
-    edge (ragged last tiles).  Against the same call with tiles switched off (FP64
+    edge (ragged last tiles) and with N_x a multiple of four (FP32 rows in float4
+    groups) or not (scalar rows).  Against the same call with tiles switched off (FP64
     to rounding, FP32 to FP32 rounding) and against the oracle at sampled beads."""
     ib = cuda_lib
     x, box = _dense_surfaces(50 + nrhs)
