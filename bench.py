@@ -780,18 +780,26 @@ def bench_polarizability(args, ib, torch, rank, world, local):
 TRAJ_WORKLOAD = ("trajectory: 8 polarizable spheres (642 beads each) + 20,000 monovalent ions, L=30, l_B=0.7, "
                  "bead radius 0.05, E0=z, mesh 192^3, tol 1e-6; step = mixed-precision solve to FP64 residual "
                  "1e-6 + forces/torques + one BD step (dt=1e-3, kT=1); initial guess: zero, the previous "
-                 "step's charges, or the learned warm start trained on the first steps")
+                 "step's charges, the learned warm start (trained first on method-generated solves of 2-8 "
+                 "spheres and rods with 0-20,000 ions in random fields of magnitude 0.1-2), or the previous "
+                 "step's charges plus the learned change; value = the learned warm start")
+TRAJ_TRAIN_SOLVES = 1000
 
 
 def bench_trajectory(args, ib, torch, rank, world, local):
+    from paper_2401_04865_gb300 import warmstart as W
     from workloads import configs as C
     torch.cuda.set_device(local)
     s = C.config5_trajectory(seed=1004 + 7919 * rank)
     dev, f64 = "cuda", torch.float64
     t = lambda a, dt=f64: torch.as_tensor(np.ascontiguousarray(a)).to(dt).to(dev)
     stream = torch.cuda.current_stream()
-    ctx = ib.pme_setup(ib.make_params(box=s.box, mesh=s.mesh, tol=s.tol, bead_radius=s.a, eps_f=s.eps,
-                                      precision=ib.IBPME_MIXED, max_rhs=1), stream)
+
+    def make_ctx(prec):
+        return ib.pme_setup(ib.make_params(box=s.box, mesh=s.mesh, tol=s.tol, bead_radius=s.a, eps_f=s.eps,
+                                           precision=prec, max_rhs=1), stream)
+
+    ctx = make_ctx(ib.IBPME_MIXED)
     n, nb = s.n, s.n_bodies
     off, Q, E0 = t(s.body_offsets, torch.int32), t(s.Q), t(s.E0[:1])
     x, X = t(s.x), t(s.X)
@@ -800,66 +808,60 @@ def bench_trajectory(args, ib, torch, rank, world, local):
     fb = torch.zeros((n, 3), dtype=f64, device=dev)
     F = torch.zeros((nb, 3), dtype=f64, device=dev)
     L = torch.zeros((nb, 3), dtype=f64, device=dev)
-    sizes = np.diff(s.body_offsets)
-    body_beads = torch.as_tensor(np.repeat(sizes > 1, sizes), device=dev)
 
-    def step(x, X, xn, Xn, k, guess, mlp=None):
-        bodies = ib.Bodies(off, X, Q)
-        opts = ib.make_opts(rtol=1e-6, guess=guess, mlp=mlp)
-        status, st = ib.ibpme_bd_advance(ctx, n, x, bodies, E0[0], opts, q[0], 1e-3, 1.0, 1.0, 4321, k, F, L, xn, Xn,
-                                         f_bead=fb)
-        if status != ib.IBPME_OK:
-            raise RuntimeError("trajectory solve did not converge")
-        return st
+    # training set: independent configurations of the trajectory's physics, solved from zero
+    t0 = time.perf_counter()
+    feat, targ, _ = W.collect(ib, ctx, (C.warm_start_training(50_000 + 10_007 * rank + k)
+                                        for k in range(TRAJ_TRAIN_SOLVES)))
+    t1 = time.perf_counter()
+    mlp, loss = W.train(ib, feat, targ, seed=5, epochs=24)
+    t2 = time.perf_counter()
+    training = {"solves": TRAJ_TRAIN_SOLVES, "rows": int(feat.shape[0]), "final_loss": loss,
+                "collect_s": t1 - t0, "train_s": t2 - t1, "epochs": 24}
+    del feat, targ
 
-    # training segment: zero-guess steps; converged charges -> (features, targets) of body beads
-    feats, targs = [], []
-    k = 0
-    for _ in range(12):
+    def run(c, guess, steps, warmup, precond=ib.IBPME_PRECOND_BODY, m=None):
+        """steps BD steps from the trajectory's start (after warmup untimed ones):
+        (ms per step, mean iterations, mean initial residual, worst final residual)."""
+        xa, Xa, xb, Xb = x.clone(), X.clone(), xn, Xn
         q.zero_()
-        step(x, X, xn, Xn, k, ib.IBPME_GUESS_ZERO)
-        f = torch.zeros((1, n, ib.IBPME_MLP_IN), dtype=torch.float32, device=dev)
-        tg = torch.zeros((1, n), dtype=torch.float32, device=dev)
-        ib.ibpme_features(ctx, n, x, ib.Bodies(off, X, Q), E0, 1, f, q, tg)
-        feats.append(f[0][body_beads])
-        targs.append(tg[0][body_beads])
-        x, xn, X, Xn, k = xn, x, Xn, X, k + 1
-    mlp = ib.ibpme_mlp_create(seed=5)
-    feat = torch.cat(feats).contiguous()
-    targ = torch.cat(targs).contiguous()
-    loss = ib.ibpme_mlp_train(mlp, feat.shape[0], feat, targ, batch=2048, epochs=60, lr=2e-3, seed=1)
-    x0, X0, k0 = x.clone(), X.clone(), k
+        its, init, worst = [], [], 0.0
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        for i in range(warmup + steps):
+            if guess == ib.IBPME_GUESS_ZERO:
+                q.zero_()
+            opts = ib.make_opts(rtol=1e-6, guess=guess, mlp=m, precond=precond)
+            if i >= warmup:
+                ev[i - warmup][0].record(stream)
+            status, st = ib.ibpme_bd_advance(c, n, xa, ib.Bodies(off, Xa, Q), E0[0], opts, q[0], 1e-3, 1.0, 1.0,
+                                             4321, i, F, L, xb, Xb, f_bead=fb)
+            if i >= warmup:
+                ev[i - warmup][1].record(stream)
+                its.append(st.iters)
+                init.append(st.init_rel_residual)
+                worst = max(worst, st.rel_residual)
+            if status != ib.IBPME_OK:
+                raise RuntimeError("trajectory solve did not converge")
+            xa, xb, Xa, Xb = xb, xa, Xb, Xa
+        torch.cuda.synchronize()
+        ms = float(np.sum([a.elapsed_time(b) for a, b in ev])) / steps
+        return {"steps_per_s": 1e3 / ms, "ms_per_step": ms, "iters_mean": float(np.mean(its)),
+                "init_rel_residual_mean": float(np.mean(init)), "worst_rel_residual": worst, "steps": steps}
 
     modes = {}
     for name, guess in (("zero", ib.IBPME_GUESS_ZERO), ("previous", ib.IBPME_GUESS_USER),
-                        ("learned", ib.IBPME_GUESS_LEARNED)):
-        x.copy_(x0)
-        X.copy_(X0)
-        k = k0
-        q.zero_()
-        for _ in range(args.warmup):
-            if guess == ib.IBPME_GUESS_ZERO:
-                q.zero_()
-            step(x, X, xn, Xn, k, guess, mlp)
-            x, xn, X, Xn, k = xn, x, Xn, X, k + 1
-        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-        its, init = [], []
-        torch.cuda.synchronize()
-        for i in range(args.steps):
-            if guess == ib.IBPME_GUESS_ZERO:
-                q.zero_()
-            ev[i][0].record(stream)
-            st = step(x, X, xn, Xn, k, guess, mlp)
-            ev[i][1].record(stream)
-            its.append(st.iters)
-            init.append(st.init_rel_residual)
-            x, xn, X, Xn, k = xn, x, Xn, X, k + 1
-        torch.cuda.synchronize()
-        ms = float(np.sum([a.elapsed_time(b) for a, b in ev]))
-        modes[name] = {"steps_per_s": args.steps / (ms / 1e3), "ms_per_step": ms / args.steps,
-                       "iters_mean": float(np.mean(its)), "init_rel_residual_mean": float(np.mean(init))}
+                        ("learned", ib.IBPME_GUESS_LEARNED), ("learned_step", ib.IBPME_GUESS_LEARNED_STEP)):
+        modes[name] = run(ctx, guess, args.steps, args.warmup, m=mlp)
     ib.ibpme_mlp_destroy(mlp)
     ib.pme_destroy(ctx)
+    # FP64 comparators on the same trajectory: the same algorithm in FP64 (body-block
+    # preconditioner, zero guess) and the plain FP64 solve (zero guess, no preconditioner)
+    ctx64 = make_ctx(ib.IBPME_FP64)
+    k64 = max(3, min(args.steps, 50))
+    fp64_same = run(ctx64, ib.IBPME_GUESS_ZERO, k64, 1)
+    kplain = max(3, min(args.steps, 10))
+    fp64_plain = run(ctx64, ib.IBPME_GUESS_ZERO, kplain, 1, precond=ib.IBPME_PRECOND_NONE)
+    ib.pme_destroy(ctx64)
     best = modes["learned"]
     return {
         "metric": "BD steps/s (induced-charge solve + forces + BD step)", "value": world * best["steps_per_s"],
@@ -869,8 +871,17 @@ def bench_trajectory(args, ib, torch, rank, world, local):
         "config": {"workload": TRAJ_WORKLOAD, "n_beads": n, "mesh": list(s.mesh),
                    "l2": "inputs resident; positions advance every step",
                    "parallelism": f"replicas x{world} (independent trajectories, no collective)"},
-        "guess_modes": modes, "training": {"samples": int(feat.shape[0]), "final_loss": loss, "solves": 12},
-        "cpu_baseline": None,
+        "guess_modes": modes, "fp64_same_algorithm": fp64_same, "fp64_plain": fp64_plain,
+        "speedup_vs_fp64_plain": best["steps_per_s"] / fp64_plain["steps_per_s"],
+        "speedup_vs_fp64_same_algorithm": best["steps_per_s"] / fp64_same["steps_per_s"],
+        "learned_vs_zero": best["steps_per_s"] / modes["zero"]["steps_per_s"],
+        "learned_step_vs_zero": modes["learned_step"]["steps_per_s"] / modes["zero"]["steps_per_s"],
+        "previous_vs_zero": modes["previous"]["steps_per_s"] / modes["zero"]["steps_per_s"],
+        "speedup_definition": ("steps/s of the learned-guess mixed-precision trajectory over steps/s of the same "
+                               "trajectory solved in FP64 from the zero guess, without preconditioner (plain) or "
+                               "with the body-block preconditioner (same algorithm); every solve to FP64 residual "
+                               "1e-6"),
+        "training": training, "cpu_baseline": None,
     }
 
 

@@ -133,7 +133,14 @@ typedef struct {
     const double* Q;           /* [N_b] net body charges (Eq. Q_tot) */
 } ibpme_bodies;
 
-enum { IBPME_GUESS_ZERO = 0, IBPME_GUESS_USER = 1, IBPME_GUESS_LEARNED = 2 };
+/* Initial guesses.  LEARNED: the learned warm start g (below).  LEARNED_STEP, for a
+ * sequence of calls on the same bodies (a trajectory): q_out holds on input the
+ * converged charges of the previous call and the guess is q + g(now) - g(previous),
+ * the learned change added to them, with g(previous) the learned guess that call
+ * left in the context; a call without one (the first, or after the body structure,
+ * bead count or field count changed) starts from g(now).  Both keep g(now) for the
+ * next call. */
+enum { IBPME_GUESS_ZERO = 0, IBPME_GUESS_USER = 1, IBPME_GUESS_LEARNED = 2, IBPME_GUESS_LEARNED_STEP = 3 };
 
 typedef struct {
     double rtol;        /* target relative residual of Eq. saddle, ||b - A u|| / ||b||; 0 -> 1e-6 */
@@ -142,7 +149,7 @@ typedef struct {
     int guess;          /* IBPME_GUESS_*; USER reads q_out as the initial charges.  The initial
                            body potentials are always the least-squares fit to the initial
                            charges (mean over each body of (M q)_j - r_j.E0) */
-    const void* mlp;    /* trained ibpme_mlp (IBPME_GUESS_LEARNED), else NULL */
+    const void* mlp;    /* trained ibpme_mlp (IBPME_GUESS_LEARNED[_STEP]), else NULL */
     int precision;      /* -1 = context precision, else IBPME_FP64 / IBPME_MIXED (mixed needs a
                            mixed context) */
     int precond;        /* IBPME_PRECOND_BODY (0, the default) or IBPME_PRECOND_NONE */
@@ -205,7 +212,7 @@ ibpme_status induced_charge_solve(ibpme_ctx* ctx, int n, const double* x, const 
  *   q_out, psi_out, S_out  as for induced_charge_solve over all n beads / N_b bodies
  *   stats       [n_configs] or NULL: per configuration, the worst right-hand side;
  *               iteration counts are those of the common loop
- * guess = IBPME_GUESS_LEARNED is not accepted here (IBPME_ERR_ARG).
+ * guess = IBPME_GUESS_LEARNED or IBPME_GUESS_LEARNED_STEP is not accepted here (IBPME_ERR_ARG).
  * Returns IBPME_ERR_NOT_CONVERGED if any configuration misses rtol. */
 ibpme_status induced_charge_solve_batch(ibpme_ctx* ctx, int n, const double* x, const ibpme_bodies* bodies,
                                         int n_configs, const int* cfg_bodies, const double* E0, int nrhs,
@@ -299,20 +306,40 @@ ibpme_status ibpme_bd_advance(ibpme_ctx* ctx, int n, const double* x, const ibpm
  *
  * A small network (IBPME_MLP_IN features -> 64 -> 64 -> 1, tanh, FP32) maps
  * per-bead features to a first guess of the induced charge of beads on
- * multi-bead bodies.  Features, for field E0 and the "fixed" charges (ions and
- * each body's net charge spread evenly over its beads) with potential psi_fix and
- * field E_fix from one PME evaluation; u = eps A (E0 + E_fix), A = 4 pi R^2 / N the
- * area per bead of a body of N beads and mean bead distance R from its reference
- * point, S the rms of |u| over the body, n = r/|r| the outward radial direction:
- *   f0 = u.n / S, f1 = |u - (u.n) n| / S, f2 = (psi_fix - <psi_fix>_body) 4 pi eps a / S,
- *   f3 = (Q/N) / S (clipped to +-10), f4 = |r|/R - 1, f5 = ln(N)/8, f6 = 10 a / R,
- *   f7 = eps A |E_fix| / S.
- * The guess is q = Q/N + S y, then shifted body by body so that sum q = Q exactly.
- * The network is trained on converged solves (ibpme_mlp_train); the solve uses it
- * with IBPME_GUESS_LEARNED and falls back to the zero guess (stats.fell_back = 1)
- * if its residual is not smaller than |b|.
+ * multi-bead bodies.  The features need no mesh evaluation: they come from the
+ * bodies' geometry, the field E0, the net charges and the free-space potential
+ * and field of the other bodies' fixed charges near the body, so the solve's
+ * first residual is the one evaluation a zero guess makes.
+ * For bead j of body b with N >= 2 beads, relative positions r from the body's
+ * reference point, R = mean |r| over the body, R_max = max |r|, A = 4 pi R^2 / N,
+ * h = sqrt(A):
+ *   d1, d6   distances from x_j to the nearest and the k-th nearest other bead of
+ *            the body, k = min(6, N - 1);
+ *   w_k      = exp(-|x_k - x_j|^2 / h^2) over the body's other beads,
+ *            m = sum w (x_k - x_j) / sum w, s2 = sum w |x_k - x_j|^2 / sum w,
+ *            C = sum w (x_k - x_j)(x_k - x_j)^T / sum w;
+ *   n        = the unit eigenvector of the smallest eigenvalue of C (the normal of
+ *            the plane that fits the neighbourhood best), signed so that n . r >= 0;
+ *            kappa = -2 (m . n) / s2 (1/R on a sphere, 1/(2 rho) on a cylinder);
+ *   phi, Es  potential and field at x_j of the fixed charges q_beta (an ion's own
+ *            charge, Q/N on a bead of another multi-bead body) of every bead beta
+ *            of another body within R_max + 6R of the body's reference point
+ *            (minimum image), with the regularised free-space kernel of Sec. II
+ *            (1/(4 pi eps r) for r >= 2a, (4a - r)/(16 pi eps a^2) below);
+ *   <.>      body means; S = eps A (|E0| + rms |Es|).
+ *   f0 = eps A (E0 . n) / S          f1 = eps A |E0 - (E0 . n) n| / S
+ *   f2 = eps A (r . E0 - <r . E0>) / (R S)
+ *   f3 = eps A (phi - <phi>) / (R S)  f4 = eps A (Es . n) / S
+ *   f5 = eps A |Es - (Es . n) n| / S  f6 = kappa R      f7 = |r| / R - 1
+ *   f8 = Q / (N S) clipped to +-10   f9 = 10 a / R      f10 = d1 / h
+ *   f11 = (d6 - d1) / h.
+ * Geometry is taken in FP32; body sums and scales in FP64.  The guess is
+ * q = Q/N + S y, then shifted body by body so that sum q = Q exactly (a body with
+ * S = 0 gets Q/N).  The network is trained on converged solves (ibpme_mlp_train);
+ * the solve uses it with IBPME_GUESS_LEARNED and falls back to the zero guess
+ * (stats.fell_back = 1) if its residual is not smaller than |b|.
  * Parameter layout (floats): W1[64][IN], b1[64], W2[64][64], b2[64], W3[64], b3. */
-#define IBPME_MLP_IN 8
+#define IBPME_MLP_IN 12
 #define IBPME_MLP_HIDDEN 64
 #define IBPME_MLP_NPARAM (IBPME_MLP_HIDDEN * IBPME_MLP_IN + IBPME_MLP_HIDDEN + IBPME_MLP_HIDDEN * IBPME_MLP_HIDDEN + \
                           IBPME_MLP_HIDDEN + IBPME_MLP_HIDDEN + 1)

@@ -31,6 +31,7 @@ IBPME_MIXED = 1
 IBPME_GUESS_ZERO = 0
 IBPME_GUESS_USER = 1
 IBPME_GUESS_LEARNED = 2
+IBPME_GUESS_LEARNED_STEP = 3
 IBPME_PRECOND_BODY = 0
 IBPME_PRECOND_NONE = 1
 
@@ -220,9 +221,9 @@ def pme_spread(ctx, n, x, q, nrhs, grid_out=None):
 
 
 IBPME_NOALLOC_MAX_BEADS = 262144
-IBPME_MLP_IN = 8
+IBPME_MLP_IN = 12
 IBPME_MLP_HIDDEN = 64
-IBPME_MLP_NPARAM = 64 * 8 + 64 + 64 * 64 + 64 + 64 + 1
+IBPME_MLP_NPARAM = 64 * IBPME_MLP_IN + 64 + 64 * 64 + 64 + 64 + 1
 
 
 def ibpme_mlp_create(seed=0):

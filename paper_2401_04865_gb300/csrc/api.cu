@@ -620,14 +620,14 @@ void solve_run(ibpme_ctx* c, int n, const double* x, const ibpme_bodies* bodies,
     a.restart = o.restart > 0 ? o.restart : 50;
     if (a.restart > 128) fail(IBPME_ERR_ARG, "restart must be <= 128");
     a.max_iter = o.max_iter > 0 ? o.max_iter : 3000;
-    if (o.guess == IBPME_GUESS_LEARNED && !o.mlp) fail(IBPME_ERR_ARG, "IBPME_GUESS_LEARNED needs opts->mlp");
-    if (o.guess != IBPME_GUESS_ZERO && o.guess != IBPME_GUESS_USER && o.guess != IBPME_GUESS_LEARNED)
-        fail(IBPME_ERR_ARG, "unknown guess mode");
-    if (o.guess == IBPME_GUESS_LEARNED && cfg_bodies) fail(IBPME_ERR_ARG, "a batched solve takes no learned guess");
+    const bool learned = o.guess == IBPME_GUESS_LEARNED || o.guess == IBPME_GUESS_LEARNED_STEP;
+    if (learned && !o.mlp) fail(IBPME_ERR_ARG, "a learned guess needs opts->mlp");
+    if (o.guess != IBPME_GUESS_ZERO && o.guess != IBPME_GUESS_USER && !learned) fail(IBPME_ERR_ARG, "unknown guess mode");
+    if (learned && cfg_bodies) fail(IBPME_ERR_ARG, "a batched solve takes no learned guess");
     if (o.precond != IBPME_PRECOND_BODY && o.precond != IBPME_PRECOND_NONE) fail(IBPME_ERR_ARG, "unknown precond");
     a.precond = o.precond == IBPME_PRECOND_BODY;
-    a.user_guess = o.guess == IBPME_GUESS_USER || o.guess == IBPME_GUESS_LEARNED;
-    a.learned = o.guess == IBPME_GUESS_LEARNED;
+    a.user_guess = o.guess == IBPME_GUESS_USER || learned;
+    a.learned = learned;
     const double* dx = static_cast<const double*>(stage_in(c, x, sizeof(double) * 3 * n, c->st_x));
     a.E0 = static_cast<const double*>(stage_in(c, E0, sizeof(double) * 3 * nrhs, c->st_E0));
     double* xw = static_cast<double*>(c->xw.ensure(sizeof(double) * 3 * n));
@@ -641,9 +641,12 @@ void solve_run(ibpme_ctx* c, int n, const double* x, const ibpme_bodies* bodies,
     call.os = stage_out(c, S_out, sizeof(double) * 3 * (size_t)nrhs * nb, c->st_out3);
     a.q = static_cast<double*>(call.oq.dev);
     a.psi = static_cast<double*>(call.op.dev);
-    if (a.learned) learned_guess(c, static_cast<const ibpme_mlp*>(o.mlp), n, xw, a.E0, nrhs, a.q);
+    if (a.learned)
+        learned_guess(c, static_cast<const ibpme_mlp*>(o.mlp), n, xw, a.E0, nrhs, a.q,
+                      o.guess == IBPME_GUESS_LEARNED_STEP);
     call.st.assign(ncfg, ibpme_solve_stats{});
     solve(c, a, call.st.data());
+    if (a.learned) learned_check(static_cast<const ibpme_mlp*>(o.mlp));   // the solve has synchronised
     if (S_out) body_dipoles(c, n, a.q, nrhs, static_cast<double*>(call.os.dev));
 }
 

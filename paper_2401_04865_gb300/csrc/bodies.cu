@@ -547,6 +547,8 @@ void bodies_upload(ibpme_ctx* c, int n, const ibpme_bodies* b, const double* xw,
         bd.host_off = off;
         bd.host_cfg = cb;
         bd.host_n = n;
+        bd.max_beads = 0;
+        for (int i = 0; i < nb; ++i) bd.max_beads = std::max(bd.max_beads, off[i + 1] - off[i]);
         ++bd.version;
     }
     bd.off_hash = off_hash ? *off_hash : 0;

@@ -262,6 +262,7 @@ struct BodyData {
     std::vector<int> uo_h, cfg_beads_h, cfg_bodies_h;
     std::vector<int> host_off, host_cfg;   // structure of the last upload (to skip rebuilding the lists)
     int host_n = -1;
+    int max_beads = 0;                     // beads of the largest body of the last upload
     unsigned long long version = 0;        // changes whenever the body structure changes
     unsigned long long off_hash = 0;       // hash of the offsets of the last upload (0: unknown)
 };
@@ -396,7 +397,10 @@ struct ibpme_ctx {
     // the FP64 mesh grid and the Krylov potentials hold the last solve's final FP64
     // residual evaluation (the field of the solution charges can be gathered from it)
     bool grid64_final = false;
-    ibp::DevBuf ml_feat, ml_scratch, ml_scales, ml_y;   // learned warm start
+    ibp::DevBuf ml_feat, ml_scratch, ml_scales, ml_y, ml_part;   // learned warm start
+    ibp::DevBuf ml_g, ml_gprev;               // [nrhs][n] learned guesses of this and of the last call
+    unsigned long long ml_prev_version = 0;   // body structure, bead and field count of ml_gprev
+    int ml_prev_n = -1, ml_prev_R = 0;
     cudaEvent_t ev_in = nullptr, ev_out = nullptr;
     ibp::StencilCache stencils;               // stencils of the current positions
     ibp::FreeSet fs;                          // the free beads on their own (Krylov operator)
@@ -479,7 +483,10 @@ void bd_step(ibpme_ctx* c, int n, const double* x, const double* f, const ibpme_
 void compute_features(ibpme_ctx* c, int n, const double* xw, const double* E0, int nrhs, float* feat,
                       DevBuf& scratch, DevBuf& scales);
 void learned_guess(ibpme_ctx* c, const ibpme_mlp* mlp, int n, const double* xw, const double* E0, int nrhs,
-                   double* q);
+                   double* q, bool step);
+// IBPME_ERR_TIMEOUT if the tensor-core pass of the last learned_guess gave up waiting
+// (call after a synchronisation of the stream that ran it).
+void learned_check(const ibpme_mlp* mlp);
 
 // ---- krylov.cu ----
 struct SolveArgs {

@@ -23,6 +23,7 @@ struct ibpme_mlp {
     int device = 0;
     ibp::DevBuf params, grad, m1, m2, perm, loss;
     ibp::DevBuf tc_err;   // set by the tensor-core forward if its mbarrier wait ran out
+    int* tc_err_host = nullptr;   // pinned copy of tc_err
     long long step = 0;
 };
 
@@ -267,19 +268,37 @@ __global__ void __launch_bounds__(kRows) mlp_forward_tc_kernel(int n, const floa
 
 // Tensor-core forward pass of n samples; returns IBPME_ERR_TIMEOUT (after the
 // kernel has freed its tensor memory) if a wait for the tensor cores ran out.
-void forward_tc(const ibpme_mlp* m, int n, const float* feat, float* out, cudaStream_t s) {
+// IBPME_ERR_TIMEOUT if the last tensor-core forward pass (already complete: the
+// caller has synchronised its stream) gave up waiting for the tensor cores.
+void forward_tc_check(const ibpme_mlp* m) {
+    if (m->tc_err_host && *m->tc_err_host) {
+        *m->tc_err_host = 0;
+        fail(IBPME_ERR_TIMEOUT, "tensor-core MLP forward: the wait for the tensor cores ran out");
+    }
+}
+
+// The tensor-core forward pass.  Its bounded waits report through a device flag;
+// with check the call synchronises and raises IBPME_ERR_TIMEOUT if it is set,
+// without it the flag is left for forward_tc_check (after a later synchronisation).
+void forward_tc(const ibpme_mlp* m, int n, const float* feat, float* out, cudaStream_t s, bool check = true) {
     if (n <= 0) return;
-    int* err = static_cast<int*>(const_cast<ibpme_mlp*>(m)->tc_err.ensure(sizeof(int)));
+    ibpme_mlp* mm = const_cast<ibpme_mlp*>(m);
+    int* err = static_cast<int*>(mm->tc_err.ensure(sizeof(int)));
     IBP_CUDA(cudaMemsetAsync(err, 0, sizeof(int), s));
     IBP_CUDA(cudaFuncSetAttribute(tc::mlp_forward_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)tc::kSmem));
     tc::mlp_forward_tc_kernel<<<div_up(n, tc::kRows), tc::kRows, tc::kSmem, s>>>(n, m->params.as<float>(), feat,
                                                                                     out, err);
     IBP_CHECK_LAUNCH();
-    int h = 0;
-    IBP_CUDA(cudaMemcpyAsync(&h, err, sizeof(int), cudaMemcpyDeviceToHost, s));
-    IBP_CUDA(cudaStreamSynchronize(s));
-    if (h) fail(IBPME_ERR_TIMEOUT, "tensor-core MLP forward: the wait for the tensor cores ran out");
+    if (!mm->tc_err_host) {
+        IBP_CUDA(cudaHostAlloc(reinterpret_cast<void**>(&mm->tc_err_host), sizeof(int), cudaHostAllocDefault));
+        *mm->tc_err_host = 0;
+    }
+    IBP_CUDA(cudaMemcpyAsync(mm->tc_err_host, err, sizeof(int), cudaMemcpyDeviceToHost, s));
+    if (check) {
+        IBP_CUDA(cudaStreamSynchronize(s));
+        forward_tc_check(m);
+    }
 }
 
 // ---- gradient of the mean squared error over a batch ----
@@ -414,77 +433,372 @@ void init_params(std::vector<float>& p, unsigned long long seed) {
 }
 
 // ---- features -----------------------------------------------------------------
-// Per multi-bead body (one warp): R = mean |r_ij|, the per-bead area
-// A = 4 pi R^2 / N, and, per right-hand side, S = rms over the body of
-// |u_ij|, u = eps A E_ext with E_ext = E0 + E_fix, and the mean of psi_fix.
-__global__ void body_scale_kernel(int nb, int n, int R, const int* __restrict__ off, const double* __restrict__ rel,
-                                  const double* __restrict__ E0, const double* __restrict__ Efix,
-                                  const double* __restrict__ psifix, double eps, double* __restrict__ bs) {
-    const int b = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+// Every feature comes from the body's own geometry, E0, the net charges and the
+// free-space potential and field of the other bodies' fixed charges near the body;
+// no mesh evaluation.
+constexpr int kBs = 6;    // per (rhs, body): R, A, S, <r.E0>, <phi>, h
+constexpr int kGeo = 8;   // per bead: d1, dk, n (3), kappa, unused (2)
+constexpr int kSrcThreads = 256;
+
+// Every bead as a source: wrapped position in FP32 and its fixed charge (an ion's
+// own charge, Q/N on a bead of a multi-bead body).
+__global__ void source_kernel(int n, const double* __restrict__ xw, const int* __restrict__ bead_body,
+                              const int* __restrict__ off, const double* __restrict__ Q, float4* __restrict__ src) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    const int b = bead_body[k];
+    src[k] = make_float4((float)xw[3 * k], (float)xw[3 * k + 1], (float)xw[3 * k + 2],
+                         (float)(Q[b] / (double)(off[b + 1] - off[b])));
+}
+
+// Per multi-bead body (one warp): R = mean |r|, R_max, the reference point wrapped
+// into the box with the source cutoff R_max + 6R (FP32), the relative positions as
+// floats.
+__global__ void body_geom_kernel(int nmb, const int* __restrict__ mb_body, const int* __restrict__ off,
+                                 const double* __restrict__ rel, const double* __restrict__ X, double Lx, double Ly,
+                                 double Lz, float4* __restrict__ rel32, double* __restrict__ Rb,
+                                 float4* __restrict__ bgeo) {
+    const int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
-    if (b >= nb) return;
-    const int s = off[b], e = off[b + 1], N = e - s;
-    double rs = 0.0;
-    for (int j = s + lane; j < e; j += 32)
-        rs += sqrt(rel[3 * j] * rel[3 * j] + rel[3 * j + 1] * rel[3 * j + 1] + rel[3 * j + 2] * rel[3 * j + 2]);
+    if (i >= nmb) return;
+    const int b = mb_body[i];
+    const int s = off[b], e = off[b + 1];
+    double rs = 0.0, rm = 0.0;
+    for (int j = s + lane; j < e; j += 32) {
+        const double x = rel[3 * j], y = rel[3 * j + 1], z = rel[3 * j + 2];
+        const double r = sqrt(x * x + y * y + z * z);
+        rs += r;
+        rm = fmax(rm, r);
+        rel32[j] = make_float4((float)x, (float)y, (float)z, 0.0f);
+    }
     rs = warp_sum(rs);
-    const double Rb = rs / N;
-    const double A = 4.0 * 3.14159265358979323846 * Rb * Rb / N;
-    for (int r = 0; r < R; ++r) {
-        double u2 = 0.0, pm = 0.0;
-        for (int j = s + lane; j < e; j += 32) {
-            const double* ef = Efix + ((size_t)r * n + j) * 3;
-            const double ux = E0[3 * r] + ef[0], uy = E0[3 * r + 1] + ef[1], uz = E0[3 * r + 2] + ef[2];
-            u2 += (ux * ux + uy * uy + uz * uz);
-            pm += psifix[(size_t)r * n + j];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) rm = fmax(rm, __shfl_xor_sync(0xffffffffu, rm, o));
+    if (lane == 0) {
+        const double R = rs / (e - s);
+        Rb[b] = R;
+        const double xb = X[3 * b] - Lx * floor(X[3 * b] / Lx), yb = X[3 * b + 1] - Ly * floor(X[3 * b + 1] / Ly),
+                     zb = X[3 * b + 2] - Lz * floor(X[3 * b + 2] / Lz);
+        bgeo[b] = make_float4((float)xb, (float)yb, (float)zb, (float)(rm + 6.0 * R));
+    }
+}
+
+// Partial phi and Es at the beads of one multi-bead body from one slice of the
+// candidate sources (grid.x: the body's place among the multi-bead bodies, grid.y:
+// chunks of 256 beads, grid.z: slices of the bead list): a source is a bead of
+// another body with a fixed charge whose minimum image lies within the body's cutoff
+// of its reference point; those of a 256-bead tile are compacted into shared memory
+// and summed with the regularised free-space kernel (FP32).  part[z][j] =
+// (phi, Es) before the 1/eps.
+__global__ void __launch_bounds__(kSrcThreads) body_field_kernel(
+    int n, int slice, const int* __restrict__ mb_body, const int* __restrict__ off,
+    const int* __restrict__ bead_body, const float4* __restrict__ src, const float4* __restrict__ rel32,
+    const float4* __restrict__ bgeo, float Lx, float Ly, float Lz, float a, float4* __restrict__ part) {
+    const int b = mb_body[blockIdx.x];
+    const int s = off[b], e = off[b + 1];
+    if (s + (int)blockIdx.y * kSrcThreads >= e) return;   // the whole block: no bead of this chunk
+    __shared__ float4 tile[kSrcThreads];
+    __shared__ int wcount[kSrcThreads / 32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int j = s + blockIdx.y * kSrcThreads + threadIdx.x;
+    const float4 g = bgeo[b];
+    const float4 rj = j < e ? rel32[j] : make_float4(0.f, 0.f, 0.f, 0.f);
+    const float c4 = 0.0795774715459476678f;                 // 1 / (4 pi)
+    const float c16 = 0.0198943678864869170f / (a * a);      // 1 / (16 pi a^2)
+    const float a2 = 2.0f * a;
+    float p = 0.f, ex = 0.f, ey = 0.f, ez = 0.f;
+    const int k0 = blockIdx.z * slice, k1 = min(n, k0 + slice);
+    for (int base = k0; base < k1; base += kSrcThreads) {
+        const int k = base + threadIdx.x;
+        bool ok = false;
+        float4 c = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (k < k1) {
+            const float4 sk = src[k];
+            if (sk.w != 0.f && bead_body[k] != b) {
+                float dx = sk.x - g.x, dy = sk.y - g.y, dz = sk.z - g.z;
+                dx -= Lx * rintf(dx / Lx);
+                dy -= Ly * rintf(dy / Ly);
+                dz -= Lz * rintf(dz / Lz);
+                if (dx * dx + dy * dy + dz * dz < g.w * g.w) {
+                    ok = true;
+                    c = make_float4(dx, dy, dz, sk.w);
+                }
+            }
         }
-        u2 = warp_sum(u2);
-        pm = warp_sum(pm);
-        if (lane == 0) {
-            double* o = bs + ((size_t)r * nb + b) * 4;
-            o[0] = Rb;
-            o[1] = A;
-            o[2] = eps * A * sqrt(u2 / N);   // S
-            o[3] = pm / N;
+        const unsigned m = __ballot_sync(0xffffffffu, ok);
+        if (lane == 0) wcount[w] = __popc(m);
+        __syncthreads();
+        int before = 0, total = 0;
+#pragma unroll
+        for (int i = 0; i < kSrcThreads / 32; ++i) {
+            const int cnt = wcount[i];
+            before += i < w ? cnt : 0;
+            total += cnt;
         }
+        if (ok) tile[before + __popc(m & ((1u << lane) - 1u))] = c;
+        __syncthreads();
+        if (j < e) {
+            for (int i = 0; i < total; ++i) {
+                const float4 q = tile[i];
+                const float vx = rj.x - q.x, vy = rj.y - q.y, vz = rj.z - q.z;
+                const float r = sqrtf(vx * vx + vy * vy + vz * vz);
+                float pot, gr;   // M(r) and -M'(r) / r
+                if (r >= a2) {
+                    const float ir = 1.0f / r;
+                    pot = c4 * ir;
+                    gr = pot * ir * ir;
+                } else {
+                    pot = c16 * (2.0f * a2 - r);
+                    gr = r > 0.f ? c16 / r : 0.f;
+                }
+                p += q.w * pot;
+                ex += q.w * gr * vx;
+                ey += q.w * gr * vy;
+                ez += q.w * gr * vz;
+            }
+        }
+        __syncthreads();
+    }
+    if (j < e) part[(size_t)blockIdx.z * n + j] = make_float4(p, ex, ey, ez);
+}
+
+// phi and Es of every bead of a multi-bead body: the slices' partial sums added in
+// slice order (the same result on every run), times 1/eps.
+__global__ void body_field_sum_kernel(int n, int slices, const int* __restrict__ bead_body,
+                                      const int* __restrict__ off, const float4* __restrict__ part, double inv_eps,
+                                      double* __restrict__ phi, double* __restrict__ Es) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n) return;
+    const int b = bead_body[j];
+    if (off[b + 1] - off[b] < 2) return;
+    float p = 0.f, ex = 0.f, ey = 0.f, ez = 0.f;
+    for (int z = 0; z < slices; ++z) {
+        const float4 v = part[(size_t)z * n + j];
+        p += v.x;
+        ex += v.y;
+        ey += v.z;
+        ez += v.w;
+    }
+    phi[j] = (double)p * inv_eps;
+    Es[3 * j] = (double)ex * inv_eps;
+    Es[3 * j + 1] = (double)ey * inv_eps;
+    Es[3 * j + 2] = (double)ez * inv_eps;
+}
+
+// Unit eigenvector of the smallest eigenvalue of the symmetric positive
+// semi-definite 3 x 3 matrix C = (c00, c11, c22, c01, c02, c12), in FP32 without
+// transcendental functions: the adjugate adj(C) has the same eigenvectors, with
+// eigenvalues the products of the other two of C's, so its dominant direction is
+// C's smallest one (also when C is singular, as for a flat neighbourhood).  Start
+// from adj(C)'s longest column and refine by six power steps (each shrinks the other
+// directions by lambda_min / lambda_mid).  false if adj(C) vanishes (the smallest
+// eigenvalue is not simple).
+__device__ bool smallest_eigvec(float c00, float c11, float c22, float c01, float c02, float c12, float* v) {
+    const float t = c00 + c11 + c22;
+    if (!(t > 0.f)) return false;
+    const float it = 1.0f / t;   // scale to trace 1
+    c00 *= it; c11 *= it; c22 *= it; c01 *= it; c02 *= it; c12 *= it;
+    const float a00 = c11 * c22 - c12 * c12, a11 = c00 * c22 - c02 * c02, a22 = c00 * c11 - c01 * c01;
+    const float a01 = c02 * c12 - c01 * c22, a02 = c01 * c12 - c02 * c11, a12 = c01 * c02 - c00 * c12;
+    const float n0 = a00 * a00 + a01 * a01 + a02 * a02, n1 = a01 * a01 + a11 * a11 + a12 * a12,
+                n2 = a02 * a02 + a12 * a12 + a22 * a22;
+    float x, y, z;
+    if (n0 >= n1 && n0 >= n2) {
+        x = a00; y = a01; z = a02;
+    } else if (n1 >= n2) {
+        x = a01; y = a11; z = a12;
+    } else {
+        x = a02; y = a12; z = a22;
+    }
+    float nn = x * x + y * y + z * z;
+    if (!(nn > 1e-30f)) return false;
+    for (int k = 0; k < 6; ++k) {
+        const float inv = rsqrtf(nn);
+        x *= inv; y *= inv; z *= inv;
+        const float u = a00 * x + a01 * y + a02 * z, w = a01 * x + a11 * y + a12 * z, q = a02 * x + a12 * y + a22 * z;
+        x = u; y = w; z = q;
+        nn = x * x + y * y + z * z;
+        if (!(nn > 1e-30f)) return false;
+    }
+    const float inv = rsqrtf(nn);
+    v[0] = x * inv;
+    v[1] = y * inv;
+    v[2] = z * inv;
+    return true;
+}
+
+// Per bead of a multi-bead body (one warp over the body's other beads): the
+// nearest and k-th nearest distances (k = min(6, N-1)), and the Gaussian
+// neighbourhood sums (weights exp(-d^2/h^2), h = sqrt(4 pi R^2 / N)) giving the
+// normal (smallest principal direction of the weighted neighbour offsets) and the
+// curvature, all in FP32.
+__global__ void bead_geom_kernel(int n, const int* __restrict__ bead_body, const int* __restrict__ off,
+                                 const float4* __restrict__ rel32, const double* __restrict__ Rb,
+                                 float* __restrict__ geo) {
+    const int j = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (j >= n) return;
+    const int b = bead_body[j];
+    const int s = off[b], e = off[b + 1], N = e - s;
+    if (N < 2) return;
+    const float h = sqrtf(12.566370614359172f / (float)N) * (float)Rb[b];
+    const float ih2 = 1.0f / (h * h);
+    const float4 rj = rel32[j];
+    constexpr int K = 6;
+    float best[K];
+#pragma unroll
+    for (int i = 0; i < K; ++i) best[i] = INFINITY;
+    // W, m (3), s2, C (6: xx yy zz xy xz yz)
+    float acc[11];
+#pragma unroll
+    for (int i = 0; i < 11; ++i) acc[i] = 0.f;
+    for (int k = s + lane; k < e; k += 32) {
+        if (k == j) continue;
+        const float4 rk = rel32[k];
+        const float dx = rk.x - rj.x, dy = rk.y - rj.y, dz = rk.z - rj.z;
+        const float d2 = dx * dx + dy * dy + dz * dz;
+        if (d2 < best[K - 1]) {   // insertion into this lane's sorted K smallest
+            float v = d2;
+#pragma unroll
+            for (int i = 0; i < K; ++i) {
+                if (v < best[i]) {
+                    const float tmp = best[i];
+                    best[i] = v;
+                    v = tmp;
+                }
+            }
+        }
+        const float w = __expf(-d2 * ih2);
+        acc[0] += w;
+        acc[1] += w * dx;
+        acc[2] += w * dy;
+        acc[3] += w * dz;
+        acc[4] += w * d2;
+        acc[5] += w * dx * dx;
+        acc[6] += w * dy * dy;
+        acc[7] += w * dz * dz;
+        acc[8] += w * dx * dy;
+        acc[9] += w * dx * dz;
+        acc[10] += w * dy * dz;
+    }
+#pragma unroll
+    for (int i = 0; i < 11; ++i) acc[i] = warp_sum(acc[i]);
+    // merge: K rounds, each removing the warp's smallest head (lowest lane on ties)
+    const int kk = N - 1 < K ? N - 1 : K;
+    float d1 = 0.f, dk = 0.f;
+    for (int i = 0; i < kk; ++i) {
+        float m = best[0];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) m = fminf(m, __shfl_xor_sync(0xffffffffu, m, o));
+        const unsigned who = __ballot_sync(0xffffffffu, best[0] == m);
+        if (lane == __ffs(who) - 1) {
+#pragma unroll
+            for (int q = 0; q < K - 1; ++q) best[q] = best[q + 1];
+            best[K - 1] = INFINITY;
+        }
+        if (i == 0) d1 = sqrtf(m);
+        if (i == kk - 1) dk = sqrtf(m);
+    }
+    if (lane == 0) {
+        const float iW = 1.0f / acc[0];
+        const float mx = acc[1] * iW, my = acc[2] * iW, mz = acc[3] * iW, s2 = acc[4] * iW;
+        float nv[3];
+        if (!smallest_eigvec(acc[5] * iW, acc[6] * iW, acc[7] * iW, acc[8] * iW, acc[9] * iW, acc[10] * iW, nv)) {
+            const float rr = sqrtf(rj.x * rj.x + rj.y * rj.y + rj.z * rj.z);
+            nv[0] = rr > 0.f ? rj.x / rr : 0.f;
+            nv[1] = rr > 0.f ? rj.y / rr : 0.f;
+            nv[2] = rr > 0.f ? rj.z / rr : 1.f;
+        }
+        if (nv[0] * rj.x + nv[1] * rj.y + nv[2] * rj.z < 0.f) {
+            nv[0] = -nv[0];
+            nv[1] = -nv[1];
+            nv[2] = -nv[2];
+        }
+        float* g = geo + (size_t)j * kGeo;
+        g[0] = d1;
+        g[1] = dk;
+        g[2] = nv[0];
+        g[3] = nv[1];
+        g[4] = nv[2];
+        g[5] = s2 > 0.f ? -2.0f * (mx * nv[0] + my * nv[1] + mz * nv[2]) / s2 : 0.f;
+        g[6] = 0.f;
+        g[7] = 0.f;
+    }
+}
+
+// Per (rhs, multi-bead body), one warp: <r.E0>, <phi>, rms |Es|, S.
+__global__ void body_stats_kernel(int nb, int nmb, int R, const int* __restrict__ mb_body,
+                                  const int* __restrict__ off, const double* __restrict__ rel,
+                                  const double* __restrict__ E0, const double* __restrict__ phi,
+                                  const double* __restrict__ Es, const double* __restrict__ Rb, double eps,
+                                  double* __restrict__ bs) {
+    const long long w = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (w >= (long long)nmb * R) return;
+    const int r = (int)(w / nmb), b = mb_body[(int)(w % nmb)];
+    const int s = off[b], e = off[b + 1], N = e - s;
+    double* o = bs + ((size_t)r * nb + b) * kBs;
+    const double ex = E0[3 * r], ey = E0[3 * r + 1], ez = E0[3 * r + 2];
+    double re = 0.0, pm = 0.0, e2 = 0.0;
+    for (int j = s + lane; j < e; j += 32) {
+        re += rel[3 * j] * ex + rel[3 * j + 1] * ey + rel[3 * j + 2] * ez;
+        pm += phi[j];
+        e2 += Es[3 * j] * Es[3 * j] + Es[3 * j + 1] * Es[3 * j + 1] + Es[3 * j + 2] * Es[3 * j + 2];
+    }
+    re = warp_sum(re) / N;
+    pm = warp_sum(pm) / N;
+    e2 = warp_sum(e2) / N;
+    if (lane == 0) {
+        const double Rv = Rb[b];
+        const double A = 4.0 * 3.14159265358979323846 * Rv * Rv / N;
+        o[0] = Rv;
+        o[1] = A;
+        o[2] = eps * A * (sqrt(ex * ex + ey * ey + ez * ez) + sqrt(e2));   // S
+        o[3] = re;
+        o[4] = pm;
+        o[5] = sqrt(A);
     }
 }
 
 __global__ void feature_kernel(int n, int nb, int R, const int* __restrict__ bead_body, const int* __restrict__ off,
                                const double* __restrict__ rel, const double* __restrict__ E0,
-                               const double* __restrict__ Efix, const double* __restrict__ psifix,
-                               const double* __restrict__ Q, const double* __restrict__ bs, double eps, double a,
-                               float* __restrict__ feat) {
+                               const double* __restrict__ phi, const double* __restrict__ Es,
+                               const float* __restrict__ geo, const double* __restrict__ Q,
+                               const double* __restrict__ bs, double eps, double a, float* __restrict__ feat) {
     const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (t >= (long long)n * R) return;
     const int r = (int)(t / n), j = (int)(t % n);
     const int b = bead_body[j];
     const int N = off[b + 1] - off[b];
     float* f = feat + (size_t)t * IN;
-    const double* o = bs + ((size_t)r * nb + b) * 4;
-    const double Rb = o[0], A = o[1], S = o[2], pm = o[3];
+    const double* o = bs + ((size_t)r * nb + b) * kBs;
+    const double Rv = o[0], A = o[1], S = o[2], re = o[3], pm = o[4], h = o[5];
     if (N < 2 || !(S > 0.0)) {
         for (int k = 0; k < IN; ++k) f[k] = 0.f;
         return;
     }
+    const float* g = geo + (size_t)j * kGeo;
+    const double nx = g[2], ny = g[3], nz = g[4];
+    const double ex = E0[3 * r], ey = E0[3 * r + 1], ez = E0[3 * r + 2];
+    const double sx = Es[3 * j], sy = Es[3 * j + 1], sz = Es[3 * j + 2];
     const double rx = rel[3 * j], ry = rel[3 * j + 1], rz = rel[3 * j + 2];
-    const double rr = sqrt(rx * rx + ry * ry + rz * rz);
-    const double nx = rr > 0 ? rx / rr : 0.0, ny = rr > 0 ? ry / rr : 0.0, nz = rr > 0 ? rz / rr : 0.0;
-    const double* ef = Efix + ((size_t)r * n + j) * 3;
-    const double ux = eps * A * (E0[3 * r] + ef[0]), uy = eps * A * (E0[3 * r + 1] + ef[1]),
-                 uz = eps * A * (E0[3 * r + 2] + ef[2]);
-    const double un = ux * nx + uy * ny + uz * nz;
-    const double tx = ux - un * nx, ty = uy - un * ny, tz = uz - un * nz;
-    const double fix = eps * A * sqrt(ef[0] * ef[0] + ef[1] * ef[1] + ef[2] * ef[2]);
+    const double en = ex * nx + ey * ny + ez * nz, sn = sx * nx + sy * ny + sz * nz;
+    const double tx = ex - en * nx, ty = ey - en * ny, tz = ez - en * nz;
+    const double ux = sx - sn * nx, uy = sy - sn * ny, uz = sz - sn * nz;
+    const double c = eps * A / S, cr = c / Rv;
     const double qb = Q[b] / N / S;
-    f[0] = (float)(un / S);
-    f[1] = (float)(sqrt(tx * tx + ty * ty + tz * tz) / S);
-    f[2] = (float)((psifix[(size_t)r * n + j] - pm) * 4.0 * 3.14159265358979323846 * eps * a / S);
-    f[3] = (float)(qb > 10.0 ? 10.0 : (qb < -10.0 ? -10.0 : qb));
-    f[4] = (float)(Rb > 0 ? rr / Rb - 1.0 : 0.0);
-    f[5] = (float)(log((double)N) / 8.0);
-    f[6] = (float)(Rb > 0 ? 10.0 * a / Rb : 0.0);
-    f[7] = (float)(fix / S);
+    f[0] = (float)(c * en);
+    f[1] = (float)(c * sqrt(tx * tx + ty * ty + tz * tz));
+    f[2] = (float)(cr * (rx * ex + ry * ey + rz * ez - re));
+    f[3] = (float)(cr * (phi[j] - pm));
+    f[4] = (float)(c * sn);
+    f[5] = (float)(c * sqrt(ux * ux + uy * uy + uz * uz));
+    f[6] = (float)((double)g[5] * Rv);
+    f[7] = (float)(sqrt(rx * rx + ry * ry + rz * rz) / Rv - 1.0);
+    f[8] = (float)(qb > 10.0 ? 10.0 : (qb < -10.0 ? -10.0 : qb));
+    f[9] = (float)(10.0 * a / Rv);
+    f[10] = (float)((double)g[0] / h);
+    f[11] = (float)(((double)g[1] - (double)g[0]) / h);
 }
 
 // training target y = (q - Q/N) / S on beads of multi-bead bodies (0 elsewhere)
@@ -496,7 +810,7 @@ __global__ void target_kernel(int n, int nb, int R, const int* __restrict__ bead
     const int r = (int)(t / n), j = (int)(t % n);
     const int b = bead_body[j];
     const int N = off[b + 1] - off[b];
-    const double S = bs[((size_t)r * nb + b) * 4 + 2];
+    const double S = bs[((size_t)r * nb + b) * kBs + 2];
     y[t] = (N > 1 && S > 0.0) ? (float)((q[t] - Q[b] / N) / S) : 0.f;
 }
 
@@ -510,19 +824,19 @@ __global__ void guess_from_net_kernel(int n, int nb, int R, const int* __restric
     const int r = (int)(t / n), j = (int)(t % n);
     const int b = bead_body[j];
     const int N = off[b + 1] - off[b];
-    const double S = bs[((size_t)r * nb + b) * 4 + 2];
+    const double S = bs[((size_t)r * nb + b) * kBs + 2];
     double v = Q[b] / N;
     if (N > 1 && S > 0.0) v += S * (double)y[t];
     q[t] = v;
 }
 
-// restore the constraint sum_j q_ij = Q_i of every body (uniform shift)
-__global__ void project_kernel(int nb, int n, int R, const int* __restrict__ off, const double* __restrict__ Q,
-                               double* __restrict__ q) {
+// restore the constraint sum_j q_ij = Q_i of every multi-bead body (uniform shift)
+__global__ void project_kernel(int nmb, int n, int R, const int* __restrict__ mb_body, const int* __restrict__ off,
+                               const double* __restrict__ Q, double* __restrict__ q) {
     const long long wid = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
-    if (wid >= (long long)nb * R) return;
-    const int r = (int)(wid / nb), b = (int)(wid % nb);
+    if (wid >= (long long)nmb * R) return;
+    const int r = (int)(wid / nmb), b = mb_body[(int)(wid % nmb)];
     const int s = off[b], e = off[b + 1];
     double sm = 0.0;
     for (int j = s + lane; j < e; j += 32) sm += q[(size_t)r * n + j];
@@ -531,70 +845,120 @@ __global__ void project_kernel(int nb, int n, int R, const int* __restrict__ off
     for (int j = s + lane; j < e; j += 32) q[(size_t)r * n + j] += shift;
 }
 
-__global__ void fixed_charge_kernel(int n, const int* __restrict__ bead_body, const int* __restrict__ off,
-                                    const double* __restrict__ Q, double* __restrict__ q) {
-    const int j = blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= n) return;
-    const int b = bead_body[j];
-    q[j] = Q[b] / (off[b + 1] - off[b]);
-}
-
 }  // namespace
 
 // Features of every bead for nrhs fields E0 [nrhs][3] (bodies already uploaded,
-// positions wrapped, context stream current).  The fixed charges -- ions and the
-// bodies' net charges spread evenly -- give psi_fix and E_fix by one PME
-// evaluation.  Also leaves the per-body scales in `scales` [nrhs][nb][4].
+// positions wrapped, context stream current).  Leaves the per-body scales in
+// `scales` [nrhs][nb][kBs].
 void compute_features(ibpme_ctx* c, int n, const double* xw, const double* E0, int nrhs, float* feat,
                       DevBuf& scratch, DevBuf& scales) {
     BodyData& bd = c->bodies;
     cudaStream_t s = c->stream;
-    double* qf = static_cast<double*>(scratch.ensure(sizeof(double) * (size_t)n * 5));
-    double* psif = qf + n;
-    double* Ef = psif + n;
-    fixed_charge_kernel<<<div_up(n, 256), 256, 0, s>>>(n, bd.bead_body.as<int>(), bd.off.as<int>(),
-                                                       bd.Q.as<double>(), qf);
+    // scratch: phi [n], Es [n][3], R_b [nb] doubles; src, rel32 [n] and bgeo [nb] float4; geo [n][kGeo] floats
+    auto up = [](size_t v) { return (v + 15) & ~(size_t)15; };
+    const size_t o_Es = up(sizeof(double) * (size_t)n), o_R = o_Es + up(sizeof(double) * 3 * (size_t)n);
+    const size_t o_src = o_R + up(sizeof(double) * (size_t)bd.nb), o_rel = o_src + sizeof(float4) * (size_t)n;
+    const size_t o_bg = o_rel + sizeof(float4) * (size_t)n, o_geo = o_bg + sizeof(float4) * (size_t)bd.nb;
+    char* base = static_cast<char*>(scratch.ensure(o_geo + sizeof(float) * kGeo * (size_t)n));
+    double* phi = reinterpret_cast<double*>(base);
+    double* Es = reinterpret_cast<double*>(base + o_Es);
+    double* Rb = reinterpret_cast<double*>(base + o_R);
+    float4* src = reinterpret_cast<float4*>(base + o_src);
+    float4* rel32 = reinterpret_cast<float4*>(base + o_rel);
+    float4* bgeo = reinterpret_cast<float4*>(base + o_bg);
+    float* geo = reinterpret_cast<float*>(base + o_geo);
+    const double* L = c->p.box;
+    source_kernel<<<div_up(n, 256), 256, 0, s>>>(n, xw, bd.bead_body.as<int>(), bd.off.as<int>(), bd.Q.as<double>(),
+                                                 src);
     IBP_CHECK_LAUNCH();
-    pme_apply(c, n, xw, qf, 1, c->have32 ? IBPME_MIXED : IBPME_FP64, psif, Ef, false);
-    // the fixed field does not depend on E0: broadcast it to every right-hand side
-    double* Efr = static_cast<double*>(c->E_r.ensure(sizeof(double) * 3 * (size_t)n * nrhs));
-    double* psir = static_cast<double*>(c->psi_r.ensure(sizeof(double) * (size_t)n * nrhs));
-    for (int r = 0; r < nrhs; ++r) {
-        IBP_CUDA(cudaMemcpyAsync(Efr + (size_t)r * 3 * n, Ef, sizeof(double) * 3 * n, cudaMemcpyDeviceToDevice, s));
-        IBP_CUDA(cudaMemcpyAsync(psir + (size_t)r * n, psif, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+    if (bd.nmb > 0) {
+        body_geom_kernel<<<div_up((long long)bd.nmb * 32, 128), 128, 0, s>>>(
+            bd.nmb, bd.mb_body.as<int>(), bd.off.as<int>(), bd.rel.as<double>(), bd.X.as<double>(), L[0], L[1], L[2],
+            rel32, Rb, bgeo);
+        IBP_CHECK_LAUNCH();
     }
-    double* bs = static_cast<double*>(scales.ensure(sizeof(double) * 4 * (size_t)bd.nb * nrhs));
-    body_scale_kernel<<<div_up((long long)bd.nb * 32, 128), 128, 0, s>>>(bd.nb, n, nrhs, bd.off.as<int>(),
-                                                                         bd.rel.as<double>(), E0, Efr, psir, c->eps,
-                                                                         bs);
+    if (bd.nmb > 0) {
+        // slices of the source list so that the grid fills the GPU about twice
+        const int chunks = div_up(bd.max_beads, kSrcThreads);
+        const long long cells = (long long)bd.nmb * chunks;
+        int slices = (int)std::min<long long>(64, std::max<long long>(1, (2 * 152 + cells - 1) / cells));
+        const int slice = div_up(div_up(n, slices), kSrcThreads) * kSrcThreads;
+        slices = div_up(n, slice);
+        float4* part = static_cast<float4*>(c->ml_part.ensure(sizeof(float4) * (size_t)slices * n));
+        const dim3 grid(bd.nmb, chunks, slices);
+        body_field_kernel<<<grid, kSrcThreads, 0, s>>>(n, slice, bd.mb_body.as<int>(), bd.off.as<int>(),
+                                                        bd.bead_body.as<int>(), src, rel32, bgeo, (float)L[0],
+                                                        (float)L[1], (float)L[2], (float)c->a, part);
+        IBP_CHECK_LAUNCH();
+        body_field_sum_kernel<<<div_up(n, 256), 256, 0, s>>>(n, slices, bd.bead_body.as<int>(), bd.off.as<int>(),
+                                                             part, 1.0 / c->eps, phi, Es);
+        IBP_CHECK_LAUNCH();
+    }
+    bead_geom_kernel<<<div_up((long long)n * 32, 128), 128, 0, s>>>(n, bd.bead_body.as<int>(), bd.off.as<int>(),
+                                                                    rel32, Rb, geo);
     IBP_CHECK_LAUNCH();
+    double* bs = static_cast<double*>(scales.ensure(sizeof(double) * kBs * (size_t)bd.nb * nrhs));
+    if (bd.nmb > 0) {
+        body_stats_kernel<<<div_up((long long)bd.nmb * nrhs * 32, 128), 128, 0, s>>>(
+            bd.nb, bd.nmb, nrhs, bd.mb_body.as<int>(), bd.off.as<int>(), bd.rel.as<double>(), E0, phi, Es, Rb, c->eps,
+            bs);
+        IBP_CHECK_LAUNCH();
+    }
     feature_kernel<<<div_up((long long)n * nrhs, 256), 256, 0, s>>>(n, bd.nb, nrhs, bd.bead_body.as<int>(),
-                                                                    bd.off.as<int>(), bd.rel.as<double>(), E0, Efr,
-                                                                    psir, bd.Q.as<double>(), bs, c->eps, c->a, feat);
+                                                                    bd.off.as<int>(), bd.rel.as<double>(), E0, phi, Es,
+                                                                    geo, bd.Q.as<double>(), bs, c->eps, c->a, feat);
     IBP_CHECK_LAUNCH();
 }
 
-// Learned initial charges q [nrhs][n] (constraint restored body by body).
+// q += g - gprev for every bead of a multi-bead body (the learned change added to
+// the previous charges); single beads keep q.
+__global__ void step_guess_kernel(long long len, int n, const int* __restrict__ bead_body, const int* __restrict__ off,
+                                  const double* __restrict__ g, const double* __restrict__ gprev,
+                                  double* __restrict__ q) {
+    const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (t >= len) return;
+    const int b = bead_body[(int)(t % n)];
+    if (off[b + 1] - off[b] > 1) q[t] += g[t] - gprev[t];
+}
+
+// Learned initial charges q [nrhs][n] (constraint restored body by body); with
+// step, q (in) holds the previous call's charges and gets the learned change.
 void learned_guess(ibpme_ctx* c, const ibpme_mlp* mlp, int n, const double* xw, const double* E0, int nrhs,
-                   double* q) {
+                   double* q, bool step) {
     DevBuf& feat = c->ml_feat;
     DevBuf& scratch = c->ml_scratch;
     DevBuf& scales = c->ml_scales;
     DevBuf& y = c->ml_y;
     BodyData& bd = c->bodies;
     cudaStream_t s = c->stream;
-    float* f = static_cast<float*>(feat.ensure(sizeof(float) * IN * (size_t)n * nrhs));
+    const long long len = (long long)n * nrhs;
+    const bool have_prev = c->ml_prev_n == n && c->ml_prev_R == nrhs && c->ml_prev_version == bd.version &&
+                           c->ml_gprev.bytes >= sizeof(double) * (size_t)len;
+    double* g = step && have_prev ? static_cast<double*>(c->ml_g.ensure(sizeof(double) * (size_t)len)) : q;
+    float* f = static_cast<float*>(feat.ensure(sizeof(float) * IN * (size_t)len));
     compute_features(c, n, xw, E0, nrhs, f, scratch, scales);
-    float* yy = static_cast<float*>(y.ensure(sizeof(float) * (size_t)n * nrhs));
-    forward_tc(mlp, n * nrhs, f, yy, s);
-    guess_from_net_kernel<<<div_up((long long)n * nrhs, 256), 256, 0, s>>>(n, bd.nb, nrhs, bd.bead_body.as<int>(),
-                                                                           bd.off.as<int>(), bd.Q.as<double>(),
-                                                                           scales.as<double>(), yy, q);
+    float* yy = static_cast<float*>(y.ensure(sizeof(float) * (size_t)len));
+    forward_tc(mlp, (int)len, f, yy, s, false);   // checked after the solve (which synchronises)
+    guess_from_net_kernel<<<div_up(len, 256), 256, 0, s>>>(n, bd.nb, nrhs, bd.bead_body.as<int>(), bd.off.as<int>(),
+                                                           bd.Q.as<double>(), scales.as<double>(), yy, g);
     IBP_CHECK_LAUNCH();
-    project_kernel<<<div_up((long long)bd.nb * nrhs * 32, 128), 128, 0, s>>>(bd.nb, n, nrhs, bd.off.as<int>(),
-                                                                             bd.Q.as<double>(), q);
-    IBP_CHECK_LAUNCH();
+    if (bd.nmb > 0) {
+        project_kernel<<<div_up((long long)bd.nmb * nrhs * 32, 128), 128, 0, s>>>(
+            bd.nmb, n, nrhs, bd.mb_body.as<int>(), bd.off.as<int>(), bd.Q.as<double>(), g);
+        IBP_CHECK_LAUNCH();
+    }
+    double* gp = static_cast<double*>(c->ml_gprev.ensure(sizeof(double) * (size_t)len));
+    if (g != q) {
+        step_guess_kernel<<<div_up(len, 256), 256, 0, s>>>(len, n, bd.bead_body.as<int>(), bd.off.as<int>(), g, gp, q);
+        IBP_CHECK_LAUNCH();
+    }
+    IBP_CUDA(cudaMemcpyAsync(gp, g, sizeof(double) * (size_t)len, cudaMemcpyDeviceToDevice, s));
+    c->ml_prev_n = n;
+    c->ml_prev_R = nrhs;
+    c->ml_prev_version = bd.version;
 }
+
+void learned_check(const ibpme_mlp* mlp) { forward_tc_check(mlp); }
 
 }  // namespace ibp
 
@@ -650,6 +1014,7 @@ IBP_API ibpme_status ibpme_mlp_create(ibpme_mlp** out, unsigned long long seed) 
 }
 
 IBP_API ibpme_status ibpme_mlp_destroy(ibpme_mlp* m) {
+    if (m && m->tc_err_host) cudaFreeHost(m->tc_err_host);
     delete m;
     return IBPME_OK;
 }

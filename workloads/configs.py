@@ -62,16 +62,17 @@ def assemble(name, bodies, ions, ion_charges, body_charges, box, a, eps, E0, **k
         offsets.append(offsets[-1] + b.shape[0])
         X.append(b.mean(axis=0))
         Q.append(qb)
-    for p, qi in zip(ions, ion_charges):
-        parts.append(p[None, :])
-        offsets.append(offsets[-1] + 1)
-        X.append(p)
-        Q.append(qi)
-    x = np.concatenate(parts) if parts else np.zeros((0, 3))
+    ions = np.asarray(ions, dtype=np.float64).reshape(-1, 3)
+    ni = ions.shape[0]
+    parts.append(ions)
+    offsets = np.concatenate([np.asarray(offsets, dtype=np.int64), offsets[-1] + 1 + np.arange(ni)])
+    X = np.concatenate([np.asarray(X, dtype=np.float64).reshape(-1, 3), ions])
+    Q = np.concatenate([np.asarray(Q, dtype=np.float64), np.asarray(ion_charges, dtype=np.float64).reshape(ni)])
+    x = np.concatenate(parts)
     return System(name=name, x=np.ascontiguousarray(x, dtype=np.float64),
                   body_offsets=np.asarray(offsets, dtype=np.int32),
-                  X=np.asarray(X, dtype=np.float64).reshape(-1, 3),
-                  Q=np.asarray(Q, dtype=np.float64),
+                  X=np.ascontiguousarray(X),
+                  Q=Q,
                   E0=np.asarray(E0, dtype=np.float64).reshape(-1, 3),
                   box=np.asarray(box, dtype=np.float64), a=float(a), eps=float(eps), **kw)
 
@@ -210,6 +211,81 @@ def config5_trajectory(n_ions: int = 20_000, seed: int = 1004, mesh=(192, 192, 1
     return assemble("eight_spheres_ions", bodies, ions, qi, [0.0] * 8, [L] * 3, 0.05,
                     eps_from_bjerrum(0.7), [[0.0, 0.0, 1.0]], mesh=tuple(mesh), tol=1e-6,
                     precision="mixed")
+
+
+def _segment_distance(p, c, axis, half, box):
+    """Distance from points p to the segment c +- half axis (minimum image)."""
+    d = p - c
+    d -= box * np.floor(d / box + 0.5)
+    t = np.clip(d @ axis, -half, half)
+    return np.linalg.norm(d - t[:, None] * axis[None, :], axis=1)
+
+
+_ICO3 = geo.icosphere(3)
+
+
+def warm_start_training(seed: int, L: float = 30.0, mesh=(192, 192, 192), max_ions: int = 20_000) -> System:
+    """One training configuration of the learned warm start: 2-8 bodies, each an
+    icosphere of radius 1 (642 beads) or a spherocylinder rod (600-900 beads,
+    aspect 2-4, radius 0.5-0.8), randomly oriented at random non-overlapping
+    positions; a random number (0..max_ions) of +-1 ions at least 2a = 0.1 from every
+    bead; a field of uniformly random direction and magnitude uniform in [0.1, 2];
+    net body charges 0 (half of the bodies) or uniform in [-3, 3].  Bead radius
+    0.05, l_B = 0.7, tol 1e-6, mixed precision: the physics of the eight-sphere
+    trajectory."""
+    rng = np.random.default_rng(seed)
+    box = np.array([L, L, L])
+    nb = int(rng.integers(2, 9))
+    bodies, placed, Q = [], [], []
+    while len(bodies) < nb:
+        if rng.random() < 0.5:
+            pts, half, rad = _ICO3.copy(), 0.0, 1.0
+        else:
+            rad, asp = rng.uniform(0.5, 0.8), rng.uniform(2.0, 4.0)
+            pts, half = geo.spherocylinder(int(rng.integers(600, 901)), asp, rad), rad * (asp - 1.0)
+        rot = geo.random_rotation(rng)
+        pts = pts @ rot.T
+        axis = rot @ np.array([0.0, 0.0, 1.0])
+        for _ in range(500):
+            c = rng.uniform(0.0, L, size=3)
+            ok = True
+            for (c2, _a2, h2, r2) in placed:
+                d = c - c2
+                d -= box * np.floor(d / box + 0.5)
+                if np.linalg.norm(d) < half + rad + h2 + r2 + 0.3:
+                    ok = False
+                    break
+            if ok:
+                placed.append((c, axis, half, rad))
+                bodies.append(pts + c)
+                Q.append(0.0 if rng.random() < 0.5 else float(rng.uniform(-3.0, 3.0)))
+                break
+        else:
+            break   # crowded: keep the bodies placed so far (at least two)
+    n_ions = int(rng.integers(0, max_ions + 1))
+    # ions anywhere at least 2a from every bead (the hard-sphere rule of the dynamics;
+    # the bead shells are permeable, so a trajectory also puts ions inside bodies)
+    from scipy.spatial import cKDTree
+    tree = cKDTree(np.mod(np.concatenate(bodies), L), boxsize=L)
+    ions = np.zeros((0, 3))
+    while ions.shape[0] < n_ions:
+        cand = rng.uniform(0.0, L, size=(2 * (n_ions - ions.shape[0]) + 16, 3))
+        near = np.zeros(len(cand), dtype=bool)
+        for (c, _axis, half, rad) in placed:
+            d = cand - c
+            d -= box * np.floor(d / box + 0.5)
+            near |= np.einsum("ij,ij->i", d, d) < (half + rad + 0.2) ** 2
+        ok = np.ones(len(cand), dtype=bool)
+        if near.any():
+            dist, _ = tree.query(cand[near])
+            ok[near] = dist >= 0.1
+        ions = np.concatenate([ions, cand[ok]])
+    ions = ions[:n_ions]
+    qi = np.where(np.arange(n_ions) % 2 == 0, 1.0, -1.0)
+    d = rng.normal(size=3)
+    E0 = d / np.linalg.norm(d) * rng.uniform(0.1, 2.0)
+    return assemble(f"warm_start_{seed}", bodies, ions, qi, Q, [L] * 3, 0.05, eps_from_bjerrum(0.7), [E0],
+                    mesh=tuple(mesh), tol=1e-6, precision="mixed")
 
 
 def small_system(seed: int = 7, n_bodies: int = 2, level: int = 1, n_ions: int = 6, L: float = 8.0,
