@@ -55,7 +55,7 @@ def buckets(sizes, ratio: float = 2.0, max_channels: int = 192, nrhs: int = 3, c
     return out
 
 
-PRECOND_MAX_BEADS = 1024   # bodies the library's body-block preconditioner covers
+PRECOND_MAX_BEADS = 8192   # bodies the library's body-block preconditioner covers
 
 
 def preconditioned(system) -> int:

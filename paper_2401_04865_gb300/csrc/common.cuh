@@ -79,9 +79,11 @@ struct DevBuf {
         }
         return p;
     }
-    // grow to b bytes keeping the content (stream-ordered copy)
+    // grow to at least b bytes keeping the content (stream-ordered copy); the
+    // capacity grows by half at least, so repeated growth copies O(final size)
     void* grow(size_t b, cudaStream_t s) {
         if (b <= bytes) return p;
+        if (b < bytes + bytes / 2) b = bytes + bytes / 2;
         void* q = nullptr;
         IBP_CUDA(cudaMalloc(&q, b));
         if (p) {
@@ -297,8 +299,8 @@ struct FreeSet {
 
 // Body-block preconditioner (precond.cu): inverses of the bodies' free-space
 // saddle blocks, cached per body shape for the life of the context.
-constexpr int kPrecondMaxBeads = 1024;                      // larger bodies are left unpreconditioned
-constexpr long long kPrecondCacheBytes = 2LL << 30;         // FP32 inverses kept at most
+constexpr int kPrecondMaxBeads = 8192;                      // larger bodies are left unpreconditioned
+constexpr long long kPrecondCacheBytes = 24LL << 30;        // FP32 inverses kept at most
 struct Precond {
     struct Shape {
         int nb;
@@ -309,8 +311,8 @@ struct Precond {
     long long used = 0, gused = 0;
     DevBuf minv, gvec, sinv, shape_off, shape_goff;   // per shape
     DevBuf pb_shape, pb_first, pb_psi, pb_n, plain;   // per solve: preconditioned bodies, identity unknowns
-    DevBuf moments, work, col;                        // set-up scratch
-    int npb = 0, nplain = 0, chunks = 0;
+    DevBuf moments, gj_d, gj_c, gj_r, gj_bad;          // set-up scratch (blocked Gauss-Jordan)
+    int npb = 0, nplain = 0, chunks = 0, maxn = 0;
     // steady state: the body structure the tables were laid out for, the shape of
     // every multi-bead body (-1: identity), and the moments of the last positions
     // (copied asynchronously into pinned memory, checked at the next solve)

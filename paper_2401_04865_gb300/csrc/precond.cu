@@ -2,7 +2,7 @@
 // (Sec. III.B, Eq. saddle), a solver choice outside the paper.
 //
 // Within one rigid body the saddle operator is dominated by the body's own
-// interactions.  For every multi-bead body of at most kPrecondMaxBeads beads
+// interactions.  For every multi-bead body of at most kPrecondMaxBeads (8,192) beads
 // the preconditioner applies the exact inverse of that body's free-space block
 //     P_b = [ -M_b  e ]      M_b(i, j) = M(|r_i - r_j|)   (Sec. II: 1/(4 pi eps r) for
 //           [  e^T  0 ]                                   r >= 2a, (4a - r)/(16 pi a^2 eps) below)
@@ -17,6 +17,8 @@
 // left to the Krylov iteration.
 #include "common.cuh"
 #include "dfloat.cuh"
+
+#include <cooperative_groups.h>
 
 #include <algorithm>
 #include <cmath>
@@ -76,53 +78,148 @@ __global__ void shape_moments_kernel(int nmb, const int* __restrict__ mb_body, c
     }
 }
 
-// M_b of one body from its beads' relative positions (row-major nb x nb)
+// M_b of one body from its beads' relative positions (row-major nb x nb, FP32)
 __global__ void block_matrix_kernel(int nb, const double* __restrict__ rel, double a, double eps,
-                                    double* __restrict__ A) {
+                                    float* __restrict__ A) {
     const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (t >= (long long)nb * nb) return;
     const int i = (int)(t / nb), j = (int)(t % nb);
     const double dx = rel[3 * i] - rel[3 * j], dy = rel[3 * i + 1] - rel[3 * j + 1],
                  dz = rel[3 * i + 2] - rel[3 * j + 2];
     const double r = sqrt(dx * dx + dy * dy + dz * dz);
-    A[t] = r >= 2.0 * a ? 1.0 / (4.0 * kPi * eps * r) : (4.0 * a - r) / (16.0 * kPi * a * a * eps);
+    A[t] = (float)(r >= 2.0 * a ? 1.0 / (4.0 * kPi * eps * r) : (4.0 * a - r) / (16.0 * kPi * a * a * eps));
 }
 
-// Gauss-Jordan inversion in place without pivoting (M_b is symmetric positive
-// definite), step k: scale row k, keep column k for the elimination.
-__global__ void gj_pivot_kernel(int nb, int k, double* __restrict__ A, double* __restrict__ colk) {
-    const double p = A[(size_t)k * nb + k];
-    __syncthreads();   // every thread has read the pivot before row k changes
-    for (int i = threadIdx.x; i < nb; i += blockDim.x) colk[i] = A[(size_t)i * nb + k];
-    __syncthreads();
-    const double ip = 1.0 / p;
-    for (int j = threadIdx.x; j < nb; j += blockDim.x) {
-        const double v = j == k ? 1.0 : A[(size_t)k * nb + j];
-        A[(size_t)k * nb + j] = v * ip;
+// Blocked Gauss-Jordan inversion in place, FP32, one cooperative launch per shape.
+// M_b is symmetric positive definite, so no pivoting.  For each panel p of kGjB
+// columns (diagonal block P):
+//   1. one block inverts P in shared memory (scalar Gauss-Jordan);
+//   2. the column panel C = A[:, p] is saved and the row panel becomes
+//      R = P^{-1} A[p, :] (R = P^{-1} on the panel's own columns);
+//   3. every other row i: A[i, j] = (j in p ? 0 : A[i, j]) - C[i, :] R[:, j]; the
+//      panel's rows take R.
+// Grid-wide barriers separate the phases (the launch is cooperative, so every
+// block is resident).  A non-positive pivot sets *bad and the result is unused.
+constexpr int kGjB = 32;           // panel width
+constexpr int kGjThreads = 256;
+constexpr int kGjTile = 64;        // output tile of the rank-kGjB update (4 x 4 per thread)
+
+__global__ void __launch_bounds__(kGjThreads) gj_blocked_kernel(int nb, float* __restrict__ A,
+                                                                 float* __restrict__ Dinv,
+                                                                 float* __restrict__ Cbuf,
+                                                                 float* __restrict__ Rbuf, int* __restrict__ bad) {
+    namespace cg = cooperative_groups;
+    cg::grid_group grid = cg::this_grid();
+    __shared__ float sD[kGjB][kGjB + 1];
+    __shared__ float colk[kGjB], rowk[kGjB];
+    __shared__ float sC[kGjTile][kGjB + 1];
+    __shared__ float sR[kGjB][kGjTile + 1];
+    const int tid = threadIdx.x;
+    const int ntiles = (nb + kGjTile - 1) / kGjTile;
+    for (int k0 = 0; k0 < nb; k0 += kGjB) {
+        const int B = min(kGjB, nb - k0);
+        // 1. the diagonal block's inverse (block 0)
+        if (blockIdx.x == 0) {
+            for (int e = tid; e < B * B; e += kGjThreads) sD[e / B][e % B] = A[(size_t)(k0 + e / B) * nb + k0 + e % B];
+            __syncthreads();
+            for (int k = 0; k < B; ++k) {
+                if (tid < B) {
+                    colk[tid] = sD[tid][k];
+                    rowk[tid] = sD[k][tid];
+                }
+                __syncthreads();
+                const float p = rowk[k];
+                if (!(p > 0.f) && tid == 0) *bad = 1;
+                const float ip = p > 0.f ? 1.0f / p : 0.f;
+                for (int e = tid; e < B * B; e += kGjThreads) {
+                    const int i = e / B, j = e % B;
+                    float v;
+                    if (i == k && j == k) v = ip;
+                    else if (i == k) v = rowk[j] * ip;
+                    else if (j == k) v = -colk[i] * ip;
+                    else v = sD[i][j] - colk[i] * rowk[j] * ip;
+                    sD[i][j] = v;
+                }
+                __syncthreads();
+            }
+            for (int e = tid; e < B * B; e += kGjThreads) Dinv[e] = sD[e / B][e % B];
+        }
+        grid.sync();
+        // 2. C = A[:, panel]; R = P^{-1} A[panel, :] (R = P^{-1} on the panel columns)
+        for (int e = tid; e < B * B; e += kGjThreads) sD[e / B][e % B] = Dinv[e];
+        __syncthreads();
+        for (long long e = blockIdx.x * (long long)kGjThreads + tid; e < (long long)nb * B;
+             e += (long long)gridDim.x * kGjThreads) {
+            const int i = (int)(e / B), c = (int)(e % B);
+            Cbuf[e] = A[(size_t)i * nb + k0 + c];
+        }
+        for (int j = blockIdx.x * kGjThreads + tid; j < nb; j += gridDim.x * kGjThreads) {
+            if (j >= k0 && j < k0 + B) {
+                for (int r = 0; r < B; ++r) Rbuf[(size_t)r * nb + j] = sD[r][j - k0];
+            } else {
+                float col[kGjB];
+                for (int c = 0; c < B; ++c) col[c] = A[(size_t)(k0 + c) * nb + j];
+                for (int r = 0; r < B; ++r) {
+                    float acc = 0.f;
+                    for (int c = 0; c < B; ++c) acc += sD[r][c] * col[c];
+                    Rbuf[(size_t)r * nb + j] = acc;
+                }
+            }
+        }
+        grid.sync();
+        // 3. rank-B update by 64 x 64 tiles: thread (ty, tx) owns rows ty + 16 u, columns tx + 16 v
+        const int ty = tid / 16, tx = tid % 16;
+        for (int t = blockIdx.x; t < ntiles * ntiles; t += gridDim.x) {
+            const int i0 = (t / ntiles) * kGjTile, j0 = (t % ntiles) * kGjTile;
+            for (int e = tid; e < kGjTile * kGjB; e += kGjThreads) {
+                const int r = e / kGjB, c = e % kGjB;
+                sC[r][c] = (i0 + r < nb && c < B) ? Cbuf[(size_t)(i0 + r) * B + c] : 0.f;
+                const int rr = e / kGjTile, cc = e % kGjTile;
+                sR[rr][cc] = (rr < B && j0 + cc < nb) ? Rbuf[(size_t)rr * nb + j0 + cc] : 0.f;
+            }
+            __syncthreads();
+            float acc[4][4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+#pragma unroll
+                for (int v = 0; v < 4; ++v) acc[u][v] = 0.f;
+            for (int c = 0; c < B; ++c) {
+                float cv[4], rv[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) cv[u] = sC[ty + 16 * u][c];
+#pragma unroll
+                for (int v = 0; v < 4; ++v) rv[v] = sR[c][tx + 16 * v];
+#pragma unroll
+                for (int u = 0; u < 4; ++u)
+#pragma unroll
+                    for (int v = 0; v < 4; ++v) acc[u][v] += cv[u] * rv[v];
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int i = i0 + ty + 16 * u;
+                if (i >= nb) continue;
+                const bool prow = i >= k0 && i < k0 + B;
+#pragma unroll
+                for (int v = 0; v < 4; ++v) {
+                    const int j = j0 + tx + 16 * v;
+                    if (j >= nb) continue;
+                    float* a = A + (size_t)i * nb + j;
+                    if (prow) *a = Rbuf[(size_t)(i - k0) * nb + j];
+                    else *a = ((j >= k0 && j < k0 + B) ? 0.f : *a) - acc[u][v];
+                }
+            }
+            __syncthreads();
+        }
+        grid.sync();
     }
 }
 
-__global__ void gj_eliminate_kernel(int nb, int k, double* __restrict__ A, const double* __restrict__ colk) {
-    const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (t >= (long long)nb * nb) return;
-    const int i = (int)(t / nb), j = (int)(t % nb);
-    if (i == k) return;
-    const double f = colk[i];
-    const double rk = A[(size_t)k * nb + j];
-    A[t] = (j == k ? 0.0 : A[t]) - f * rk;
-}
-
-// g = M^{-1} e (row sums), M^{-1} rounded to FP32
-__global__ void finish_shape_kernel(int nb, const double* __restrict__ A, float* __restrict__ minv,
-                                    float* __restrict__ g) {
+// g = M^{-1} e (row sums of the FP32 inverse, summed in FP64)
+__global__ void finish_shape_kernel(int nb, const float* __restrict__ minv, float* __restrict__ g) {
     __shared__ double sh[32];
     const int i = blockIdx.x;
     double acc = 0.0;
-    for (int j = threadIdx.x; j < nb; j += blockDim.x) {
-        const double v = A[(size_t)i * nb + j];
-        minv[(size_t)i * nb + j] = (float)v;
-        acc += v;
-    }
+    for (int j = threadIdx.x; j < nb; j += blockDim.x) acc += (double)minv[(size_t)i * nb + j];
     acc = warp_sum(acc);
     if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = acc;
     __syncthreads();
@@ -165,7 +262,7 @@ precond_apply_kernel(bool dir, int npb, int chunks, int nk, long long ustride, c
     // u of the body as double-float: the FP32 inverse times it accumulates on the FP32
     // pipes (an FP64 multiply-add and a conversion per entry made this kernel wait on
     // GB300's FP64 rate), to about 2^-44 of each row's magnitude
-    __shared__ float2 v[kPrecondMaxBeads];
+    extern __shared__ float2 v[];   // the body's u as hi + lo floats (maxn entries)
     __shared__ df sh[32];
     __shared__ double tpsi;
     const int r = blockIdx.y;
@@ -246,6 +343,32 @@ void queue_moments(ibpme_ctx* c) {
 }
 
 }  // namespace
+
+// A (nb x nb, FP32, symmetric positive definite) -> A^{-1} in place: one cooperative
+// launch of the blocked Gauss-Jordan kernel, as many blocks as can be resident
+// (at most one per 64 x 64 output tile).
+void invert_spd(ibpme_ctx* c, int nb, float* A) {
+    Precond& P = c->pre;
+    cudaStream_t s = c->stream;
+    float* Dinv = static_cast<float*>(P.gj_d.ensure(sizeof(float) * kGjB * kGjB));
+    float* Cbuf = static_cast<float*>(P.gj_c.ensure(sizeof(float) * (size_t)nb * kGjB));
+    float* Rbuf = static_cast<float*>(P.gj_r.ensure(sizeof(float) * (size_t)nb * kGjB));
+    int* bad = static_cast<int*>(P.gj_bad.ensure(sizeof(int)));
+    IBP_CUDA(cudaMemsetAsync(bad, 0, sizeof(int), s));
+    int dev = 0, sms = 0, per_sm = 0;
+    IBP_CUDA(cudaGetDevice(&dev));
+    IBP_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    IBP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, gj_blocked_kernel, kGjThreads, 0));
+    const int tiles = div_up(nb, kGjTile) * div_up(nb, kGjTile);
+    int blocks = std::max(1, std::min(per_sm * sms, std::max(tiles, div_up(nb, kGjThreads))));
+    void* args[] = {&nb, &A, &Dinv, &Cbuf, &Rbuf, &bad};
+    IBP_CUDA(cudaLaunchCooperativeKernel((const void*)gj_blocked_kernel, dim3(blocks), dim3(kGjThreads), args, 0, s));
+    IBP_CHECK_LAUNCH();
+    int hbad = 0;
+    IBP_CUDA(cudaMemcpyAsync(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost, s));
+    IBP_CUDA(cudaStreamSynchronize(s));
+    if (hbad) fail(IBPME_ERR_NONFINITE, "body block of %d beads is not positive definite", nb);
+}
 
 bool precond_prepare(ibpme_ctx* c) {
     Precond& P = c->pre;
@@ -338,18 +461,13 @@ bool precond_prepare(ibpme_ctx* c) {
             P.minv.grow(sizeof(float) * (size_t)P.used, s);
             P.gvec.grow(sizeof(float) * (size_t)P.gused, s);
             P.sinv.grow(sizeof(double) * (P.shapes.size() + 1), s);
-            double* A = static_cast<double*>(P.work.ensure(sizeof(double) * (size_t)nb * nb));
-            double* colk = static_cast<double*>(P.col.ensure(sizeof(double) * (size_t)nb));
+            float* A = P.minv.as<float>() + sp.off;   // inverted in place in the cache
             const double* rel = bd.rel.as<double>() + 3 * (size_t)off[mb_body[b]];
             const long long nn = (long long)nb * nb;
             block_matrix_kernel<<<div_up(nn, 256), 256, 0, s>>>(nb, rel, c->a, c->eps, A);
             IBP_CHECK_LAUNCH();
-            for (int k = 0; k < nb; ++k) {
-                gj_pivot_kernel<<<1, 256, 0, s>>>(nb, k, A, colk);
-                gj_eliminate_kernel<<<div_up(nn, 256), 256, 0, s>>>(nb, k, A, colk);
-            }
-            IBP_CHECK_LAUNCH();
-            finish_shape_kernel<<<nb, 128, 0, s>>>(nb, A, P.minv.as<float>() + sp.off, P.gvec.as<float>() + sp.goff);
+            invert_spd(c, nb, A);
+            finish_shape_kernel<<<nb, 128, 0, s>>>(nb, A, P.gvec.as<float>() + sp.goff);
             IBP_CHECK_LAUNCH();
             id = (int)P.shapes.size();
             shape_s_kernel<<<1, 256, 0, s>>>(nb, P.gvec.as<float>() + sp.goff, P.sinv.as<double>() + id);
@@ -396,6 +514,7 @@ bool precond_prepare(ibpme_ctx* c) {
     int maxn = 0;
     for (int v : pb_n) maxn = std::max(maxn, v);
     P.chunks = div_up(maxn, kRowsPerBlock);
+    P.maxn = maxn;
     P.prep_valid = true;
     queue_moments(c);
     return true;
@@ -405,7 +524,14 @@ void precond_apply(ibpme_ctx* c, int R, const double* u, long long ustride, cons
                    bool dir) {
     const Precond& P = c->pre;
     const int blocks = P.npb * P.chunks + div_up(P.nplain > 0 ? P.nplain : 1, kApplyThreads);
-    precond_apply_kernel<<<dim3(blocks, R), kApplyThreads, 0, c->stream>>>(
+    const size_t smem = sizeof(float2) * (size_t)std::max(1, P.maxn);
+    static bool attr = false;
+    if (!attr) {
+        IBP_CUDA(cudaFuncSetAttribute(precond_apply_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)(sizeof(float2) * kPrecondMaxBeads)));
+        attr = true;
+    }
+    precond_apply_kernel<<<dim3(blocks, R), kApplyThreads, smem, c->stream>>>(
         dir, P.npb, P.chunks, nk, ustride, jdev, P.pb_shape.as<int>(), P.pb_first.as<int>(), P.pb_psi.as<int>(),
         P.pb_n.as<int>(), P.shape_off.as<long long>(), P.shape_goff.as<long long>(), P.minv.as<float>(),
         P.gvec.as<float>(),

@@ -179,5 +179,5 @@ def test_buckets_never_mix_classes_and_preconditioned_flag():
     S = type("S", (), {})
     small, big = S(), S()
     small.body_offsets = np.array([0, 642, 643, 644])      # a sphere and two ions
-    big.body_offsets = np.array([0, 642, 642 + 1500])      # a sphere and a 1,500-bead body
+    big.body_offsets = np.array([0, 642, 642 + 9000])      # a sphere and a 9,000-bead body
     assert B.preconditioned(small) == 1 and B.preconditioned(big) == 0

@@ -609,19 +609,20 @@ def test_fp64_mesh_double_float_transforms_reach_tight_tolerance(cuda_lib):
 
 
 def test_preconditioner_skips_configurations_with_large_bodies(cuda_lib):
-    """In a batch, a configuration holding a body above the block limit (1,024
+    """In a batch, a configuration holding a body above the block limit (8,192
     beads) runs unpreconditioned while the others are preconditioned; every
     configuration still matches its single-system solve."""
     import torch
     from workloads import geometry as geo
     ib = cuda_lib
     L = 12.0
-    big = geo.ellipsoid(1400, [1.0, 1.5, 2.0]) + L / 2
+    big = geo.ellipsoid(8400, [1.0, 1.5, 2.0]) + L / 2
     small = geo.icosphere(2) * 0.8 + L / 2
     E0 = np.eye(3)
     a = 0.45 * min(geo.min_spacing(big), geo.min_spacing(small))
     parts = [C.assemble("big", [big], [], [], [0.0], [L] * 3, a, 1.0, E0, mesh=(64, 64, 64), tol=1e-6),
              C.assemble("small", [small], [], [], [0.0], [L] * 3, a, 1.0, E0, mesh=(64, 64, 64), tol=1e-6)]
+    assert parts[0].n > 8192
     s, cfg = C.stack(parts)
     ctx = context(ib, s, precision="fp64")
     try:
@@ -640,6 +641,38 @@ def test_preconditioner_skips_configurations_with_large_bodies(cuda_lib):
             assert status1 == ib.IBPME_OK
             assert rel_err(got[:, lo:lo + p.n], qs.cpu().numpy()) < 1e-6
             lo += p.n
+    finally:
+        ib.pme_destroy(ctx)
+
+
+def test_preconditioner_covers_bodies_of_thousands_of_beads(cuda_lib):
+    """Bodies of 1,500 and 3,000 beads (an ellipsoid and a rod, above the former
+    1,024-bead limit) get their block inverse from the blocked Gauss-Jordan kernel:
+    the preconditioned solve matches the unpreconditioned one and needs at most a
+    third of its iterations."""
+    import torch
+    from workloads import geometry as geo
+    ib = cuda_lib
+    L = 14.0
+    ell = geo.ellipsoid(1500, [1.0, 1.5, 2.0]) + [4.0, 4.0, 7.0]
+    rod = geo.spherocylinder(3000, 4.0, 0.8) + [10.0, 10.0, 7.0]
+    a = 0.45 * min(geo.min_spacing(ell), geo.min_spacing(rod))
+    s = C.assemble("large", [ell, rod], [], [], [0.5, -0.5], [L] * 3, a, 1.0, [[0.3, 0.2, 1.0]],
+                   mesh=(64, 64, 64), tol=1e-6)
+    ctx = context(ib, s, precision="mixed")
+    try:
+        out = {}
+        for mode in (ib.IBPME_PRECOND_BODY, ib.IBPME_PRECOND_NONE):
+            bodies = ib.Bodies(cuda(s.body_offsets.astype(np.int32)), cuda(s.X), cuda(s.Q))
+            q = torch.zeros((1, s.n), dtype=torch.float64, device="cuda")
+            status, st = ib.induced_charge_solve(ctx, s.n, cuda(s.x), bodies, cuda(s.E0), 1,
+                                                 ib.make_opts(rtol=1e-8, precond=mode), q)
+            torch.cuda.synchronize()
+            assert status == ib.IBPME_OK and st.rel_residual <= 1e-8
+            out[mode] = (st.iters, q.cpu().numpy())
+        it_body, it_none = out[ib.IBPME_PRECOND_BODY][0], out[ib.IBPME_PRECOND_NONE][0]
+        assert it_body * 3 <= it_none, (it_body, it_none)
+        assert rel_err(out[ib.IBPME_PRECOND_BODY][1], out[ib.IBPME_PRECOND_NONE][1]) < 1e-5
     finally:
         ib.pme_destroy(ctx)
 
