@@ -281,8 +281,21 @@ void pme_reserve(ibpme_ctx* c, int n, int nrhs, bool field) {
     c->scalars.ensure(sizeof(double) * (size_t)(nrhs * c->ncfg));
 }
 
+namespace {
+
+// out[r][free_idx[f]] = v[r][f]
+__global__ void free_scatter_kernel(int nf, int n, int R, const int* __restrict__ free_idx, const double* __restrict__ v,
+                                    double* __restrict__ out) {
+    const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (t >= (long long)nf * R) return;
+    const int r = (int)(t / nf), f = (int)(t % nf);
+    out[(size_t)r * n + free_idx[f]] = v[t];
+}
+
+}  // namespace
+
 void pme_apply(ibpme_ctx* c, int n, const double* xw, const double* q, int nrhs, int prec, double* psi,
-               double* E, bool near_ready, bool near32) {
+               double* E, bool near_ready, bool near32, const FreeMesh* fm) {
     c->grid64_final = false;   // the meshes are about to hold other charges
     if (!near_ready) near_build(c, n, xw, E != nullptr);
     const size_t m = (size_t)nrhs * n;
@@ -320,9 +333,19 @@ void pme_apply(ibpme_ctx* c, int n, const double* xw, const double* q, int nrhs,
         c->mesh32.transform(ch, c->stream);
         c->mesh32.gather(n, xw, nrhs, c->bcfg, pk, ek, c->stream, sc);
     } else {
-        c->mesh64.spread(n, xw, q, nrhs, c->bcfg, c->ncfg, c->stream, sc);
+        if (fm && fm->dq)
+            c->mesh64.spread(fm->nf, fm->xf, fm->dq, nrhs, fm->cfg, c->ncfg, c->stream, fm->sc, true);
+        else
+            c->mesh64.spread(n, xw, q, nrhs, c->bcfg, c->ncfg, c->stream, sc);
         c->mesh64.transform(ch, c->stream);
-        c->mesh64.gather(n, xw, nrhs, c->bcfg, pk, ek, c->stream, sc);
+        if (fm && fm->tmp && !E) {
+            c->mesh64.gather(fm->nf, fm->xf, nrhs, fm->cfg, fm->tmp, nullptr, c->stream, fm->sc);
+            free_scatter_kernel<<<div_up((long long)fm->nf * nrhs, 256), 256, 0, c->stream>>>(
+                fm->nf, n, nrhs, fm->free_idx, fm->tmp, pk);
+            IBP_CHECK_LAUNCH();
+        } else {
+            c->mesh64.gather(n, xw, nrhs, c->bcfg, pk, ek, c->stream, sc);
+        }
     }
     IBP_CUDA(cudaStreamWaitEvent(c->stream, c->ev_join, 0));
     if (m) {

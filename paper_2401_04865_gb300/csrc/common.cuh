@@ -167,15 +167,18 @@ struct Mesh {
     DevBuf green_df;   // the Green's table as (hi, lo) float pairs for the double-float transforms
     DevBuf grid_df;    // [rcap][G] (hi, lo) floats: the transformed grid of the double-float transforms
     bool potential_df = false;   // the last transform left the potential in grid_df (gathers read it)
+    unsigned long long writes = 0;   // spreads into grid so far (a kept grid is intact while this holds)
     void init(const MeshGeom& geom, int channels, double xi, double eta, double a, cudaStream_t s);
     void destroy();
     void ensure_channels(int ch);
     void plans(int ch, cudaStream_t s);   // every resource a transform of ch channels needs
     // bead_cfg (device, or NULL for one configuration) maps each bead to its configuration
     // sc: cached stencils of these positions, or NULL to derive them in the kernels
+    // accumulate: add to the grid as it is instead of zeroing it first
     void spread(int n, const double* xw, const double* q, int nrhs, const int* bead_cfg, int ncfg, cudaStream_t s,
-                const StencilCache* sc = nullptr);
-    void transform(int ch, cudaStream_t s);   // R2C, scale, C2R over ch channels
+                const StencilCache* sc = nullptr, bool accumulate = false);
+    // R2C, scale, C2R over ch channels; the double-float transforms leave grid as it was
+    void transform(int ch, cudaStream_t s);
     void gather(int n, const double* xw, int nrhs, const int* bead_cfg, double* psi, double* E, cudaStream_t s,
                 const StencilCache* sc = nullptr);
 };
@@ -458,8 +461,25 @@ void wrap_positions(ibpme_ctx* c, int n, const double* x, double* xw);
 // near32: real-space pass in FP32 too (only the inner operator of a mixed solve)
 // every buffer pme_apply needs for n beads and nrhs fields (before a stream capture)
 void pme_reserve(ibpme_ctx* c, int n, int nrhs, bool field);
+// The FP64 mesh pass on the free beads only (nf beads at xf, bead free_idx[f] of the
+// full list, configuration cfg[f] or NULL for one, stencils sc):
+//   dq != NULL: add the charges dq [nrhs][nf] to a grid that still holds an earlier
+//               spread (the caller guarantees it holds the spread of q - dq);
+//   tmp != NULL: gather the mesh potential at the free beads only (through tmp
+//               [nrhs][nf]); the other beads' results are then not written.
+struct FreeMesh {
+    int nf;
+    const double* xf;
+    const int* free_idx;
+    const int* cfg;
+    const StencilCache* sc;
+    const double* dq;
+    double* tmp;
+};
+// With fm (FP64 only) the mesh pass takes the free-bead forms above; the real-space
+// pass and the k = 0 term still take q on every bead.
 void pme_apply(ibpme_ctx* c, int n, const double* xw, const double* q, int nrhs, int prec,
-               double* psi, double* E, bool near_ready, bool near32 = false);
+               double* psi, double* E, bool near_ready, bool near32 = false, const FreeMesh* fm = nullptr);
 // Prepare the free-bead operator for the positions xw of the last near_build and nrhs
 // fields (after near_build, before any capture); false if it cannot serve this call.
 bool free_prepare(ibpme_ctx* c, const double* xw, int nrhs);

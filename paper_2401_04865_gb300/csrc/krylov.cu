@@ -38,6 +38,7 @@ struct Krylov {
     DevBuf V, H, cs, sn, g, y, w, x, d, r, rc, part, scal, active, qop, psi, psi_tot, qtot, Ax, norms, jdev;
     DevBuf pu, pt, pz;   // preconditioned operand, cycle update before and after P^{-1}
     DevBuf qc, psif;     // [R][nfree] charges and potentials of the free beads (free-bead operator)
+    DevBuf qkeep, dqf;   // charges whose spread the FP64 grid holds [R][n]; their change on the free beads
     // one captured Arnoldi iteration per mesh precision, replayed for every j
     cudaGraphExec_t exec[2] = {nullptr, nullptr};
     std::vector<long long> sig[2];
@@ -493,6 +494,18 @@ __global__ void compose_kernel(int n, int nk, int R, const int* __restrict__ bea
     qtot[t] = f >= 0 ? x[(size_t)r * nk + f] : Q[bead_body[j]];
 }
 
+// dqf[r][f] = qtot - qkeep at free bead f (the charges added since the kept FP64
+// grid was spread), and qkeep takes qtot there (ion charges do not change in a solve)
+__global__ void delta_kernel(int nfree, int n, int R, const int* __restrict__ free_idx,
+                             const double* __restrict__ qtot, double* __restrict__ qkeep, double* __restrict__ dqf) {
+    const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (t >= (long long)nfree * R) return;
+    const int r = (int)(t / nfree), f = (int)(t % nfree);
+    const size_t j = (size_t)r * n + free_idx[f];
+    dqf[t] = qtot[j] - qkeep[j];
+    qkeep[j] = qtot[j];
+}
+
 // Least-squares body potentials for given charges: Psi'_b = mean over the body's
 // beads of ((M q)_j - r_j.E0), the value that minimises the bead rows' residual.
 __global__ void fit_psi_kernel(int nmb, int nk, int n, int R, const int* __restrict__ mb_body,
@@ -632,6 +645,13 @@ struct Solver {
     bool dir = false;            // prescribed bead potentials (M q = a.bead_psi), not Eq. saddle
     std::vector<double> bnorm;   // |b| per system
     bool want_b = false;         // the next norms() call also fetches |b|
+    // The FP64 grid of this solve's last FP64 residual: the double-float transforms
+    // leave it intact, so the next FP64 residual spreads only the free beads' change
+    // (while no other spread has written the FP64 mesh since: the mesh counts its
+    // spreads, and an FP64 Krylov cycle, whose spreads run in graph replays, drops it)
+    bool keep = false;
+    unsigned long long keep_writes = 0;
+    bool ions_stale = false;   // the last FP64 residual gathered the mesh at the free beads only
 
     Solver(ibpme_ctx* c_, const SolveArgs& a_) : c(c_), k(c_->kry), a(a_) {
         n = a.n;
@@ -675,9 +695,9 @@ struct Solver {
         k->norms.ensure(sizeof(double) * 2 * S);   // |v|^2 per system, then |b|^2 per system
         k->jdev.ensure(sizeof(int));
         const size_t full = (size_t)R * n;
-        for (DevBuf* b : {&k->qop, &k->psi, &k->psi_tot, &k->qtot}) b->ensure(sizeof(double) * full);
+        for (DevBuf* b : {&k->qop, &k->psi, &k->psi_tot, &k->qtot, &k->qkeep}) b->ensure(sizeof(double) * full);
         const size_t fr = (size_t)R * (nfree > 0 ? nfree : 1);
-        for (DevBuf* b : {&k->qc, &k->psif}) b->ensure(sizeof(double) * fr);
+        for (DevBuf* b : {&k->qc, &k->psif, &k->dqf}) b->ensure(sizeof(double) * fr);
     }
 
     // y = A(prec) u for the reduced saddle operator; u[r] starts at u + r * ustride
@@ -903,7 +923,32 @@ struct Solver {
             compose_kernel<<<blocks_for((long long)n * R), 256, 0, s()>>>(n, nk, R, I(bd.bead_unk), I(bd.bead_body),
                                                                            bd.Q.as<double>(), D(k->x), D(k->qtot));
             IBP_CHECK_LAUNCH();
-            pme_apply(c, n, a.xw, D(k->qtot), R, prec, D(k->psi_tot), nullptr, true);
+            const bool fp64 = prec == IBPME_FP64;
+            const bool can_keep = fp64 && use_free && c->mesh64.df && nfree > 0;
+            const StencilCache* fsc = can_keep ? free_stencil_cache(c) : nullptr;
+            FreeMesh fm{nfree, c->fs.xf.as<double>(), I(bd.free_idx), ncfg > 1 ? bd.free_cfg.as<int>() : nullptr,
+                        fsc, nullptr, nullptr};
+            if (can_keep && fsc && keep && c->mesh64.writes == keep_writes) {
+                delta_kernel<<<blocks_for((long long)nfree * R), 256, 0, s()>>>(nfree, n, R, I(bd.free_idx), D(k->qtot),
+                                                                                 D(k->qkeep), D(k->dqf));
+                IBP_CHECK_LAUNCH();
+                fm.dq = D(k->dqf);
+                pme_apply(c, n, a.xw, D(k->qtot), R, prec, D(k->psi_tot), nullptr, true, false, &fm);
+                ions_stale = false;
+            } else {
+                // the initial residual of an FP64 start: a later FP64 residual follows (or
+                // is forced), so the mesh potential is gathered at the free beads only
+                const bool partial = can_keep && fsc && fit_psi;
+                fm.tmp = partial ? D(k->psif) : nullptr;
+                pme_apply(c, n, a.xw, D(k->qtot), R, prec, D(k->psi_tot), nullptr, true, false,
+                          partial ? &fm : nullptr);
+                ions_stale = partial;
+                keep = can_keep && fsc;
+                if (keep)
+                    IBP_CUDA(cudaMemcpyAsync(k->qkeep.p, k->qtot.p, sizeof(double) * (size_t)R * n,
+                                             cudaMemcpyDeviceToDevice, s()));
+            }
+            keep_writes = c->mesh64.writes;
             if (prec == IBPME_FP64) ++matvec64;
             c->grid64_final = prec == IBPME_FP64;
         }
@@ -930,6 +975,9 @@ struct Solver {
     void gmres(int prec, const double* rhs, double* dd, const std::vector<double>& target,
                const std::vector<double>& rn0) {
         const long long len = (long long)nk * R;
+        // FP64 iterations spread into the FP64 mesh inside graph replays, which the
+        // mesh's host-side write count does not see: the kept grid is gone
+        if (prec == IBPME_FP64) keep = false;
         IBP_CUDA(cudaMemsetAsync(dd, 0, sizeof(double) * len, s()));
         const double* res_vec = rhs;   // residual the next cycle starts from
         std::vector<double> rn = rn0;
@@ -1105,7 +1153,7 @@ struct Solver {
                                  outer, i, iters, relres(i), matvec64);
         }
         // the reported residual and the ions' potentials come from an FP64 evaluation
-        if (!res64) res = residual(IBPME_FP64);
+        if (!res64 || ions_stale) res = residual(IBPME_FP64);
         // outputs
         extract_kernel<<<blocks_for((long long)std::max(n, nb) * R), 256, 0, s()>>>(
             n, nb, nk, R, I(bd.bead_body), I(bd.off), I(bd.bead_unk), I(bd.body_unk), D(k->x), bd.Q.as<double>(),

@@ -1805,11 +1805,12 @@ void Mesh<T>::destroy() {
 
 template <typename T>
 void Mesh<T>::spread(int n, const double* xw, const double* q, int nrhs, const int* bead_cfg, int ncfg,
-                     cudaStream_t s, const StencilCache* sc) {
+                     cudaStream_t s, const StencilCache* sc, bool accumulate) {
     ProfScope ps(mesh_stage<T>(ST_SPREAD), s);
     ensure_channels(nrhs * ncfg);
     potential_df = false;
-    IBP_CUDA(cudaMemsetAsync(grid.p, 0, sizeof(T) * (size_t)g.G * nrhs * ncfg, s));
+    ++writes;
+    if (!accumulate) IBP_CUDA(cudaMemsetAsync(grid.p, 0, sizeof(T) * (size_t)g.G * nrhs * ncfg, s));
     if (n == 0) return;
     // Pair lanes while a bead's columns are split over warps (few beads); with one
     // warp per bead the row-walking kernel keeps its atomics of consecutive
