@@ -59,7 +59,8 @@ struct Krylov {
 
 namespace {
 
-constexpr int kChunk = 2048;   // vector elements per block in the multi-block Arnoldi kernels
+constexpr int kChunk = 512;   // vector elements per block in the multi-block Arnoldi kernels (FP64-pipe
+                              // bound: short chunks spread a 41,152-unknown system over 81 SMs)
 constexpr int kThreads = 256;
 
 // scal[s][*] slots
