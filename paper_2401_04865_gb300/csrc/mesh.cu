@@ -1568,6 +1568,24 @@ size_t tile_smem_bytes(const MeshGeom& g, int nrhs) {
     return sizeof(T) * (size_t)nrhs * E * E * E;
 }
 
+// Blocks of a tile kernel resident on the whole GPU at once (cached per kernel and
+// shared-memory size; the dynamic shared memory attribute is set by then).
+int tile_resident_blocks(const void* fn, size_t smem) {
+    static std::map<std::pair<const void*, size_t>, int> cache;
+    static std::mutex mu;
+    std::lock_guard<std::mutex> lock(mu);
+    const auto key = std::make_pair(fn, smem);
+    auto it = cache.find(key);
+    if (it != cache.end()) return it->second;
+    int dev = 0, sms = 0, per = 0;
+    IBP_CUDA(cudaGetDevice(&dev));
+    IBP_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    IBP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fn, kTileThreads, smem));
+    const int r = std::max(1, per) * std::max(1, sms);
+    cache.emplace(key, r);
+    return r;
+}
+
 // Opt-in to more than 48 KB of dynamic shared memory for every tiled kernel,
 // once per device (outside any stream capture: called when bins are built).
 template <typename K>
@@ -1599,6 +1617,36 @@ void tile_attrs() {
     tile_attrs_nr<T, 8>();
 }
 
+// The resident block counts of the tile kernels for this mesh's region size, queried
+// here (outside any stream capture) so that launches inside captures find them cached.
+template <typename T, int NR>
+void tile_resident_nr(const MeshGeom& g) {
+    const size_t b = tile_smem_bytes<T>(g, NR);
+    if (b > kTileSmemMax) return;
+    tile_resident_blocks((const void*)spread_tiles_kernel<T, NR, 0>, b);
+    tile_resident_blocks((const void*)gather_tiles_kernel<T, NR, true, 0>, b);
+    tile_resident_blocks((const void*)gather_tiles_kernel<T, NR, false, 0>, b);
+    if constexpr (NR <= 3) {
+        if (g.P == 9) {
+            tile_resident_blocks((const void*)spread_tiles_kernel<T, NR, 9>, b);
+            tile_resident_blocks((const void*)gather_tiles_kernel<T, NR, true, 9>, b);
+            tile_resident_blocks((const void*)gather_tiles_kernel<T, NR, false, 9>, b);
+        }
+    }
+}
+
+template <typename T>
+void tile_resident(const MeshGeom& g) {
+    tile_resident_nr<T, 1>(g);
+    tile_resident_nr<T, 2>(g);
+    tile_resident_nr<T, 3>(g);
+    tile_resident_nr<T, 4>(g);
+    tile_resident_nr<T, 5>(g);
+    tile_resident_nr<T, 6>(g);
+    tile_resident_nr<T, 7>(g);
+    tile_resident_nr<T, 8>(g);
+}
+
 void tile_attrs_once() {
     constexpr int kMaxDev = 64;
     static bool done[kMaxDev] = {};
@@ -1614,12 +1662,22 @@ void tile_attrs_once() {
 }
 
 template <typename T, int NR>
-void launch_tiles(bool spread, bool grad, const TileArgs& TA, int n, const double* q, T* grid, double* psi,
+void launch_tiles(bool spread, bool grad, const TileArgs& TA0, int n, const double* q, T* grid, double* psi,
                   double* E, cudaStream_t s) {
-    const size_t bytes = tile_smem_bytes<T>(TA.A.g, NR);
-    const int blocks = div_up(n, TA.chunk);
+    const size_t bytes = tile_smem_bytes<T>(TA0.A.g, NR);
     bool p9 = false;
-    if constexpr (NR <= 3) p9 = TA.A.g.P == 9;
+    if constexpr (NR <= 3) p9 = TA0.A.g.P == 9;
+    const void* fn;
+    if (spread) fn = p9 ? (const void*)spread_tiles_kernel<T, NR, 9> : (const void*)spread_tiles_kernel<T, NR, 0>;
+    else if (grad) fn = p9 ? (const void*)gather_tiles_kernel<T, NR, true, 9> : (const void*)gather_tiles_kernel<T, NR, true, 0>;
+    else fn = p9 ? (const void*)gather_tiles_kernel<T, NR, false, 9> : (const void*)gather_tiles_kernel<T, NR, false, 0>;
+    // beads per block so that the grid fills whole waves of resident blocks (a
+    // partial last wave runs at the cost of a full one)
+    TileArgs TA = TA0;
+    const int resident = tile_resident_blocks(fn, bytes);
+    const int waves = div_up(n, resident * kTileChunk);
+    TA.chunk = std::max(1, std::min(kTileChunk, div_up(n, waves * resident)));
+    const int blocks = div_up(n, TA.chunk);
     if (spread) {
         if constexpr (NR <= 3) {
             if (p9) {
@@ -1933,6 +1991,8 @@ void build_stencils(ibpme_ctx* c, StencilCache& b, int n, const double* xw, cons
             b.tiles = false;
         } else {
             tile_attrs_once();
+            tile_resident<float>(g);
+            tile_resident<double>(g);
             const int nk = (int)nkeys;
             int* count = static_cast<int*>(b.tile_count.ensure(sizeof(int) * nk));
             int* cursor = static_cast<int*>(b.tile_cursor.ensure(sizeof(int) * nk));
