@@ -882,7 +882,7 @@ PairArgs pair_args(const MeshGeom& g, const StencilCache& b, int n) {
 // holds their first stencil node; every stencil of a tile then lies inside one
 // region of E^3 nodes, E = kTileNodes + P - 1.  A block takes kTileChunk
 // consecutive sorted beads and splits them into runs of one tile.  A run of at
-// least tile_min<T>() beads is spread into the region in shared memory and the region
+// least kTileMin beads is spread into the region in shared memory and the region
 // is added to the grid once (one atomic per non-zero node); a gather stages the
 // region in shared memory and reads every stencil from there.  Beads of
 // shorter runs (isolated ions) use the direct per-bead path.
@@ -890,10 +890,9 @@ PairArgs pair_args(const MeshGeom& g, const StencilCache& b, int n) {
 constexpr int kTileChunk = 128;     // most sorted beads per block
 constexpr int kTileThreads = 256;
 constexpr int kTileWarps = kTileThreads / 32;
-constexpr int kTileMin = 8;         // beads of one tile that go through shared memory (FP64)
-constexpr int kTileMin32 = 24;      // the same for FP32, whose direct path has 16-byte atomics and loads
-template <typename T>
-__host__ __device__ constexpr int tile_min() { return sizeof(T) == 4 ? kTileMin32 : kTileMin; }
+constexpr int kTileMin = 24;        // beads of one tile that go through shared memory: a sphere's
+                                    // surface puts 5-20 beads in a tile, which the direct path
+                                    // serves faster than staging a whole region
 constexpr size_t kTileSmemMax = 192 * 1024;
 
 struct TileArgs {
@@ -1144,7 +1143,7 @@ spread_tiles_kernel(TileArgs TA, int n, const double* __restrict__ q, T* __restr
     const bool v4x = (g.N[0] & 3) == 0;
     for (int t = w; t < m; t += kTileWarps) {
         const int r = R.of[t];
-        if (R.start[r + 1] - R.start[r] < tile_min<T>()) {
+        if (R.start[r + 1] - R.start[r] < kTileMin) {
             if constexpr (sizeof(T) == 4 && PC > 0) {
                 if (v4x) {
                     spread_bead_v4<NR, PC>(A, n, TA.sorted[p0 + t], lane, q, reinterpret_cast<float*>(grid));
@@ -1158,7 +1157,7 @@ spread_tiles_kernel(TileArgs TA, int n, const double* __restrict__ q, T* __restr
     const int P = PC ? PC : g.P, P2 = P * P;
     for (int r = 0; r < R.count; ++r) {
         const int a = R.start[r], b = R.start[r + 1];
-        if (b - a < tile_min<T>()) continue;   // block-uniform
+        if (b - a < kTileMin) continue;   // block-uniform
         const int key = TA.key[p0 + a];
         const int tile = key % TA.ntiles, cfg = key / TA.ntiles;
         const int ox = (tile % TA.tn[0]) * kTileNodes;
@@ -1419,7 +1418,7 @@ gather_tiles_kernel(TileArgs TA, int n, const T* __restrict__ grid, double* __re
     const bool v4x = (g.N[0] & 3) == 0;
     for (int t = w; t < m; t += kTileWarps) {
         const int r = R.of[t];
-        if (R.start[r + 1] - R.start[r] < tile_min<T>()) {
+        if (R.start[r + 1] - R.start[r] < kTileMin) {
             if constexpr (sizeof(T) == 8) {
                 if (dfg) {
                     gather_bead_df<NR, GRAD, PC>(A, n, TA.sorted[p0 + t], lane, psi, E);
@@ -1446,7 +1445,7 @@ gather_tiles_kernel(TileArgs TA, int n, const T* __restrict__ grid, double* __re
     }
     for (int r = 0; r < R.count; ++r) {
         const int a = R.start[r], b = R.start[r + 1];
-        if (b - a < tile_min<T>()) continue;   // block-uniform
+        if (b - a < kTileMin) continue;   // block-uniform
         const int key = TA.key[p0 + a];
         const int tile = key % TA.ntiles, cfg = key / TA.ntiles;
         const int ox = (tile % TA.tn[0]) * kTileNodes;
