@@ -297,6 +297,7 @@ __global__ void free_scatter_kernel(int nf, int n, int R, const int* __restrict_
 void pme_apply(ibpme_ctx* c, int n, const double* xw, const double* q, int nrhs, int prec, double* psi,
                double* E, bool near_ready, bool near32, const FreeMesh* fm) {
     c->grid64_final = false;   // the meshes are about to hold other charges
+    c->field64_ready = false;
     if (!near_ready) near_build(c, n, xw, E != nullptr);
     const size_t m = (size_t)nrhs * n;
     pme_reserve(c, n, nrhs, E != nullptr);
@@ -344,7 +345,8 @@ void pme_apply(ibpme_ctx* c, int n, const double* xw, const double* q, int nrhs,
                 fm->nf, n, nrhs, fm->free_idx, fm->tmp, pk);
             IBP_CHECK_LAUNCH();
         } else {
-            c->mesh64.gather(n, xw, nrhs, c->bcfg, pk, ek, c->stream, sc);
+            c->mesh64.gather(n, xw, nrhs, c->bcfg, pk, ek ? ek : (fm ? fm->ek : nullptr), c->stream, sc);
+            c->field64_ready = !E && fm && fm->ek;
         }
     }
     IBP_CUDA(cudaStreamWaitEvent(c->stream, c->ev_join, 0));
@@ -382,6 +384,7 @@ void pme_apply_free(ibpme_ctx* c, const double* qc, int nrhs, int prec, double* 
     FreeSet& fs = c->fs;
     const int n = fs.nfree;
     c->grid64_final = false;   // the meshes are about to hold other charges
+    c->field64_ready = false;
     if (n == 0) return;
     double* pr = fs.psi_r.as<double>();
     double* pk = fs.psi_k.as<double>();
@@ -738,12 +741,15 @@ const double* solution_field(ibpme_ctx* c, int n, const double* xw, const double
         near_field(c, n, xw, q, 1, er);
     }
     IBP_CUDA(cudaEventRecord(c->ev_join, c->aux));
-    const StencilCache* sc = stencil_cache(c, n, xw);
-    c->mesh64.gather(n, xw, 1, nullptr, c->psi_k.as<double>(), ek, c->stream, sc);
+    if (!c->field64_ready) {   // the final residual did not gather the mesh field with its potential
+        const StencilCache* sc = stencil_cache(c, n, xw);
+        c->mesh64.gather(n, xw, 1, nullptr, c->psi_k.as<double>(), ek, c->stream, sc);
+    }
     IBP_CUDA(cudaStreamWaitEvent(c->stream, c->ev_join, 0));
     add_kernel<<<div_up(3LL * n, 256), 256, 0, c->stream>>>(3LL * n, er, ek, E);
     IBP_CHECK_LAUNCH();
     c->grid64_final = false;
+    c->field64_ready = false;
     return psi64;
 }
 
@@ -816,6 +822,7 @@ IBP_API ibpme_status ibpme_bd_advance(ibpme_ctx* c, int n, const double* x, cons
         // the solve: positions staged and wrapped, bodies uploaded and the near table
         // built once for the whole step
         SolveCall call;
+        call.a.want_field = true;   // the force pass follows
         solve_run(c, n, x, bodies, 1, nullptr, E0, 1, opts, q_io, psi_out, nullptr, call);
         const ibpme_status status = solve_status(call, t0, stats);
         if (status != IBPME_OK) {   // not converged: charges written, nothing moves

@@ -402,6 +402,8 @@ struct ibpme_ctx {
     // the FP64 mesh grid and the Krylov potentials hold the last solve's final FP64
     // residual evaluation (the field of the solution charges can be gathered from it)
     bool grid64_final = false;
+    // E_k holds the mesh field of that evaluation at every bead (gathered with its potential)
+    bool field64_ready = false;
     ibp::DevBuf ml_feat, ml_scratch, ml_scales, ml_y, ml_part;   // learned warm start
     ibp::DevBuf ml_g, ml_gprev;               // [nrhs][n] learned guesses of this and of the last call
     unsigned long long ml_prev_version = 0;   // body structure, bead and field count of ml_gprev
@@ -475,6 +477,7 @@ struct FreeMesh {
     const StencilCache* sc;
     const double* dq;
     double* tmp;
+    double* ek = nullptr;   // also gather the mesh field at every bead into ek [nrhs][n][3]
 };
 // With fm (FP64 only) the mesh pass takes the free-bead forms above; the real-space
 // pass and the k = 0 term still take q on every bead.
@@ -527,6 +530,10 @@ struct SolveArgs {
     // no unknowns (their rows become the identity with zero right-hand side), every
     // body must have two beads or more, and E0, Q and psi are not used.
     const double* bead_psi = nullptr;
+    // The caller needs the field of the solution next (the BD step): the FP64 residuals
+    // after the first also gather the mesh field into the context (one field, one
+    // configuration), so that the force pass does not gather the mesh again.
+    bool want_field = false;
 };
 void solve(ibpme_ctx* c, const SolveArgs& a, ibpme_solve_stats* st);
 // FP64 potentials [nrhs][n] of the last solve's final residual evaluation (its FP64

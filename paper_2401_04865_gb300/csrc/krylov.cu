@@ -929,6 +929,13 @@ struct Solver {
             const StencilCache* fsc = can_keep ? free_stencil_cache(c) : nullptr;
             FreeMesh fm{nfree, c->fs.xf.as<double>(), I(bd.free_idx), ncfg > 1 ? bd.free_cfg.as<int>() : nullptr,
                         fsc, nullptr, nullptr};
+            // a residual that may be the last one gathers the mesh field with the potential
+            // when the force pass follows (one field, one configuration)
+            const bool field = fp64 && a.want_field && R == 1 && ncfg == 1 && !(can_keep && fsc && fit_psi);
+            if (field) {
+                pme_reserve(c, n, 1, true);
+                fm.ek = c->E_k.as<double>();
+            }
             if (can_keep && fsc && keep && c->mesh64.writes == keep_writes) {
                 delta_kernel<<<blocks_for((long long)nfree * R), 256, 0, s()>>>(nfree, n, R, I(bd.free_idx), D(k->qtot),
                                                                                  D(k->qkeep), D(k->dqf));
@@ -942,7 +949,7 @@ struct Solver {
                 const bool partial = can_keep && fsc && fit_psi;
                 fm.tmp = partial ? D(k->psif) : nullptr;
                 pme_apply(c, n, a.xw, D(k->qtot), R, prec, D(k->psi_tot), nullptr, true, false,
-                          partial ? &fm : nullptr);
+                          partial || field ? &fm : nullptr);
                 ions_stale = partial;
                 keep = can_keep && fsc;
                 if (keep)
