@@ -194,6 +194,11 @@ struct NearList {
     DevBuf cell_of, cell_count, cell_start64, cell_start, cursor;
     DevBuf cell_beads;             // beads sorted by cell: row t of the pair table is bead cell_beads[t]
     DevBuf row_count, rowptr;
+    // the count pass also keeps each row's first ell_cap columns (rows padded to ell_cap,
+    // sized from the previous build's longest row); when no row is longer, the table
+    // is a copy of them and the second search pass is skipped
+    DevBuf ell, row_max;
+    int ell_cap = 0;
     DevBuf prow;                   // row (sorted position) of every pair
     DevBuf col, val, gfac;
     DevBuf pair32;                 // (col, FP32 val) per pair: inner operator of mixed-precision solves

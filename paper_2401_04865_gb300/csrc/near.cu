@@ -301,19 +301,47 @@ __device__ __forceinline__ void for_neighbours(int alpha, const double* __restri
 // The pair table is stored in the cell-sorted bead order: row t belongs to bead
 // cell_beads[t] and its columns are sorted positions too, so the rows a block
 // works on, and the charges they gather, sit close together in memory.
-__global__ void pair_count_kernel(int n, const double* __restrict__ xw, const float4* __restrict__ xf, PairConst k,
-                                  const int* __restrict__ cell_of,
-                                  const int* __restrict__ cell_start, const int* __restrict__ cell_beads,
-                                  int* __restrict__ row_count) {
+// The pairs of each row counted (row_count[t]), its first cap columns kept in
+// ell[t][0 .. cap) in the order pair_fill_kernel writes them, and the longest row
+// in *row_max.
+__global__ void pair_count_ell_kernel(int n, const double* __restrict__ xw, const float4* __restrict__ xf, PairConst k,
+                                      const int* __restrict__ cell_of, const int* __restrict__ cell_start,
+                                      const int* __restrict__ cell_beads, int cap, int* __restrict__ row_count,
+                                      int* __restrict__ ell, int* __restrict__ row_max) {
     const int t = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (t >= n) return;
     const int alpha = cell_beads[t];
-    int cnt = 0;
-    for_neighbours(alpha, xw, xf, k, cell_of, cell_start, cell_beads, lane,
-                   [&](int, int, bool within) { cnt += within ? 1 : 0; });
-    cnt = warp_sum(cnt);
-    if (lane == 0) row_count[t] = cnt;
+    int base = 0;
+    const unsigned lt = (1u << lane) - 1u;
+    int* row = ell + (size_t)t * cap;
+    for_neighbours(alpha, xw, xf, k, cell_of, cell_start, cell_beads, lane, [&](int, int slot_b, bool within) {
+        const unsigned m = __ballot_sync(0xffffffffu, within);
+        if (within) {
+            const int slot = base + __popc(m & lt);
+            if (slot < cap) row[slot] = slot_b;
+        }
+        base += __popc(m);
+    });
+    if (lane == 0) {
+        row_count[t] = base;
+        atomicMax(row_max, base);
+    }
+}
+
+// CSR table from the padded rows (every row at most cap long): one warp per row
+__global__ void ell_compact_kernel(int n, int cap, const int* __restrict__ ell, const long long* __restrict__ rowptr,
+                                   int* __restrict__ col, int* __restrict__ prow) {
+    const int t = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (t >= n) return;
+    const long long s = rowptr[t];
+    const int cnt = (int)(rowptr[t + 1] - s);
+    const int* row = ell + (size_t)t * cap;
+    for (int i = lane; i < cnt; i += 32) {
+        col[s + i] = row[i];
+        prow[s + i] = t;
+    }
 }
 
 // The columns of each row (the same walk and decisions as the count) and the row of
@@ -1531,18 +1559,28 @@ void near_build(ibpme_ctx* c, int n, const double* xw, bool need_grad) {
     int* row_count = static_cast<int*>(nl.row_count.ensure(sizeof(int) * (n + 1)));
     long long* rowptr = static_cast<long long*>(nl.rowptr.ensure(sizeof(long long) * (n + 1)));
     float4* xf = static_cast<float4*>(nl.xf.ensure(sizeof(float4) * (n + 1)));
+    int* row_max = static_cast<int*>(nl.row_max.ensure(sizeof(int)));
+    IBP_CUDA(cudaMemsetAsync(row_max, 0, sizeof(int), s));
+    // padded rows only while they stay small next to the table itself
+    const int cap = (long long)nl.ell_cap * n <= (1LL << 28) ? nl.ell_cap : 0;
+    int* ell = cap > 0 ? static_cast<int*>(nl.ell.ensure(sizeof(int) * (size_t)cap * n)) : nullptr;
     if (n > 0) {
         pos32_kernel<<<div_up(n, 256), 256, 0, s>>>(n, xw, xf);
         IBP_CHECK_LAUNCH();
-        pair_count_kernel<<<div_up((long long)n * 32, 128), 128, 0, s>>>(n, xw, xf, k, cell_of, cell_start,
-                                                                          cell_beads, row_count);
+        pair_count_ell_kernel<<<div_up((long long)n * 32, 128), 128, 0, s>>>(n, xw, xf, k, cell_of, cell_start,
+                                                                              cell_beads, cap, row_count, ell,
+                                                                              row_max);
         IBP_CHECK_LAUNCH();
     }
     scan_counts(row_count, rowptr, n, nl.scan_tmp, s);
-    long long* host_total = static_cast<long long*>(pinned_host(c, sizeof(long long)));
+    long long* host_total = static_cast<long long*>(pinned_host(c, 2 * sizeof(long long)));
     IBP_CUDA(cudaMemcpyAsync(host_total, rowptr + n, sizeof(long long), cudaMemcpyDeviceToHost, s));
+    IBP_CUDA(cudaMemcpyAsync(host_total + 1, row_max, sizeof(int), cudaMemcpyDeviceToHost, s));
     IBP_CUDA(cudaStreamSynchronize(s));
-    nl.npairs = *host_total;
+    nl.npairs = host_total[0];
+    const int longest = *reinterpret_cast<const int*>(host_total + 1);
+    const bool from_ell = n > 0 && cap > 0 && longest <= cap;
+    nl.ell_cap = ((longest + longest / 4 + 8) + 7) / 8 * 8;   // the next build's padding
     nl.have_grad = true;
     const size_t np = (size_t)(nl.npairs > 0 ? nl.npairs : 1);
     int* col = static_cast<int*>(nl.col.ensure(sizeof(int) * np));
@@ -1554,8 +1592,11 @@ void near_build(ibpme_ctx* c, int n, const double* xw, bool need_grad) {
     nl.qs.ensure(sizeof(double) * (size_t)(n + 1) * kMaxRhs);
     if (n > 0) {
         int* prow = static_cast<int*>(nl.prow.ensure(sizeof(int) * np));
-        pair_fill_kernel<<<div_up((long long)n * 32, 128), 128, 0, s>>>(n, xw, xf, k, cell_of, cell_start,
-                                                                         cell_beads, rowptr, col, prow);
+        if (from_ell)
+            ell_compact_kernel<<<div_up((long long)n * 32, 128), 128, 0, s>>>(n, cap, ell, rowptr, col, prow);
+        else
+            pair_fill_kernel<<<div_up((long long)n * 32, 128), 128, 0, s>>>(n, xw, xf, k, cell_of, cell_start,
+                                                                             cell_beads, rowptr, col, prow);
         IBP_CHECK_LAUNCH();
         if (nl.npairs > 0 && k.K > 0 && nl.npairs < (1LL << 31)) {
             // table pairs in double-float arithmetic, overlapping beads listed and valued exactly
