@@ -52,7 +52,10 @@ typedef enum {
     IBPME_ERR_OOM = 4,            /* device allocation failed */
     IBPME_ERR_NOT_CONVERGED = 5,  /* the Krylov solve hit max_iter; outputs hold the last iterate */
     IBPME_ERR_UNEQUAL_RADII = 6,  /* reserved: one bead radius per system (Sec. III.A) */
-    IBPME_ERR_TIMEOUT = 7,        /* a bounded device wait ran out */
+    IBPME_ERR_TIMEOUT = 7,        /* a bounded device wait ran out: the tensor cores of the
+                                     learned guess, or the tensor (TMA) copies of a tiled mesh
+                                     gather (reported after the gather's stream synchronised:
+                                     by that call, or by the context's next call) */
     IBPME_ERR_NONFINITE = 8       /* NaN/Inf in an input or in the iteration */
 } ibpme_status;
 

@@ -294,6 +294,14 @@ __global__ void free_scatter_kernel(int nf, int n, int R, const int* __restrict_
 
 }  // namespace
 
+void tma_check(ibpme_ctx* c) {
+    const int e32 = c->have32 ? c->mesh32.tma_failed() : 0;
+    const int e64 = c->mesh64.tma_failed();
+    if (e32 == 1 || e64 == 1) fail(IBPME_ERR_TIMEOUT, "a tensor copy of a tiled mesh gather was not complete in time");
+    if (e32 || e64)   // a check before the copy failed: the gather loaded the region itself
+        fail(IBPME_ERR_CUDA, "tensor copy of a tiled mesh gather refused by its check %d", e32 ? e32 : e64);
+}
+
 void pme_apply(ibpme_ctx* c, int n, const double* xw, const double* q, int nrhs, int prec, double* psi,
                double* E, bool near_ready, bool near32, const FreeMesh* fm) {
     c->grid64_final = false;   // the meshes are about to hold other charges
@@ -557,6 +565,7 @@ IBP_API ibpme_status pme_field(ibpme_ctx* c, int n, const double* x, const doubl
     return guard([&]() -> ibpme_status {
         if (!c) fail(IBPME_ERR_ARG, "ctx is NULL");
         DeviceScope ds(c->device);
+        tma_check(c);
         check_n(n);
         if (nrhs < 1 || nrhs > c->p.max_rhs) fail(IBPME_ERR_ARG, "nrhs %d outside 1..%d", nrhs, c->p.max_rhs);
         if (n > 0 && (!x || !q || !psi)) fail(IBPME_ERR_ARG, "x, q and psi are required");
@@ -573,7 +582,10 @@ IBP_API ibpme_status pme_field(ibpme_ctx* c, int n, const double* x, const doubl
                   false);
         finish_out(c, op);
         finish_out(c, oe);
-        if (op.host || oe.host) IBP_CUDA(cudaStreamSynchronize(c->stream));
+        if (op.host || oe.host) {
+            IBP_CUDA(cudaStreamSynchronize(c->stream));
+            tma_check(c);
+        }
         return IBPME_OK;
     });
 }
@@ -671,7 +683,9 @@ void solve_run(ibpme_ctx* c, int n, const double* x, const ibpme_bodies* bodies,
         learned_guess(c, static_cast<const ibpme_mlp*>(o.mlp), n, xw, a.E0, nrhs, a.q,
                       o.guess == IBPME_GUESS_LEARNED_STEP);
     call.st.assign(ncfg, ibpme_solve_stats{});
+    tma_check(c);   // a gather of an earlier call, finished by now
     solve(c, a, call.st.data());
+    tma_check(c);   // the solve's last residual has synchronised
     if (a.learned) learned_check(static_cast<const ibpme_mlp*>(o.mlp));   // the solve has synchronised
     if (S_out) body_dipoles(c, n, a.q, nrhs, static_cast<double*>(call.os.dev));
 }

@@ -168,6 +168,15 @@ struct Mesh {
     DevBuf grid_df;    // [rcap][G] (hi, lo) floats: the transformed grid of the double-float transforms
     bool potential_df = false;   // the last transform left the potential in grid_df (gathers read it)
     unsigned long long writes = 0;   // spreads into grid so far (a kept grid is intact while this holds)
+    // tensor map (CUtensorMap bytes) of the grid the tiled gathers stage their regions
+    // from with cp.async.bulk.tensor, for the buffer, channel count and element size below
+    alignas(64) unsigned char tmap[128] = {};
+    const void* tm_base = nullptr;
+    int tm_ch = 0, tm_es = 0, tm_E = 0;
+    bool tm_ok = false;
+    int* tma_err_host = nullptr;   // mapped host flag: a bounded wait for a tensor copy ran out
+    int* tma_err_dev = nullptr;
+    int tma_failed();              // read and clear the flag (after a synchronisation): 0, or its code
     void init(const MeshGeom& geom, int channels, double xi, double eta, double a, cudaStream_t s);
     void destroy();
     void ensure_channels(int ch);
@@ -468,6 +477,9 @@ void wrap_positions(ibpme_ctx* c, int n, const double* x, double* xw);
 // near32: real-space pass in FP32 too (only the inner operator of a mixed solve)
 // every buffer pme_apply needs for n beads and nrhs fields (before a stream capture)
 void pme_reserve(ibpme_ctx* c, int n, int nrhs, bool field);
+// IBPME_ERR_TIMEOUT if a tiled gather's bounded wait for its tensor copies ran out
+// since the last check (read after the gather's stream has synchronised)
+void tma_check(ibpme_ctx* c);
 // The FP64 mesh pass on the free beads only (nf beads at xf, bead free_idx[f] of the
 // full list, configuration cfg[f] or NULL for one, stencils sc):
 //   dq != NULL: add the charges dq [nrhs][nf] to a grid that still holds an earlier

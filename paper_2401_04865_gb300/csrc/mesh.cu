@@ -11,8 +11,12 @@
 #include "common.cuh"
 #include "dfloat.cuh"
 
+#include <cuda.h>   // CUtensorMap (tensor maps of the TMA region loads)
+#include <cudaTypedefs.h>
+
 #include <cmath>
 #include <cstdlib>
+#include <cstring>
 #include <mutex>
 
 namespace ibp {
@@ -894,8 +898,13 @@ constexpr int kTileMin = 24;        // beads of one tile that go through shared 
                                     // surface puts 5-20 beads in a tile, which the direct path
                                     // serves faster than staging a whole region
 constexpr size_t kTileSmemMax = 192 * 1024;
+constexpr size_t kTmaPad = 128;     // dynamic shared memory a gather adds to align its region
 
 struct TileArgs {
+    bool tma = false;       // the kernel's tensor map describes this grid: regions that do not
+                            // wrap are loaded with cp.async.bulk.tensor
+    int* tma_err = nullptr; // set when a bounded wait for a tensor copy ran out (1) or a check failed (2-6)
+    int tma_zext = 0;       // z extent of the tensor map (N_z x channels)
     PairArgs A;             // geometry and cached stencils (one warp per bead)
     const int* sorted;      // bead at each sorted position
     const int* key;         // configuration * ntiles + tile at each sorted position
@@ -904,6 +913,90 @@ struct TileArgs {
     int E;                  // region edge in nodes
     int chunk;              // sorted beads per block (<= kTileChunk)
 };
+
+// ---- TMA region loads ------------------------------------------------------------
+// A gather's region of E^3 nodes per channel, when it does not wrap around the box,
+// comes in as one 3-D tensor copy per channel (the grid described as N_x x N_y x
+// (N_z channels), channel c's region at z = c N_z + oz) into the block's shared
+// memory, completing on an mbarrier.  x offsets are multiples of 8 nodes and the box
+// edge E times the element size a multiple of 16 bytes (checked on the host).
+constexpr int kTmaWaitLimit = 1 << 22;   // polls of the mbarrier before the load is given up
+
+__device__ __forceinline__ unsigned smem_addr(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void tma_barrier_init(uint64_t* mbar) {
+    if (threadIdx.x == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(mbar)) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+}
+
+__device__ __forceinline__ bool tma_poll(uint64_t* mbar, unsigned phase) {
+    unsigned ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_addr(mbar)), "r"(phase)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait for the current phase; true when it completed.
+__device__ __forceinline__ bool tma_wait(uint64_t* mbar, unsigned phase) {
+    for (int it = 0; it < kTmaWaitLimit; ++it) {
+        if (tma_poll(mbar, phase)) return true;
+        if (it > 32) __nanosleep(64);
+    }
+    return false;
+}
+
+// Thread 0 checks and issues the nr copies (bytes each) of the region at (ox, oy,
+// z0 + c zstep) into dst + c bytes; every thread then waits.  Returns (block-uniform)
+// 1 when the region is in shared memory, -1 when a check failed before any copy was
+// issued (the code is recorded in *err, the caller loads the region itself: the
+// destination and the mbarrier aligned, x a multiple of 16 bytes, the boxes inside the
+// z extent, the tensor map aligned), 0 when the wait ran out (recorded; the copies are
+// waited for once more and the caller returns).
+__device__ int tma_region(const CUtensorMap* tm, unsigned char* dst, int nr, unsigned bytes, int es, int E, int ox,
+                          int oy, int z0, int zstep, int zext, uint64_t* mbar, unsigned& phase, int* err) {
+    __shared__ int verdict;
+    if (threadIdx.x == 0) {
+        int code = 0;
+        if ((smem_addr(dst) & 127u) != 0u) code = 2;
+        else if ((smem_addr(mbar) & 7u) != 0u) code = 3;
+        else if (((long long)ox * es) % 16 != 0 || ox < 0 || oy < 0 || z0 < 0) code = 4;
+        else if (z0 + (nr - 1) * zstep + E > zext) code = 5;
+        else if ((reinterpret_cast<unsigned long long>(tm) & 63ull) != 0ull) code = 6;
+        verdict = code;
+        if (code) {
+            if (err) atomicExch(err, code);
+        } else {
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // earlier reads of the region are done
+            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(mbar)),
+                         "r"(bytes * (unsigned)nr)
+                         : "memory");
+            for (int c = 0; c < nr; ++c)
+                asm volatile(
+                    "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, "
+                    "%4}], [%5];" ::"r"(smem_addr(dst + (size_t)c * bytes)),
+                    "l"(reinterpret_cast<unsigned long long>(tm)), "r"(ox), "r"(oy), "r"(z0 + c * zstep),
+                    "r"(smem_addr(mbar))
+                    : "memory");
+        }
+    }
+    __syncthreads();
+    if (verdict != 0) return -1;
+    const bool done = tma_wait(mbar, phase);
+    const bool bad = __syncthreads_or(!done);
+    if (bad) {
+        if (threadIdx.x == 0 && err) atomicExch(err, 1);
+        tma_wait(mbar, phase);   // the copies may still land: give them the time once more
+        __syncthreads();
+    }
+    phase ^= 1u;
+    return bad ? 0 : 1;
+}
 
 __global__ void tile_count_kernel(int n, const int4* __restrict__ start, int tn0, int tn1, int tn2,
                                   int* __restrict__ count, int* __restrict__ key) {
@@ -1130,7 +1223,8 @@ __device__ __forceinline__ void spread_bead_direct(const PairArgs& A, int n, int
 template <typename T, int NR, int PC>
 __global__ void __launch_bounds__(kTileThreads)
 spread_tiles_kernel(TileArgs TA, int n, const double* __restrict__ q, T* __restrict__ grid) {
-    extern __shared__ __align__(16) unsigned char tile_smem[];
+    extern __shared__ __align__(16) unsigned char tile_smem_base[];
+    unsigned char* tile_smem = tile_smem_base;
     T* reg = reinterpret_cast<T*>(tile_smem);
     __shared__ TileRuns R;
     const int p0 = blockIdx.x * TA.chunk;
@@ -1330,7 +1424,8 @@ __device__ __forceinline__ void gather_bead_direct(const PairArgs& A, int n, int
 // double-float arithmetic.
 template <int NR, bool GRAD, int PC>
 __device__ void gather_tiles_df(const TileArgs& TA, const TileRuns& R, int p0, int n, float2* __restrict__ reg,
-                                double* __restrict__ psi, double* __restrict__ E) {
+                                double* __restrict__ psi, double* __restrict__ E, const CUtensorMap* tm,
+                                uint64_t* mbar, unsigned& phase) {
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const PairArgs& A = TA.A;
     const MeshGeom& g = A.g;
@@ -1345,14 +1440,24 @@ __device__ void gather_tiles_df(const TileArgs& TA, const TileRuns& R, int p0, i
         const int oy = ((tile / TA.tn[0]) % TA.tn[1]) * kTileNodes;
         const int oz = (tile / (TA.tn[0] * TA.tn[1])) * kTileNodes;
         const float2* gr = A.gdf + (size_t)cfg * NR * g.G;
-        for (int u = threadIdx.x; u < NR * E3; u += kTileThreads) {
-            const int c = u / E3, rem = u - c * E3;
-            const int z = rem / E2, y = (rem / Ee) % Ee, x = rem % Ee;
-            const size_t off = ((size_t)wrap_once(oz + z, g.N[2]) * g.N[1] + wrap_once(oy + y, g.N[1])) * g.N[0] +
-                               wrap_once(ox + x, g.N[0]);
-            reg[u] = __ldg(gr + (size_t)c * g.G + off);
+        const bool inside = ox + Ee <= g.N[0] && oy + Ee <= g.N[1] && oz + Ee <= g.N[2];
+        int got = -1;
+        if (TA.tma && inside) {
+            got = tma_region(tm, reinterpret_cast<unsigned char*>(reg), NR, (unsigned)(sizeof(float2) * E3),
+                             (int)sizeof(float2), Ee, ox, oy, cfg * NR * g.N[2] + oz, g.N[2], TA.tma_zext, mbar, phase,
+                             TA.tma_err);
+            if (got == 0) return;
         }
-        __syncthreads();
+        if (got < 0) {
+            for (int u = threadIdx.x; u < NR * E3; u += kTileThreads) {
+                const int c = u / E3, rem = u - c * E3;
+                const int z = rem / E2, y = (rem / Ee) % Ee, x = rem % Ee;
+                const size_t off = ((size_t)wrap_once(oz + z, g.N[2]) * g.N[1] + wrap_once(oy + y, g.N[1])) * g.N[0] +
+                                   wrap_once(ox + x, g.N[0]);
+                reg[u] = __ldg(gr + (size_t)c * g.G + off);
+            }
+            __syncthreads();
+        }
         for (int t = a + w; t < b; t += kTileWarps) {
             const int bead = TA.sorted[p0 + t];
             const int4 st = A.start[bead];
@@ -1403,10 +1508,21 @@ __device__ void gather_tiles_df(const TileArgs& TA, const TileRuns& R, int p0, i
 
 template <typename T, int NR, bool GRAD, int PC>
 __global__ void __launch_bounds__(kTileThreads)
-gather_tiles_kernel(TileArgs TA, int n, const T* __restrict__ grid, double* __restrict__ psi, double* __restrict__ E) {
-    extern __shared__ __align__(16) unsigned char tile_smem[];
+gather_tiles_kernel(TileArgs TA, int n, const T* __restrict__ grid, double* __restrict__ psi, double* __restrict__ E,
+                    const __grid_constant__ CUtensorMap tmap) {
+    extern __shared__ __align__(16) unsigned char tile_smem_base[];
+    // the region starts at the first 128-byte boundary of the dynamic shared memory
+    // (a tensor copy's destination must be 128-byte aligned; kTmaPad bytes are reserved)
+    unsigned char* tile_smem = tile_smem_base + ((128u - (smem_addr(tile_smem_base) & 127u)) & 127u);
     T* reg = reinterpret_cast<T*>(tile_smem);
     __shared__ TileRuns R;
+    __shared__ uint64_t tma_bar;
+    unsigned phase = 0;
+    if (TA.tma && (smem_addr(tile_smem) & 127u) != 0u) {   // cannot happen: recorded, plain loads instead
+        if (threadIdx.x == 0 && TA.tma_err) atomicExch(TA.tma_err, 2);
+        TA.tma = false;
+    }
+    if (TA.tma) tma_barrier_init(&tma_bar);   // block-uniform
     const int p0 = blockIdx.x * TA.chunk;
     const int m = min(TA.chunk, n - p0);
     tile_runs(TA.key, p0, m, R);
@@ -1439,7 +1555,8 @@ gather_tiles_kernel(TileArgs TA, int n, const T* __restrict__ grid, double* __re
     const int P = PC ? PC : g.P, P2 = P * P;
     if constexpr (sizeof(T) == 8) {
         if (dfg) {
-            gather_tiles_df<NR, GRAD, PC>(TA, R, p0, n, reinterpret_cast<float2*>(tile_smem), psi, E);
+            gather_tiles_df<NR, GRAD, PC>(TA, R, p0, n, reinterpret_cast<float2*>(tile_smem), psi, E, &tmap, &tma_bar,
+                                          phase);
             return;
         }
     }
@@ -1452,25 +1569,34 @@ gather_tiles_kernel(TileArgs TA, int n, const T* __restrict__ grid, double* __re
         const int oy = ((tile / TA.tn[0]) % TA.tn[1]) * kTileNodes;
         const int oz = (tile / (TA.tn[0] * TA.tn[1])) * kTileNodes;
         const T* gr = grid + (size_t)cfg * NR * g.G;
-        for (int u = threadIdx.x; u < NR * E3; u += kTileThreads) {
-            const int c = u / E3, rem = u - c * E3;
-            const int z = rem / E2, y = (rem / Ee) % Ee, x = rem % Ee;
-            const size_t off = ((size_t)wrap_once(oz + z, g.N[2]) * g.N[1] + wrap_once(oy + y, g.N[1])) * g.N[0] +
-                               wrap_once(ox + x, g.N[0]);
-            T v;
-            if constexpr (sizeof(T) == 8) {
-                if (A.gdf) {
-                    const float2 t = __ldg(A.gdf + (size_t)(cfg * NR + c) * g.G + off);
-                    v = df_join(df{t.x, t.y});
+        const bool inside = ox + Ee <= g.N[0] && oy + Ee <= g.N[1] && oz + Ee <= g.N[2];
+        int got = -1;
+        if (sizeof(T) == 4 && TA.tma && inside) {
+            got = tma_region(&tmap, tile_smem, NR, (unsigned)(sizeof(T) * E3), (int)sizeof(T), Ee, ox, oy,
+                             cfg * NR * g.N[2] + oz, g.N[2], TA.tma_zext, &tma_bar, phase, TA.tma_err);
+            if (got == 0) return;
+        }
+        if (got < 0) {
+            for (int u = threadIdx.x; u < NR * E3; u += kTileThreads) {
+                const int c = u / E3, rem = u - c * E3;
+                const int z = rem / E2, y = (rem / Ee) % Ee, x = rem % Ee;
+                const size_t off = ((size_t)wrap_once(oz + z, g.N[2]) * g.N[1] + wrap_once(oy + y, g.N[1])) * g.N[0] +
+                                   wrap_once(ox + x, g.N[0]);
+                T v;
+                if constexpr (sizeof(T) == 8) {
+                    if (A.gdf) {
+                        const float2 t = __ldg(A.gdf + (size_t)(cfg * NR + c) * g.G + off);
+                        v = df_join(df{t.x, t.y});
+                    } else {
+                        v = __ldg(gr + (size_t)c * g.G + off);
+                    }
                 } else {
                     v = __ldg(gr + (size_t)c * g.G + off);
                 }
-            } else {
-                v = __ldg(gr + (size_t)c * g.G + off);
+                reg[u] = v;
             }
-            reg[u] = v;
+            __syncthreads();
         }
-        __syncthreads();
         for (int t = a + w; t < b; t += kTileWarps) {
             const int bead = TA.sorted[p0 + t];
             const int4 st = A.start[bead];
@@ -1623,16 +1749,16 @@ void tile_attrs() {
 // here (outside any stream capture) so that launches inside captures find them cached.
 template <typename T, int NR>
 void tile_resident_nr(const MeshGeom& g) {
-    const size_t b = tile_smem_bytes<T>(g, NR);
-    if (b > kTileSmemMax) return;
+    const size_t b = tile_smem_bytes<T>(g, NR), bg = b + kTmaPad;
+    if (bg > kTileSmemMax) return;
     tile_resident_blocks((const void*)spread_tiles_kernel<T, NR, 0>, b);
-    tile_resident_blocks((const void*)gather_tiles_kernel<T, NR, true, 0>, b);
-    tile_resident_blocks((const void*)gather_tiles_kernel<T, NR, false, 0>, b);
+    tile_resident_blocks((const void*)gather_tiles_kernel<T, NR, true, 0>, bg);
+    tile_resident_blocks((const void*)gather_tiles_kernel<T, NR, false, 0>, bg);
     if constexpr (NR <= 3) {
         if (g.P == 9) {
             tile_resident_blocks((const void*)spread_tiles_kernel<T, NR, 9>, b);
-            tile_resident_blocks((const void*)gather_tiles_kernel<T, NR, true, 9>, b);
-            tile_resident_blocks((const void*)gather_tiles_kernel<T, NR, false, 9>, b);
+            tile_resident_blocks((const void*)gather_tiles_kernel<T, NR, true, 9>, bg);
+            tile_resident_blocks((const void*)gather_tiles_kernel<T, NR, false, 9>, bg);
         }
     }
 }
@@ -1665,8 +1791,11 @@ void tile_attrs_once() {
 
 template <typename T, int NR>
 void launch_tiles(bool spread, bool grad, const TileArgs& TA0, int n, const double* q, T* grid, double* psi,
-                  double* E, cudaStream_t s) {
-    const size_t bytes = tile_smem_bytes<T>(TA0.A.g, NR);
+                  double* E, cudaStream_t s, const CUtensorMap* tm) {
+    CUtensorMap tmv;
+    memset(&tmv, 0, sizeof(tmv));
+    if (tm) tmv = *tm;
+    const size_t bytes = tile_smem_bytes<T>(TA0.A.g, NR) + (spread ? 0 : kTmaPad);
     bool p9 = false;
     if constexpr (NR <= 3) p9 = TA0.A.g.P == 9;
     const void* fn;
@@ -1691,42 +1820,91 @@ void launch_tiles(bool spread, bool grad, const TileArgs& TA0, int n, const doub
     } else if (grad) {
         if constexpr (NR <= 3) {
             if (p9) {
-                gather_tiles_kernel<T, NR, true, 9><<<blocks, kTileThreads, bytes, s>>>(TA, n, grid, psi, E);
+                gather_tiles_kernel<T, NR, true, 9><<<blocks, kTileThreads, bytes, s>>>(TA, n, grid, psi, E, tmv);
                 return;
             }
         }
-        gather_tiles_kernel<T, NR, true, 0><<<blocks, kTileThreads, bytes, s>>>(TA, n, grid, psi, E);
+        gather_tiles_kernel<T, NR, true, 0><<<blocks, kTileThreads, bytes, s>>>(TA, n, grid, psi, E, tmv);
     } else {
         if constexpr (NR <= 3) {
             if (p9) {
-                gather_tiles_kernel<T, NR, false, 9><<<blocks, kTileThreads, bytes, s>>>(TA, n, grid, psi, nullptr);
+                gather_tiles_kernel<T, NR, false, 9><<<blocks, kTileThreads, bytes, s>>>(TA, n, grid, psi, nullptr, tmv);
                 return;
             }
         }
-        gather_tiles_kernel<T, NR, false, 0><<<blocks, kTileThreads, bytes, s>>>(TA, n, grid, psi, nullptr);
+        gather_tiles_kernel<T, NR, false, 0><<<blocks, kTileThreads, bytes, s>>>(TA, n, grid, psi, nullptr, tmv);
     }
 }
 
 template <typename T>
 void tiles_dispatch(int nrhs, bool spread, bool grad, const TileArgs& TA, int n, const double* q, T* grid,
-                    double* psi, double* E, cudaStream_t s) {
+                    double* psi, double* E, cudaStream_t s, const CUtensorMap* tm = nullptr) {
     switch (nrhs) {
-        case 1: launch_tiles<T, 1>(spread, grad, TA, n, q, grid, psi, E, s); break;
-        case 2: launch_tiles<T, 2>(spread, grad, TA, n, q, grid, psi, E, s); break;
-        case 3: launch_tiles<T, 3>(spread, grad, TA, n, q, grid, psi, E, s); break;
-        case 4: launch_tiles<T, 4>(spread, grad, TA, n, q, grid, psi, E, s); break;
-        case 5: launch_tiles<T, 5>(spread, grad, TA, n, q, grid, psi, E, s); break;
-        case 6: launch_tiles<T, 6>(spread, grad, TA, n, q, grid, psi, E, s); break;
-        case 7: launch_tiles<T, 7>(spread, grad, TA, n, q, grid, psi, E, s); break;
-        default: launch_tiles<T, 8>(spread, grad, TA, n, q, grid, psi, E, s); break;
+        case 1: launch_tiles<T, 1>(spread, grad, TA, n, q, grid, psi, E, s, tm); break;
+        case 2: launch_tiles<T, 2>(spread, grad, TA, n, q, grid, psi, E, s, tm); break;
+        case 3: launch_tiles<T, 3>(spread, grad, TA, n, q, grid, psi, E, s, tm); break;
+        case 4: launch_tiles<T, 4>(spread, grad, TA, n, q, grid, psi, E, s, tm); break;
+        case 5: launch_tiles<T, 5>(spread, grad, TA, n, q, grid, psi, E, s, tm); break;
+        case 6: launch_tiles<T, 6>(spread, grad, TA, n, q, grid, psi, E, s, tm); break;
+        case 7: launch_tiles<T, 7>(spread, grad, TA, n, q, grid, psi, E, s, tm); break;
+        default: launch_tiles<T, 8>(spread, grad, TA, n, q, grid, psi, E, s, tm); break;
     }
+}
+
+// The tensor map of the grid the tiled gathers read (base: the FP32 grid, or the
+// double-float potential as (hi, lo) pairs of es = 8 bytes), built once per buffer and
+// channel count; NULL when a region's box cannot be copied by TMA (the box edge or a
+// grid row not a multiple of 16 bytes, a region larger than the grid) or IBPME_NO_TMA
+// is set (the switch lets tests compare both paths).
+const CUtensorMap* grid_tmap(unsigned char* bytes, const void*& tm_base, int& tm_ch, int& tm_es, int& tm_E,
+                             bool& tm_ok, const MeshGeom& g, const void* base, int channels, int es) {
+    if (std::getenv("IBPME_NO_TMA") != nullptr) return nullptr;
+    const int E = kTileNodes + g.P - 1;
+    if (tm_base == base && tm_ch == channels && tm_es == es && tm_E == E) {
+        return tm_ok ? reinterpret_cast<const CUtensorMap*>(bytes) : nullptr;
+    }
+    tm_base = base;
+    tm_ch = channels;
+    tm_es = es;
+    tm_E = E;
+    tm_ok = false;
+    if ((E * es) % 16 != 0 || ((size_t)g.N[0] * es) % 16 != 0 || E > 256 || E > g.N[0] || E > g.N[1] ||
+        E > g.N[2] || (reinterpret_cast<size_t>(base) & 15) != 0)
+        return nullptr;
+    static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+    static std::mutex mu;
+    {
+        std::lock_guard<std::mutex> lock(mu);
+        if (!encode) {
+            void* fn = nullptr;
+            cudaDriverEntryPointQueryResult q{};
+            if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) !=
+                    cudaSuccess ||
+                q != cudaDriverEntryPointSuccess || !fn) {
+                cudaGetLastError();
+                return nullptr;
+            }
+            encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+        }
+    }
+    const cuuint64_t dims[3] = {(cuuint64_t)g.N[0], (cuuint64_t)g.N[1], (cuuint64_t)g.N[2] * (cuuint64_t)channels};
+    const cuuint64_t strides[2] = {(cuuint64_t)g.N[0] * es, (cuuint64_t)g.N[0] * g.N[1] * es};
+    const cuuint32_t box[3] = {(cuuint32_t)E, (cuuint32_t)E, (cuuint32_t)E};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    CUtensorMap* m = reinterpret_cast<CUtensorMap*>(bytes);
+    const CUresult r = encode(m, es == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 3,
+                              const_cast<void*>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                              CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    tm_ok = r == CUDA_SUCCESS;
+    return tm_ok ? m : nullptr;
 }
 
 // The tiled path serves a call when the cache holds tile bins and the region of
 // all its channels fits in shared memory.
 template <typename T>
 bool tiles_fit(const MeshGeom& g, const StencilCache* sc, int nrhs) {
-    return sc && sc->tiles && nrhs <= 8 && tile_smem_bytes<T>(g, nrhs) <= kTileSmemMax;
+    return sc && sc->tiles && nrhs <= 8 && tile_smem_bytes<T>(g, nrhs) + kTmaPad <= kTileSmemMax;
 }
 
 // G(k)/(N_x N_y N_z) on the half spectrum, Eq. after H_hat:
@@ -1791,6 +1969,11 @@ template <typename T>
 void Mesh<T>::init(const MeshGeom& geom, int channels, double xi, double eta, double a, cudaStream_t s) {
     g = geom;
     rcap = 0;
+    if (!tma_err_host) {   // here, outside any stream capture (the gathers only write it)
+        IBP_CUDA(cudaHostAlloc(reinterpret_cast<void**>(&tma_err_host), sizeof(int), cudaHostAllocMapped));
+        *tma_err_host = 0;
+        IBP_CUDA(cudaHostGetDevicePointer(reinterpret_cast<void**>(&tma_err_dev), tma_err_host, 0));
+    }
     df = sizeof(T) == 8 && df_fft_supported(g);
     if (df) df_fft_init(g, df_tw, s);
     ensure_channels(channels);
@@ -1870,6 +2053,11 @@ void Mesh<T>::destroy() {
     potential_df = false;
     work.release();
     rcap = 0;
+    if (tma_err_host) cudaFreeHost(tma_err_host);
+    tma_err_host = nullptr;
+    tma_err_dev = nullptr;
+    tm_base = nullptr;
+    tm_ok = false;
 }
 
 template <typename T>
@@ -1940,7 +2128,15 @@ void Mesh<T>::gather(int n, const double* xw, int nrhs, const int* bead_cfg, dou
     if (tiles_fit<T>(g, sc, nrhs)) {
         TileArgs TA = tile_args(g, *sc, n);
         TA.A.gdf = gdf;
-        tiles_dispatch<T>(nrhs, false, E != nullptr, TA, n, nullptr, grid.as<T>(), psi, E, s);
+        const CUtensorMap* tm = nullptr;
+        if ((sizeof(T) == 4 || gdf) && tma_err_dev) {
+            tm = gdf ? grid_tmap(tmap, tm_base, tm_ch, tm_es, tm_E, tm_ok, g, grid_df.p, rcap, 8)
+                     : grid_tmap(tmap, tm_base, tm_ch, tm_es, tm_E, tm_ok, g, grid.p, rcap, 4);
+        }
+        TA.tma = tm != nullptr;
+        TA.tma_err = tma_err_dev;
+        TA.tma_zext = g.N[2] * rcap;
+        tiles_dispatch<T>(nrhs, false, E != nullptr, TA, n, nullptr, grid.as<T>(), psi, E, s, tm);
         IBP_CHECK_LAUNCH();
         return;
     }
@@ -1960,6 +2156,14 @@ void Mesh<T>::gather(int n, const double* xw, int nrhs, const int* bead_cfg, dou
     else
         gather_dispatch<T, false>(n, xw, nrhs, bead_cfg, g, grid.as<T>(), gdf, psi, nullptr, s);
     IBP_CHECK_LAUNCH();
+}
+
+template <typename T>
+int Mesh<T>::tma_failed() {
+    if (!tma_err_host || *tma_err_host == 0) return 0;
+    const int v = *tma_err_host;
+    *tma_err_host = 0;
+    return v;
 }
 
 template struct Mesh<float>;

@@ -196,6 +196,42 @@ def test_tiled_mesh_path_matches_direct_path_and_oracle(cuda_lib, nrhs, mesh, mo
             assert rel_err(e[r][t], ref_E) < bar, (prec, r, rel_err(e[r][t], ref_E))
 
 
+@pytest.mark.parametrize("nrhs,mesh", [(1, (36, 44, 52)), (3, (40, 48, 56)), (2, (38, 44, 50))])
+def test_tma_region_loads_equal_plain_loads(cuda_lib, nrhs, mesh, monkeypatch):
+    """The tiled gathers stage the region of a tile that does not wrap around the box
+    with cp.async.bulk.tensor copies (FP32 grid, and the double-float FP64 potential);
+    the field and potential equal those of the same call with plain loads
+    (IBPME_NO_TMA) to the rounding of the spread's atomics (their order differs from
+    call to call), in both precisions, with tiles that wrap (a sphere across the corner)
+    served by the plain loads in the same launch.  N_x = 38 has FP32 rows that are no
+    multiple of 16 bytes: its FP32 gathers keep the plain loads.  A second call on each
+    context reports any refused copy or expired wait of the first."""
+    ib = cuda_lib
+    x, box = _dense_surfaces(70 + nrhs)
+    n = x.shape[0]
+    q = np.stack([random_neutral_charges(n, 300 + r) for r in range(nrhs)])
+    kw = dict(box=box, mesh=mesh, tol=1e-6, bead_radius=0.01, eps_f=0.8, max_rhs=4)
+    out = {}
+    for tma in (True, False):
+        if tma:
+            monkeypatch.delenv("IBPME_NO_TMA", raising=False)
+        else:
+            monkeypatch.setenv("IBPME_NO_TMA", "1")
+        for prec in (ib.IBPME_FP64, ib.IBPME_MIXED):
+            ctx = ib.pme_setup(ib.make_params(precision=prec, **kw))
+            try:
+                out[tma, prec] = _field(ib, ctx, x, q, nrhs=nrhs)
+                # the next call reports a refused tensor copy or an expired wait of this one
+                _field(ib, ctx, x, q, nrhs=nrhs)
+            finally:
+                ib.pme_destroy(ctx)
+    monkeypatch.delenv("IBPME_NO_TMA", raising=False)
+    for prec, bar in ((ib.IBPME_FP64, 1e-12), (ib.IBPME_MIXED, 2e-6)):
+        (pt, et), (pp, ep) = out[True, prec], out[False, prec]
+        for r in range(nrhs):
+            assert rel_err(pt[r], pp[r]) < bar and rel_err(et[r], ep[r]) < bar, (prec, r)
+
+
 def test_spectral_error_decays_exponentially_with_the_stencil_width(cuda_lib):
     """Sec. III.D.2: with xi and the mesh fixed and eta = h^2 xi^2 P / pi, the window
     truncation and quadrature errors are both e^{-pi P / 2}.  The FP64 potential of a
