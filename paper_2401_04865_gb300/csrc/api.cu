@@ -306,6 +306,7 @@ void pme_apply(ibpme_ctx* c, int n, const double* xw, const double* q, int nrhs,
                double* E, bool near_ready, bool near32, const FreeMesh* fm) {
     c->grid64_final = false;   // the meshes are about to hold other charges
     c->field64_ready = false;
+    c->near_field_ready = false;
     if (!near_ready) near_build(c, n, xw, E != nullptr);
     const size_t m = (size_t)nrhs * n;
     pme_reserve(c, n, nrhs, E != nullptr);
@@ -332,6 +333,7 @@ void pme_apply(ibpme_ctx* c, int n, const double* xw, const double* q, int nrhs,
         c->stream = c->aux;
         near_apply(c, n, q, nrhs, pr, near32 && prec == IBPME_MIXED);
         if (E) near_field(c, n, xw, q, nrhs, er);
+        else if (fm && fm->er) near_field(c, n, xw, q, nrhs, fm->er);
     }
     IBP_CUDA(cudaEventRecord(c->ev_join, c->aux));
     const int ch = nrhs * c->ncfg;
@@ -355,6 +357,7 @@ void pme_apply(ibpme_ctx* c, int n, const double* xw, const double* q, int nrhs,
         } else {
             c->mesh64.gather(n, xw, nrhs, c->bcfg, pk, ek ? ek : (fm ? fm->ek : nullptr), c->stream, sc);
             c->field64_ready = !E && fm && fm->ek;
+            c->near_field_ready = !E && fm && fm->er;
         }
     }
     IBP_CUDA(cudaStreamWaitEvent(c->stream, c->ev_join, 0));
@@ -393,6 +396,7 @@ void pme_apply_free(ibpme_ctx* c, const double* qc, int nrhs, int prec, double* 
     const int n = fs.nfree;
     c->grid64_final = false;   // the meshes are about to hold other charges
     c->field64_ready = false;
+    c->near_field_ready = false;
     if (n == 0) return;
     double* pr = fs.psi_r.as<double>();
     double* pk = fs.psi_k.as<double>();
@@ -743,16 +747,21 @@ const double* solution_field(ibpme_ctx* c, int n, const double* xw, const double
     double* er = c->E_r.as<double>();
     double* ek = c->E_k.as<double>();
     const cudaStream_t main = c->stream;
-    IBP_CUDA(cudaEventRecord(c->ev_fork, main));
-    IBP_CUDA(cudaStreamWaitEvent(c->aux, c->ev_fork, 0));
-    {
-        struct Restore {
-            ibpme_ctx* c;
-            cudaStream_t s;
-            ~Restore() { c->stream = s; }
-        } restore{c, main};
-        c->stream = c->aux;
-        near_field(c, n, xw, q, 1, er);
+    if (!c->near_field_ready) {   // the final residual did not compute the real-space field beside its mesh pass
+        IBP_CUDA(cudaEventRecord(c->ev_fork, main));
+        IBP_CUDA(cudaStreamWaitEvent(c->aux, c->ev_fork, 0));
+        {
+            struct Restore {
+                ibpme_ctx* c;
+                cudaStream_t s;
+                ~Restore() { c->stream = s; }
+            } restore{c, main};
+            c->stream = c->aux;
+            near_field(c, n, xw, q, 1, er);
+        }
+    } else {
+        IBP_CUDA(cudaEventRecord(c->ev_fork, main));   // nothing on the second stream: join at once
+        IBP_CUDA(cudaStreamWaitEvent(c->aux, c->ev_fork, 0));
     }
     IBP_CUDA(cudaEventRecord(c->ev_join, c->aux));
     if (!c->field64_ready) {   // the final residual did not gather the mesh field with its potential
@@ -764,6 +773,7 @@ const double* solution_field(ibpme_ctx* c, int n, const double* xw, const double
     IBP_CHECK_LAUNCH();
     c->grid64_final = false;
     c->field64_ready = false;
+    c->near_field_ready = false;
     return psi64;
 }
 

@@ -416,8 +416,10 @@ struct ibpme_ctx {
     // the FP64 mesh grid and the Krylov potentials hold the last solve's final FP64
     // residual evaluation (the field of the solution charges can be gathered from it)
     bool grid64_final = false;
-    // E_k holds the mesh field of that evaluation at every bead (gathered with its potential)
+    // E_k holds the mesh field of that evaluation at every bead (gathered with its potential),
+    // E_r its real-space field
     bool field64_ready = false;
+    bool near_field_ready = false;
     ibp::DevBuf ml_feat, ml_scratch, ml_scales, ml_y, ml_part;   // learned warm start
     ibp::DevBuf ml_g, ml_gprev;               // [nrhs][n] learned guesses of this and of the last call
     unsigned long long ml_prev_version = 0;   // body structure, bead and field count of ml_gprev
@@ -495,6 +497,7 @@ struct FreeMesh {
     const double* dq;
     double* tmp;
     double* ek = nullptr;   // also gather the mesh field at every bead into ek [nrhs][n][3]
+    double* er = nullptr;   // and the real-space field into er (on the second stream, beside the mesh)
 };
 // With fm (FP64 only) the mesh pass takes the free-bead forms above; the real-space
 // pass and the k = 0 term still take q on every bead.

@@ -935,6 +935,7 @@ struct Solver {
             if (field) {
                 pme_reserve(c, n, 1, true);
                 fm.ek = c->E_k.as<double>();
+                fm.er = c->E_r.as<double>();
             }
             if (can_keep && fsc && keep && c->mesh64.writes == keep_writes) {
                 delta_kernel<<<blocks_for((long long)nfree * R), 256, 0, s()>>>(nfree, n, R, I(bd.free_idx), D(k->qtot),
