@@ -16,7 +16,9 @@
  *     |k| <= k_c of the structure factor (Sec. III.D, Eq. splitting, first
  *     term), no grid, no FFT, no Gaussian spreading;
  *   - the free-space regularized tensor M(r) (Sec. II, real-space form of
- *     Eq. M00_Fourier).
+ *     Eq. M00_Fourier);
+ *   - the same sums for beads of unequal radii (the *2 and *_radii functions
+ *     at the end), kernel j0(k a_alpha) j0(k a_beta)/k^2.
  *
  * Conventions: x is [n][3] row-major, q is [n], the box is orthorhombic with
  * side lengths L[3] and volume V = L0*L1*L2, eps is the fluid permittivity
@@ -355,6 +357,231 @@ void ibo_real_matrix(int n, const double *x, const double *L, double a, double x
                         if (r >= rc)
                             continue;
                         m += (r == 0.0) ? self : ibo_phi_real(r, a, xi);
+                    }
+            Mr[(size_t)al * n + be] = m;
+        }
+    }
+}
+
+/* ------------------------------------------------------------------------
+ * Beads of unequal radii.
+ *
+ * A bead of radius a carries its charge on a spherical shell of radius a;
+ * the shell's Fourier transform is j0(ka), which is where the j0^2(ka) of
+ * Eq. M00_Fourier comes from.  Two beads of radii a and b therefore interact
+ * through j0(ka) j0(kb)/k^2 (the paper fixes one radius, Sec. III.A; this is
+ * the same construction with two).  In real space the pair kernel is the
+ * average of the point kernel over both shells.  For a radial kernel f with
+ * s f(|s|) extended to an odd function of s and F any C^1 function with
+ * F'' = s f(|s|), the average over shells of radii a and b with centres r
+ * apart is
+ *     [F(r+a+b) - F(r+a-b) - F(r-a+b) + F(r-a-b)] / (4 a b r),
+ * because the distance from a fixed point to a uniform point of a shell of
+ * radius b is distributed with density s/(2 b r) on [|r-b|, r+b].
+ * ------------------------------------------------------------------------ */
+
+/* F for the unscreened kernel 1/(4 pi s): F'' = sign(s)/(4 pi). */
+static double F_coulomb(double s)
+{
+    return s * fabs(s) / (8.0 * PI);
+}
+
+/* F for the screened kernel erfc(xi s)/(4 pi s) (the real-space share of
+ * Eq. splitting): F(s) = sign(s) f(|s|)/(4 pi) with
+ * f(u) = (u^2/2 + 1/(4 xi^2)) erfc(xi u) - u e^{-xi^2 u^2}/(2 xi sqrt(pi)) - 1/(4 xi^2),
+ * f(0) = 0, f'' = erfc(xi u). */
+static double F_screened(double s, double xi)
+{
+    const double u = fabs(s);
+    const double f = (0.5 * u * u + 0.25 / (xi * xi)) * erfc(xi * u)
+                   - u * exp(-xi * xi * u * u) / (2.0 * xi * sqrt(PI)) - 0.25 / (xi * xi);
+    return (s < 0.0 ? -f : f) / (4.0 * PI);
+}
+
+/* F' of the screened kernel (even in s): (u erfc(xi u) - e^{-xi^2 u^2}/(xi sqrt(pi)))/(4 pi). */
+static double dF_screened(double s, double xi)
+{
+    const double u = fabs(s);
+    return (u * erfc(xi * u) - exp(-xi * xi * u * u) / (xi * sqrt(PI))) / (4.0 * PI);
+}
+
+/* F' of the unscreened kernel: |s|/(4 pi). */
+static double dF_coulomb(double s)
+{
+    return fabs(s) / (4.0 * PI);
+}
+
+/* Free-space shell-shell potential W(r; a, b) without 1/eps: the real-space
+ * form of j0(ka) j0(kb)/k^2.  Equals M(r) above for a = b. */
+double ibo_M_free2(double r, double a, double b)
+{
+    if (r == 0.0)   /* r -> 0 limit: [F'(a+b) - F'(|a-b|)] / (2ab) */
+        return (dF_coulomb(a + b) - dF_coulomb(a - b)) / (2.0 * a * b);
+    return (F_coulomb(r + a + b) - F_coulomb(r + a - b) - F_coulomb(r - a + b) + F_coulomb(r - a - b))
+           / (4.0 * a * b * r);
+}
+
+/* Real-space Ewald kernel of a pair of radii a and b, without 1/eps: the
+ * inverse transform of j0(ka) j0(kb)(1 - e^{-k^2/(4 xi^2)})/k^2.  At r = 0 it
+ * takes the limit [F'(a+b) - F'(|a-b|)]/(2ab), which for a = b is the self
+ * term of Sec. III.D.1. */
+double ibo_phi_real2(double r, double a, double b, double xi)
+{
+    if (r == 0.0)
+        return (dF_screened(a + b, xi) - dF_screened(a - b, xi)) / (2.0 * a * b);
+    return (F_screened(r + a + b, xi) - F_screened(r + a - b, xi) - F_screened(r - a + b, xi)
+            + F_screened(r - a - b, xi)) / (4.0 * a * b * r);
+}
+
+/* d/dr of ibo_phi_real2 for r > 0: N'(r)/(4abr) - phi/r with N the bracket. */
+double ibo_dphi_real2(double r, double a, double b, double xi)
+{
+    const double dN = dF_screened(r + a + b, xi) - dF_screened(r + a - b, xi) - dF_screened(r - a + b, xi)
+                    + dF_screened(r - a - b, xi);
+    return dN / (4.0 * a * b * r) - ibo_phi_real2(r, a, b, xi) / r;
+}
+
+/* ibo_real_sum with a radius per bead (rad[n]): each pair takes
+ * ibo_phi_real2 of its two radii, each target its own self term. */
+void ibo_real_sum_radii(int n, const double *x, const double *q, const double *L,
+                        const double *rad, double xi, double rc, double eps,
+                        int nt, const int *targets, double *psi, double *E)
+{
+    const int m0 = image_range(rc, L[0]), m1 = image_range(rc, L[1]), m2 = image_range(rc, L[2]);
+#pragma omp parallel for schedule(dynamic, 4)
+    for (int t = 0; t < nt; ++t) {
+        const int al = targets[t];
+        const double a = rad[al];
+        double p = ibo_phi_real2(0.0, a, a, xi) * q[al];
+        double ex = 0.0, ey = 0.0, ez = 0.0;
+        for (int be = 0; be < n; ++be) {
+            const double b = rad[be];
+            double dx0 = x[3 * al + 0] - x[3 * be + 0];
+            double dy0 = x[3 * al + 1] - x[3 * be + 1];
+            double dz0 = x[3 * al + 2] - x[3 * be + 2];
+            dx0 -= L[0] * floor(dx0 / L[0] + 0.5);
+            dy0 -= L[1] * floor(dy0 / L[1] + 0.5);
+            dz0 -= L[2] * floor(dz0 / L[2] + 0.5);
+            for (int i = -m0; i <= m0; ++i)
+                for (int j = -m1; j <= m1; ++j)
+                    for (int k = -m2; k <= m2; ++k) {
+                        if (be == al && i == 0 && j == 0 && k == 0)
+                            continue;
+                        const double dx = dx0 + i * L[0], dy = dy0 + j * L[1], dz = dz0 + k * L[2];
+                        const double r = sqrt(dx * dx + dy * dy + dz * dz);
+                        if (r >= rc)
+                            continue;
+                        p += ibo_phi_real2(r, a, b, xi) * q[be];
+                        if (E && r > 0.0) {
+                            const double f = -ibo_dphi_real2(r, a, b, xi) / r * q[be];
+                            ex += f * dx; ey += f * dy; ez += f * dz;
+                        }
+                    }
+        }
+        psi[t] = p / eps;
+        if (E) {
+            E[3 * t + 0] = ex / eps;
+            E[3 * t + 1] = ey / eps;
+            E[3 * t + 2] = ez / eps;
+        }
+    }
+}
+
+/* ibo_wave_sum with a radius per bead: the structure factor weighs each
+ * source by j0(k a_beta), each target's sum by j0(k a_alpha), and the weight
+ * is e^{-k^2/(4 xi^2)}/k^2 (no j0 in it).  Results are OVERWRITTEN. */
+void ibo_wave_sum_radii(int n, const double *x, const double *q, const double *L,
+                        const double *rad, double xi, double kc, double eps,
+                        int nt, const int *targets, double *psi, double *E)
+{
+    const int mx = (int)floor(kc * L[0] / (2.0 * PI));
+    const int my = (int)floor(kc * L[1] / (2.0 * PI));
+    const int mz = (int)floor(kc * L[2] / (2.0 * PI));
+    const double V = L[0] * L[1] * L[2];
+    size_t nk = 0;
+    int *km = malloc(sizeof(int) * 3 * (size_t)(2 * mx + 1) * (2 * my + 1) * (2 * mz + 1));
+    for (int i = -mx; i <= mx; ++i)
+        for (int j = -my; j <= my; ++j)
+            for (int k = -mz; k <= mz; ++k) {
+                if (i == 0 && j == 0 && k == 0)
+                    continue;
+                const double kx = 2.0 * PI * i / L[0], ky = 2.0 * PI * j / L[1], kz = 2.0 * PI * k / L[2];
+                if (kx * kx + ky * ky + kz * kz > kc * kc)
+                    continue;
+                km[3 * nk + 0] = i; km[3 * nk + 1] = j; km[3 * nk + 2] = k;
+                ++nk;
+            }
+    double *Sre = malloc(sizeof(double) * (nk ? nk : 1)), *Sim = malloc(sizeof(double) * (nk ? nk : 1));
+#pragma omp parallel for schedule(dynamic, 16)
+    for (size_t t = 0; t < nk; ++t) {
+        const double kx = 2.0 * PI * km[3 * t] / L[0], ky = 2.0 * PI * km[3 * t + 1] / L[1],
+                     kz = 2.0 * PI * km[3 * t + 2] / L[2];
+        const double kk = sqrt(kx * kx + ky * ky + kz * kz);
+        double sre = 0.0, sim = 0.0;
+        for (int b = 0; b < n; ++b) {
+            const double th = kx * x[3 * b] + ky * x[3 * b + 1] + kz * x[3 * b + 2];
+            const double w = q[b] * sin(kk * rad[b]) / (kk * rad[b]);
+            sre += w * cos(th);
+            sim += w * sin(th);
+        }
+        Sre[t] = sre;
+        Sim[t] = sim;
+    }
+#pragma omp parallel for schedule(dynamic, 4)
+    for (int tt = 0; tt < nt; ++tt) {
+        const int al = targets[tt];
+        double p = 0.0, ex = 0.0, ey = 0.0, ez = 0.0;
+        for (size_t t = 0; t < nk; ++t) {
+            const double kx = 2.0 * PI * km[3 * t] / L[0], ky = 2.0 * PI * km[3 * t + 1] / L[1],
+                         kz = 2.0 * PI * km[3 * t + 2] / L[2];
+            const double k2 = kx * kx + ky * ky + kz * kz, kk = sqrt(k2);
+            const double G = sin(kk * rad[al]) / (kk * rad[al]) * exp(-k2 / (4.0 * xi * xi)) / k2;
+            const double th = kx * x[3 * al] + ky * x[3 * al + 1] + kz * x[3 * al + 2];
+            const double re = cos(th), im = sin(th);
+            p += G * (re * Sre[t] + im * Sim[t]);
+            if (E) {
+                const double zim = im * Sre[t] - re * Sim[t];
+                ex += G * kx * zim;
+                ey += G * ky * zim;
+                ez += G * kz * zim;
+            }
+        }
+        psi[tt] = p / (eps * V);
+        if (E) {
+            E[3 * tt + 0] = ex / (eps * V);
+            E[3 * tt + 1] = ey / (eps * V);
+            E[3 * tt + 2] = ez / (eps * V);
+        }
+    }
+    free(km); free(Sre); free(Sim);
+}
+
+/* ibo_real_matrix with a radius per bead. */
+void ibo_real_matrix_radii(int n, const double *x, const double *L, const double *rad, double xi, double rc,
+                           double *Mr)
+{
+    const int m0 = image_range(rc, L[0]), m1 = image_range(rc, L[1]), m2 = image_range(rc, L[2]);
+#pragma omp parallel for schedule(dynamic, 4)
+    for (int al = 0; al < n; ++al) {
+        for (int be = 0; be < n; ++be) {
+            const double a = rad[al], b = rad[be];
+            double dx0 = x[3 * al + 0] - x[3 * be + 0];
+            double dy0 = x[3 * al + 1] - x[3 * be + 1];
+            double dz0 = x[3 * al + 2] - x[3 * be + 2];
+            dx0 -= L[0] * floor(dx0 / L[0] + 0.5);
+            dy0 -= L[1] * floor(dy0 / L[1] + 0.5);
+            dz0 -= L[2] * floor(dz0 / L[2] + 0.5);
+            double m = (al == be) ? ibo_phi_real2(0.0, a, a, xi) : 0.0;
+            for (int i = -m0; i <= m0; ++i)
+                for (int j = -m1; j <= m1; ++j)
+                    for (int k = -m2; k <= m2; ++k) {
+                        if (al == be && i == 0 && j == 0 && k == 0)
+                            continue;
+                        const double dx = dx0 + i * L[0], dy = dy0 + j * L[1], dz = dz0 + k * L[2];
+                        const double r = sqrt(dx * dx + dy * dy + dz * dz);
+                        if (r >= rc)
+                            continue;
+                        m += ibo_phi_real2(r, a, b, xi);
                     }
             Mr[(size_t)al * n + be] = m;
         }

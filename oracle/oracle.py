@@ -9,6 +9,9 @@ What it computes, each function citing the passage it follows:
 * Ewald sums of the regularized potential tensor M (Sec. II, Eq. M00_Fourier;
   Sec. III.D, Eq. splitting): real space directly over image shells, wave
   space as an explicit k-vector sum (both in ``ewald_ref.c``), self term.
+  Beads of unequal radii (the paper fixes one, Sec. III.A): pass one radius
+  per bead; pairs then interact through j0(k a_alpha) j0(k a_beta)/k^2, the
+  real-space kernel being the average of erfc(xi s)/(4 pi s) over both shells.
 * The dense matrix M for small systems (real part from ``ewald_ref.c``, wave
   part as C diag(G) C^T + S diag(G) S^T with C = cos(K x), S = sin(K x)).
 * The saddle system of Eq. saddle, solved by dense LU (numpy.linalg.solve)
@@ -60,6 +63,18 @@ def lib():
         L.ibo_wave_vectors.argtypes = [p, d, d, d, ctypes.c_long, p]
         L.ibo_real_matrix.restype = None
         L.ibo_real_matrix.argtypes = [i, p, p, d, d, d, p]
+        L.ibo_M_free2.restype = d
+        L.ibo_M_free2.argtypes = [d, d, d]
+        L.ibo_phi_real2.restype = d
+        L.ibo_phi_real2.argtypes = [d, d, d, d]
+        L.ibo_dphi_real2.restype = d
+        L.ibo_dphi_real2.argtypes = [d, d, d, d]
+        L.ibo_real_sum_radii.restype = None
+        L.ibo_real_sum_radii.argtypes = [i, p, p, p, p, d, d, d, i, p, p, p]
+        L.ibo_wave_sum_radii.restype = None
+        L.ibo_wave_sum_radii.argtypes = [i, p, p, p, p, d, d, d, i, p, p, p]
+        L.ibo_real_matrix_radii.restype = None
+        L.ibo_real_matrix_radii.argtypes = [i, p, p, p, d, d, p]
         L.ibo_num_threads.restype = i
         _LIB = L
     return _LIB
@@ -102,6 +117,36 @@ def phi_self(a: float, xi: float) -> float:
     return lib().ibo_phi_self(float(a), float(xi))
 
 
+def M_free2(r: float, a: float, b: float) -> float:
+    """Free-space potential between shells of radii a and b (real-space form of
+    j0(ka) j0(kb)/k^2), without 1/eps."""
+    return lib().ibo_M_free2(float(r), float(a), float(b))
+
+
+def phi_real2(r: float, a: float, b: float, xi: float) -> float:
+    """Real-space Ewald kernel of two beads of radii a and b (ewald_ref.c)."""
+    return lib().ibo_phi_real2(float(r), float(a), float(b), float(xi))
+
+
+def dphi_real2(r: float, a: float, b: float, xi: float) -> float:
+    """d phi_real2 / dr."""
+    return lib().ibo_dphi_real2(float(r), float(a), float(b), float(xi))
+
+
+def _radii(a, n):
+    """None for one radius (a scalar), else the per-bead radii as a C array."""
+    if np.ndim(a) == 0:
+        return None
+    rad = _c(a).reshape(-1)
+    if rad.shape[0] != n:
+        raise ValueError("one radius per bead expected")
+    return rad
+
+
+def _amax(a) -> float:
+    return float(np.max(a))
+
+
 # ---------------------------------------------------------------------------
 # Ewald sums
 # ---------------------------------------------------------------------------
@@ -119,7 +164,7 @@ def ewald_split(box, a: float, n_src: int, tol: float = 1e-13, xi: float | None 
     if xi is None:
         xi = math.sqrt(math.pi) * (max(n_src, 1) / V ** 2) ** (1.0 / 6.0)
     s = math.sqrt(math.log(1.0 / tol))
-    rc = s / xi + 2.0 * a
+    rc = s / xi + 2.0 * _amax(a)
     kc = 2.0 * xi * s
     return float(xi), float(rc), float(kc)
 
@@ -138,7 +183,8 @@ def k0_term(box, xi, eps):
 def potential(x, q, box, a, eps, targets=None, field=False, xi=None, tol=1e-13):
     """psi_alpha - psi_0 (and E_alpha) at the targets, Eq. splitting + self term.
 
-    x: [n,3]; q: [n]; box: [3]; returns psi [nt] (and E [nt,3]).
+    x: [n,3]; q: [n]; box: [3]; a: the bead radius, or one radius per bead [n]
+    (pair kernel j0(k a_alpha) j0(k a_beta)/k^2); returns psi [nt] (and E [nt,3]).
     """
     x = _c(x).reshape(-1, 3)
     q = _c(q).reshape(-1)
@@ -154,8 +200,15 @@ def potential(x, q, box, a, eps, targets=None, field=False, xi=None, tol=1e-13):
     pk = np.zeros(nt)
     Er = np.zeros((nt, 3)) if field else None
     Ek = np.zeros((nt, 3)) if field else None
-    L.ibo_real_sum(n, _ptr(x), _ptr(q), _ptr(box), a, xi, rc, eps, nt, _ptr(targets), _ptr(pr), _ptr(Er))
-    L.ibo_wave_sum(n, _ptr(x), _ptr(q), _ptr(box), a, xi, kc, eps, nt, _ptr(targets), _ptr(pk), _ptr(Ek))
+    rad = _radii(a, n)
+    if rad is None:
+        L.ibo_real_sum(n, _ptr(x), _ptr(q), _ptr(box), a, xi, rc, eps, nt, _ptr(targets), _ptr(pr), _ptr(Er))
+        L.ibo_wave_sum(n, _ptr(x), _ptr(q), _ptr(box), a, xi, kc, eps, nt, _ptr(targets), _ptr(pk), _ptr(Ek))
+    else:
+        L.ibo_real_sum_radii(n, _ptr(x), _ptr(q), _ptr(box), _ptr(rad), xi, rc, eps, nt, _ptr(targets), _ptr(pr),
+                             _ptr(Er))
+        L.ibo_wave_sum_radii(n, _ptr(x), _ptr(q), _ptr(box), _ptr(rad), xi, kc, eps, nt, _ptr(targets), _ptr(pk),
+                             _ptr(Ek))
     # k = 0 is excluded from M (Sec. II); the real-space image sum carries it (see k0_term)
     pb = -k0_term(box, xi, eps) * float(np.sum(q))
     if field:
@@ -177,21 +230,34 @@ def M_dense(x, box, a, eps, xi=None, tol=1e-13, k_chunk=4096):
 
     M = (1/eps) [ real-space matrix (with self term) + (1/V) sum_k G(k) cos(k.(x_a - x_b)) ].
     The wave part uses cos(k.(x_a-x_b)) = cos(k.x_a)cos(k.x_b) + sin(k.x_a)sin(k.x_b),
-    i.e. C diag(G) C^T + S diag(G) S^T, accumulated over chunks of k.
+    i.e. C diag(G) C^T + S diag(G) S^T, accumulated over chunks of k.  With one radius
+    per bead the j0 factors move out of G onto the rows: C_ak = j0(k a_a) cos(k.x_a).
     """
     x = _c(x).reshape(-1, 3)
     box = _c(box).reshape(3)
     n = x.shape[0]
     xi, rc, kc = ewald_split(box, a, n, tol, xi)
+    rad = _radii(a, n)
     Mr = np.zeros((n, n))
-    lib().ibo_real_matrix(n, _ptr(x), _ptr(box), a, xi, rc, _ptr(Mr))
-    K, G = wave_vectors(box, a, xi, kc)
+    if rad is None:
+        lib().ibo_real_matrix(n, _ptr(x), _ptr(box), a, xi, rc, _ptr(Mr))
+        K, G = wave_vectors(box, a, xi, kc)
+    else:
+        lib().ibo_real_matrix_radii(n, _ptr(x), _ptr(box), _ptr(rad), xi, rc, _ptr(Mr))
+        K, _ = wave_vectors(box, 1.0, xi, kc)
+        k2 = np.sum(K * K, axis=1)
+        G = np.exp(-k2 / (4.0 * xi * xi)) / k2
     V = float(np.prod(box))
     Mw = np.zeros((n, n))
     for s in range(0, K.shape[0], k_chunk):
         ph = x @ K[s:s + k_chunk].T
         C = np.cos(ph)
         S = np.sin(ph)
+        if rad is not None:
+            kk = np.sqrt(np.sum(K[s:s + k_chunk] ** 2, axis=1))
+            J = np.sin(rad[:, None] * kk[None, :]) / (rad[:, None] * kk[None, :])
+            C = C * J
+            S = S * J
         g = G[s:s + k_chunk]
         Mw += (C * g) @ C.T + (S * g) @ S.T
     return (Mr + Mw / V) / eps - k0_term(box, xi, eps)
@@ -616,7 +682,7 @@ def reference_solution(x, body_offsets, X, Q, E0, box, a, eps, dense=None, xi=No
 
 
 __all__ = [
-    "lib", "num_threads", "k0_term", "M_free", "phi_real", "dphi_real", "phi_self", "ewald_split",
+    "lib", "num_threads", "k0_term", "M_free", "phi_real", "dphi_real", "phi_self", "M_free2", "phi_real2", "dphi_real2", "ewald_split",
     "potential", "wave_vectors", "M_dense", "spread_grid", "min_image", "body_index", "sigma_matrix",
     "relative_positions", "saddle_rhs", "saddle_matrix", "solve_dense", "gmres", "sigma_prime",
     "grand_capacitance",
