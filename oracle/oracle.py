@@ -593,17 +593,20 @@ def normals(entity: int, step: int, seed: int, count: int = 6):
 
 def hard_sphere_forces(x, body_offsets, box, a, gamma, dt):
     """Pair forces of U^hs = gamma/(4 dt) (r - 2a)^2 for r < 2a (Eq. hardsphereFD),
-    between beads of different bodies (beads of one rigid body do not repel)."""
+    between beads of different bodies (beads of one rigid body do not repel).
+    With one radius per bead the contact distance 2a of a pair is a_alpha + a_beta."""
     x = _c(x).reshape(-1, 3)
     n = x.shape[0]
+    rad = np.full(n, float(a)) if np.ndim(a) == 0 else _c(a).reshape(-1)
     bid = body_index(body_offsets)
     f = np.zeros((n, 3))
     for al in range(n):
         d = min_image(x[al] - x, box)
         r = np.sqrt((d * d).sum(axis=1))
-        mask = (r < 2.0 * a) & (bid != bid[al]) & (r > 0)
-        # -dU/dr along (x_al - x_be)/r, with dU/dr = gamma/(2 dt) (r - 2a)
-        mag = gamma / (2.0 * dt) * (2.0 * a - r[mask])
+        contact = rad[al] + rad
+        mask = (r < contact) & (bid != bid[al]) & (r > 0)
+        # -dU/dr along (x_al - x_be)/r, with dU/dr = gamma/(2 dt) (r - contact)
+        mag = gamma / (2.0 * dt) * (contact[mask] - r[mask])
         f[al] = (mag[:, None] * d[mask] / r[mask][:, None]).sum(axis=0)
     return f
 

@@ -218,3 +218,42 @@ def test_field_with_radii_is_minus_the_energy_gradient():
             Um = 0.5 * q @ o.M_dense(xm, box, rad, 1.0) @ q
             fd = -(Up - Um) / (2 * h) / q[al]
             assert abs(E[al, c] - fd) <= 2e-6 * max(abs(fd), 1e-2)
+
+
+def test_hard_sphere_force_with_radii_is_minus_gradient():
+    """Eq. hardsphereFD with the contact distance a_alpha + a_beta of two radii:
+    the forces are minus the gradient of sum gamma/(4 dt) (r - a_alpha - a_beta)^2
+    over overlapping pairs of different bodies (central differences)."""
+    rng = np.random.default_rng(2)
+    L = 3.0
+    x = rng.uniform(0, L, size=(10, 3))
+    x[1] = x[0] + [0.3, 0.05, 0.0]
+    x[4] = x[3] + [0.0, 0.2, 0.1]
+    rad = np.array([0.35, 0.12, 0.12, 0.35, 0.12, 0.2, 0.2, 0.12, 0.35, 0.12])
+    off = [0, 1, 2, 3, 5, 6, 7, 8, 9, 10]   # beads 3 and 4 share a body
+    box = np.array([L, L, L])
+    gamma, dt = 1.3, 0.01
+
+    def U(y):
+        bid = o.body_index(off)
+        u = 0.0
+        for i in range(len(y)):
+            for j in range(i + 1, len(y)):
+                if bid[i] == bid[j]:
+                    continue
+                r = np.linalg.norm(o.min_image(y[i] - y[j], box))
+                c = rad[i] + rad[j]
+                if r < c:
+                    u += gamma / (4 * dt) * (r - c) ** 2
+        return u
+
+    f = o.hard_sphere_forces(x, off, box, rad, gamma, dt)
+    assert np.abs(f[0]).max() > 1.0 and np.abs(f[3]).max() < 1e-12 and np.abs(f[4]).max() < 1e-12
+    h = 1e-6
+    for i in [0, 1, 2, 5]:
+        for c in range(3):
+            xp, xm = x.copy(), x.copy()
+            xp[i, c] += h
+            xm[i, c] -= h
+            fd = -(U(xp) - U(xm)) / (2 * h)
+            assert abs(f[i, c] - fd) < 1e-5 * max(1.0, abs(fd))
