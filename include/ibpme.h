@@ -44,6 +44,8 @@ extern "C" {
 
 typedef struct ibpme_ctx ibpme_ctx;
 
+#define IBPME_MAX_RADIUS_CLASSES 4
+
 typedef enum {
     IBPME_OK = 0,
     IBPME_ERR_ARG = 1,            /* invalid argument (sizes, box, mesh < P, r_cut >= L/2, ...) */
@@ -51,7 +53,8 @@ typedef enum {
     IBPME_ERR_CUFFT = 3,          /* a cuFFT call failed */
     IBPME_ERR_OOM = 4,            /* device allocation failed */
     IBPME_ERR_NOT_CONVERGED = 5,  /* the Krylov solve hit max_iter; outputs hold the last iterate */
-    IBPME_ERR_UNEQUAL_RADII = 6,  /* reserved: one bead radius per system (Sec. III.A) */
+    IBPME_ERR_UNEQUAL_RADII = 6,  /* the call does not take beads of unequal radii (radius classes):
+                                     the batched solve and the learned warm start */
     IBPME_ERR_TIMEOUT = 7,        /* a bounded device wait ran out: the tensor cores of the
                                      learned guess, or the tensor (TMA) copies of a tiled mesh
                                      gather (reported after the gather's stream synchronised:
@@ -84,10 +87,15 @@ typedef struct {
     double r_cut;         /* real-space cutoff, 0 = auto; must be < L/2 */
     int P;                /* stencil points per axis (<= 32), 0 = auto */
     double tol;           /* accuracy target of the automatic rules (e.g. 1e-6); 0 -> 1e-6 */
-    double bead_radius;   /* a, shared by all beads (> 0) */
+    double bead_radius;   /* a, shared by all beads (> 0); ignored with radius classes, where
+                             ibpme_get_params reports the largest class radius */
     double eps_f;         /* fluid permittivity (> 0); eps_f = 1/(4 pi l_B) with kT = 1 */
     int precision;        /* IBPME_FP64 or IBPME_MIXED */
     int max_rhs;          /* largest nrhs a call will pass (1..8); 0 -> 3 */
+    int n_radius_classes; /* 0 or 1: every bead has bead_radius; 2..IBPME_MAX_RADIUS_CLASSES:
+                             beads of unequal radii, bead b of radius class_radius[cls[b]]
+                             with cls bound by ibpme_set_radius_classes */
+    double class_radius[IBPME_MAX_RADIUS_CLASSES];   /* radii of the classes (> 0) */
 } ibpme_params;
 
 /* Create a context: resolves the automatic parameters, allocates the meshes
@@ -104,6 +112,27 @@ ibpme_status ibpme_set_stream(ibpme_ctx* ctx, void* cuda_stream);
 
 /* Copy the resolved parameters (all "auto" fields filled in) to *out. */
 ibpme_status ibpme_get_params(const ibpme_ctx* ctx, ibpme_params* out);
+
+/* Beads of unequal radii (the paper fixes one radius, Sec. III.A; this is its
+ * direct extension).  A bead of radius a carries its charge on a shell whose
+ * transform is j0(ka), so beads alpha and beta interact through
+ *     M_hat(k) = j0(k a_alpha) j0(k a_beta) / (eps k^2)
+ * in place of j0^2(ka)/(eps k^2) of Eq. M00_Fourier.  The library spreads each
+ * class into its own mesh channel, combines the transformed channels with
+ * j0(k a_c) j0(k a_d), gathers each bead from its own class's channel, and gives
+ * every pair within r_cut its two-radius real-space kernel (the average of
+ * erfc(xi s)/(4 pi eps s) over both shells), every bead its own class's self term;
+ * the auto r_cut uses the largest class radius; the body-block preconditioner
+ * and the hard-sphere forces of ibpme_bd_advance (contact at a_alpha + a_beta)
+ * take the bead radii too.
+ *   n    number of beads of the calls that follow (>= 0); 0 unbinds
+ *   cls  host array [n] of class indices in 0 .. n_radius_classes - 1, copied
+ * A context created with n_radius_classes >= 2 needs a binding for the bead
+ * count of every call (IBPME_ERR_ARG otherwise); positions may change between
+ * calls, classes stay with the bead index.  induced_charge_solve_batch and
+ * the learned guesses return IBPME_ERR_UNEQUAL_RADII on such a context.
+ * IBPME_ERR_ARG if the context has no radius classes or an index is out of range. */
+ibpme_status ibpme_set_radius_classes(ibpme_ctx* ctx, int n, const int* cls);
 
 /* Message of the last error raised on the calling thread ("" if none). */
 const char* ibpme_last_error(void);

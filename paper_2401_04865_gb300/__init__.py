@@ -40,7 +40,8 @@ _d, _i, _p = ctypes.c_double, ctypes.c_int, ctypes.c_void_p
 
 class ibpme_params(ctypes.Structure):
     _fields_ = [("box", _d * 3), ("mesh", _i * 3), ("xi", _d), ("eta", _d), ("r_cut", _d), ("P", _i),
-                ("tol", _d), ("bead_radius", _d), ("eps_f", _d), ("precision", _i), ("max_rhs", _i)]
+                ("tol", _d), ("bead_radius", _d), ("eps_f", _d), ("precision", _i), ("max_rhs", _i),
+                ("n_radius_classes", _i), ("class_radius", _d * 4)]
 
 
 class ibpme_bodies(ctypes.Structure):
@@ -76,6 +77,7 @@ SIGNATURES = {
     "ibpme_set_stream": (_i, [_p, _p]),
     "ibpme_get_params": (_i, [_p, ctypes.POINTER(ibpme_params)]),
     "ibpme_last_error": (ctypes.c_char_p, []),
+    "ibpme_set_radius_classes": (_i, [_p, _i, _p]),
     "pme_spread": (_i, [_p, _i, _p, _p, _i, _p]),
     "pme_field": (_i, [_p, _i, _p, _p, _i, _p, _p]),
     "induced_charge_solve": (_i, [_p, _i, _p, ctypes.POINTER(ibpme_bodies), _p, _i,
@@ -173,8 +175,11 @@ def _stream_handle(stream):
     return stream.cuda_stream
 
 
+IBPME_MAX_RADIUS_CLASSES = 4
+
+
 def make_params(box, mesh=(0, 0, 0), tol=1e-6, bead_radius=0.1, eps_f=1.0, precision=IBPME_FP64, max_rhs=3,
-                xi=0.0, eta=0.0, r_cut=0.0, P=0) -> ibpme_params:
+                xi=0.0, eta=0.0, r_cut=0.0, P=0, class_radius=()) -> ibpme_params:
     p = ibpme_params()
     for d in range(3):
         p.box[d] = float(box[d])
@@ -182,6 +187,11 @@ def make_params(box, mesh=(0, 0, 0), tol=1e-6, bead_radius=0.1, eps_f=1.0, preci
     p.xi, p.eta, p.r_cut, p.P = float(xi), float(eta), float(r_cut), int(P)
     p.tol, p.bead_radius, p.eps_f = float(tol), float(bead_radius), float(eps_f)
     p.precision, p.max_rhs = int(precision), int(max_rhs)
+    if len(class_radius) > IBPME_MAX_RADIUS_CLASSES:
+        raise ValueError("at most %d radius classes" % IBPME_MAX_RADIUS_CLASSES)
+    p.n_radius_classes = len(class_radius)
+    for i, r in enumerate(class_radius):
+        p.class_radius[i] = float(r)
     return p
 
 
@@ -206,6 +216,14 @@ def pme_destroy(ctx):
 
 def ibpme_set_stream(ctx, stream):
     return _check(load().ibpme_set_stream(ctx, _stream_handle(stream)), "ibpme_set_stream")
+
+
+def ibpme_set_radius_classes(ctx, n, cls):
+    """Bind the radius class of each of n beads (host int array; None or n = 0 unbinds)."""
+    arr = None if cls is None else np.ascontiguousarray(np.asarray(cls).reshape(-1), dtype=np.int32)
+    if arr is not None and arr.shape[0] != int(n):
+        raise ValueError("one class per bead expected")
+    return _check(load().ibpme_set_radius_classes(ctx, int(n), ptr(arr, np.int32)), "ibpme_set_radius_classes")
 
 
 def ibpme_get_params(ctx) -> ibpme_params:

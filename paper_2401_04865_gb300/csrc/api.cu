@@ -182,6 +182,19 @@ void resolve_params(const ibpme_params* in, ibpme_params* p) {
     *p = *in;
     for (int d = 0; d < 3; ++d)
         if (!(p->box[d] > 0.0) || !std::isfinite(p->box[d])) fail(IBPME_ERR_ARG, "box[%d] must be > 0", d);
+    if (p->n_radius_classes < 0 || p->n_radius_classes > IBPME_MAX_RADIUS_CLASSES)
+        fail(IBPME_ERR_ARG, "n_radius_classes must be in 0..%d", IBPME_MAX_RADIUS_CLASSES);
+    if (p->n_radius_classes >= 2) {   // the largest class radius stands for a in the rules below
+        double amax = 0.0;
+        for (int k = 0; k < p->n_radius_classes; ++k) {
+            const double r = p->class_radius[k];
+            if (!(r > 0.0) || !std::isfinite(r)) fail(IBPME_ERR_ARG, "class_radius[%d] must be > 0", k);
+            amax = std::fmax(amax, r);
+        }
+        p->bead_radius = amax;
+    } else {
+        p->n_radius_classes = 0;
+    }
     if (!(p->bead_radius > 0.0)) fail(IBPME_ERR_ARG, "bead_radius must be > 0");
     if (!(p->eps_f > 0.0)) fail(IBPME_ERR_ARG, "eps_f must be > 0");
     if (p->precision != IBPME_FP64 && p->precision != IBPME_MIXED) fail(IBPME_ERR_ARG, "unknown precision");
@@ -248,6 +261,13 @@ namespace {
 
 void check_n(int n) {
     if (n < 0) fail(IBPME_ERR_ARG, "n must be >= 0");
+}
+
+// A context with radius classes needs them bound for the call's bead count.
+void check_classes(const ibpme_ctx* c, int n) {
+    if (c->ncls > 1 && n > 0 && c->cls_n != n)
+        fail(IBPME_ERR_ARG, "radius classes are bound for %d beads, the call has %d (ibpme_set_radius_classes)",
+             c->cls_n, n);
 }
 
 }  // namespace
@@ -336,18 +356,21 @@ void pme_apply(ibpme_ctx* c, int n, const double* xw, const double* q, int nrhs,
         else if (fm && fm->er) near_field(c, n, xw, q, nrhs, fm->er);
     }
     IBP_CUDA(cudaEventRecord(c->ev_join, c->aux));
-    const int ch = nrhs * c->ncfg;
+    // mesh channel groups: the radius classes, else the configurations
+    const int* mg = mesh_cfg(c);
+    const int ng = mesh_groups(c);
+    const int ch = nrhs * ng;
     const StencilCache* sc = stencil_cache(c, n, xw);
     if (prec == IBPME_MIXED) {
         if (!c->have32) fail(IBPME_ERR_ARG, "mixed precision needs a context created with IBPME_MIXED");
-        c->mesh32.spread(n, xw, q, nrhs, c->bcfg, c->ncfg, c->stream, sc);
+        c->mesh32.spread(n, xw, q, nrhs, mg, ng, c->stream, sc);
         c->mesh32.transform(ch, c->stream);
-        c->mesh32.gather(n, xw, nrhs, c->bcfg, pk, ek, c->stream, sc);
+        c->mesh32.gather(n, xw, nrhs, mg, pk, ek, c->stream, sc);
     } else {
         if (fm && fm->dq)
-            c->mesh64.spread(fm->nf, fm->xf, fm->dq, nrhs, fm->cfg, c->ncfg, c->stream, fm->sc, true);
+            c->mesh64.spread(fm->nf, fm->xf, fm->dq, nrhs, fm->cfg, ng, c->stream, fm->sc, true);
         else
-            c->mesh64.spread(n, xw, q, nrhs, c->bcfg, c->ncfg, c->stream, sc);
+            c->mesh64.spread(n, xw, q, nrhs, mg, ng, c->stream, sc);
         c->mesh64.transform(ch, c->stream);
         if (fm && fm->tmp && !E) {
             c->mesh64.gather(fm->nf, fm->xf, nrhs, fm->cfg, fm->tmp, nullptr, c->stream, fm->sc);
@@ -355,15 +378,16 @@ void pme_apply(ibpme_ctx* c, int n, const double* xw, const double* q, int nrhs,
                 fm->nf, n, nrhs, fm->free_idx, fm->tmp, pk);
             IBP_CHECK_LAUNCH();
         } else {
-            c->mesh64.gather(n, xw, nrhs, c->bcfg, pk, ek ? ek : (fm ? fm->ek : nullptr), c->stream, sc);
+            c->mesh64.gather(n, xw, nrhs, mg, pk, ek ? ek : (fm ? fm->ek : nullptr), c->stream, sc);
             c->field64_ready = !E && fm && fm->ek;
             c->near_field_ready = !E && fm && fm->er;
         }
     }
     IBP_CUDA(cudaStreamWaitEvent(c->stream, c->ev_join, 0));
     if (m) {
-        double* qsum = static_cast<double*>(c->scalars.ensure(sizeof(double) * (size_t)ch));
-        IBP_CUDA(cudaMemsetAsync(qsum, 0, sizeof(double) * ch, c->stream));
+        const int nq = nrhs * c->ncfg;   // k = 0 sums per configuration
+        double* qsum = static_cast<double*>(c->scalars.ensure(sizeof(double) * (size_t)nq));
+        IBP_CUDA(cudaMemsetAsync(qsum, 0, sizeof(double) * nq, c->stream));
         qsum_kernel<<<dim3(div_up(n, 256) < 64 ? div_up(n, 256) : 64, nrhs), 256, 0, c->stream>>>(n, nrhs, q,
                                                                                                 c->bcfg, qsum);
         IBP_CHECK_LAUNCH();
@@ -402,6 +426,8 @@ void pme_apply_free(ibpme_ctx* c, const double* qc, int nrhs, int prec, double* 
     double* pk = fs.psi_k.as<double>();
     const double* xf = fs.xf.as<double>();
     const int* fcfg = c->ncfg > 1 ? c->bodies.free_cfg.as<int>() : nullptr;
+    const int* fmg = c->ncls > 1 ? c->fs.cls_f.as<int>() : fcfg;   // mesh channel group of each free bead
+    const int ng = mesh_groups(c);
     // near field on the second stream, as in pme_apply
     const cudaStream_t main = c->stream;
     IBP_CUDA(cudaEventRecord(c->ev_fork, main));
@@ -416,21 +442,21 @@ void pme_apply_free(ibpme_ctx* c, const double* qc, int nrhs, int prec, double* 
         near_apply_free(c, qc, nrhs, pr, near32 && prec == IBPME_MIXED);
     }
     IBP_CUDA(cudaEventRecord(c->ev_join, c->aux));
-    const int ch = nrhs * c->ncfg;
+    const int ch = nrhs * ng;
     const StencilCache* sc = free_stencil_cache(c);
     if (prec == IBPME_MIXED) {
         if (!c->have32) fail(IBPME_ERR_ARG, "mixed precision needs a context created with IBPME_MIXED");
-        c->mesh32.spread(n, xf, qc, nrhs, fcfg, c->ncfg, c->stream, sc);
+        c->mesh32.spread(n, xf, qc, nrhs, fmg, ng, c->stream, sc);
         c->mesh32.transform(ch, c->stream);
-        c->mesh32.gather(n, xf, nrhs, fcfg, pk, nullptr, c->stream, sc);
+        c->mesh32.gather(n, xf, nrhs, fmg, pk, nullptr, c->stream, sc);
     } else {
-        c->mesh64.spread(n, xf, qc, nrhs, fcfg, c->ncfg, c->stream, sc);
+        c->mesh64.spread(n, xf, qc, nrhs, fmg, ng, c->stream, sc);
         c->mesh64.transform(ch, c->stream);
-        c->mesh64.gather(n, xf, nrhs, fcfg, pk, nullptr, c->stream, sc);
+        c->mesh64.gather(n, xf, nrhs, fmg, pk, nullptr, c->stream, sc);
     }
     IBP_CUDA(cudaStreamWaitEvent(c->stream, c->ev_join, 0));
     double* qsum = fs.qsum.as<double>();
-    IBP_CUDA(cudaMemsetAsync(qsum, 0, sizeof(double) * ch, c->stream));
+    IBP_CUDA(cudaMemsetAsync(qsum, 0, sizeof(double) * nrhs * c->ncfg, c->stream));
     qsum_kernel<<<dim3(div_up(n, 256) < 64 ? div_up(n, 256) : 64, nrhs), 256, 0, c->stream>>>(n, nrhs, qc, fcfg, qsum);
     IBP_CHECK_LAUNCH();
     const double V = c->p.box[0] * c->p.box[1] * c->p.box[2];
@@ -466,11 +492,15 @@ IBP_API ibpme_status pme_setup(ibpme_ctx** ctx, const ibpme_params* params, void
             c->eps = c->p.eps_f;
             c->P = c->p.P;
             c->geom = make_geom(c->p);
-            c->mesh64.init(c->geom, c->p.max_rhs, c->xi, c->eta, c->a, c->stream);
-            c->mesh64.plans(1, c->stream);
+            if (c->p.n_radius_classes >= 2) {
+                c->ncls = c->p.n_radius_classes;
+                for (int k = 0; k < c->ncls; ++k) c->cls_a[k] = c->p.class_radius[k];
+            }
+            c->mesh64.init(c->geom, c->p.max_rhs, c->xi, c->eta, c->a, c->stream, c->ncls, c->cls_a);
+            c->mesh64.plans(c->ncls, c->stream);
             if (c->p.precision == IBPME_MIXED) {
-                c->mesh32.init(c->geom, c->p.max_rhs, c->xi, c->eta, c->a, c->stream);
-                c->mesh32.plans(1, c->stream);
+                c->mesh32.init(c->geom, c->p.max_rhs, c->xi, c->eta, c->a, c->stream, c->ncls, c->cls_a);
+                c->mesh32.plans(c->ncls, c->stream);
                 c->have32 = true;
             }
             IBP_CUDA(cudaStreamCreateWithFlags(&c->work, cudaStreamNonBlocking));
@@ -526,6 +556,38 @@ IBP_API ibpme_status ibpme_set_stream(ibpme_ctx* c, void* cuda_stream) {
     return IBPME_OK;
 }
 
+IBP_API ibpme_status ibpme_set_radius_classes(ibpme_ctx* c, int n, const int* cls) {
+    return guard([&]() -> ibpme_status {
+        if (!c) fail(IBPME_ERR_ARG, "ctx is NULL");
+        DeviceScope ds(c->device);
+        if (c->ncls < 2) fail(IBPME_ERR_ARG, "the context was created without radius classes");
+        check_n(n);
+        if (n > 0 && !cls) fail(IBPME_ERR_ARG, "cls is required");
+        if (n > 0 && is_device_ptr(cls)) fail(IBPME_ERR_ARG, "cls must be a host array");
+        std::vector<int> h(cls, cls + n);
+        for (int i = 0; i < n; ++i)
+            if (h[i] < 0 || h[i] >= c->ncls) fail(IBPME_ERR_ARG, "cls[%d] = %d outside 0..%d", i, h[i], c->ncls - 1);
+        IBP_CUDA(cudaStreamSynchronize(c->stream));   // no earlier call still reads the old binding
+        c->cls.ensure(sizeof(int) * (size_t)(n ? n : 1));
+        if (n > 0) {
+            IBP_CUDA(cudaMemcpyAsync(c->cls.p, h.data(), sizeof(int) * (size_t)n, cudaMemcpyHostToDevice, c->stream));
+            IBP_CUDA(cudaStreamSynchronize(c->stream));
+        }
+        c->cls_h = std::move(h);
+        c->cls_n = n > 0 ? n : -1;
+        ++c->cls_version;
+        // everything keyed by the bead classes is rebuilt by the next call
+        c->near.fp_valid = false;
+        c->stencils.valid = false;
+        c->fs.valid = false;
+        c->fs.sc.valid = false;
+        c->grid64_final = false;
+        c->field64_ready = false;
+        c->near_field_ready = false;
+        return IBPME_OK;
+    });
+}
+
 IBP_API ibpme_status ibpme_get_params(const ibpme_ctx* c, ibpme_params* out) {
     if (!c || !out) {
         set_error("NULL argument");
@@ -571,6 +633,7 @@ IBP_API ibpme_status pme_field(ibpme_ctx* c, int n, const double* x, const doubl
         DeviceScope ds(c->device);
         tma_check(c);
         check_n(n);
+        check_classes(c, n);
         if (nrhs < 1 || nrhs > c->p.max_rhs) fail(IBPME_ERR_ARG, "nrhs %d outside 1..%d", nrhs, c->p.max_rhs);
         if (n > 0 && (!x || !q || !psi)) fail(IBPME_ERR_ARG, "x, q and psi are required");
         const double* dx = static_cast<const double*>(stage_in(c, x, sizeof(double) * 3 * n, c->st_x));
@@ -644,6 +707,9 @@ void solve_run(ibpme_ctx* c, int n, const double* x, const ibpme_bodies* bodies,
                double* S_out, SolveCall& call) {
     check_n(n);
     if (n == 0) fail(IBPME_ERR_ARG, "a solve needs at least one bead");
+    if (c->ncls > 1 && ncfg > 1)
+        fail(IBPME_ERR_UNEQUAL_RADII, "the batched solve takes one bead radius (this context has radius classes)");
+    check_classes(c, n);
     if (nrhs < 1 || nrhs > c->p.max_rhs) fail(IBPME_ERR_ARG, "nrhs %d outside 1..%d", nrhs, c->p.max_rhs);
     if (!x || !E0 || !q_out) fail(IBPME_ERR_ARG, "x, E0 and q_out are required");
     if (ncfg < 1) fail(IBPME_ERR_ARG, "n_configs must be >= 1");
@@ -666,6 +732,8 @@ void solve_run(ibpme_ctx* c, int n, const double* x, const ibpme_bodies* bodies,
     if (learned && !o.mlp) fail(IBPME_ERR_ARG, "a learned guess needs opts->mlp");
     if (o.guess != IBPME_GUESS_ZERO && o.guess != IBPME_GUESS_USER && !learned) fail(IBPME_ERR_ARG, "unknown guess mode");
     if (learned && cfg_bodies) fail(IBPME_ERR_ARG, "a batched solve takes no learned guess");
+    if (learned && c->ncls > 1)
+        fail(IBPME_ERR_UNEQUAL_RADII, "the learned guess takes one bead radius (this context has radius classes)");
     if (o.precond != IBPME_PRECOND_BODY && o.precond != IBPME_PRECOND_NONE) fail(IBPME_ERR_ARG, "unknown precond");
     a.precond = o.precond == IBPME_PRECOND_BODY;
     a.user_guess = o.guess == IBPME_GUESS_USER || learned;
@@ -766,7 +834,7 @@ const double* solution_field(ibpme_ctx* c, int n, const double* xw, const double
     IBP_CUDA(cudaEventRecord(c->ev_join, c->aux));
     if (!c->field64_ready) {   // the final residual did not gather the mesh field with its potential
         const StencilCache* sc = stencil_cache(c, n, xw);
-        c->mesh64.gather(n, xw, 1, nullptr, c->psi_k.as<double>(), ek, c->stream, sc);
+        c->mesh64.gather(n, xw, 1, mesh_cfg(c), c->psi_k.as<double>(), ek, c->stream, sc);
     }
     IBP_CUDA(cudaStreamWaitEvent(c->stream, c->ev_join, 0));
     add_kernel<<<div_up(3LL * n, 256), 256, 0, c->stream>>>(3LL * n, er, ek, E);
@@ -804,6 +872,7 @@ IBP_API ibpme_status body_force_torque(ibpme_ctx* c, int n, const double* x, con
         if (!c) fail(IBPME_ERR_ARG, "ctx is NULL");
         DeviceScope ds(c->device);
         check_n(n);
+        check_classes(c, n);
         if (n == 0) fail(IBPME_ERR_ARG, "n must be >= 1");
         if (!x || !q || !E0 || !F || !L) fail(IBPME_ERR_ARG, "x, q, E0, F and L are required");
         const int nb = bodies ? bodies->n_bodies : 0;
@@ -890,6 +959,7 @@ IBP_API ibpme_status ibpme_bd_step(ibpme_ctx* c, int n, const double* x, const i
         if (!c) fail(IBPME_ERR_ARG, "ctx is NULL");
         DeviceScope ds(c->device);
         check_n(n);
+        check_classes(c, n);
         if (n == 0) fail(IBPME_ERR_ARG, "n must be >= 1");
         if (!x || !f_bead || !bd || !x_out || !X_out) fail(IBPME_ERR_ARG, "missing argument");
         if (!(bd->dt > 0) || !(bd->gamma > 0) || !(bd->kT >= 0)) fail(IBPME_ERR_ARG, "need dt > 0, gamma > 0, kT >= 0");
@@ -976,6 +1046,7 @@ IBP_API ibpme_status ibpme_capacitance(ibpme_ctx* c, int n, const double* x, con
         DeviceScope ds(c->device);
         const auto t0 = std::chrono::steady_clock::now();
         check_n(n);
+        check_classes(c, n);
         if (n == 0) fail(IBPME_ERR_ARG, "the capacitance needs at least one body");
         if (!x || !bodies || !C_out) fail(IBPME_ERR_ARG, "x, bodies and C_out are required");
         const int nb = bodies->n_bodies;

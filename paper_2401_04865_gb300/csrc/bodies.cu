@@ -257,11 +257,19 @@ __global__ void hard_sphere_list_kernel(const int* __restrict__ ov_count, const 
     }
 }
 
+// Radii of the radius classes (beads of unequal radii: contact at a_alpha + a_beta).
+struct HsRadii {
+    double a[IBPME_MAX_RADIUS_CLASSES];
+};
+
+// cls: radius class of each bead, or NULL for one radius a (the FP32 screen then
+// takes a as the largest radius).
 __global__ void hard_sphere_kernel(int n, const double* __restrict__ xw, const float4* __restrict__ xf, double L0,
                                    double L1, double L2, const long long* __restrict__ rowptr,
                                    const int* __restrict__ col, const int* __restrict__ order,
-                                   const int* __restrict__ bead_body, double a, double coef,
-                                   const double* __restrict__ f_in, double* __restrict__ f_out) {
+                                   const int* __restrict__ bead_body, double a, const int* __restrict__ cls,
+                                   HsRadii R, double coef, const double* __restrict__ f_in,
+                                   double* __restrict__ f_out) {
     const int t = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (t >= n) return;
@@ -282,9 +290,10 @@ __global__ void hard_sphere_kernel(int n, const double* __restrict__ xw, const f
         const double dy = min_image_wrapped(y0 - xw[3 * be + 1], L1);
         const double dz = min_image_wrapped(z0 - xw[3 * be + 2], L2);
         const double r2 = dx * dx + dy * dy + dz * dz;
-        if (r2 < 4.0 * a * a && r2 > 0.0) {   // overlap: the only pairs that need r
+        const double contact = cls ? R.a[cls[al]] + R.a[cls[be]] : 2.0 * a;
+        if (r2 < contact * contact && r2 > 0.0) {   // overlap: the only pairs that need r
             const double r = sqrt(r2);
-            const double m = coef * (2.0 * a - r) / r;
+            const double m = coef * (contact - r) / r;
             fx += m * dx;
             fy += m * dy;
             fz += m * dz;
@@ -608,16 +617,19 @@ void bd_step(ibpme_ctx* c, int n, const double* xw, const double* f, const ibpme
     ProfScope ps(ST_BODIES, s);
     double* ftot = static_cast<double*>(bd.scratch.ensure(sizeof(double) * (3 * (size_t)n + 9 * (size_t)bd.nb)));
     double* Rm = ftot + 3 * (size_t)n;
-    if (nl.ov_valid) {
+    if (nl.ov_valid && c->ncls == 1) {
         IBP_CUDA(cudaMemcpyAsync(ftot, f, sizeof(double) * 3 * (size_t)n, cudaMemcpyDeviceToDevice, s));
         hard_sphere_list_kernel<<<152 * 4, 128, 0, s>>>(nl.ov_count.as<int>(), nl.ov_list.as<int>(), xw, c->p.box[0],
                                                         c->p.box[1], c->p.box[2], nl.prow.as<int>(), nl.col.as<int>(),
                                                         nl.cell_beads.as<int>(), bd.bead_body.as<int>(), c->a,
                                                         p->gamma / (2.0 * p->dt), ftot);
     } else {
+        HsRadii R{};
+        for (int k = 0; k < c->ncls; ++k) R.a[k] = c->cls_a[k];
         hard_sphere_kernel<<<div_up((long long)n * 32, 128), 128, 0, s>>>(
             n, xw, nl.xf.as<float4>(), c->p.box[0], c->p.box[1], c->p.box[2], nl.rowptr.as<long long>(),
-            nl.col.as<int>(), nl.cell_beads.as<int>(), bd.bead_body.as<int>(), c->a, p->gamma / (2.0 * p->dt), f, ftot);
+            nl.col.as<int>(), nl.cell_beads.as<int>(), bd.bead_body.as<int>(), c->a,
+            c->ncls > 1 ? c->cls.as<int>() : nullptr, R, p->gamma / (2.0 * p->dt), f, ftot);
     }
     IBP_CHECK_LAUNCH();
     BdConst bc{p->dt, p->gamma, p->kT, p->seed, (unsigned)(p->step & 0xffffffffLL)};

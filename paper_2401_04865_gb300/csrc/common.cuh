@@ -131,6 +131,7 @@ struct StencilCache {
     bool valid = false;
     unsigned long long fp = 0;   // position fingerprint the cache belongs to
     int n = 0, ncfg = 0;
+    unsigned long long cls_key = 0;   // radius-class binding the channels belong to (0: none)
     DevBuf start;                // int4 per bead: first node (x, y, z), configuration
     DevBuf frac;                 // double4 per bead: (first node - x / h) per axis
     DevBuf frac32;               // float4 per bead: the same offsets in FP32 (FP32 kernels)
@@ -151,14 +152,18 @@ constexpr int kTileNodes = 8;    // tile edge in grid nodes
 
 // Spectral-Ewald mesh engine in one precision: grids, spectrum, Green's table, plans.
 // A grid "channel" holds one right-hand side of one configuration: channel
-// cfg * nrhs + r (a single system is configuration 0).
+// cfg * nrhs + r (a single system is configuration 0).  With beads of unequal
+// radii the channels group the beads by radius class instead (channel
+// class * nrhs + r) and the scaling combines them (see transform).
 template <typename T>
 struct Mesh {
     MeshGeom g{};
     int rcap = 0;   // channels the buffers hold
     DevBuf grid;    // [rcap][G] real
     DevBuf spec;    // [rcap][Gc] complex
-    DevBuf green;   // [Gc] real: G(k) / (N_x N_y N_z), 0 at k = 0
+    DevBuf green;   // [Gc] real: G(k) / (N_x N_y N_z), 0 at k = 0 (without j0^2 with radius classes)
+    int ncls = 1;   // radius classes (1: one radius, its j0^2 inside green)
+    DevBuf jtab;    // [ncls][Gc] real: j0(k a_c) of each class
     DevBuf work;    // cuFFT work area shared by the plans
     std::map<int, std::pair<cufftHandle, cufftHandle>> plan;   // R2C and C2R plans by channel count
     // FP64 meshes of power-of-two sizes: double-float transforms instead of cuFFT (dffft.cu)
@@ -177,7 +182,9 @@ struct Mesh {
     int* tma_err_host = nullptr;   // mapped host flag: a bounded wait for a tensor copy ran out
     int* tma_err_dev = nullptr;
     int tma_failed();              // read and clear the flag (after a synchronisation): 0, or its code
-    void init(const MeshGeom& geom, int channels, double xi, double eta, double a, cudaStream_t s);
+    // ncls > 1: radius classes of radii cls_a[0 .. ncls) (no double-float transforms then)
+    void init(const MeshGeom& geom, int channels, double xi, double eta, double a, cudaStream_t s, int ncls = 1,
+              const double* cls_a = nullptr);
     void destroy();
     void ensure_channels(int ch);
     void plans(int ch, cudaStream_t s);   // every resource a transform of ch channels needs
@@ -186,7 +193,9 @@ struct Mesh {
     // accumulate: add to the grid as it is instead of zeroing it first
     void spread(int n, const double* xw, const double* q, int nrhs, const int* bead_cfg, int ncfg, cudaStream_t s,
                 const StencilCache* sc = nullptr, bool accumulate = false);
-    // R2C, scale, C2R over ch channels; the double-float transforms leave grid as it was
+    // R2C, scale, C2R over ch channels; the double-float transforms leave grid as it was.
+    // With radius classes the ch channels are ncls groups of ch / ncls right-hand sides and
+    // the scaling sets channel (d, r) to G(k) j0(k a_d) sum_c j0(k a_c) channel (c, r)
     void transform(int ch, cudaStream_t s);
     void gather(int n, const double* xw, int nrhs, const int* bead_cfg, double* psi, double* E, cudaStream_t s,
                 const StencilCache* sc = nullptr);
@@ -230,6 +239,8 @@ struct NearList {
     int fp_pre_n = -1;
     const double* fp_pre_xw = nullptr;
     int ncfg = 1;
+    unsigned long long cls_key = 0;   // radius-class binding of the pair values (0: none)
+    DevBuf self_b;                 // [n] self term of each bead's radius class (radius classes only)
     // Compact bodies: multi-bead bodies within min(r_c, L/4) of their centre.
     // Their intra-body pairs are left out of the table and evaluated directly
     // by the compact kernels (FP32 for the inner operator, double-float for the
@@ -312,6 +323,8 @@ struct FreeSet {
     int cb_ntasks = 0;
     unsigned long long cb_tasks_key = 0;
     DevBuf psi_r, psi_k, qsum;        // [R][nfree] partial potentials, [channels] charge sums
+    DevBuf cls_f, self_f;             // radius classes: class and self term of each free bead
+    unsigned long long cls_key = 0;   // the binding they belong to
 };
 
 // Body-block preconditioner (precond.cu): inverses of the bodies' free-space
@@ -322,6 +335,7 @@ struct Precond {
     struct Shape {
         int nb;
         double m2, m4;        // rotation-invariant moments of the bead cloud
+        unsigned long long ckey;   // hash of the beads' radius classes in bead order (0: one radius)
         long long off, goff;  // element offsets of M^{-1} and of g in minv / gvec
     };
     std::vector<Shape> shapes;
@@ -334,6 +348,7 @@ struct Precond {
     // every multi-bead body (-1: identity), and the moments of the last positions
     // (copied asynchronously into pinned memory, checked at the next solve)
     unsigned long long prep_version = 0;
+    unsigned long long prep_cls = 0;        // radius-class binding of that preparation
     bool prep_valid = false;
     std::vector<int> assign;
     double* hm_pin = nullptr;
@@ -428,12 +443,29 @@ struct ibpme_ctx {
     ibp::StencilCache stencils;               // stencils of the current positions
     ibp::FreeSet fs;                          // the free beads on their own (Krylov operator)
     ibp::DevBuf cap_psi, cap_q, cap_zero;     // grand capacitance: bead potentials, charges, zeros
+    // beads of unequal radii: ncls classes of radii cls_a (ncls = 1: every bead has radius a);
+    // cls [cls_n] binds a class to each bead of the calls with cls_n beads
+    int ncls = 1;
+    double cls_a[IBPME_MAX_RADIUS_CLASSES] = {};
+    int cls_n = -1;
+    ibp::DevBuf cls;
+    std::vector<int> cls_h;
+    unsigned long long cls_version = 0;       // bumped by every binding (cache keys; 0: none)
     ibp::Precond pre;                         // body-block preconditioner
     cudaStream_t aux = nullptr;               // second branch of a PME evaluation (near field)
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
 };
 
 namespace ibp {
+
+// The mesh channel group of each bead (device, or NULL for one group) and the number of
+// groups: the radius classes with beads of unequal radii, else the configurations.
+inline const int* mesh_cfg(const ibpme_ctx* c) {
+    return c->ncls > 1 ? static_cast<const int*>(c->cls.p) : c->bcfg;
+}
+inline int mesh_groups(const ibpme_ctx* c) { return c->ncls > 1 ? c->ncls : c->ncfg; }
+// The binding key of the radius classes (0 with one radius).
+inline unsigned long long cls_key(const ibpme_ctx* c) { return c->ncls > 1 ? c->cls_version : 0; }
 
 // ---- near.cu ----
 // exclusive scan of n int counts into n + 1 int64 offsets (out[n] = total)

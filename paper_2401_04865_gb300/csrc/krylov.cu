@@ -794,7 +794,8 @@ struct Solver {
         const Mesh<double>& m64 = c->mesh64;
         // make every lazily created resource exist before capture (this may grow the meshes
         // and build the stencil cache of these positions)
-        if (prec == IBPME_MIXED) c->mesh32.plans(R * ncfg, s()); else c->mesh64.plans(R * ncfg, s());
+        const int ng = mesh_groups(c);   // mesh channel groups: radius classes or configurations
+        if (prec == IBPME_MIXED) c->mesh32.plans(R * ng, s()); else c->mesh64.plans(R * ng, s());
         stencil_cache(c, n, a.xw);
         pme_reserve(c, n, R, false);
         auto P = [](const void* p) { return (long long)(size_t)p; };
@@ -804,6 +805,8 @@ struct Solver {
                                       P(c->near.val.p), P(c->near.pair32.p), P(c->near.qf.p), P(c->near.qs.p), P(c->near.cell_beads.p), P(c->near.rowptr.p), P(a.xw), P(bd.free_idx.p),
                                       P(bd.free_unk.p), P(bd.bead_body.p), P(bd.body_unk.p), P(bd.mb_unk.p),
                                       P(bd.mb_first.p), P(bd.mb_cnt.p), P(bd.uo.p), P(c->bcfg),
+                                      (long long)cls_key(c), P(c->cls.p), P(c->near.self_b.p), P(c->fs.cls_f.p),
+                                      P(c->fs.self_f.p),
                                       (long long)c->stencils.valid, P(c->stencils.start.p), P(c->stencils.frac.p), P(c->stencils.frac32.p),
                                       (long long)c->stencils.tiles, (long long)c->stencils.tile_n[0],
                                       (long long)c->stencils.tile_n[1], (long long)c->stencils.tile_n[2],
@@ -927,8 +930,9 @@ struct Solver {
             const bool fp64 = prec == IBPME_FP64;
             const bool can_keep = fp64 && use_free && c->mesh64.df && nfree > 0;
             const StencilCache* fsc = can_keep ? free_stencil_cache(c) : nullptr;
-            FreeMesh fm{nfree, c->fs.xf.as<double>(), I(bd.free_idx), ncfg > 1 ? bd.free_cfg.as<int>() : nullptr,
-                        fsc, nullptr, nullptr};
+            FreeMesh fm{nfree, c->fs.xf.as<double>(), I(bd.free_idx),
+                        c->ncls > 1 ? c->fs.cls_f.as<int>() : (ncfg > 1 ? bd.free_cfg.as<int>() : nullptr), fsc,
+                        nullptr, nullptr};
             // a residual that may be the last one gathers the mesh field with the potential
             // when the force pass follows (one field, one configuration)
             const bool field = fp64 && a.want_field && R == 1 && ncfg == 1 && !(can_keep && fsc && fit_psi);

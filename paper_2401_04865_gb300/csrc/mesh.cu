@@ -1907,8 +1907,23 @@ bool tiles_fit(const MeshGeom& g, const StencilCache* sc, int nrhs) {
     return sc && sc->tiles && nrhs <= 8 && tile_smem_bytes<T>(g, nrhs) + kTmaPad <= kTileSmemMax;
 }
 
+// |k| of half-spectrum entry t (x fastest, N_x / 2 + 1 entries per row).
+__device__ __forceinline__ double half_spectrum_k2(const MeshGeom& g, long long t) {
+    const int nxh = g.N[0] / 2 + 1;
+    const double two_pi = 6.283185307179586476925286766559;
+    const int kx_i = (int)(t % nxh);
+    const long long rest = t / nxh;
+    const int ky_i = (int)(rest % g.N[1]);
+    const int kz_i = (int)(rest / g.N[1]);
+    const int my = ky_i <= g.N[1] / 2 ? ky_i : ky_i - g.N[1];
+    const int mz = kz_i <= g.N[2] / 2 ? kz_i : kz_i - g.N[2];
+    const double kx = two_pi * kx_i / g.L[0], ky = two_pi * my / g.L[1], kz = two_pi * mz / g.L[2];
+    return kx * kx + ky * ky + kz * kz;
+}
+
 // G(k)/(N_x N_y N_z) on the half spectrum, Eq. after H_hat:
 // j0^2(k a) e^{-(1 - eta) k^2 / (4 xi^2)} / k^2, zero at k = 0 (Sec. II, k = 0 removed).
+// a = 0 leaves the j0^2 factor out (radius classes apply theirs in mix_kernel).
 template <typename T>
 __global__ void green_kernel(MeshGeom g, double xi, double eta, double a, T* __restrict__ green) {
     const int nxh = g.N[0] / 2 + 1;
@@ -1927,10 +1942,56 @@ __global__ void green_kernel(MeshGeom g, double xi, double eta, double a, T* __r
         double v = 0.0;
         if (k2 > 0.0) {
             const double k = sqrt(k2);
-            const double j0 = sin(k * a) / (k * a);
+            const double j0 = a > 0.0 ? sin(k * a) / (k * a) : 1.0;
             v = j0 * j0 * exp(-(1.0 - eta) * k2 / (4.0 * xi * xi)) / k2 * norm;
         }
         green[t] = (T)v;
+    }
+}
+
+// j0(k a_c) = sin(k a_c) / (k a_c) of every class on the half spectrum (1 at k = 0).
+struct ClassRadii {
+    double a[IBPME_MAX_RADIUS_CLASSES];
+};
+
+template <typename T>
+__global__ void class_j0_kernel(MeshGeom g, int ncls, ClassRadii R, T* __restrict__ jtab) {
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < g.Gc;
+         t += (long long)gridDim.x * blockDim.x) {
+        const double k = sqrt(half_spectrum_k2(g, t));
+        for (int c = 0; c < ncls; ++c) {
+            const double x = k * R.a[c];
+            jtab[(size_t)c * g.Gc + t] = (T)(x > 0.0 ? sin(x) / x : 1.0);
+        }
+    }
+}
+
+// Scaling with radius classes (the pair kernel j0(k a_c) j0(k a_d) G(k)): for each
+// right-hand side r, S = sum_c j0(k a_c) H_hat(c, r), then channel (d, r) becomes
+// G(k) j0(k a_d) S.  The source and the target factor of every pair are applied, so
+// each bead's gather from its own class's channel sees every class's charges.
+template <typename T>
+__global__ void mix_kernel(long long Gc, int nrhs, int ncls, const T* __restrict__ green, const T* __restrict__ jtab,
+                           typename Cplx<T>::type* __restrict__ spec) {
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < Gc; t += (long long)gridDim.x * blockDim.x) {
+        const T gk = green[t];
+        T j[IBPME_MAX_RADIUS_CLASSES];
+        for (int c = 0; c < ncls; ++c) j[c] = jtab[(size_t)c * Gc + t];
+        for (int r = 0; r < nrhs; ++r) {
+            T sx = 0, sy = 0;
+            for (int c = 0; c < ncls; ++c) {
+                const typename Cplx<T>::type v = spec[(size_t)(c * nrhs + r) * Gc + t];
+                sx += j[c] * v.x;
+                sy += j[c] * v.y;
+            }
+            for (int d = 0; d < ncls; ++d) {
+                const T f = gk * j[d];
+                typename Cplx<T>::type o;
+                o.x = f * sx;
+                o.y = f * sy;
+                spec[(size_t)(d * nrhs + r) * Gc + t] = o;
+            }
+        }
     }
 }
 
@@ -1966,20 +2027,30 @@ int grid_blocks(long long work, int threads) {
 }  // namespace
 
 template <typename T>
-void Mesh<T>::init(const MeshGeom& geom, int channels, double xi, double eta, double a, cudaStream_t s) {
+void Mesh<T>::init(const MeshGeom& geom, int channels, double xi, double eta, double a, cudaStream_t s, int nc,
+                   const double* cls_a) {
     g = geom;
     rcap = 0;
+    ncls = nc > 1 ? nc : 1;
     if (!tma_err_host) {   // here, outside any stream capture (the gathers only write it)
         IBP_CUDA(cudaHostAlloc(reinterpret_cast<void**>(&tma_err_host), sizeof(int), cudaHostAllocMapped));
         *tma_err_host = 0;
         IBP_CUDA(cudaHostGetDevicePointer(reinterpret_cast<void**>(&tma_err_dev), tma_err_host, 0));
     }
-    df = sizeof(T) == 8 && df_fft_supported(g);
+    // the double-float transforms fuse the scaling of one channel at a time: one radius only
+    df = sizeof(T) == 8 && df_fft_supported(g) && ncls == 1;
     if (df) df_fft_init(g, df_tw, s);
-    ensure_channels(channels);
+    ensure_channels(channels * ncls);
     green.ensure(sizeof(T) * (size_t)g.Gc);
-    green_kernel<T><<<grid_blocks(g.Gc, 256), 256, 0, s>>>(g, xi, eta, a, green.as<T>());
+    green_kernel<T><<<grid_blocks(g.Gc, 256), 256, 0, s>>>(g, xi, eta, ncls > 1 ? 0.0 : a, green.as<T>());
     IBP_CHECK_LAUNCH();
+    if (ncls > 1) {
+        ClassRadii R{};
+        for (int c = 0; c < ncls; ++c) R.a[c] = cls_a[c];
+        jtab.ensure(sizeof(T) * (size_t)g.Gc * ncls);
+        class_j0_kernel<T><<<grid_blocks(g.Gc, 256), 256, 0, s>>>(g, ncls, R, jtab.as<T>());
+        IBP_CHECK_LAUNCH();
+    }
     if constexpr (sizeof(T) == 8) {
         if (df) {
             green_df.ensure(sizeof(float2) * (size_t)g.Gc);
@@ -2048,6 +2119,7 @@ void Mesh<T>::destroy() {
     grid.release();
     spec.release();
     green.release();
+    jtab.release();
     green_df.release();
     grid_df.release();
     potential_df = false;
@@ -2107,7 +2179,13 @@ void Mesh<T>::transform(int ch, cudaStream_t s) {
     }
     {
         ProfScope ps(mesh_stage<T>(ST_SCALE), s);
-        scale_kernel<T><<<dim3(grid_blocks(g.Gc, 256), ch), 256, 0, s>>>(g.Gc, green.as<T>(), spec.as<C>());
+        if (ncls > 1) {
+            if (ch % ncls) fail(IBPME_ERR_ARG, "internal: %d channels for %d radius classes", ch, ncls);
+            mix_kernel<T><<<grid_blocks(g.Gc, 256), 256, 0, s>>>(g.Gc, ch / ncls, ncls, green.as<T>(), jtab.as<T>(),
+                                                               spec.as<C>());
+        } else {
+            scale_kernel<T><<<dim3(grid_blocks(g.Gc, 256), ch), 256, 0, s>>>(g.Gc, green.as<T>(), spec.as<C>());
+        }
         IBP_CHECK_LAUNCH();
     }
     ProfScope ps(mesh_stage<T>(ST_FFT_INV), s);
@@ -2192,7 +2270,7 @@ void build_stencils(ibpme_ctx* c, StencilCache& b, int n, const double* xw, cons
               std::getenv("IBPME_NO_TILES") == nullptr;   // the switch lets tests compare both paths
     if (b.tiles) {
         for (int d = 0; d < 3; ++d) b.tile_n[d] = div_up(g.N[d], kTileNodes);
-        const long long nkeys = (long long)b.tile_n[0] * b.tile_n[1] * b.tile_n[2] * c->ncfg;
+        const long long nkeys = (long long)b.tile_n[0] * b.tile_n[1] * b.tile_n[2] * mesh_groups(c);
         if (nkeys > (1LL << 30)) {
             b.tiles = false;
         } else {
@@ -2218,7 +2296,8 @@ void build_stencils(ibpme_ctx* c, StencilCache& b, int n, const double* xw, cons
     }
     b.fp = c->near.fp;
     b.n = n;
-    b.ncfg = c->ncfg;
+    b.ncfg = mesh_groups(c);
+    b.cls_key = cls_key(c);
     b.valid = true;
 }
 
@@ -2227,8 +2306,8 @@ void build_stencils(ibpme_ctx* c, StencilCache& b, int n, const double* xw, cons
 const StencilCache* stencil_cache(ibpme_ctx* c, int n, const double* xw) {
     if (n == 0 || !c->near.fp_valid) return nullptr;   // no fingerprint of these positions: no cache key
     StencilCache& b = c->stencils;
-    if (b.valid && b.fp == c->near.fp && b.n == n && b.ncfg == c->ncfg) return &b;
-    build_stencils(c, b, n, xw, c->bcfg);
+    if (b.valid && b.fp == c->near.fp && b.n == n && b.ncfg == mesh_groups(c) && b.cls_key == cls_key(c)) return &b;
+    build_stencils(c, b, n, xw, mesh_cfg(c));
     return &b;
 }
 
@@ -2237,8 +2316,9 @@ const StencilCache* free_stencil_cache(ibpme_ctx* c) {
     const int n = fs.nfree;
     if (n == 0 || !fs.valid) return nullptr;
     StencilCache& b = c->fs.sc;
-    if (b.valid && b.fp == c->near.fp && b.n == n && b.ncfg == c->ncfg) return &b;
-    build_stencils(c, b, n, fs.xf.as<double>(), c->ncfg > 1 ? c->bodies.free_cfg.as<int>() : nullptr);
+    if (b.valid && b.fp == c->near.fp && b.n == n && b.ncfg == mesh_groups(c) && b.cls_key == cls_key(c)) return &b;
+    const int* grp = c->ncls > 1 ? c->fs.cls_f.as<int>() : (c->ncfg > 1 ? c->bodies.free_cfg.as<int>() : nullptr);
+    build_stencils(c, b, n, fs.xf.as<double>(), grp);
     return &b;
 }
 

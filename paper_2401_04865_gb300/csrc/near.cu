@@ -44,6 +44,11 @@ struct PairConst {
     // pairs inside one compact body are not tabulated (NULL: every pair is)
     const int* bbody;   // body of each bead
     const int* cflag;   // compact flag of each body
+    // beads of unequal radii (ncls > 1): class of each bead, class radii and self terms
+    int ncls;
+    const int* cls;
+    double ra[IBPME_MAX_RADIUS_CLASSES];
+    double selfc[IBPME_MAX_RADIUS_CLASSES];
 };
 
 constexpr int kOctaveIntervals = 128;   // intervals per octave of u (a power of two)
@@ -70,6 +75,47 @@ __device__ __forceinline__ void pair_kernel(double r, const PairConst& k, double
         phi += -1.0 / (4.0 * kPi * r) + (4.0 * k.a - r) / (16.0 * kPi * k.a * k.a);
         dphi += 1.0 / (4.0 * kPi * r * r) - 1.0 / (16.0 * kPi * k.a * k.a);
     }
+}
+
+// Two radii a and b (beads of unequal radii).  A bead's charge sits on a shell of
+// its radius, so the pair kernel is the average of erfc(xi s)/(4 pi s) over both
+// shells.  With g and A, B above taken at a b in place of a^2, the average is
+//   phi_r = [g(r+a+b) - g(r+a-b) - g(r-a+b) + g(r-a-b)] / r
+//           - sum over the negative arguments s of sign_s s^2 / (16 pi a b r)
+// (the second line turns g, taken as printed for s < 0, into the odd extension
+// the shell average needs; for a = b it is the Heaviside term of the one-radius
+// kernel).  Coincident beads (r = 0) take the limit
+//   [F'(a+b) - F'(|a-b|)] / (2ab),  F'(u) = (u erfc(xi u) - e^{-xi^2 u^2}/(xi sqrt(pi))) / (4 pi),
+// which for a = b is the self term.
+__device__ void pair_kernel2(double r, double a, double b, double xi, double& phi, double& dphi) {
+    const double A = 1.0 / (32.0 * pow(kPi, 1.5) * a * b * xi);
+    const double B = 1.0 / (64.0 * kPi * a * b * xi * xi);
+    const double c2 = 1.0 / (16.0 * kPi * a * b);
+    const double x2 = xi * xi;
+    const double sv[4] = {r + a + b, r + a - b, r - a + b, r - a - b};
+    const double sg[4] = {1.0, -1.0, -1.0, 1.0};
+    double N = 0.0, dN = 0.0;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const double u = sv[i];
+        const double e = exp(-u * u * x2);
+        const double ec = erfc(u * xi);
+        N += sg[i] * (-A * u * e + B * (2.0 * x2 * u * u + 1.0) * ec);
+        dN += sg[i] * (-2.0 * A * e + 4.0 * B * x2 * u * ec);
+        if (u < 0.0) {
+            N -= c2 * sg[i] * u * u;
+            dN -= 2.0 * c2 * sg[i] * u;
+        }
+    }
+    phi = N / r;
+    dphi = dN / r - N / (r * r);
+}
+
+__device__ double pair_limit2(double a, double b, double xi) {
+    auto dF = [xi](double u) {
+        return (u * erfc(xi * u) - exp(-xi * xi * u * u) / (xi * sqrt(kPi))) / (4.0 * kPi);
+    };
+    return (dF(a + b) - dF(fabs(a - b))) / (2.0 * a * b);
 }
 
 // phi_r, phi_r', phi_r'' for r >= 2a from the second-difference form, with
@@ -401,7 +447,43 @@ __global__ void pair_values_kernel(long long np, const double* __restrict__ xw, 
     if (gfac) gfac[p] = g;
 }
 
-// psi_r[r][alpha] = (phi_self q_alpha + sum_pairs phi_r q_beta) / eps.
+// Pair values with radius classes: the exact two-radius kernel of each pair in FP64
+// (every pair of classes has its own kernel; no table).
+__global__ void pair_values_cls_kernel(long long np, const double* __restrict__ xw, PairConst k,
+                                       const int* __restrict__ prow, const int* __restrict__ col,
+                                       const int* __restrict__ order, double* __restrict__ val,
+                                       uint2* __restrict__ pair32, double* __restrict__ gfac) {
+    const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= np) return;
+    const int a = order[prow[p]], cb = col[p], b = order[cb];
+    const double dx = min_image_wrapped(xw[3 * a + 0] - xw[3 * b + 0], k.L[0]);
+    const double dy = min_image_wrapped(xw[3 * a + 1] - xw[3 * b + 1], k.L[1]);
+    const double dz = min_image_wrapped(xw[3 * a + 2] - xw[3 * b + 2], k.L[2]);
+    const double r2 = dx * dx + dy * dy + dz * dz;
+    const double ra = k.ra[k.cls[a]], rb = k.ra[k.cls[b]];
+    double phi, g;
+    if (r2 > 0.0) {
+        const double r = sqrt(r2);
+        double dphi;
+        pair_kernel2(r, ra, rb, k.xi, phi, dphi);
+        g = -dphi / r;
+    } else {
+        phi = pair_limit2(ra, rb, k.xi);   // coincident beads: the r -> 0 limit, no field
+        g = 0.0;
+    }
+    val[p] = phi;
+    pair32[p] = make_uint2((unsigned)cb, __float_as_uint((float)phi));
+    if (gfac) gfac[p] = g;
+}
+
+// Self term of each bead's class (radius classes).
+__global__ void class_self_kernel(int n, const int* __restrict__ cls, PairConst k, double* __restrict__ self_b) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) self_b[i] = k.selfc[cls[i]];
+}
+
+// psi_r[r][alpha] = (phi_self q_alpha + sum_pairs phi_r q_beta) / eps; with radius
+// classes phi_self is selfv[alpha].
 // One warp per row for NR right-hand sides; four independent accumulation
 // chains per lane keep several gathers in flight on long rows.  The charges are
 // first packed in the sorted order with the right-hand sides interleaved, so a
@@ -417,8 +499,8 @@ __global__ void pack_q64_kernel(int n, int nrhs, const int* __restrict__ order, 
 template <int NR>
 __global__ void near_apply_kernel(int n, const long long* __restrict__ rowptr, const int* __restrict__ col,
                                   const double* __restrict__ val, const int* __restrict__ order, double self,
-                                  double inv_eps, const double* __restrict__ qs, const double* __restrict__ q,
-                                  double* __restrict__ psi) {
+                                  const double* __restrict__ selfv, double inv_eps, const double* __restrict__ qs,
+                                  const double* __restrict__ q, double* __restrict__ psi) {
     const int t = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (t >= n) return;
@@ -445,10 +527,11 @@ __global__ void near_apply_kernel(int n, const long long* __restrict__ rowptr, c
         for (int r = 0; r < NR; ++r) acc[0][r] += v * qb[r];
     }
     const int alpha = order[t];
+    const double sf = selfv ? selfv[alpha] : self;
 #pragma unroll
     for (int r = 0; r < NR; ++r) {
         const double sum = warp_sum((acc[0][r] + acc[1][r]) + (acc[2][r] + acc[3][r]));
-        if (lane == 0) psi[(size_t)r * n + alpha] = (sum + self * q[(size_t)r * n + alpha]) * inv_eps;
+        if (lane == 0) psi[(size_t)r * n + alpha] = (sum + sf * q[(size_t)r * n + alpha]) * inv_eps;
     }
 }
 
@@ -471,8 +554,8 @@ constexpr int kChains32 = 8;   // pairs per lane in flight in the FP32 pass
 
 template <int NR>
 __global__ void near_apply32_kernel(int n, const long long* __restrict__ rowptr, const uint2* __restrict__ pair32,
-                                    const int* __restrict__ order, double self, double inv_eps,
-                                    const float4* __restrict__ qf, const double* __restrict__ q,
+                                    const int* __restrict__ order, double self, const double* __restrict__ selfv,
+                                    double inv_eps, const float4* __restrict__ qf, const double* __restrict__ q,
                                     double* __restrict__ psi) {
     const int t = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
@@ -507,10 +590,11 @@ __global__ void near_apply32_kernel(int n, const long long* __restrict__ rowptr,
         for (int r = 0; r < NR; ++r) acc[r] += v * qb[r];
     }
     const int alpha = order[t];
+    const double sf = selfv ? selfv[alpha] : self;
 #pragma unroll
     for (int r = 0; r < NR; ++r) {
         const double sum = warp_sum((double)acc[r]);
-        if (lane == 0) psi[(size_t)r * n + alpha] = (sum + self * q[(size_t)r * n + alpha]) * inv_eps;
+        if (lane == 0) psi[(size_t)r * n + alpha] = (sum + sf * q[(size_t)r * n + alpha]) * inv_eps;
     }
 }
 
@@ -1288,6 +1372,14 @@ PairConst make_const(const ibpme_ctx* c) {
         while (k.K < kMaxOctaves && ldexp(1.0, k.K) < uc) ++k.K;
         if (uc <= 1.0) k.K = 0;                        // r_c <= 2a: no tabulated range
     }
+    k.ncls = c->ncls;
+    k.cls = c->ncls > 1 ? c->cls.as<int>() : nullptr;
+    for (int q = 0; q < c->ncls && c->ncls > 1; ++q) {
+        const double a = c->cls_a[q];
+        k.ra[q] = a;
+        k.selfc[q] = (1.0 - exp(-4.0 * a * a * c->xi * c->xi)) / (8.0 * pow(kPi, 1.5) * a * a * c->xi) +
+                     erfc(2.0 * a * c->xi) / (4.0 * kPi * a);
+    }
     for (int d = 0; d < 3; ++d) {
         k.L[d] = c->p.box[d];
         k.nc[d] = c->near.nc[d];
@@ -1509,14 +1601,19 @@ void near_build(ibpme_ctx* c, int n, const double* xw, bool need_grad) {
     }
     // compact bodies whenever the call has bodies (their structure is part of the cache key)
     const BodyData& bd = c->bodies;
+    // (the compact kernels and the double-float pair values take one bead radius)
     const bool want_cb = c->bodies_current && bd.nmb > 0 && bd.host_n == n && make_const(c).K > 0 &&
+                         c->ncls == 1 &&
                          std::getenv("IBPME_NO_COMPACT") == nullptr;   // the switch lets tests compare both paths
     const unsigned long long cb_key = want_cb ? bd.version : 0;
-    if (nl.fp_valid && nl.n == n && nl.fp == print && nl.ncfg == c->ncfg && nl.cb_key == cb_key) return;
+    if (nl.fp_valid && nl.n == n && nl.fp == print && nl.ncfg == c->ncfg && nl.cb_key == cb_key &&
+        nl.cls_key == cls_key(c))
+        return;
     nl.fp_valid = false;
     nl.ov_valid = false;
     nl.cb_on = false;
     nl.cb_key = cb_key;
+    nl.cls_key = cls_key(c);
     nl.n = n;
     nl.rc = c->rc;
     int ncells = 1;
@@ -1598,7 +1695,16 @@ void near_build(ibpme_ctx* c, int n, const double* xw, bool need_grad) {
             pair_fill_kernel<<<div_up((long long)n * 32, 128), 128, 0, s>>>(n, xw, xf, k, cell_of, cell_start,
                                                                              cell_beads, rowptr, col, prow);
         IBP_CHECK_LAUNCH();
-        if (nl.npairs > 0 && k.K > 0 && nl.npairs < (1LL << 31)) {
+        if (c->ncls > 1) {   // beads of unequal radii: the exact two-radius kernel per pair
+            double* self_b = static_cast<double*>(nl.self_b.ensure(sizeof(double) * (size_t)n));
+            class_self_kernel<<<div_up(n, 256), 256, 0, s>>>(n, k.cls, k, self_b);
+            IBP_CHECK_LAUNCH();
+            if (nl.npairs > 0) {
+                pair_values_cls_kernel<<<div_up(nl.npairs, 256), 256, 0, s>>>(nl.npairs, xw, k, prow, col,
+                                                                              cell_beads, val, pair32, gfac);
+                IBP_CHECK_LAUNCH();
+            }
+        } else if (nl.npairs > 0 && k.K > 0 && nl.npairs < (1LL << 31)) {
             // table pairs in double-float arithmetic, overlapping beads listed and valued exactly
             float4* xdf = static_cast<float4*>(nl.xdf.ensure(sizeof(float4) * 2 * (size_t)(n + 1)));
             pos_df_kernel<<<div_up(n, 256), 256, 0, s>>>(n, xw, xdf);
@@ -1645,16 +1751,17 @@ void near_apply(ibpme_ctx* c, int n, const double* q, int nrhs, double* psi_r, b
     const double ie = 1.0 / c->eps;
     cudaStream_t s = c->stream;
     const int* od = nl.cell_beads.as<int>();
+    const double* sv = c->ncls > 1 ? nl.self_b.as<double>() : nullptr;   // self term of each bead's class
     if (fp32) {
         float4* qf = static_cast<float4*>(nl.qf.ensure(sizeof(float4) * n));
         pack_q32_kernel<<<div_up(n, 256), 256, 0, s>>>(n, nrhs, od, q, qf);
         IBP_CHECK_LAUNCH();
         const uint2* pc = nl.pair32.as<uint2>();
         switch (nrhs) {
-            case 1: near_apply32_kernel<1><<<blocks, 128, 0, s>>>(n, rp, pc, od, k.self, ie, qf, q, psi_r); break;
-            case 2: near_apply32_kernel<2><<<blocks, 128, 0, s>>>(n, rp, pc, od, k.self, ie, qf, q, psi_r); break;
-            case 3: near_apply32_kernel<3><<<blocks, 128, 0, s>>>(n, rp, pc, od, k.self, ie, qf, q, psi_r); break;
-            default: near_apply32_kernel<4><<<blocks, 128, 0, s>>>(n, rp, pc, od, k.self, ie, qf, q, psi_r); break;
+            case 1: near_apply32_kernel<1><<<blocks, 128, 0, s>>>(n, rp, pc, od, k.self, sv, ie, qf, q, psi_r); break;
+            case 2: near_apply32_kernel<2><<<blocks, 128, 0, s>>>(n, rp, pc, od, k.self, sv, ie, qf, q, psi_r); break;
+            case 3: near_apply32_kernel<3><<<blocks, 128, 0, s>>>(n, rp, pc, od, k.self, sv, ie, qf, q, psi_r); break;
+            default: near_apply32_kernel<4><<<blocks, 128, 0, s>>>(n, rp, pc, od, k.self, sv, ie, qf, q, psi_r); break;
         }
         IBP_CHECK_LAUNCH();
         if (nl.cb_on && nl.cb_ntasks > 0) compact_apply<true>(c, cb_args(c), n, q, nrhs, psi_r);
@@ -1664,14 +1771,14 @@ void near_apply(ibpme_ctx* c, int n, const double* q, int nrhs, double* psi_r, b
     pack_q64_kernel<<<div_up(n, 256), 256, 0, s>>>(n, nrhs, od, q, qs);
     IBP_CHECK_LAUNCH();
     switch (nrhs) {
-        case 1: near_apply_kernel<1><<<blocks, 128, 0, s>>>(n, rp, cl, vl, od, k.self, ie, qs, q, psi_r); break;
-        case 2: near_apply_kernel<2><<<blocks, 128, 0, s>>>(n, rp, cl, vl, od, k.self, ie, qs, q, psi_r); break;
-        case 3: near_apply_kernel<3><<<blocks, 128, 0, s>>>(n, rp, cl, vl, od, k.self, ie, qs, q, psi_r); break;
-        case 4: near_apply_kernel<4><<<blocks, 128, 0, s>>>(n, rp, cl, vl, od, k.self, ie, qs, q, psi_r); break;
-        case 5: near_apply_kernel<5><<<blocks, 128, 0, s>>>(n, rp, cl, vl, od, k.self, ie, qs, q, psi_r); break;
-        case 6: near_apply_kernel<6><<<blocks, 128, 0, s>>>(n, rp, cl, vl, od, k.self, ie, qs, q, psi_r); break;
-        case 7: near_apply_kernel<7><<<blocks, 128, 0, s>>>(n, rp, cl, vl, od, k.self, ie, qs, q, psi_r); break;
-        default: near_apply_kernel<8><<<blocks, 128, 0, s>>>(n, rp, cl, vl, od, k.self, ie, qs, q, psi_r); break;
+        case 1: near_apply_kernel<1><<<blocks, 128, 0, s>>>(n, rp, cl, vl, od, k.self, sv, ie, qs, q, psi_r); break;
+        case 2: near_apply_kernel<2><<<blocks, 128, 0, s>>>(n, rp, cl, vl, od, k.self, sv, ie, qs, q, psi_r); break;
+        case 3: near_apply_kernel<3><<<blocks, 128, 0, s>>>(n, rp, cl, vl, od, k.self, sv, ie, qs, q, psi_r); break;
+        case 4: near_apply_kernel<4><<<blocks, 128, 0, s>>>(n, rp, cl, vl, od, k.self, sv, ie, qs, q, psi_r); break;
+        case 5: near_apply_kernel<5><<<blocks, 128, 0, s>>>(n, rp, cl, vl, od, k.self, sv, ie, qs, q, psi_r); break;
+        case 6: near_apply_kernel<6><<<blocks, 128, 0, s>>>(n, rp, cl, vl, od, k.self, sv, ie, qs, q, psi_r); break;
+        case 7: near_apply_kernel<7><<<blocks, 128, 0, s>>>(n, rp, cl, vl, od, k.self, sv, ie, qs, q, psi_r); break;
+        default: near_apply_kernel<8><<<blocks, 128, 0, s>>>(n, rp, cl, vl, od, k.self, sv, ie, qs, q, psi_r); break;
     }
     IBP_CHECK_LAUNCH();
     if (nl.cb_on && nl.cb_ntasks > 0) compact_apply<false>(c, cb_args(c), n, q, nrhs, psi_r);
@@ -1721,6 +1828,16 @@ __global__ void free_positions_kernel(int nfree, const int* __restrict__ free_id
     if (i >= 3 * nfree) return;
     const int f = i / 3, d = i - 3 * f;
     xf[i] = xw[3 * free_idx[f] + d];
+}
+
+// Radius class and self term of each free bead.
+__global__ void free_class_kernel(int nfree, const int* __restrict__ free_idx, const int* __restrict__ cls,
+                                  const double* __restrict__ self_b, int* __restrict__ cls_f,
+                                  double* __restrict__ self_f) {
+    const int f = blockIdx.x * blockDim.x + threadIdx.x;
+    if (f >= nfree) return;
+    cls_f[f] = cls[free_idx[f]];
+    self_f[f] = self_b[free_idx[f]];
 }
 
 // Compact-body relative positions in list order.
@@ -1783,11 +1900,19 @@ bool near_free_build(ibpme_ctx* c, const double* xw) {
     const BodyData& bd = c->bodies;
     const int n = nl.n, nf = bd.nfree;
     if (!nl.fp_valid || !c->bodies_current || bd.host_n != n || nf == 0) return false;
-    if (fs.valid && fs.fp == nl.fp && fs.version == bd.version && fs.nfree == nf) return true;
+    if (fs.valid && fs.fp == nl.fp && fs.version == bd.version && fs.nfree == nf && fs.cls_key == cls_key(c))
+        return true;
     cudaStream_t s = c->stream;
     fs.valid = false;
     fs.nfree = nf;
     const int* fidx = bd.free_idx.as<int>();
+    if (c->ncls > 1) {   // class and self term of each free bead
+        int* cf = static_cast<int*>(fs.cls_f.ensure(sizeof(int) * (size_t)nf));
+        double* sf = static_cast<double*>(fs.self_f.ensure(sizeof(double) * (size_t)nf));
+        free_class_kernel<<<div_up(nf, 256), 256, 0, s>>>(nf, fidx, c->cls.as<int>(), nl.self_b.as<double>(), cf, sf);
+        IBP_CHECK_LAUNCH();
+    }
+    fs.cls_key = cls_key(c);
     double* xf = static_cast<double*>(fs.xf.ensure(sizeof(double) * 3 * (size_t)nf));
     free_positions_kernel<<<div_up(3LL * nf, 256), 256, 0, s>>>(nf, fidx, xw, xf);
     IBP_CHECK_LAUNCH();
@@ -1862,16 +1987,17 @@ void near_apply_free(ibpme_ctx* c, const double* qc, int nrhs, double* psi_r, bo
     cudaStream_t s = c->stream;
     const int* od = c->bodies.iota.as<int>();   // rows are list positions already
     const bool cb = c->near.cb_on && fs.cb_ntasks > 0;
+    const double* sv = c->ncls > 1 ? fs.self_f.as<double>() : nullptr;
     if (fp32) {
         float4* qf = fs.qf.as<float4>();
         pack_q32_kernel<<<div_up(n, 256), 256, 0, s>>>(n, nrhs, od, qc, qf);
         IBP_CHECK_LAUNCH();
         const uint2* pc = fs.pair32.as<uint2>();
         switch (nrhs) {
-            case 1: near_apply32_kernel<1><<<blocks, 128, 0, s>>>(n, rp, pc, od, k.self, ie, qf, qc, psi_r); break;
-            case 2: near_apply32_kernel<2><<<blocks, 128, 0, s>>>(n, rp, pc, od, k.self, ie, qf, qc, psi_r); break;
-            case 3: near_apply32_kernel<3><<<blocks, 128, 0, s>>>(n, rp, pc, od, k.self, ie, qf, qc, psi_r); break;
-            default: near_apply32_kernel<4><<<blocks, 128, 0, s>>>(n, rp, pc, od, k.self, ie, qf, qc, psi_r); break;
+            case 1: near_apply32_kernel<1><<<blocks, 128, 0, s>>>(n, rp, pc, od, k.self, sv, ie, qf, qc, psi_r); break;
+            case 2: near_apply32_kernel<2><<<blocks, 128, 0, s>>>(n, rp, pc, od, k.self, sv, ie, qf, qc, psi_r); break;
+            case 3: near_apply32_kernel<3><<<blocks, 128, 0, s>>>(n, rp, pc, od, k.self, sv, ie, qf, qc, psi_r); break;
+            default: near_apply32_kernel<4><<<blocks, 128, 0, s>>>(n, rp, pc, od, k.self, sv, ie, qf, qc, psi_r); break;
         }
         IBP_CHECK_LAUNCH();
         if (cb) compact_apply<true>(c, cb_args_free(c), n, qc, nrhs, psi_r);
@@ -1883,14 +2009,14 @@ void near_apply_free(ibpme_ctx* c, const double* qc, int nrhs, double* psi_r, bo
     const int* cl = fs.col.as<int>();
     const double* vl = fs.val.as<double>();
     switch (nrhs) {
-        case 1: near_apply_kernel<1><<<blocks, 128, 0, s>>>(n, rp, cl, vl, od, k.self, ie, qs, qc, psi_r); break;
-        case 2: near_apply_kernel<2><<<blocks, 128, 0, s>>>(n, rp, cl, vl, od, k.self, ie, qs, qc, psi_r); break;
-        case 3: near_apply_kernel<3><<<blocks, 128, 0, s>>>(n, rp, cl, vl, od, k.self, ie, qs, qc, psi_r); break;
-        case 4: near_apply_kernel<4><<<blocks, 128, 0, s>>>(n, rp, cl, vl, od, k.self, ie, qs, qc, psi_r); break;
-        case 5: near_apply_kernel<5><<<blocks, 128, 0, s>>>(n, rp, cl, vl, od, k.self, ie, qs, qc, psi_r); break;
-        case 6: near_apply_kernel<6><<<blocks, 128, 0, s>>>(n, rp, cl, vl, od, k.self, ie, qs, qc, psi_r); break;
-        case 7: near_apply_kernel<7><<<blocks, 128, 0, s>>>(n, rp, cl, vl, od, k.self, ie, qs, qc, psi_r); break;
-        default: near_apply_kernel<8><<<blocks, 128, 0, s>>>(n, rp, cl, vl, od, k.self, ie, qs, qc, psi_r); break;
+        case 1: near_apply_kernel<1><<<blocks, 128, 0, s>>>(n, rp, cl, vl, od, k.self, sv, ie, qs, qc, psi_r); break;
+        case 2: near_apply_kernel<2><<<blocks, 128, 0, s>>>(n, rp, cl, vl, od, k.self, sv, ie, qs, qc, psi_r); break;
+        case 3: near_apply_kernel<3><<<blocks, 128, 0, s>>>(n, rp, cl, vl, od, k.self, sv, ie, qs, qc, psi_r); break;
+        case 4: near_apply_kernel<4><<<blocks, 128, 0, s>>>(n, rp, cl, vl, od, k.self, sv, ie, qs, qc, psi_r); break;
+        case 5: near_apply_kernel<5><<<blocks, 128, 0, s>>>(n, rp, cl, vl, od, k.self, sv, ie, qs, qc, psi_r); break;
+        case 6: near_apply_kernel<6><<<blocks, 128, 0, s>>>(n, rp, cl, vl, od, k.self, sv, ie, qs, qc, psi_r); break;
+        case 7: near_apply_kernel<7><<<blocks, 128, 0, s>>>(n, rp, cl, vl, od, k.self, sv, ie, qs, qc, psi_r); break;
+        default: near_apply_kernel<8><<<blocks, 128, 0, s>>>(n, rp, cl, vl, od, k.self, sv, ie, qs, qc, psi_r); break;
     }
     IBP_CHECK_LAUNCH();
     if (cb) compact_apply<false>(c, cb_args_free(c), n, qc, nrhs, psi_r);

@@ -78,15 +78,34 @@ __global__ void shape_moments_kernel(int nmb, const int* __restrict__ mb_body, c
     }
 }
 
-// M_b of one body from its beads' relative positions (row-major nb x nb, FP32)
+struct PrecondRadii {
+    double a[IBPME_MAX_RADIUS_CLASSES];
+};
+
+// Free-space potential between shells of radii a and b, centres r apart (the real-space
+// form of j0(ka) j0(kb)/k^2): 1/(4 pi r) apart, 1/(4 pi max(a, b)) one inside the
+// other, (2(ab + ar + br) - a^2 - b^2 - r^2)/(16 pi a b r) overlapping; for a = b the
+// (4a - r)/(16 pi a^2) of Sec. II.
+__device__ __forceinline__ double shell_pair(double r, double a, double b) {
+    if (r >= a + b) return 1.0 / (4.0 * kPi * r);
+    if (r <= fabs(a - b)) return 1.0 / (4.0 * kPi * fmax(a, b));
+    return (2.0 * (a * b + a * r + b * r) - a * a - b * b - r * r) / (16.0 * kPi * a * b * r);
+}
+
+// M_b of one body from its beads' relative positions (row-major nb x nb, FP32);
+// cls: the beads' radius classes (NULL: every bead has radius a)
 __global__ void block_matrix_kernel(int nb, const double* __restrict__ rel, double a, double eps,
-                                    float* __restrict__ A) {
+                                    const int* __restrict__ cls, PrecondRadii R, float* __restrict__ A) {
     const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (t >= (long long)nb * nb) return;
     const int i = (int)(t / nb), j = (int)(t % nb);
     const double dx = rel[3 * i] - rel[3 * j], dy = rel[3 * i + 1] - rel[3 * j + 1],
                  dz = rel[3 * i + 2] - rel[3 * j + 2];
     const double r = sqrt(dx * dx + dy * dy + dz * dz);
+    if (cls) {
+        A[t] = (float)(shell_pair(r, R.a[cls[i]], R.a[cls[j]]) / eps);
+        return;
+    }
     A[t] = (float)(r >= 2.0 * a ? 1.0 / (4.0 * kPi * eps * r) : (4.0 * a - r) / (16.0 * kPi * a * a * eps));
 }
 
@@ -322,6 +341,14 @@ bool shape_matches(const Precond::Shape& sp, int nb, double m2, double m4) {
            std::fabs(sp.m4 - m4) <= 1e-9 * std::fabs(m4) + 1e-300;
 }
 
+// Order-dependent hash of the radius classes of beads first .. first + nb - 1 (0: one radius).
+unsigned long long class_hash(const ibpme_ctx* c, int first, int nb) {
+    if (c->ncls < 2) return 0;
+    unsigned long long h = 0x9E3779B97F4A7C15ull;
+    for (int i = 0; i < nb; ++i) h = (h ^ (unsigned long long)(c->cls_h[first + i] + 1)) * 0x100000001B3ull;
+    return h | 1ull;
+}
+
 // Moments of the current positions into pinned memory, without waiting (the
 // solve synchronises before it returns, so the next call can read them).
 void queue_moments(ibpme_ctx* c) {
@@ -384,7 +411,8 @@ bool precond_prepare(ibpme_ctx* c) {
     // the next check.  A body that changed shape is caught one solve late, which
     // costs iterations, not accuracy (a right preconditioner does not change the
     // solution).
-    if (P.prep_valid && P.prep_version == bd.version && P.hm_pin && (int)P.assign.size() == bd.nmb) {
+    if (P.prep_valid && P.prep_version == bd.version && P.prep_cls == cls_key(c) && P.hm_pin &&
+        (int)P.assign.size() == bd.nmb) {
         bool same = true;
         for (int b = 0; b < bd.nmb && same; ++b) {
             const int id = P.assign[b];
@@ -428,9 +456,10 @@ bool precond_prepare(ibpme_ctx* c) {
         const int nb = mb_cnt[b];
         if (nb > kPrecondMaxBeads || !cfg_ok[cfg_of(mb_body[b])]) continue;
         const double m2 = hm[2 * b], m4 = hm[2 * b + 1];
+        const unsigned long long ck = class_hash(c, off[mb_body[b]], nb);
         int id = -1;
         for (size_t q = 0; q < P.shapes.size(); ++q) {
-            if (shape_matches(P.shapes[q], nb, m2, m4)) {
+            if (P.shapes[q].ckey == ck && shape_matches(P.shapes[q], nb, m2, m4)) {
                 id = (int)q;
                 break;
             }
@@ -454,6 +483,7 @@ bool precond_prepare(ibpme_ctx* c) {
             sp.nb = nb;
             sp.m2 = m2;
             sp.m4 = m4;
+            sp.ckey = ck;
             sp.off = P.used;
             sp.goff = P.gused;
             P.used += (long long)nb * nb;
@@ -464,7 +494,10 @@ bool precond_prepare(ibpme_ctx* c) {
             float* A = P.minv.as<float>() + sp.off;   // inverted in place in the cache
             const double* rel = bd.rel.as<double>() + 3 * (size_t)off[mb_body[b]];
             const long long nn = (long long)nb * nb;
-            block_matrix_kernel<<<div_up(nn, 256), 256, 0, s>>>(nb, rel, c->a, c->eps, A);
+            PrecondRadii R{};
+            for (int q = 0; q < c->ncls; ++q) R.a[q] = c->cls_a[q];
+            const int* bcls = c->ncls > 1 ? c->cls.as<int>() + off[mb_body[b]] : nullptr;
+            block_matrix_kernel<<<div_up(nn, 256), 256, 0, s>>>(nb, rel, c->a, c->eps, bcls, R, A);
             IBP_CHECK_LAUNCH();
             invert_spd(c, nb, A);
             finish_shape_kernel<<<nb, 128, 0, s>>>(nb, A, P.gvec.as<float>() + sp.goff);
@@ -484,6 +517,7 @@ bool precond_prepare(ibpme_ctx* c) {
     }
     P.assign = assign;
     P.prep_version = bd.version;
+    P.prep_cls = cls_key(c);
     if (pb_shape.empty()) {
         P.prep_valid = true;   // the structure is known to leave every body unpreconditioned
         queue_moments(c);
