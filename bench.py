@@ -560,6 +560,7 @@ def bench_ours(args, ib, torch, rank, world, local):
     st.close()
     if wl == "lattice" and not args.skip_second:
         out["charged_sphere"] = second_workload(ib, torch, rank, flush, max(10, args.steps))
+        out["unequal_radii"] = radii_workload(ib, torch, s, flush, max(10, args.steps), value / world)
     elif wl != "lattice" and not args.skip_scale:
         out["pme_at_scale"] = pme_at_scale(ib, torch, flush, 10)
     return out, s
@@ -577,6 +578,33 @@ def second_workload(ib, torch, rank, flush, k):
     out = {"workload": SPHERE, "solves_per_s": k / (sum(ms) / 1e3), "ms_per_step": sum(ms) / k, "steps": k,
            "iters": st.last_stats.iters, "pme_evals_per_s": pme["evals_per_s"], "pme_roofline": pme["roofline"]}
     st.close()
+    return out
+
+
+RADII_WORKLOAD = ("the lattice step with the 100,000 ions at bead radius 0.1 and the surface beads at 0.05 "
+                  "(two radius classes: class mesh channels, two-radius pair kernel)")
+
+
+def radii_workload(ib, torch, s, flush, k, one_radius_value):
+    """The lattice step (same system, guess and precision) with beads of two radii:
+    the ions at twice the surface beads' radius."""
+    ion = np.diff(s.body_offsets)[np.repeat(np.arange(s.n_bodies), np.diff(s.body_offsets))] == 1
+    ctx = ib.pme_setup(ib.make_params(box=s.box, mesh=s.mesh, tol=s.tol, eps_f=s.eps, precision=ib.IBPME_MIXED,
+                                      max_rhs=1, class_radius=(s.a, 2.0 * s.a)), torch.cuda.current_stream())
+    try:
+        ib.ibpme_set_radius_classes(ctx, s.n, ion.astype(np.int32))
+        st = Step(ib, torch, s, ib.IBPME_MIXED, GUESS["lattice"], ctx=ctx)
+        for _ in range(5):
+            st.run()
+        torch.cuda.synchronize()
+        ms = timed_steps(torch, st, k, flush, st.stream)
+        rate = k / (sum(ms) / 1e3)
+        out = {"workload": RADII_WORKLOAD, "solves_per_s": rate, "ms_per_step": sum(ms) / k, "steps": k,
+               "iters": st.last_stats.iters, "r_cut": ib.ibpme_get_params(ctx).r_cut,
+               "vs_one_radius": rate / one_radius_value}
+        st.close()
+    finally:
+        ib.pme_destroy(ctx)
     return out
 
 

@@ -170,6 +170,7 @@ struct Mesh {
     bool df = false;
     DevBuf df_tw[3], df_buf;
     DevBuf green_df;   // the Green's table as (hi, lo) float pairs for the double-float transforms
+    DevBuf jtab_df;    // [ncls][Gc] j0(k a_c) as (hi, lo) float pairs (radius classes)
     DevBuf grid_df;    // [rcap][G] (hi, lo) floats: the transformed grid of the double-float transforms
     bool potential_df = false;   // the last transform left the potential in grid_df (gathers read it)
     unsigned long long writes = 0;   // spreads into grid so far (a kept grid is intact while this holds)
@@ -241,6 +242,8 @@ struct NearList {
     int ncfg = 1;
     unsigned long long cls_key = 0;   // radius-class binding of the pair values (0: none)
     DevBuf self_b;                 // [n] self term of each bead's radius class (radius classes only)
+    DevBuf cls_table, cls_tab32, cls_tabdf;   // radius classes: the tables of every pair of classes
+    int cls_K = 0;                 // their octaves (0: no tables, every pair takes the exact kernel)
     // Compact bodies: multi-bead bodies within min(r_c, L/4) of their centre.
     // Their intra-body pairs are left out of the table and evaluated directly
     // by the compact kernels (FP32 for the inner operator, double-float for the
@@ -493,8 +496,9 @@ void near_apply_free(ibpme_ctx* c, const double* qc, int nrhs, double* psi_r, bo
 // ---- dffft.cu ----
 bool df_fft_supported(const MeshGeom& g);
 void df_fft_init(const MeshGeom& g, DevBuf tw[3], cudaStream_t s);
+// ncls > 1: radius classes, the channels mixed by j0(k a_c) j0(k a_d) (jtab [ncls][Gc] hi + lo)
 void df_fft_convolve(const MeshGeom& g, int ch, const float2* green, const double* grid, float2* out, float4* S,
-                     DevBuf tw[3], cudaStream_t s);
+                     DevBuf tw[3], cudaStream_t s, int ncls = 1, const float2* jtab = nullptr);
 
 // ---- mesh.cu ----
 // Cached stencils for the current positions (rebuilt when the position

@@ -15,6 +15,7 @@
 #include "common.cuh"
 #include "dfloat.cuh"
 
+#include <algorithm>
 #include <cmath>
 #include <vector>
 
@@ -283,9 +284,11 @@ dfy_kernel(DfGeom d, float4* __restrict__ S, const float4* __restrict__ tw, int 
 
 // z pass on the half spectrum: forward FFT, Green's-function scaling (the FP64
 // half-spectrum table split into hi + lo floats), inverse FFT, for columns
-// x0 .. x0 + cols at one y
+// x0 .. x0 + cols at one y.  mode 1 stops after the forward FFT and mode 2 runs the
+// inverse FFT alone (radius classes: the scaling mixes the channels in between).
 __global__ void __launch_bounds__(kDfThreads, kDfMinBlocks)
-dfz_scale_kernel(DfGeom d, float4* __restrict__ S, const float4* __restrict__ tw, const float2* __restrict__ green) {
+dfz_scale_kernel(DfGeom d, float4* __restrict__ S, const float4* __restrict__ tw, const float2* __restrict__ green,
+                 int mode) {
     __shared__ float4 buf[kDfSmem];
     const int n = d.n[2], cols = d.pl[2], ny = d.n[1], h = d.h, ls = df_ls(n), pts = cols * n;
     const size_t ch = blockIdx.y;
@@ -298,23 +301,49 @@ dfz_scale_kernel(DfGeom d, float4* __restrict__ S, const float4* __restrict__ tw
         buf[c * ls + sw(z)] = x0 + c < h ? col[(size_t)z * zstride + c] : make_float4(0.f, 0.f, 0.f, 0.f);
     }
     __syncthreads();
-    fft_lines<false>(buf, n, d.logn[2], pts, tw);
-    for (int e = threadIdx.x; e < pts; e += kDfThreads) {
-        const int c = e / n, z = e % n;
-        if (x0 + c >= h) continue;
-        const float2 gv = green[((size_t)z * ny + y) * h + x0 + c];
-        const df gk = {gv.x, gv.y};
-        float4& slot = buf[c * ls + sw(z)];
-        dfc v = load_c(slot);
-        v.re = df_mul(v.re, gk);
-        v.im = df_mul(v.im, gk);
-        slot = store_c(v);
+    if (mode != 2) fft_lines<false>(buf, n, d.logn[2], pts, tw);
+    if (mode == 0) {
+        for (int e = threadIdx.x; e < pts; e += kDfThreads) {
+            const int c = e / n, z = e % n;
+            if (x0 + c >= h) continue;
+            const float2 gv = green[((size_t)z * ny + y) * h + x0 + c];
+            const df gk = {gv.x, gv.y};
+            float4& slot = buf[c * ls + sw(z)];
+            dfc v = load_c(slot);
+            v.re = df_mul(v.re, gk);
+            v.im = df_mul(v.im, gk);
+            slot = store_c(v);
+        }
+        __syncthreads();
     }
-    __syncthreads();
-    fft_lines<true>(buf, n, d.logn[2], pts, tw);
+    if (mode != 1) fft_lines<true>(buf, n, d.logn[2], pts, tw);
     for (int e = threadIdx.x; e < pts; e += kDfThreads) {
         const int z = e / cols, c = e % cols;
         if (x0 + c < h) col[(size_t)z * zstride + c] = buf[c * ls + sw(z)];
+    }
+}
+
+// Scaling with radius classes between the z passes, in double-float arithmetic: for
+// every right-hand side r, S = sum_c j0(k a_c) H(c, r), then H(d, r) = G(k) j0(k a_d) S,
+// G and j0 as hi + lo floats ([Gh] and [ncls][Gh]).
+__global__ void dfz_mix_kernel(long long Gh, int nrhs, int ncls, float4* __restrict__ S,
+                               const float2* __restrict__ green, const float2* __restrict__ jtab) {
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < Gh; t += (long long)gridDim.x * blockDim.x) {
+        const df gk = {green[t].x, green[t].y};
+        df j[IBPME_MAX_RADIUS_CLASSES];
+        for (int c = 0; c < ncls; ++c) j[c] = df{jtab[(size_t)c * Gh + t].x, jtab[(size_t)c * Gh + t].y};
+        for (int r = 0; r < nrhs; ++r) {
+            dfc sum = {{0.0f, 0.0f}, {0.0f, 0.0f}};
+            for (int c = 0; c < ncls; ++c) {
+                const dfc v = load_c(S[(size_t)(c * nrhs + r) * Gh + t]);
+                sum.re = df_add(sum.re, df_mul(v.re, j[c]));
+                sum.im = df_add(sum.im, df_mul(v.im, j[c]));
+            }
+            for (int dd = 0; dd < ncls; ++dd) {
+                const df f = df_mul(gk, j[dd]);
+                S[(size_t)(dd * nrhs + r) * Gh + t] = store_c(dfc{df_mul(sum.re, f), df_mul(sum.im, f)});
+            }
+        }
     }
 }
 
@@ -371,7 +400,7 @@ void df_fft_init(const MeshGeom& g, DevBuf tw[3], cudaStream_t s) {
 // grid (FP64, [ch][G]) -> out ([ch][G], hi + lo floats): the inverse transform of G(k)
 // times the grid's transform.
 void df_fft_convolve(const MeshGeom& g, int ch, const float2* green, const double* grid, float2* out, float4* S,
-                     DevBuf tw[3], cudaStream_t s) {
+                     DevBuf tw[3], cudaStream_t s, int ncls, const float2* jtab) {
     DfGeom d;
     for (int a = 0; a < 3; ++a) {
         d.n[a] = g.N[a];
@@ -395,7 +424,17 @@ void df_fft_convolve(const MeshGeom& g, int ch, const float2* green, const doubl
     }
     {
         ProfScope ps(ST_SCALE64, s);
-        dfz_scale_kernel<<<gz, kDfThreads, 0, s>>>(d, S, tw[2].as<float4>(), green);
+        if (ncls > 1) {
+            if (ch % ncls) fail(IBPME_ERR_ARG, "internal: %d channels for %d radius classes", ch, ncls);
+            dfz_scale_kernel<<<gz, kDfThreads, 0, s>>>(d, S, tw[2].as<float4>(), green, 1);
+            IBP_CHECK_LAUNCH();
+            const long long blocks = std::min<long long>((d.Gh + 255) / 256, 152LL * 16);
+            dfz_mix_kernel<<<(unsigned)blocks, 256, 0, s>>>(d.Gh, ch / ncls, ncls, S, green, jtab);
+            IBP_CHECK_LAUNCH();
+            dfz_scale_kernel<<<gz, kDfThreads, 0, s>>>(d, S, tw[2].as<float4>(), green, 2);
+        } else {
+            dfz_scale_kernel<<<gz, kDfThreads, 0, s>>>(d, S, tw[2].as<float4>(), green, 0);
+        }
         IBP_CHECK_LAUNCH();
     }
     ProfScope ps(ST_FFT_INV64, s);

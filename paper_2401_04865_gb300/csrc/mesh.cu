@@ -2037,8 +2037,7 @@ void Mesh<T>::init(const MeshGeom& geom, int channels, double xi, double eta, do
         *tma_err_host = 0;
         IBP_CUDA(cudaHostGetDevicePointer(reinterpret_cast<void**>(&tma_err_dev), tma_err_host, 0));
     }
-    // the double-float transforms fuse the scaling of one channel at a time: one radius only
-    df = sizeof(T) == 8 && df_fft_supported(g) && ncls == 1;
+    df = sizeof(T) == 8 && df_fft_supported(g);
     if (df) df_fft_init(g, df_tw, s);
     ensure_channels(channels * ncls);
     green.ensure(sizeof(T) * (size_t)g.Gc);
@@ -2056,6 +2055,12 @@ void Mesh<T>::init(const MeshGeom& geom, int channels, double xi, double eta, do
             green_df.ensure(sizeof(float2) * (size_t)g.Gc);
             green_split_kernel<<<grid_blocks(g.Gc, 256), 256, 0, s>>>(g.Gc, green.as<double>(), green_df.as<float2>());
             IBP_CHECK_LAUNCH();
+            if (ncls > 1) {
+                jtab_df.ensure(sizeof(float2) * (size_t)g.Gc * ncls);
+                green_split_kernel<<<grid_blocks(g.Gc * ncls, 256), 256, 0, s>>>(g.Gc * ncls, jtab.as<double>(),
+                                                                                  jtab_df.as<float2>());
+                IBP_CHECK_LAUNCH();
+            }
         }
     }
 }
@@ -2120,6 +2125,7 @@ void Mesh<T>::destroy() {
     spec.release();
     green.release();
     jtab.release();
+    jtab_df.release();
     green_df.release();
     grid_df.release();
     potential_df = false;
@@ -2161,7 +2167,7 @@ void Mesh<T>::transform(int ch, cudaStream_t s) {
     if constexpr (sizeof(T) == 8) {
         if (df) {
             df_fft_convolve(g, ch, green_df.as<float2>(), grid.as<double>(), grid_df.as<float2>(), df_buf.as<float4>(),
-                            df_tw, s);
+                            df_tw, s, ncls, jtab_df.as<float2>());
             potential_df = true;
             return;
         }

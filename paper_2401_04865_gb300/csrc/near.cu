@@ -118,6 +118,46 @@ __device__ double pair_limit2(double a, double b, double xi) {
     return (dF(a + b) - dF(fabs(a - b))) / (2.0 * a * b);
 }
 
+// phi_r, phi_r', phi_r'' of two radii for r >= a + b (every argument of g is >= 0
+// there, so no correction term), with g''(u) = 4 B xi^2 erfc(u xi).
+__device__ void pair_kernel2_d2(double r, double a, double b, double xi, double& phi, double& dphi, double& d2phi) {
+    const double A = 1.0 / (32.0 * pow(kPi, 1.5) * a * b * xi);
+    const double B = 1.0 / (64.0 * kPi * a * b * xi * xi);
+    const double x2 = xi * xi;
+    const double sv[4] = {r + a + b, r + a - b, r - a + b, r - a - b};
+    const double sg[4] = {1.0, -1.0, -1.0, 1.0};
+    double N = 0.0, dN = 0.0, d2N = 0.0;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const double u = sv[i];
+        const double e = exp(-u * u * x2);
+        const double ec = erfc(u * xi);
+        N += sg[i] * (-A * u * e + B * (2.0 * x2 * u * u + 1.0) * ec);
+        dN += sg[i] * (-2.0 * A * e + 4.0 * B * x2 * u * ec);
+        d2N += sg[i] * 4.0 * B * x2 * ec;
+    }
+    phi = N / r;
+    dphi = dN / r - N / (r * r);
+    d2phi = d2N / r - 2.0 * dN / (r * r) + 2.0 * N / (r * r * r);
+}
+
+// The table of a pair of radii a, b in u = r^2 / (a + b)^2 (nodes as in table_kernel,
+// with du/dr = 2 r / (a + b)^2).
+__global__ void table2_kernel(double a, double b, double xi, int K, double* __restrict__ table) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j > K * kOctaveIntervals) return;
+    const int e = j / kOctaveIntervals, i = j % kOctaveIntervals;
+    const double u = ldexp(1.0 + (double)i / kOctaveIntervals, e);
+    const double r = (a + b) * sqrt(u);
+    double p, d, d2;
+    pair_kernel2_d2(r, a, b, xi, p, d, d2);
+    const double s = (a + b) * (a + b) / (2.0 * r);
+    table[4 * j + 0] = p;
+    table[4 * j + 1] = d * s;
+    table[4 * j + 2] = -d / r;
+    table[4 * j + 3] = (d / (r * r) - d2 / r) * s;
+}
+
 // phi_r, phi_r', phi_r'' for r >= 2a from the second-difference form, with
 // g''(u) = 4 B xi^2 erfc(u xi) (the Heaviside term vanishes there).
 __device__ void pair_kernel_d2(double r, const PairConst& k, double& phi, double& dphi, double& d2phi) {
@@ -1144,19 +1184,63 @@ __global__ void pair_values_exact_kernel(const int* __restrict__ ov_count, const
         const double dz = min_image_wrapped(xw[3 * a + 2] - xw[3 * b + 2], k.L[2]);
         const double r2 = dx * dx + dy * dy + dz * dz;
         double phi, g;
+        const double ra = k.ncls > 1 ? k.ra[k.cls[a]] : k.a, rb = k.ncls > 1 ? k.ra[k.cls[b]] : k.a;
         if (r2 > 0.0) {
             const double r = sqrt(r2);
             double dphi;
-            pair_kernel(r, k, phi, dphi);
+            if (k.ncls > 1)
+                pair_kernel2(r, ra, rb, k.xi, phi, dphi);
+            else
+                pair_kernel(r, k, phi, dphi);
             g = -dphi / r;
         } else {
-            phi = k.self;   // coincident beads: the r -> 0 limit, no field
+            // coincident beads: the r -> 0 limit, no field
+            phi = k.ncls > 1 ? pair_limit2(ra, rb, k.xi) : k.self;
             g = 0.0;
         }
         val[p] = phi;
         pair32[p] = make_uint2((unsigned)cb, __float_as_uint((float)phi));
         if (gfac) gfac[p] = g;
     }
+}
+
+// Radius classes: the table of each pair of classes (c, d) at tabdf + (c ncls + d) stride,
+// in u = r^2 inv_s2[c ncls + d] with inv_s2 = 1 / (a_c + a_d)^2.
+struct DfClassArgs {
+    const int* cls;
+    int ncls;
+    long long stride;
+    df inv_s2[IBPME_MAX_RADIUS_CLASSES * IBPME_MAX_RADIUS_CLASSES];
+};
+
+__global__ void pair_values_df_cls_kernel(long long np, DfPairArgs A, DfClassArgs C, const int* __restrict__ prow,
+                                          const int* __restrict__ col, const int* __restrict__ order,
+                                          double* __restrict__ val, uint2* __restrict__ pair32,
+                                          double* __restrict__ gfac, int* __restrict__ ov_list,
+                                          int* __restrict__ ov_count) {
+    const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= np) return;
+    const int a = order[prow[p]], cb = col[p], b = order[cb];
+    const float4 ah = A.xdf[2 * a], al = A.xdf[2 * a + 1], bh = A.xdf[2 * b], bl = A.xdf[2 * b + 1];
+    const df dx = df_min_image(df_sub(df{ah.x, al.x}, df{bh.x, bl.x}), A.L[0], A.halfL[0]);
+    const df dy = df_min_image(df_sub(df{ah.y, al.y}, df{bh.y, bl.y}), A.L[1], A.halfL[1]);
+    const df dz = df_min_image(df_sub(df{ah.z, al.z}, df{bh.z, bl.z}), A.L[2], A.halfL[2]);
+    const df r2 = df_add(df_add(df_sqr(dx), df_sqr(dy)), df_sqr(dz));
+    const int pc = C.cls[a] * C.ncls + C.cls[b];
+    const df u = df_mul(r2, C.inv_s2[pc]);
+    if (!(u.hi > 1.0f || (u.hi == 1.0f && u.lo >= 0.0f))) {   // r < a_c + a_d: the exact kernel
+        ov_list[atomicAdd(ov_count, 1)] = (int)p;
+        return;
+    }
+    df s;
+    const int j = cb_interval(u, A.K, s);
+    const float4* tab = A.tabdf + (size_t)pc * C.stride;
+    const float4 t0 = tab[3 * j], t1 = tab[3 * j + 1], t2 = tab[3 * j + 2];
+    const df phi = cb_poly(t0, t1.x, t1.y, s);
+    const df g = cb_poly(make_float4(t1.z, t1.w, t2.x, t2.y), t2.z, t2.w, s);
+    val[p] = df_join(phi);
+    pair32[p] = make_uint2((unsigned)cb, __float_as_uint(__fadd_rn(phi.hi, phi.lo)));
+    if (gfac) gfac[p] = df_join(g);
 }
 
 // The real-space field of near_field_kernel in double-float arithmetic: differences
@@ -1407,6 +1491,33 @@ void near_setup(ibpme_ctx* c) {
         float4* tdf = static_cast<float4*>(nl.tab_df.ensure(sizeof(float4) * 3 * nt));
         compact_table_kernel<<<div_up(nt, 128), 128, 0, c->stream>>>(nt, nl.table.as<double>(), t32, tdf);
         IBP_CHECK_LAUNCH();
+    }
+    if (c->ncls > 1) {   // one table per pair of radius classes, octaves up to the largest u
+        int K = 0;
+        for (int a = 0; a < c->ncls; ++a)
+            for (int b = 0; b < c->ncls; ++b) {
+                const double uc = c->rc * c->rc / ((c->cls_a[a] + c->cls_a[b]) * (c->cls_a[a] + c->cls_a[b]));
+                int ka = 0;
+                while (ka < kMaxOctaves && ldexp(1.0, ka) < uc) ++ka;
+                if (uc > 1.0) K = std::max(K, ka);
+            }
+        nl.cls_K = K;
+        if (K > 0) {
+            const int nodes = K * kOctaveIntervals + 1, nt = K * kOctaveIntervals, np = c->ncls * c->ncls;
+            double* tab = static_cast<double*>(nl.cls_table.ensure(sizeof(double) * 4 * (size_t)nodes * np));
+            float4* tdf = static_cast<float4*>(nl.cls_tabdf.ensure(sizeof(float4) * 3 * (size_t)nt * np));
+            float4* t32 = static_cast<float4*>(nl.cls_tab32.ensure(sizeof(float4) * (size_t)nt * np));
+            for (int a = 0; a < c->ncls; ++a)
+                for (int b = 0; b < c->ncls; ++b) {
+                    const int q = a * c->ncls + b;
+                    table2_kernel<<<div_up(nodes, 128), 128, 0, c->stream>>>(c->cls_a[a], c->cls_a[b], c->xi, K,
+                                                                            tab + 4 * (size_t)nodes * q);
+                    IBP_CHECK_LAUNCH();
+                    compact_table_kernel<<<div_up(nt, 128), 128, 0, c->stream>>>(
+                        nt, tab + 4 * (size_t)nodes * q, t32 + (size_t)nt * q, tdf + 3 * (size_t)nt * q);
+                    IBP_CHECK_LAUNCH();
+                }
+        }
     }
     compact_attrs();
     nl.fp_valid = false;
@@ -1699,7 +1810,39 @@ void near_build(ibpme_ctx* c, int n, const double* xw, bool need_grad) {
             double* self_b = static_cast<double*>(nl.self_b.ensure(sizeof(double) * (size_t)n));
             class_self_kernel<<<div_up(n, 256), 256, 0, s>>>(n, k.cls, k, self_b);
             IBP_CHECK_LAUNCH();
-            if (nl.npairs > 0) {
+            if (nl.npairs > 0 && nl.cls_K > 0 && nl.npairs < (1LL << 31)) {
+                // double-float tables per pair of classes, overlapping shells listed and valued exactly
+                float4* xdf = static_cast<float4*>(nl.xdf.ensure(sizeof(float4) * 2 * (size_t)(n + 1)));
+                pos_df_kernel<<<div_up(n, 256), 256, 0, s>>>(n, xw, xdf);
+                IBP_CHECK_LAUNCH();
+                int* ov_list = static_cast<int*>(nl.ov_list.ensure(sizeof(int) * np));
+                int* ov_count = static_cast<int*>(nl.ov_count.ensure(sizeof(int)));
+                IBP_CUDA(cudaMemsetAsync(ov_count, 0, sizeof(int), s));
+                DfPairArgs A{};
+                A.xdf = xdf;
+                A.tabdf = nl.cls_tabdf.as<float4>();
+                A.K = nl.cls_K;
+                for (int d = 0; d < 3; ++d) {
+                    A.L[d] = host_df(k.L[d]);
+                    A.halfL[d] = (float)(0.5 * k.L[d]);
+                }
+                DfClassArgs CA{};
+                CA.cls = k.cls;
+                CA.ncls = c->ncls;
+                CA.stride = 3LL * nl.cls_K * kOctaveIntervals;
+                for (int a2 = 0; a2 < c->ncls; ++a2)
+                    for (int b2 = 0; b2 < c->ncls; ++b2) {
+                        const double sab = c->cls_a[a2] + c->cls_a[b2];
+                        CA.inv_s2[a2 * c->ncls + b2] = host_df(1.0 / (sab * sab));
+                    }
+                pair_values_df_cls_kernel<<<div_up(nl.npairs, 256), 256, 0, s>>>(
+                    nl.npairs, A, CA, prow, col, cell_beads, val, pair32, gfac, ov_list, ov_count);
+                IBP_CHECK_LAUNCH();
+                pair_values_exact_kernel<<<152 * 4, 128, 0, s>>>(ov_count, ov_list, xw, k, prow, col, cell_beads, val,
+                                                                 pair32, gfac);
+                IBP_CHECK_LAUNCH();
+                nl.ov_valid = true;
+            } else if (nl.npairs > 0) {
                 pair_values_cls_kernel<<<div_up(nl.npairs, 256), 256, 0, s>>>(nl.npairs, xw, k, prow, col,
                                                                               cell_beads, val, pair32, gfac);
                 IBP_CHECK_LAUNCH();
