@@ -594,14 +594,19 @@ def radii_workload(ib, torch, s, flush, k, one_radius_value):
     try:
         ib.ibpme_set_radius_classes(ctx, s.n, ion.astype(np.int32))
         st = Step(ib, torch, s, ib.IBPME_MIXED, GUESS["lattice"], ctx=ctx)
-        for _ in range(5):
+        for _ in range(4):
             st.run()
+        ib.ibpme_profile((1 << len(ib.STAGES)) - 1)   # stage times of one warm step, outside the timed steps
+        st.run()
         torch.cuda.synchronize()
+        prof = ib.ibpme_profile_read()
+        ib.ibpme_profile(0)
         ms = timed_steps(torch, st, k, flush, st.stream)
         rate = k / (sum(ms) / 1e3)
         out = {"workload": RADII_WORKLOAD, "solves_per_s": rate, "ms_per_step": sum(ms) / k, "steps": k,
                "iters": st.last_stats.iters, "r_cut": ib.ibpme_get_params(ctx).r_cut,
-               "vs_one_radius": rate / one_radius_value}
+               "vs_one_radius": rate / one_radius_value,
+               "warm_stage_ms": {kk: {"ms": round(v[0], 4), "launches": v[1]} for kk, v in prof.items() if v[1]}}
         st.close()
     finally:
         ib.pme_destroy(ctx)
