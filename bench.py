@@ -561,6 +561,7 @@ def bench_ours(args, ib, torch, rank, world, local):
     if wl == "lattice" and not args.skip_second:
         out["charged_sphere"] = second_workload(ib, torch, rank, flush, max(10, args.steps))
         out["unequal_radii"] = radii_workload(ib, torch, s, flush, max(10, args.steps), value / world)
+        out["rpy_mobility"] = rpy_at_scale(ib, torch, s, flush, max(10, args.steps))
     elif wl != "lattice" and not args.skip_scale:
         out["pme_at_scale"] = pme_at_scale(ib, torch, flush, 10)
     return out, s
@@ -611,6 +612,43 @@ def radii_workload(ib, torch, s, flush, k, one_radius_value):
     finally:
         ib.pme_destroy(ctx)
     return out
+
+
+RPY_WORKLOAD = ("RPY mobility product U = M F (periodic Rotne-Prager-Yamakawa, Hasimoto split on the "
+                "spectral-Ewald mesh) at the lattice's 141,088 bead positions, bead radius 0.05, 256^3 FP32 mesh, "
+                "FP64 real space, tol 1e-6, random forces")
+
+
+def rpy_at_scale(ib, torch, s, flush, k):
+    """The RPY mobility product at the lattice positions (FP32 mesh of three force channels,
+    FP64 real space); positions unchanged between products, L2 flushed before each."""
+    ctx = ib.pme_setup(ib.make_params(box=s.box, mesh=s.mesh, tol=s.tol, bead_radius=s.a, eps_f=s.eps,
+                                      precision=ib.IBPME_MIXED, max_rhs=3), torch.cuda.current_stream())
+    try:
+        stream = torch.cuda.current_stream()
+        x = torch.as_tensor(np.ascontiguousarray(s.x), device="cuda")
+        F = torch.as_tensor(np.random.default_rng(7).normal(size=(s.n, 3)), device="cuda")
+        U = torch.zeros_like(F)
+        for _ in range(3):
+            ib.ibpme_rpy_mobility(ctx, s.n, x, F, 1.0, U)
+        ib.ibpme_profile((1 << len(ib.STAGES)) - 1)   # stage times of one warm product
+        ib.ibpme_rpy_mobility(ctx, s.n, x, F, 1.0, U)
+        torch.cuda.synchronize()
+        prof = ib.ibpme_profile_read()
+        ib.ibpme_profile(0)
+        tot = 0.0
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        for _ in range(k):
+            flush.zero_()
+            e0.record(stream)
+            ib.ibpme_rpy_mobility(ctx, s.n, x, F, 1.0, U)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            tot += e0.elapsed_time(e1)
+    finally:
+        ib.pme_destroy(ctx)
+    return {"workload": RPY_WORKLOAD, "products_per_s": k / (tot / 1e3), "ms_per_product": tot / k, "steps": k,
+            "warm_stage_ms": {kk: {"ms": round(v[0], 4), "launches": v[1]} for kk, v in prof.items() if v[1]}}
 
 
 def pme_rate(ib, torch, st, flush, k):

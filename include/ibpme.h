@@ -134,6 +134,25 @@ ibpme_status ibpme_get_params(const ibpme_ctx* ctx, ibpme_params* out);
  * IBPME_ERR_ARG if the context has no radius classes or an index is out of range. */
 ibpme_status ibpme_set_radius_classes(ibpme_ctx* ctx, int n, const int* cls);
 
+/* Hydrodynamic mobility with the Rotne-Prager-Yamakawa tensor: the interactions the
+ * paper neglects and names as the way to add them (Sec. V.A, Eq. velocity):
+ *     U_alpha = sum_beta M^H_alpha_beta . F_beta,
+ * M^H the RPY tensor of beads of radius bead_radius in a fluid of viscosity mu, i.e.
+ * the Oseen tensor averaged over both beads' surfaces, M_hat(k) = j0^2(ka)(I - k_hat
+ * k_hat)/(mu k^2), summed over the periodic images with the k = 0 mode left out.
+ * Computed with the context's spectral-Ewald split (xi, mesh, P, r_cut) under
+ * Hasimoto's weight (1 + k^2/(4 xi^2)) e^{-k^2/(4 xi^2)}: the three force components
+ * spread, transformed, projected and gathered like three right-hand sides, the real
+ * space from a table of the two radial functions of M_RPY minus the wave kernel.
+ * The mesh runs in the context's precision (FP32 in IBPME_MIXED), the real space in FP64.
+ *   n    number of beads (>= 0)
+ *   x    [n][3] positions; F [n][3] forces; U [n][3] velocities (output, overwritten)
+ *   mu   viscosity (> 0)
+ * Pointers may be host or device memory (host outputs are written when the call
+ * returns).  IBPME_ERR_ARG for a NULL pointer with n > 0 or mu <= 0;
+ * IBPME_ERR_UNEQUAL_RADII on a context with radius classes. */
+ibpme_status ibpme_rpy_mobility(ibpme_ctx* ctx, int n, const double* x, const double* F, double mu, double* U);
+
 /* Message of the last error raised on the calling thread ("" if none). */
 const char* ibpme_last_error(void);
 

@@ -78,6 +78,7 @@ SIGNATURES = {
     "ibpme_get_params": (_i, [_p, ctypes.POINTER(ibpme_params)]),
     "ibpme_last_error": (ctypes.c_char_p, []),
     "ibpme_set_radius_classes": (_i, [_p, _i, _p]),
+    "ibpme_rpy_mobility": (_i, [_p, _i, _p, _p, _d, _p]),
     "pme_spread": (_i, [_p, _i, _p, _p, _i, _p]),
     "pme_field": (_i, [_p, _i, _p, _p, _i, _p, _p]),
     "induced_charge_solve": (_i, [_p, _i, _p, ctypes.POINTER(ibpme_bodies), _p, _i,
@@ -224,6 +225,11 @@ def ibpme_set_radius_classes(ctx, n, cls):
     if arr is not None and arr.shape[0] != int(n):
         raise ValueError("one class per bead expected")
     return _check(load().ibpme_set_radius_classes(ctx, int(n), ptr(arr, np.int32)), "ibpme_set_radius_classes")
+
+
+def ibpme_rpy_mobility(ctx, n, x, F, mu, U):
+    """U [n][3] = periodic RPY mobility (viscosity mu) times the forces F [n][3] at x [n][3]."""
+    return _check(load().ibpme_rpy_mobility(ctx, int(n), ptr(x), ptr(F), float(mu), ptr(U)), "ibpme_rpy_mobility")
 
 
 def ibpme_get_params(ctx) -> ibpme_params:

@@ -657,6 +657,34 @@ IBP_API ibpme_status pme_field(ibpme_ctx* c, int n, const double* x, const doubl
     });
 }
 
+IBP_API ibpme_status ibpme_rpy_mobility(ibpme_ctx* c, int n, const double* x, const double* F, double mu,
+                                        double* U) {
+    return guard([&]() -> ibpme_status {
+        if (!c) fail(IBPME_ERR_ARG, "ctx is NULL");
+        DeviceScope ds(c->device);
+        tma_check(c);
+        check_n(n);
+        if (!(mu > 0.0) || !std::isfinite(mu)) fail(IBPME_ERR_ARG, "mu must be > 0");
+        if (c->ncls > 1) fail(IBPME_ERR_UNEQUAL_RADII, "the RPY mobility takes one bead radius");
+        if (n > 0 && (!x || !F || !U)) fail(IBPME_ERR_ARG, "x, F and U are required");
+        const double* dx = static_cast<const double*>(stage_in(c, x, sizeof(double) * 3 * n, c->st_x));
+        const double* dF = static_cast<const double*>(stage_in(c, F, sizeof(double) * 3 * n, c->st_q));
+        OutArg ou = stage_out(c, U, sizeof(double) * 3 * (size_t)n, c->st_out1);
+        if (n == 0) return IBPME_OK;
+        double* xw = static_cast<double*>(c->xw.ensure(sizeof(double) * 3 * n));
+        wrap_positions(c, n, dx, xw);
+        c->bodies_current = false;   // beads without bodies: every pair goes through the table
+        c->near.fp_pre_valid = false;
+        rpy_apply(c, n, xw, dF, mu, static_cast<double*>(ou.dev));
+        finish_out(c, ou);
+        if (ou.host) {
+            IBP_CUDA(cudaStreamSynchronize(c->stream));
+            tma_check(c);
+        }
+        return IBPME_OK;
+    });
+}
+
 namespace {
 
 struct BodiesDev {

@@ -200,6 +200,15 @@ struct Mesh {
     void transform(int ch, cudaStream_t s);
     void gather(int n, const double* xw, int nrhs, const int* bead_cfg, double* psi, double* E, cudaStream_t s,
                 const StencilCache* sc = nullptr);
+    // The RPY mobility's wave space on three force channels (one system): R2C, then every
+    // k takes fac (1 + k^2/(4 xi^2)) G(k) (I - k_hat k_hat) of the three transforms, C2R
+    void transform_rpy(double fac, double xi, cudaStream_t s);
+};
+
+// Scaling of the RPY wave space (Hasimoto's weight and the transverse projection).
+struct RpyScale {
+    double L[3];
+    double xi, fac;
 };
 
 // Cell list and real-space pair table (Sec. III.D.1, Sec. III.D.3 step 1).
@@ -454,6 +463,11 @@ struct ibpme_ctx {
     ibp::DevBuf cls;
     std::vector<int> cls_h;
     unsigned long long cls_version = 0;       // bumped by every binding (cache keys; 0: none)
+    // RPY mobility: real-space radial table (A, B at mu = 1) for (a, xi, r_c) of rpy_key
+    ibp::DevBuf rpy_tab, rpy_F, rpy_Uk;
+    double rpy_key[3] = {0.0, 0.0, 0.0};
+    double rpy_h = 0.0, rpy_self = 0.0;
+    int rpy_nodes = 0;
     ibp::Precond pre;                         // body-block preconditioner
     cudaStream_t aux = nullptr;               // second branch of a PME evaluation (near field)
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
@@ -497,8 +511,14 @@ void near_apply_free(ibpme_ctx* c, const double* qc, int nrhs, double* psi_r, bo
 bool df_fft_supported(const MeshGeom& g);
 void df_fft_init(const MeshGeom& g, DevBuf tw[3], cudaStream_t s);
 // ncls > 1: radius classes, the channels mixed by j0(k a_c) j0(k a_d) (jtab [ncls][Gc] hi + lo)
+// rpy != NULL: three force channels scaled as in Mesh::transform_rpy
 void df_fft_convolve(const MeshGeom& g, int ch, const float2* green, const double* grid, float2* out, float4* S,
-                     DevBuf tw[3], cudaStream_t s, int ncls = 1, const float2* jtab = nullptr);
+                     DevBuf tw[3], cudaStream_t s, int ncls = 1, const float2* jtab = nullptr,
+                     const RpyScale* rpy = nullptr);
+
+// ---- rpy.cu ----
+// U [n][3] = periodic RPY mobility (viscosity mu) times F [n][3] at the wrapped positions xw
+void rpy_apply(ibpme_ctx* c, int n, const double* xw, const double* F, double mu, double* U);
 
 // ---- mesh.cu ----
 // Cached stencils for the current positions (rebuilt when the position

@@ -347,6 +347,39 @@ __global__ void dfz_mix_kernel(long long Gh, int nrhs, int ncls, float4* __restr
     }
 }
 
+// RPY wave space between the z passes (three force channels): F(k) becomes
+// fac (1 + k^2/(4 xi^2)) G(k) (I - k_hat k_hat) F(k), the scalar and the projection
+// formed in FP64 per k and applied in double-float arithmetic; zero at k = 0.
+__global__ void dfz_rpy_kernel(DfGeom d, RpyScale R, float4* __restrict__ S, const float2* __restrict__ green) {
+    const double two_pi = 6.283185307179586476925286766559;
+    const int h = d.h, ny = d.n[1], nz = d.n[2];
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < d.Gh;
+         t += (long long)gridDim.x * blockDim.x) {
+        const int x = (int)(t % h);
+        const long long rest = t / h;
+        const int y = (int)(rest % ny), z = (int)(rest / ny);
+        const int my = y <= ny / 2 ? y : y - ny, mz = z <= nz / 2 ? z : z - nz;
+        const double k[3] = {two_pi * x / R.L[0], two_pi * my / R.L[1], two_pi * mz / R.L[2]};
+        const double k2 = k[0] * k[0] + k[1] * k[1] + k[2] * k[2];
+        dfc v[3];
+        for (int c = 0; c < 3; ++c) v[c] = load_c(S[(size_t)c * d.Gh + t]);
+        if (k2 == 0.0) {
+            for (int c = 0; c < 3; ++c) S[(size_t)c * d.Gh + t] = make_float4(0.f, 0.f, 0.f, 0.f);
+            continue;
+        }
+        const double w = ((double)green[t].x + (double)green[t].y) * (1.0 + k2 / (4.0 * R.xi * R.xi)) * R.fac;
+        for (int c = 0; c < 3; ++c) {
+            dfc o = {{0.0f, 0.0f}, {0.0f, 0.0f}};
+            for (int e = 0; e < 3; ++e) {
+                const df p = df_split(w * ((c == e ? 1.0 : 0.0) - k[c] * k[e] / k2));
+                o.re = df_add(o.re, df_mul(v[e].re, p));
+                o.im = df_add(o.im, df_mul(v[e].im, p));
+            }
+            S[(size_t)c * d.Gh + t] = store_c(o);
+        }
+    }
+}
+
 int ilog2(int v) {
     int l = 0;
     while ((1 << l) < v) ++l;
@@ -400,7 +433,7 @@ void df_fft_init(const MeshGeom& g, DevBuf tw[3], cudaStream_t s) {
 // grid (FP64, [ch][G]) -> out ([ch][G], hi + lo floats): the inverse transform of G(k)
 // times the grid's transform.
 void df_fft_convolve(const MeshGeom& g, int ch, const float2* green, const double* grid, float2* out, float4* S,
-                     DevBuf tw[3], cudaStream_t s, int ncls, const float2* jtab) {
+                     DevBuf tw[3], cudaStream_t s, int ncls, const float2* jtab, const RpyScale* rpy) {
     DfGeom d;
     for (int a = 0; a < 3; ++a) {
         d.n[a] = g.N[a];
@@ -424,7 +457,15 @@ void df_fft_convolve(const MeshGeom& g, int ch, const float2* green, const doubl
     }
     {
         ProfScope ps(ST_SCALE64, s);
-        if (ncls > 1) {
+        if (rpy) {
+            if (ch != 3) fail(IBPME_ERR_ARG, "internal: the RPY scaling takes three channels, not %d", ch);
+            dfz_scale_kernel<<<gz, kDfThreads, 0, s>>>(d, S, tw[2].as<float4>(), green, 1);
+            IBP_CHECK_LAUNCH();
+            const long long blocks = std::min<long long>((d.Gh + 255) / 256, 152LL * 16);
+            dfz_rpy_kernel<<<(unsigned)blocks, 256, 0, s>>>(d, *rpy, S, green);
+            IBP_CHECK_LAUNCH();
+            dfz_scale_kernel<<<gz, kDfThreads, 0, s>>>(d, S, tw[2].as<float4>(), green, 2);
+        } else if (ncls > 1) {
             if (ch % ncls) fail(IBPME_ERR_ARG, "internal: %d channels for %d radius classes", ch, ncls);
             dfz_scale_kernel<<<gz, kDfThreads, 0, s>>>(d, S, tw[2].as<float4>(), green, 1);
             IBP_CHECK_LAUNCH();

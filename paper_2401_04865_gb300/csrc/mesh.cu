@@ -1966,6 +1966,42 @@ __global__ void class_j0_kernel(MeshGeom g, int ncls, ClassRadii R, T* __restric
     }
 }
 
+// RPY wave space: the three force channels F(k) become fac (1 + k^2/(4 xi^2)) G(k)
+// (I - k_hat k_hat) F(k) (Hasimoto's weight; G carries j0^2(ka) and the window's
+// e^{-(1 - eta) k^2/(4 xi^2)}); zero at k = 0.
+template <typename T>
+__global__ void rpy_project_kernel(MeshGeom g, double fac, double xi, const T* __restrict__ green,
+                                   typename Cplx<T>::type* __restrict__ spec) {
+    const int nxh = g.N[0] / 2 + 1;
+    const T two_pi = (T)6.283185307179586476925286766559;
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < g.Gc;
+         t += (long long)gridDim.x * blockDim.x) {
+        const int kx_i = (int)(t % nxh);
+        const long long rest = t / nxh;
+        const int ky_i = (int)(rest % g.N[1]);
+        const int kz_i = (int)(rest / g.N[1]);
+        const int my = ky_i <= g.N[1] / 2 ? ky_i : ky_i - g.N[1];
+        const int mz = kz_i <= g.N[2] / 2 ? kz_i : kz_i - g.N[2];
+        const T k[3] = {two_pi * kx_i / (T)g.L[0], two_pi * my / (T)g.L[1], two_pi * mz / (T)g.L[2]};
+        const T k2 = k[0] * k[0] + k[1] * k[1] + k[2] * k[2];
+        typename Cplx<T>::type v[3];
+        for (int c = 0; c < 3; ++c) v[c] = spec[(size_t)c * g.Gc + t];
+        typename Cplx<T>::type o[3];
+        if (k2 > (T)0) {
+            const T w = green[t] * ((T)1 + k2 / (T)(4.0 * xi * xi)) * (T)fac;
+            const T kr = k[0] * v[0].x + k[1] * v[1].x + k[2] * v[2].x;   // k . F
+            const T ki = k[0] * v[0].y + k[1] * v[1].y + k[2] * v[2].y;
+            for (int c = 0; c < 3; ++c) {
+                o[c].x = w * (v[c].x - k[c] * kr / k2);
+                o[c].y = w * (v[c].y - k[c] * ki / k2);
+            }
+        } else {
+            for (int c = 0; c < 3; ++c) o[c].x = o[c].y = (T)0;
+        }
+        for (int c = 0; c < 3; ++c) spec[(size_t)c * g.Gc + t] = o[c];
+    }
+}
+
 // Scaling with radius classes (the pair kernel j0(k a_c) j0(k a_d) G(k)): for each
 // right-hand side r, S = sum_c j0(k a_c) H_hat(c, r), then channel (d, r) becomes
 // G(k) j0(k a_d) S.  The source and the target factor of every pair are applied, so
@@ -2192,6 +2228,43 @@ void Mesh<T>::transform(int ch, cudaStream_t s) {
         } else {
             scale_kernel<T><<<dim3(grid_blocks(g.Gc, 256), ch), 256, 0, s>>>(g.Gc, green.as<T>(), spec.as<C>());
         }
+        IBP_CHECK_LAUNCH();
+    }
+    ProfScope ps(mesh_stage<T>(ST_FFT_INV), s);
+    if constexpr (sizeof(T) == 8) {
+        IBP_CUFFT(cufftExecZ2D(pl.second, spec.as<C>(), grid.as<double>()));
+    } else {
+        IBP_CUFFT(cufftExecC2R(pl.second, spec.as<C>(), grid.as<float>()));
+    }
+}
+
+template <typename T>
+void Mesh<T>::transform_rpy(double fac, double xi, cudaStream_t s) {
+    if (ncls > 1) fail(IBPME_ERR_UNEQUAL_RADII, "the RPY mobility takes one bead radius");
+    plans(3, s);
+    if constexpr (sizeof(T) == 8) {
+        if (df) {
+            RpyScale R{{g.L[0], g.L[1], g.L[2]}, xi, fac};
+            df_fft_convolve(g, 3, green_df.as<float2>(), grid.as<double>(), grid_df.as<float2>(), df_buf.as<float4>(),
+                            df_tw, s, 1, nullptr, &R);
+            potential_df = true;
+            return;
+        }
+    }
+    potential_df = false;
+    const auto& pl = plan.at(3);
+    using C = typename Cplx<T>::type;
+    {
+        ProfScope ps(mesh_stage<T>(ST_FFT_FWD), s);
+        if constexpr (sizeof(T) == 8) {
+            IBP_CUFFT(cufftExecD2Z(pl.first, grid.as<double>(), spec.as<C>()));
+        } else {
+            IBP_CUFFT(cufftExecR2C(pl.first, grid.as<float>(), spec.as<C>()));
+        }
+    }
+    {
+        ProfScope ps(mesh_stage<T>(ST_SCALE), s);
+        rpy_project_kernel<T><<<grid_blocks(g.Gc, 256), 256, 0, s>>>(g, fac, xi, green.as<T>(), spec.as<C>());
         IBP_CHECK_LAUNCH();
     }
     ProfScope ps(mesh_stage<T>(ST_FFT_INV), s);
