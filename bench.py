@@ -651,6 +651,88 @@ def rpy_at_scale(ib, torch, s, flush, k):
             "warm_stage_ms": {kk: {"ms": round(v[0], 4), "launches": v[1]} for kk, v in prof.items() if v[1]}}
 
 
+def bench_rpy(args, ib, torch, rank, world, local):
+    """--workload rpy: the RPY mobility product at the lattice positions, K products timed
+    with CUDA events (L2 flushed before each), the dominant own kernel against the HBM peak,
+    and the same product through host buffers end to end."""
+    from workloads import configs as C
+    torch.cuda.set_device(local)
+    s = C.config3(seed=1002 + 7919 * rank)
+    stream = torch.cuda.current_stream()
+    ctx = ib.pme_setup(ib.make_params(box=s.box, mesh=s.mesh, tol=s.tol, bead_radius=s.a, eps_f=s.eps,
+                                      precision=ib.IBPME_MIXED, max_rhs=3), stream)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
+    x = torch.as_tensor(np.ascontiguousarray(s.x), device="cuda")
+    Fh = np.random.default_rng(7 + rank).normal(size=(s.n, 3))
+    F = torch.as_tensor(Fh, device="cuda")
+    U = torch.zeros_like(F)
+    for _ in range(args.warmup):
+        ib.ibpme_rpy_mobility(ctx, s.n, x, F, 1.0, U)
+    cand = ("spread", "gather", "rpy_near")
+    mask = 0
+    for k in cand:
+        mask |= 1 << ib.STAGES.index(k)
+    ib.ibpme_profile(mask)
+    launches0 = ib.ibpme_kernel_launches()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    with ClockSampler(local) as clk:
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+        for i in range(args.steps):
+            flush.zero_()
+            ev[i][0].record(stream)
+            ib.ibpme_rpy_mobility(ctx, s.n, x, F, 1.0, U)
+            ev[i][1].record(stream)
+        torch.cuda.synchronize()
+    launches = ib.ibpme_kernel_launches() - launches0
+    prof = ib.ibpme_profile_read()
+    ib.ibpme_profile(0)
+    total_ms = float(sum(a.elapsed_time(b) for a, b in ev))
+    if world > 1:
+        t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t.item())
+    npairs = pair_count(ib, ctx, s, s.x)
+    # algorithmic bytes per launch: the spread writes three FP32 grids and reads positions and forces;
+    # the gather reads three grids and writes three velocities; the real space reads positions, forces,
+    # row offsets and columns once and writes the velocities
+    G = int(np.prod(s.mesh))
+    alg = {"spread": 3 * G * 4 + s.n * 48, "gather": 3 * G * 4 + s.n * 48,
+           "rpy_near": s.n * (24 + 24 + 24 + 8 + 4) + 4 * npairs}
+    own = {k: v for k, v in prof.items() if k in cand and v[1] > 0}
+    dom = max(own, key=lambda k: own[k][0])
+    t_dom = own[dom][0] / own[dom][1] / 1e3
+    peak, kind = peaks()
+    # end to end: host positions and forces in, host velocities out
+    xh = np.ascontiguousarray(s.x)
+    Uh = np.zeros((s.n, 3))
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        ib.ibpme_rpy_mobility(ctx, s.n, xh, Fh, 1.0, Uh)
+    e2e_s = time.perf_counter() - t0
+    ib.pme_destroy(ctx)
+    value = world * args.steps / (total_ms / 1e3)
+    return {
+        "metric": "RPY mobility products/s", "value": value, "unit": "products/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32 mesh / f64 real space",
+        "data": "synthetic",
+        "config": {"workload": RPY_WORKLOAD, "n_beads": s.n, "mesh": list(s.mesh), "pairs": int(npairs),
+                   "l2": "flushed (256 MB write) before each product"},
+        "roofline": {"bound": "hbm", "kernel": dom, "achieved": alg[dom] / t_dom / 1e9, "peak": peak, "unit": "GB/s",
+                     "frac": alg[dom] / t_dom / 1e9 / peak, "alg_bytes_per_launch": alg[dom],
+                     "ms_per_launch": t_dom * 1e3, "peak_source": kind, "traffic": None},
+        "stage_ms_per_product": {k: round(v[0] / args.steps, 4) for k, v in own.items()},
+        "e2e": {"value": world * args.steps / e2e_s, "unit": "products/s", "h2d_bytes_per_step": 2 * 24 * s.n,
+                "d2h_bytes_per_step": 24 * s.n},
+        "gpu_launches": int(launches), "clocks": clk.summary(),
+        "cpu_baseline": None,
+        "cpu_baseline_note": ("not timed: the oracle's explicit k-sum over 141,088 sources and its radial "
+                              "quadrature per pair take far beyond a bounded sample"),
+    }
+
+
 def pme_rate(ib, torch, st, flush, k):
     """PME evaluations (pme_field, potential of one field, FP32 mesh) of the step's
     system at its current positions and charges; L2 flushed before each one."""
@@ -1076,7 +1158,7 @@ def main():
     ap.add_argument("--skip-second", action="store_true",
                     help="lattice workload: do not time the charged-sphere workload beside it")
     ap.add_argument("--workload", default="lattice",
-                    choices=["lattice", "charged-sphere", "polarizability", "trajectory"],
+                    choices=["lattice", "charged-sphere", "polarizability", "trajectory", "rpy"],
                     help="the headline lattice step, the charged-sphere step, the batched polarizability "
                          "solve, or a BD trajectory comparing initial guesses")
     ap.add_argument("--bucket-ratio", type=float, default=1.6,
@@ -1098,8 +1180,8 @@ def main():
     if world > 1:
         torch.cuda.set_device(local)
         torch.distributed.init_process_group("nccl", device_id=torch.device("cuda", local))
-    if args.workload in ("polarizability", "trajectory"):
-        fn = bench_polarizability if args.workload == "polarizability" else bench_trajectory
+    if args.workload in ("polarizability", "trajectory", "rpy"):
+        fn = {"polarizability": bench_polarizability, "trajectory": bench_trajectory, "rpy": bench_rpy}[args.workload]
         out = fn(args, ib, torch, rank, world, local)
         if rank == 0:
             print(json.dumps(out), flush=True)

@@ -385,6 +385,7 @@ enum Stage {
     ST_GATHER64,
     ST_NEAR_APPLY32,     // real-space SpMV, FP32 pass (inner operator of mixed solves)
     ST_NEAR_FIELD,       // real-space field (force pass)
+    ST_RPY_NEAR,         // real-space share of the RPY mobility
     ST_COUNT
 };
 // stage of a mesh step for the mesh precision T
@@ -464,7 +465,7 @@ struct ibpme_ctx {
     std::vector<int> cls_h;
     unsigned long long cls_version = 0;       // bumped by every binding (cache keys; 0: none)
     // RPY mobility: real-space radial table (A, B at mu = 1) for (a, xi, r_c) of rpy_key
-    ibp::DevBuf rpy_tab, rpy_F, rpy_Uk;
+    ibp::DevBuf rpy_tab, rpy_tab32, rpy_F, rpy_F4, rpy_Uk;
     double rpy_key[3] = {0.0, 0.0, 0.0};
     double rpy_h = 0.0, rpy_self = 0.0;
     int rpy_nodes = 0;

@@ -66,7 +66,7 @@ Profiler& prof() {
 const char* kStageNames[ST_COUNT] = {"near_build", "near_apply", "spread", "fft_forward", "scale",
                                      "fft_inverse", "gather", "krylov", "bodies", "spread64",
                                      "fft_forward64", "scale64", "fft_inverse64", "gather64", "near_apply32",
-                                     "near_field"};
+                                     "near_field", "rpy_near"};
 
 }  // namespace
 

@@ -167,6 +167,69 @@ __global__ void rpy_near_kernel(int n, const long long* __restrict__ rowptr, con
         for (int c = 0; c < 3; ++c) U[3 * al + c] = (u[c] + self * F[3 * al + c]) * inv_mu;
 }
 
+// The same in FP32 for a mixed-precision context (its mesh is FP32 too): FP32 positions
+// of the pair search, a float copy of the table and the forces, FP32 sums per lane and
+// FP64 across the warp.  GB300's FP64 rate made the FP64 pass the cost of the product.
+struct RpyTab32 {
+    const float2* tab;
+    int nodes;
+    float inv_h;
+};
+
+__device__ __forceinline__ float2 rpy_interp32(const RpyTab32& T, float r) {
+    const float u = r * T.inv_h;
+    int i = (int)u;
+    i = i > T.nodes - 3 ? T.nodes - 3 : i;
+    const float t = u - (float)i;
+    const float2 p1 = T.tab[i], p2 = T.tab[i + 1], p3 = T.tab[i + 2];
+    const float2 p0 = i > 0 ? T.tab[i - 1] : make_float2(2.0f * p1.x - p2.x, 2.0f * p1.y - p2.y);
+    const float t2 = t * t, t3 = t2 * t;
+    const float w0 = -0.5f * t3 + t2 - 0.5f * t, w1 = 1.5f * t3 - 2.5f * t2 + 1.0f;
+    const float w2 = -1.5f * t3 + 2.0f * t2 + 0.5f * t, w3 = 0.5f * t3 - 0.5f * t2;
+    return make_float2(w0 * p0.x + w1 * p1.x + w2 * p2.x + w3 * p3.x, w0 * p0.y + w1 * p1.y + w2 * p2.y + w3 * p3.y);
+}
+
+__global__ void rpy_near32_kernel(int n, const long long* __restrict__ rowptr, const int* __restrict__ col,
+                                  const int* __restrict__ order, const float4* __restrict__ xf, float L0, float L1,
+                                  float L2, RpyTab32 T, double self, double inv_mu, const float4* __restrict__ F4,
+                                  const double* __restrict__ F, double* __restrict__ U) {
+    const int t = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (t >= n) return;
+    const int al = order[t];
+    const float4 pa = xf[al];
+    float u[3] = {0.0f, 0.0f, 0.0f};
+    for (long long p = rowptr[t] + lane; p < rowptr[t + 1]; p += 32) {
+        const int be = order[col[p]];
+        const float4 pb = xf[be];
+        const float d[3] = {min_image_wrapped(pa.x - pb.x, L0), min_image_wrapped(pa.y - pb.y, L1),
+                            min_image_wrapped(pa.z - pb.z, L2)};
+        const float r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+        const float r = sqrtf(r2);
+        const float2 ab = rpy_interp32(T, r);
+        const float4 f = F4[be];
+        const float ef = r2 > 0.0f ? (d[0] * f.x + d[1] * f.y + d[2] * f.z) / r2 : 0.0f;
+        u[0] += ab.x * f.x + ab.y * ef * d[0];
+        u[1] += ab.x * f.y + ab.y * ef * d[1];
+        u[2] += ab.x * f.z + ab.y * ef * d[2];
+    }
+    double v[3];
+    for (int c = 0; c < 3; ++c) v[c] = warp_sum((double)u[c]);
+    if (lane == 0)
+        for (int c = 0; c < 3; ++c) U[3 * al + c] = (v[c] + self * F[3 * al + c]) * inv_mu;
+}
+
+// forces as float4 (x, y, z, 0) and the table as float2, for the FP32 pass
+__global__ void rpy_f4_kernel(int n, const double* __restrict__ F, float4* __restrict__ F4) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) F4[i] = make_float4((float)F[3 * i], (float)F[3 * i + 1], (float)F[3 * i + 2], 0.0f);
+}
+
+__global__ void rpy_tab32_kernel(int nodes, const double2* __restrict__ tab, float2* __restrict__ t32) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < nodes) t32[i] = make_float2((float)tab[i].x, (float)tab[i].y);
+}
+
 // U[i][d] += Uk[d][i]
 __global__ void rpy_combine_kernel(int n, const double* __restrict__ Uk, double* __restrict__ U) {
     const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
@@ -207,6 +270,10 @@ void rpy_table(ibpme_ctx* c) {
     double2 self{};
     IBP_CUDA(cudaMemcpyAsync(&self, tab, sizeof(double2), cudaMemcpyDeviceToHost, c->stream));
     IBP_CUDA(cudaStreamSynchronize(c->stream));   // the host vectors and the quadrature buffers go out of scope
+    float2* t32 = static_cast<float2*>(c->rpy_tab32.ensure(sizeof(float2) * (size_t)nodes));
+    rpy_tab32_kernel<<<div_up(nodes, 128), 128, 0, c->stream>>>(nodes, tab, t32);
+    IBP_CHECK_LAUNCH();
+    IBP_CUDA(cudaStreamSynchronize(c->stream));
     c->rpy_self = self.x;
     c->rpy_h = h;
     c->rpy_nodes = nodes;
@@ -243,9 +310,20 @@ void rpy_apply(ibpme_ctx* c, int n, const double* xw, const double* F, double mu
     }
     const NearList& nl = c->near;
     RpyTab T{c->rpy_tab.as<double2>(), c->rpy_nodes, 1.0 / c->rpy_h};
-    rpy_near_kernel<<<div_up((long long)n * 32, 128), 128, 0, s>>>(
-        n, nl.rowptr.as<long long>(), nl.col.as<int>(), nl.cell_beads.as<int>(), xw, c->p.box[0], c->p.box[1],
-        c->p.box[2], T, c->rpy_self, 1.0 / mu, F, U);
+    ProfScope ps(ST_RPY_NEAR, s);
+    if (c->p.precision == IBPME_MIXED) {
+        float4* F4 = static_cast<float4*>(c->rpy_F4.ensure(sizeof(float4) * (size_t)n));
+        rpy_f4_kernel<<<div_up(n, 256), 256, 0, s>>>(n, F, F4);
+        IBP_CHECK_LAUNCH();
+        RpyTab32 T32{c->rpy_tab32.as<float2>(), c->rpy_nodes, (float)(1.0 / c->rpy_h)};
+        rpy_near32_kernel<<<div_up((long long)n * 32, 128), 128, 0, s>>>(
+            n, nl.rowptr.as<long long>(), nl.col.as<int>(), nl.cell_beads.as<int>(), nl.xf.as<float4>(),
+            (float)c->p.box[0], (float)c->p.box[1], (float)c->p.box[2], T32, c->rpy_self, 1.0 / mu, F4, F, U);
+    } else {
+        rpy_near_kernel<<<div_up((long long)n * 32, 128), 128, 0, s>>>(
+            n, nl.rowptr.as<long long>(), nl.col.as<int>(), nl.cell_beads.as<int>(), xw, c->p.box[0], c->p.box[1],
+            c->p.box[2], T, c->rpy_self, 1.0 / mu, F, U);
+    }
     IBP_CHECK_LAUNCH();
     rpy_combine_kernel<<<div_up(3LL * n, 256), 256, 0, s>>>(n, Uk, U);
     IBP_CHECK_LAUNCH();
