@@ -465,7 +465,8 @@ long long ibpme_kernel_launches(void);
  * 6 gather (2-6: FP32 mesh), 7 krylov (Arnoldi/Givens kernels of one iteration),
  * 8 bodies, 9-13 the FP64 mesh (spread64, fft_forward64, scale64, fft_inverse64,
  * gather64), 14 near_apply32 (the FP32 real-space pass of a mixed solve's inner
- * operator), 15 near_field (real-space field of the force pass).
+ * operator), 15 near_field (real-space field of the force pass), 16 rpy_near (the
+ * real-space share of ibpme_rpy_mobility).
  * ibpme_profile(mask) enables CUDA-event timing of the stages in the bit mask
  * (0 disables) and resets the totals; each enabled stage then records an event
  * pair on the stream it runs on. */

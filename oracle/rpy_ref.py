@@ -16,6 +16,8 @@ gradient).  The sum is split with Hasimoto's weight H(k) = (1 + k^2/(4 xi^2)) e^
     real space: sum over images of M_r(r) = M_RPY(r) - M_w(r) with M_w the inverse
     transform of the wave kernel over all k, a radial quadrature; M_r decays like
     e^{-xi^2 r^2} because (1 - H(k))/k^2 is smooth at k = 0 (no k = 0 correction).
+The rigid-body mobility problem of the paper's last equation (constraint forces and body motions)
+is solved densely on top of it (rigid_mobility).
 An isotropic kernel f(k) (I - k_hat k_hat) has the real-space form A(r) I + B(r) r_hat r_hat with
     A = 1/(2 pi^2) int f k^2 [j0(kr) - j1(kr)/(kr)] dk,  B = 1/(2 pi^2) int f k^2 [3 j1(kr)/(kr) - j0(kr)] dk.
 """
@@ -157,4 +159,54 @@ def rpy_matrix(x, box, a: float, mu: float = 1.0, xi=None, tol=1e-13):
     return M
 
 
-__all__ = ["rpy_free", "rpy_wave_radial", "rpy_real_radial", "rpy_split", "rpy_mobility", "rpy_matrix"]
+def rigid_operator(x, X, body_offsets, box):
+    """K (3n x 6 n_b): bead velocities K W = U_b + Omega_b x r_j of rigid-body motions W = (U, Omega)
+    per body, r_j the bead's minimum-image position relative to its body's reference point.
+    Single-bead bodies move by U alone (their Omega columns are zero)."""
+    x = np.ascontiguousarray(x, dtype=np.float64).reshape(-1, 3)
+    off = np.asarray(body_offsets, dtype=np.int64)
+    n, nb = x.shape[0], len(off) - 1
+    X = np.asarray(X, dtype=np.float64).reshape(nb, 3)
+    box = np.asarray(box, dtype=np.float64)
+    K = np.zeros((3 * n, 6 * nb))
+    for b in range(nb):
+        for j in range(off[b], off[b + 1]):
+            K[3 * j:3 * j + 3, 6 * b:6 * b + 3] = np.eye(3)
+            if off[b + 1] - off[b] > 1:
+                r = x[j] - X[b]
+                r -= box * np.floor(r / box + 0.5)
+                # Omega x r = -[r]_x Omega
+                K[3 * j:3 * j + 3, 6 * b + 3:6 * b + 6] = -np.array([[0.0, -r[2], r[1]], [r[2], 0.0, -r[0]],
+                                                                      [-r[1], r[0], 0.0]])
+    return K
+
+
+def rigid_mobility(x, X, body_offsets, box, a: float, FL, mu: float = 1.0, M=None):
+    """Rigid-body mobility problem (the paper's last equation, physical sign): bead constraint
+    forces f and body motions W = (U, Omega) with
+        M f = K W          (the beads move rigidly with their bodies),
+        K^T f = (F, L)     (the bead forces add up to each body's force and torque),
+    M the periodic RPY mobility of the beads.  A single-bead body has no rotation: its Omega is
+    set to zero and its torque is not an equation.  Dense LU.  FL: [n_b, 6] (F, L);
+    returns W [n_b, 6] and f [n, 3]."""
+    x = np.ascontiguousarray(x, dtype=np.float64).reshape(-1, 3)
+    off = np.asarray(body_offsets, dtype=np.int64)
+    n, nb = x.shape[0], len(off) - 1
+    if M is None:
+        M = rpy_matrix(x, box, a, mu)
+    K = rigid_operator(x, X, off, box)
+    A = np.block([[M, -K], [K.T, np.zeros((6 * nb, 6 * nb))]])
+    rhs = np.zeros(3 * n + 6 * nb)
+    G = np.array(FL, dtype=np.float64).reshape(nb, 6).copy()
+    for b in range(nb):
+        if off[b + 1] - off[b] == 1:
+            G[b, 3:] = 0.0
+            for d in range(3):
+                A[3 * n + 6 * b + 3 + d, 3 * n + 6 * b + 3 + d] = 1.0
+    rhs[3 * n:] = G.reshape(-1)
+    z = np.linalg.solve(A, rhs)
+    return z[3 * n:].reshape(nb, 6), z[:3 * n].reshape(n, 3)
+
+
+__all__ = ["rpy_free", "rpy_wave_radial", "rpy_real_radial", "rpy_split", "rpy_mobility", "rpy_matrix",
+           "rigid_operator", "rigid_mobility"]

@@ -128,3 +128,53 @@ def test_dense_mobility_symmetric_positive_definite():
     assert ev.min() > 0
     U = R.rpy_mobility(x, F, box, 0.2)
     assert np.abs(M @ F.reshape(-1) - U.reshape(-1)).max() < 1e-12 * np.abs(U).max()
+
+
+def _square(L=6.0, R_=0.45, a=0.2, free=True):
+    """Four beads on a square of half-diagonal R_ in the plane z = L/2, centred in a cubic box
+    (the square's fourfold symmetry about z is then a symmetry of the periodic lattice), and
+    optionally a free bead."""
+    c = np.array([L / 2, L / 2, L / 2])
+    sq = np.array([[R_, 0, 0], [0, R_, 0], [-R_, 0, 0], [0, -R_, 0]]) + c
+    if not free:
+        return sq, c[None, :], np.array([0, 4]), np.array([L, L, L]), a
+    x = np.vstack([sq, [[0.6, 0.9, 1.3]]])
+    return x, np.array([c, x[4]]), np.array([0, 4, 5]), np.array([L, L, L]), a
+
+
+def test_rigid_square_translation_and_rotation_closed_forms():
+    """A rigid square of four beads: pulled along its normal z each bead carries F/4 (symmetry),
+    so U_z = sum_k (M_1k)_zz / 4; turned by a torque L about z each bead carries L/(4R) along its
+    tangent, so Omega_z R = (sum_k M_1k t_k)_t L/(4R) (M the periodic pair tensors, t_k the
+    tangents).  A collinear body would leave its spin about its own axis undetermined."""
+    x, X, off, box, a = _square(free=False)
+    M = R.rpy_matrix(x, box, a)
+    R_ = 0.45
+    W, f = R.rigid_mobility(x, X, off, box, a, [[0, 0, 1.0, 0, 0, 0]], M=M)
+    assert np.abs(f - [0, 0, 0.25]).max() < 1e-12
+    uz = sum(M[2, 3 * k + 2] for k in range(4)) * 0.25
+    assert abs(W[0, 2] - uz) < 1e-12 * abs(uz) and np.abs(W[0, [0, 1, 3, 4, 5]]).max() < 1e-12 * abs(uz)
+    W, f = R.rigid_mobility(x, X, off, box, a, [[0, 0, 0, 0, 0, 1.0]], M=M)
+    t = np.array([[0, 1.0, 0], [-1.0, 0, 0], [0, -1.0, 0], [1.0, 0, 0]])     # tangents (counter-clockwise)
+    assert np.abs(f - t / (4 * R_)).max() < 1e-10
+    u1 = sum(M[0:3, 3 * k:3 * k + 3] @ t[k] for k in range(4)) / (4 * R_)
+    assert abs(W[0, 5] * R_ - u1[1]) < 1e-10 * abs(u1[1])
+
+
+def test_rigid_grand_mobility_symmetric_positive_definite():
+    """The body mobility (U, Omega) = N (F, L) of rigid bodies is symmetric positive definite
+    (reciprocal theorem): the square's 6 x 6 and the free bead's 3 x 3 blocks and their coupling;
+    the free bead's rotation stays zero."""
+    x, X, off, box, a = _square()
+    M = R.rpy_matrix(x, box, a)
+    cols = []
+    dofs = [(0, k) for k in range(6)] + [(1, k) for k in range(3)]
+    for b, k in dofs:
+        FL = np.zeros((2, 6))
+        FL[b, k] = 1.0
+        W, _ = R.rigid_mobility(x, X, off, box, a, FL, M=M)
+        assert np.abs(W[1, 3:]).max() == 0.0
+        cols.append([W[bb, kk] for bb, kk in dofs])
+    N = np.array(cols).T
+    assert np.abs(N - N.T).max() < 1e-12 * np.abs(N).max()
+    assert np.linalg.eigvalsh(0.5 * (N + N.T)).min() > 0
