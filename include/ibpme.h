@@ -453,6 +453,35 @@ ibpme_status ibpme_features(ibpme_ctx* ctx, int n, const double* x, const ibpme_
 ibpme_status pme_spread_noalloc(const ibpme_params* params, int n, const double* x, const double* q, int nrhs,
                                 void* grid_out, void* cuda_stream);
 
+/* Rigid-body mobility problem of the paper's last equation (the hydrodynamic
+ * integrator it hands the body forces and torques to, here with the periodic RPY
+ * mobility of ibpme_rpy_mobility): bead constraint forces f and body motions
+ * W = (U, Omega) with
+ *     M^H f = U_b + Omega_b x r_j   for every bead j of body b (rigid motion),
+ *     sum_j f_j = F_b,  sum_j r_j x f_j = L_b,
+ * r_j the minimum-image position of bead j relative to X_b.  (The paper writes the
+ * system with +Sigma'''^T; its (U, Omega) is minus the motion here.)  A single-bead
+ * body moves by U alone: its Omega is returned as 0 and its torque ignored.  Bodies
+ * of two or more beads must not be collinear (a rod of beads has no resistance to
+ * spinning about its axis, and the system is then singular).  Solved by restarted
+ * GMRES (classical Gram-Schmidt twice per step) on the unknowns (f, W), each
+ * iteration one RPY mobility product in the context's precision.
+ *   n, x     beads [n][3]; bodies: n_bodies, body_offsets, X (Q is not used)
+ *   FL       [n_bodies][6] forces and torques (F, L) per body
+ *   mu       viscosity (> 0)
+ *   opts     rtol (0 -> 1e-6) on ||b - A z|| / ||b||, restart (0 -> 50, <= 200),
+ *            max_iter (0 -> 3000); the other fields are ignored; NULL = defaults
+ *   W        [n_bodies][6] output (U, Omega); f_out [n][3] constraint forces or NULL
+ *   stats    iters, outer, rel_residual, time_ms (or NULL)
+ * In an IBPME_MIXED context the product runs its mesh and real space in FP32 and
+ * is exact to about 1e-7, so rtol much below 1e-6 is not reached there.
+ * Pointers may be host or device memory.  IBPME_ERR_NOT_CONVERGED when max_iter
+ * iterations do not reach rtol (the outputs hold the last iterate);
+ * IBPME_ERR_UNEQUAL_RADII on a context with radius classes. */
+ibpme_status ibpme_rigid_mobility(ibpme_ctx* ctx, int n, const double* x, const ibpme_bodies* bodies,
+                                  const double* FL, double mu, const ibpme_solve_opts* opts, double* W,
+                                  double* f_out, ibpme_solve_stats* stats);
+
 /* ---- Instrumentation (no counterpart in the paper) ---- */
 
 /* Number of kernel launches the library has issued in this process (its own

@@ -79,6 +79,8 @@ SIGNATURES = {
     "ibpme_last_error": (ctypes.c_char_p, []),
     "ibpme_set_radius_classes": (_i, [_p, _i, _p]),
     "ibpme_rpy_mobility": (_i, [_p, _i, _p, _p, _d, _p]),
+    "ibpme_rigid_mobility": (_i, [_p, _i, _p, ctypes.POINTER(ibpme_bodies), _p, _d,
+                                  ctypes.POINTER(ibpme_solve_opts), _p, _p, ctypes.POINTER(ibpme_solve_stats)]),
     "pme_spread": (_i, [_p, _i, _p, _p, _i, _p]),
     "pme_field": (_i, [_p, _i, _p, _p, _i, _p, _p]),
     "induced_charge_solve": (_i, [_p, _i, _p, ctypes.POINTER(ibpme_bodies), _p, _i,
@@ -230,6 +232,19 @@ def ibpme_set_radius_classes(ctx, n, cls):
 def ibpme_rpy_mobility(ctx, n, x, F, mu, U):
     """U [n][3] = periodic RPY mobility (viscosity mu) times the forces F [n][3] at x [n][3]."""
     return _check(load().ibpme_rpy_mobility(ctx, int(n), ptr(x), ptr(F), float(mu), ptr(U)), "ibpme_rpy_mobility")
+
+
+def ibpme_rigid_mobility(ctx, n, x, bodies: Bodies, FL, mu, opts: ibpme_solve_opts | None, W, f_out=None):
+    """Rigid-body mobility problem: FL [n_bodies][6] (F, L) -> W [n_bodies][6] (U, Omega) and the bead
+    constraint forces f_out [n][3].  Returns (status, stats); raises on any status other than OK /
+    NOT_CONVERGED."""
+    st = ibpme_solve_stats()
+    status = load().ibpme_rigid_mobility(ctx, int(n), ptr(x), ctypes.byref(bodies.c), ptr(FL), float(mu),
+                                         ctypes.byref(opts) if opts is not None else None, ptr(W), ptr(f_out),
+                                         ctypes.byref(st))
+    if status not in (IBPME_OK, IBPME_ERR_NOT_CONVERGED):
+        _check(status, "ibpme_rigid_mobility")
+    return status, st
 
 
 def ibpme_get_params(ctx) -> ibpme_params:

@@ -875,6 +875,53 @@ const double* solution_field(ibpme_ctx* c, int n, const double* xw, const double
 
 }  // namespace
 
+IBP_API ibpme_status ibpme_rigid_mobility(ibpme_ctx* c, int n, const double* x, const ibpme_bodies* bodies,
+                                          const double* FL, double mu, const ibpme_solve_opts* opts, double* W,
+                                          double* f_out, ibpme_solve_stats* stats) {
+    return guard([&]() -> ibpme_status {
+        if (!c) fail(IBPME_ERR_ARG, "ctx is NULL");
+        DeviceScope ds(c->device);
+        const auto t0 = std::chrono::steady_clock::now();
+        tma_check(c);
+        check_n(n);
+        if (n == 0) fail(IBPME_ERR_ARG, "the mobility problem needs at least one bead");
+        if (!(mu > 0.0) || !std::isfinite(mu)) fail(IBPME_ERR_ARG, "mu must be > 0");
+        if (c->ncls > 1) fail(IBPME_ERR_UNEQUAL_RADII, "the RPY mobility takes one bead radius");
+        if (!x || !bodies || !FL || !W) fail(IBPME_ERR_ARG, "x, bodies, FL and W are required");
+        ibpme_solve_opts o{};
+        if (opts) o = *opts;
+        const double rtol = o.rtol > 0 ? o.rtol : 1e-6;
+        const int restart = o.restart > 0 ? o.restart : 50;
+        if (restart > 200) fail(IBPME_ERR_ARG, "restart must be <= 200");
+        const int max_iter = o.max_iter > 0 ? o.max_iter : 3000;
+        const double* dx = static_cast<const double*>(stage_in(c, x, sizeof(double) * 3 * n, c->st_x));
+        double* xw = static_cast<double*>(c->xw.ensure(sizeof(double) * 3 * n));
+        wrap_positions(c, n, dx, xw);
+        prepare_bodies(c, n, bodies, xw);
+        c->bodies_current = false;   // the RPY pass takes every pair from the table (no compact bodies)
+        const int nb = bodies->n_bodies;
+        const double* dFL = static_cast<const double*>(stage_in(c, FL, sizeof(double) * 6 * nb, c->st_E0));
+        OutArg ow = stage_out(c, W, sizeof(double) * 6 * (size_t)nb, c->st_out1);
+        OutArg of = stage_out(c, f_out, sizeof(double) * 3 * (size_t)n, c->st_out2);
+        ibpme_solve_stats st{};
+        ibpme_status status = IBPME_OK;
+        try {
+            rigid_solve(c, n, xw, dFL, mu, rtol, restart, max_iter, static_cast<double*>(ow.dev),
+                        static_cast<double*>(of.dev), &st);
+        } catch (const Error& e) {
+            if (e.status != IBPME_ERR_NOT_CONVERGED) throw;
+            status = IBPME_ERR_NOT_CONVERGED;   // outputs hold the last iterate
+        }
+        finish_out(c, ow);
+        finish_out(c, of);
+        IBP_CUDA(cudaStreamSynchronize(c->stream));
+        st.time_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+        if (stats) *stats = st;
+        if (status != IBPME_OK) fail(status, "rigid mobility did not reach rtol %g in %d iterations", rtol, st.iters);
+        return IBPME_OK;
+    });
+}
+
 IBP_API ibpme_status induced_charge_solve(ibpme_ctx* c, int n, const double* x, const ibpme_bodies* bodies,
                                           const double* E0, int nrhs, const ibpme_solve_opts* opts,
                                           double* q_out, double* psi_out, double* S_out,

@@ -466,6 +466,7 @@ struct ibpme_ctx {
     unsigned long long cls_version = 0;       // bumped by every binding (cache keys; 0: none)
     // RPY mobility: real-space radial table (A, B at mu = 1) for (a, xi, r_c) of rpy_key
     ibp::DevBuf rpy_tab, rpy_tab32, rpy_F, rpy_F4, rpy_Uk;
+    ibp::DevBuf rig_V, rig_w, rig_b, rig_x, rig_dot, rig_FL;   // rigid-body mobility GMRES
     double rpy_key[3] = {0.0, 0.0, 0.0};
     double rpy_h = 0.0, rpy_self = 0.0;
     int rpy_nodes = 0;
@@ -520,6 +521,11 @@ void df_fft_convolve(const MeshGeom& g, int ch, const float2* green, const doubl
 // ---- rpy.cu ----
 // U [n][3] = periodic RPY mobility (viscosity mu) times F [n][3] at the wrapped positions xw
 void rpy_apply(ibpme_ctx* c, int n, const double* xw, const double* F, double mu, double* U);
+// Rigid-body mobility problem on the uploaded bodies: FL [nb][6] (F, L) -> W_out [nb][6] (U, Omega),
+// f_out [n][3] (or NULL) bead constraint forces; restarted GMRES(m) to rtol (IBPME_ERR_NOT_CONVERGED
+// past max_iter iterations, outputs hold the last iterate); all pointers device
+void rigid_solve(ibpme_ctx* c, int n, const double* xw, const double* FL, double mu, double rtol, int m,
+                 int max_iter, double* W_out, double* f_out, ibpme_solve_stats* st);
 
 // ---- mesh.cu ----
 // Cached stencils for the current positions (rebuilt when the position

@@ -24,6 +24,7 @@
 //     electrostatic pair table within r_c adds A F_beta + B r_hat (r_hat . F_beta).
 #include "common.cuh"
 
+#include <algorithm>
 #include <cmath>
 #include <vector>
 
@@ -282,6 +283,91 @@ void rpy_table(ibpme_ctx* c) {
     c->rpy_key[2] = rc;
 }
 
+// ---- rigid-body mobility problem (the paper's last equation, physical sign) ----
+// Unknowns z = [f (n x 3 bead constraint forces); W (n_b x 6 body motions U, Omega)], operator
+//     [ M f - K W ;  K^T f ]   with (K W)_j = U_b + Omega_b x r_j,  K^T f = (sum f, sum r x f),
+// right-hand side [0; (F, L)].  A single-bead body moves by U alone: its Omega rows hold Omega
+// itself (right-hand side 0), so the system stays regular.
+
+// y_f -= K W
+__global__ void rigid_kw_kernel(int n, const int* __restrict__ bead_body, const int* __restrict__ off,
+                                const double* __restrict__ rel, const double* __restrict__ W,
+                                double* __restrict__ y) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n) return;
+    const int b = bead_body[j];
+    const double* w = W + 6 * (size_t)b;
+    double u[3] = {w[0], w[1], w[2]};
+    if (off[b + 1] - off[b] > 1) {
+        const double r[3] = {rel[3 * j], rel[3 * j + 1], rel[3 * j + 2]};
+        u[0] += w[4] * r[2] - w[5] * r[1];
+        u[1] += w[5] * r[0] - w[3] * r[2];
+        u[2] += w[3] * r[1] - w[4] * r[0];
+    }
+    for (int d = 0; d < 3; ++d) y[3 * j + d] -= u[d];
+}
+
+// y_W = (F, L) of the bead forces per body; Omega for single-bead bodies
+__global__ void rigid_body_rows_kernel(int nb, const int* __restrict__ off, const double* __restrict__ F,
+                                       const double* __restrict__ L, const double* __restrict__ W,
+                                       double* __restrict__ yW) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= nb) return;
+    const bool multi = off[b + 1] - off[b] > 1;
+    for (int d = 0; d < 3; ++d) {
+        yW[6 * b + d] = F[3 * b + d];
+        yW[6 * b + 3 + d] = multi ? L[3 * b + d] : W[6 * b + 3 + d];
+    }
+}
+
+// b = [0; (F, L)] with the torque rows of single-bead bodies zero
+__global__ void rigid_rhs_kernel(int n, int nb, const int* __restrict__ off, const double* __restrict__ FL,
+                                 double* __restrict__ b) {
+    const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (t < 3LL * n) {
+        b[t] = 0.0;
+        return;
+    }
+    const long long k = t - 3LL * n;
+    if (k >= 6LL * nb) return;
+    const int body = (int)(k / 6), c = (int)(k % 6);
+    b[t] = (c < 3 || off[body + 1] - off[body] > 1) ? FL[k] : 0.0;
+}
+
+// out[v] += sum_i V[v][i] w[i] for v < nv (out zeroed by the caller); blockIdx.y = v
+__global__ void multi_dot_kernel(long long N, const double* __restrict__ V, long long ldv,
+                                 const double* __restrict__ w, double* __restrict__ out) {
+    __shared__ double sh[32];
+    const double* v = V + (size_t)blockIdx.y * ldv;
+    double acc = 0.0;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x)
+        acc += v[i] * w[i];
+    acc = warp_sum(acc);
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        double t = threadIdx.x < (blockDim.x >> 5) ? sh[threadIdx.x] : 0.0;
+        t = warp_sum(t);
+        if (threadIdx.x == 0) atomicAdd(out + blockIdx.y, t);
+    }
+}
+
+// w[i] += s sum_v coef[v] V[v][i]
+__global__ void multi_axpy_kernel(long long N, const double* __restrict__ V, long long ldv, int nv,
+                                  const double* __restrict__ coef, double s, double* __restrict__ w) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x) {
+        double acc = 0.0;
+        for (int v = 0; v < nv; ++v) acc += coef[v] * V[(size_t)v * ldv + i];
+        w[i] += s * acc;
+    }
+}
+
+// dst = s src
+__global__ void scale_copy_kernel(long long N, double s, const double* __restrict__ src, double* __restrict__ dst) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x)
+        dst[i] = s * src[i];
+}
+
 }  // namespace
 
 void rpy_apply(ibpme_ctx* c, int n, const double* xw, const double* F, double mu, double* U) {
@@ -327,6 +413,132 @@ void rpy_apply(ibpme_ctx* c, int n, const double* xw, const double* F, double mu
     IBP_CHECK_LAUNCH();
     rpy_combine_kernel<<<div_up(3LL * n, 256), 256, 0, s>>>(n, Uk, U);
     IBP_CHECK_LAUNCH();
+}
+
+namespace {
+
+// y = A z for the rigid-body mobility operator (bodies uploaded, positions xw)
+void rigid_apply(ibpme_ctx* c, int n, const double* xw, double mu, const double* z, double* y) {
+    const BodyData& bd = c->bodies;
+    cudaStream_t s = c->stream;
+    const int nb = bd.nb;
+    rpy_apply(c, n, xw, z, mu, y);
+    rigid_kw_kernel<<<div_up(n, 256), 256, 0, s>>>(n, bd.bead_body.as<int>(), bd.off.as<int>(), bd.rel.as<double>(),
+                                                    z + 3 * (size_t)n, y);
+    IBP_CHECK_LAUNCH();
+    double* FL = static_cast<double*>(c->rig_FL.ensure(sizeof(double) * 6 * (size_t)nb));
+    body_reduce_force_torque(c, n, z, FL, FL + 3 * (size_t)nb);
+    rigid_body_rows_kernel<<<div_up(nb, 256), 256, 0, s>>>(nb, bd.off.as<int>(), FL, FL + 3 * (size_t)nb,
+                                                           z + 3 * (size_t)n, y + 3 * (size_t)n);
+    IBP_CHECK_LAUNCH();
+}
+
+int vec_blocks(long long N) { return (int)std::min<long long>(div_up(N, 256), 152LL * 8); }
+
+}  // namespace
+
+void rigid_solve(ibpme_ctx* c, int n, const double* xw, const double* FL, double mu, double rtol, int m,
+                 int max_iter, double* W_out, double* f_out, ibpme_solve_stats* st) {
+    cudaStream_t s = c->stream;
+    const int nb = c->bodies.nb;
+    const long long N = 3LL * n + 6LL * nb;
+    double* V = static_cast<double*>(c->rig_V.ensure(sizeof(double) * (size_t)N * (m + 1)));
+    double* w = static_cast<double*>(c->rig_w.ensure(sizeof(double) * (size_t)N));
+    double* b = static_cast<double*>(c->rig_b.ensure(sizeof(double) * (size_t)N));
+    double* x = static_cast<double*>(c->rig_x.ensure(sizeof(double) * (size_t)N));
+    double* dd = static_cast<double*>(c->rig_dot.ensure(sizeof(double) * (size_t)(m + 2)));
+    const int vb = vec_blocks(N);
+    std::vector<double> hh(m + 2);
+    auto dots = [&](const double* Vs, int nv, const double* v) {   // V[0..nv) . v -> hh
+        IBP_CUDA(cudaMemsetAsync(dd, 0, sizeof(double) * nv, s));
+        multi_dot_kernel<<<dim3(vb, nv), 256, 0, s>>>(N, Vs, N, v, dd);
+        IBP_CHECK_LAUNCH();
+        IBP_CUDA(cudaMemcpyAsync(hh.data(), dd, sizeof(double) * nv, cudaMemcpyDeviceToHost, s));
+        IBP_CUDA(cudaStreamSynchronize(s));
+    };
+    auto axpy = [&](const double* Vs, int nv, const double* coef_h, double sc, double* v) {   // v += sc V coef
+        IBP_CUDA(cudaMemcpyAsync(dd, coef_h, sizeof(double) * nv, cudaMemcpyHostToDevice, s));
+        multi_axpy_kernel<<<vb, 256, 0, s>>>(N, Vs, N, nv, dd, sc, v);
+        IBP_CHECK_LAUNCH();
+        IBP_CUDA(cudaStreamSynchronize(s));   // coef_h is reused
+    };
+    rigid_rhs_kernel<<<(unsigned)div_up(N, 256), 256, 0, s>>>(n, nb, c->bodies.off.as<int>(), FL, b);
+    IBP_CHECK_LAUNCH();
+    IBP_CUDA(cudaMemsetAsync(x, 0, sizeof(double) * (size_t)N, s));
+    dots(b, 1, b);
+    const double bnorm = std::sqrt(hh[0]);
+    int iters = 0, outer = 0;
+    double rel = 0.0;
+    std::vector<double> H((size_t)(m + 1) * m), cs(m), sn(m), g(m + 1), y(m);
+    while (true) {
+        // r = b - A x into V_0
+        if (iters == 0) {
+            IBP_CUDA(cudaMemcpyAsync(V, b, sizeof(double) * (size_t)N, cudaMemcpyDeviceToDevice, s));
+        } else {
+            rigid_apply(c, n, xw, mu, x, w);
+            scale_copy_kernel<<<vb, 256, 0, s>>>(N, 1.0, b, V);
+            IBP_CHECK_LAUNCH();
+            const double one = 1.0;
+            axpy(w, 1, &one, -1.0, V);
+        }
+        dots(V, 1, V);
+        const double beta = std::sqrt(hh[0]);
+        rel = bnorm > 0.0 ? beta / bnorm : 0.0;
+        if (bnorm == 0.0 || rel <= rtol || iters >= max_iter) break;
+        ++outer;
+        scale_copy_kernel<<<vb, 256, 0, s>>>(N, 1.0 / beta, V, V);
+        IBP_CHECK_LAUNCH();
+        std::fill(g.begin(), g.end(), 0.0);
+        g[0] = beta;
+        int k = 0;
+        for (int j = 0; j < m && iters < max_iter; ++j) {
+            double* vj1 = V + (size_t)(j + 1) * N;
+            rigid_apply(c, n, xw, mu, V + (size_t)j * N, vj1);
+            std::vector<double> h(j + 2, 0.0);
+            for (int pass = 0; pass < 2; ++pass) {   // classical Gram-Schmidt, twice
+                dots(V, j + 1, vj1);
+                for (int i = 0; i <= j; ++i) h[i] += hh[i];
+                axpy(V, j + 1, hh.data(), -1.0, vj1);
+            }
+            dots(vj1, 1, vj1);
+            h[j + 1] = std::sqrt(hh[0]);
+            if (h[j + 1] > 0.0) {
+                scale_copy_kernel<<<vb, 256, 0, s>>>(N, 1.0 / h[j + 1], vj1, vj1);
+                IBP_CHECK_LAUNCH();
+            }
+            for (int i = 0; i < j; ++i) {   // earlier rotations
+                const double t = cs[i] * h[i] + sn[i] * h[i + 1];
+                h[i + 1] = -sn[i] * h[i] + cs[i] * h[i + 1];
+                h[i] = t;
+            }
+            const double den = std::hypot(h[j], h[j + 1]);
+            cs[j] = den > 0.0 ? h[j] / den : 1.0;
+            sn[j] = den > 0.0 ? h[j + 1] / den : 0.0;
+            h[j] = den;
+            g[j + 1] = -sn[j] * g[j];
+            g[j] = cs[j] * g[j];
+            for (int i = 0; i <= j; ++i) H[(size_t)i * m + j] = h[i];
+            ++iters;
+            k = j + 1;
+            if (std::fabs(g[j + 1]) <= rtol * bnorm || h[j + 1] == 0.0) break;
+        }
+        for (int i = k - 1; i >= 0; --i) {   // H y = g, upper triangular
+            double t = g[i];
+            for (int l = i + 1; l < k; ++l) t -= H[(size_t)i * m + l] * y[l];
+            y[i] = t / H[(size_t)i * m + i];
+        }
+        axpy(V, k, y.data(), 1.0, x);
+    }
+    IBP_CUDA(cudaMemcpyAsync(W_out, x + 3 * (size_t)n, sizeof(double) * 6 * (size_t)nb, cudaMemcpyDeviceToDevice, s));
+    if (f_out)
+        IBP_CUDA(cudaMemcpyAsync(f_out, x, sizeof(double) * 3 * (size_t)n, cudaMemcpyDeviceToDevice, s));
+    if (st) {
+        st->iters = iters;
+        st->outer = outer;
+        st->rel_residual = rel;
+    }
+    if (!(rel <= rtol)) fail(IBPME_ERR_NOT_CONVERGED, "rigid mobility: relative residual %.3g after %d iterations",
+                             rel, iters);
 }
 
 }  // namespace ibp
