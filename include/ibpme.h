@@ -465,12 +465,17 @@ ibpme_status pme_spread_noalloc(const ibpme_params* params, int n, const double*
  * of two or more beads must not be collinear (a rod of beads has no resistance to
  * spinning about its axis, and the system is then singular).  Solved by restarted
  * GMRES (classical Gram-Schmidt twice per step) on the unknowns (f, W), each
- * iteration one RPY mobility product in the context's precision.
+ * iteration one RPY mobility product in the context's precision, right-
+ * preconditioned by default (opts->precond = IBPME_PRECOND_BODY) with the exact
+ * inverse of every multi-bead body's own block under the free-space RPY tensor
+ * (an FP32 inverse of its 3 n_b x 3 n_b mobility, built at every call, bodies of
+ * up to 2,730 beads; larger ones leave the solve unpreconditioned) and of every
+ * single bead's; IBPME_PRECOND_NONE iterates on the bare system.
  *   n, x     beads [n][3]; bodies: n_bodies, body_offsets, X (Q is not used)
  *   FL       [n_bodies][6] forces and torques (F, L) per body
  *   mu       viscosity (> 0)
  *   opts     rtol (0 -> 1e-6) on ||b - A z|| / ||b||, restart (0 -> 50, <= 200),
- *            max_iter (0 -> 3000); the other fields are ignored; NULL = defaults
+ *            max_iter (0 -> 3000), precond; the other fields are ignored; NULL = defaults
  *   W        [n_bodies][6] output (U, Omega); f_out [n][3] constraint forces or NULL
  *   stats    iters, outer, rel_residual, time_ms (or NULL)
  * In an IBPME_MIXED context the product runs its mesh and real space in FP32 and

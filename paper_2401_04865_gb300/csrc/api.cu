@@ -907,7 +907,7 @@ IBP_API ibpme_status ibpme_rigid_mobility(ibpme_ctx* c, int n, const double* x, 
         ibpme_status status = IBPME_OK;
         try {
             rigid_solve(c, n, xw, dFL, mu, rtol, restart, max_iter, static_cast<double*>(ow.dev),
-                        static_cast<double*>(of.dev), &st);
+                        static_cast<double*>(of.dev), &st, o.precond != IBPME_PRECOND_NONE);
         } catch (const Error& e) {
             if (e.status != IBPME_ERR_NOT_CONVERGED) throw;
             status = IBPME_ERR_NOT_CONVERGED;   // outputs hold the last iterate

@@ -467,6 +467,8 @@ struct ibpme_ctx {
     // RPY mobility: real-space radial table (A, B at mu = 1) for (a, xi, r_c) of rpy_key
     ibp::DevBuf rpy_tab, rpy_tab32, rpy_F, rpy_F4, rpy_Uk;
     ibp::DevBuf rig_V, rig_w, rig_b, rig_x, rig_dot, rig_FL;   // rigid-body mobility GMRES
+    ibp::DevBuf rig_z, rig_u, rig_t, rig_minv, rig_G, rig_Sinv, rig_pb, rig_moff, rig_goff, rig_idx;   // and its
+    int rig_nmb = 0, rig_maxn = 0;   // body-block preconditioner
     double rpy_key[3] = {0.0, 0.0, 0.0};
     double rpy_h = 0.0, rpy_self = 0.0;
     int rpy_nodes = 0;
@@ -525,7 +527,10 @@ void rpy_apply(ibpme_ctx* c, int n, const double* xw, const double* F, double mu
 // f_out [n][3] (or NULL) bead constraint forces; restarted GMRES(m) to rtol (IBPME_ERR_NOT_CONVERGED
 // past max_iter iterations, outputs hold the last iterate); all pointers device
 void rigid_solve(ibpme_ctx* c, int n, const double* xw, const double* FL, double mu, double rtol, int m,
-                 int max_iter, double* W_out, double* f_out, ibpme_solve_stats* st);
+                 int max_iter, double* W_out, double* f_out, ibpme_solve_stats* st, bool precond = true);
+// ---- precond.cu ----
+// A (nb x nb, FP32, symmetric positive definite) -> A^{-1} in place (blocked Gauss-Jordan)
+void invert_spd(ibpme_ctx* c, int nb, float* A);
 
 // ---- mesh.cu ----
 // Cached stencils for the current positions (rebuilt when the position

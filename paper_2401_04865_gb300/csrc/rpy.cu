@@ -417,6 +417,141 @@ void rpy_apply(ibpme_ctx* c, int n, const double* xw, const double* F, double mu
 
 namespace {
 
+// ---- body-block preconditioner of the rigid-body mobility problem ----
+// For every multi-bead body the exact inverse of its own block with the free-space RPY
+// tensor of its beads M_b (3 n_b x 3 n_b, FP32 inverse): [M_b -K_b; K_b^T 0]^{-1} [v; g] is
+//     t = M_b^{-1} v,  W = S^{-1} (g - K_b^T t),  f = t + G W,   G = M_b^{-1} K_b, S = K_b^T G;
+// for a single bead (self mobility m = 1/(6 pi mu a)) f = g_F, U = m g_F - v, Omega = g_Omega.
+// GMRES then iterates on A P^{-1}, whose remaining coupling is between bodies.
+
+// M_b of one body: entry (3i+p, 3j+q) = (A delta_pq + B r_p r_q / r^2) / mu (free-space RPY)
+__global__ void rigid_block_kernel(int nb, const double* __restrict__ rel, double a, double inv_mu,
+                                   float* __restrict__ M) {
+    const long long m3 = 3LL * nb;
+    const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (t >= m3 * m3) return;
+    const int row = (int)(t / m3), col = (int)(t % m3);
+    const int i = row / 3, p = row % 3, j = col / 3, q = col % 3;
+    const double d[3] = {rel[3 * i] - rel[3 * j], rel[3 * i + 1] - rel[3 * j + 1], rel[3 * i + 2] - rel[3 * j + 2]};
+    const double r = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+    double A, B;
+    rpy_free(r, a, A, B);
+    const double v = (p == q ? A : 0.0) + (r > 0.0 ? B * d[p] * d[q] / (r * r) : 0.0);
+    M[t] = (float)(v * inv_mu);
+}
+
+// G = M_b^{-1} K_b (3 n_b x 6, row-major), one thread per entry
+__global__ void rigid_g_kernel(int nb, const float* __restrict__ Minv, const double* __restrict__ rel,
+                               double* __restrict__ G) {
+    const int m3 = 3 * nb;
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= m3 * 6) return;
+    const int row = t / 6, k = t % 6;
+    double acc = 0.0;
+    for (int col = 0; col < m3; ++col) {
+        const int j = col / 3, q = col % 3;
+        double kv;
+        if (k < 3) {
+            kv = q == k ? 1.0 : 0.0;
+        } else {   // (e_{k-3} x r_j)_q
+            const double* r = rel + 3 * j;
+            const int e = k - 3;
+            kv = e == 0 ? (q == 1 ? -r[2] : (q == 2 ? r[1] : 0.0))
+               : e == 1 ? (q == 0 ? r[2] : (q == 2 ? -r[0] : 0.0))
+                        : (q == 0 ? -r[1] : (q == 1 ? r[0] : 0.0));
+        }
+        acc += (double)Minv[(size_t)row * m3 + col] * kv;
+    }
+    G[t] = acc;
+}
+
+// t = M_b^{-1} v for every preconditioned body: blockIdx.y = body, one warp per row
+__global__ void rigid_pre_minv_kernel(const int4* __restrict__ pb, const long long* __restrict__ moff,
+                                      const float* __restrict__ Minv, const double* __restrict__ v,
+                                      double* __restrict__ tvec) {
+    const int4 P = pb[blockIdx.y];   // (body, first bead, beads, -)
+    const int m3 = 3 * P.z;
+    const int row = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (row >= m3) return;
+    const float* Mr = Minv + moff[blockIdx.y] + (size_t)row * m3;
+    const double* vb = v + 3 * (size_t)P.y;
+    double acc = 0.0;
+    for (int col = lane; col < m3; col += 32) acc += (double)Mr[col] * vb[col];
+    acc = warp_sum(acc);
+    if (lane == 0) tvec[3 * (size_t)P.y + row] = acc;
+}
+
+// W_b = S^{-1} (g_b - K_b^T t) per preconditioned body (one block each)
+__global__ void rigid_pre_body_kernel(const int4* __restrict__ pb, const double* __restrict__ rel,
+                                      const double* __restrict__ Sinv, const double* __restrict__ tvec,
+                                      const double* __restrict__ gW, double* __restrict__ outW) {
+    __shared__ double sh[6][32];
+    const int4 P = pb[blockIdx.x];
+    double acc[6] = {0, 0, 0, 0, 0, 0};
+    for (int j = P.y + threadIdx.x; j < P.y + P.z; j += blockDim.x) {
+        const double* t = tvec + 3 * (size_t)j;
+        const double* r = rel + 3 * (size_t)j;
+        acc[0] += t[0];
+        acc[1] += t[1];
+        acc[2] += t[2];
+        acc[3] += r[1] * t[2] - r[2] * t[1];
+        acc[4] += r[2] * t[0] - r[0] * t[2];
+        acc[5] += r[0] * t[1] - r[1] * t[0];
+    }
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    for (int k = 0; k < 6; ++k) {
+        const double v = warp_sum(acc[k]);
+        if (lane == 0) sh[k][w] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double h[6];
+        for (int k = 0; k < 6; ++k) {
+            double v = 0.0;
+            for (int q = 0; q < (int)(blockDim.x >> 5); ++q) v += sh[k][q];
+            h[k] = gW[6 * (size_t)P.x + k] - v;
+        }
+        const double* Si = Sinv + 36 * (size_t)blockIdx.x;
+        for (int k = 0; k < 6; ++k) {
+            double v = 0.0;
+            for (int l = 0; l < 6; ++l) v += Si[6 * k + l] * h[l];
+            outW[6 * (size_t)P.x + k] = v;
+        }
+    }
+}
+
+// f_j = t_j + G_j W_b for beads of preconditioned bodies; single beads exactly; (body index of
+// each bead's preconditioned block in pre_of, -1 for single beads)
+__global__ void rigid_pre_bead_kernel(int n, const int* __restrict__ bead_body, const int* __restrict__ off,
+                                      const int* __restrict__ pre_first, const long long* __restrict__ goff,
+                                      const int* __restrict__ pre_of, const double* __restrict__ G,
+                                      const double* __restrict__ tvec, double mself, const double* __restrict__ v,
+                                      double* __restrict__ out) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n) return;
+    const int b = bead_body[j];
+    const long long nw = 3LL * n;
+    const double* gW = v + nw + 6 * (size_t)b;
+    double* oW = out + nw + 6 * (size_t)b;
+    if (off[b + 1] - off[b] == 1) {
+        for (int d = 0; d < 3; ++d) {
+            out[3 * (size_t)j + d] = gW[d];
+            oW[d] = mself * gW[d] - v[3 * (size_t)j + d];
+            oW[3 + d] = gW[3 + d];
+        }
+        return;
+    }
+    const int q = pre_of[b];
+    const double* W = out + nw + 6 * (size_t)b;
+    const double* Gj = G + goff[q] + 18 * (size_t)(j - pre_first[q]);
+    for (int d = 0; d < 3; ++d) {
+        double acc = tvec[3 * (size_t)j + d];
+        for (int k = 0; k < 6; ++k) acc += Gj[6 * d + k] * W[k];
+        out[3 * (size_t)j + d] = acc;
+    }
+}
+
 // y = A z for the rigid-body mobility operator (bodies uploaded, positions xw)
 void rigid_apply(ibpme_ctx* c, int n, const double* xw, double mu, const double* z, double* y) {
     const BodyData& bd = c->bodies;
@@ -435,13 +570,136 @@ void rigid_apply(ibpme_ctx* c, int n, const double* xw, double mu, const double*
 
 int vec_blocks(long long N) { return (int)std::min<long long>(div_up(N, 256), 152LL * 8); }
 
+// The blocks of every multi-bead body at the current positions; false when a body is too
+// large for the dense inverse (the solve then runs unpreconditioned).
+bool rigid_precond_build(ibpme_ctx* c, int n, double mu) {
+    const BodyData& bd = c->bodies;
+    cudaStream_t s = c->stream;
+    const std::vector<int>& off = bd.host_off;
+    const int nb = bd.nb;
+    std::vector<int4> pb;
+    std::vector<long long> moff, goff;
+    std::vector<int> pre_of(nb, -1), pre_first;
+    long long mtot = 0, gtot = 0;
+    int maxn = 0;
+    for (int b = 0; b < nb; ++b) {
+        const int k = off[b + 1] - off[b];
+        if (k < 2) continue;
+        if (3 * k > kPrecondMaxBeads) return false;
+        pre_of[b] = (int)pb.size();
+        pb.push_back(make_int4(b, off[b], k, 0));
+        pre_first.push_back(off[b]);
+        moff.push_back(mtot);
+        goff.push_back(gtot);
+        mtot += 9LL * k * k;
+        gtot += 18LL * k;
+        maxn = std::max(maxn, k);
+    }
+    const int nmb = (int)pb.size();
+    c->rig_nmb = nmb;
+    c->rig_maxn = maxn;
+    if (nmb == 0) return true;
+    float* minv = static_cast<float*>(c->rig_minv.ensure(sizeof(float) * (size_t)mtot));
+    double* G = static_cast<double*>(c->rig_G.ensure(sizeof(double) * (size_t)gtot));
+    std::vector<double> rel(3 * (size_t)n);
+    IBP_CUDA(cudaMemcpyAsync(rel.data(), bd.rel.p, sizeof(double) * 3 * (size_t)n, cudaMemcpyDeviceToHost, s));
+    IBP_CUDA(cudaStreamSynchronize(s));
+    std::vector<double> Sinv(36 * (size_t)nmb), Gh;
+    for (int q = 0; q < nmb; ++q) {
+        const int k = pb[q].z, first = pb[q].y, m3 = 3 * k;
+        float* A = minv + moff[q];
+        const double* relb = bd.rel.as<double>() + 3 * (size_t)first;
+        rigid_block_kernel<<<(unsigned)div_up((long long)m3 * m3, 256), 256, 0, s>>>(k, relb, c->a, 1.0 / mu, A);
+        IBP_CHECK_LAUNCH();
+        invert_spd(c, m3, A);
+        rigid_g_kernel<<<div_up(m3 * 6, 128), 128, 0, s>>>(k, A, relb, G + goff[q]);
+        IBP_CHECK_LAUNCH();
+        Gh.resize((size_t)m3 * 6);
+        IBP_CUDA(cudaMemcpyAsync(Gh.data(), G + goff[q], sizeof(double) * Gh.size(), cudaMemcpyDeviceToHost, s));
+        IBP_CUDA(cudaStreamSynchronize(s));
+        // S = K^T G (6 x 6), then its inverse by Gauss-Jordan with partial pivoting
+        double S[6][12] = {};
+        for (int j = 0; j < k; ++j) {
+            const double* r = rel.data() + 3 * (size_t)(first + j);
+            for (int qq = 0; qq < 3; ++qq) {
+                const double* g = Gh.data() + 6 * (size_t)(3 * j + qq);
+                // K row (3j+qq): translation e_qq, rotation columns (e_e x r)_qq
+                double kr[6] = {0, 0, 0, 0, 0, 0};
+                kr[qq] = 1.0;
+                kr[3] = qq == 1 ? -r[2] : (qq == 2 ? r[1] : 0.0);
+                kr[4] = qq == 0 ? r[2] : (qq == 2 ? -r[0] : 0.0);
+                kr[5] = qq == 0 ? -r[1] : (qq == 1 ? r[0] : 0.0);
+                for (int a2 = 0; a2 < 6; ++a2)
+                    for (int l = 0; l < 6; ++l) S[a2][l] += kr[a2] * g[l];
+            }
+        }
+        for (int a2 = 0; a2 < 6; ++a2) S[a2][6 + a2] = 1.0;
+        for (int col = 0; col < 6; ++col) {
+            int piv = col;
+            for (int r2 = col + 1; r2 < 6; ++r2)
+                if (std::fabs(S[r2][col]) > std::fabs(S[piv][col])) piv = r2;
+            if (!(std::fabs(S[piv][col]) > 0.0))
+                fail(IBPME_ERR_ARG, "body %d: its beads are collinear (no resistance to spin about its axis)",
+                     pb[q].x);
+            for (int l = 0; l < 12; ++l) std::swap(S[col][l], S[piv][l]);
+            const double d = S[col][col];
+            for (int l = 0; l < 12; ++l) S[col][l] /= d;
+            for (int r2 = 0; r2 < 6; ++r2) {
+                if (r2 == col) continue;
+                const double f = S[r2][col];
+                for (int l = 0; l < 12; ++l) S[r2][l] -= f * S[col][l];
+            }
+        }
+        for (int a2 = 0; a2 < 6; ++a2)
+            for (int l = 0; l < 6; ++l) Sinv[36 * (size_t)q + 6 * a2 + l] = S[a2][6 + l];
+    }
+    auto up = [&](DevBuf& dst, const void* src, size_t bytes) {
+        dst.ensure(bytes > 0 ? bytes : 4);
+        if (bytes) IBP_CUDA(cudaMemcpyAsync(dst.p, src, bytes, cudaMemcpyHostToDevice, s));
+    };
+    up(c->rig_Sinv, Sinv.data(), sizeof(double) * Sinv.size());
+    up(c->rig_pb, pb.data(), sizeof(int4) * pb.size());
+    up(c->rig_moff, moff.data(), sizeof(long long) * moff.size());
+    up(c->rig_goff, goff.data(), sizeof(long long) * goff.size());
+    std::vector<int> idx(pre_of);
+    idx.insert(idx.end(), pre_first.begin(), pre_first.end());   // [nb] pre_of, then [nmb] first beads
+    up(c->rig_idx, idx.data(), sizeof(int) * idx.size());
+    IBP_CUDA(cudaStreamSynchronize(s));   // the host vectors go out of scope
+    return true;
+}
+
+// out = P^{-1} v
+void rigid_precond_apply(ibpme_ctx* c, int n, double mu, const double* v, double* out) {
+    const BodyData& bd = c->bodies;
+    cudaStream_t s = c->stream;
+    double* t = static_cast<double*>(c->rig_t.ensure(sizeof(double) * 3 * (size_t)n));
+    const int nmb = c->rig_nmb;
+    if (nmb > 0) {
+        rigid_pre_minv_kernel<<<dim3(div_up(3 * c->rig_maxn, 8), nmb), 256, 0, s>>>(
+            c->rig_pb.as<int4>(), c->rig_moff.as<long long>(), c->rig_minv.as<float>(), v, t);
+        IBP_CHECK_LAUNCH();
+        rigid_pre_body_kernel<<<nmb, 128, 0, s>>>(c->rig_pb.as<int4>(), bd.rel.as<double>(), c->rig_Sinv.as<double>(),
+                                                  t, v + 3 * (size_t)n, out + 3 * (size_t)n);
+        IBP_CHECK_LAUNCH();
+    }
+    const int* idx = c->rig_idx.as<int>();
+    rigid_pre_bead_kernel<<<div_up(n, 256), 256, 0, s>>>(
+        n, bd.bead_body.as<int>(), bd.off.as<int>(), nmb > 0 ? idx + bd.nb : nullptr, c->rig_goff.as<long long>(),
+        idx, c->rig_G.as<double>(), t, 1.0 / (6.0 * kPi * mu * c->a), v, out);
+    IBP_CHECK_LAUNCH();
+}
+
 }  // namespace
 
 void rigid_solve(ibpme_ctx* c, int n, const double* xw, const double* FL, double mu, double rtol, int m,
-                 int max_iter, double* W_out, double* f_out, ibpme_solve_stats* st) {
+                 int max_iter, double* W_out, double* f_out, ibpme_solve_stats* st, bool precond) {
     cudaStream_t s = c->stream;
     const int nb = c->bodies.nb;
     const long long N = 3LL * n + 6LL * nb;
+    // right preconditioning: Arnoldi on A P^{-1}, x = P^{-1} (V y)
+    const bool pre = precond && rigid_precond_build(c, n, mu);
+    double* zb = pre ? static_cast<double*>(c->rig_z.ensure(sizeof(double) * (size_t)N)) : nullptr;
+    double* ub = pre ? static_cast<double*>(c->rig_u.ensure(sizeof(double) * (size_t)N)) : nullptr;
     double* V = static_cast<double*>(c->rig_V.ensure(sizeof(double) * (size_t)N * (m + 1)));
     double* w = static_cast<double*>(c->rig_w.ensure(sizeof(double) * (size_t)N));
     double* b = static_cast<double*>(c->rig_b.ensure(sizeof(double) * (size_t)N));
@@ -493,7 +751,12 @@ void rigid_solve(ibpme_ctx* c, int n, const double* xw, const double* FL, double
         int k = 0;
         for (int j = 0; j < m && iters < max_iter; ++j) {
             double* vj1 = V + (size_t)(j + 1) * N;
-            rigid_apply(c, n, xw, mu, V + (size_t)j * N, vj1);
+            if (pre) {
+                rigid_precond_apply(c, n, mu, V + (size_t)j * N, zb);
+                rigid_apply(c, n, xw, mu, zb, vj1);
+            } else {
+                rigid_apply(c, n, xw, mu, V + (size_t)j * N, vj1);
+            }
             std::vector<double> h(j + 2, 0.0);
             for (int pass = 0; pass < 2; ++pass) {   // classical Gram-Schmidt, twice
                 dots(V, j + 1, vj1);
@@ -527,7 +790,15 @@ void rigid_solve(ibpme_ctx* c, int n, const double* xw, const double* FL, double
             for (int l = i + 1; l < k; ++l) t -= H[(size_t)i * m + l] * y[l];
             y[i] = t / H[(size_t)i * m + i];
         }
-        axpy(V, k, y.data(), 1.0, x);
+        if (pre) {
+            IBP_CUDA(cudaMemsetAsync(ub, 0, sizeof(double) * (size_t)N, s));
+            axpy(V, k, y.data(), 1.0, ub);
+            rigid_precond_apply(c, n, mu, ub, zb);
+            const double one = 1.0;
+            axpy(zb, 1, &one, 1.0, x);
+        } else {
+            axpy(V, k, y.data(), 1.0, x);
+        }
     }
     IBP_CUDA(cudaMemcpyAsync(W_out, x + 3 * (size_t)n, sizeof(double) * 6 * (size_t)nb, cudaMemcpyDeviceToDevice, s));
     if (f_out)

@@ -4,7 +4,8 @@ Against the oracle's dense LU of the same saddle system on the periodic RPY mobi
 (oracle/rpy_ref.py, pinned in test_oracle_rpy.py): a square of four beads, a twelve-bead
 icosahedron and three free beads.  Bars: 1e-5 (FP64) and 1e-3 (mixed) of each output's
 largest magnitude; the constraint forces add up to each body's force; single-bead
-bodies do not rotate; an iteration limit returns IBPME_ERR_NOT_CONVERGED.
+bodies do not rotate; the body-block preconditioner gives the same solution in fewer
+iterations; an iteration limit returns IBPME_ERR_NOT_CONVERGED.
 """
 import functools
 
@@ -80,6 +81,18 @@ def test_rigid_mobility_matches_dense_oracle(cuda_lib, prec):
     assert rel_err(f, fr) < bar, rel_err(f, fr)
     assert np.abs(W[2:, 3:]).max() == 0.0                      # single beads do not rotate
     same = 1e-9 if prec == "fp64" else 1e-4
+    if prec == "fp64":   # the body-block preconditioner changes the iterations, not the solution
+        ctx = _ctx(ib, prec)
+        try:
+            Wn = torch.zeros((len(X), 6), dtype=torch.float64, device="cuda")
+            status, stn = ib.ibpme_rigid_mobility(ctx, len(x), cuda(x), ib.Bodies(cuda(off), cuda(X),
+                                                  cuda(np.zeros(len(X)))), cuda(FL), MU,
+                                                  ib.make_opts(rtol=rtol, precond=ib.IBPME_PRECOND_NONE), Wn)
+            torch.cuda.synchronize()
+            assert status == ib.IBPME_OK and st.iters < stn.iters, (st.iters, stn.iters)
+            assert np.abs(Wn.cpu().numpy() - W).max() < 1e-8 * np.abs(W).max()
+        finally:
+            ib.pme_destroy(ctx)
     for b in range(len(X)):                                     # sum of the constraint forces = F
         assert np.abs(f[off[b]:off[b + 1]].sum(axis=0) - FL[b, :3]).max() < 10 * rtol * np.abs(FL).max()
     assert np.abs(Wh - W).max() < same * np.abs(W).max() and np.abs(fh - f).max() < same * np.abs(f).max()
@@ -94,9 +107,9 @@ def test_rigid_mobility_iteration_limit(cuda_lib):
         bodies = ib.Bodies(cuda(off), cuda(X), cuda(np.zeros(len(X))))
         W = torch.zeros((len(X), 6), dtype=torch.float64, device="cuda")
         status, st = ib.ibpme_rigid_mobility(ctx, len(x), cuda(x), bodies, cuda(FL), MU,
-                                             ib.make_opts(rtol=1e-12, max_iter=2), W)
+                                             ib.make_opts(rtol=1e-14, max_iter=2), W)
         torch.cuda.synchronize()
-        assert status == ib.IBPME_ERR_NOT_CONVERGED and st.iters == 2 and st.rel_residual > 1e-12
+        assert status == ib.IBPME_ERR_NOT_CONVERGED and st.iters == 2 and st.rel_residual > 1e-14
         assert np.isfinite(W.cpu().numpy()).all()
         with pytest.raises(ib.IbpmeError) as e:
             ib.ibpme_rigid_mobility(ctx, len(x), cuda(x), bodies, cuda(FL), 0.0, None, W)
