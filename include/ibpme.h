@@ -471,7 +471,8 @@ ibpme_status pme_spread_noalloc(const ibpme_params* params, int n, const double*
  * (an FP32 inverse of its 3 n_b x 3 n_b mobility, built at every call, bodies of
  * up to 2,730 beads; larger ones leave the solve unpreconditioned) and of every
  * single bead's; IBPME_PRECOND_NONE iterates on the bare system.
- *   n, x     beads [n][3]; bodies: n_bodies, body_offsets, X (Q is not used)
+ *   n, x     beads [n][3]; bodies: n_bodies, body_offsets, X (Q must point to n_bodies
+ *            doubles, as for the other calls, but its values are not used)
  *   FL       [n_bodies][6] forces and torques (F, L) per body
  *   mu       viscosity (> 0)
  *   opts     rtol (0 -> 1e-6) on ||b - A z|| / ||b||, restart (0 -> 50, <= 200),
